@@ -1,0 +1,142 @@
+"""Constant-traction zone energy and brute-force re-solve (test infrastructure).
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).  Dense FP64 linear
+algebra on tiny periodic grids.
+
+* ``strain_matrix`` writes the strain-displacement map B_p of one material point
+  (6 x 3*nnodes, trilinear shape functions, two points per cell edge), so that
+  eps_p = Ebar + B_p u.
+* ``equilibrium`` minimises the total elastic energy
+  Pi(u) = sum_p 1/2 V (Ebar + B_p u) . C_p (Ebar + B_p u) over the periodic
+  displacement (the quasi-static state the explicit solver of Sec. "Elastic
+  Deformation" seeks), by a dense least-squares solve.
+* ``brute_force_shift`` re-solves the whole domain before and after a trial
+  reorientation and returns the change of Pi: the exact elastic part of
+  [[H]]* that Sec. "Hybrid Monte Carlo Methodology" calls intractable.
+* ``zone_shift`` is the approximation of Eq. 6: a zone Omega_1 (a cube of
+  points around the site, or the whole domain) is re-equilibrated with the
+  forces that the reservoir Omega_2 exerts on its nodes held at their current
+  values (constant traction), and the shift is the change of the zone's energy
+  minus the work of those fixed forces.  For the single-point zone this is
+  Eq. 8 in the constant-traction reading; for the whole domain it is the
+  brute-force shift.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+H = 2.0   # cell edge, voxels
+VP = 1.0  # particle volume
+
+
+def strain_matrix(shape, x, y, z):
+    nz, ny, nx = shape
+    nbx, nby, nbz = nx // 2, ny // 2, nz // 2
+    nn = nbx * nby * nbz
+    B = np.zeros((6, 3 * nn))
+    cx, cy, cz = x // 2, y // 2, z // 2
+    xi = np.array([((x & 1) + 0.5) / H, ((y & 1) + 0.5) / H, ((z & 1) + 0.5) / H])
+    for dk in (0, 1):
+        for dj in (0, 1):
+            for di in (0, 1):
+                n = [xi[0] if di else 1 - xi[0], xi[1] if dj else 1 - xi[1], xi[2] if dk else 1 - xi[2]]
+                s = [(1 if di else -1) / H, (1 if dj else -1) / H, (1 if dk else -1) / H]
+                g = (s[0] * n[1] * n[2], n[0] * s[1] * n[2], n[0] * n[1] * s[2])
+                I = ((cx + di) % nbx) + nbx * (((cy + dj) % nby) + nby * ((cz + dk) % nbz))
+                B[:, 3 * I + 0] += (g[0], 0, 0, 0, g[2], g[1])
+                B[:, 3 * I + 1] += (0, g[1], 0, g[2], 0, g[0])
+                B[:, 3 * I + 2] += (0, 0, g[2], g[1], g[0], 0)
+    return B
+
+
+def all_strain_matrices(shape):
+    nz, ny, nx = shape
+    out = []
+    for z in range(nz):
+        for y in range(ny):
+            for x in range(nx):
+                out.append(strain_matrix(shape, x, y, z))
+    return np.stack(out)  # (N, 6, 3nn), natural point order
+
+
+def assemble(Bs, Cp, Ebar, points=None):
+    """K = sum V B^T C B, F = sum V B^T C Ebar over the chosen points."""
+    idx = range(Bs.shape[0]) if points is None else points
+    n = Bs.shape[2]
+    K = np.zeros((n, n))
+    F = np.zeros(n)
+    for p in idx:
+        BC = Bs[p].T @ Cp[p]
+        K += VP * BC @ Bs[p]
+        F += VP * BC @ Ebar
+    return K, F
+
+
+def energy(Bs, Cp, Ebar, u, points=None):
+    idx = range(Bs.shape[0]) if points is None else points
+    W = 0.0
+    for p in idx:
+        e = Ebar + Bs[p] @ u
+        W += 0.5 * VP * e @ Cp[p] @ e
+    return W
+
+
+def equilibrium(Bs, Cp, Ebar):
+    K, F = assemble(Bs, Cp, Ebar)
+    u, *_ = np.linalg.lstsq(K, -F, rcond=None)
+    return u, energy(Bs, Cp, Ebar, u)
+
+
+def point_stiffness(spins, Ct):
+    return Ct[np.asarray(spins).reshape(-1)]
+
+
+def brute_force_shift(spins, Ct, Ebar, p, q_new, Bs=None):
+    shape = spins.shape
+    Bs = all_strain_matrices(shape) if Bs is None else Bs
+    Cp = point_stiffness(spins, Ct)
+    _, W0 = equilibrium(Bs, Cp, Ebar)
+    Cp2 = Cp.copy()
+    Cp2[p] = Ct[q_new]
+    _, W1 = equilibrium(Bs, Cp2, Ebar)
+    return W1 - W0
+
+
+def zone_points(shape, p, r):
+    """Points of the periodic cube of half-width r around point p (r < 0: all)."""
+    nz, ny, nx = shape
+    if r < 0:
+        return list(range(nx * ny * nz))
+    x, y, z = p % nx, (p // nx) % ny, p // (nx * ny)
+    assert 2 * r + 1 <= min(nx, ny, nz)
+    pts = []
+    for dz in range(-r, r + 1):
+        for dy in range(-r, r + 1):
+            for dx in range(-r, r + 1):
+                pts.append(((x + dx) % nx) + nx * (((y + dy) % ny) + ny * ((z + dz) % nz)))
+    return pts
+
+
+def zone_shift(spins, Ct, Ebar, u0, p, q_new, r, Bs=None):
+    """Eq. 6 for a zone of half-width r around point p (r < 0: whole domain),
+    about the current displacement u0."""
+    shape = spins.shape
+    Bs = all_strain_matrices(shape) if Bs is None else Bs
+    Cp = point_stiffness(spins, Ct)
+    pts = zone_points(shape, p, r)
+    dofs = np.nonzero(np.abs(Bs[pts]).sum(axis=(0, 1)) > 0)[0]
+    # dead forces of the reservoir on the zone's nodes, frozen at the current state
+    g = np.zeros(Bs.shape[2])
+    for s in pts:
+        g += VP * Bs[s].T @ (Cp[s] @ (Ebar + Bs[s] @ u0))
+    W_old = energy(Bs, Cp, Ebar, u0, pts) - g @ u0
+    Cp2 = Cp.copy()
+    Cp2[p] = Ct[q_new]
+    K, F = assemble(Bs, Cp2, Ebar, pts)
+    Kd = K[np.ix_(dofs, dofs)]
+    rhs = (g - F)[dofs]
+    du, *_ = np.linalg.lstsq(Kd, rhs, rcond=None)
+    u1 = u0.copy()
+    u1[dofs] = du
+    W_new = energy(Bs, Cp2, Ebar, u1, pts) - g @ u1
+    return W_new - W_old

@@ -1,0 +1,139 @@
+"""Oracle pins for the explicit MPM stress solve (CPU only)."""
+import numpy as np
+import pytest
+
+import hmc_synth as S
+import oracle as O
+import oracle.zone as Z
+
+C3 = (246.5, 147.3, 124.7)
+
+
+@pytest.fixture(scope="module")
+def poly8():
+    shape = (8, 8, 8)
+    eul = S.euler_uniform_so3(8, 1)
+    sp = S.voronoi_spins(shape, 6, 8, 3)
+    A, Ct, St = O.tables(eul, *C3)
+    Bs = Z.all_strain_matrices(shape)
+    return dict(shape=shape, eul=eul, sp=sp, A=A, Ct=Ct, St=St, Bs=Bs)
+
+
+def test_lumped_mass_is_eight_voxels():
+    m = O.lumped_mass((6, 8, 10))
+    assert np.allclose(m, 8.0, atol=1e-13)
+
+
+def test_strain_of_linear_field_is_exact():
+    """Nodal displacement sampled from a linear field G x gives strain sym(G) at every point."""
+    shape = (6, 8, 4)
+    nz, ny, nx = shape
+    rng = np.random.default_rng(1)
+    G = rng.normal(size=(3, 3)) * 1e-3
+    # a periodic field cannot be linear; use G with the linear part folded into Ebar and u = 0,
+    # plus a checker on u: a single-node displacement produces the trilinear gradient
+    E = np.array([G[0, 0], G[1, 1], G[2, 2], G[1, 2] + G[2, 1], G[0, 2] + G[2, 0], G[0, 1] + G[1, 0]])
+    u = np.zeros(((nx // 2) * (ny // 2) * (nz // 2), 3))
+    for (x, y, z) in [(0, 0, 0), (3, 5, 2), (5, 7, 3)]:
+        assert np.allclose(O.point_strain(shape, u, E, x, y, z), E, atol=1e-18)
+    # unit x-displacement of node (1,1,1): point (2,2,2) sits at xi = 1/4 from it
+    I = 1 + (nx // 2) * (1 + (ny // 2) * 1)
+    u[I, 0] = 1.0
+    e = O.point_strain(shape, u, np.zeros(6), 2, 2, 2)
+    # dN/dx = -(1/h) (1 - 1/4)^2 for the lower corner seen from xi = (1/4,1/4,1/4)
+    assert abs(e[0] - (-(0.5) * 0.75 * 0.75)) < 1e-15
+    assert e[1] == 0 and e[2] == 0 and e[3] == 0
+    assert abs(e[4] - (-(0.5) * 0.75 * 0.75)) < 1e-15 and abs(e[5] - (-(0.5) * 0.75 * 0.75)) < 1e-15
+
+
+def test_force_matches_assembled_stiffness(poly8):
+    rng = np.random.default_rng(0)
+    u = rng.normal(size=(64, 3)) * 1e-3
+    E = rng.normal(size=6) * 1e-3
+    f = O.internal_force(poly8["sp"], poly8["Ct"], u, E)
+    K, F = Z.assemble(poly8["Bs"], Z.point_stiffness(poly8["sp"], poly8["Ct"]), E)
+    assert np.abs(f.ravel() + K @ u.ravel() + F).max() < 1e-13 * np.abs(f).max()
+    assert np.abs(f.sum(axis=0)).max() < 1e-13 * np.abs(f).max()  # no net force (periodic)
+    # the strain map of the C routine and the dense B matrices agree
+    for p in (0, 77, 300, 511):
+        x, y, z = p % 8, (p // 8) % 8, p // 64
+        assert np.allclose(O.point_strain(poly8["shape"], u, E, x, y, z), E + poly8["Bs"][p] @ u.ravel(), atol=1e-16)
+
+
+def test_homogeneous_block_closed_form():
+    """A single orientation under uniaxial control: sigma = eps0 / (n.S'.n) n(x)n at once, u stays 0."""
+    rng = np.random.default_rng(5)
+    for trial in range(3):
+        eul = rng.random((1, 3)) * 6
+        n = rng.normal(size=3)
+        h = O.OracleHMC((6, 6, 6), 1, load_axis=n, strain=1.3e-3, mpm_steps_per_mcs=4)
+        h.set_orientations(eul, np.zeros((6, 6, 6), dtype=np.uint16))
+        h.mpm_steps(7)
+        assert np.abs(h.u).max() < 1e-15
+        sig = h.stress()
+        nn, N, _ = O.axis_vectors(n)
+        s = 1.3e-3 / (N @ h.St[0] @ N)
+        assert np.allclose(sig, s * N[None, :], rtol=0, atol=1e-12 * abs(s))
+        assert abs(h.W - 216 * 0.5 * s * 1.3e-3) < 1e-12 * h.W
+    # along [001] with the workload constants at 1e-3: 0.13631 GPa
+    h = O.OracleHMC((4, 4, 4), 1, load_axis=(0, 0, 1), strain=1e-3)
+    h.set_orientations(np.zeros((1, 3)), np.zeros((4, 4, 4), dtype=np.uint16))
+    assert abs(h.stress()[0, 2] - 0.13631) < 5e-6
+
+
+def test_explicit_step_is_stable(poly8):
+    K, _ = Z.assemble(poly8["Bs"], Z.point_stiffness(poly8["sp"], poly8["Ct"]), np.zeros(6))
+    w_max = np.sqrt(np.linalg.eigvalsh(K / 8.0)[-1])
+    assert w_max * O.default_dt(*C3) < 1.0  # symplectic Euler needs < 2
+
+
+def test_explicit_iteration_reaches_direct_equilibrium(poly8):
+    E = np.array([-3e-4, -4e-4, 1e-3, 1e-4, 0, -2e-4])
+    u_star, W_star = Z.equilibrium(poly8["Bs"], Z.point_stiffness(poly8["sp"], poly8["Ct"]), E)
+    u = np.zeros((64, 3))
+    v = np.zeros((64, 3))
+    O.mpm_steps(poly8["sp"], poly8["Ct"], E, u, v, 2500, 0.1, 0.05)
+    assert np.abs(u.ravel() - u_star).max() < 1e-8 * np.abs(u_star).max()
+    _, _, W = O.stress_field(poly8["sp"], poly8["Ct"], u, E)
+    assert abs(W - W_star) < 1e-9 * W_star
+
+
+def test_effective_modulus_between_reuss_and_voigt(poly8):
+    """Hill: the homogenised uniaxial modulus of the discrete polycrystal lies in its own bounds."""
+    Cp = Z.point_stiffness(poly8["sp"], poly8["Ct"])
+    Ceff = np.zeros((6, 6))
+    for j in range(6):
+        E = np.zeros(6)
+        E[j] = 1e-3
+        u, _ = Z.equilibrium(poly8["Bs"], Cp, E)
+        sig, mean, _ = O.stress_field(poly8["sp"], poly8["Ct"], u.reshape(-1, 3), E)
+        Ceff[:, j] = mean / 1e-3
+    counts = O.orientation_counts(poly8["sp"], 8)
+    f = counts / counts.sum()
+    CV = np.einsum("q,qij->ij", f, poly8["Ct"])
+    SR = O.reuss_compliance(poly8["St"], counts)
+    for n in ([0, 0, 1.0], [1, 1, 1.0], [1, 2, 0.5]):
+        _, N, _ = O.axis_vectors(n)
+        E_eff = 1 / (N @ np.linalg.inv(Ceff) @ N)
+        E_V = 1 / (N @ np.linalg.inv(CV) @ N)
+        E_R = 1 / (N @ SR @ N)
+        assert E_R <= E_eff * (1 + 1e-12) and E_eff <= E_V * (1 + 1e-12)
+        assert E_R < E_V
+
+
+def test_uniaxial_control_converges_to_uniaxial_mean_stress(poly8):
+    Cp = Z.point_stiffness(poly8["sp"], poly8["Ct"])
+    counts = O.orientation_counts(poly8["sp"], 8)
+    SR = O.reuss_compliance(poly8["St"], counts)
+    n = np.array([1.0, 1.0, 1.0])
+    E = O.initial_uniaxial_strain(SR, n, 2e-3)
+    for _ in range(60):
+        u, _ = Z.equilibrium(poly8["Bs"], Cp, E)
+        _, mean, _ = O.stress_field(poly8["sp"], poly8["Ct"], u.reshape(-1, 3), E)
+        E = O.update_uniaxial_strain(E, mean, SR, n, 2e-3)
+    u, _ = Z.equilibrium(poly8["Bs"], Cp, E)
+    _, mean, _ = O.stress_field(poly8["sp"], poly8["Ct"], u.reshape(-1, 3), E)
+    nn, N, Ns = O.axis_vectors(n)
+    assert abs(N @ E - 2e-3) < 1e-15
+    lateral = mean - (Ns @ mean) * N
+    assert np.abs(lateral).max() < 1e-9 * abs(Ns @ mean)

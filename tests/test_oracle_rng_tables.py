@@ -1,0 +1,212 @@
+"""Oracle pins: Philox stream, orientation tables, calibration (CPU only)."""
+import itertools
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from conftest import ROOT, golden
+
+
+def test_philox_known_answers():
+    with open(os.path.join(ROOT, "tests", "golden", "philox4x32_10_kat.txt")) as f:
+        rows = [l.split() for l in f if l.strip() and not l.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        w = [int(x, 16) for x in r]
+        out = O.philox4x32_10(w[0:4], w[4:6])
+        assert out.tolist() == w[6:10]
+
+
+def test_philox_matches_triton_library_routine():
+    """Triton's CPU interpreter implements Philox4x32-10 (counter (c0,0,0,0),
+    key (seed lo, seed hi)); the oracle must agree word for word."""
+    os.environ.setdefault("TRITON_INTERPRET", "1")
+    if os.environ["TRITON_INTERPRET"] != "1":
+        pytest.skip("triton interpreter disabled")
+    tl = pytest.importorskip("triton.language")
+    triton = pytest.importorskip("triton")
+    torch = pytest.importorskip("torch")
+
+    @triton.jit
+    def k(out_ptr, seed, c0_ptr, n: tl.constexpr):
+        offs = tl.arange(0, n)
+        c0 = tl.load(c0_ptr + offs)
+        a, b, c, d = tl.randint4x(seed, c0, 10)
+        tl.store(out_ptr + offs * 4 + 0, a)
+        tl.store(out_ptr + offs * 4 + 1, b)
+        tl.store(out_ptr + offs * 4 + 2, c)
+        tl.store(out_ptr + offs * 4 + 3, d)
+
+    rng = np.random.default_rng(7)
+    seed = int(rng.integers(1, 1 << 62))
+    c0 = rng.integers(0, 1 << 31, size=16).astype(np.int32)
+    out = torch.zeros(64, dtype=torch.int32)
+    try:
+        k[(1,)](out, seed, torch.from_numpy(c0), 16)
+    except Exception as e:  # pragma: no cover - interpreter unavailable on this host
+        pytest.skip(f"triton interpreter unusable: {e}")
+    got = (out.numpy().astype(np.int64) & 0xFFFFFFFF).reshape(16, 4)
+    for i in range(16):
+        ref = O.philox4x32_10([int(c0[i]), 0, 0, 0], [seed & 0xFFFFFFFF, seed >> 32])
+        assert got[i].tolist() == ref.tolist()
+
+
+def test_philox_uniformity():
+    """Bucket counts of the trial word over 60k counters are uniform (chi-square)."""
+    vals = np.array([O.philox4x32_10([i, 3, 0, 0], [11, 0])[0] for i in range(60000)], dtype=np.uint64)
+    b = ((vals * 6) >> 32).astype(np.int64)
+    cnt = np.bincount(b, minlength=6)
+    chi2 = ((cnt - 10000.0) ** 2 / 10000.0).sum()
+    assert chi2 < 25.0  # 5 dof, p ~ 1e-4
+
+
+def _rz(a):
+    c, s = math.cos(a), math.sin(a)
+    return np.array([[c, -s, 0], [s, c, 0], [0, 0, 1.0]])
+
+
+def test_euler_special_cases():
+    A = O.euler_to_A(0.3, 0.0, 0.0)
+    assert np.allclose(A, _rz(0.3), atol=1e-15)
+    A = O.euler_to_A(0.2, 0.0, 0.5)  # two z rotations compose
+    assert np.allclose(A, _rz(0.7), atol=1e-15)
+    A = O.euler_to_A(0.0, math.pi / 2, 0.0)  # y rotation by 90 deg takes z to x
+    assert np.allclose(A @ [0, 0, 1.0], [1, 0, 0], atol=1e-15)
+    rng = np.random.default_rng(1)
+    for _ in range(20):
+        A = O.euler_to_A(*rng.random(3) * 6)
+        assert np.allclose(A @ A.T, np.eye(3), atol=1e-14)
+        assert abs(np.linalg.det(A) - 1) < 1e-14
+
+
+def _cubic_voigt(c11, c12, c44):
+    C = np.zeros((6, 6))
+    C[:3, :3] = c12
+    C[0, 0] = C[1, 1] = C[2, 2] = c11
+    C[3, 3] = C[4, 4] = C[5, 5] = c44
+    return C
+
+
+def _cube_rotations():
+    out = []
+    for perm in itertools.permutations(range(3)):
+        for signs in itertools.product((1, -1), repeat=3):
+            R = np.zeros((3, 3))
+            for i, (p, s) in enumerate(zip(perm, signs)):
+                R[i, p] = s
+            if abs(np.linalg.det(R) - 1) < 1e-12:
+                out.append(R)
+    return out
+
+
+def test_stiffness_identity_and_cube_symmetry():
+    c = (246.5, 147.3, 124.7)
+    ref = _cubic_voigt(*c)
+    rots = _cube_rotations()
+    assert len(rots) == 24
+    for R in rots:
+        assert np.allclose(O.rotated_stiffness(*c, R), ref, atol=1e-12)
+
+
+def test_stiffness_symmetry_and_invariants():
+    c11, c12, c44 = 246.5, 147.3, 124.7
+    rng = np.random.default_rng(2)
+    for _ in range(10):
+        A = O.euler_to_A(*rng.random(3) * 6)
+        Cp = O.rotated_stiffness(c11, c12, c44, A)
+        assert np.allclose(Cp, Cp.T, atol=1e-12)
+        # C'_iijj (bulk) and C'_ijij are rotation invariants
+        assert abs(Cp[:3, :3].sum() - 3 * (c11 + 2 * c12)) < 1e-10
+        assert abs(np.trace(Cp[:3, :3]) + 2 * np.trace(Cp[3:, 3:]) - (3 * c11 + 6 * c44)) < 1e-10
+
+
+def _young_closed_form(c11, c12, c44, l):
+    """1/E = S11 - 2 (S11 - S12 - S44/2)(l1^2 l2^2 + l2^2 l3^2 + l3^2 l1^2), crystal-frame cosines l."""
+    d = (c11 - c12) * (c11 + 2 * c12)
+    S11, S12, S44 = (c11 + c12) / d, -c12 / d, 1.0 / c44
+    J = l[0] ** 2 * l[1] ** 2 + l[1] ** 2 * l[2] ** 2 + l[2] ** 2 * l[0] ** 2
+    return 1.0 / (S11 - 2 * (S11 - S12 - 0.5 * S44) * J)
+
+
+def test_compliance_closed_form_and_young_direction_convention():
+    c11, c12, c44 = 246.5, 147.3, 124.7
+    S = O.invert6(_cubic_voigt(c11, c12, c44))
+    d = (c11 - c12) * (c11 + 2 * c12)
+    assert abs(S[0, 0] - (c11 + c12) / d) < 1e-15
+    assert abs(S[0, 1] + c12 / d) < 1e-15
+    assert abs(S[3, 3] - 1 / c44) < 1e-15
+    rng = np.random.default_rng(3)
+    eul = rng.random((12, 3)) * 6
+    A, Ct, St = O.tables(eul, c11, c12, c44)
+    for q in range(12):
+        assert np.allclose(Ct[q] @ St[q], np.eye(6), atol=1e-12)
+        n = rng.normal(size=3)
+        n /= np.linalg.norm(n)
+        E = O.young_modulus_along(St[q:q + 1], n)[0]
+        # A maps crystal to sample, so the crystal-frame cosines of n are A^T n
+        assert abs(E - _young_closed_form(c11, c12, c44, A[q].T @ n)) < 1e-9 * E
+
+
+def test_young_modulus_matches_paper_fit():
+    g = golden("young_fit_ni.txt")
+    phis = np.arange(0, 91, 5.0)
+    eul = np.stack([np.radians(phis), 0 * phis, 0 * phis], axis=1)
+    _, _, St = O.tables(eul, g["c11"], g["c12"], g["c44"])
+    x = O.young_modulus_along(St, [1, 0, 0]) / g["c11"]
+    fit = g["a"] * np.exp(-(phis - 45) ** 2 / (2 * g["b_deg"] ** 2)) + g["c"]
+    assert np.max(np.abs(x - fit)) < 0.01
+    assert abs(x[0] - g["x_lo"]) < 0.005 and abs(x[9] - g["x_hi"]) < 0.005  # phi = 0 and 45
+    assert np.argmax(x) == 9 and np.argmin(x) in (0, 18)  # 45 deg stiffest, 0/90 softest
+
+
+def test_compliance_cubic_decomposition():
+    """1/2 s.S'.s = 1/2 [S12 tr(s)^2 + S44/2 |s|^2 + (S11-S12-S44/2) sum_m (a_m.s.a_m)^2]."""
+    c11, c12, c44 = 246.5, 147.3, 124.7
+    d = (c11 - c12) * (c11 + 2 * c12)
+    S11, S12, S44 = (c11 + c12) / d, -c12 / d, 1.0 / c44
+    rng = np.random.default_rng(4)
+    A, Ct, St = O.tables(rng.random((6, 3)) * 6, c11, c12, c44)
+    for q in range(6):
+        s = rng.normal(size=6)
+        T = np.array([[s[0], s[5], s[4]], [s[5], s[1], s[3]], [s[4], s[3], s[2]]])
+        phi = sum((A[q][:, m] @ T @ A[q][:, m]) ** 2 for m in range(3))
+        w = 0.5 * (S12 * np.trace(T) ** 2 + 0.5 * S44 * (T * T).sum() + (S11 - S12 - 0.5 * S44) * phi)
+        assert abs(0.5 * s @ St[q] @ s - w) < 1e-14 * max(1, abs(w))
+
+
+def test_calibration_table1():
+    g = golden("calibration_table1.txt")
+    K = int(g["K"])
+    kw = dict(gamma_s=g["gamma_s"], l0=g["l0"], gamma_star=g["gamma_star"])
+    assert abs(O.characteristic_energy(K, **kw) - g["E0"]) < 1e-14 * g["E0"] + 1e-25
+    assert abs(O.characteristic_time(K, m_star=g["m_star"], m_s=g["m_s"], gamma_s=g["gamma_s"], l0=g["l0"])
+               - g["t0"]) < 1e-9
+    # Eq. 13 scale: Delta^3 l0^3 / (2 E0) per J/m^3, i.e. Delta l0 gamma* / (2 gamma_s)
+    lam = O.elastic_scale(32)
+    assert abs(lam - 1e9 * (1 / 32) * 1e-3 * 2.4 / (2 * 0.45)) < 1e-9 * lam
+
+
+def test_polycrystal_modulus_within_uniform_bounds():
+    """The paper's 221 GPa lies between the Reuss and Voigt moduli of an untextured Ni polycrystal."""
+    g = golden("polycrystal_modulus.txt")
+    c11, c12, c44 = g["c11"], g["c12"], g["c44"]
+    # isotropic averages over SO(3) in closed form
+    A = c11 + 2 * c12
+    B = c11 - c12
+    G_V = (B + 3 * c44) / 5
+    K = A / 3
+    G_R = 5 * B * c44 / (4 * c44 + 3 * B)
+    E_V = 9 * K * G_V / (3 * K + G_V)
+    E_R = 9 * K * G_R / (3 * K + G_R)
+    assert E_R < g["E_mpm"] < E_V and E_R < g["E_exp"] < E_V
+    # the sampled bounds of the oracle's tables agree with the closed forms
+    import hmc_synth as S
+    eul = S.euler_uniform_so3(4000, 9)
+    _, Ct, St = O.tables(eul, c11, c12, c44)
+    n = np.array([0, 0, 1.0])
+    Ev = O.young_modulus_along(np.linalg.inv(Ct.mean(axis=0))[None], n)[0]
+    Er = O.young_modulus_along(St.mean(axis=0)[None], n)[0]
+    assert abs(Ev - E_V) < 0.01 * E_V and abs(Er - E_R) < 0.01 * E_R
