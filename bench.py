@@ -1,0 +1,374 @@
+#!/usr/bin/env python
+"""Throughput of the hybrid Monte Carlo hot path on GB300.
+
+One step = one Monte Carlo step (MCS) of the whole hot path on the 256^3
+workload: 50 fused explicit MPM steps, the stress of every point, the red and
+the black half sweep, and the end-of-step reduction / loading update -- one
+replay of the captured CUDA graph behind ``hmc_mc_sweeps``.
+
+Prints ONE JSON line (rank 0):
+  value   site-updates/s of the whole job (every site is visited once per MCS),
+          CUDA events on the library's stream, inputs resident in HBM
+  e2e     the same metric through the C ABI with host buffers: every step
+          uploads the spin field from pinned host memory and reads it back
+  roofline        the dominant kernel (the fused MPM step), ALU-bound (FP32)
+  roofline_sweep  the red/black half sweep, HBM-bound
+  cpu_baseline    the FP64 CPU oracle on a bounded crop of the same workload
+
+``--impl reference`` times the oracle instead (the CPU arm): each step is one
+full oracle MCS on a 64^3 crop of the workload's microstructure.
+
+Multi-GPU (torchrun): every rank runs an independent replica (Philox replica
+id = rank) of the workload -- replicas only, weak scaling, no collective on the
+data path; the timed region is bracketed by barriers and the max time over
+ranks is used.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# FP32 peak of the ALU roofline: 152 SMs x 128 FP32 lanes x 2 flop per FMA x clock
+GB300_SMS, FP32_LANES = 152, 128
+# algorithmic flops of one point in one fused MPM step, separable trilinear form
+# (corner differences, gradient interpolation, strain, 6x6 Hooke, traction sums,
+# force interpolation, corner assembly, node update), FMA = 2 flop
+MPM_FLOP_PER_POINT = 138
+MPM_BYTES_PER_POINT = {"f32": 8, "f64": 14}      # spin 2 + (u,v) read + (u,v) write, per point
+SWEEP_BYTES_PER_SITE = {"f32": 28, "f64": 52}    # spin read + write + stored stress read
+STRESS_BYTES_PER_SITE = {"f32": 27.5, "f64": 53}  # spin 2 + u read (per point) + stress write
+CROP = 64
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="ni256")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), float(p.get("sm_max_mhz", 2070.0)), "measured"
+    except Exception:
+        return 6800.0, 2070.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples every 200 ms during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            d = os.path.join(ROOT, "gpurun_out") if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else None
+            fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv", dir=d)
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def kernel_traffic(kernel):
+    """Per-launch DRAM bytes from the committed ncu summary, if the kernel's
+    source is unchanged since the capture (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    src = {"mpm": "k_mpm.cu", "sweep": "k_sweep.cu"}[kernel]
+    try:
+        sha = hashlib.sha256(open(os.path.join(ROOT, "paper_1009_0457_gb300", "csrc", src), "rb").read()).hexdigest()[:16]
+        for line in open(path):
+            f = line.split()
+            if len(f) >= 4 and not line.startswith("#") and f[0] == kernel and f[1] == sha:
+                return float(f[2])
+    except Exception:
+        pass
+    return None
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def crop_spec(spins, euler):
+    return spins[:CROP, :CROP, :CROP].copy(), euler
+
+
+def oracle_mcs_rate(spec, euler, spins, n_mcs):
+    """site-updates/s of the oracle (FP64, 1 thread) over n_mcs full MCS on a crop."""
+    import oracle as O
+    sp, eul = crop_spec(spins, euler)
+    o = O.OracleHMC(sp.shape, spec["Q"], J=spec["J"], kT=spec["kT"], c11=spec["c11"], c12=spec["c12"],
+                    c44=spec["c44"], load_axis=spec["axis"], strain=spec["strain"],
+                    mpm_steps_per_mcs=spec["mpm_steps"], seed=12345)
+    o.set_orientations(eul, sp)
+    t0 = time.perf_counter()
+    o.mc_sweeps(n_mcs)
+    t = time.perf_counter() - t0
+    return sp.size * n_mcs / t, t, sp.size
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import hmc_synth as S
+    spec, euler, spins = S.workload_inputs(args.workload)
+    import oracle as O
+    sp, eul = crop_spec(spins, euler)
+    o = O.OracleHMC(sp.shape, spec["Q"], J=spec["J"], kT=spec["kT"], c11=spec["c11"], c12=spec["c12"],
+                    c44=spec["c44"], load_axis=spec["axis"], strain=spec["strain"],
+                    mpm_steps_per_mcs=spec["mpm_steps"], seed=12345)
+    o.set_orientations(eul, sp)
+    o.mc_sweeps(args.warmup)
+    t0 = time.perf_counter()
+    o.mc_sweeps(args.steps)
+    t = time.perf_counter() - t0
+    value = sp.size * args.steps / t
+    sample = (f"{CROP}^3 crop ({sp.size} sites) of the {args.workload} microstructure; each step one full "
+              f"oracle MCS ({spec['mpm_steps']} MPM steps, stress, red+black sweep), FP64, 1 thread")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "site-updates/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(spec, args.workload),
+            "cpu_baseline": {"kind": "oracle", "value": value, "unit": "site-updates/s", "cores": 1, "sample": sample},
+            "e2e": {"value": value, "unit": "site-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+METRIC = "HMC site-updates/s and MPM cell-steps/s at 1 GB300; fraction of HBM roofline"
+
+
+def workload_config(spec, name):
+    nz, ny, nx = spec["shape"]
+    return {"workload": f"{name}: {nx}x{ny}x{nz} Ni polycrystal, Q={spec['Q']} orientations uniform on SO(3), "
+                        f"periodic Voronoi of {spec['n_seeds']} grains, uniaxial strain {spec['strain']} along "
+                        f"{list(spec['axis'])} with traction-free sides, J=1, kT=0.7, {spec['mpm_steps']} explicit "
+                        f"MPM steps per MCS, FP32 stress and zone energy, FP64 reductions",
+            "sites": nx * ny * nz, "orientations": spec["Q"], "mpm_steps_per_mcs": spec["mpm_steps"],
+            "l2": "inputs larger than L2 (spins, nodal state and stored stress resident in HBM)"}
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    import hmc_synth as S
+    import paper_1009_0457_gb300 as G
+
+    spec, euler, spins = S.workload_inputs(args.workload)
+    nz, ny, nx = spec["shape"]
+    N = nx * ny * nz
+    stream = torch.cuda.Stream()
+    common = dict(J=spec["J"], kT=spec["kT"], c11=spec["c11"], c12=spec["c12"], c44=spec["c44"],
+                  load_axis=spec["axis"], strain=spec["strain"], mpm_steps_per_mcs=spec["mpm_steps"],
+                  seed=0x5EED0000 + 3, replica=rank, stream=stream.cuda_stream)
+    h = G.HMC(spec["shape"], spec["Q"], precision=G.HMC_FP32, **common)
+    h.set_orientations(euler, spins)
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def tmax(t):
+        if ws > 1:
+            import torch.distributed as dist
+            x = torch.tensor([t], device="cuda", dtype=torch.float64)
+            dist.all_reduce(x, op=dist.ReduceOp.MAX)
+            return float(x.item())
+        return t
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3
+
+    # warm-up (captures the graph)
+    G.lib.hmc_mc_sweeps(h.h, args.warmup, None)
+    h.synchronize()
+
+    # ---- timed region: K MCS --------------------------------------------------
+    clocks = Clocks(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    st = G.lib.hmc_mc_sweeps(h.h, args.steps, None)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    assert st == 0, G.hmc_last_error(h.h)
+    t_local = e0.elapsed_time(e1) / 1e3
+    t = tmax(t_local)
+    value = N * args.steps * ws / t
+    launches = args.steps * (spec["mpm_steps"] + 4)
+
+    # ---- per-kernel timing on the same stream (roofline) ----------------------
+    n_mpm = 50
+    t_mpm = timed(lambda: G.lib.hmc_mpm_steps(h.h, n_mpm, None)) / n_mpm
+    t_stress = timed(lambda: G.lib.hmc_compute_stress(h.h, None, None))
+    t_sweep = [timed(lambda c=c: G.lib.hmc_sweep_half(h.h, c, None)) for c in (0, 1, 0, 1)]
+    t_sweep = statistics.median(t_sweep)
+    hbm, sm_max, peak_src = peaks()
+    fp32_peak = GB300_SMS * FP32_LANES * 2 * sm_max * 1e6 / 1e12
+    mpm_tflops = MPM_FLOP_PER_POINT * N / t_mpm / 1e12
+    sweep_gbs = SWEEP_BYTES_PER_SITE["f32"] * (N / 2) / t_sweep / 1e9
+    roofline = {"kernel": "k_mpm_step<float> (fused explicit MPM step)", "bound": "alu",
+                "achieved": mpm_tflops, "peak": fp32_peak, "unit": "TFLOP/s", "frac": mpm_tflops / fp32_peak,
+                "traffic": kernel_traffic("mpm"),
+                "algorithmic": f"{MPM_FLOP_PER_POINT} flop/point x {N} points per launch",
+                "peak_source": f"derived: {GB300_SMS} SMs x {FP32_LANES} FP32 lanes x 2 flop x {sm_max:.0f} MHz "
+                               f"(max SM clock, {peak_src})",
+                "hbm_view": {"achieved_gbs": MPM_BYTES_PER_POINT["f32"] * N / t_mpm / 1e9, "peak": hbm,
+                             "frac": MPM_BYTES_PER_POINT["f32"] * N / t_mpm / 1e9 / hbm}}
+    roofline_sweep = {"kernel": "k_sweep<float, elastic> (red/black half sweep)", "bound": "hbm",
+                      "achieved": sweep_gbs, "peak": hbm, "unit": "GB/s", "frac": sweep_gbs / hbm,
+                      "traffic": kernel_traffic("sweep"),
+                      "algorithmic": f"{SWEEP_BYTES_PER_SITE['f32']} B/site x {N // 2} sites per launch",
+                      "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_src})"}
+
+    # ---- end to end through the C ABI with host buffers -----------------------
+    pin_in = torch.from_numpy(spins.reshape(-1).view(np.int16)).pin_memory()
+    pin_out = torch.empty(N, dtype=torch.int16).pin_memory()
+    a_in = pin_in.numpy().view(np.uint16)
+    a_out = pin_out.numpy().view(np.uint16)
+    e2e_steps = max(1, min(args.steps, 5))
+    for _ in range(1):
+        G.hmc_set_spins(h.h, a_in)
+        G.lib.hmc_mc_sweeps(h.h, 1, None)
+        G.hmc_get_spins(h.h, a_out)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        G.hmc_set_spins(h.h, a_in)
+        G.lib.hmc_mc_sweeps(h.h, 1, None)
+        G.hmc_get_spins(h.h, a_out)
+    torch.cuda.synchronize()
+    t_e2e = tmax(time.perf_counter() - t0)
+    e2e = {"value": N * e2e_steps * ws / t_e2e, "unit": "site-updates/s", "h2d_bytes_per_step": 2 * N,
+           "d2h_bytes_per_step": 2 * N, "steps": e2e_steps,
+           "path": "hmc_set_spins(pinned host) + hmc_mc_sweeps(1) + hmc_get_spins(pinned host), wall clock"}
+
+    # ---- plain FP64 form on the same GPU --------------------------------------
+    fp64 = None
+    if not args.no_fp64:
+        h64 = G.HMC(spec["shape"], spec["Q"], precision=G.HMC_FP64, **common)
+        h64.set_orientations(euler, spins)
+        G.lib.hmc_mc_sweeps(h64.h, 1, None)
+        h64.synchronize()
+        k64 = 2
+        t64 = timed(lambda: G.lib.hmc_mc_sweeps(h64.h, k64, None))
+        t64_mpm = timed(lambda: G.lib.hmc_mpm_steps(h64.h, 5, None)) / 5
+        v64 = N * k64 / t64
+        fp64 = {"value": v64, "unit": "site-updates/s", "steps": k64, "speedup_fp32_over_fp64": value / ws / v64,
+                "mpm_cell_steps_per_s": N / t64_mpm, "mpm_ms_per_step": t64_mpm * 1e3}
+        h64.close()
+
+    # ---- CPU oracle on the host cores (rank 0, one GPU only) ------------------
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        v, tt, n = oracle_mcs_rate(spec, euler, spins, 1)
+        cpu = {"kind": "oracle", "value": v, "unit": "site-updates/s", "cores": 1,
+               "sample": f"{CROP}^3 crop ({n} sites) of the workload's microstructure, one full MCS "
+                         f"({spec['mpm_steps']} MPM steps, stress, red+black sweep), FP64, {tt:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "site-updates/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(spec, args.workload),
+            "mpm_cell_steps_per_s": N * ws / t_mpm, "mpm_ms_per_step": t_mpm * 1e3,
+            "stress_ms": t_stress * 1e3, "half_sweep_ms": t_sweep * 1e3,
+            "roofline": roofline, "roofline_sweep": roofline_sweep,
+            "e2e": e2e, "gpu_launches": launches, "clocks": clk, "fp64_form": fp64, "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    h.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,216 @@
+/*
+ * hmc.h -- C ABI of the GB300 (sm_103a) hybrid Monte Carlo library.
+ *
+ * Method: Zhang, Bartel & Lusk, "Parallelized Hybrid Monte Carlo Simulation of
+ * Stress-Induced Texture Evolution".  A Q-state Potts model of grain
+ * orientations on a periodic nx x ny x nz voxel lattice (Sec. "Hybrid Monte
+ * Carlo Methodology", Eq. 4) evolves by red/black checkerboard Metropolis
+ * sweeps (Sec. "Microstructural Evolution"; Eq. 5).  Each trial's energy change
+ * is the bond-energy change plus the elastic shift of a one-point
+ * constant-traction zone (Eqs. 6-8), scaled to MC units by Eq. 13.  The stress
+ * comes from a time-explicit material point method (MPM) run towards the
+ * quasi-static state before every Monte Carlo step (Sec. "Elastic
+ * Deformation"; the loading schedule of Sec. "Results": equilibrate, then one
+ * Monte Carlo step).
+ *
+ * Conventions shared by every entry point:
+ *  - Host arrays passed in are caller-owned, read during the call and not
+ *    retained.  Host arrays passed out are caller-allocated with the stated
+ *    sizes.  The handle owns all device memory it uses.
+ *  - Site arrays are in natural order, x fastest: p = x + nx*(y + ny*z).
+ *    Node arrays (the MPM background mesh, one node per 2x2x2 voxel cell) are
+ *    in natural order of nodes: I = i + (nx/2)*(j + (ny/2)*k), 3 values per
+ *    node (x,y,z).  Tensors are Voigt (11,22,33,23,13,12); strains carry
+ *    engineering shear, stresses tensor components.  Stress unit: GPa.
+ *  - Work is ordered on the handle's stream.  Calls that return values to the
+ *    host synchronise that stream before returning.
+ *  - Every call returns an hmc_status; no C++ exception crosses the ABI.  A
+ *    failed call leaves the handle valid; hmc_last_error() describes the
+ *    failure.  CUDA errors map to HMC_ERR_CUDA, allocation failures to
+ *    HMC_ERR_OOM, calls before hmc_set_orientations to HMC_ERR_STATE.
+ */
+#ifndef HMC_H_
+#define HMC_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hmc_handle hmc_handle;
+
+typedef enum {
+    HMC_OK = 0,
+    HMC_ERR_ARG = -1,
+    HMC_ERR_CUDA = -2,
+    HMC_ERR_OOM = -3,
+    HMC_ERR_STATE = -4,
+    HMC_ERR_NONFINITE = -5,
+    HMC_ERR_TIMEOUT = -6
+} hmc_status;
+
+/* Loading control.  UNIAXIAL: the mean strain along load_axis is held at
+ * `strain` and the other five mean stresses are driven to zero once per
+ * Monte Carlo step (traction-free sides of a periodic cell).  STRAIN6: all six
+ * mean strain components are prescribed by `strain6`. */
+enum { HMC_BC_UNIAXIAL = 0, HMC_BC_STRAIN6 = 1 };
+/* Elastic term of the trial energy: off (pure Potts) or the one-point
+ * constant-traction zone shift w(q_old) - w(q_new), w(q) = 1/2 s.S'(q).s. */
+enum { HMC_ELASTIC_OFF = 0, HMC_ELASTIC_TRACTION = 1 };
+/* Trial orientation: copy a random one of the six neighbours, or draw
+ * uniformly from 0..Q-1. */
+enum { HMC_TRIAL_NEIGHBOR = 0, HMC_TRIAL_UNIFORM_Q = 1 };
+/* Arithmetic of the MPM step, the stress and the zone energy. */
+enum { HMC_FP64 = 0, HMC_FP32 = 1 };
+/* Texture measures of hmc_texture_histogram. */
+enum { HMC_HIST_PER_Q = 0, HMC_HIST_ANGLE_100 = 1, HMC_HIST_YOUNG = 2 };
+
+typedef struct {
+    int32_t nx, ny, nz;          /* voxels per edge; even, >= 4; periodic            */
+    int32_t n_orient;            /* Q, 1..65535                                       */
+    double J, kT;                /* Potts bond energy and MC temperature (alpha=kT/J) */
+    double c11, c12, c44;        /* cubic stiffness of the crystal frame, GPa         */
+    int32_t bc;                  /* HMC_BC_*                                          */
+    double load_axis[3];         /* UNIAXIAL load direction (normalised here)         */
+    double strain;               /* UNIAXIAL strain along load_axis                   */
+    double strain6[6];           /* STRAIN6 mean strain (Voigt, engineering shear)    */
+    double elastic_scale;        /* lambda: MC energy per GPa of energy density;
+                                    < 0 selects the calibration of Eqs. 11-13 with
+                                    the Table 1 constants and Delta = 1/max(nx,ny,nz) */
+    int32_t elastic;             /* HMC_ELASTIC_*                                     */
+    int32_t trial;               /* HMC_TRIAL_*                                       */
+    int32_t mpm_steps_per_mcs;   /* explicit MPM steps before each MC step, >= 0     */
+    double dt;                   /* explicit time step; <= 0 selects 0.5 h / c_max   */
+    double damping;              /* velocity damping per step; < 0 selects 0.05       */
+    int32_t precision;           /* HMC_FP64 | HMC_FP32                               */
+    uint64_t seed;               /* Philox key of the trial stream                    */
+    uint32_t replica;            /* third Philox counter word (ensemble member)       */
+    void *stream;                /* cudaStream_t for all work; NULL = library-owned   */
+} hmc_params;
+
+/* Scalars the library derived from the parameters, and its counters. */
+typedef struct {
+    double dt, damping, elastic_scale;
+    double strain_bar[6];        /* current mean strain Ebar                          */
+    uint32_t mcs;                /* Monte Carlo steps completed (Philox word 1)       */
+    int32_t u_buffer;            /* which displacement buffer holds the current state */
+    int64_t n_sites, n_nodes;
+} hmc_info;
+
+/* Fill *p with defaults: 32^3, Q = 64, J = 1, kT = 0.7, Ni constants
+ * 246.5/147.3/124.7 GPa, uniaxial 1e-3 along z, calibrated lambda, traction
+ * shift, neighbour trials, 50 MPM steps per MCS, default dt and damping,
+ * FP32, seed 1, replica 0, library stream. */
+void hmc_default_params(hmc_params *p);
+
+/* Create a handle for one replica.  Validates *p (HMC_ERR_ARG on odd or small
+ * edges, Q out of range, bad enums, non-finite constants, singular stiffness)
+ * and allocates every device buffer for the grid.  *out is NULL on failure. */
+hmc_status hmc_create(const hmc_params *p, hmc_handle **out);
+
+/* Release the handle and all its device memory (NULL is a no-op). */
+void hmc_destroy(hmc_handle *h);
+
+/* Orientation table and initial spin field (Sec. "Elastic Deformation",
+ * Eqs. 16-18; Sec. "Results", random initial orientations).
+ *   euler_zyz: Q x 3 doubles (phi, theta, psi), radians; A = Rz(phi) Ry(theta)
+ *              Rz(psi) maps crystal-frame vectors to the sample frame.
+ *   spins:     N = nx*ny*nz orientation indices 0..Q-1, natural order.
+ * Builds the rotated stiffness C'(q) (Voigt 6x6) and the zone-energy table in
+ * FP64 on the host, uploads them and the spins, zeroes the nodal displacement
+ * and velocity, resets the MC step counter to 0, and sets the mean strain
+ * (UNIAXIAL: strain / (n.S_R.n) S_R:(n(x)n) with S_R the Reuss compliance of
+ * these spins; STRAIN6: strain6).  HMC_ERR_ARG if a spin is >= Q or an angle
+ * is not finite. */
+hmc_status hmc_set_orientations(hmc_handle *h, const double *euler_zyz, const uint16_t *spins);
+
+/* Replace the spin field only (N values, natural order, each < Q); tables,
+ * nodal state, mean strain and counters are kept. */
+hmc_status hmc_set_spins(hmc_handle *h, const uint16_t *spins);
+
+/* Copy the spin field out (N values, natural order). */
+hmc_status hmc_get_spins(hmc_handle *h, uint16_t *spins);
+
+/* nsteps explicit MPM steps (Sec. "Elastic Deformation"): per material point
+ * strain = Ebar + sym(grad u) from the trilinear nodal field, stress =
+ * C'(q) strain (Eq. 1), internal nodal force -sum_p V sigma_p.gradN, then
+ * v <- (1 - damping) v + dt f / m and u <- u + dt v on the periodic mesh.
+ * If elastic_energy is not NULL, the stress of the final state is computed
+ * (as hmc_compute_stress) and its elastic energy written there. */
+hmc_status hmc_mpm_steps(hmc_handle *h, int32_t nsteps, double *elastic_energy);
+
+/* Stress of every point from the current displacement, stored on the device
+ * for the sweeps; optionally returns the mean stress (6) and the elastic
+ * energy sum_p 1/2 sigma_p.eps_p (one voxel volume per point), each reduced
+ * in FP64 across the domain.  Either pointer may be NULL. */
+hmc_status hmc_compute_stress(hmc_handle *h, double *mean_stress, double *elastic_energy);
+
+/* One red/black half sweep (Sec. "Microstructural Evolution"): every site of
+ * `colour` ((x+y+z) even = 0 = red) draws Philox4x32-10 with counter
+ * (site, mcs, replica, 0) and key seed, picks a trial orientation, and is
+ * accepted by Eq. 5 on J*(change of unlike-neighbour count) plus lambda times
+ * the stored-stress zone shift.  The MC step counter is not advanced.
+ * *accepted (nullable) receives the number of sites that changed. */
+hmc_status hmc_sweep_half(hmc_handle *h, int32_t colour, int64_t *accepted);
+
+/* Close a Monte Carlo step: with UNIAXIAL control update the mean strain from
+ * the mean stress of the last hmc_compute_stress, then advance the counter. */
+hmc_status hmc_end_mcs(hmc_handle *h);
+
+/* n_mcs Monte Carlo steps, each: mpm_steps_per_mcs MPM steps, stress, red
+ * half sweep, black half sweep (stress frozen over the step), end of step.
+ * Replayed from a captured CUDA graph.  *accepted (nullable) receives the
+ * number of spin changes over all n_mcs steps. */
+hmc_status hmc_mc_sweeps(hmc_handle *h, int32_t n_mcs, int64_t *accepted);
+
+/* Texture of the current spin field (Sec. "Results").  counts_per_q (Q int64,
+ * nullable): volume of each orientation, summing exactly to N.  fractions
+ * (nbins doubles, nullable) by kind: PER_Q: nbins = Q, counts / N;
+ * ANGLE_100: angle between the load axis and the nearest crystal <100> in
+ * bins of 90/nbins degrees; YOUNG: E(load axis)/c11 in nbins equal bins
+ * between the <100> and <111> moduli.  Counts are int64, fractions FP64. */
+hmc_status hmc_texture_histogram(hmc_handle *h, int32_t kind, int32_t nbins, double *fractions,
+                                 int64_t *counts_per_q);
+
+/* Statistics of the current state: number of unlike nearest-neighbour bonds
+ * (each counted once, int64; the bond energy is J times it), elastic energy and
+ * mean stress (6) from the stored stress (FP64).  Any pointer may be NULL. */
+hmc_status hmc_energy(hmc_handle *h, int64_t *unlike_bonds, double *elastic_energy, double *mean_stress);
+
+/* Stored stress of every point (N x 6 doubles, natural order), i.e. the
+ * stress the next half sweeps read.  hmc_set_stress replaces it (rounded to
+ * the handle's precision), so that a sweep can be run on a given stress. */
+hmc_status hmc_get_stress(hmc_handle *h, double *sigma);
+hmc_status hmc_set_stress(hmc_handle *h, const double *sigma);
+
+/* Nodal displacement and velocity (nnodes x 3 doubles each; either NULL). */
+hmc_status hmc_get_nodal(hmc_handle *h, double *u, double *v);
+hmc_status hmc_set_nodal(hmc_handle *h, const double *u, const double *v);
+
+/* Mean strain Ebar (6, Voigt engineering). */
+hmc_status hmc_get_strain(hmc_handle *h, double *strain_bar);
+hmc_status hmc_set_strain(hmc_handle *h, const double *strain_bar);
+
+/* Derived scalars and counters. */
+hmc_status hmc_get_info(hmc_handle *h, hmc_info *info);
+
+/* Checkpoint: spins, nodal u and v, mean strain and the MC step counter.  With
+ * buf == NULL, *bytes receives the size; otherwise *bytes must be at least
+ * that size.  The counter-based stream makes a resumed run bit-identical. */
+hmc_status hmc_get_state(hmc_handle *h, void *buf, size_t *bytes);
+hmc_status hmc_set_state(hmc_handle *h, const void *buf, size_t bytes);
+
+/* Wait for all work on the handle's stream. */
+hmc_status hmc_synchronize(hmc_handle *h);
+
+/* Message of the last failed call on h (or of the last failed hmc_create when
+ * h is NULL).  Valid until the next call on the same handle. */
+const char *hmc_last_error(const hmc_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HMC_H_ */

@@ -1,0 +1,906 @@
+// C ABI of libhmc (declared and documented in include/hmc.h): handle lifetime,
+// host-side orientation tables in FP64, device buffers, and the stream order of
+// the Monte Carlo step.  Host code only; the kernels live in k_*.cu.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "hmc.h"
+#include "hmc_internal.h"
+
+using hmc::DevState;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+// Table 1 constants of the calibration (Sec. "Results") used for the default lambda.
+constexpr double kGammaStar = 2.4, kGammaS = 0.45, kL0 = 1.0e-3;
+
+int slot_local_h(int s) { static const int t[8] = {0, 3, 5, 6, 1, 2, 4, 7}; return t[s]; }
+
+}  // namespace
+
+struct hmc_handle {
+    hmc_params p{};
+    int nbx = 0, nby = 0, nbz = 0;
+    long long nblk = 0, N = 0, nnodes = 0;
+    cudaStream_t stream = nullptr, cap = nullptr;
+    bool own_stream = false, oriented = false;
+    int num_sms = 0, zc = 4, nparts = 0;
+    size_t tsize = 4;
+    // device buffers
+    uint4 *spins = nullptr;
+    uint16_t *stage16 = nullptr;
+    void *u[2] = {nullptr, nullptr};
+    void *v = nullptr;
+    int cur = 0;
+    void *sig = nullptr, *ctab = nullptr, *wtab = nullptr;
+    unsigned long long *thr = nullptr, *counts = nullptr, *bins = nullptr;
+    double *partials = nullptr, *fractions = nullptr;
+    int32_t *binmap = nullptr;
+    int bins_cap = 0;
+    DevState *st = nullptr;
+    // derived scalars
+    double dt = 0, damping = 0, lam = 0, lam_sd_half = 0, S11 = 0, S12 = 0, S44 = 0;
+    double axis[3] = {0, 0, 1};
+    // host tables (FP64)
+    std::vector<double> A, Cv, Sv;
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    std::string err;
+};
+
+namespace {
+
+hmc_status fail(hmc_handle *h, hmc_status s, const std::string &msg) {
+    if (h)
+        h->err = msg;
+    else
+        g_create_error = msg;
+    return s;
+}
+
+hmc_status cuda_fail(hmc_handle *h, cudaError_t e, const char *what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return fail(h, e == cudaErrorMemoryAllocation ? HMC_ERR_OOM : HMC_ERR_CUDA, m);
+}
+
+#define HMC_CK(h, call, what)                             \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return cuda_fail(h, e_, what); \
+    } while (0)
+
+// ---- FP64 host tables -------------------------------------------------------
+
+// A = Rz(phi) Ry(theta) Rz(psi) written out in closed form (Eq. 18, z-y-z angles).
+void euler_zyz(double phi, double theta, double psi, double *A) {
+    const double cf = std::cos(phi), sf = std::sin(phi), ct = std::cos(theta), st = std::sin(theta);
+    const double cp = std::cos(psi), sp = std::sin(psi);
+    A[0] = cf * ct * cp - sf * sp; A[1] = -cf * ct * sp - sf * cp; A[2] = cf * st;
+    A[3] = sf * ct * cp + cf * sp; A[4] = -sf * ct * sp + cf * cp; A[5] = sf * st;
+    A[6] = -st * cp;               A[7] = st * sp;                 A[8] = ct;
+}
+
+const int VI[6] = {0, 1, 2, 1, 0, 0}, VJ[6] = {0, 1, 2, 2, 2, 1};
+
+// Bond matrices of a rotation (Bond 1943): stress sigma' = M sigma, engineering
+// strain eps' = Ns eps; then C' = M C M^T and S' = Ns S Ns^T (Eq. 17 in 6x6 form).
+void bond(const double *A, double *M, double *Ns) {
+    for (int I = 0; I < 6; ++I)
+        for (int J = 0; J < 6; ++J) {
+            const int i = VI[I], j = VJ[I], k = VI[J], l = VJ[J];
+            const double a = A[3 * i + k] * A[3 * j + l], b = A[3 * i + l] * A[3 * j + k];
+            M[6 * I + J] = (k == l) ? a : a + b;
+            const double fi = (I < 3) ? 1.0 : 2.0;
+            Ns[6 * I + J] = fi * ((k == l) ? a : 0.5 * (a + b));
+        }
+}
+
+void congruence(const double *M, const double *X, double *out) {  // M X M^T
+    double t[36];
+    for (int i = 0; i < 6; ++i)
+        for (int j = 0; j < 6; ++j) {
+            double s = 0;
+            for (int k = 0; k < 6; ++k) s += M[6 * i + k] * X[6 * k + j];
+            t[6 * i + j] = s;
+        }
+    for (int i = 0; i < 6; ++i)
+        for (int j = 0; j < 6; ++j) {
+            double s = 0;
+            for (int k = 0; k < 6; ++k) s += t[6 * i + k] * M[6 * j + k];
+            out[6 * i + j] = s;
+        }
+}
+
+template <typename T>
+std::vector<T> pack_ctab(const std::vector<double> &Cv, int Q) {
+    std::vector<T> out((size_t)Q * 24, T(0));
+    for (int q = 0; q < Q; ++q) {
+        int n = 0;
+        for (int i = 0; i < 6; ++i)
+            for (int j = i; j < 6; ++j) out[(size_t)q * 24 + n++] = (T)Cv[(size_t)q * 36 + 6 * i + j];
+    }
+    return out;
+}
+
+template <typename T>
+std::vector<T> pack_wtab(const std::vector<double> &A, int Q) {
+    std::vector<T> out((size_t)Q * 20, T(0));
+    for (int q = 0; q < Q; ++q)
+        for (int m = 0; m < 3; ++m) {
+            const double *a = &A[(size_t)q * 9];
+            const double a1 = a[0 * 3 + m], a2 = a[1 * 3 + m], a3 = a[2 * 3 + m];
+            T *w = &out[(size_t)q * 20 + 6 * m];
+            w[0] = (T)(a1 * a1); w[1] = (T)(a2 * a2); w[2] = (T)(a3 * a3);
+            w[3] = (T)(2 * a2 * a3); w[4] = (T)(2 * a1 * a3); w[5] = (T)(2 * a1 * a2);
+        }
+    return out;
+}
+
+void axis_vectors(const double *n, double *N, double *Nsv) {
+    N[0] = n[0] * n[0]; N[1] = n[1] * n[1]; N[2] = n[2] * n[2];
+    N[3] = n[1] * n[2]; N[4] = n[0] * n[2]; N[5] = n[0] * n[1];
+    for (int i = 0; i < 6; ++i) Nsv[i] = (i < 3) ? N[i] : 2 * N[i];
+}
+
+// ---- launches ---------------------------------------------------------------
+
+template <typename T>
+cudaError_t enqueue_mpm(hmc_handle *h, cudaStream_t s) {
+    hmc::MpmArgs<T> a;
+    a.spins = h->spins;
+    a.u_in = static_cast<const T *>(h->u[h->cur]);
+    a.u_out = static_cast<T *>(h->u[h->cur ^ 1]);
+    a.v = static_cast<T *>(h->v);
+    a.ctab = static_cast<const T *>(h->ctab);
+    a.st = h->st;
+    a.nbx = h->nbx; a.nby = h->nby; a.nbz = h->nbz; a.zc = h->zc;
+    a.dt = (T)h->dt;
+    a.dt_over_m = (T)(h->dt / 8.0);  // lumped mass rho * V * sum_p N_I(x_p) = 8 voxels
+    a.keep = (T)(1.0 - h->damping);
+    cudaError_t e = hmc::launch_mpm_step<T>(a, s);
+    h->cur ^= 1;
+    return e;
+}
+
+template <typename T>
+cudaError_t enqueue_stress(hmc_handle *h, cudaStream_t s) {
+    hmc::StressArgs<T> a;
+    a.spins = h->spins;
+    a.u = static_cast<const T *>(h->u[h->cur]);
+    a.ctab = static_cast<const T *>(h->ctab);
+    a.st = h->st;
+    a.sig = static_cast<T *>(h->sig);
+    a.partials = h->partials;
+    a.nbx = h->nbx; a.nby = h->nby; a.nbz = h->nbz;
+    a.nblk = h->nblk;
+    return hmc::launch_stress<T>(a, h->nparts, s);
+}
+
+template <typename T>
+cudaError_t enqueue_sweep(hmc_handle *h, int colour, cudaStream_t s) {
+    hmc::SweepArgs<T> a;
+    a.spins = h->spins;
+    a.sig = static_cast<const T *>(h->sig);
+    a.wtab = static_cast<const T *>(h->wtab);
+    a.thr = h->thr;
+    a.st = h->st;
+    a.nx = h->p.nx; a.ny = h->p.ny; a.nz = h->p.nz;
+    a.nbx = h->nbx; a.nby = h->nby; a.nbz = h->nbz;
+    a.nblk = h->nblk;
+    a.key0 = (uint32_t)(h->p.seed & 0xffffffffull);
+    a.key1 = (uint32_t)(h->p.seed >> 32);
+    a.replica = h->p.replica;
+    a.trial = h->p.trial;
+    a.nq = h->p.n_orient;
+    a.J = (T)h->p.J;
+    a.kT = (T)h->p.kT;
+    a.lam_sd_half = (T)h->lam_sd_half;
+    return hmc::launch_sweep<T>(a, colour, h->p.elastic == HMC_ELASTIC_TRACTION, s);
+}
+
+cudaError_t enq_mpm(hmc_handle *h, cudaStream_t s) {
+    return h->p.precision == HMC_FP32 ? enqueue_mpm<float>(h, s) : enqueue_mpm<double>(h, s);
+}
+cudaError_t enq_stress(hmc_handle *h, cudaStream_t s) {
+    return h->p.precision == HMC_FP32 ? enqueue_stress<float>(h, s) : enqueue_stress<double>(h, s);
+}
+cudaError_t enq_sweep(hmc_handle *h, int c, cudaStream_t s) {
+    return h->p.precision == HMC_FP32 ? enqueue_sweep<float>(h, c, s) : enqueue_sweep<double>(h, c, s);
+}
+
+// One Monte Carlo step on stream s (also used while capturing the graph).
+cudaError_t enqueue_mcs(hmc_handle *h, cudaStream_t s) {
+    cudaError_t e;
+    for (int k = 0; k < h->p.mpm_steps_per_mcs; ++k)
+        if ((e = enq_mpm(h, s)) != cudaSuccess) return e;
+    if ((e = enq_stress(h, s)) != cudaSuccess) return e;
+    if ((e = enq_sweep(h, 0, s)) != cudaSuccess) return e;
+    if ((e = enq_sweep(h, 1, s)) != cudaSuccess) return e;
+    return hmc::launch_end_mcs(h->st, h->partials, h->nparts, h->N, 1, 1, s);
+}
+
+hmc_status need_oriented(hmc_handle *h) {
+    if (!h) return HMC_ERR_ARG;
+    if (!h->oriented) return fail(h, HMC_ERR_STATE, "hmc_set_orientations has not been called");
+    return HMC_OK;
+}
+
+// Copy a natural-order spin field to the device, check every index < Q there
+// (the handle's field is untouched if one is not), then pack it into blocks.
+hmc_status upload_spins(hmc_handle *h, const uint16_t *spins) {
+    int bad = 0;
+    HMC_CK(h, cudaMemcpyAsync(h->stage16, spins, sizeof(uint16_t) * h->N, cudaMemcpyHostToDevice, h->stream), "spin upload");
+    HMC_CK(h, cudaMemsetAsync(&h->st->bad_spin, 0, sizeof(int32_t), h->stream), "memset");
+    HMC_CK(h, hmc::launch_check_spins(h->stage16, h->N, h->p.n_orient, h->st, h->stream), "spin check");
+    HMC_CK(h, cudaMemcpyAsync(&bad, &h->st->bad_spin, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream), "download");
+    HMC_CK(h, cudaStreamSynchronize(h->stream), "sync");
+    if (bad) {
+        for (long long i = 0; i < h->N; ++i)
+            if (spins[i] >= (uint32_t)h->p.n_orient)
+                return fail(h, HMC_ERR_ARG, "spin value >= n_orient at site " + std::to_string(i));
+        return fail(h, HMC_ERR_ARG, "spin value >= n_orient");
+    }
+    HMC_CK(h, hmc::launch_pack_spins(h->stage16, h->spins, h->p.nx, h->p.ny, h->p.nz, h->stream), "pack spins");
+    return HMC_OK;
+}
+
+std::string validate(const hmc_params *p) {
+    if (!p) return "params is NULL";
+    auto even = [](int n) { return n >= 4 && n % 2 == 0; };
+    if (!even(p->nx) || !even(p->ny) || !even(p->nz)) return "grid edges must be even and >= 4";
+    if ((long long)p->nx * p->ny * p->nz > (1ll << 32) - 1) return "grid larger than 2^32 - 1 sites";
+    if (p->n_orient < 1 || p->n_orient > 65535) return "n_orient must be in 1..65535";
+    const double vals[] = {p->J, p->kT, p->c11, p->c12, p->c44, p->strain, p->dt, p->damping, p->elastic_scale};
+    for (double x : vals)
+        if (!std::isfinite(x)) return "non-finite parameter";
+    if (p->kT < 0) return "kT must be >= 0";
+    if (p->bc != HMC_BC_UNIAXIAL && p->bc != HMC_BC_STRAIN6) return "bad bc";
+    if (p->elastic != HMC_ELASTIC_OFF && p->elastic != HMC_ELASTIC_TRACTION) return "bad elastic";
+    if (p->trial != HMC_TRIAL_NEIGHBOR && p->trial != HMC_TRIAL_UNIFORM_Q) return "bad trial";
+    if (p->precision != HMC_FP32 && p->precision != HMC_FP64) return "bad precision";
+    if (p->mpm_steps_per_mcs < 0) return "mpm_steps_per_mcs must be >= 0";
+    if (p->damping >= 1.0) return "damping must be < 1";
+    // cubic stability: C11 - C12 > 0, C11 + 2 C12 > 0, C44 > 0
+    if (!(p->c11 - p->c12 > 0 && p->c11 + 2 * p->c12 > 0 && p->c44 > 0)) return "stiffness not positive definite";
+    if (p->bc == HMC_BC_UNIAXIAL) {
+        const double n2 = p->load_axis[0] * p->load_axis[0] + p->load_axis[1] * p->load_axis[1] + p->load_axis[2] * p->load_axis[2];
+        if (!(n2 > 0) || !std::isfinite(n2)) return "load_axis must be a non-zero finite vector";
+    }
+    for (int i = 0; i < 6; ++i)
+        if (!std::isfinite(p->strain6[i])) return "non-finite strain6";
+    return "";
+}
+
+void destroy_buffers(hmc_handle *h) {
+    for (int i = 0; i < 2; ++i)
+        if (h->gexec[i]) cudaGraphExecDestroy(h->gexec[i]);
+    void *bufs[] = {h->spins, h->stage16, h->u[0], h->u[1], h->v, h->sig, h->ctab, h->wtab, h->thr, h->counts,
+                    h->bins, h->partials, h->fractions, h->binmap, h->st};
+    for (void *b : bufs)
+        if (b) cudaFree(b);
+    if (h->cap) cudaStreamDestroy(h->cap);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+}
+
+template <typename T>
+void unpack_stress_host(const hmc_handle *h, const std::vector<T> &packed, double *out) {
+    const int nx = h->p.nx, ny = h->p.ny;
+    for (long long b = 0; b < h->nblk; ++b) {
+        const int bx = (int)(b % h->nbx);
+        const long long r = b / h->nbx;
+        const int by = (int)(r % h->nby), bz = (int)(r / h->nby);
+        for (int s = 0; s < 8; ++s) {
+            const int L = slot_local_h(s), c = s >> 2, i = s & 3;
+            const long long x = 2 * bx + (L & 1), y = 2 * by + ((L >> 1) & 1), z = 2 * bz + (L >> 2);
+            const long long p = x + nx * (y + (long long)ny * z);
+            for (int k = 0; k < 6; ++k) out[6 * p + k] = (double)packed[4 * ((size_t)(c * 6 + k) * h->nblk + b) + i];
+        }
+    }
+}
+
+template <typename T>
+void pack_stress_host(const hmc_handle *h, const double *in, std::vector<T> &packed) {
+    const int nx = h->p.nx, ny = h->p.ny;
+    for (long long b = 0; b < h->nblk; ++b) {
+        const int bx = (int)(b % h->nbx);
+        const long long r = b / h->nbx;
+        const int by = (int)(r % h->nby), bz = (int)(r / h->nby);
+        for (int s = 0; s < 8; ++s) {
+            const int L = slot_local_h(s), c = s >> 2, i = s & 3;
+            const long long x = 2 * bx + (L & 1), y = 2 * by + ((L >> 1) & 1), z = 2 * bz + (L >> 2);
+            const long long p = x + nx * (y + (long long)ny * z);
+            for (int k = 0; k < 6; ++k) packed[4 * ((size_t)(c * 6 + k) * h->nblk + b) + i] = (T)in[6 * p + k];
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+void hmc_default_params(hmc_params *p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->nx = p->ny = p->nz = 32;
+    p->n_orient = 64;
+    p->J = 1.0;
+    p->kT = 0.7;
+    p->c11 = 246.5; p->c12 = 147.3; p->c44 = 124.7;
+    p->bc = HMC_BC_UNIAXIAL;
+    p->load_axis[2] = 1.0;
+    p->strain = 1e-3;
+    p->elastic_scale = -1.0;
+    p->elastic = HMC_ELASTIC_TRACTION;
+    p->trial = HMC_TRIAL_NEIGHBOR;
+    p->mpm_steps_per_mcs = 50;
+    p->dt = -1.0;
+    p->damping = -1.0;
+    p->precision = HMC_FP32;
+    p->seed = 1;
+    p->replica = 0;
+    p->stream = nullptr;
+}
+
+hmc_status hmc_create(const hmc_params *p, hmc_handle **out) {
+    if (!out) return fail(nullptr, HMC_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    const std::string msg = validate(p);
+    if (!msg.empty()) return fail(nullptr, HMC_ERR_ARG, msg);
+    hmc_handle *h = new (std::nothrow) hmc_handle();
+    if (!h) return fail(nullptr, HMC_ERR_OOM, "host allocation failed");
+    h->p = *p;
+    h->nbx = p->nx / 2; h->nby = p->ny / 2; h->nbz = p->nz / 2;
+    h->nblk = (long long)h->nbx * h->nby * h->nbz;
+    h->N = 8 * h->nblk;
+    h->nnodes = h->nblk;
+    h->tsize = p->precision == HMC_FP32 ? 4 : 8;
+    const double lam_max = std::fmax(std::fmax(p->c11 + 2 * p->c12, p->c11 - p->c12), 2 * p->c44);
+    h->dt = p->dt > 0 ? p->dt : 0.5 * 2.0 / std::sqrt(lam_max);
+    h->damping = p->damping >= 0 ? p->damping : 0.05;
+    const int K = std::max(p->nx, std::max(p->ny, p->nz));
+    h->lam = p->elastic_scale >= 0 ? p->elastic_scale : 1e9 * (1.0 / K) * kL0 * kGammaStar / (2.0 * kGammaS);
+    const double dd = (p->c11 - p->c12) * (p->c11 + 2 * p->c12);
+    h->S11 = (p->c11 + p->c12) / dd;
+    h->S12 = -p->c12 / dd;
+    h->S44 = 1.0 / p->c44;
+    h->lam_sd_half = 0.5 * h->lam * (h->S11 - h->S12 - 0.5 * h->S44);
+    if (p->bc == HMC_BC_UNIAXIAL) {
+        const double n = std::sqrt(p->load_axis[0] * p->load_axis[0] + p->load_axis[1] * p->load_axis[1] +
+                                   p->load_axis[2] * p->load_axis[2]);
+        for (int i = 0; i < 3; ++i) h->axis[i] = p->load_axis[i] / n;
+    }
+
+    auto bail = [&](hmc_status s) {
+        g_create_error = h->err;
+        destroy_buffers(h);
+        delete h;
+        return s;
+    };
+    cudaError_t e;
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return bail(cuda_fail(h, e, "cudaGetDevice"));
+    if ((e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+        return bail(cuda_fail(h, e, "device attribute"));
+    if (p->stream) {
+        h->stream = static_cast<cudaStream_t>(p->stream);
+    } else {
+        if ((e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking)) != cudaSuccess)
+            return bail(cuda_fail(h, e, "stream create"));
+        h->own_stream = true;
+    }
+    if ((e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking)) != cudaSuccess)
+        return bail(cuda_fail(h, e, "capture stream create"));
+    h->zc = hmc::mpm_zchunk(h->nbx, h->nby, h->nbz, h->num_sms);
+    h->nparts = hmc::stress_grid(h->nblk);
+    struct Alloc { void **ptr; size_t bytes; const char *what; };
+    const size_t nodes_b = h->tsize * 3 * (size_t)h->nnodes;
+    Alloc allocs[] = {
+        {(void **)&h->spins, sizeof(uint4) * (size_t)h->nblk, "spins"},
+        {(void **)&h->stage16, sizeof(uint16_t) * (size_t)h->N, "spin staging"},
+        {&h->u[0], nodes_b, "u0"}, {&h->u[1], nodes_b, "u1"}, {&h->v, nodes_b, "v"},
+        {&h->sig, h->tsize * 48 * (size_t)h->nblk, "stress"},
+        {&h->ctab, h->tsize * 24 * (size_t)p->n_orient, "stiffness table"},
+        {&h->wtab, h->tsize * 20 * (size_t)p->n_orient, "zone table"},
+        {(void **)&h->thr, sizeof(unsigned long long) * 8, "threshold table"},
+        {(void **)&h->counts, sizeof(unsigned long long) * (size_t)p->n_orient, "orientation counts"},
+        {(void **)&h->partials, sizeof(double) * 7 * (size_t)h->nparts, "partials"},
+        {(void **)&h->st, sizeof(DevState), "device state"},
+    };
+    for (auto &a : allocs) {
+        if ((e = cudaMalloc(a.ptr, a.bytes)) != cudaSuccess) return bail(cuda_fail(h, e, a.what));
+    }
+    // integer Metropolis thresholds for an integer bond-energy change k (Eq. 5)
+    unsigned long long thr[8];
+    for (int k = 0; k < 8; ++k) {
+        double t;
+        if (k <= 0)
+            t = 4294967296.0;
+        else if (!(p->kT > 0.0))
+            t = 0.0;
+        else
+            t = std::ceil(std::exp(-(double)k * p->J / p->kT) * 4294967296.0 - 0.5);
+        thr[k] = (unsigned long long)t;
+    }
+    if ((e = cudaMemcpy(h->thr, thr, sizeof(thr), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return bail(cuda_fail(h, e, "threshold upload"));
+    DevState st;
+    std::memset(&st, 0, sizeof(st));
+    st.bc = p->bc;
+    if ((e = cudaMemcpy(h->st, &st, sizeof(st), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return bail(cuda_fail(h, e, "state upload"));
+    const size_t zero_bytes[] = {nodes_b, nodes_b, nodes_b};
+    void *zero_ptrs[] = {h->u[0], h->u[1], h->v};
+    for (int i = 0; i < 3; ++i)
+        if ((e = cudaMemset(zero_ptrs[i], 0, zero_bytes[i])) != cudaSuccess) return bail(cuda_fail(h, e, "memset"));
+    // the MPM kernel's dynamic shared memory opt-in, set before any capture
+    if ((e = hmc::mpm_prepare()) != cudaSuccess) return bail(cuda_fail(h, e, "MPM kernel attribute"));
+    *out = h;
+    return HMC_OK;
+}
+
+void hmc_destroy(hmc_handle *h) {
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    destroy_buffers(h);
+    delete h;
+}
+
+hmc_status hmc_set_orientations(hmc_handle *h, const double *euler, const uint16_t *spins) {
+    if (!h) return HMC_ERR_ARG;
+    if (!euler || !spins) return fail(h, HMC_ERR_ARG, "NULL euler or spins");
+    const int Q = h->p.n_orient;
+    for (int i = 0; i < 3 * Q; ++i)
+        if (!std::isfinite(euler[i])) return fail(h, HMC_ERR_ARG, "non-finite Euler angle");
+    for (long long i = 0; i < h->N; ++i)
+        if (spins[i] >= (uint32_t)Q) return fail(h, HMC_ERR_ARG, "spin value >= n_orient at site " + std::to_string(i));
+    h->A.assign((size_t)Q * 9, 0.0);
+    h->Cv.assign((size_t)Q * 36, 0.0);
+    h->Sv.assign((size_t)Q * 36, 0.0);
+    double C0[36] = {0}, S0[36] = {0};
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            C0[6 * i + j] = (i == j) ? h->p.c11 : h->p.c12;
+            S0[6 * i + j] = (i == j) ? h->S11 : h->S12;
+        }
+    for (int i = 3; i < 6; ++i) {
+        C0[6 * i + i] = h->p.c44;
+        S0[6 * i + i] = h->S44;
+    }
+    for (int q = 0; q < Q; ++q) {
+        double M[36], Ns[36];
+        euler_zyz(euler[3 * q], euler[3 * q + 1], euler[3 * q + 2], &h->A[(size_t)q * 9]);
+        bond(&h->A[(size_t)q * 9], M, Ns);
+        congruence(M, C0, &h->Cv[(size_t)q * 36]);
+        congruence(Ns, S0, &h->Sv[(size_t)q * 36]);
+    }
+    // Reuss compliance of the initial volume fractions, and the initial mean strain
+    std::vector<long long> cnt(Q, 0);
+    for (long long i = 0; i < h->N; ++i) cnt[spins[i]]++;
+    DevState st;
+    std::memset(&st, 0, sizeof(st));
+    for (int q = 0; q < Q; ++q)
+        if (cnt[q])
+            for (int k = 0; k < 36; ++k) st.sr[k] += (double)cnt[q] / (double)h->N * h->Sv[(size_t)q * 36 + k];
+    st.bc = h->p.bc;
+    st.eps0 = h->p.strain;
+    if (h->p.bc == HMC_BC_UNIAXIAL) {
+        axis_vectors(h->axis, st.axN, st.axNs);
+        for (int i = 0; i < 6; ++i) {
+            double s = 0;
+            for (int j = 0; j < 6; ++j) s += st.sr[6 * i + j] * st.axN[j];
+            st.axB[i] = s;
+        }
+        st.axNB = 0;
+        for (int i = 0; i < 6; ++i) st.axNB += st.axN[i] * st.axB[i];
+        for (int i = 0; i < 6; ++i) st.ebar[i] = h->p.strain / st.axNB * st.axB[i];
+    } else {
+        for (int i = 0; i < 6; ++i) st.ebar[i] = h->p.strain6[i];
+    }
+    for (int i = 0; i < 6; ++i) st.ebar_f[i] = (float)st.ebar[i];
+    HMC_CK(h, cudaStreamSynchronize(h->stream), "sync");
+    HMC_CK(h, cudaMemcpy(h->st, &st, sizeof(st), cudaMemcpyHostToDevice), "state upload");
+    if (h->p.precision == HMC_FP32) {
+        auto c = pack_ctab<float>(h->Cv, Q);
+        auto w = pack_wtab<float>(h->A, Q);
+        HMC_CK(h, cudaMemcpy(h->ctab, c.data(), c.size() * sizeof(float), cudaMemcpyHostToDevice), "table upload");
+        HMC_CK(h, cudaMemcpy(h->wtab, w.data(), w.size() * sizeof(float), cudaMemcpyHostToDevice), "table upload");
+    } else {
+        auto c = pack_ctab<double>(h->Cv, Q);
+        auto w = pack_wtab<double>(h->A, Q);
+        HMC_CK(h, cudaMemcpy(h->ctab, c.data(), c.size() * sizeof(double), cudaMemcpyHostToDevice), "table upload");
+        HMC_CK(h, cudaMemcpy(h->wtab, w.data(), w.size() * sizeof(double), cudaMemcpyHostToDevice), "table upload");
+    }
+    const size_t nodes_b = h->tsize * 3 * (size_t)h->nnodes;
+    HMC_CK(h, cudaMemsetAsync(h->u[0], 0, nodes_b, h->stream), "memset u");
+    HMC_CK(h, cudaMemsetAsync(h->u[1], 0, nodes_b, h->stream), "memset u");
+    HMC_CK(h, cudaMemsetAsync(h->v, 0, nodes_b, h->stream), "memset v");
+    HMC_CK(h, cudaMemsetAsync(h->sig, 0, h->tsize * 48 * (size_t)h->nblk, h->stream), "memset sigma");
+    h->cur = 0;
+    hmc_status s = upload_spins(h, spins);
+    if (s != HMC_OK) return s;
+    HMC_CK(h, cudaStreamSynchronize(h->stream), "sync");
+    h->oriented = true;
+    return HMC_OK;
+}
+
+hmc_status hmc_set_spins(hmc_handle *h, const uint16_t *spins) {
+    hmc_status s = need_oriented(h);
+    if (s != HMC_OK) return s;
+    if (!spins) return fail(h, HMC_ERR_ARG, "NULL spins");
+    if ((s = upload_spins(h, spins)) != HMC_OK) return s;
+    HMC_CK(h, cudaStreamSynchronize(h->stream), "sync");
+    return HMC_OK;
+}
+
+hmc_status hmc_get_spins(hmc_handle *h, uint16_t *spins) {
+    hmc_status s = need_oriented(h);
+    if (s != HMC_OK) return s;
+    if (!spins) return fail(h, HMC_ERR_ARG, "NULL spins");
+    HMC_CK(h, hmc::launch_unpack_spins(h->spins, h->stage16, h->p.nx, h->p.ny, h->p.nz, h->stream), "unpack spins");
+    HMC_CK(h, cudaMemcpyAsync(spins, h->stage16, sizeof(uint16_t) * h->N, cudaMemcpyDeviceToHost, h->stream), "spin download");
+    HMC_CK(h, cudaStreamSynchronize(h->stream), "sync");
+    return HMC_OK;
+}
+
+static hmc_status read_stats(hmc_handle *h, double *mean, double *energy) {
+    DevState st;
+    HMC_CK(h, cudaMemcpyAsync(&st, h->st, sizeof(st), cudaMemcpyDeviceToHost, h->stream), "state download");
+    HMC_CK(h, cudaStreamSynchronize(h->stream), "sync");
+    if (st.nonfinite) return fail(h, HMC_ERR_NONFINITE, "non-finite stress or energy");
+    if (mean)
+        for (int i = 0; i < 6; ++i) mean[i] = st.mean_sigma[i];
+    if (energy) *energy = st.energy;
+    return HMC_OK;
+}
+
+hmc_status hmc_compute_stress(hmc_handle *h, double *mean, double *energy) {
+    hmc_status s = need_oriented(h);
+    if (s != HMC_OK) return s;
+    HMC_CK(h, enq_stress(h, h->stream), "stress launch");
+    HMC_CK(h, hmc::launch_end_mcs(h->st, h->partials, h->nparts, h->N, 0, 0, h->stream), "reduction launch");
+    if (mean || energy) return read_stats(h, mean, energy);
+    return HMC_OK;
+}
+
+hmc_status hmc_mpm_steps(hmc_handle *h, int32_t nsteps, double *energy) {
+    hmc_status s = need_oriented(h);
+    if (s != HMC_OK) return s;
+    if (nsteps < 0) return fail(h, HMC_ERR_ARG, "nsteps < 0");
+    for (int k = 0; k < nsteps; ++k) HMC_CK(h, enq_mpm(h, h->stream), "MPM launch");
+    if (energy) return hmc_compute_stress(h, nullptr, energy);
+    return HMC_OK;
+}
+
+static hmc_status read_accepted(hmc_handle *h, int64_t *acc) {
+    unsigned long long a = 0;
+    HMC_CK(h, cudaMemcpyAsync(&a, &h->st->accepted, sizeof(a), cudaMemcpyDeviceToHost, h->stream), "download");
+    HMC_CK(h, cudaStreamSynchronize(h->stream), "sync");
+    *acc = (int64_t)a;
+    return HMC_OK;
+}
+
+hmc_status hmc_sweep_half(hmc_handle *h, int32_t colour, int64_t *accepted) {
+    hmc_status s = need_oriented(h);
+    if (s != HMC_OK) return s;
+    if (colour != 0 && colour != 1) return fail(h, HMC_ERR_ARG, "colour must be 0 or 1");
+    HMC_CK(h, cudaMemsetAsync(&h->st->accepted, 0, sizeof(unsigned long long), h->stream), "memset");
+    HMC_CK(h, enq_sweep(h, colour, h->stream), "sweep launch");
+    if (accepted) return read_accepted(h, accepted);
+    return HMC_OK;
+}
+
+hmc_status hmc_end_mcs(hmc_handle *h) {
+    hmc_status s = need_oriented(h);
+    if (s != HMC_OK) return s;
+    HMC_CK(h, hmc::launch_end_mcs(h->st, h->partials, h->nparts, h->N, 1, 1, h->stream), "end-of-step launch");
+    return HMC_OK;
+}
+
+hmc_status hmc_mc_sweeps(hmc_handle *h, int32_t n_mcs, int64_t *accepted) {
+    hmc_status s = need_oriented(h);
+    if (s != HMC_OK) return s;
+    if (n_mcs < 0) return fail(h, HMC_ERR_ARG, "n_mcs < 0");
+    HMC_CK(h, cudaMemsetAsync(&h->st->accepted, 0, sizeof(unsigned long long), h->stream), "memset");
+    for (int m = 0; m < n_mcs; ++m) {
+        const int c0 = h->cur;
+        if (!h->gexec[c0]) {
+            // capture one step starting from this displacement buffer
+            cudaGraph_t g = nullptr;
+            HMC_CK(h, cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
+            cudaError_t e = enqueue_mcs(h, h->cap);
+            cudaError_t e2 = cudaStreamEndCapture(h->cap, &g);
+            h->cur = c0;
+            if (e != cudaSuccess) {
+                if (g) cudaGraphDestroy(g);
+                return cuda_fail(h, e, "capture");
+            }
+            if (e2 != cudaSuccess) return cuda_fail(h, e2, "end capture");
+            e = cudaGraphInstantiate(&h->gexec[c0], g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) {
+                h->gexec[c0] = nullptr;
+                return cuda_fail(h, e, "graph instantiate");
+            }
+        }
+        HMC_CK(h, cudaGraphLaunch(h->gexec[c0], h->stream), "graph launch");
+        if (h->p.mpm_steps_per_mcs & 1) h->cur ^= 1;
+    }
+    if (accepted) return read_accepted(h, accepted);
+    return HMC_OK;
+}
+
+hmc_status hmc_texture_histogram(hmc_handle *h, int32_t kind, int32_t nbins, double *fractions, int64_t *counts_per_q) {
+    hmc_status s = need_oriented(h);
+    if (s != HMC_OK) return s;
+    const int Q = h->p.n_orient;
+    if (fractions) {
+        if (kind == HMC_HIST_PER_Q && nbins != Q) return fail(h, HMC_ERR_ARG, "PER_Q needs nbins == n_orient");
+        if (kind != HMC_HIST_PER_Q && kind != HMC_HIST_ANGLE_100 && kind != HMC_HIST_YOUNG) return fail(h, HMC_ERR_ARG, "bad kind");
+        if (nbins < 1) return fail(h, HMC_ERR_ARG, "nbins < 1");
+    }
+    HMC_CK(h, cudaMemsetAsync(h->counts, 0, sizeof(unsigned long long) * Q, h->stream), "memset");
+    HMC_CK(h, cudaMemsetAsync(&h->st->unlike, 0, sizeof(unsigned long long), h->stream), "memset");
+    HMC_CK(h, hmc::launch_bonds_counts(h->spins, h->nbx, h->nby, h->nbz, Q, h->counts, h->st, h->stream), "counts launch");
+    if (fractions) {
+        std::vector<int32_t> map(Q);
+        for (int q = 0; q < Q; ++q) {
+            const double *A = &h->A[(size_t)q * 9];
+            int b = q;
+            if (kind == HMC_HIST_ANGLE_100) {
+                double c = 0;
+                for (int m = 0; m < 3; ++m) {
+                    const double d = std::fabs(A[0 * 3 + m] * h->axis[0] + A[1 * 3 + m] * h->axis[1] + A[2 * 3 + m] * h->axis[2]);
+                    c = std::fmax(c, d);
+                }
+                const double ang = std::acos(std::fmin(1.0, c)) * 180.0 / M_PI;
+                b = (int)(ang / (90.0 / nbins));
+            } else if (kind == HMC_HIST_YOUNG) {
+                double N[6], Nsv[6];
+                axis_vectors(h->axis, N, Nsv);
+                double nsn = 0;
+                for (int i = 0; i < 6; ++i)
+                    for (int j = 0; j < 6; ++j) nsn += N[i] * h->Sv[(size_t)q * 36 + 6 * i + j] * N[j];
+                const double x = 1.0 / nsn / h->p.c11;
+                const double sd = h->S11 - h->S12 - 0.5 * h->S44;
+                const double e1 = 1.0 / h->S11 / h->p.c11, e2 = 1.0 / (h->S11 - 2.0 * sd / 3.0) / h->p.c11;
+                const double lo = std::fmin(e1, e2), hi = std::fmax(e1, e2);
+                b = hi > lo ? (int)((x - lo) / (hi - lo) * nbins) : 0;
+            }
+            map[q] = b < 0 ? 0 : (b >= nbins ? nbins - 1 : b);
+        }
+        if (h->bins_cap < nbins) {
+            if (h->bins) cudaFree(h->bins);
+            if (h->fractions) cudaFree(h->fractions);
+            h->bins = nullptr;
+            h->fractions = nullptr;
+            h->bins_cap = 0;
+            HMC_CK(h, cudaMalloc(&h->bins, sizeof(unsigned long long) * nbins), "bins");
+            HMC_CK(h, cudaMalloc(&h->fractions, sizeof(double) * nbins), "fractions");
+            h->bins_cap = nbins;
+        }
+        if (!h->binmap) HMC_CK(h, cudaMalloc(&h->binmap, sizeof(int32_t) * Q), "binmap");
+        HMC_CK(h, cudaMemcpyAsync(h->binmap, map.data(), sizeof(int32_t) * Q, cudaMemcpyHostToDevice, h->stream), "binmap");
+        HMC_CK(h, cudaMemsetAsync(h->bins, 0, sizeof(unsigned long long) * nbins, h->stream), "memset");
+        HMC_CK(h, hmc::launch_bins(h->counts, h->binmap, Q, nbins, h->bins, h->fractions, h->N, h->stream), "bins launch");
+        HMC_CK(h, cudaMemcpyAsync(fractions, h->fractions, sizeof(double) * nbins, cudaMemcpyDeviceToHost, h->stream), "download");
+    }
+    if (counts_per_q)
+        HMC_CK(h, cudaMemcpyAsync(counts_per_q, h->counts, sizeof(int64_t) * Q, cudaMemcpyDeviceToHost, h->stream), "download");
+    HMC_CK(h, cudaStreamSynchronize(h->stream), "sync");
+    return HMC_OK;
+}
+
+hmc_status hmc_energy(hmc_handle *h, int64_t *unlike, double *energy, double *mean) {
+    hmc_status s = need_oriented(h);
+    if (s != HMC_OK) return s;
+    if (unlike) {
+        HMC_CK(h, cudaMemsetAsync(h->counts, 0, sizeof(unsigned long long) * h->p.n_orient, h->stream), "memset");
+        HMC_CK(h, cudaMemsetAsync(&h->st->unlike, 0, sizeof(unsigned long long), h->stream), "memset");
+        HMC_CK(h, hmc::launch_bonds_counts(h->spins, h->nbx, h->nby, h->nbz, h->p.n_orient, h->counts, h->st, h->stream),
+               "bonds launch");
+        unsigned long long u = 0;
+        HMC_CK(h, cudaMemcpyAsync(&u, &h->st->unlike, sizeof(u), cudaMemcpyDeviceToHost, h->stream), "download");
+        HMC_CK(h, cudaStreamSynchronize(h->stream), "sync");
+        *unlike = (int64_t)u;
+    }
+    if (energy || mean) return read_stats(h, mean, energy);
+    return HMC_OK;
+}
+
+hmc_status hmc_get_stress(hmc_handle *h, double *sigma) {
+    hmc_status s = need_oriented(h);
+    if (s != HMC_OK) return s;
+    if (!sigma) return fail(h, HMC_ERR_ARG, "NULL sigma");
+    const size_t n = 48 * (size_t)h->nblk;
+    if (h->p.precision == HMC_FP32) {
+        std::vector<float> t(n);
+        HMC_CK(h, cudaMemcpyAsync(t.data(), h->sig, n * sizeof(float), cudaMemcpyDeviceToHost, h->stream), "download");
+        HMC_CK(h, cudaStreamSynchronize(h->stream), "sync");
+        unpack_stress_host<float>(h, t, sigma);
+    } else {
+        std::vector<double> t(n);
+        HMC_CK(h, cudaMemcpyAsync(t.data(), h->sig, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "download");
+        HMC_CK(h, cudaStreamSynchronize(h->stream), "sync");
+        unpack_stress_host<double>(h, t, sigma);
+    }
+    return HMC_OK;
+}
+
+hmc_status hmc_set_stress(hmc_handle *h, const double *sigma) {
+    hmc_status s = need_oriented(h);
+    if (s != HMC_OK) return s;
+    if (!sigma) return fail(h, HMC_ERR_ARG, "NULL sigma");
+    for (long long i = 0; i < 6 * h->N; ++i)
+        if (!std::isfinite(sigma[i])) return fail(h, HMC_ERR_ARG, "non-finite stress");
+    const size_t n = 48 * (size_t)h->nblk;
+    HMC_CK(h, cudaStreamSynchronize(h->stream), "sync");
+    if (h->p.precision == HMC_FP32) {
+        std::vector<float> t(n);
+        pack_stress_host<float>(h, sigma, t);
+        HMC_CK(h, cudaMemcpy(h->sig, t.data(), n * sizeof(float), cudaMemcpyHostToDevice), "upload");
+    } else {
+        std::vector<double> t(n);
+        pack_stress_host<double>(h, sigma, t);
+        HMC_CK(h, cudaMemcpy(h->sig, t.data(), n * sizeof(double), cudaMemcpyHostToDevice), "upload");
+    }
+    return HMC_OK;
+}
+
+static hmc_status nodal_io(hmc_handle *h, void *dev, double *host, bool to_host) {
+    const size_t n = 3 * (size_t)h->nnodes;
+    if (h->p.precision == HMC_FP64) {
+        if (to_host)
+            HMC_CK(h, cudaMemcpyAsync(host, dev, n * 8, cudaMemcpyDeviceToHost, h->stream), "download");
+        else
+            HMC_CK(h, cudaMemcpyAsync(dev, host, n * 8, cudaMemcpyHostToDevice, h->stream), "upload");
+        HMC_CK(h, cudaStreamSynchronize(h->stream), "sync");
+        return HMC_OK;
+    }
+    std::vector<float> t(n);
+    if (to_host) {
+        HMC_CK(h, cudaMemcpyAsync(t.data(), dev, n * 4, cudaMemcpyDeviceToHost, h->stream), "download");
+        HMC_CK(h, cudaStreamSynchronize(h->stream), "sync");
+        for (size_t i = 0; i < n; ++i) host[i] = t[i];
+    } else {
+        for (size_t i = 0; i < n; ++i) t[i] = (float)host[i];
+        HMC_CK(h, cudaMemcpyAsync(dev, t.data(), n * 4, cudaMemcpyHostToDevice, h->stream), "upload");
+        HMC_CK(h, cudaStreamSynchronize(h->stream), "sync");
+    }
+    return HMC_OK;
+}
+
+hmc_status hmc_get_nodal(hmc_handle *h, double *u, double *v) {
+    hmc_status s = need_oriented(h);
+    if (s != HMC_OK) return s;
+    if (u && (s = nodal_io(h, h->u[h->cur], u, true)) != HMC_OK) return s;
+    if (v && (s = nodal_io(h, h->v, v, true)) != HMC_OK) return s;
+    return HMC_OK;
+}
+
+hmc_status hmc_set_nodal(hmc_handle *h, const double *u, const double *v) {
+    hmc_status s = need_oriented(h);
+    if (s != HMC_OK) return s;
+    const size_t n = 3 * (size_t)h->nnodes;
+    for (const double *a : {u, v})
+        if (a)
+            for (size_t i = 0; i < n; ++i)
+                if (!std::isfinite(a[i])) return fail(h, HMC_ERR_ARG, "non-finite nodal value");
+    if (u && (s = nodal_io(h, h->u[h->cur], const_cast<double *>(u), false)) != HMC_OK) return s;
+    if (v && (s = nodal_io(h, h->v, const_cast<double *>(v), false)) != HMC_OK) return s;
+    return HMC_OK;
+}
+
+hmc_status hmc_get_strain(hmc_handle *h, double *e) {
+    if (!h) return HMC_ERR_ARG;
+    if (!e) return fail(h, HMC_ERR_ARG, "NULL strain");
+    HMC_CK(h, cudaMemcpyAsync(e, h->st->ebar, sizeof(double) * 6, cudaMemcpyDeviceToHost, h->stream), "download");
+    HMC_CK(h, cudaStreamSynchronize(h->stream), "sync");
+    return HMC_OK;
+}
+
+hmc_status hmc_set_strain(hmc_handle *h, const double *e) {
+    if (!h) return HMC_ERR_ARG;
+    if (!e) return fail(h, HMC_ERR_ARG, "NULL strain");
+    double d[6];
+    float f[6];
+    for (int i = 0; i < 6; ++i) {
+        if (!std::isfinite(e[i])) return fail(h, HMC_ERR_ARG, "non-finite strain");
+        d[i] = e[i];
+        f[i] = (float)e[i];
+    }
+    HMC_CK(h, cudaMemcpyAsync(h->st->ebar, d, sizeof(d), cudaMemcpyHostToDevice, h->stream), "upload");
+    HMC_CK(h, cudaMemcpyAsync(h->st->ebar_f, f, sizeof(f), cudaMemcpyHostToDevice, h->stream), "upload");
+    HMC_CK(h, cudaStreamSynchronize(h->stream), "sync");
+    return HMC_OK;
+}
+
+hmc_status hmc_get_info(hmc_handle *h, hmc_info *info) {
+    if (!h) return HMC_ERR_ARG;
+    if (!info) return fail(h, HMC_ERR_ARG, "NULL info");
+    DevState st;
+    HMC_CK(h, cudaMemcpyAsync(&st, h->st, sizeof(st), cudaMemcpyDeviceToHost, h->stream), "download");
+    HMC_CK(h, cudaStreamSynchronize(h->stream), "sync");
+    info->dt = h->dt;
+    info->damping = h->damping;
+    info->elastic_scale = h->lam;
+    for (int i = 0; i < 6; ++i) info->strain_bar[i] = st.ebar[i];
+    info->mcs = st.mcs;
+    info->u_buffer = h->cur;
+    info->n_sites = h->N;
+    info->n_nodes = h->nnodes;
+    return HMC_OK;
+}
+
+namespace {
+struct StateHeader {
+    char magic[8];
+    int32_t nx, ny, nz, precision;
+    uint32_t mcs, pad;
+    double ebar[6];
+};
+}  // namespace
+
+hmc_status hmc_get_state(hmc_handle *h, void *buf, size_t *bytes) {
+    hmc_status s = need_oriented(h);
+    if (s != HMC_OK) return s;
+    if (!bytes) return fail(h, HMC_ERR_ARG, "NULL bytes");
+    const size_t need = sizeof(StateHeader) + 2 * (size_t)h->N + 2 * 3 * 8 * (size_t)h->nnodes;
+    if (!buf) {
+        *bytes = need;
+        return HMC_OK;
+    }
+    if (*bytes < need) return fail(h, HMC_ERR_ARG, "buffer too small");
+    StateHeader hd;
+    std::memset(&hd, 0, sizeof(hd));
+    std::memcpy(hd.magic, "HMCSTAT1", 8);
+    hd.nx = h->p.nx; hd.ny = h->p.ny; hd.nz = h->p.nz; hd.precision = h->p.precision;
+    DevState st;
+    HMC_CK(h, cudaMemcpyAsync(&st, h->st, sizeof(st), cudaMemcpyDeviceToHost, h->stream), "download");
+    HMC_CK(h, cudaStreamSynchronize(h->stream), "sync");
+    hd.mcs = st.mcs;
+    for (int i = 0; i < 6; ++i) hd.ebar[i] = st.ebar[i];
+    char *p = static_cast<char *>(buf);
+    std::memcpy(p, &hd, sizeof(hd));
+    p += sizeof(hd);
+    if ((s = hmc_get_spins(h, reinterpret_cast<uint16_t *>(p))) != HMC_OK) return s;
+    p += 2 * (size_t)h->N;
+    double *u = reinterpret_cast<double *>(p), *v = u + 3 * (size_t)h->nnodes;
+    if ((s = hmc_get_nodal(h, u, v)) != HMC_OK) return s;
+    *bytes = need;
+    return HMC_OK;
+}
+
+hmc_status hmc_set_state(hmc_handle *h, const void *buf, size_t bytes) {
+    hmc_status s = need_oriented(h);
+    if (s != HMC_OK) return s;
+    const size_t need = sizeof(StateHeader) + 2 * (size_t)h->N + 2 * 3 * 8 * (size_t)h->nnodes;
+    if (!buf || bytes < need) return fail(h, HMC_ERR_ARG, "state buffer too small");
+    StateHeader hd;
+    std::memcpy(&hd, buf, sizeof(hd));
+    if (std::memcmp(hd.magic, "HMCSTAT1", 8) != 0 || hd.nx != h->p.nx || hd.ny != h->p.ny || hd.nz != h->p.nz)
+        return fail(h, HMC_ERR_ARG, "state does not match this handle");
+    const char *p = static_cast<const char *>(buf) + sizeof(hd);
+    if ((s = hmc_set_spins(h, reinterpret_cast<const uint16_t *>(p))) != HMC_OK) return s;
+    p += 2 * (size_t)h->N;
+    const double *u = reinterpret_cast<const double *>(p), *v = u + 3 * (size_t)h->nnodes;
+    if ((s = hmc_set_nodal(h, u, v)) != HMC_OK) return s;
+    if ((s = hmc_set_strain(h, hd.ebar)) != HMC_OK) return s;
+    HMC_CK(h, cudaMemcpyAsync(&h->st->mcs, &hd.mcs, sizeof(uint32_t), cudaMemcpyHostToDevice, h->stream), "upload");
+    HMC_CK(h, cudaStreamSynchronize(h->stream), "sync");
+    return HMC_OK;
+}
+
+hmc_status hmc_synchronize(hmc_handle *h) {
+    if (!h) return HMC_ERR_ARG;
+    HMC_CK(h, cudaStreamSynchronize(h->stream), "sync");
+    return HMC_OK;
+}
+
+const char *hmc_last_error(const hmc_handle *h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+}  // extern "C"

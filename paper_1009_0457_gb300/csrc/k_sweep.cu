@@ -1,0 +1,169 @@
+// Red/black checkerboard half sweep (Sec. "Microstructural Evolution") with the
+// Metropolis rule (Eq. 5) on the bond-energy change of the Potts Hamiltonian
+// (Eq. 4, bonds counted once, 6 neighbours, periodic) plus the one-point
+// constant-traction zone shift (Eqs. 6-8 and 13) from the stored stress.
+//
+// One thread per 2x2x2 block: it tries the block's four sites of the sweep's
+// colour.  Loads per block: the block's 16 B of spins, the other colour's
+// 8 B quad of the six face neighbours (cache hits: every quad is some other
+// thread's own), and six 16 B stress vectors (FP32).  Writes: the colour's
+// 8 B quad when a site changed.  Same-colour sites share no neighbour, so the
+// in-place update is race free.
+#include "hmc_device.cuh"
+
+namespace hmc {
+
+namespace {
+
+template <typename T>
+struct Vec4;
+template <>
+struct Vec4<float> {
+    float v[4];
+    __device__ __forceinline__ void load(const float *p) {
+        const float4 t = __ldcs(reinterpret_cast<const float4 *>(p));  // streamed once per sweep
+        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    }
+};
+template <>
+struct Vec4<double> {
+    double v[4];
+    __device__ __forceinline__ void load(const double *p) {
+        const double2 a = __ldcs(reinterpret_cast<const double2 *>(p));
+        const double2 b = __ldcs(reinterpret_cast<const double2 *>(p) + 1);
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    }
+};
+
+// Phi(q; sigma) = sum over the three crystal axes of (a_m . sigma . a_m)^2, from
+// the Voigt weight vectors of the axes.  For one cubic material the zone energy
+// w(q) = 1/2 sigma.S'(q).sigma = 1/2 [S12 tr^2 + S44/2 |sigma|^2 + s_d Phi(q)], so
+// w(q_old) - w(q_new) = s_d / 2 (Phi(q_old) - Phi(q_new)).
+template <typename T>
+__device__ __forceinline__ T zone_phi(const T *__restrict__ w, const T (&s)[6]) {
+    T acc = T(0);
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+        const T *r = w + 6 * m;
+        const T p = __ldg(r) * s[0] + __ldg(r + 1) * s[1] + __ldg(r + 2) * s[2] + __ldg(r + 3) * s[3] +
+                    __ldg(r + 4) * s[4] + __ldg(r + 5) * s[5];
+        acc += p * p;
+    }
+    return acc;
+}
+
+__device__ __forceinline__ float log_t(float x) { return logf(x); }
+__device__ __forceinline__ double log_t(double x) { return log(x); }
+
+template <typename T, bool ELASTIC>
+__global__ void __launch_bounds__(256) k_sweep(SweepArgs<T> a, int colour) {
+    const long long blk = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    int nacc = 0;
+    if (blk < a.nblk) {
+        const int bx = (int)(blk % a.nbx);
+        const long long r = blk / a.nbx;
+        const int by = (int)(r % a.nby), bz = (int)(r / a.nby);
+        const long long sxy = a.nbx, sxz = (long long)a.nbx * a.nby;
+        const long long bxm = blk + (bx == 0 ? a.nbx - 1 : -1), bxp = blk + (bx == a.nbx - 1 ? 1 - a.nbx : 1);
+        const long long bym = blk + (by == 0 ? (a.nby - 1) * sxy : -sxy);
+        const long long byp = blk + (by == a.nby - 1 ? -(a.nby - 1) * sxy : sxy);
+        const long long bzm = blk + (bz == 0 ? (a.nbz - 1) * sxz : -sxz);
+        const long long bzp = blk + (bz == a.nbz - 1 ? -(a.nbz - 1) * sxz : sxz);
+        const uint2 *q2 = reinterpret_cast<const uint2 *>(a.spins);
+        const int oc = colour ^ 1;
+        const uint4 own4 = a.spins[blk];
+        const uint2 mine = colour ? make_uint2(own4.z, own4.w) : make_uint2(own4.x, own4.y);
+        const uint2 O = oc ? make_uint2(own4.z, own4.w) : make_uint2(own4.x, own4.y);
+        const uint2 Oxm = __ldg(q2 + 2 * bxm + oc), Oxp = __ldg(q2 + 2 * bxp + oc);
+        const uint2 Oym = __ldg(q2 + 2 * bym + oc), Oyp = __ldg(q2 + 2 * byp + oc);
+        const uint2 Ozm = __ldg(q2 + 2 * bzm + oc), Ozp = __ldg(q2 + 2 * bzp + oc);
+        T sg[6][4];
+        if (ELASTIC) {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                Vec4<T> t;
+                t.load(a.sig + 4ll * ((long long)(colour * 6 + k) * a.nblk + blk));
+#pragma unroll
+                for (int i = 0; i < 4; ++i) sg[k][i] = t.v[i];
+            }
+        }
+        const uint32_t mcs = a.st->mcs;
+        uint16_t out[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int L = slot_local(4 * colour + i);
+            const int lx = L & 1, ly = (L >> 1) & 1, lz = L >> 2;
+            const uint16_t q = quad_get(mine, i);
+            uint16_t nb[6];
+            nb[0] = quad_get(lx ? O : Oxm, i);
+            nb[1] = quad_get(lx ? Oxp : O, i);
+            nb[2] = quad_get(ly ? O : Oym, i ^ 1);
+            nb[3] = quad_get(ly ? Oyp : O, i ^ 1);
+            nb[4] = quad_get(lz ? O : Ozm, i ^ 2);
+            nb[5] = quad_get(lz ? Ozp : O, i ^ 2);
+            const uint32_t x = 2u * bx + lx, y = 2u * by + ly, z = 2u * bz + lz;
+            const uint32_t site = x + (uint32_t)a.nx * (y + (uint32_t)a.ny * z);
+            const uint2 rn = philox_r01(site, mcs, a.replica, 0u, a.key0, a.key1);
+            uint16_t qn;
+            if (a.trial == 0) {
+                const uint32_t k = __umulhi(rn.x, 6u);
+                qn = nb[0];
+#pragma unroll
+                for (int j = 1; j < 6; ++j)
+                    if (k == (uint32_t)j) qn = nb[j];
+            } else {
+                qn = (uint16_t)__umulhi(rn.x, (uint32_t)a.nq);
+            }
+            out[i] = q;
+            if (qn == q) continue;
+            int dE = 0;
+#pragma unroll
+            for (int j = 0; j < 6; ++j) dE += (nb[j] == q) - (nb[j] == qn);
+            T dHe = T(0);
+            if (ELASTIC) {
+                T s[6];
+#pragma unroll
+                for (int k = 0; k < 6; ++k) s[k] = sg[k][i];
+                dHe = a.lam_sd_half * (zone_phi<T>(a.wtab + 20ll * q, s) - zone_phi<T>(a.wtab + 20ll * qn, s));
+            }
+            bool acc;
+            if (!ELASTIC || dHe == T(0)) {
+                acc = dE <= 0 || (unsigned long long)rn.y < __ldg(a.thr + dE);
+            } else {
+                const T H = a.J * (T)dE + dHe;
+                const T u01 = ((T)rn.y + T(0.5)) * T(2.3283064365386963e-10);
+                const T t = a.kT > T(0) ? -a.kT * log_t(u01) : T(0);
+                acc = H <= t;
+            }
+            if (acc) {
+                out[i] = qn;
+                ++nacc;
+            }
+        }
+        if (nacc) {
+            uint2 w;
+            w.x = (uint32_t)out[0] | ((uint32_t)out[1] << 16);
+            w.y = (uint32_t)out[2] | ((uint32_t)out[3] << 16);
+            reinterpret_cast<uint2 *>(a.spins)[2 * blk + colour] = w;
+        }
+    }
+    const unsigned tot = __reduce_add_sync(0xffffffffu, (unsigned)nacc);
+    if ((threadIdx.x & 31) == 0 && tot) atomicAdd(&a.st->accepted, (unsigned long long)tot);
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_sweep(const SweepArgs<T> &a, int colour, bool elastic, cudaStream_t s) {
+    const int grid = (int)((a.nblk + 255) / 256);
+    if (elastic)
+        k_sweep<T, true><<<grid, 256, 0, s>>>(a, colour);
+    else
+        k_sweep<T, false><<<grid, 256, 0, s>>>(a, colour);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_sweep<float>(const SweepArgs<float> &, int, bool, cudaStream_t);
+template cudaError_t launch_sweep<double>(const SweepArgs<double> &, int, bool, cudaStream_t);
+
+}  // namespace hmc

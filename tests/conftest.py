@@ -8,6 +8,16 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 
+def build_libhmc():
+    """Build libhmc.so (if stale) without importing the package first."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location(
+        "paper_1009_0457_gb300_build", os.path.join(ROOT, "paper_1009_0457_gb300", "build.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod.build()
+
+
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (sm_103a) and the built CUDA library")
 
