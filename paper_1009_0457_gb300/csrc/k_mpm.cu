@@ -4,41 +4,45 @@
 // velocity / displacement update of every node -- one kernel, one pass over
 // the spins and the nodal state.
 //
-// Tiling: a CTA of 16x16 threads owns a 16x16 column of nodes and marches up
-// a chunk of node planes in z.  For every cell plane it computes the 17x17
-// cells that touch its nodes (one cell ring of halo in x and y), each cell's
-// eight points in one thread, and writes each cell's eight nodal force
-// contributions to shared memory; a node's force is then the sum of its four
-// cells below and four cells above, the latter carried in registers from the
-// previous plane.  Displacements are read from one buffer and written to the
-// other, so CTAs never race on the halo.
+// Tiling: a CTA of 16x16 threads computes a 16x16 patch of cells per cell
+// plane (one thread per cell, all eight points of the cell) and owns the
+// 15x15 nodes whose four lower and four upper cells all lie in the patch.  It
+// marches up a chunk of planes in z: each cell writes its eight nodal force
+// contributions to shared memory, and a node's force is the sum of its four
+// cells below (carried in registers from the previous plane) and four above.
+// Node planes are triple-buffered in shared memory (structure of arrays, so
+// neighbouring threads hit neighbouring banks) and the next plane's spins and
+// the owned node's velocity are fetched one plane ahead.  Displacements are
+// read from one buffer and written to the other, so CTAs never race on the halo.
 #include "hmc_device.cuh"
 
 namespace hmc {
 
 namespace {
 
-constexpr int TX = 16, TY = 16, CX = TX + 1, CY = TY + 1, NXS = TX + 2, NYS = TY + 2;
-constexpr int NTHR = TX * TY;
+constexpr int CT = 16;        // cells per patch edge = threads per edge
+constexpr int OT = CT - 1;    // owned nodes per patch edge
+constexpr int NT = CT + 1;    // node-plane tile edge (one node of halo each side)
+constexpr int NTHR = CT * CT;
 
 template <typename T>
 struct MpmSmem {
-    T us[2][NYS][NXS][3];  // node planes kk and kk+1 (with one node of halo on each side)
-    T fb[CY][CX][4][3];    // cell contributions to their four lower nodes (plane kk)
-    T ft[CY][CX][4][3];    // cell contributions to their four upper nodes (plane kk+1)
+    T us[3][3][NT][NT];   // node planes (buffer, component, j, i)
+    T fb[4][3][CT][CT];   // cell contributions to their lower corner nodes (corner I+2J, component)
+    T ft[4][3][CT][CT];   // ... to their upper corner nodes
 };
 
 template <typename T>
-__device__ __forceinline__ void load_plane(MpmSmem<T> &sm, int slot, const T *__restrict__ u, int i0, int j0,
-                                           int k, int nbx, int nby, int nbz) {
+__device__ __forceinline__ void load_plane(MpmSmem<T> &sm, int buf, const T *__restrict__ u, int i0, int j0, int k,
+                                           int nbx, int nby, int nbz) {
     const int gk = wrapi(k, nbz);
-    for (int t = threadIdx.x; t < NYS * NXS; t += NTHR) {
-        const int li = t % NXS, lj = t / NXS;
+    for (int t = threadIdx.x; t < NT * NT; t += NTHR) {
+        const int li = t % NT, lj = t / NT;
         const int gi = wrapi(i0 - 1 + li, nbx), gj = wrapi(j0 - 1 + lj, nby);
         const long long n = 3ll * (gi + (long long)nbx * (gj + (long long)nby * gk));
-        sm.us[slot][lj][li][0] = u[n];
-        sm.us[slot][lj][li][1] = u[n + 1];
-        sm.us[slot][lj][li][2] = u[n + 2];
+        sm.us[buf][0][lj][li] = __ldg(u + n);
+        sm.us[buf][1][lj][li] = __ldg(u + n + 1);
+        sm.us[buf][2][lj][li] = __ldg(u + n + 2);
     }
 }
 
@@ -56,13 +60,19 @@ __device__ __forceinline__ void cell_forces(const T (&u)[8][3], const uint4 &sp,
         for (int j = 0; j < 2; ++j)
 #pragma unroll
             for (int d = 0; d < 3; ++d) tx[i][j][d] = ty[i][j][d] = tz[i][j][d] = T(0);
+    Row24<T> row;
+    uint32_t qprev = 0xffffffffu;
 #pragma unroll
     for (int L = 0; L < 8; ++L) {
         const int a = L & 1, b = (L >> 1) & 1, c = L >> 2;
         T e[6], s[6];
         point_strain<T>(g, eb, a, b, c, e);
-        Row24<T> row;
-        row.load(ctab + 24ll * spin_of(sp, local_slot(L)));
+        // points of one cell mostly share one orientation: fetch the row only when it changes
+        const uint32_t q = spin_of(sp, local_slot(L));
+        if (q != qprev) {
+            row.load(ctab + 24ll * q);
+            qprev = q;
+        }
         hooke21<T>(row.v, e, s);
         // columns of sigma: x = (s0,s5,s4), y = (s5,s1,s3), z = (s4,s3,s2)
         tx[b][c][0] += s[0]; tx[b][c][1] += s[5]; tx[b][c][2] += s[4];
@@ -94,27 +104,38 @@ __global__ void __launch_bounds__(NTHR, (sizeof(T) == 4 ? 2 : 1)) k_mpm_step(Mpm
     extern __shared__ __align__(16) unsigned char smem_raw[];
     MpmSmem<T> &sm = *reinterpret_cast<MpmSmem<T> *>(smem_raw);
     const int tid = threadIdx.x;
-    const int tx = tid % TX, ty = tid / TX;
-    const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY, k0 = blockIdx.z * a.zc;
+    const int lci = tid % CT, lcj = tid / CT;           // this thread's cell in the patch
+    const int i0 = blockIdx.x * OT, j0 = blockIdx.y * OT, k0 = blockIdx.z * a.zc;
     const int kend = min(k0 + a.zc, a.nbz);
-    const int ni = i0 + tx, nj = j0 + ty;
-    const bool own = ni < a.nbx && nj < a.nby;
-    // cells needed by the owned nodes: local cell index lc = cell - (i0 - 1) <= last owned - i0 + 1
-    const int lci_max = min(TX, a.nbx - i0), lcj_max = min(TY, a.nby - j0);
+    const int ni = i0 - 1 + lci, nj = j0 - 1 + lcj;      // node at the cell's lower corner
+    const bool own = lci >= 1 && lcj >= 1 && ni < a.nbx && nj < a.nby;
+    // a cell is needed when some owned node uses it: local index <= last owned local index
+    const bool need = lci <= min(OT, a.nbx - i0) && lcj <= min(OT, a.nby - j0);
+    const int gi = wrapi(ni, a.nbx), gj = wrapi(nj, a.nby);
+    const long long col = gi + (long long)a.nbx * gj;   // (i, j) column offset of cell and node
+    const long long plane = (long long)a.nbx * a.nby;
     T eb[6];
     load_ebar<T>(a.st, eb);
 
-    int cur = 0;
-    load_plane<T>(sm, 0, a.u_in, i0, j0, k0 - 1, a.nbx, a.nby, a.nbz);
-    load_plane<T>(sm, 1, a.u_in, i0, j0, k0, a.nbx, a.nby, a.nbz);
+    int b0 = 0, b1 = 1, b2 = 2;
+    load_plane<T>(sm, b0, a.u_in, i0, j0, k0 - 1, a.nbx, a.nby, a.nbz);
+    load_plane<T>(sm, b1, a.u_in, i0, j0, k0, a.nbx, a.nby, a.nbz);
+    uint4 sp = need ? __ldg(a.spins + col + plane * wrapi(k0 - 1, a.nbz)) : make_uint4(0, 0, 0, 0);
     __syncthreads();
 
     T acc[3] = {T(0), T(0), T(0)};
     for (int kk = k0 - 1; kk < kend; ++kk) {
-        const int gk = wrapi(kk, a.nbz);
-        for (int c = tid; c < CX * CY; c += NTHR) {
-            const int lci = c % CX, lcj = c / CX;
-            if (lci > lci_max || lcj > lcj_max) continue;
+        // one plane ahead: next plane's spins, this plane's owned velocity, plane kk+2 of u
+        uint4 sp_next = make_uint4(0, 0, 0, 0);
+        if (need && kk + 1 < kend) sp_next = __ldg(a.spins + col + plane * (kk + 1));
+        T vold[3] = {T(0), T(0), T(0)};
+        const long long nidx = 3ll * (col + plane * (long long)(kk < 0 ? 0 : kk));
+        if (own && kk >= k0) {
+#pragma unroll
+            for (int d = 0; d < 3; ++d) vold[d] = a.v[nidx + d];
+        }
+        if (kk + 1 < kend) load_plane<T>(sm, b2, a.u_in, i0, j0, kk + 2, a.nbx, a.nby, a.nbz);
+        if (need) {
             T u[8][3];
 #pragma unroll
             for (int K = 0; K < 2; ++K)
@@ -123,9 +144,7 @@ __global__ void __launch_bounds__(NTHR, (sizeof(T) == 4 ? 2 : 1)) k_mpm_step(Mpm
 #pragma unroll
                     for (int I = 0; I < 2; ++I)
 #pragma unroll
-                        for (int d = 0; d < 3; ++d) u[corner(I, J, K)][d] = sm.us[cur ^ K][lcj + J][lci + I][d];
-            const int gi = wrapi(i0 - 1 + lci, a.nbx), gj = wrapi(j0 - 1 + lcj, a.nby);
-            const uint4 sp = __ldg(a.spins + (gi + (long long)a.nbx * (gj + (long long)a.nby * gk)));
+                        for (int d = 0; d < 3; ++d) u[corner(I, J, K)][d] = sm.us[K ? b1 : b0][d][lcj + J][lci + I];
             T f[8][3];
             cell_forces<T>(u, sp, a.ctab, eb, f);
 #pragma unroll
@@ -134,32 +153,34 @@ __global__ void __launch_bounds__(NTHR, (sizeof(T) == 4 ? 2 : 1)) k_mpm_step(Mpm
                 for (int I = 0; I < 2; ++I)
 #pragma unroll
                     for (int d = 0; d < 3; ++d) {
-                        sm.fb[lcj][lci][I + 2 * J][d] = f[corner(I, J, 0)][d];
-                        sm.ft[lcj][lci][I + 2 * J][d] = f[corner(I, J, 1)][d];
+                        sm.fb[I + 2 * J][d][lcj][lci] = f[corner(I, J, 0)][d];
+                        sm.ft[I + 2 * J][d][lcj][lci] = f[corner(I, J, 1)][d];
                     }
         }
         __syncthreads();
         if (own) {
+            // cells (lci-1, lcj-1), (lci, lcj-1), (lci-1, lcj), (lci, lcj) see this node as corner 3, 2, 1, 0
             if (kk >= k0) {
-                const long long n = 3ll * (ni + (long long)a.nbx * (nj + (long long)a.nby * kk));
 #pragma unroll
                 for (int d = 0; d < 3; ++d) {
-                    const T f = acc[d] + sm.fb[ty][tx][3][d] + sm.fb[ty][tx + 1][2][d] + sm.fb[ty + 1][tx][1][d] +
-                                sm.fb[ty + 1][tx + 1][0][d];
-                    const T vn = a.keep * a.v[n + d] + a.dt_over_m * f;
-                    a.v[n + d] = vn;
-                    a.u_out[n + d] = sm.us[cur][ty + 1][tx + 1][d] + a.dt * vn;
+                    const T f = acc[d] + sm.fb[3][d][lcj - 1][lci - 1] + sm.fb[2][d][lcj - 1][lci] +
+                                sm.fb[1][d][lcj][lci - 1] + sm.fb[0][d][lcj][lci];
+                    const T vn = a.keep * vold[d] + a.dt_over_m * f;
+                    a.v[nidx + d] = vn;
+                    a.u_out[nidx + d] = sm.us[b0][d][lcj][lci] + a.dt * vn;
                 }
             }
 #pragma unroll
             for (int d = 0; d < 3; ++d)
-                acc[d] = sm.ft[ty][tx][3][d] + sm.ft[ty][tx + 1][2][d] + sm.ft[ty + 1][tx][1][d] +
-                         sm.ft[ty + 1][tx + 1][0][d];
+                acc[d] = sm.ft[3][d][lcj - 1][lci - 1] + sm.ft[2][d][lcj - 1][lci] + sm.ft[1][d][lcj][lci - 1] +
+                         sm.ft[0][d][lcj][lci];
         }
         __syncthreads();
-        if (kk + 1 < kend) load_plane<T>(sm, cur, a.u_in, i0, j0, kk + 2, a.nbx, a.nby, a.nbz);
-        cur ^= 1;
-        __syncthreads();
+        const int t = b0;
+        b0 = b1;
+        b1 = b2;
+        b2 = t;
+        sp = sp_next;
     }
 }
 
@@ -168,7 +189,7 @@ __global__ void __launch_bounds__(NTHR, (sizeof(T) == 4 ? 2 : 1)) k_mpm_step(Mpm
 int mpm_zchunk(int nbx, int nby, int nbz, int num_sms) {
     // enough CTAs for several waves of two resident CTAs per SM, but chunks of
     // at least 4 planes so the one-plane z halo stays a small overhead
-    const long long tiles = (long long)((nbx + TX - 1) / TX) * ((nby + TY - 1) / TY);
+    const long long tiles = (long long)((nbx + OT - 1) / OT) * ((nby + OT - 1) / OT);
     const long long target = 8ll * num_sms;
     long long chunks = (target + tiles - 1) / tiles;
     int zc = (int)((nbz + chunks - 1) / chunks);
@@ -188,7 +209,7 @@ cudaError_t mpm_prepare() {
 template <typename T>
 cudaError_t launch_mpm_step(const MpmArgs<T> &a, cudaStream_t s) {
     const size_t smem = sizeof(MpmSmem<T>);
-    dim3 grid((a.nbx + TX - 1) / TX, (a.nby + TY - 1) / TY, (a.nbz + a.zc - 1) / a.zc);
+    dim3 grid((a.nbx + OT - 1) / OT, (a.nby + OT - 1) / OT, (a.nbz + a.zc - 1) / a.zc);
     k_mpm_step<T><<<grid, NTHR, smem, s>>>(a);
     return cudaGetLastError();
 }

@@ -108,13 +108,18 @@ __global__ void __launch_bounds__(256) k_stress(StressArgs<T> a) {
         cell_gradients<T>(u, g);
         const uint4 sp = __ldg(a.spins + blk);
         T out[2][6][4];
+        Row24<T> row;
+        uint32_t qprev = 0xffffffffu;
 #pragma unroll
         for (int slot = 0; slot < 8; ++slot) {
             const int L = slot_local(slot);
             T e[6], s[6];
             point_strain<T>(g, eb, L & 1, (L >> 1) & 1, L >> 2, e);
-            Row24<T> row;
-            row.load(a.ctab + 24ll * spin_of(sp, slot));
+            const uint32_t q = spin_of(sp, slot);  // points of a cell mostly share one orientation
+            if (q != qprev) {
+                row.load(a.ctab + 24ll * q);
+                qprev = q;
+            }
             hooke21<T>(row.v, e, s);
             T w = T(0);
 #pragma unroll

@@ -40,13 +40,41 @@ struct Vec4<double> {
 // w(q) = 1/2 sigma.S'(q).sigma = 1/2 [S12 tr^2 + S44/2 |sigma|^2 + s_d Phi(q)], so
 // w(q_old) - w(q_new) = s_d / 2 (Phi(q_old) - Phi(q_new)).
 template <typename T>
+struct Row20;
+template <>
+struct Row20<float> {
+    float v[20];
+    __device__ __forceinline__ void load(const float *p) {
+        const float4 *q = reinterpret_cast<const float4 *>(p);
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+            const float4 t = __ldg(q + i);
+            v[4 * i] = t.x; v[4 * i + 1] = t.y; v[4 * i + 2] = t.z; v[4 * i + 3] = t.w;
+        }
+    }
+};
+template <>
+struct Row20<double> {
+    double v[20];
+    __device__ __forceinline__ void load(const double *p) {
+        const double2 *q = reinterpret_cast<const double2 *>(p);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const double2 t = __ldg(q + i);
+            v[2 * i] = t.x; v[2 * i + 1] = t.y;
+        }
+    }
+};
+
+template <typename T>
 __device__ __forceinline__ T zone_phi(const T *__restrict__ w, const T (&s)[6]) {
+    Row20<T> r;
+    r.load(w);
     T acc = T(0);
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
-        const T *r = w + 6 * m;
-        const T p = __ldg(r) * s[0] + __ldg(r + 1) * s[1] + __ldg(r + 2) * s[2] + __ldg(r + 3) * s[3] +
-                    __ldg(r + 4) * s[4] + __ldg(r + 5) * s[5];
+        const T p = r.v[6 * m] * s[0] + r.v[6 * m + 1] * s[1] + r.v[6 * m + 2] * s[2] + r.v[6 * m + 3] * s[3] +
+                    r.v[6 * m + 4] * s[4] + r.v[6 * m + 5] * s[5];
         acc += p * p;
     }
     return acc;
