@@ -202,6 +202,34 @@ hmc_status hmc_get_info(hmc_handle *h, hmc_info *info);
 hmc_status hmc_get_state(hmc_handle *h, void *buf, size_t *bytes);
 hmc_status hmc_set_state(hmc_handle *h, const void *buf, size_t bytes);
 
+/* Allocation-free stress pass (no counterpart in the paper; a library
+ * service).  For callers that cannot allocate device memory where they need
+ * the stress -- code inside another framework's memory pool or a fixed-budget
+ * arena, or code that must not call cudaMalloc/cudaFree because those calls
+ * synchronise the device.  Computes what hmc_compute_stress and
+ * hmc_get_stress give (stress of every point in FP32; mean stress and elastic
+ * energy reduced in FP64) from caller-owned DEVICE buffers, and allocates
+ * nothing: its only scratch, the per-CTA partial sums of the fixed-order
+ * reduction, lives in a static 512 KiB device array that every GPU loading
+ * the library holds until the process exits.
+ *   d_spins   N = nx*ny*nz orientation indices, natural order (device)
+ *   d_u       (nx/2)(ny/2)(nz/2) x 3 nodal displacements, FP32 (device)
+ *   d_ctab    Q x 36 rotated stiffness C'(q), full Voigt 6x6 row-major, FP32 (device)
+ *   strain_bar  6 doubles (HOST), mean strain, Voigt engineering shear
+ *   d_sigma   N x 6 FP32 output, natural order (device)
+ *   d_mean    6 doubles output (device);  d_energy  1 double output (device)
+ *   stream    cudaStream_t, NULL = legacy default stream
+ * Grids above 16,777,216 points (2,097,152 cells) are rejected with
+ * HMC_ERR_ARG.  Work is enqueued on `stream` and not waited for.  The first
+ * call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the scratch array: calls whose
+ * work overlaps on the GPU race.  Errors are reported through
+ * hmc_last_error(NULL). */
+hmc_status hmc_stress_noalloc(const uint16_t *d_spins, const float *d_u, const float *d_ctab,
+                              const double *strain_bar, int32_t nx, int32_t ny, int32_t nz, float *d_sigma,
+                              double *d_mean, double *d_energy, void *stream);
+
 /* Wait for all work on the handle's stream. */
 hmc_status hmc_synchronize(hmc_handle *h);
 

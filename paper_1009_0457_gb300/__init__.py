@@ -94,6 +94,8 @@ def _load():
         "hmc_get_state": (st, [H, C.c_void_p, C.POINTER(C.c_size_t)]),
         "hmc_set_state": (st, [H, C.c_void_p, C.c_size_t]),
         "hmc_synchronize": (st, [H]),
+        "hmc_stress_noalloc": (st, [C.c_void_p, C.c_void_p, C.c_void_p, dp, C.c_int32, C.c_int32, C.c_int32,
+                                    C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
         "hmc_last_error": (C.c_char_p, [H]),
     }
     for name, (res, args) in sig.items():
@@ -251,6 +253,14 @@ def hmc_get_state(h) -> bytes:
 def hmc_set_state(h, blob: bytes):
     buf = C.create_string_buffer(blob, len(blob))
     _check(h, lib.hmc_set_state(h, buf, len(blob)))
+
+
+def hmc_stress_noalloc(d_spins, d_u, d_ctab, strain_bar, nx, ny, nz, d_sigma, d_mean, d_energy, stream=None):
+    """Allocation-free stress pass on caller-owned device buffers (integer device
+    pointers, e.g. ``tensor.data_ptr()``); see include/hmc.h."""
+    e = np.ascontiguousarray(strain_bar, dtype=np.float64)
+    _check(None, lib.hmc_stress_noalloc(d_spins, d_u, d_ctab, _ptr(e, C.c_double), int(nx), int(ny), int(nz),
+                                        d_sigma, d_mean, d_energy, stream))
 
 
 def hmc_last_error(h=None) -> str:

@@ -24,6 +24,11 @@ int slot_local_h(int s) { static const int t[8] = {0, 3, 5, 6, 1, 2, 4, 7}; retu
 
 }  // namespace
 
+namespace hmc {
+// Error text for entry points that take no handle, returned by hmc_last_error(NULL).
+void set_unbound_error(const std::string &msg) { g_create_error = msg; }
+}  // namespace hmc
+
 struct hmc_handle {
     hmc_params p{};
     int nbx = 0, nby = 0, nbz = 0;
