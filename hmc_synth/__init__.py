@@ -124,11 +124,26 @@ WORKLOADS = {
 
 
 def workload_inputs(name: str):
-    """(spec, euler (Q,3), spins (nz,ny,nx) uint16) of a named workload."""
+    """(spec, euler (Q,3), spins (nz,ny,nx) uint16) of a named workload.  With
+    HMC_SYNTH_CACHE set to a directory, the Voronoi field is kept there as .npy
+    (it is a pure function of the workload's seeds)."""
+    import os
     w = dict(WORKLOADS[name])
     w.update(COMMON)
     euler = euler_uniform_so3(w["Q"], w["euler_seed"])
+    cache = os.environ.get("HMC_SYNTH_CACHE")
+    path = None
+    if cache:
+        os.makedirs(cache, exist_ok=True)
+        path = os.path.join(cache, f"{name}_voronoi_{w['n_seeds']}_{w['voronoi_seed']}.npy")
+        if os.path.exists(path):
+            spins = np.load(path)
+            if spins.shape == tuple(w["shape"]) and spins.dtype == np.uint16:
+                return w, euler, spins
     spins = voronoi_spins(w["shape"], w["n_seeds"], w["Q"], w["voronoi_seed"])
+    if path:
+        np.save(path + ".tmp.npy", spins)
+        os.replace(path + ".tmp.npy", path)
     return w, euler, spins
 
 

@@ -48,6 +48,7 @@ def lib():
         L.orc_point_stress.argtypes = [i, i, i, u16p, dp, dp, dp, i, i, i, dp]
         L.orc_internal_force.argtypes = [i, i, i, u16p, dp, dp, dp, dp]
         L.orc_lumped_mass.argtypes = [i, i, i, dp]
+        L.orc_node_force.argtypes = [i, i, i, u16p, dp, dp, dp, i, i, i, dp]
         L.orc_mpm_step.argtypes = [i, i, i, u16p, dp, dp, dp, dp, C.c_double, C.c_double, dp, dp]
         L.orc_stress_field.argtypes = [i, i, i, u16p, dp, dp, dp, dp, dp, dp]
         L.orc_point_zone_shift.argtypes = [dp, dp, dp]
@@ -58,6 +59,8 @@ def lib():
                                      C.c_double, C.c_double, i, i, i, C.c_double, dp, dp,
                                      u16p, dp, dp]
         L.orc_site_trial.restype = C.c_int
+        L.orc_site_trial_at.argtypes = L.orc_site_trial.argtypes
+        L.orc_site_trial_at.restype = C.c_int
         L.orc_half_sweep.argtypes = [i, i, i, u16p, i, C.c_uint64, C.c_uint32, C.c_uint32,
                                      C.c_double, C.c_double, i, i, i, C.c_double, dp, dp,
                                      u8p, dp, dp]
@@ -237,6 +240,17 @@ def internal_force(spins, Ct, u, Ebar):
     return f
 
 
+def node_force(spins, Ct, u, Ebar, i, j, k):
+    """Internal force of node (i,j,k), gathered over its 64 points."""
+    nz, ny, nx = spins.shape
+    s = np.ascontiguousarray(spins, dtype=np.uint16)
+    Cf, u, E = _f64(Ct), _f64(u), _f64(Ebar)
+    f = np.zeros(3)
+    lib().orc_node_force(nx, ny, nz, _p(s, C.c_uint16), _p(Cf, C.c_double), _p(u, C.c_double),
+                         _p(E, C.c_double), int(i), int(j), int(k), _p(f, C.c_double))
+    return f
+
+
 def lumped_mass(shape):
     nz, ny, nx = shape
     m = np.zeros((nz // 2) * (ny // 2) * (nx // 2))
@@ -300,6 +314,22 @@ def site_trial(spins, x, y, z, seed, mcs, replica, J, kT, trial, Q, elastic, lam
                                float(J), float(kT), int(trial), int(Q), int(elastic), float(lam),
                                _p(Sf, C.c_double), _p(sg, C.c_double), _p(qn, C.c_uint16),
                                _p(dH, C.c_double), _p(t, C.c_double))
+    return bool(acc), int(qn[0]), float(dH[0]), float(t[0])
+
+
+def site_trial_at(spins, x, y, z, seed, mcs, replica, J, kT, trial, Q, elastic, lam, St, sig_p):
+    """One trial with the site's own stress sig_p (6 values) instead of a whole field."""
+    nz, ny, nx = spins.shape
+    s = np.ascontiguousarray(spins, dtype=np.uint16)
+    Sf = _f64(St) if St is not None else np.zeros(36)
+    sg = _f64(sig_p) if sig_p is not None else np.zeros(6)
+    qn = np.zeros(1, dtype=np.uint16)
+    dH = np.zeros(1)
+    t = np.zeros(1)
+    acc = lib().orc_site_trial_at(nx, ny, nz, _p(s, C.c_uint16), x, y, z, int(seed), int(mcs), int(replica),
+                                  float(J), float(kT), int(trial), int(Q), int(elastic), float(lam),
+                                  _p(Sf, C.c_double), _p(sg, C.c_double), _p(qn, C.c_uint16),
+                                  _p(dH, C.c_double), _p(t, C.c_double))
     return bool(acc), int(qn[0]), float(dH[0]), float(t[0])
 
 

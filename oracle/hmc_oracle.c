@@ -267,6 +267,36 @@ void orc_internal_force(int nx, int ny, int nz, const uint16_t *spin, const doub
             }
 }
 
+/* Internal force of one node (i,j,k): the same sum as orc_internal_force,
+ * gathered over the 64 points of the node's eight cells. */
+void orc_node_force(int nx, int ny, int nz, const uint16_t *spin, const double *Ctab, const double *u,
+                    const double Ebar[6], int i, int j, int k, double f[3])
+{
+    f[0] = f[1] = f[2] = 0.0;
+    for (int dk = 0; dk < 2; ++dk)
+        for (int dj = 0; dj < 2; ++dj)
+            for (int di = 0; di < 2; ++di) {
+                /* the cell that has this node as corner (di,dj,dk) */
+                int cx = wrap(i - di, nx / 2), cy = wrap(j - dj, ny / 2), cz = wrap(k - dk, nz / 2);
+                for (int lz = 0; lz < 2; ++lz)
+                    for (int ly = 0; ly < 2; ++ly)
+                        for (int lx = 0; lx < 2; ++lx) {
+                            int x = 2 * cx + lx, y = 2 * cy + ly, z = 2 * cz + lz;
+                            double sig[6], xi[3], N, g[3];
+                            int ccx, ccy, ccz;
+                            orc_point_stress(nx, ny, nz, spin, Ctab, u, Ebar, x, y, z, sig);
+                            point_cell(x, y, z, &ccx, &ccy, &ccz, xi);
+                            trilinear(di, dj, dk, xi, &N, g);
+                            double S[3][3] = {{sig[0], sig[5], sig[4]}, {sig[5], sig[1], sig[3]}, {sig[4], sig[3], sig[2]}};
+                            for (int a = 0; a < 3; ++a) {
+                                double t = 0.0;
+                                for (int b = 0; b < 3; ++b) t += S[a][b] * g[b];
+                                f[a] -= MPM_VP * t;
+                            }
+                        }
+            }
+}
+
 /* Lumped nodal mass m_I = sum_p rho V_p N_I(x_p). */
 void orc_lumped_mass(int nx, int ny, int nz, double *m)
 {
@@ -364,11 +394,12 @@ enum { ORC_TRIAL_NEIGHBOR = 0, ORC_TRIAL_UNIFORM_Q = 1 };
  * current spin field (Eqs. 4-5 with the elastic shift of Eqs. 8 and 13).
  * Returns 1 if the spin changes.  *q_new receives the trial state, *dH the
  * total change in MC energy units, *thresh the Metropolis threshold
- * -kT ln u (or -1 when the integer table decided). */
-int orc_site_trial(int nx, int ny, int nz, const uint16_t *spin, int x, int y, int z,
-                   uint64_t seed, uint32_t mcs, uint32_t replica, double J, double kT,
-                   int trial_mode, int Q, int elastic, double lambda, const double *Stab,
-                   const double *sig, uint16_t *q_new, double *dH, double *thresh)
+ * -kT ln u (or -1 when the integer table decided).  sig_p is the site's
+ * stress (6 values; unused when the elastic term is off). */
+int orc_site_trial_at(int nx, int ny, int nz, const uint16_t *spin, int x, int y, int z,
+                      uint64_t seed, uint32_t mcs, uint32_t replica, double J, double kT,
+                      int trial_mode, int Q, int elastic, double lambda, const double *Stab,
+                      const double *sig_p, uint16_t *q_new, double *dH, double *thresh)
 {
     int64_t p = (int64_t)x + (int64_t)nx * ((int64_t)y + (int64_t)ny * z);
     uint32_t ctr[4] = {(uint32_t)p, mcs, replica, 0u};
@@ -404,7 +435,7 @@ int orc_site_trial(int nx, int ny, int nz, const uint16_t *spin, int x, int y, i
     }
     int dE = n_old - n_new;
     double dHe = 0.0;
-    if (elastic) dHe = lambda * orc_point_zone_shift(Stab + 36 * (int64_t)q, Stab + 36 * (int64_t)qt, sig + 6 * p);
+    if (elastic) dHe = lambda * orc_point_zone_shift(Stab + 36 * (int64_t)q, Stab + 36 * (int64_t)qt, sig_p);
     if (dHe == 0.0) {
         *dH = J * dE;
         if (dE <= 0) return 1;
@@ -416,6 +447,17 @@ int orc_site_trial(int nx, int ny, int nz, const uint16_t *spin, int x, int y, i
     *dH = H;
     *thresh = t;
     return H <= t;
+}
+
+/* The same trial with the stress taken from a whole field (N x 6). */
+int orc_site_trial(int nx, int ny, int nz, const uint16_t *spin, int x, int y, int z,
+                   uint64_t seed, uint32_t mcs, uint32_t replica, double J, double kT,
+                   int trial_mode, int Q, int elastic, double lambda, const double *Stab,
+                   const double *sig, uint16_t *q_new, double *dH, double *thresh)
+{
+    int64_t p = (int64_t)x + (int64_t)nx * ((int64_t)y + (int64_t)ny * z);
+    return orc_site_trial_at(nx, ny, nz, spin, x, y, z, seed, mcs, replica, J, kT, trial_mode, Q, elastic,
+                             lambda, Stab, elastic ? sig + 6 * p : NULL, q_new, dH, thresh);
 }
 
 /* Red/black half sweep (Sec. "Microstructural Evolution"): every site of one

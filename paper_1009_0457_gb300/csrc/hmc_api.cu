@@ -35,7 +35,7 @@ struct hmc_handle {
     long long nblk = 0, N = 0, nnodes = 0;
     cudaStream_t stream = nullptr, cap = nullptr;
     bool own_stream = false, oriented = false;
-    int num_sms = 0, zc = 4, nparts = 0;
+    int num_sms = 0, mpm_grid = 1, nparts = 0;
     size_t tsize = 4;
     // device buffers
     uint4 *spins = nullptr;
@@ -163,7 +163,10 @@ cudaError_t enqueue_mpm(hmc_handle *h, cudaStream_t s) {
     a.v = static_cast<T *>(h->v);
     a.ctab = static_cast<const T *>(h->ctab);
     a.st = h->st;
-    a.nbx = h->nbx; a.nby = h->nby; a.nbz = h->nbz; a.zc = h->zc;
+    a.nbx = h->nbx; a.nby = h->nby; a.nbz = h->nbz;
+    a.tiles_x = hmc::mpm_tiles(h->nbx);
+    a.tiles_y = hmc::mpm_tiles(h->nby);
+    a.grid = h->mpm_grid;
     a.dt = (T)h->dt;
     a.dt_over_m = (T)(h->dt / 8.0);  // lumped mass rho * V * sum_p N_I(x_p) = 8 voxels
     a.keep = (T)(1.0 - h->damping);
@@ -400,7 +403,9 @@ hmc_status hmc_create(const hmc_params *p, hmc_handle **out) {
     }
     if ((e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking)) != cudaSuccess)
         return bail(cuda_fail(h, e, "capture stream create"));
-    h->zc = hmc::mpm_zchunk(h->nbx, h->nby, h->nbz, h->num_sms);
+    if ((e = hmc::mpm_prepare()) != cudaSuccess) return bail(cuda_fail(h, e, "MPM kernel attribute"));
+    h->mpm_grid = p->precision == HMC_FP32 ? hmc::mpm_grid<float>(h->nbx, h->nby, h->nbz, h->num_sms)
+                                           : hmc::mpm_grid<double>(h->nbx, h->nby, h->nbz, h->num_sms);
     h->nparts = hmc::stress_grid(h->nblk);
     struct Alloc { void **ptr; size_t bytes; const char *what; };
     const size_t nodes_b = h->tsize * 3 * (size_t)h->nnodes;
@@ -442,8 +447,6 @@ hmc_status hmc_create(const hmc_params *p, hmc_handle **out) {
     void *zero_ptrs[] = {h->u[0], h->u[1], h->v};
     for (int i = 0; i < 3; ++i)
         if ((e = cudaMemset(zero_ptrs[i], 0, zero_bytes[i])) != cudaSuccess) return bail(cuda_fail(h, e, "memset"));
-    // the MPM kernel's dynamic shared memory opt-in, set before any capture
-    if ((e = hmc::mpm_prepare()) != cudaSuccess) return bail(cuda_fail(h, e, "MPM kernel attribute"));
     *out = h;
     return HMC_OK;
 }

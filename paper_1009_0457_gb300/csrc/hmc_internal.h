@@ -50,7 +50,9 @@ struct MpmArgs {
     T *v;
     const T *ctab;
     const DevState *st;
-    int nbx, nby, nbz, zc;
+    int nbx, nby, nbz;
+    int tiles_x, tiles_y;    // 15-node tiles per edge
+    int grid;                // persistent CTAs
     T dt, dt_over_m, keep;   // keep = 1 - damping
 };
 
@@ -89,7 +91,9 @@ template <typename T>
 cudaError_t launch_sweep(const SweepArgs<T> &a, int colour, bool elastic, cudaStream_t s);
 int stress_grid(long long nblk);
 cudaError_t mpm_prepare();  // opt the MPM kernel into its dynamic shared memory (once, before any capture)
-int mpm_zchunk(int nbx, int nby, int nbz, int num_sms);
+int mpm_tiles(int nb);      // node tiles along one edge
+template <typename T>
+int mpm_grid(int nbx, int nby, int nbz, int num_sms);
 
 cudaError_t launch_end_mcs(DevState *st, const double *partials, int nparts, long long n_sites,
                            int update_strain, int advance, cudaStream_t s);

@@ -116,6 +116,14 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs<T> a, int colour) {
             }
         }
         const uint32_t mcs = a.st->mcs;
+        // the four sites' Philox draws first: four independent chains for the scheduler
+        uint2 rnd[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int L = slot_local(4 * colour + i);
+            const uint32_t x = 2u * bx + (L & 1), y = 2u * by + ((L >> 1) & 1), z = 2u * bz + (L >> 2);
+            rnd[i] = philox_r01(x + (uint32_t)a.nx * (y + (uint32_t)a.ny * z), mcs, a.replica, 0u, a.key0, a.key1);
+        }
         uint16_t out[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
@@ -129,9 +137,7 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs<T> a, int colour) {
             nb[3] = quad_get(ly ? Oyp : O, i ^ 1);
             nb[4] = quad_get(lz ? O : Ozm, i ^ 2);
             nb[5] = quad_get(lz ? Ozp : O, i ^ 2);
-            const uint32_t x = 2u * bx + lx, y = 2u * by + ly, z = 2u * bz + lz;
-            const uint32_t site = x + (uint32_t)a.nx * (y + (uint32_t)a.ny * z);
-            const uint2 rn = philox_r01(site, mcs, a.replica, 0u, a.key0, a.key1);
+            const uint2 rn = rnd[i];
             uint16_t qn;
             if (a.trial == 0) {
                 const uint32_t k = __umulhi(rn.x, 6u);

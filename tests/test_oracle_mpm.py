@@ -60,6 +60,16 @@ def test_force_matches_assembled_stiffness(poly8):
         assert np.allclose(O.point_strain(poly8["shape"], u, E, x, y, z), E + poly8["Bs"][p] @ u.ravel(), atol=1e-16)
 
 
+def test_node_force_gather_equals_scatter(poly8):
+    rng = np.random.default_rng(3)
+    u = rng.normal(size=(64, 3)) * 1e-3
+    E = rng.normal(size=6) * 1e-3
+    f = O.internal_force(poly8["sp"], poly8["Ct"], u, E)
+    for I in range(64):
+        i, j, k = I % 4, (I // 4) % 4, I // 16
+        assert np.allclose(O.node_force(poly8["sp"], poly8["Ct"], u, E, i, j, k), f[I], rtol=1e-12, atol=1e-15)
+
+
 def test_homogeneous_block_closed_form():
     """A single orientation under uniaxial control: sigma = eps0 / (n.S'.n) n(x)n at once, u stays 0."""
     rng = np.random.default_rng(5)
