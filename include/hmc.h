@@ -110,6 +110,30 @@ void hmc_default_params(hmc_params *p);
  * and allocates every device buffer for the grid.  *out is NULL on failure. */
 hmc_status hmc_create(const hmc_params *p, hmc_handle **out);
 
+/* Batched ensemble: one handle holding n_replicas independent replicas
+ * (params[r] for replica r), each swept in the same launches -- every phase of
+ * the Monte Carlo step (MPM step, stress, half sweeps, end of step) is one
+ * launch over all replicas, replayed from one CUDA graph.  Replicas may differ
+ * in nx, ny, nz, load_axis, strain, strain6, elastic_scale, seed and replica;
+ * all other fields must be equal (HMC_ERR_ARG otherwise).  Each replica's
+ * spins, stress and Monte Carlo stream are exactly those of the same
+ * replica run alone.  hmc_create(p, out) is hmc_batch_create(p, 1, out). */
+hmc_status hmc_batch_create(const hmc_params *params, int32_t n_replicas, hmc_handle **out);
+
+/* Select the replica that the per-replica accessors act on (hmc_set_spins,
+ * hmc_get_spins, hmc_get/set_stress, hmc_get/set_nodal, hmc_get/set_strain,
+ * hmc_texture_histogram, hmc_energy, hmc_get_info, hmc_get/set_state);
+ * replica 0 after creation. */
+hmc_status hmc_select_replica(hmc_handle *h, int32_t r);
+
+/* Launch configuration chosen by the autotuner at the first MPM step (or the
+ * default before it): MPM patch shape (0: 16x16 cells, 1: 32x8, 2: 8x32) and
+ * the number of persistent MPM CTAs.  The autotuner times every candidate on
+ * scratch copies of the nodal state; all candidates give bit-identical
+ * results.  Environment variable HMC_AUTOTUNE=0 keeps the 16x16 default;
+ * HMC_MPM_SHAPE=0|1|2 forces one shape. */
+hmc_status hmc_get_tuning(hmc_handle *h, int32_t *mpm_shape, int32_t *mpm_grid);
+
 /* Release the handle and all its device memory (NULL is a no-op). */
 void hmc_destroy(hmc_handle *h);
 
@@ -117,7 +141,8 @@ void hmc_destroy(hmc_handle *h);
  * Eqs. 16-18; Sec. "Results", random initial orientations).
  *   euler_zyz: Q x 3 doubles (phi, theta, psi), radians; A = Rz(phi) Ry(theta)
  *              Rz(psi) maps crystal-frame vectors to the sample frame.
- *   spins:     N = nx*ny*nz orientation indices 0..Q-1, natural order.
+ *   spins:     N = nx*ny*nz orientation indices 0..Q-1, natural order (for a
+ *              batch: every replica's field in replica order, back to back).
  * Builds the rotated stiffness C'(q) (Voigt 6x6) and the zone-energy table in
  * FP64 on the host, uploads them and the spins, zeroes the nodal displacement
  * and velocity, resets the MC step counter to 0, and sets the mean strain
@@ -162,7 +187,7 @@ hmc_status hmc_end_mcs(hmc_handle *h);
 /* n_mcs Monte Carlo steps, each: mpm_steps_per_mcs MPM steps, stress, red
  * half sweep, black half sweep (stress frozen over the step), end of step.
  * Replayed from a captured CUDA graph.  *accepted (nullable) receives the
- * number of spin changes over all n_mcs steps. */
+ * number of spin changes over all n_mcs steps and all replicas. */
 hmc_status hmc_mc_sweeps(hmc_handle *h, int32_t n_mcs, int64_t *accepted);
 
 /* Texture of the current spin field (Sec. "Results").  counts_per_q (Q int64,

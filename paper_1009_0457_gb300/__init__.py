@@ -73,6 +73,9 @@ def _load():
     sig = {
         "hmc_default_params": (None, [C.POINTER(hmc_params)]),
         "hmc_create": (st, [C.POINTER(hmc_params), C.POINTER(H)]),
+        "hmc_batch_create": (st, [C.POINTER(hmc_params), C.c_int32, C.POINTER(H)]),
+        "hmc_select_replica": (st, [H, C.c_int32]),
+        "hmc_get_tuning": (st, [H, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
         "hmc_destroy": (None, [H]),
         "hmc_set_orientations": (st, [H, dp, u16p]),
         "hmc_set_spins": (st, [H, u16p]),
@@ -136,6 +139,24 @@ def hmc_create(p: hmc_params):
     h = C.c_void_p()
     _check(None, lib.hmc_create(C.byref(p), C.byref(h)))
     return h
+
+
+def hmc_batch_create(params):
+    """One handle over len(params) replicas (a sequence of hmc_params)."""
+    arr = (hmc_params * len(params))(*params)
+    h = C.c_void_p()
+    _check(None, lib.hmc_batch_create(arr, len(params), C.byref(h)))
+    return h
+
+
+def hmc_select_replica(h, r):
+    _check(h, lib.hmc_select_replica(h, int(r)))
+
+
+def hmc_get_tuning(h):
+    s, g = C.c_int32(), C.c_int32()
+    _check(h, lib.hmc_get_tuning(h, C.byref(s), C.byref(g)))
+    return s.value, g.value
 
 
 def hmc_destroy(h):
@@ -283,6 +304,9 @@ class HMC:
         self.n_sites = nx * ny * nz
         self.n_nodes = self.n_sites // 8
 
+    def tuning(self):
+        return hmc_get_tuning(self.h)
+
     def close(self):
         if self.h:
             hmc_destroy(self.h)
@@ -356,6 +380,67 @@ class HMC:
 
     def set_state(self, blob):
         hmc_set_state(self.h, blob)
+
+    def synchronize(self):
+        hmc_synchronize(self.h)
+
+
+class HMCBatch:
+    """A batched ensemble: replica r has shape shapes[r] = (nz, ny, nx) and the
+    keyword overrides per_replica[r]; ``common`` applies to all."""
+
+    def __init__(self, shapes, n_orient, per_replica=None, **common):
+        self.shapes = [tuple(s) for s in shapes]
+        self.n_orient = n_orient
+        per_replica = per_replica or [{} for _ in shapes]
+        self.params = []
+        for (nz, ny, nx), kw in zip(self.shapes, per_replica):
+            d = dict(common)
+            d.update(kw)
+            self.params.append(hmc_default_params(nx=nx, ny=ny, nz=nz, n_orient=n_orient, **d))
+        self.h = hmc_batch_create(self.params)
+        self.sel = 0
+
+    def close(self):
+        if self.h:
+            hmc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def select(self, r):
+        hmc_select_replica(self.h, r)
+        self.sel = r
+
+    def set_orientations(self, euler, spins_list):
+        flat = np.concatenate([np.asarray(s, dtype=np.uint16).reshape(-1) for s in spins_list])
+        hmc_set_orientations(self.h, euler, flat)
+
+    def spins(self, r):
+        self.select(r)
+        n = int(np.prod(self.shapes[r]))
+        return hmc_get_spins(self.h, np.zeros(n, dtype=np.uint16)).reshape(self.shapes[r])
+
+    def nodal(self, r):
+        self.select(r)
+        return hmc_get_nodal(self.h, int(np.prod(self.shapes[r])) // 8)
+
+    def strain(self, r):
+        self.select(r)
+        return hmc_get_strain(self.h)
+
+    def mc_sweeps(self, n):
+        return hmc_mc_sweeps(self.h, n)
+
+    def mpm_steps(self, n):
+        return hmc_mpm_steps(self.h, n)
+
+    def tuning(self):
+        return hmc_get_tuning(self.h)
 
     def synchronize(self):
         hmc_synchronize(self.h)

@@ -1,11 +1,19 @@
 // C ABI of libhmc (declared and documented in include/hmc.h): handle lifetime,
-// host-side orientation tables in FP64, device buffers, and the stream order of
-// the Monte Carlo step.  Host code only; the kernels live in k_*.cu.
+// host-side orientation tables in FP64, device buffers, the stream order of
+// the Monte Carlo step, and the launch-shape autotuner.  A handle holds a
+// batch of replicas (hmc_create makes a batch of one); every kernel of the
+// Monte Carlo step runs once per phase over all replicas.  Host code only;
+// the kernels live in k_*.cu.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "hmc.h"
@@ -22,6 +30,20 @@ constexpr double kGammaStar = 2.4, kGammaS = 0.45, kL0 = 1.0e-3;
 
 int slot_local_h(int s) { static const int t[8] = {0, 3, 5, 6, 1, 2, 4, 7}; return t[s]; }
 
+// Autotuner results, per batch signature, for the life of the process.
+std::mutex g_tune_mutex;
+std::map<std::string, std::pair<int, int>> g_tune_cache;
+
+// Host view of one replica.
+struct RepHost {
+    hmc_params p{};
+    int nbx = 0, nby = 0, nbz = 0;
+    long long nblk = 0, N = 0, blk_off = 0;
+    int cta_off = 0, ncta = 0;
+    double axis[3] = {0, 0, 1};
+    double lam = 0, lam_sd_half = 0;
+};
+
 }  // namespace
 
 namespace hmc {
@@ -30,12 +52,14 @@ void set_unbound_error(const std::string &msg) { g_create_error = msg; }
 }  // namespace hmc
 
 struct hmc_handle {
-    hmc_params p{};
-    int nbx = 0, nby = 0, nbz = 0;
-    long long nblk = 0, N = 0, nnodes = 0;
+    hmc_params p{};                 // shared parameters (replica 0's copy)
+    std::vector<RepHost> reps;
+    int R = 1, sel = 0;
+    long long nblk_total = 0, N_total = 0, N_max = 0;
+    int nctas = 0;
     cudaStream_t stream = nullptr, cap = nullptr;
     bool own_stream = false, oriented = false;
-    int num_sms = 0, mpm_grid = 1, nparts = 0;
+    int num_sms = 0;
     size_t tsize = 4;
     // device buffers
     uint4 *spins = nullptr;
@@ -48,10 +72,16 @@ struct hmc_handle {
     double *partials = nullptr, *fractions = nullptr;
     int32_t *binmap = nullptr;
     int bins_cap = 0;
-    DevState *st = nullptr;
+    DevState *st = nullptr;               // R device states
+    hmc::Replica *d_reps = nullptr;       // R descriptors
+    int *d_cta_rep = nullptr;             // replica of every sweep / stress CTA
+    hmc::MpmSched *d_sched = nullptr;     // R + 1 MPM schedules for the chosen shape
+    // MPM launch configuration (autotuned)
+    int mpm_shape = hmc::MPM_16x16, mpm_grid = 1;
+    long long mpm_total = 0;
+    bool tuned = false;
     // derived scalars
-    double dt = 0, damping = 0, lam = 0, lam_sd_half = 0, S11 = 0, S12 = 0, S44 = 0;
-    double axis[3] = {0, 0, 1};
+    double dt = 0, damping = 0, S11 = 0, S12 = 0, S44 = 0;
     // host tables (FP64)
     std::vector<double> A, Cv, Sv;
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
@@ -78,6 +108,10 @@ hmc_status cuda_fail(hmc_handle *h, cudaError_t e, const char *what) {
         cudaError_t e_ = (call);                          \
         if (e_ != cudaSuccess) return cuda_fail(h, e_, what); \
     } while (0)
+
+RepHost &selr(hmc_handle *h) { return h->reps[h->sel]; }
+DevState *sel_st(hmc_handle *h) { return h->st + h->sel; }
+size_t node_bytes(const hmc_handle *h) { return h->tsize * 3 * (size_t)h->nblk_total; }
 
 // ---- FP64 host tables -------------------------------------------------------
 
@@ -155,22 +189,30 @@ void axis_vectors(const double *n, double *N, double *Nsv) {
 // ---- launches ---------------------------------------------------------------
 
 template <typename T>
-cudaError_t enqueue_mpm(hmc_handle *h, cudaStream_t s) {
+hmc::MpmArgs<T> mpm_args(hmc_handle *h, const void *u_in, void *u_out, void *v) {
     hmc::MpmArgs<T> a;
+    a.reps = h->d_reps;
+    a.sched = h->d_sched;
+    a.nrep = h->R;
+    a.total = h->mpm_total;
     a.spins = h->spins;
-    a.u_in = static_cast<const T *>(h->u[h->cur]);
-    a.u_out = static_cast<T *>(h->u[h->cur ^ 1]);
-    a.v = static_cast<T *>(h->v);
+    a.u_in = static_cast<const T *>(u_in);
+    a.u_out = static_cast<T *>(u_out);
+    a.v = static_cast<T *>(v);
     a.ctab = static_cast<const T *>(h->ctab);
-    a.st = h->st;
-    a.nbx = h->nbx; a.nby = h->nby; a.nbz = h->nbz;
-    a.tiles_x = hmc::mpm_tiles(h->nbx);
-    a.tiles_y = hmc::mpm_tiles(h->nby);
-    a.grid = h->mpm_grid;
     a.dt = (T)h->dt;
     a.dt_over_m = (T)(h->dt / 8.0);  // lumped mass rho * V * sum_p N_I(x_p) = 8 voxels
     a.keep = (T)(1.0 - h->damping);
-    cudaError_t e = hmc::launch_mpm_step<T>(a, s);
+    a.grid = h->mpm_grid;
+    return a;
+}
+
+cudaError_t enq_mpm(hmc_handle *h, cudaStream_t s) {
+    cudaError_t e;
+    if (h->p.precision == HMC_FP32)
+        e = hmc::launch_mpm_step<float>(mpm_args<float>(h, h->u[h->cur], h->u[h->cur ^ 1], h->v), h->mpm_shape, s);
+    else
+        e = hmc::launch_mpm_step<double>(mpm_args<double>(h, h->u[h->cur], h->u[h->cur ^ 1], h->v), h->mpm_shape, s);
     h->cur ^= 1;
     return e;
 }
@@ -178,42 +220,34 @@ cudaError_t enqueue_mpm(hmc_handle *h, cudaStream_t s) {
 template <typename T>
 cudaError_t enqueue_stress(hmc_handle *h, cudaStream_t s) {
     hmc::StressArgs<T> a;
+    a.reps = h->d_reps;
+    a.cta_rep = h->d_cta_rep;
     a.spins = h->spins;
     a.u = static_cast<const T *>(h->u[h->cur]);
     a.ctab = static_cast<const T *>(h->ctab);
-    a.st = h->st;
     a.sig = static_cast<T *>(h->sig);
     a.partials = h->partials;
-    a.nbx = h->nbx; a.nby = h->nby; a.nbz = h->nbz;
-    a.nblk = h->nblk;
-    return hmc::launch_stress<T>(a, h->nparts, s);
+    a.nctas = h->nctas;
+    return hmc::launch_stress<T>(a, s);
 }
 
 template <typename T>
 cudaError_t enqueue_sweep(hmc_handle *h, int colour, cudaStream_t s) {
     hmc::SweepArgs<T> a;
+    a.reps = h->d_reps;
+    a.cta_rep = h->d_cta_rep;
     a.spins = h->spins;
     a.sig = static_cast<const T *>(h->sig);
     a.wtab = static_cast<const T *>(h->wtab);
     a.thr = h->thr;
-    a.st = h->st;
-    a.nx = h->p.nx; a.ny = h->p.ny; a.nz = h->p.nz;
-    a.nbx = h->nbx; a.nby = h->nby; a.nbz = h->nbz;
-    a.nblk = h->nblk;
-    a.key0 = (uint32_t)(h->p.seed & 0xffffffffull);
-    a.key1 = (uint32_t)(h->p.seed >> 32);
-    a.replica = h->p.replica;
     a.trial = h->p.trial;
     a.nq = h->p.n_orient;
     a.J = (T)h->p.J;
     a.kT = (T)h->p.kT;
-    a.lam_sd_half = (T)h->lam_sd_half;
+    a.nctas = h->nctas;
     return hmc::launch_sweep<T>(a, colour, h->p.elastic == HMC_ELASTIC_TRACTION, s);
 }
 
-cudaError_t enq_mpm(hmc_handle *h, cudaStream_t s) {
-    return h->p.precision == HMC_FP32 ? enqueue_mpm<float>(h, s) : enqueue_mpm<double>(h, s);
-}
 cudaError_t enq_stress(hmc_handle *h, cudaStream_t s) {
     return h->p.precision == HMC_FP32 ? enqueue_stress<float>(h, s) : enqueue_stress<double>(h, s);
 }
@@ -221,7 +255,7 @@ cudaError_t enq_sweep(hmc_handle *h, int c, cudaStream_t s) {
     return h->p.precision == HMC_FP32 ? enqueue_sweep<float>(h, c, s) : enqueue_sweep<double>(h, c, s);
 }
 
-// One Monte Carlo step on stream s (also used while capturing the graph).
+// One Monte Carlo step of every replica on stream s (also used while capturing the graph).
 cudaError_t enqueue_mcs(hmc_handle *h, cudaStream_t s) {
     cudaError_t e;
     for (int k = 0; k < h->p.mpm_steps_per_mcs; ++k)
@@ -229,7 +263,23 @@ cudaError_t enqueue_mcs(hmc_handle *h, cudaStream_t s) {
     if ((e = enq_stress(h, s)) != cudaSuccess) return e;
     if ((e = enq_sweep(h, 0, s)) != cudaSuccess) return e;
     if ((e = enq_sweep(h, 1, s)) != cudaSuccess) return e;
-    return hmc::launch_end_mcs(h->st, h->partials, h->nparts, h->N, 1, 1, s);
+    return hmc::launch_end_mcs(h->d_reps, h->R, h->partials, 1, 1, s);
+}
+
+cudaError_t reset_accepted(hmc_handle *h) {
+    return cudaMemset2DAsync(&h->st->accepted, sizeof(DevState), 0, sizeof(unsigned long long), h->R, h->stream);
+}
+
+hmc_status read_accepted(hmc_handle *h, int64_t *acc) {
+    std::vector<unsigned long long> a(h->R);
+    HMC_CK(h, cudaMemcpy2DAsync(a.data(), sizeof(unsigned long long), &h->st->accepted, sizeof(DevState),
+                                sizeof(unsigned long long), h->R, cudaMemcpyDeviceToHost, h->stream),
+           "download");
+    HMC_CK(h, cudaStreamSynchronize(h->stream), "sync");
+    int64_t s = 0;
+    for (auto x : a) s += (int64_t)x;
+    *acc = s;
+    return HMC_OK;
 }
 
 hmc_status need_oriented(hmc_handle *h) {
@@ -238,22 +288,27 @@ hmc_status need_oriented(hmc_handle *h) {
     return HMC_OK;
 }
 
-// Copy a natural-order spin field to the device, check every index < Q there
-// (the handle's field is untouched if one is not), then pack it into blocks.
-hmc_status upload_spins(hmc_handle *h, const uint16_t *spins) {
+// Copy one replica's natural-order spin field to the device, check every index
+// < Q there (the replica's field is untouched if one is not), then pack it.
+hmc_status upload_spins(hmc_handle *h, int r, const uint16_t *spins) {
+    RepHost &R = h->reps[r];
     int bad = 0;
-    HMC_CK(h, cudaMemcpyAsync(h->stage16, spins, sizeof(uint16_t) * h->N, cudaMemcpyHostToDevice, h->stream), "spin upload");
-    HMC_CK(h, cudaMemsetAsync(&h->st->bad_spin, 0, sizeof(int32_t), h->stream), "memset");
-    HMC_CK(h, hmc::launch_check_spins(h->stage16, h->N, h->p.n_orient, h->st, h->stream), "spin check");
-    HMC_CK(h, cudaMemcpyAsync(&bad, &h->st->bad_spin, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream), "download");
+    HMC_CK(h, cudaMemcpyAsync(h->stage16, spins, sizeof(uint16_t) * R.N, cudaMemcpyHostToDevice, h->stream),
+           "spin upload");
+    HMC_CK(h, cudaMemsetAsync(&h->st[r].bad_spin, 0, sizeof(int32_t), h->stream), "memset");
+    HMC_CK(h, hmc::launch_check_spins(h->stage16, R.N, h->p.n_orient, h->st + r, h->stream), "spin check");
+    HMC_CK(h, cudaMemcpyAsync(&bad, &h->st[r].bad_spin, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream),
+           "download");
     HMC_CK(h, cudaStreamSynchronize(h->stream), "sync");
     if (bad) {
-        for (long long i = 0; i < h->N; ++i)
+        for (long long i = 0; i < R.N; ++i)
             if (spins[i] >= (uint32_t)h->p.n_orient)
-                return fail(h, HMC_ERR_ARG, "spin value >= n_orient at site " + std::to_string(i));
+                return fail(h, HMC_ERR_ARG, "spin value >= n_orient at site " + std::to_string(i) +
+                                                (h->R > 1 ? " of replica " + std::to_string(r) : ""));
         return fail(h, HMC_ERR_ARG, "spin value >= n_orient");
     }
-    HMC_CK(h, hmc::launch_pack_spins(h->stage16, h->spins, h->p.nx, h->p.ny, h->p.nz, h->stream), "pack spins");
+    HMC_CK(h, hmc::launch_pack_spins(h->stage16, h->spins + R.blk_off, R.p.nx, R.p.ny, R.p.nz, h->stream),
+           "pack spins");
     return HMC_OK;
 }
 
@@ -276,7 +331,8 @@ std::string validate(const hmc_params *p) {
     // cubic stability: C11 - C12 > 0, C11 + 2 C12 > 0, C44 > 0
     if (!(p->c11 - p->c12 > 0 && p->c11 + 2 * p->c12 > 0 && p->c44 > 0)) return "stiffness not positive definite";
     if (p->bc == HMC_BC_UNIAXIAL) {
-        const double n2 = p->load_axis[0] * p->load_axis[0] + p->load_axis[1] * p->load_axis[1] + p->load_axis[2] * p->load_axis[2];
+        const double n2 = p->load_axis[0] * p->load_axis[0] + p->load_axis[1] * p->load_axis[1] +
+                          p->load_axis[2] * p->load_axis[2];
         if (!(n2 > 0) || !std::isfinite(n2)) return "load_axis must be a non-zero finite vector";
     }
     for (int i = 0; i < 6; ++i)
@@ -284,11 +340,22 @@ std::string validate(const hmc_params *p) {
     return "";
 }
 
+// Fields every replica of a batch must share.
+std::string validate_shared(const hmc_params *a, const hmc_params *b) {
+    if (a->n_orient != b->n_orient || a->J != b->J || a->kT != b->kT || a->c11 != b->c11 || a->c12 != b->c12 ||
+        a->c44 != b->c44 || a->bc != b->bc || a->elastic != b->elastic || a->trial != b->trial ||
+        a->mpm_steps_per_mcs != b->mpm_steps_per_mcs || a->dt != b->dt || a->damping != b->damping ||
+        a->precision != b->precision || a->stream != b->stream)
+        return "replicas of a batch must share n_orient, J, kT, c11, c12, c44, bc, elastic, trial, "
+               "mpm_steps_per_mcs, dt, damping, precision and stream";
+    return "";
+}
+
 void destroy_buffers(hmc_handle *h) {
     for (int i = 0; i < 2; ++i)
         if (h->gexec[i]) cudaGraphExecDestroy(h->gexec[i]);
     void *bufs[] = {h->spins, h->stage16, h->u[0], h->u[1], h->v, h->sig, h->ctab, h->wtab, h->thr, h->counts,
-                    h->bins, h->partials, h->fractions, h->binmap, h->st};
+                    h->bins, h->partials, h->fractions, h->binmap, h->st, h->d_reps, h->d_cta_rep, h->d_sched};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (h->cap) cudaStreamDestroy(h->cap);
@@ -296,36 +363,212 @@ void destroy_buffers(hmc_handle *h) {
 }
 
 template <typename T>
-void unpack_stress_host(const hmc_handle *h, const std::vector<T> &packed, double *out) {
-    const int nx = h->p.nx, ny = h->p.ny;
-    for (long long b = 0; b < h->nblk; ++b) {
-        const int bx = (int)(b % h->nbx);
-        const long long r = b / h->nbx;
-        const int by = (int)(r % h->nby), bz = (int)(r / h->nby);
+void unpack_stress_host(const RepHost &R, const std::vector<T> &packed, double *out) {
+    const int nx = R.p.nx, ny = R.p.ny;
+    for (long long b = 0; b < R.nblk; ++b) {
+        const int bx = (int)(b % R.nbx);
+        const long long r = b / R.nbx;
+        const int by = (int)(r % R.nby), bz = (int)(r / R.nby);
         for (int s = 0; s < 8; ++s) {
             const int L = slot_local_h(s), c = s >> 2, i = s & 3;
             const long long x = 2 * bx + (L & 1), y = 2 * by + ((L >> 1) & 1), z = 2 * bz + (L >> 2);
             const long long p = x + nx * (y + (long long)ny * z);
-            for (int k = 0; k < 6; ++k) out[6 * p + k] = (double)packed[4 * ((size_t)(c * 6 + k) * h->nblk + b) + i];
+            for (int k = 0; k < 6; ++k) out[6 * p + k] = (double)packed[4 * ((size_t)(c * 6 + k) * R.nblk + b) + i];
         }
     }
 }
 
 template <typename T>
-void pack_stress_host(const hmc_handle *h, const double *in, std::vector<T> &packed) {
-    const int nx = h->p.nx, ny = h->p.ny;
-    for (long long b = 0; b < h->nblk; ++b) {
-        const int bx = (int)(b % h->nbx);
-        const long long r = b / h->nbx;
-        const int by = (int)(r % h->nby), bz = (int)(r / h->nby);
+void pack_stress_host(const RepHost &R, const double *in, std::vector<T> &packed) {
+    const int nx = R.p.nx, ny = R.p.ny;
+    for (long long b = 0; b < R.nblk; ++b) {
+        const int bx = (int)(b % R.nbx);
+        const long long r = b / R.nbx;
+        const int by = (int)(r % R.nby), bz = (int)(r / R.nby);
         for (int s = 0; s < 8; ++s) {
             const int L = slot_local_h(s), c = s >> 2, i = s & 3;
             const long long x = 2 * bx + (L & 1), y = 2 * by + ((L >> 1) & 1), z = 2 * bz + (L >> 2);
             const long long p = x + nx * (y + (long long)ny * z);
-            for (int k = 0; k < 6; ++k) packed[4 * ((size_t)(c * 6 + k) * h->nblk + b) + i] = (T)in[6 * p + k];
+            for (int k = 0; k < 6; ++k) packed[4 * ((size_t)(c * 6 + k) * R.nblk + b) + i] = (T)in[6 * p + k];
         }
     }
 }
+
+// ---- MPM schedule and autotuner --------------------------------------------
+
+hmc_status upload_sched(hmc_handle *h, int shape) {
+    const int ox = hmc::mpm_shape_cx(shape) - 1, oy = hmc::mpm_shape_cy(shape) - 1;
+    std::vector<hmc::MpmSched> sc(h->R + 1);
+    long long off = 0;
+    for (int r = 0; r < h->R; ++r) {
+        const RepHost &R = h->reps[r];
+        sc[r].tiles_x = (R.nbx + ox - 1) / ox;
+        sc[r].tiles_y = (R.nby + oy - 1) / oy;
+        sc[r].plane_off = off;
+        off += (long long)sc[r].tiles_x * sc[r].tiles_y * R.nbz;
+    }
+    sc[h->R].tiles_x = sc[h->R].tiles_y = 0;
+    sc[h->R].plane_off = off;
+    h->mpm_total = off;
+    HMC_CK(h, cudaStreamSynchronize(h->stream), "sync");
+    HMC_CK(h, cudaMemcpy(h->d_sched, sc.data(), sizeof(hmc::MpmSched) * sc.size(), cudaMemcpyHostToDevice),
+           "schedule upload");
+    return HMC_OK;
+}
+
+int grid_for_shape(hmc_handle *h, int shape, int per_sm_limit) {
+    int per_sm = h->p.precision == HMC_FP32 ? hmc::mpm_per_sm<float>(shape) : hmc::mpm_per_sm<double>(shape);
+    if (per_sm_limit > 0 && per_sm > per_sm_limit) per_sm = per_sm_limit;
+    long long g = (long long)per_sm * h->num_sms;
+    const long long cap = (h->mpm_total + 3) / 4;  // at least four planes per CTA
+    if (g > cap) g = cap;
+    return (int)(g < 1 ? 1 : g);
+}
+
+std::string tune_signature(const hmc_handle *h) {
+    std::string s = std::to_string(h->p.precision) + ":" + std::to_string(h->num_sms);
+    for (const auto &R : h->reps)
+        s += ":" + std::to_string(R.nbx) + "x" + std::to_string(R.nby) + "x" + std::to_string(R.nbz);
+    return s;
+}
+
+// Pick the MPM patch shape and persistent-grid size by timing every candidate
+// on scratch copies of the nodal state (the simulation state is not touched),
+// once per batch signature; HMC_AUTOTUNE=0 keeps the 16x16 default and
+// HMC_MPM_SHAPE forces one shape.  Every
+// candidate computes bit-identical results: the per-cell arithmetic and the
+// order of each node's force sum do not depend on the tiling.
+hmc_status ensure_tuned(hmc_handle *h) {
+    if (h->tuned) return HMC_OK;
+    hmc_status s = HMC_OK;
+    const char *env = std::getenv("HMC_AUTOTUNE");
+    const bool enabled = !(env && env[0] == '0');
+    // HMC_MPM_SHAPE=0|1|2 forces a patch shape (with its default grid), bypassing the tuner
+    const char *forced = std::getenv("HMC_MPM_SHAPE");
+    if (forced && forced[0] >= '0' && forced[0] < '0' + hmc::MPM_NSHAPES && forced[1] == 0) {
+        const int shape = forced[0] - '0';
+        if ((s = upload_sched(h, shape)) != HMC_OK) return s;
+        h->mpm_shape = shape;
+        h->mpm_grid = grid_for_shape(h, shape, 0);
+        h->tuned = true;
+        return HMC_OK;
+    }
+    const std::string sig = tune_signature(h);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        auto it = g_tune_cache.find(sig);
+        if (it != g_tune_cache.end()) {
+            if ((s = upload_sched(h, it->second.first)) != HMC_OK) return s;
+            h->mpm_shape = it->second.first;
+            h->mpm_grid = it->second.second;
+            h->tuned = true;
+            return HMC_OK;
+        }
+    }
+    int best_shape = hmc::MPM_16x16;
+    if ((s = upload_sched(h, best_shape)) != HMC_OK) return s;
+    int best_grid = grid_for_shape(h, best_shape, 0);
+    if (enabled) {
+        const size_t nb = node_bytes(h);
+        void *uo = nullptr, *vs = nullptr;
+        HMC_CK(h, cudaMalloc(&uo, nb), "autotune scratch");
+        if (cudaMalloc(&vs, nb) != cudaSuccess) {
+            cudaFree(uo);
+            return fail(h, HMC_ERR_OOM, "autotune scratch");
+        }
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        float best = 1e30f;
+        cudaError_t err = cudaMemcpyAsync(vs, h->v, nb, cudaMemcpyDeviceToDevice, h->stream);
+        for (int shape = 0; shape < hmc::MPM_NSHAPES && err == cudaSuccess && s == HMC_OK; ++shape) {
+            if ((s = upload_sched(h, shape)) != HMC_OK) break;
+            for (int lim : {0, 1}) {
+                const int grid = grid_for_shape(h, shape, lim);
+                if (lim == 1 && grid == grid_for_shape(h, shape, 0)) continue;
+                const int saved_grid = h->mpm_grid;
+                h->mpm_grid = grid;
+                auto launch = [&]() {
+                    return h->p.precision == HMC_FP32
+                               ? hmc::launch_mpm_step<float>(mpm_args<float>(h, h->u[h->cur], uo, vs), shape, h->stream)
+                               : hmc::launch_mpm_step<double>(mpm_args<double>(h, h->u[h->cur], uo, vs), shape,
+                                                              h->stream);
+                };
+                err = launch();
+                if (err == cudaSuccess) err = cudaEventRecord(e0, h->stream);
+                for (int k = 0; k < 3 && err == cudaSuccess; ++k) err = launch();
+                if (err == cudaSuccess) err = cudaEventRecord(e1, h->stream);
+                if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+                float ms = 0;
+                if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+                h->mpm_grid = saved_grid;
+                if (err == cudaSuccess && ms < best) {
+                    best = ms;
+                    best_shape = shape;
+                    best_grid = grid;
+                }
+                if (err != cudaSuccess) break;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        cudaStreamSynchronize(h->stream);
+        cudaFree(uo);
+        cudaFree(vs);
+        if (s != HMC_OK) return s;
+        if (err != cudaSuccess) return cuda_fail(h, err, "autotune");
+        if ((s = upload_sched(h, best_shape)) != HMC_OK) return s;
+    }
+    h->mpm_shape = best_shape;
+    h->mpm_grid = best_grid;
+    h->tuned = true;
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tune_cache[sig] = {best_shape, best_grid};
+    return HMC_OK;
+}
+
+hmc_status read_stats(hmc_handle *h, double *mean, double *energy) {
+    DevState st;
+    HMC_CK(h, cudaMemcpyAsync(&st, sel_st(h), sizeof(st), cudaMemcpyDeviceToHost, h->stream), "state download");
+    HMC_CK(h, cudaStreamSynchronize(h->stream), "sync");
+    if (st.nonfinite) return fail(h, HMC_ERR_NONFINITE, "non-finite stress or energy");
+    if (mean)
+        for (int i = 0; i < 6; ++i) mean[i] = st.mean_sigma[i];
+    if (energy) *energy = st.energy;
+    return HMC_OK;
+}
+
+hmc_status nodal_io(hmc_handle *h, void *dev_base, double *host, bool to_host) {
+    const RepHost &R = selr(h);
+    const size_t n = 3 * (size_t)R.nblk;
+    char *dev = static_cast<char *>(dev_base) + h->tsize * 3 * (size_t)R.blk_off;
+    if (h->p.precision == HMC_FP64) {
+        if (to_host)
+            HMC_CK(h, cudaMemcpyAsync(host, dev, n * 8, cudaMemcpyDeviceToHost, h->stream), "download");
+        else
+            HMC_CK(h, cudaMemcpyAsync(dev, host, n * 8, cudaMemcpyHostToDevice, h->stream), "upload");
+        HMC_CK(h, cudaStreamSynchronize(h->stream), "sync");
+        return HMC_OK;
+    }
+    std::vector<float> t(n);
+    if (to_host) {
+        HMC_CK(h, cudaMemcpyAsync(t.data(), dev, n * 4, cudaMemcpyDeviceToHost, h->stream), "download");
+        HMC_CK(h, cudaStreamSynchronize(h->stream), "sync");
+        for (size_t i = 0; i < n; ++i) host[i] = t[i];
+    } else {
+        for (size_t i = 0; i < n; ++i) t[i] = (float)host[i];
+        HMC_CK(h, cudaMemcpyAsync(dev, t.data(), n * 4, cudaMemcpyHostToDevice, h->stream), "upload");
+        HMC_CK(h, cudaStreamSynchronize(h->stream), "sync");
+    }
+    return HMC_OK;
+}
+
+struct StateHeader {
+    char magic[8];
+    int32_t nx, ny, nz, precision;
+    uint32_t mcs, pad;
+    double ebar[6];
+};
 
 }  // namespace
 
@@ -354,34 +597,56 @@ void hmc_default_params(hmc_params *p) {
     p->stream = nullptr;
 }
 
-hmc_status hmc_create(const hmc_params *p, hmc_handle **out) {
+hmc_status hmc_batch_create(const hmc_params *params, int32_t n_replicas, hmc_handle **out) {
     if (!out) return fail(nullptr, HMC_ERR_ARG, "out is NULL");
     *out = nullptr;
-    const std::string msg = validate(p);
-    if (!msg.empty()) return fail(nullptr, HMC_ERR_ARG, msg);
+    if (!params || n_replicas < 1) return fail(nullptr, HMC_ERR_ARG, "need params for at least one replica");
+    for (int r = 0; r < n_replicas; ++r) {
+        std::string msg = validate(params + r);
+        if (msg.empty() && r > 0) msg = validate_shared(params, params + r);
+        if (!msg.empty())
+            return fail(nullptr, HMC_ERR_ARG, n_replicas > 1 ? "replica " + std::to_string(r) + ": " + msg : msg);
+    }
     hmc_handle *h = new (std::nothrow) hmc_handle();
     if (!h) return fail(nullptr, HMC_ERR_OOM, "host allocation failed");
+    const hmc_params *p = params;
     h->p = *p;
-    h->nbx = p->nx / 2; h->nby = p->ny / 2; h->nbz = p->nz / 2;
-    h->nblk = (long long)h->nbx * h->nby * h->nbz;
-    h->N = 8 * h->nblk;
-    h->nnodes = h->nblk;
+    h->R = n_replicas;
     h->tsize = p->precision == HMC_FP32 ? 4 : 8;
     const double lam_max = std::fmax(std::fmax(p->c11 + 2 * p->c12, p->c11 - p->c12), 2 * p->c44);
     h->dt = p->dt > 0 ? p->dt : 0.5 * 2.0 / std::sqrt(lam_max);
     h->damping = p->damping >= 0 ? p->damping : 0.05;
-    const int K = std::max(p->nx, std::max(p->ny, p->nz));
-    h->lam = p->elastic_scale >= 0 ? p->elastic_scale : 1e9 * (1.0 / K) * kL0 * kGammaStar / (2.0 * kGammaS);
     const double dd = (p->c11 - p->c12) * (p->c11 + 2 * p->c12);
     h->S11 = (p->c11 + p->c12) / dd;
     h->S12 = -p->c12 / dd;
     h->S44 = 1.0 / p->c44;
-    h->lam_sd_half = 0.5 * h->lam * (h->S11 - h->S12 - 0.5 * h->S44);
-    if (p->bc == HMC_BC_UNIAXIAL) {
-        const double n = std::sqrt(p->load_axis[0] * p->load_axis[0] + p->load_axis[1] * p->load_axis[1] +
-                                   p->load_axis[2] * p->load_axis[2]);
-        for (int i = 0; i < 3; ++i) h->axis[i] = p->load_axis[i] / n;
+    h->reps.resize(n_replicas);
+    long long blk = 0;
+    int cta = 0;
+    for (int r = 0; r < n_replicas; ++r) {
+        RepHost &R = h->reps[r];
+        R.p = params[r];
+        R.nbx = R.p.nx / 2; R.nby = R.p.ny / 2; R.nbz = R.p.nz / 2;
+        R.nblk = (long long)R.nbx * R.nby * R.nbz;
+        R.N = 8 * R.nblk;
+        R.blk_off = blk;
+        blk += R.nblk;
+        R.ncta = (int)((R.nblk + hmc::BLOCK_THREADS - 1) / hmc::BLOCK_THREADS);
+        R.cta_off = cta;
+        cta += R.ncta;
+        const int K = std::max(R.p.nx, std::max(R.p.ny, R.p.nz));
+        R.lam = R.p.elastic_scale >= 0 ? R.p.elastic_scale : 1e9 * (1.0 / K) * kL0 * kGammaStar / (2.0 * kGammaS);
+        R.lam_sd_half = 0.5 * R.lam * (h->S11 - h->S12 - 0.5 * h->S44);
+        if (R.p.bc == HMC_BC_UNIAXIAL) {
+            const double n = std::sqrt(R.p.load_axis[0] * R.p.load_axis[0] + R.p.load_axis[1] * R.p.load_axis[1] +
+                                       R.p.load_axis[2] * R.p.load_axis[2]);
+            for (int i = 0; i < 3; ++i) R.axis[i] = R.p.load_axis[i] / n;
+        }
+        h->N_total += R.N;
+        h->N_max = std::max(h->N_max, R.N);
     }
+    h->nblk_total = blk;
+    h->nctas = cta;
 
     auto bail = [&](hmc_status s) {
         g_create_error = h->err;
@@ -404,22 +669,22 @@ hmc_status hmc_create(const hmc_params *p, hmc_handle **out) {
     if ((e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking)) != cudaSuccess)
         return bail(cuda_fail(h, e, "capture stream create"));
     if ((e = hmc::mpm_prepare()) != cudaSuccess) return bail(cuda_fail(h, e, "MPM kernel attribute"));
-    h->mpm_grid = p->precision == HMC_FP32 ? hmc::mpm_grid<float>(h->nbx, h->nby, h->nbz, h->num_sms)
-                                           : hmc::mpm_grid<double>(h->nbx, h->nby, h->nbz, h->num_sms);
-    h->nparts = hmc::stress_grid(h->nblk);
     struct Alloc { void **ptr; size_t bytes; const char *what; };
-    const size_t nodes_b = h->tsize * 3 * (size_t)h->nnodes;
+    const size_t nodes_b = node_bytes(h);
     Alloc allocs[] = {
-        {(void **)&h->spins, sizeof(uint4) * (size_t)h->nblk, "spins"},
-        {(void **)&h->stage16, sizeof(uint16_t) * (size_t)h->N, "spin staging"},
+        {(void **)&h->spins, sizeof(uint4) * (size_t)h->nblk_total, "spins"},
+        {(void **)&h->stage16, sizeof(uint16_t) * (size_t)h->N_max, "spin staging"},
         {&h->u[0], nodes_b, "u0"}, {&h->u[1], nodes_b, "u1"}, {&h->v, nodes_b, "v"},
-        {&h->sig, h->tsize * 48 * (size_t)h->nblk, "stress"},
+        {&h->sig, h->tsize * 48 * (size_t)h->nblk_total, "stress"},
         {&h->ctab, h->tsize * 24 * (size_t)p->n_orient, "stiffness table"},
         {&h->wtab, h->tsize * 20 * (size_t)p->n_orient, "zone table"},
         {(void **)&h->thr, sizeof(unsigned long long) * 8, "threshold table"},
         {(void **)&h->counts, sizeof(unsigned long long) * (size_t)p->n_orient, "orientation counts"},
-        {(void **)&h->partials, sizeof(double) * 7 * (size_t)h->nparts, "partials"},
-        {(void **)&h->st, sizeof(DevState), "device state"},
+        {(void **)&h->partials, sizeof(double) * 7 * (size_t)h->nctas, "partials"},
+        {(void **)&h->st, sizeof(DevState) * (size_t)h->R, "device state"},
+        {(void **)&h->d_reps, sizeof(hmc::Replica) * (size_t)h->R, "replica table"},
+        {(void **)&h->d_cta_rep, sizeof(int) * (size_t)h->nctas, "CTA table"},
+        {(void **)&h->d_sched, sizeof(hmc::MpmSched) * (size_t)(h->R + 1), "MPM schedule"},
     };
     for (auto &a : allocs) {
         if ((e = cudaMalloc(a.ptr, a.bytes)) != cudaSuccess) return bail(cuda_fail(h, e, a.what));
@@ -438,18 +703,44 @@ hmc_status hmc_create(const hmc_params *p, hmc_handle **out) {
     }
     if ((e = cudaMemcpy(h->thr, thr, sizeof(thr), cudaMemcpyHostToDevice)) != cudaSuccess)
         return bail(cuda_fail(h, e, "threshold upload"));
-    DevState st;
-    std::memset(&st, 0, sizeof(st));
-    st.bc = p->bc;
-    if ((e = cudaMemcpy(h->st, &st, sizeof(st), cudaMemcpyHostToDevice)) != cudaSuccess)
-        return bail(cuda_fail(h, e, "state upload"));
-    const size_t zero_bytes[] = {nodes_b, nodes_b, nodes_b};
+    std::vector<DevState> st(h->R);
+    std::vector<hmc::Replica> rd(h->R);
+    std::vector<int> ctarep(h->nctas);
+    for (int r = 0; r < h->R; ++r) {
+        const RepHost &R = h->reps[r];
+        std::memset(&st[r], 0, sizeof(DevState));
+        st[r].bc = R.p.bc;
+        std::memset(&rd[r], 0, sizeof(hmc::Replica));
+        rd[r].nx = R.p.nx; rd[r].ny = R.p.ny; rd[r].nz = R.p.nz;
+        rd[r].nbx = R.nbx; rd[r].nby = R.nby; rd[r].nbz = R.nbz;
+        rd[r].nblk = (int)R.nblk;
+        rd[r].cta_off = R.cta_off;
+        rd[r].ncta = R.ncta;
+        rd[r].blk_off = R.blk_off;
+        rd[r].key0 = (uint32_t)(R.p.seed & 0xffffffffull);
+        rd[r].key1 = (uint32_t)(R.p.seed >> 32);
+        rd[r].replica = R.p.replica;
+        rd[r].lam_sd_half = R.lam_sd_half;
+        rd[r].st = h->st + r;
+        for (int c = 0; c < R.ncta; ++c) ctarep[R.cta_off + c] = r;
+    }
+    if ((e = cudaMemcpy(h->st, st.data(), sizeof(DevState) * st.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(h->d_reps, rd.data(), sizeof(hmc::Replica) * rd.size(), cudaMemcpyHostToDevice)) !=
+            cudaSuccess ||
+        (e = cudaMemcpy(h->d_cta_rep, ctarep.data(), sizeof(int) * ctarep.size(), cudaMemcpyHostToDevice)) !=
+            cudaSuccess)
+        return bail(cuda_fail(h, e, "descriptor upload"));
     void *zero_ptrs[] = {h->u[0], h->u[1], h->v};
-    for (int i = 0; i < 3; ++i)
-        if ((e = cudaMemset(zero_ptrs[i], 0, zero_bytes[i])) != cudaSuccess) return bail(cuda_fail(h, e, "memset"));
+    for (void *z : zero_ptrs)
+        if ((e = cudaMemset(z, 0, nodes_b)) != cudaSuccess) return bail(cuda_fail(h, e, "memset"));
+    hmc_status s = upload_sched(h, h->mpm_shape);
+    if (s != HMC_OK) return bail(s);
+    h->mpm_grid = grid_for_shape(h, h->mpm_shape, 0);
     *out = h;
     return HMC_OK;
 }
+
+hmc_status hmc_create(const hmc_params *p, hmc_handle **out) { return hmc_batch_create(p, 1, out); }
 
 void hmc_destroy(hmc_handle *h) {
     if (!h) return;
@@ -458,14 +749,29 @@ void hmc_destroy(hmc_handle *h) {
     delete h;
 }
 
+hmc_status hmc_select_replica(hmc_handle *h, int32_t r) {
+    if (!h) return HMC_ERR_ARG;
+    if (r < 0 || r >= h->R) return fail(h, HMC_ERR_ARG, "replica index out of range");
+    h->sel = r;
+    return HMC_OK;
+}
+
+hmc_status hmc_get_tuning(hmc_handle *h, int32_t *mpm_shape, int32_t *mpm_grid) {
+    if (!h) return HMC_ERR_ARG;
+    if (mpm_shape) *mpm_shape = h->mpm_shape;
+    if (mpm_grid) *mpm_grid = h->mpm_grid;
+    return HMC_OK;
+}
+
 hmc_status hmc_set_orientations(hmc_handle *h, const double *euler, const uint16_t *spins) {
     if (!h) return HMC_ERR_ARG;
     if (!euler || !spins) return fail(h, HMC_ERR_ARG, "NULL euler or spins");
     const int Q = h->p.n_orient;
     for (int i = 0; i < 3 * Q; ++i)
         if (!std::isfinite(euler[i])) return fail(h, HMC_ERR_ARG, "non-finite Euler angle");
-    for (long long i = 0; i < h->N; ++i)
-        if (spins[i] >= (uint32_t)Q) return fail(h, HMC_ERR_ARG, "spin value >= n_orient at site " + std::to_string(i));
+    for (long long i = 0; i < h->N_total; ++i)
+        if (spins[i] >= (uint32_t)Q)
+            return fail(h, HMC_ERR_ARG, "spin value >= n_orient at site " + std::to_string(i));
     h->A.assign((size_t)Q * 9, 0.0);
     h->Cv.assign((size_t)Q * 36, 0.0);
     h->Sv.assign((size_t)Q * 36, 0.0);
@@ -486,32 +792,38 @@ hmc_status hmc_set_orientations(hmc_handle *h, const double *euler, const uint16
         congruence(M, C0, &h->Cv[(size_t)q * 36]);
         congruence(Ns, S0, &h->Sv[(size_t)q * 36]);
     }
-    // Reuss compliance of the initial volume fractions, and the initial mean strain
-    std::vector<long long> cnt(Q, 0);
-    for (long long i = 0; i < h->N; ++i) cnt[spins[i]]++;
-    DevState st;
-    std::memset(&st, 0, sizeof(st));
-    for (int q = 0; q < Q; ++q)
-        if (cnt[q])
-            for (int k = 0; k < 36; ++k) st.sr[k] += (double)cnt[q] / (double)h->N * h->Sv[(size_t)q * 36 + k];
-    st.bc = h->p.bc;
-    st.eps0 = h->p.strain;
-    if (h->p.bc == HMC_BC_UNIAXIAL) {
-        axis_vectors(h->axis, st.axN, st.axNs);
-        for (int i = 0; i < 6; ++i) {
-            double s = 0;
-            for (int j = 0; j < 6; ++j) s += st.sr[6 * i + j] * st.axN[j];
-            st.axB[i] = s;
-        }
-        st.axNB = 0;
-        for (int i = 0; i < 6; ++i) st.axNB += st.axN[i] * st.axB[i];
-        for (int i = 0; i < 6; ++i) st.ebar[i] = h->p.strain / st.axNB * st.axB[i];
-    } else {
-        for (int i = 0; i < 6; ++i) st.ebar[i] = h->p.strain6[i];
-    }
-    for (int i = 0; i < 6; ++i) st.ebar_f[i] = (float)st.ebar[i];
     HMC_CK(h, cudaStreamSynchronize(h->stream), "sync");
-    HMC_CK(h, cudaMemcpy(h->st, &st, sizeof(st), cudaMemcpyHostToDevice), "state upload");
+    // per replica: Reuss compliance of its initial volume fractions, initial mean strain
+    std::vector<DevState> st(h->R);
+    long long site = 0;
+    for (int r = 0; r < h->R; ++r) {
+        const RepHost &R = h->reps[r];
+        std::vector<long long> cnt(Q, 0);
+        for (long long i = 0; i < R.N; ++i) cnt[spins[site + i]]++;
+        DevState &d = st[r];
+        std::memset(&d, 0, sizeof(d));
+        for (int q = 0; q < Q; ++q)
+            if (cnt[q])
+                for (int k = 0; k < 36; ++k) d.sr[k] += (double)cnt[q] / (double)R.N * h->Sv[(size_t)q * 36 + k];
+        d.bc = R.p.bc;
+        d.eps0 = R.p.strain;
+        if (R.p.bc == HMC_BC_UNIAXIAL) {
+            axis_vectors(R.axis, d.axN, d.axNs);
+            for (int i = 0; i < 6; ++i) {
+                double s = 0;
+                for (int j = 0; j < 6; ++j) s += d.sr[6 * i + j] * d.axN[j];
+                d.axB[i] = s;
+            }
+            d.axNB = 0;
+            for (int i = 0; i < 6; ++i) d.axNB += d.axN[i] * d.axB[i];
+            for (int i = 0; i < 6; ++i) d.ebar[i] = R.p.strain / d.axNB * d.axB[i];
+        } else {
+            for (int i = 0; i < 6; ++i) d.ebar[i] = R.p.strain6[i];
+        }
+        for (int i = 0; i < 6; ++i) d.ebar_f[i] = (float)d.ebar[i];
+        site += R.N;
+    }
+    HMC_CK(h, cudaMemcpy(h->st, st.data(), sizeof(DevState) * h->R, cudaMemcpyHostToDevice), "state upload");
     if (h->p.precision == HMC_FP32) {
         auto c = pack_ctab<float>(h->Cv, Q);
         auto w = pack_wtab<float>(h->A, Q);
@@ -523,14 +835,18 @@ hmc_status hmc_set_orientations(hmc_handle *h, const double *euler, const uint16
         HMC_CK(h, cudaMemcpy(h->ctab, c.data(), c.size() * sizeof(double), cudaMemcpyHostToDevice), "table upload");
         HMC_CK(h, cudaMemcpy(h->wtab, w.data(), w.size() * sizeof(double), cudaMemcpyHostToDevice), "table upload");
     }
-    const size_t nodes_b = h->tsize * 3 * (size_t)h->nnodes;
+    const size_t nodes_b = node_bytes(h);
     HMC_CK(h, cudaMemsetAsync(h->u[0], 0, nodes_b, h->stream), "memset u");
     HMC_CK(h, cudaMemsetAsync(h->u[1], 0, nodes_b, h->stream), "memset u");
     HMC_CK(h, cudaMemsetAsync(h->v, 0, nodes_b, h->stream), "memset v");
-    HMC_CK(h, cudaMemsetAsync(h->sig, 0, h->tsize * 48 * (size_t)h->nblk, h->stream), "memset sigma");
+    HMC_CK(h, cudaMemsetAsync(h->sig, 0, h->tsize * 48 * (size_t)h->nblk_total, h->stream), "memset sigma");
     h->cur = 0;
-    hmc_status s = upload_spins(h, spins);
-    if (s != HMC_OK) return s;
+    site = 0;
+    for (int r = 0; r < h->R; ++r) {
+        hmc_status s = upload_spins(h, r, spins + site);
+        if (s != HMC_OK) return s;
+        site += h->reps[r].N;
+    }
     HMC_CK(h, cudaStreamSynchronize(h->stream), "sync");
     h->oriented = true;
     return HMC_OK;
@@ -540,7 +856,7 @@ hmc_status hmc_set_spins(hmc_handle *h, const uint16_t *spins) {
     hmc_status s = need_oriented(h);
     if (s != HMC_OK) return s;
     if (!spins) return fail(h, HMC_ERR_ARG, "NULL spins");
-    if ((s = upload_spins(h, spins)) != HMC_OK) return s;
+    if ((s = upload_spins(h, h->sel, spins)) != HMC_OK) return s;
     HMC_CK(h, cudaStreamSynchronize(h->stream), "sync");
     return HMC_OK;
 }
@@ -549,20 +865,12 @@ hmc_status hmc_get_spins(hmc_handle *h, uint16_t *spins) {
     hmc_status s = need_oriented(h);
     if (s != HMC_OK) return s;
     if (!spins) return fail(h, HMC_ERR_ARG, "NULL spins");
-    HMC_CK(h, hmc::launch_unpack_spins(h->spins, h->stage16, h->p.nx, h->p.ny, h->p.nz, h->stream), "unpack spins");
-    HMC_CK(h, cudaMemcpyAsync(spins, h->stage16, sizeof(uint16_t) * h->N, cudaMemcpyDeviceToHost, h->stream), "spin download");
+    const RepHost &R = selr(h);
+    HMC_CK(h, hmc::launch_unpack_spins(h->spins + R.blk_off, h->stage16, R.p.nx, R.p.ny, R.p.nz, h->stream),
+           "unpack spins");
+    HMC_CK(h, cudaMemcpyAsync(spins, h->stage16, sizeof(uint16_t) * R.N, cudaMemcpyDeviceToHost, h->stream),
+           "spin download");
     HMC_CK(h, cudaStreamSynchronize(h->stream), "sync");
-    return HMC_OK;
-}
-
-static hmc_status read_stats(hmc_handle *h, double *mean, double *energy) {
-    DevState st;
-    HMC_CK(h, cudaMemcpyAsync(&st, h->st, sizeof(st), cudaMemcpyDeviceToHost, h->stream), "state download");
-    HMC_CK(h, cudaStreamSynchronize(h->stream), "sync");
-    if (st.nonfinite) return fail(h, HMC_ERR_NONFINITE, "non-finite stress or energy");
-    if (mean)
-        for (int i = 0; i < 6; ++i) mean[i] = st.mean_sigma[i];
-    if (energy) *energy = st.energy;
     return HMC_OK;
 }
 
@@ -570,7 +878,7 @@ hmc_status hmc_compute_stress(hmc_handle *h, double *mean, double *energy) {
     hmc_status s = need_oriented(h);
     if (s != HMC_OK) return s;
     HMC_CK(h, enq_stress(h, h->stream), "stress launch");
-    HMC_CK(h, hmc::launch_end_mcs(h->st, h->partials, h->nparts, h->N, 0, 0, h->stream), "reduction launch");
+    HMC_CK(h, hmc::launch_end_mcs(h->d_reps, h->R, h->partials, 0, 0, h->stream), "reduction launch");
     if (mean || energy) return read_stats(h, mean, energy);
     return HMC_OK;
 }
@@ -579,16 +887,9 @@ hmc_status hmc_mpm_steps(hmc_handle *h, int32_t nsteps, double *energy) {
     hmc_status s = need_oriented(h);
     if (s != HMC_OK) return s;
     if (nsteps < 0) return fail(h, HMC_ERR_ARG, "nsteps < 0");
+    if (nsteps > 0 && (s = ensure_tuned(h)) != HMC_OK) return s;
     for (int k = 0; k < nsteps; ++k) HMC_CK(h, enq_mpm(h, h->stream), "MPM launch");
     if (energy) return hmc_compute_stress(h, nullptr, energy);
-    return HMC_OK;
-}
-
-static hmc_status read_accepted(hmc_handle *h, int64_t *acc) {
-    unsigned long long a = 0;
-    HMC_CK(h, cudaMemcpyAsync(&a, &h->st->accepted, sizeof(a), cudaMemcpyDeviceToHost, h->stream), "download");
-    HMC_CK(h, cudaStreamSynchronize(h->stream), "sync");
-    *acc = (int64_t)a;
     return HMC_OK;
 }
 
@@ -596,7 +897,7 @@ hmc_status hmc_sweep_half(hmc_handle *h, int32_t colour, int64_t *accepted) {
     hmc_status s = need_oriented(h);
     if (s != HMC_OK) return s;
     if (colour != 0 && colour != 1) return fail(h, HMC_ERR_ARG, "colour must be 0 or 1");
-    HMC_CK(h, cudaMemsetAsync(&h->st->accepted, 0, sizeof(unsigned long long), h->stream), "memset");
+    HMC_CK(h, reset_accepted(h), "memset");
     HMC_CK(h, enq_sweep(h, colour, h->stream), "sweep launch");
     if (accepted) return read_accepted(h, accepted);
     return HMC_OK;
@@ -605,7 +906,7 @@ hmc_status hmc_sweep_half(hmc_handle *h, int32_t colour, int64_t *accepted) {
 hmc_status hmc_end_mcs(hmc_handle *h) {
     hmc_status s = need_oriented(h);
     if (s != HMC_OK) return s;
-    HMC_CK(h, hmc::launch_end_mcs(h->st, h->partials, h->nparts, h->N, 1, 1, h->stream), "end-of-step launch");
+    HMC_CK(h, hmc::launch_end_mcs(h->d_reps, h->R, h->partials, 1, 1, h->stream), "end-of-step launch");
     return HMC_OK;
 }
 
@@ -613,11 +914,12 @@ hmc_status hmc_mc_sweeps(hmc_handle *h, int32_t n_mcs, int64_t *accepted) {
     hmc_status s = need_oriented(h);
     if (s != HMC_OK) return s;
     if (n_mcs < 0) return fail(h, HMC_ERR_ARG, "n_mcs < 0");
-    HMC_CK(h, cudaMemsetAsync(&h->st->accepted, 0, sizeof(unsigned long long), h->stream), "memset");
+    if (n_mcs > 0 && h->p.mpm_steps_per_mcs > 0 && (s = ensure_tuned(h)) != HMC_OK) return s;
+    HMC_CK(h, reset_accepted(h), "memset");
     for (int m = 0; m < n_mcs; ++m) {
         const int c0 = h->cur;
         if (!h->gexec[c0]) {
-            // capture one step starting from this displacement buffer
+            // capture one step of every replica starting from this displacement buffer
             cudaGraph_t g = nullptr;
             HMC_CK(h, cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
             cudaError_t e = enqueue_mcs(h, h->cap);
@@ -642,18 +944,22 @@ hmc_status hmc_mc_sweeps(hmc_handle *h, int32_t n_mcs, int64_t *accepted) {
     return HMC_OK;
 }
 
-hmc_status hmc_texture_histogram(hmc_handle *h, int32_t kind, int32_t nbins, double *fractions, int64_t *counts_per_q) {
+hmc_status hmc_texture_histogram(hmc_handle *h, int32_t kind, int32_t nbins, double *fractions,
+                                 int64_t *counts_per_q) {
     hmc_status s = need_oriented(h);
     if (s != HMC_OK) return s;
     const int Q = h->p.n_orient;
+    const RepHost &R = selr(h);
     if (fractions) {
         if (kind == HMC_HIST_PER_Q && nbins != Q) return fail(h, HMC_ERR_ARG, "PER_Q needs nbins == n_orient");
-        if (kind != HMC_HIST_PER_Q && kind != HMC_HIST_ANGLE_100 && kind != HMC_HIST_YOUNG) return fail(h, HMC_ERR_ARG, "bad kind");
+        if (kind != HMC_HIST_PER_Q && kind != HMC_HIST_ANGLE_100 && kind != HMC_HIST_YOUNG)
+            return fail(h, HMC_ERR_ARG, "bad kind");
         if (nbins < 1) return fail(h, HMC_ERR_ARG, "nbins < 1");
     }
     HMC_CK(h, cudaMemsetAsync(h->counts, 0, sizeof(unsigned long long) * Q, h->stream), "memset");
-    HMC_CK(h, cudaMemsetAsync(&h->st->unlike, 0, sizeof(unsigned long long), h->stream), "memset");
-    HMC_CK(h, hmc::launch_bonds_counts(h->spins, h->nbx, h->nby, h->nbz, Q, h->counts, h->st, h->stream), "counts launch");
+    HMC_CK(h, cudaMemsetAsync(&sel_st(h)->unlike, 0, sizeof(unsigned long long), h->stream), "memset");
+    HMC_CK(h, hmc::launch_bonds_counts(h->spins + R.blk_off, R.nbx, R.nby, R.nbz, Q, h->counts, sel_st(h), h->stream),
+           "counts launch");
     if (fractions) {
         std::vector<int32_t> map(Q);
         for (int q = 0; q < Q; ++q) {
@@ -662,14 +968,15 @@ hmc_status hmc_texture_histogram(hmc_handle *h, int32_t kind, int32_t nbins, dou
             if (kind == HMC_HIST_ANGLE_100) {
                 double c = 0;
                 for (int m = 0; m < 3; ++m) {
-                    const double d = std::fabs(A[0 * 3 + m] * h->axis[0] + A[1 * 3 + m] * h->axis[1] + A[2 * 3 + m] * h->axis[2]);
+                    const double d =
+                        std::fabs(A[0 * 3 + m] * R.axis[0] + A[1 * 3 + m] * R.axis[1] + A[2 * 3 + m] * R.axis[2]);
                     c = std::fmax(c, d);
                 }
                 const double ang = std::acos(std::fmin(1.0, c)) * 180.0 / M_PI;
                 b = (int)(ang / (90.0 / nbins));
             } else if (kind == HMC_HIST_YOUNG) {
                 double N[6], Nsv[6];
-                axis_vectors(h->axis, N, Nsv);
+                axis_vectors(R.axis, N, Nsv);
                 double nsn = 0;
                 for (int i = 0; i < 6; ++i)
                     for (int j = 0; j < 6; ++j) nsn += N[i] * h->Sv[(size_t)q * 36 + 6 * i + j] * N[j];
@@ -682,6 +989,7 @@ hmc_status hmc_texture_histogram(hmc_handle *h, int32_t kind, int32_t nbins, dou
             map[q] = b < 0 ? 0 : (b >= nbins ? nbins - 1 : b);
         }
         if (h->bins_cap < nbins) {
+            HMC_CK(h, cudaStreamSynchronize(h->stream), "sync");
             if (h->bins) cudaFree(h->bins);
             if (h->fractions) cudaFree(h->fractions);
             h->bins = nullptr;
@@ -692,13 +1000,17 @@ hmc_status hmc_texture_histogram(hmc_handle *h, int32_t kind, int32_t nbins, dou
             h->bins_cap = nbins;
         }
         if (!h->binmap) HMC_CK(h, cudaMalloc(&h->binmap, sizeof(int32_t) * Q), "binmap");
-        HMC_CK(h, cudaMemcpyAsync(h->binmap, map.data(), sizeof(int32_t) * Q, cudaMemcpyHostToDevice, h->stream), "binmap");
+        HMC_CK(h, cudaMemcpyAsync(h->binmap, map.data(), sizeof(int32_t) * Q, cudaMemcpyHostToDevice, h->stream),
+               "binmap");
         HMC_CK(h, cudaMemsetAsync(h->bins, 0, sizeof(unsigned long long) * nbins, h->stream), "memset");
-        HMC_CK(h, hmc::launch_bins(h->counts, h->binmap, Q, nbins, h->bins, h->fractions, h->N, h->stream), "bins launch");
-        HMC_CK(h, cudaMemcpyAsync(fractions, h->fractions, sizeof(double) * nbins, cudaMemcpyDeviceToHost, h->stream), "download");
+        HMC_CK(h, hmc::launch_bins(h->counts, h->binmap, Q, nbins, h->bins, h->fractions, R.N, h->stream),
+               "bins launch");
+        HMC_CK(h, cudaMemcpyAsync(fractions, h->fractions, sizeof(double) * nbins, cudaMemcpyDeviceToHost, h->stream),
+               "download");
     }
     if (counts_per_q)
-        HMC_CK(h, cudaMemcpyAsync(counts_per_q, h->counts, sizeof(int64_t) * Q, cudaMemcpyDeviceToHost, h->stream), "download");
+        HMC_CK(h, cudaMemcpyAsync(counts_per_q, h->counts, sizeof(int64_t) * Q, cudaMemcpyDeviceToHost, h->stream),
+               "download");
     HMC_CK(h, cudaStreamSynchronize(h->stream), "sync");
     return HMC_OK;
 }
@@ -706,13 +1018,15 @@ hmc_status hmc_texture_histogram(hmc_handle *h, int32_t kind, int32_t nbins, dou
 hmc_status hmc_energy(hmc_handle *h, int64_t *unlike, double *energy, double *mean) {
     hmc_status s = need_oriented(h);
     if (s != HMC_OK) return s;
+    const RepHost &R = selr(h);
     if (unlike) {
         HMC_CK(h, cudaMemsetAsync(h->counts, 0, sizeof(unsigned long long) * h->p.n_orient, h->stream), "memset");
-        HMC_CK(h, cudaMemsetAsync(&h->st->unlike, 0, sizeof(unsigned long long), h->stream), "memset");
-        HMC_CK(h, hmc::launch_bonds_counts(h->spins, h->nbx, h->nby, h->nbz, h->p.n_orient, h->counts, h->st, h->stream),
+        HMC_CK(h, cudaMemsetAsync(&sel_st(h)->unlike, 0, sizeof(unsigned long long), h->stream), "memset");
+        HMC_CK(h, hmc::launch_bonds_counts(h->spins + R.blk_off, R.nbx, R.nby, R.nbz, h->p.n_orient, h->counts,
+                                           sel_st(h), h->stream),
                "bonds launch");
         unsigned long long u = 0;
-        HMC_CK(h, cudaMemcpyAsync(&u, &h->st->unlike, sizeof(u), cudaMemcpyDeviceToHost, h->stream), "download");
+        HMC_CK(h, cudaMemcpyAsync(&u, &sel_st(h)->unlike, sizeof(u), cudaMemcpyDeviceToHost, h->stream), "download");
         HMC_CK(h, cudaStreamSynchronize(h->stream), "sync");
         *unlike = (int64_t)u;
     }
@@ -724,17 +1038,19 @@ hmc_status hmc_get_stress(hmc_handle *h, double *sigma) {
     hmc_status s = need_oriented(h);
     if (s != HMC_OK) return s;
     if (!sigma) return fail(h, HMC_ERR_ARG, "NULL sigma");
-    const size_t n = 48 * (size_t)h->nblk;
+    const RepHost &R = selr(h);
+    const size_t n = 48 * (size_t)R.nblk;
+    const char *src = static_cast<const char *>(h->sig) + h->tsize * 48 * (size_t)R.blk_off;
     if (h->p.precision == HMC_FP32) {
         std::vector<float> t(n);
-        HMC_CK(h, cudaMemcpyAsync(t.data(), h->sig, n * sizeof(float), cudaMemcpyDeviceToHost, h->stream), "download");
+        HMC_CK(h, cudaMemcpyAsync(t.data(), src, n * sizeof(float), cudaMemcpyDeviceToHost, h->stream), "download");
         HMC_CK(h, cudaStreamSynchronize(h->stream), "sync");
-        unpack_stress_host<float>(h, t, sigma);
+        unpack_stress_host<float>(R, t, sigma);
     } else {
         std::vector<double> t(n);
-        HMC_CK(h, cudaMemcpyAsync(t.data(), h->sig, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "download");
+        HMC_CK(h, cudaMemcpyAsync(t.data(), src, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "download");
         HMC_CK(h, cudaStreamSynchronize(h->stream), "sync");
-        unpack_stress_host<double>(h, t, sigma);
+        unpack_stress_host<double>(R, t, sigma);
     }
     return HMC_OK;
 }
@@ -743,41 +1059,20 @@ hmc_status hmc_set_stress(hmc_handle *h, const double *sigma) {
     hmc_status s = need_oriented(h);
     if (s != HMC_OK) return s;
     if (!sigma) return fail(h, HMC_ERR_ARG, "NULL sigma");
-    for (long long i = 0; i < 6 * h->N; ++i)
+    const RepHost &R = selr(h);
+    for (long long i = 0; i < 6 * R.N; ++i)
         if (!std::isfinite(sigma[i])) return fail(h, HMC_ERR_ARG, "non-finite stress");
-    const size_t n = 48 * (size_t)h->nblk;
+    const size_t n = 48 * (size_t)R.nblk;
+    char *dst = static_cast<char *>(h->sig) + h->tsize * 48 * (size_t)R.blk_off;
     HMC_CK(h, cudaStreamSynchronize(h->stream), "sync");
     if (h->p.precision == HMC_FP32) {
         std::vector<float> t(n);
-        pack_stress_host<float>(h, sigma, t);
-        HMC_CK(h, cudaMemcpy(h->sig, t.data(), n * sizeof(float), cudaMemcpyHostToDevice), "upload");
+        pack_stress_host<float>(R, sigma, t);
+        HMC_CK(h, cudaMemcpy(dst, t.data(), n * sizeof(float), cudaMemcpyHostToDevice), "upload");
     } else {
         std::vector<double> t(n);
-        pack_stress_host<double>(h, sigma, t);
-        HMC_CK(h, cudaMemcpy(h->sig, t.data(), n * sizeof(double), cudaMemcpyHostToDevice), "upload");
-    }
-    return HMC_OK;
-}
-
-static hmc_status nodal_io(hmc_handle *h, void *dev, double *host, bool to_host) {
-    const size_t n = 3 * (size_t)h->nnodes;
-    if (h->p.precision == HMC_FP64) {
-        if (to_host)
-            HMC_CK(h, cudaMemcpyAsync(host, dev, n * 8, cudaMemcpyDeviceToHost, h->stream), "download");
-        else
-            HMC_CK(h, cudaMemcpyAsync(dev, host, n * 8, cudaMemcpyHostToDevice, h->stream), "upload");
-        HMC_CK(h, cudaStreamSynchronize(h->stream), "sync");
-        return HMC_OK;
-    }
-    std::vector<float> t(n);
-    if (to_host) {
-        HMC_CK(h, cudaMemcpyAsync(t.data(), dev, n * 4, cudaMemcpyDeviceToHost, h->stream), "download");
-        HMC_CK(h, cudaStreamSynchronize(h->stream), "sync");
-        for (size_t i = 0; i < n; ++i) host[i] = t[i];
-    } else {
-        for (size_t i = 0; i < n; ++i) t[i] = (float)host[i];
-        HMC_CK(h, cudaMemcpyAsync(dev, t.data(), n * 4, cudaMemcpyHostToDevice, h->stream), "upload");
-        HMC_CK(h, cudaStreamSynchronize(h->stream), "sync");
+        pack_stress_host<double>(R, sigma, t);
+        HMC_CK(h, cudaMemcpy(dst, t.data(), n * sizeof(double), cudaMemcpyHostToDevice), "upload");
     }
     return HMC_OK;
 }
@@ -793,7 +1088,7 @@ hmc_status hmc_get_nodal(hmc_handle *h, double *u, double *v) {
 hmc_status hmc_set_nodal(hmc_handle *h, const double *u, const double *v) {
     hmc_status s = need_oriented(h);
     if (s != HMC_OK) return s;
-    const size_t n = 3 * (size_t)h->nnodes;
+    const size_t n = 3 * (size_t)selr(h).nblk;
     for (const double *a : {u, v})
         if (a)
             for (size_t i = 0; i < n; ++i)
@@ -806,7 +1101,7 @@ hmc_status hmc_set_nodal(hmc_handle *h, const double *u, const double *v) {
 hmc_status hmc_get_strain(hmc_handle *h, double *e) {
     if (!h) return HMC_ERR_ARG;
     if (!e) return fail(h, HMC_ERR_ARG, "NULL strain");
-    HMC_CK(h, cudaMemcpyAsync(e, h->st->ebar, sizeof(double) * 6, cudaMemcpyDeviceToHost, h->stream), "download");
+    HMC_CK(h, cudaMemcpyAsync(e, sel_st(h)->ebar, sizeof(double) * 6, cudaMemcpyDeviceToHost, h->stream), "download");
     HMC_CK(h, cudaStreamSynchronize(h->stream), "sync");
     return HMC_OK;
 }
@@ -821,8 +1116,8 @@ hmc_status hmc_set_strain(hmc_handle *h, const double *e) {
         d[i] = e[i];
         f[i] = (float)e[i];
     }
-    HMC_CK(h, cudaMemcpyAsync(h->st->ebar, d, sizeof(d), cudaMemcpyHostToDevice, h->stream), "upload");
-    HMC_CK(h, cudaMemcpyAsync(h->st->ebar_f, f, sizeof(f), cudaMemcpyHostToDevice, h->stream), "upload");
+    HMC_CK(h, cudaMemcpyAsync(sel_st(h)->ebar, d, sizeof(d), cudaMemcpyHostToDevice, h->stream), "upload");
+    HMC_CK(h, cudaMemcpyAsync(sel_st(h)->ebar_f, f, sizeof(f), cudaMemcpyHostToDevice, h->stream), "upload");
     HMC_CK(h, cudaStreamSynchronize(h->stream), "sync");
     return HMC_OK;
 }
@@ -831,33 +1126,26 @@ hmc_status hmc_get_info(hmc_handle *h, hmc_info *info) {
     if (!h) return HMC_ERR_ARG;
     if (!info) return fail(h, HMC_ERR_ARG, "NULL info");
     DevState st;
-    HMC_CK(h, cudaMemcpyAsync(&st, h->st, sizeof(st), cudaMemcpyDeviceToHost, h->stream), "download");
+    HMC_CK(h, cudaMemcpyAsync(&st, sel_st(h), sizeof(st), cudaMemcpyDeviceToHost, h->stream), "download");
     HMC_CK(h, cudaStreamSynchronize(h->stream), "sync");
+    const RepHost &R = selr(h);
     info->dt = h->dt;
     info->damping = h->damping;
-    info->elastic_scale = h->lam;
+    info->elastic_scale = R.lam;
     for (int i = 0; i < 6; ++i) info->strain_bar[i] = st.ebar[i];
     info->mcs = st.mcs;
     info->u_buffer = h->cur;
-    info->n_sites = h->N;
-    info->n_nodes = h->nnodes;
+    info->n_sites = R.N;
+    info->n_nodes = R.nblk;
     return HMC_OK;
 }
-
-namespace {
-struct StateHeader {
-    char magic[8];
-    int32_t nx, ny, nz, precision;
-    uint32_t mcs, pad;
-    double ebar[6];
-};
-}  // namespace
 
 hmc_status hmc_get_state(hmc_handle *h, void *buf, size_t *bytes) {
     hmc_status s = need_oriented(h);
     if (s != HMC_OK) return s;
     if (!bytes) return fail(h, HMC_ERR_ARG, "NULL bytes");
-    const size_t need = sizeof(StateHeader) + 2 * (size_t)h->N + 2 * 3 * 8 * (size_t)h->nnodes;
+    const RepHost &R = selr(h);
+    const size_t need = sizeof(StateHeader) + 2 * (size_t)R.N + 2 * 3 * 8 * (size_t)R.nblk;
     if (!buf) {
         *bytes = need;
         return HMC_OK;
@@ -866,9 +1154,9 @@ hmc_status hmc_get_state(hmc_handle *h, void *buf, size_t *bytes) {
     StateHeader hd;
     std::memset(&hd, 0, sizeof(hd));
     std::memcpy(hd.magic, "HMCSTAT1", 8);
-    hd.nx = h->p.nx; hd.ny = h->p.ny; hd.nz = h->p.nz; hd.precision = h->p.precision;
+    hd.nx = R.p.nx; hd.ny = R.p.ny; hd.nz = R.p.nz; hd.precision = h->p.precision;
     DevState st;
-    HMC_CK(h, cudaMemcpyAsync(&st, h->st, sizeof(st), cudaMemcpyDeviceToHost, h->stream), "download");
+    HMC_CK(h, cudaMemcpyAsync(&st, sel_st(h), sizeof(st), cudaMemcpyDeviceToHost, h->stream), "download");
     HMC_CK(h, cudaStreamSynchronize(h->stream), "sync");
     hd.mcs = st.mcs;
     for (int i = 0; i < 6; ++i) hd.ebar[i] = st.ebar[i];
@@ -876,8 +1164,8 @@ hmc_status hmc_get_state(hmc_handle *h, void *buf, size_t *bytes) {
     std::memcpy(p, &hd, sizeof(hd));
     p += sizeof(hd);
     if ((s = hmc_get_spins(h, reinterpret_cast<uint16_t *>(p))) != HMC_OK) return s;
-    p += 2 * (size_t)h->N;
-    double *u = reinterpret_cast<double *>(p), *v = u + 3 * (size_t)h->nnodes;
+    p += 2 * (size_t)R.N;
+    double *u = reinterpret_cast<double *>(p), *v = u + 3 * (size_t)R.nblk;
     if ((s = hmc_get_nodal(h, u, v)) != HMC_OK) return s;
     *bytes = need;
     return HMC_OK;
@@ -886,19 +1174,21 @@ hmc_status hmc_get_state(hmc_handle *h, void *buf, size_t *bytes) {
 hmc_status hmc_set_state(hmc_handle *h, const void *buf, size_t bytes) {
     hmc_status s = need_oriented(h);
     if (s != HMC_OK) return s;
-    const size_t need = sizeof(StateHeader) + 2 * (size_t)h->N + 2 * 3 * 8 * (size_t)h->nnodes;
+    const RepHost &R = selr(h);
+    const size_t need = sizeof(StateHeader) + 2 * (size_t)R.N + 2 * 3 * 8 * (size_t)R.nblk;
     if (!buf || bytes < need) return fail(h, HMC_ERR_ARG, "state buffer too small");
     StateHeader hd;
     std::memcpy(&hd, buf, sizeof(hd));
-    if (std::memcmp(hd.magic, "HMCSTAT1", 8) != 0 || hd.nx != h->p.nx || hd.ny != h->p.ny || hd.nz != h->p.nz)
-        return fail(h, HMC_ERR_ARG, "state does not match this handle");
+    if (std::memcmp(hd.magic, "HMCSTAT1", 8) != 0 || hd.nx != R.p.nx || hd.ny != R.p.ny || hd.nz != R.p.nz)
+        return fail(h, HMC_ERR_ARG, "state does not match this replica");
     const char *p = static_cast<const char *>(buf) + sizeof(hd);
     if ((s = hmc_set_spins(h, reinterpret_cast<const uint16_t *>(p))) != HMC_OK) return s;
-    p += 2 * (size_t)h->N;
-    const double *u = reinterpret_cast<const double *>(p), *v = u + 3 * (size_t)h->nnodes;
+    p += 2 * (size_t)R.N;
+    const double *u = reinterpret_cast<const double *>(p), *v = u + 3 * (size_t)R.nblk;
     if ((s = hmc_set_nodal(h, u, v)) != HMC_OK) return s;
     if ((s = hmc_set_strain(h, hd.ebar)) != HMC_OK) return s;
-    HMC_CK(h, cudaMemcpyAsync(&h->st->mcs, &hd.mcs, sizeof(uint32_t), cudaMemcpyHostToDevice, h->stream), "upload");
+    HMC_CK(h, cudaMemcpyAsync(&sel_st(h)->mcs, &hd.mcs, sizeof(uint32_t), cudaMemcpyHostToDevice, h->stream),
+           "upload");
     HMC_CK(h, cudaStreamSynchronize(h->stream), "sync");
     return HMC_OK;
 }

@@ -42,61 +42,90 @@ struct DevState {
     int32_t bad_spin;        // set by the upload check when a spin is >= Q
 };
 
+// One replica of a batch (a single handle is a batch of one).  Replica r's
+// blocks, nodes and stress occupy [blk_off, blk_off + nblk) of the batch
+// arrays (nodes are indexed like blocks, 3 values each; the stress of a
+// replica is its own [2][6][nblk][4] array at 48 * blk_off).
+struct Replica {
+    int nx, ny, nz, nbx, nby, nbz;
+    int nblk;                 // 2x2x2 blocks = MPM cells = background nodes
+    int cta_off, ncta;        // its CTAs in the block-parallel grids (BLOCK_THREADS each)
+    int pad;
+    long long blk_off;
+    uint32_t key0, key1, replica, pad2;
+    double lam_sd_half;       // lambda * (S11 - S12 - S44/2) / 2
+    DevState *st;
+};
+
+constexpr int BLOCK_THREADS = 256;   // threads of the sweep and stress CTAs
+
+// MPM work decomposition of one replica for the chosen patch shape: tiles of
+// owned nodes per edge and the first (tile-major, plane-minor) work item.
+struct MpmSched {
+    int tiles_x, tiles_y;
+    long long plane_off;      // entry nrep holds the total
+};
+
 template <typename T>
 struct MpmArgs {
+    const Replica *reps;
+    const MpmSched *sched;   // nrep + 1 entries
+    int nrep;
+    long long total;         // work items of the whole batch
     const uint4 *spins;
     const T *u_in;
     T *u_out;
     T *v;
     const T *ctab;
-    const DevState *st;
-    int nbx, nby, nbz;
-    int tiles_x, tiles_y;    // 15-node tiles per edge
-    int grid;                // persistent CTAs
     T dt, dt_over_m, keep;   // keep = 1 - damping
+    int grid;                // persistent CTAs
 };
 
 template <typename T>
 struct StressArgs {
+    const Replica *reps;
+    const int *cta_rep;      // replica of every CTA
     const uint4 *spins;
     const T *u;
     const T *ctab;
-    const DevState *st;
     T *sig;
     double *partials;        // 7 doubles per CTA: sum sigma (6), sum 1/2 sigma.eps
-    int nbx, nby, nbz;
-    long long nblk;
+    int nctas;
 };
 
 template <typename T>
 struct SweepArgs {
+    const Replica *reps;
+    const int *cta_rep;
     uint4 *spins;
     const T *sig;
     const T *wtab;
     const unsigned long long *thr;   // integer Metropolis thresholds for dE = 0..7
-    DevState *st;
-    int nx, ny, nz, nbx, nby, nbz;
-    long long nblk;
-    uint32_t key0, key1, replica;
     int trial, nq;
-    T J, kT, lam_sd_half;            // lambda * (S11 - S12 - S44/2) / 2
+    T J, kT;
+    int nctas;
 };
+
+// MPM patch shapes (cells per patch edge; owned nodes = cells - 1).
+enum MpmShape { MPM_16x16 = 0, MPM_32x8 = 1, MPM_8x32 = 2, MPM_NSHAPES = 3 };
+int mpm_shape_cx(int shape);
+int mpm_shape_cy(int shape);
 
 // Launchers (return cudaGetLastError of the launch).
 template <typename T>
-cudaError_t launch_mpm_step(const MpmArgs<T> &a, cudaStream_t s);
+cudaError_t launch_mpm_step(const MpmArgs<T> &a, int shape, cudaStream_t s);
 template <typename T>
-cudaError_t launch_stress(const StressArgs<T> &a, int grid, cudaStream_t s);
+cudaError_t launch_stress(const StressArgs<T> &a, cudaStream_t s);
 template <typename T>
 cudaError_t launch_sweep(const SweepArgs<T> &a, int colour, bool elastic, cudaStream_t s);
-int stress_grid(long long nblk);
-cudaError_t mpm_prepare();  // opt the MPM kernel into its dynamic shared memory (once, before any capture)
-int mpm_tiles(int nb);      // node tiles along one edge
+cudaError_t mpm_prepare();  // opt the MPM kernels into their dynamic shared memory (once, before any capture)
 template <typename T>
-int mpm_grid(int nbx, int nby, int nbz, int num_sms);
+int mpm_per_sm(int shape);  // resident MPM CTAs per SM
 
-cudaError_t launch_end_mcs(DevState *st, const double *partials, int nparts, long long n_sites,
-                           int update_strain, int advance, cudaStream_t s);
+// One CTA per replica: fixed-order FP64 sum of its stress partials, loading
+// update (update_strain) and MCS counter (advance).
+cudaError_t launch_end_mcs(const Replica *reps, int nrep, const double *partials, int update_strain, int advance,
+                           cudaStream_t s);
 cudaError_t launch_check_spins(const uint16_t *nat, long long n, int nq, DevState *st, cudaStream_t s);
 cudaError_t launch_pack_spins(const uint16_t *nat, uint4 *blk, int nx, int ny, int nz, cudaStream_t s);
 cudaError_t launch_unpack_spins(const uint4 *blk, uint16_t *nat, int nx, int ny, int nz, cudaStream_t s);

@@ -4,9 +4,10 @@
 // velocity / displacement update of every node -- one kernel, one pass over
 // the spins and the nodal state.
 //
-// Tiling: a CTA of 16x16 threads computes a 16x16 patch of cells per cell
-// plane (one thread per cell, all eight points of the cell) and owns the
-// 15x15 nodes whose four lower and four upper cells all lie in the patch.  It
+// Tiling: a CTA of CX x CY threads (16x16, 32x8 or 8x32, chosen per batch by
+// the autotuner) computes a CX x CY patch of cells per cell plane (one thread
+// per cell, all eight points of the cell) and owns the (CX-1) x (CY-1) nodes
+// whose four lower and four upper cells all lie in the patch.  It
 // marches up a chunk of planes in z: each cell writes its eight nodal force
 // contributions to shared memory, and a node's force is the sum of its four
 // cells below (carried in registers from the previous plane) and four above.
@@ -15,10 +16,12 @@
 // the owned node's velocity are fetched one plane ahead.  Displacements are
 // read from one buffer and written to the other, so CTAs never race on the halo.
 //
-// Scheduling: the (tile, plane) space is cut into one contiguous range per
-// resident CTA (a persistent grid of occupancy x SMs), so every CTA marches
-// about the same number of planes and pays the one-plane restart only where
-// its range enters a new tile.
+// Scheduling: the (replica, tile, plane) space of the whole batch is cut into
+// one contiguous range per resident CTA (a persistent grid of occupancy x
+// SMs), so every CTA marches about the same number of planes, over replicas of
+// any size, and pays the one-plane restart only where its range enters a new
+// tile.  The next node plane is read into registers before the cells of the
+// current plane are computed and stored to shared memory after them.
 //
 // Scaling: the interpolation weights 3/4 and 1/4 of the trilinear shape
 // functions at the points 1/4 and 3/4 of the cell are applied as 3 and 1; the
@@ -31,31 +34,52 @@ namespace hmc {
 
 namespace {
 
-constexpr int CT = 16;        // cells per patch edge = threads per edge
-constexpr int OT = CT - 1;    // owned nodes per patch edge
-constexpr int NT = CT + 1;    // node-plane tile edge (one node of halo each side)
-constexpr int NTHR = CT * CT;
-
-template <typename T>
+template <int CX, int CY>
 struct MpmSmem {
-    T us[3][3][NT][NT];   // node planes (buffer, component, j, i)
-    T fb[4][3][CT][CT];   // cell contributions to their lower corner nodes (corner I+2J, component)
-    T ft[4][3][CT][CT];   // ... to their upper corner nodes
+    static constexpr int NX = CX + 1, NY = CY + 1;   // node tile (one node of halo each side)
+    template <typename T>
+    struct S {
+        T us[3][3][NY][NX];   // node planes (buffer, component, j, i), held as u/32
+        T fb[4][3][CY][CX];   // cell contributions to their lower corner nodes (corner I+2J, component)
+        T ft[4][3][CY][CX];   // ... to their upper corner nodes
+    };
 };
 
-template <typename T>
-__device__ __forceinline__ void load_plane(MpmSmem<T> &sm, int buf, const T *__restrict__ u, int i0, int j0, int k,
-                                           int nbx, int nby, int nbz) {
-    const int gk = wrapi(k, nbz);
-    for (int t = threadIdx.x; t < NT * NT; t += NTHR) {
-        const int li = t % NT, lj = t / NT;
-        const int gi = wrapi(i0 - 1 + li, nbx), gj = wrapi(j0 - 1 + lj, nby);
-        const long long n = 3ll * (gi + (long long)nbx * (gj + (long long)nby * gk));
-        sm.us[buf][0][lj][li] = __ldg(u + n) * T(0.03125);
-        sm.us[buf][1][lj][li] = __ldg(u + n + 1) * T(0.03125);
-        sm.us[buf][2][lj][li] = __ldg(u + n + 2) * T(0.03125);
+// Node plane k of the tile with origin (i0, j0) (one node of halo on each side),
+// read from global memory into registers / written to shared memory.
+template <typename T, int CX, int CY>
+struct PlaneLoad {
+    static constexpr int NX = CX + 1, NY = CY + 1, NN = NX * NY, NTHR = CX * CY;
+    static constexpr int PER = (NN + NTHR - 1) / NTHR;
+    T r[PER][3];
+    __device__ __forceinline__ void fetch(const T *__restrict__ u, long long node0, int i0, int j0, int k, int nbx,
+                                          int nby, int nbz) {
+        const int gk = wrapi(k, nbz);
+#pragma unroll
+        for (int m = 0; m < PER; ++m) {
+            const int t = threadIdx.x + m * NTHR;
+            if (t < NN) {
+                const int li = t % NX, lj = t / NX;
+                const int gi = wrapi(i0 - 1 + li, nbx), gj = wrapi(j0 - 1 + lj, nby);
+                const long long n = 3ll * (node0 + gi + nbx * (gj + nby * gk));
+                r[m][0] = __ldg(u + n);
+                r[m][1] = __ldg(u + n + 1);
+                r[m][2] = __ldg(u + n + 2);
+            }
+        }
     }
-}
+    __device__ __forceinline__ void store(T (&us)[3][NY][NX]) const {
+#pragma unroll
+        for (int m = 0; m < PER; ++m) {
+            const int t = threadIdx.x + m * NTHR;
+            if (t < NN) {
+                const int li = t % NX, lj = t / NX;
+#pragma unroll
+                for (int d = 0; d < 3; ++d) us[d][lj][li] = r[m][d] * T(0.03125);
+            }
+        }
+    }
+};
 
 // 2x2 -> 2x2 transform with weights 3 (same side) and 1 (other side) in both
 // indices: o[b][c] = sum_J sum_K W(J,b) W(K,c) d[J][K], eight FMAs.
@@ -151,51 +175,63 @@ __device__ __forceinline__ void cell_forces(const T (&u)[8][3], const uint4 &sp,
     }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(NTHR, (sizeof(T) == 4 ? 2 : 1)) k_mpm_step(MpmArgs<T> a) {
+template <typename T, int CX, int CY>
+__global__ void __launch_bounds__(CX *CY, (sizeof(T) == 4 ? 2 : 1)) k_mpm_step(MpmArgs<T> a) {
+    constexpr int OX = CX - 1, OY = CY - 1;
+    using Smem = typename MpmSmem<CX, CY>::template S<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    MpmSmem<T> &sm = *reinterpret_cast<MpmSmem<T> *>(smem_raw);
+    Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
     const int tid = threadIdx.x;
-    const int lci = tid % CT, lcj = tid / CT;           // this thread's cell in the patch
-    const long long plane = (long long)a.nbx * a.nby;
+    const int lci = tid % CX, lcj = tid / CX;            // this thread's cell in the patch
     const T fscale = -a.dt_over_m * T(0.03125);          // -dt / (32 m)
-    T eb[6];
-    load_ebar<T>(a.st, eb);
-    // this CTA's contiguous range of the linear (tile, plane) index
-    const long long total = (long long)a.tiles_x * a.tiles_y * a.nbz;
-    long long w = total * blockIdx.x / gridDim.x;
-    const long long wend = total * (blockIdx.x + 1) / gridDim.x;
+    // this CTA's contiguous range of the linear (replica, tile, plane) index
+    long long w = a.total * blockIdx.x / gridDim.x;
+    const long long wend = a.total * (blockIdx.x + 1) / gridDim.x;
+    int r = 0;
     while (w < wend) {
-        const int tile = (int)(w / a.nbz);
-        const int k0 = (int)(w % a.nbz);
-        const int kend = (int)min((long long)a.nbz, (long long)k0 + (wend - w));
+        while (a.sched[r + 1].plane_off <= w) ++r;        // replica of work item w (ranges are ascending)
+        const Replica &R = a.reps[r];
+        const MpmSched &SC = a.sched[r];
+        const int nbx = R.nbx, nby = R.nby, nbz = R.nbz;
+        const long long lw = w - SC.plane_off;
+        const int tile = (int)(lw / nbz);
+        const int k0 = (int)(lw - (long long)tile * nbz);
+        const long long rem = min(wend, a.sched[r + 1].plane_off) - w;
+        const int kend = (int)min((long long)nbz, (long long)k0 + rem);
         w += kend - k0;
-        const int i0 = (tile % a.tiles_x) * OT, j0 = (tile / a.tiles_x) * OT;
+        const int i0 = (tile % SC.tiles_x) * OX, j0 = (tile / SC.tiles_x) * OY;
         const int ni = i0 - 1 + lci, nj = j0 - 1 + lcj;      // node at the cell's lower corner
-        const bool own = lci >= 1 && lcj >= 1 && ni < a.nbx && nj < a.nby;
+        const bool own = lci >= 1 && lcj >= 1 && ni < nbx && nj < nby;
         // a cell is needed when some owned node uses it: local index <= last owned local index
-        const bool need = lci <= min(OT, a.nbx - i0) && lcj <= min(OT, a.nby - j0);
-        const int gi = wrapi(ni, a.nbx), gj = wrapi(nj, a.nby);
-        const long long col = gi + (long long)a.nbx * gj;   // (i, j) column offset of cell and node
+        const bool need = lci <= min(OX, nbx - i0) && lcj <= min(OY, nby - j0);
+        const int gi = wrapi(ni, nbx), gj = wrapi(nj, nby);
+        const int plane = nbx * nby;
+        const long long col = R.blk_off + gi + nbx * gj;    // (i, j) column of this cell and node in the batch
+        T eb[6];
+        load_ebar<T>(R.st, eb);
 
+        PlaneLoad<T, CX, CY> pl;
         int b0 = 0, b1 = 1, b2 = 2;
-        load_plane<T>(sm, b0, a.u_in, i0, j0, k0 - 1, a.nbx, a.nby, a.nbz);
-        load_plane<T>(sm, b1, a.u_in, i0, j0, k0, a.nbx, a.nby, a.nbz);
-        uint4 sp = need ? __ldg(a.spins + col + plane * wrapi(k0 - 1, a.nbz)) : make_uint4(0, 0, 0, 0);
+        pl.fetch(a.u_in, R.blk_off, i0, j0, k0 - 1, nbx, nby, nbz);
+        pl.store(sm.us[b0]);
+        pl.fetch(a.u_in, R.blk_off, i0, j0, k0, nbx, nby, nbz);
+        pl.store(sm.us[b1]);
+        uint4 sp = need ? __ldg(a.spins + col + (long long)plane * wrapi(k0 - 1, nbz)) : make_uint4(0, 0, 0, 0);
         __syncthreads();
 
         T acc[3] = {T(0), T(0), T(0)};
         for (int kk = k0 - 1; kk < kend; ++kk) {
-            // one plane ahead: next plane's spins, this plane's owned velocity, plane kk+2 of u
+            // one plane ahead: next plane's spins and u, this plane's owned velocity
             uint4 sp_next = make_uint4(0, 0, 0, 0);
-            if (need && kk + 1 < kend) sp_next = __ldg(a.spins + col + plane * (kk + 1));
+            if (need && kk + 1 < kend) sp_next = __ldg(a.spins + col + (long long)plane * (kk + 1));
             T vold[3] = {T(0), T(0), T(0)};
-            const long long nidx = 3ll * (col + plane * (long long)(kk < 0 ? 0 : kk));
+            const long long nidx = 3ll * (col + (long long)plane * (kk < 0 ? 0 : kk));
             if (own && kk >= k0) {
 #pragma unroll
                 for (int d = 0; d < 3; ++d) vold[d] = a.v[nidx + d];
             }
-            if (kk + 1 < kend) load_plane<T>(sm, b2, a.u_in, i0, j0, kk + 2, a.nbx, a.nby, a.nbz);
+            const bool more = kk + 1 < kend;
+            if (more) pl.fetch(a.u_in, R.blk_off, i0, j0, kk + 2, nbx, nby, nbz);
             if (need) {
                 T u[8][3];
 #pragma unroll
@@ -218,6 +254,7 @@ __global__ void __launch_bounds__(NTHR, (sizeof(T) == 4 ? 2 : 1)) k_mpm_step(Mpm
                             sm.ft[I + 2 * J][d][lcj][lci] = f[corner(I, J, 1)][d];
                         }
             }
+            if (more) pl.store(sm.us[b2]);   // buffer b2 was last read before the previous barrier
             __syncthreads();
             if (own) {
                 // cells (lci-1, lcj-1), (lci, lcj-1), (lci-1, lcj), (lci, lcj) see this node as corner 3, 2, 1, 0
@@ -246,42 +283,61 @@ __global__ void __launch_bounds__(NTHR, (sizeof(T) == 4 ? 2 : 1)) k_mpm_step(Mpm
     }
 }
 
+template <typename T, int CX, int CY>
+size_t smem_of() {
+    return sizeof(typename MpmSmem<CX, CY>::template S<T>);
+}
+
 }  // namespace
 
-int mpm_tiles(int nb) { return (nb + OT - 1) / OT; }
+int mpm_shape_cx(int shape) { return shape == MPM_32x8 ? 32 : shape == MPM_8x32 ? 8 : 16; }
+int mpm_shape_cy(int shape) { return shape == MPM_32x8 ? 8 : shape == MPM_8x32 ? 32 : 16; }
+
+template <typename T>
+static cudaError_t prepare_t() {
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_mpm_step<T, 16, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem_of<T, 16, 16>())) != cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(k_mpm_step<T, 32, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem_of<T, 32, 8>())) != cudaSuccess)
+        return e;
+    return cudaFuncSetAttribute(k_mpm_step<T, 8, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem_of<T, 8, 32>());
+}
 
 cudaError_t mpm_prepare() {
-    cudaError_t e = cudaFuncSetAttribute(k_mpm_step<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sizeof(MpmSmem<float>));
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_mpm_step<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)sizeof(MpmSmem<double>));
+    cudaError_t e = prepare_t<float>();
+    return e != cudaSuccess ? e : prepare_t<double>();
 }
 
-// Persistent grid: resident CTAs per SM x SMs, but at least four planes per CTA.
 template <typename T>
-int mpm_grid(int nbx, int nby, int nbz, int num_sms) {
-    int per_sm = 1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mpm_step<T>, NTHR, sizeof(MpmSmem<T>)) !=
-            cudaSuccess ||
-        per_sm < 1)
-        per_sm = 1;
-    const long long planes = (long long)mpm_tiles(nbx) * mpm_tiles(nby) * nbz;
-    long long g = (long long)per_sm * num_sms;
-    const long long cap = (planes + 3) / 4;
-    if (g > cap) g = cap;
-    return (int)(g < 1 ? 1 : g);
+int mpm_per_sm(int shape) {
+    int n = 1;
+    cudaError_t e;
+    if (shape == MPM_32x8)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_mpm_step<T, 32, 8>, 256, smem_of<T, 32, 8>());
+    else if (shape == MPM_8x32)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_mpm_step<T, 8, 32>, 256, smem_of<T, 8, 32>());
+    else
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_mpm_step<T, 16, 16>, 256, smem_of<T, 16, 16>());
+    return (e != cudaSuccess || n < 1) ? 1 : n;
 }
-template int mpm_grid<float>(int, int, int, int);
-template int mpm_grid<double>(int, int, int, int);
+template int mpm_per_sm<float>(int);
+template int mpm_per_sm<double>(int);
 
 template <typename T>
-cudaError_t launch_mpm_step(const MpmArgs<T> &a, cudaStream_t s) {
-    k_mpm_step<T><<<a.grid, NTHR, sizeof(MpmSmem<T>), s>>>(a);
+cudaError_t launch_mpm_step(const MpmArgs<T> &a, int shape, cudaStream_t s) {
+    if (shape == MPM_32x8)
+        k_mpm_step<T, 32, 8><<<a.grid, 256, smem_of<T, 32, 8>(), s>>>(a);
+    else if (shape == MPM_8x32)
+        k_mpm_step<T, 8, 32><<<a.grid, 256, smem_of<T, 8, 32>(), s>>>(a);
+    else
+        k_mpm_step<T, 16, 16><<<a.grid, 256, smem_of<T, 16, 16>(), s>>>(a);
     return cudaGetLastError();
 }
 
-template cudaError_t launch_mpm_step<float>(const MpmArgs<float> &, cudaStream_t);
-template cudaError_t launch_mpm_step<double>(const MpmArgs<double> &, cudaStream_t);
+template cudaError_t launch_mpm_step<float>(const MpmArgs<float> &, int, cudaStream_t);
+template cudaError_t launch_mpm_step<double>(const MpmArgs<double> &, int, cudaStream_t);
 
 }  // namespace hmc

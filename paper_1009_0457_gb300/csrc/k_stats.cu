@@ -75,38 +75,42 @@ __device__ __forceinline__ void store4<double>(double *p, const double (&v)[4]) 
 }
 
 // Stress of the eight points of each cell from the current displacement; the
-// colour-packed stress array is what the half sweeps read.  Each CTA writes
-// its partial sums of sigma and of 1/2 sigma.eps (FP64 across warps; within a
-// warp FP32 TwoSum pairs or FP64, by T) for a fixed-order final reduction.
+// colour-packed stress array is what the half sweeps read.  Each CTA covers 256
+// blocks of one replica and writes its partial sums of sigma and of
+// 1/2 sigma.eps (FP64 across warps; within a warp FP32 TwoSum pairs or FP64,
+// by T) for a fixed-order final reduction.
 template <typename T>
-__global__ void __launch_bounds__(256) k_stress(StressArgs<T> a) {
-    __shared__ double red[8][7];
+__global__ void __launch_bounds__(BLOCK_THREADS) k_stress(StressArgs<T> a) {
+    __shared__ double red[BLOCK_THREADS / 32][7];
+    const int rep = __ldg(a.cta_rep + blockIdx.x);
+    const Replica &R = a.reps[rep];
+    const int blk = (blockIdx.x - R.cta_off) * BLOCK_THREADS + threadIdx.x;
     Acc7<T> acc;
     acc.zero();
-    T eb[6];
-    load_ebar<T>(a.st, eb);
-    for (long long blk = (long long)blockIdx.x * blockDim.x + threadIdx.x; blk < a.nblk;
-         blk += (long long)gridDim.x * blockDim.x) {
-        const int bx = (int)(blk % a.nbx);
-        const long long r = blk / a.nbx;
-        const int by = (int)(r % a.nby), bz = (int)(r / a.nby);
-        T u[8][3];
+    if (blk < R.nblk) {
+        T eb[6];
+        load_ebar<T>(R.st, eb);
+        const int nbx = R.nbx, nby = R.nby, nbz = R.nbz;
+        const int bx = blk % nbx, rr = blk / nbx;
+        const int by = rr % nby, bz = rr / nby;
+        const T *u = a.u + 3 * R.blk_off;
+        T uc[8][3];
 #pragma unroll
         for (int K = 0; K < 2; ++K)
 #pragma unroll
             for (int J = 0; J < 2; ++J)
 #pragma unroll
                 for (int I = 0; I < 2; ++I) {
-                    const int gi = bx + I == a.nbx ? 0 : bx + I;
-                    const int gj = by + J == a.nby ? 0 : by + J;
-                    const int gk = bz + K == a.nbz ? 0 : bz + K;
-                    const long long n = 3ll * (gi + (long long)a.nbx * (gj + (long long)a.nby * gk));
+                    const int gi = bx + I == nbx ? 0 : bx + I;
+                    const int gj = by + J == nby ? 0 : by + J;
+                    const int gk = bz + K == nbz ? 0 : bz + K;
+                    const int n = 3 * (gi + nbx * (gj + nby * gk));
 #pragma unroll
-                    for (int d = 0; d < 3; ++d) u[corner(I, J, K)][d] = __ldg(a.u + n + d);
+                    for (int d = 0; d < 3; ++d) uc[corner(I, J, K)][d] = __ldg(u + n + d);
                 }
         CellGrad<T> g;
-        cell_gradients<T>(u, g);
-        const uint4 sp = __ldg(a.spins + blk);
+        cell_gradients<T>(uc, g);
+        const uint4 sp = __ldg(a.spins + R.blk_off + blk);
         T out[2][6][4];
         Row24<T> row;
         uint32_t qprev = 0xffffffffu;
@@ -130,10 +134,11 @@ __global__ void __launch_bounds__(256) k_stress(StressArgs<T> a) {
             }
             acc.add(6, T(0.5) * w);
         }
+        T *sig = a.sig + 48ll * R.blk_off;
 #pragma unroll
         for (int c = 0; c < 2; ++c)
 #pragma unroll
-            for (int k = 0; k < 6; ++k) store4<T>(a.sig + 4ll * ((long long)(c * 6 + k) * a.nblk + blk), out[c][k]);
+            for (int k = 0; k < 6; ++k) store4<T>(sig + 4ll * ((long long)(c * 6 + k) * R.nblk + blk), out[c][k]);
     }
     acc.warp_reduce();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -142,19 +147,21 @@ __global__ void __launch_bounds__(256) k_stress(StressArgs<T> a) {
     __syncthreads();
     if (threadIdx.x < 7) {
         double s = 0.0;
-        for (int w = 0; w < 8; ++w) s += red[w][threadIdx.x];
+        for (int w = 0; w < BLOCK_THREADS / 32; ++w) s += red[w][threadIdx.x];
         a.partials[7ll * blockIdx.x + threadIdx.x] = s;
     }
 }
 
-// Fixed-order FP64 reduction of the stress partials, uniaxial control update of
-// the mean strain, and the Monte Carlo step counter.
-__global__ void __launch_bounds__(256) k_end_mcs(DevState *st, const double *partials, int nparts,
-                                                  long long n_sites, int update_strain, int advance) {
+// One CTA per replica: fixed-order FP64 reduction of its stress partials,
+// uniaxial control update of its mean strain, and its Monte Carlo step counter.
+__global__ void __launch_bounds__(256) k_end_mcs(const Replica *reps, const double *partials, int update_strain,
+                                                  int advance) {
     __shared__ double red[256][7];
+    const Replica &R = reps[blockIdx.x];
+    DevState *st = R.st;
     double s[7] = {0, 0, 0, 0, 0, 0, 0};
-    for (int p = threadIdx.x; p < nparts; p += 256)
-        for (int i = 0; i < 7; ++i) s[i] += partials[7ll * p + i];
+    for (int p = threadIdx.x; p < R.ncta; p += 256)
+        for (int i = 0; i < 7; ++i) s[i] += partials[7ll * (R.cta_off + p) + i];
     for (int i = 0; i < 7; ++i) red[threadIdx.x][i] = s[i];
     __syncthreads();
     for (int w = 128; w; w >>= 1) {
@@ -163,10 +170,11 @@ __global__ void __launch_bounds__(256) k_end_mcs(DevState *st, const double *par
         __syncthreads();
     }
     if (threadIdx.x == 0) {
+        const double n_sites = 8.0 * (double)R.nblk;
         double mean[6];
         int bad = 0;
         for (int i = 0; i < 6; ++i) {
-            mean[i] = red[0][i] / (double)n_sites;
+            mean[i] = red[0][i] / n_sites;
             st->mean_sigma[i] = mean[i];
             bad |= !isfinite(mean[i]);
         }
@@ -298,23 +306,17 @@ __global__ void k_bins(const unsigned long long *counts, const int32_t *binmap, 
 
 }  // namespace
 
-int stress_grid(long long nblk) {
-    long long g = (nblk + 255) / 256;
-    if (g > 65535ll * 16) g = 65535ll * 16;
-    return (int)g;
-}
-
 template <typename T>
-cudaError_t launch_stress(const StressArgs<T> &a, int grid, cudaStream_t s) {
-    k_stress<T><<<grid, 256, 0, s>>>(a);
+cudaError_t launch_stress(const StressArgs<T> &a, cudaStream_t s) {
+    k_stress<T><<<a.nctas, BLOCK_THREADS, 0, s>>>(a);
     return cudaGetLastError();
 }
-template cudaError_t launch_stress<float>(const StressArgs<float> &, int, cudaStream_t);
-template cudaError_t launch_stress<double>(const StressArgs<double> &, int, cudaStream_t);
+template cudaError_t launch_stress<float>(const StressArgs<float> &, cudaStream_t);
+template cudaError_t launch_stress<double>(const StressArgs<double> &, cudaStream_t);
 
-cudaError_t launch_end_mcs(DevState *st, const double *partials, int nparts, long long n_sites, int update_strain,
-                           int advance, cudaStream_t s) {
-    k_end_mcs<<<1, 256, 0, s>>>(st, partials, nparts, n_sites, update_strain, advance);
+cudaError_t launch_end_mcs(const Replica *reps, int nrep, const double *partials, int update_strain, int advance,
+                           cudaStream_t s) {
+    k_end_mcs<<<nrep, 256, 0, s>>>(reps, partials, update_strain, advance);
     return cudaGetLastError();
 }
 

@@ -4,7 +4,7 @@
 // constant-traction zone shift (Eqs. 6-8 and 13) from the stored stress.
 //
 // One thread per 2x2x2 block: it tries the block's four sites of the sweep's
-// colour.  Loads per block: the block's 16 B of spins, the other colour's
+// colour.  A CTA covers 256 blocks of one replica of the batch.  Loads per block: the block's 16 B of spins, the other colour's
 // 8 B quad of the six face neighbours (cache hits: every quad is some other
 // thread's own), and six 16 B stress vectors (FP32).  Writes: the colour's
 // 8 B quad when a site changed.  Same-colour sites share no neighbour, so the
@@ -84,22 +84,25 @@ __device__ __forceinline__ float log_t(float x) { return logf(x); }
 __device__ __forceinline__ double log_t(double x) { return log(x); }
 
 template <typename T, bool ELASTIC>
-__global__ void __launch_bounds__(256) k_sweep(SweepArgs<T> a, int colour) {
-    const long long blk = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(BLOCK_THREADS, (sizeof(T) == 4 ? 3 : 2)) k_sweep(SweepArgs<T> a, int colour) {
+    const int r = __ldg(a.cta_rep + blockIdx.x);
+    const Replica &R = a.reps[r];
+    const int blk = (blockIdx.x - R.cta_off) * BLOCK_THREADS + threadIdx.x;  // block within the replica
     int nacc = 0;
-    if (blk < a.nblk) {
-        const int bx = (int)(blk % a.nbx);
-        const long long r = blk / a.nbx;
-        const int by = (int)(r % a.nby), bz = (int)(r / a.nby);
-        const long long sxy = a.nbx, sxz = (long long)a.nbx * a.nby;
-        const long long bxm = blk + (bx == 0 ? a.nbx - 1 : -1), bxp = blk + (bx == a.nbx - 1 ? 1 - a.nbx : 1);
-        const long long bym = blk + (by == 0 ? (a.nby - 1) * sxy : -sxy);
-        const long long byp = blk + (by == a.nby - 1 ? -(a.nby - 1) * sxy : sxy);
-        const long long bzm = blk + (bz == 0 ? (a.nbz - 1) * sxz : -sxz);
-        const long long bzp = blk + (bz == a.nbz - 1 ? -(a.nbz - 1) * sxz : sxz);
-        const uint2 *q2 = reinterpret_cast<const uint2 *>(a.spins);
+    if (blk < R.nblk) {
+        const int nbx = R.nbx, nby = R.nby, nbz = R.nbz;
+        const int bx = blk % nbx, rr = blk / nbx;
+        const int by = rr % nby, bz = rr / nby;
+        const int sxy = nbx, sxz = nbx * nby;
+        const int bxm = blk + (bx == 0 ? nbx - 1 : -1), bxp = blk + (bx == nbx - 1 ? 1 - nbx : 1);
+        const int bym = blk + (by == 0 ? (nby - 1) * sxy : -sxy);
+        const int byp = blk + (by == nby - 1 ? -(nby - 1) * sxy : sxy);
+        const int bzm = blk + (bz == 0 ? (nbz - 1) * sxz : -sxz);
+        const int bzp = blk + (bz == nbz - 1 ? -(nbz - 1) * sxz : sxz);
+        uint4 *spins = a.spins + R.blk_off;
+        const uint2 *q2 = reinterpret_cast<const uint2 *>(spins);
         const int oc = colour ^ 1;
-        const uint4 own4 = a.spins[blk];
+        const uint4 own4 = spins[blk];
         const uint2 mine = colour ? make_uint2(own4.z, own4.w) : make_uint2(own4.x, own4.y);
         const uint2 O = oc ? make_uint2(own4.z, own4.w) : make_uint2(own4.x, own4.y);
         const uint2 Oxm = __ldg(q2 + 2 * bxm + oc), Oxp = __ldg(q2 + 2 * bxp + oc);
@@ -107,23 +110,25 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs<T> a, int colour) {
         const uint2 Ozm = __ldg(q2 + 2 * bzm + oc), Ozp = __ldg(q2 + 2 * bzp + oc);
         T sg[6][4];
         if (ELASTIC) {
+            const T *sig = a.sig + 48ll * R.blk_off;
 #pragma unroll
             for (int k = 0; k < 6; ++k) {
                 Vec4<T> t;
-                t.load(a.sig + 4ll * ((long long)(colour * 6 + k) * a.nblk + blk));
+                t.load(sig + 4ll * ((long long)(colour * 6 + k) * R.nblk + blk));
 #pragma unroll
                 for (int i = 0; i < 4; ++i) sg[k][i] = t.v[i];
             }
         }
-        const uint32_t mcs = a.st->mcs;
+        const uint32_t mcs = R.st->mcs;
         // the four sites' Philox draws first: four independent chains for the scheduler
         uint2 rnd[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const int L = slot_local(4 * colour + i);
             const uint32_t x = 2u * bx + (L & 1), y = 2u * by + ((L >> 1) & 1), z = 2u * bz + (L >> 2);
-            rnd[i] = philox_r01(x + (uint32_t)a.nx * (y + (uint32_t)a.ny * z), mcs, a.replica, 0u, a.key0, a.key1);
+            rnd[i] = philox_r01(x + (uint32_t)R.nx * (y + (uint32_t)R.ny * z), mcs, R.replica, 0u, R.key0, R.key1);
         }
+        const T lam_sd_half = (T)R.lam_sd_half;
         uint16_t out[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
@@ -158,7 +163,7 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs<T> a, int colour) {
                 T s[6];
 #pragma unroll
                 for (int k = 0; k < 6; ++k) s[k] = sg[k][i];
-                dHe = a.lam_sd_half * (zone_phi<T>(a.wtab + 20ll * q, s) - zone_phi<T>(a.wtab + 20ll * qn, s));
+                dHe = lam_sd_half * (zone_phi<T>(a.wtab + 20ll * q, s) - zone_phi<T>(a.wtab + 20ll * qn, s));
             }
             bool acc;
             if (!ELASTIC || dHe == T(0)) {
@@ -178,22 +183,22 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs<T> a, int colour) {
             uint2 w;
             w.x = (uint32_t)out[0] | ((uint32_t)out[1] << 16);
             w.y = (uint32_t)out[2] | ((uint32_t)out[3] << 16);
-            reinterpret_cast<uint2 *>(a.spins)[2 * blk + colour] = w;
+            reinterpret_cast<uint2 *>(spins)[2 * blk + colour] = w;
         }
     }
+    // a CTA belongs to one replica: warp totals go to that replica's counter
     const unsigned tot = __reduce_add_sync(0xffffffffu, (unsigned)nacc);
-    if ((threadIdx.x & 31) == 0 && tot) atomicAdd(&a.st->accepted, (unsigned long long)tot);
+    if ((threadIdx.x & 31) == 0 && tot) atomicAdd(&R.st->accepted, (unsigned long long)tot);
 }
 
 }  // namespace
 
 template <typename T>
 cudaError_t launch_sweep(const SweepArgs<T> &a, int colour, bool elastic, cudaStream_t s) {
-    const int grid = (int)((a.nblk + 255) / 256);
     if (elastic)
-        k_sweep<T, true><<<grid, 256, 0, s>>>(a, colour);
+        k_sweep<T, true><<<a.nctas, BLOCK_THREADS, 0, s>>>(a, colour);
     else
-        k_sweep<T, false><<<grid, 256, 0, s>>>(a, colour);
+        k_sweep<T, false><<<a.nctas, BLOCK_THREADS, 0, s>>>(a, colour);
     return cudaGetLastError();
 }
 
