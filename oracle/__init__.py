@@ -48,6 +48,7 @@ def lib():
         L.orc_point_stress.argtypes = [i, i, i, u16p, dp, dp, dp, i, i, i, dp]
         L.orc_internal_force.argtypes = [i, i, i, u16p, dp, dp, dp, dp]
         L.orc_lumped_mass.argtypes = [i, i, i, dp]
+        L.orc_strain_field.argtypes = [i, i, i, dp, dp, dp]
         L.orc_node_force.argtypes = [i, i, i, u16p, dp, dp, dp, i, i, i, dp]
         L.orc_mpm_step.argtypes = [i, i, i, u16p, dp, dp, dp, dp, C.c_double, C.c_double, dp, dp]
         L.orc_stress_field.argtypes = [i, i, i, u16p, dp, dp, dp, dp, dp, dp]
@@ -249,6 +250,15 @@ def node_force(spins, Ct, u, Ebar, i, j, k):
     lib().orc_node_force(nx, ny, nz, _p(s, C.c_uint16), _p(Cf, C.c_double), _p(u, C.c_double),
                          _p(E, C.c_double), int(i), int(j), int(k), _p(f, C.c_double))
     return f
+
+
+def strain_field(shape, u, Ebar):
+    """(N,6) strain of every point."""
+    nz, ny, nx = shape
+    u, E = _f64(u), _f64(Ebar)
+    eps = np.zeros((nx * ny * nz, 6))
+    lib().orc_strain_field(nx, ny, nz, _p(u, C.c_double), _p(E, C.c_double), _p(eps, C.c_double))
+    return eps
 
 
 def lumped_mass(shape):

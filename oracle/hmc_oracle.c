@@ -217,6 +217,17 @@ void orc_point_strain(int nx, int ny, int nz, const double *u, const double Ebar
     eps[5] = Ebar[5] + G[0][1] + G[1][0];
 }
 
+/* Strain of every point (N x 6). */
+void orc_strain_field(int nx, int ny, int nz, const double *u, const double Ebar[6], double *eps)
+{
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                int64_t p = (int64_t)x + (int64_t)nx * ((int64_t)y + (int64_t)ny * z);
+                orc_point_strain(nx, ny, nz, u, Ebar, x, y, z, eps + 6 * p);
+            }
+}
+
 /* Hooke's law, Eq. 1: S = C eps with the point's rotated stiffness. */
 static void hooke(const double *C, const double eps[6], double sig[6])
 {
