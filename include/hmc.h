@@ -255,6 +255,25 @@ hmc_status hmc_stress_noalloc(const uint16_t *d_spins, const float *d_u, const f
                               const double *strain_bar, int32_t nx, int32_t ny, int32_t nz, float *d_sigma,
                               double *d_mean, double *d_energy, void *stream);
 
+/* Adjoint of the explicit MPM stress solve (single-replica handles).  The map:
+ * nsteps explicit MPM steps from the current nodal state with the spins
+ * frozen (Sec. "Elastic Deformation"), parameters theta = (C11, C12, C44,
+ * Ebar_1..6) -- the cubic constants of the handle and its current mean strain
+ * -- and outputs W = sum_p w_p and the per-point field w_p = 1/2 eps_p.C'_p.eps_p
+ * = 1/2 sigma_p.S'_p.sigma_p (the one-point zone energy of Eq. 8 read at
+ * constant traction) at the final state.
+ * hmc_adjoint_forward runs the map (the handle's state advances by nsteps MPM
+ * steps), keeping (u, v) every checkpoint_every steps on the device; *W
+ * (nullable) and w_field (N doubles, natural order, nullable) receive the
+ * outputs.  hmc_adjoint_backward then returns in grad[9] the gradient
+ * dL/dtheta of L = gW W + sum_p g_p w_p (g_field: N doubles, nullable = 0) by
+ * a reverse sweep that recomputes each checkpoint segment forward; it needs
+ * the state that hmc_adjoint_forward left (HMC_ERR_STATE if anything changed
+ * the spins, nodal state, mean strain or orientations since).  The adjoint
+ * buffers are allocated by the first forward call and kept with the handle. */
+hmc_status hmc_adjoint_forward(hmc_handle *h, int32_t nsteps, int32_t checkpoint_every, double *W, double *w_field);
+hmc_status hmc_adjoint_backward(hmc_handle *h, double gW, const double *g_field, double *grad);
+
 /* Wait for all work on the handle's stream. */
 hmc_status hmc_synchronize(hmc_handle *h);
 

@@ -97,6 +97,8 @@ def _load():
         "hmc_get_state": (st, [H, C.c_void_p, C.POINTER(C.c_size_t)]),
         "hmc_set_state": (st, [H, C.c_void_p, C.c_size_t]),
         "hmc_synchronize": (st, [H]),
+        "hmc_adjoint_forward": (st, [H, C.c_int32, C.c_int32, dp, dp]),
+        "hmc_adjoint_backward": (st, [H, C.c_double, dp, dp]),
         "hmc_stress_noalloc": (st, [C.c_void_p, C.c_void_p, C.c_void_p, dp, C.c_int32, C.c_int32, C.c_int32,
                                     C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
         "hmc_last_error": (C.c_char_p, [H]),
@@ -282,6 +284,22 @@ def hmc_stress_noalloc(d_spins, d_u, d_ctab, strain_bar, nx, ny, nz, d_sigma, d_
     e = np.ascontiguousarray(strain_bar, dtype=np.float64)
     _check(None, lib.hmc_stress_noalloc(d_spins, d_u, d_ctab, _ptr(e, C.c_double), int(nx), int(ny), int(nz),
                                         d_sigma, d_mean, d_energy, stream))
+
+
+def hmc_adjoint_forward(h, nsteps, checkpoint_every, n_sites=None):
+    """Run the MPM map keeping checkpoints; returns (W, w field or None)."""
+    W = np.zeros(1)
+    w = None if n_sites is None else np.zeros(n_sites)
+    _check(h, lib.hmc_adjoint_forward(h, int(nsteps), int(checkpoint_every), _ptr(W, C.c_double), _ptr(w, C.c_double)))
+    return float(W[0]), w
+
+
+def hmc_adjoint_backward(h, gW, g_field=None):
+    """d(gW W + g.w)/d(C11, C12, C44, Ebar_1..6) after hmc_adjoint_forward."""
+    g = None if g_field is None else np.ascontiguousarray(g_field, dtype=np.float64).reshape(-1)
+    out = np.zeros(9)
+    _check(h, lib.hmc_adjoint_backward(h, float(gW), _ptr(g, C.c_double), _ptr(out, C.c_double)))
+    return out
 
 
 def hmc_last_error(h=None) -> str:

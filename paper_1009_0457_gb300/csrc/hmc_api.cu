@@ -18,6 +18,7 @@
 
 #include "hmc.h"
 #include "hmc_internal.h"
+#include "hmc_adjoint.h"
 
 using hmc::DevState;
 
@@ -86,6 +87,21 @@ struct hmc_handle {
     std::vector<double> A, Cv, Sv;
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     std::string err;
+    // adjoint of the MPM solve (single replica; allocated by the first hmc_adjoint_forward)
+    struct {
+        int steps = 0, ck = 0, nseg = 0, nctas = 0;
+        bool have_forward = false;
+        long long state_version = -1;
+        int rtab_version = -1;
+        void *rtab = nullptr, *lam = nullptr, *ubar = nullptr, *tmp = nullptr, *vtmp = nullptr, *seg = nullptr;
+        void *ck_u = nullptr, *ck_v = nullptr, *w = nullptr, *g = nullptr, *fcell = nullptr;
+        double *partials = nullptr, *grad = nullptr;
+        hmc::Replica *reps0 = nullptr;   // descriptors whose state has Ebar = 0
+        DevState *st0 = nullptr;
+        double ebar[6] = {0, 0, 0, 0, 0, 0};
+    } adj;
+    long long state_version = 0;   // advanced by every call that changes spins, nodal state or Ebar
+    int orient_version = 0;
 };
 
 namespace {
@@ -351,7 +367,24 @@ std::string validate_shared(const hmc_params *a, const hmc_params *b) {
     return "";
 }
 
+void free_adjoint(hmc_handle *h) {
+    void *bufs[] = {h->adj.rtab, h->adj.lam, h->adj.ubar, h->adj.tmp, h->adj.vtmp, h->adj.seg, h->adj.ck_u,
+                    h->adj.ck_v, h->adj.w, h->adj.g, h->adj.fcell, h->adj.partials, h->adj.grad, h->adj.reps0,
+                    h->adj.st0};
+    for (void *b : bufs)
+        if (b) cudaFree(b);
+    h->adj.rtab = h->adj.lam = h->adj.ubar = h->adj.tmp = h->adj.vtmp = h->adj.seg = nullptr;
+    h->adj.ck_u = h->adj.ck_v = h->adj.w = h->adj.g = h->adj.fcell = nullptr;
+    h->adj.partials = h->adj.grad = nullptr;
+    h->adj.reps0 = nullptr;
+    h->adj.st0 = nullptr;
+    h->adj.steps = h->adj.ck = h->adj.nseg = 0;
+    h->adj.have_forward = false;
+    h->adj.rtab_version = -1;
+}
+
 void destroy_buffers(hmc_handle *h) {
+    free_adjoint(h);
     for (int i = 0; i < 2; ++i)
         if (h->gexec[i]) cudaGraphExecDestroy(h->gexec[i]);
     void *bufs[] = {h->spins, h->stage16, h->u[0], h->u[1], h->v, h->sig, h->ctab, h->wtab, h->thr, h->counts,
@@ -764,6 +797,7 @@ hmc_status hmc_get_tuning(hmc_handle *h, int32_t *mpm_shape, int32_t *mpm_grid) 
 }
 
 hmc_status hmc_set_orientations(hmc_handle *h, const double *euler, const uint16_t *spins) {
+    if (h) ++h->state_version;
     if (!h) return HMC_ERR_ARG;
     if (!euler || !spins) return fail(h, HMC_ERR_ARG, "NULL euler or spins");
     const int Q = h->p.n_orient;
@@ -849,10 +883,12 @@ hmc_status hmc_set_orientations(hmc_handle *h, const double *euler, const uint16
     }
     HMC_CK(h, cudaStreamSynchronize(h->stream), "sync");
     h->oriented = true;
+    ++h->orient_version;
     return HMC_OK;
 }
 
 hmc_status hmc_set_spins(hmc_handle *h, const uint16_t *spins) {
+    if (h) ++h->state_version;
     hmc_status s = need_oriented(h);
     if (s != HMC_OK) return s;
     if (!spins) return fail(h, HMC_ERR_ARG, "NULL spins");
@@ -884,6 +920,7 @@ hmc_status hmc_compute_stress(hmc_handle *h, double *mean, double *energy) {
 }
 
 hmc_status hmc_mpm_steps(hmc_handle *h, int32_t nsteps, double *energy) {
+    if (h) ++h->state_version;
     hmc_status s = need_oriented(h);
     if (s != HMC_OK) return s;
     if (nsteps < 0) return fail(h, HMC_ERR_ARG, "nsteps < 0");
@@ -894,6 +931,7 @@ hmc_status hmc_mpm_steps(hmc_handle *h, int32_t nsteps, double *energy) {
 }
 
 hmc_status hmc_sweep_half(hmc_handle *h, int32_t colour, int64_t *accepted) {
+    if (h) ++h->state_version;
     hmc_status s = need_oriented(h);
     if (s != HMC_OK) return s;
     if (colour != 0 && colour != 1) return fail(h, HMC_ERR_ARG, "colour must be 0 or 1");
@@ -904,6 +942,7 @@ hmc_status hmc_sweep_half(hmc_handle *h, int32_t colour, int64_t *accepted) {
 }
 
 hmc_status hmc_end_mcs(hmc_handle *h) {
+    if (h) ++h->state_version;
     hmc_status s = need_oriented(h);
     if (s != HMC_OK) return s;
     HMC_CK(h, hmc::launch_end_mcs(h->d_reps, h->R, h->partials, 1, 1, h->stream), "end-of-step launch");
@@ -911,6 +950,7 @@ hmc_status hmc_end_mcs(hmc_handle *h) {
 }
 
 hmc_status hmc_mc_sweeps(hmc_handle *h, int32_t n_mcs, int64_t *accepted) {
+    if (h) ++h->state_version;
     hmc_status s = need_oriented(h);
     if (s != HMC_OK) return s;
     if (n_mcs < 0) return fail(h, HMC_ERR_ARG, "n_mcs < 0");
@@ -1086,6 +1126,7 @@ hmc_status hmc_get_nodal(hmc_handle *h, double *u, double *v) {
 }
 
 hmc_status hmc_set_nodal(hmc_handle *h, const double *u, const double *v) {
+    if (h) ++h->state_version;
     hmc_status s = need_oriented(h);
     if (s != HMC_OK) return s;
     const size_t n = 3 * (size_t)selr(h).nblk;
@@ -1107,6 +1148,7 @@ hmc_status hmc_get_strain(hmc_handle *h, double *e) {
 }
 
 hmc_status hmc_set_strain(hmc_handle *h, const double *e) {
+    if (h) ++h->state_version;
     if (!h) return HMC_ERR_ARG;
     if (!e) return fail(h, HMC_ERR_ARG, "NULL strain");
     double d[6];
@@ -1200,5 +1242,247 @@ hmc_status hmc_synchronize(hmc_handle *h) {
 }
 
 const char *hmc_last_error(const hmc_handle *h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+}  // extern "C"
+
+// ---- adjoint of the explicit MPM solve ---------------------------------------
+
+namespace {
+
+template <typename T>
+cudaError_t mpm_custom(hmc_handle *h, const void *uin, void *uout, void *v, const hmc::Replica *reps, double keep) {
+    hmc::MpmArgs<T> a = mpm_args<T>(h, uin, uout, v);
+    a.reps = reps;
+    a.keep = (T)keep;
+    return hmc::launch_mpm_step<T>(a, h->mpm_shape, h->stream);
+}
+
+cudaError_t mpm_custom_any(hmc_handle *h, const void *uin, void *uout, void *v, const hmc::Replica *reps,
+                           double keep) {
+    return h->p.precision == HMC_FP32 ? mpm_custom<float>(h, uin, uout, v, reps, keep)
+                                      : mpm_custom<double>(h, uin, uout, v, reps, keep);
+}
+
+template <typename T>
+hmc::AdjArgs<T> adj_args(hmc_handle *h) {
+    hmc::AdjArgs<T> a;
+    const RepHost &R = h->reps[0];
+    a.spins = h->spins;
+    a.ctab = static_cast<const T *>(h->ctab);
+    a.rtab = static_cast<const T *>(h->adj.rtab);
+    a.partials = h->adj.partials;
+    for (int i = 0; i < 6; ++i) a.ebar[i] = (T)h->adj.ebar[i];
+    a.nx = R.p.nx; a.ny = R.p.ny; a.nz = R.p.nz;
+    a.nbx = R.nbx; a.nby = R.nby; a.nbz = R.nbz;
+    a.nblk = (int)R.nblk;
+    return a;
+}
+
+char *seg_ptr(hmc_handle *h, void *base, int j) { return static_cast<char *>(base) + (size_t)j * node_bytes(h); }
+
+hmc_status adj_alloc(hmc_handle *h, int steps, int ck) {
+    auto &A = h->adj;
+    const int nseg = (steps + ck - 1) / ck;
+    if (A.lam && A.steps == steps && A.ck == ck) return HMC_OK;
+    HMC_CK(h, cudaStreamSynchronize(h->stream), "sync");
+    free_adjoint(h);
+    const RepHost &R = h->reps[0];
+    const size_t nb = node_bytes(h);
+    A.nctas = (int)((R.nblk + 255) / 256);
+    struct Alloc { void **ptr; size_t bytes; const char *what; };
+    Alloc allocs[] = {
+        {&A.rtab, h->tsize * 72 * (size_t)h->p.n_orient, "basis tables"},
+        {&A.lam, nb, "adjoint lambda"}, {&A.ubar, nb, "adjoint u"}, {&A.tmp, nb, "adjoint scratch"},
+        {&A.vtmp, nb, "segment velocity"}, {&A.seg, nb * (size_t)ck, "segment states"},
+        {&A.ck_u, nb * (size_t)nseg, "checkpoints u"}, {&A.ck_v, nb * (size_t)nseg, "checkpoints v"},
+        {&A.w, h->tsize * (size_t)R.N, "field w"}, {&A.g, h->tsize * (size_t)R.N, "cotangent field"},
+        {&A.fcell, h->tsize * 24 * (size_t)R.nblk, "cell contributions"},
+        {(void **)&A.partials, sizeof(double) * 10 * (size_t)A.nctas, "adjoint partials"},
+        {(void **)&A.grad, sizeof(double) * 10, "gradient"},
+        {(void **)&A.reps0, sizeof(hmc::Replica), "adjoint descriptor"},
+        {(void **)&A.st0, sizeof(DevState), "adjoint state"},
+    };
+    for (auto &a : allocs) {
+        cudaError_t e = cudaMalloc(a.ptr, a.bytes);
+        if (e != cudaSuccess) {
+            free_adjoint(h);
+            return cuda_fail(h, e, a.what);
+        }
+    }
+    A.steps = steps;
+    A.ck = ck;
+    A.nseg = nseg;
+    // the replica's descriptor with a zero mean strain, for F(lambda; Ebar = 0)
+    hmc::Replica rd;
+    HMC_CK(h, cudaMemcpy(&rd, h->d_reps, sizeof(rd), cudaMemcpyDeviceToHost), "descriptor download");
+    rd.st = A.st0;
+    DevState z;
+    std::memset(&z, 0, sizeof(z));
+    HMC_CK(h, cudaMemcpy(A.reps0, &rd, sizeof(rd), cudaMemcpyHostToDevice), "descriptor upload");
+    HMC_CK(h, cudaMemcpy(A.st0, &z, sizeof(z), cudaMemcpyHostToDevice), "state upload");
+    return HMC_OK;
+}
+
+// Rotated basis tensors R_1, R_2, R_3 (C' = C11 R_1 + C12 R_2 + C44 R_3) by the
+// same Bond transform as the stiffness table.
+hmc_status adj_tables(hmc_handle *h) {
+    auto &A = h->adj;
+    if (A.rtab_version == h->orient_version) return HMC_OK;
+    const int Q = h->p.n_orient;
+    std::vector<double> Rv((size_t)Q * 3 * 36);
+    for (int i = 0; i < 3; ++i) {
+        double B[36] = {0};
+        const double c11 = i == 0, c12 = i == 1, c44 = i == 2;
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) B[6 * a + b] = (a == b) ? c11 : c12;
+        for (int a = 3; a < 6; ++a) B[6 * a + a] = c44;
+        for (int q = 0; q < Q; ++q) {
+            double M[36], Ns[36];
+            bond(&h->A[(size_t)q * 9], M, Ns);
+            congruence(M, B, &Rv[((size_t)q * 3 + i) * 36]);
+        }
+    }
+    auto pack = [&](auto tag) -> hmc_status {
+        using T = decltype(tag);
+        std::vector<T> out((size_t)Q * 72, T(0));
+        for (int q = 0; q < Q; ++q)
+            for (int i = 0; i < 3; ++i) {
+                int n = 0;
+                for (int a = 0; a < 6; ++a)
+                    for (int b = a; b < 6; ++b) out[(size_t)q * 72 + 24 * i + n++] = (T)Rv[((size_t)q * 3 + i) * 36 + 6 * a + b];
+            }
+        HMC_CK(h, cudaMemcpy(A.rtab, out.data(), out.size() * sizeof(T), cudaMemcpyHostToDevice), "basis upload");
+        return HMC_OK;
+    };
+    hmc_status s = h->p.precision == HMC_FP32 ? pack(float()) : pack(double());
+    if (s != HMC_OK) return s;
+    A.rtab_version = h->orient_version;
+    return HMC_OK;
+}
+
+template <typename T>
+cudaError_t adj_terminal(hmc_handle *h, const T *g, double gW, T *w) {
+    return hmc::launch_adj_terminal<T>(adj_args<T>(h), static_cast<const T *>(h->u[h->cur]), g, (T)gW, w,
+                                       static_cast<T *>(h->adj.fcell), h->stream);
+}
+
+template <typename T>
+hmc_status adj_backward_t(hmc_handle *h, double gW, const double *g_field, double *grad) {
+    auto &A = h->adj;
+    const RepHost &R = h->reps[0];
+    const double c = h->dt / 8.0;
+    const T *g = nullptr;
+    if (g_field) {
+        std::vector<T> t((size_t)R.N);
+        for (long long i = 0; i < R.N; ++i) {
+            if (!std::isfinite(g_field[i])) return fail(h, HMC_ERR_ARG, "non-finite cotangent");
+            t[i] = (T)g_field[i];
+        }
+        HMC_CK(h, cudaMemcpyAsync(A.g, t.data(), t.size() * sizeof(T), cudaMemcpyHostToDevice, h->stream), "upload");
+        HMC_CK(h, cudaStreamSynchronize(h->stream), "sync");
+        g = static_cast<const T *>(A.g);
+    }
+    HMC_CK(h, cudaMemsetAsync(A.grad, 0, sizeof(double) * 10, h->stream), "memset");
+    // terminal: direct parameter terms and ubar^T = sum_p alpha_p B_p^T sigma_p, lambda^T = dt ubar^T
+    HMC_CK(h, adj_terminal<T>(h, g, gW, nullptr), "terminal launch");
+    HMC_CK(h, hmc::launch_adj_reduce(A.partials, A.nctas, 10, 10, 1.0, A.grad, h->stream), "reduce launch");
+    const hmc::AdjArgs<T> aa = adj_args<T>(h);
+    HMC_CK(h, hmc::launch_adj_gather<T>(aa, static_cast<const T *>(A.fcell), T(1), static_cast<T *>(A.ubar), h->stream),
+           "gather launch");
+    HMC_CK(h, hmc::launch_adj_gather<T>(aa, static_cast<const T *>(A.fcell), (T)h->dt, static_cast<T *>(A.lam),
+                                        h->stream),
+           "gather launch");
+    const size_t nb = node_bytes(h);
+    for (int s = A.nseg - 1; s >= 0; --s) {
+        const int n0 = s * A.ck, len = std::min(A.ck, A.steps - n0);
+        // recompute the segment's forward states u^{n0} .. u^{n0+len-1} from its checkpoint
+        HMC_CK(h, cudaMemcpyAsync(seg_ptr(h, A.seg, 0), seg_ptr(h, A.ck_u, s), nb, cudaMemcpyDeviceToDevice, h->stream),
+               "checkpoint copy");
+        HMC_CK(h, cudaMemcpyAsync(A.vtmp, seg_ptr(h, A.ck_v, s), nb, cudaMemcpyDeviceToDevice, h->stream),
+               "checkpoint copy");
+        for (int j = 1; j < len; ++j)
+            HMC_CK(h, mpm_custom<T>(h, seg_ptr(h, A.seg, j - 1), seg_ptr(h, A.seg, j), A.vtmp, h->d_reps,
+                                    1.0 - h->damping),
+                   "recompute launch");
+        for (int j = len - 1; j >= 0; --j) {
+            HMC_CK(h, hmc::launch_adj_params<T>(aa, static_cast<const T *>(A.lam),
+                                                reinterpret_cast<const T *>(seg_ptr(h, A.seg, j)), h->stream),
+                   "parameter launch");
+            HMC_CK(h, hmc::launch_adj_reduce(A.partials, A.nctas, 9, 9, -c, A.grad + 1, h->stream), "reduce launch");
+            // ubar^n = ubar^{n+1} + c F(lambda^{n+1}; 0); tmp = lambda^{n+1} + dt ubar^n
+            HMC_CK(h, mpm_custom<T>(h, A.lam, A.tmp, A.ubar, A.reps0, 1.0), "adjoint step launch");
+            HMC_CK(h, hmc::launch_adj_lambda<T>(3ll * R.nblk, static_cast<const T *>(A.tmp), (T)h->damping,
+                                                static_cast<T *>(A.lam), h->stream),
+                   "lambda launch");
+        }
+    }
+    double out[10];
+    HMC_CK(h, cudaMemcpyAsync(out, A.grad, sizeof(out), cudaMemcpyDeviceToHost, h->stream), "download");
+    HMC_CK(h, cudaStreamSynchronize(h->stream), "sync");
+    for (int k = 0; k < 9; ++k) {
+        if (!std::isfinite(out[1 + k])) return fail(h, HMC_ERR_NONFINITE, "non-finite gradient");
+        grad[k] = out[1 + k];
+    }
+    return HMC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+hmc_status hmc_adjoint_forward(hmc_handle *h, int32_t nsteps, int32_t checkpoint_every, double *W, double *w_field) {
+    hmc_status s = need_oriented(h);
+    if (s != HMC_OK) return s;
+    if (h->R != 1) return fail(h, HMC_ERR_STATE, "the adjoint runs on single-replica handles");
+    if (nsteps < 1 || checkpoint_every < 1) return fail(h, HMC_ERR_ARG, "nsteps and checkpoint_every must be >= 1");
+    if ((s = ensure_tuned(h)) != HMC_OK) return s;
+    if ((s = adj_alloc(h, nsteps, checkpoint_every)) != HMC_OK) return s;
+    if ((s = adj_tables(h)) != HMC_OK) return s;
+    auto &A = h->adj;
+    HMC_CK(h, cudaMemcpyAsync(A.ebar, h->st[0].ebar, sizeof(A.ebar), cudaMemcpyDeviceToHost, h->stream), "download");
+    HMC_CK(h, cudaStreamSynchronize(h->stream), "sync");
+    const size_t nb = node_bytes(h);
+    for (int sg = 0; sg < A.nseg; ++sg) {
+        HMC_CK(h, cudaMemcpyAsync(seg_ptr(h, A.ck_u, sg), h->u[h->cur], nb, cudaMemcpyDeviceToDevice, h->stream),
+               "checkpoint");
+        HMC_CK(h, cudaMemcpyAsync(seg_ptr(h, A.ck_v, sg), h->v, nb, cudaMemcpyDeviceToDevice, h->stream), "checkpoint");
+        const int len = std::min(A.ck, A.steps - sg * A.ck);
+        for (int j = 0; j < len; ++j) HMC_CK(h, enq_mpm(h, h->stream), "MPM launch");
+    }
+    HMC_CK(h, cudaMemsetAsync(A.grad, 0, sizeof(double) * 10, h->stream), "memset");
+    if (h->p.precision == HMC_FP32)
+        HMC_CK(h, adj_terminal<float>(h, nullptr, 0.0, static_cast<float *>(A.w)), "terminal launch");
+    else
+        HMC_CK(h, adj_terminal<double>(h, nullptr, 0.0, static_cast<double *>(A.w)), "terminal launch");
+    HMC_CK(h, hmc::launch_adj_reduce(A.partials, A.nctas, 10, 10, 1.0, A.grad, h->stream), "reduce launch");
+    const RepHost &R = h->reps[0];
+    if (W) HMC_CK(h, cudaMemcpyAsync(W, A.grad, sizeof(double), cudaMemcpyDeviceToHost, h->stream), "download");
+    if (w_field) {
+        if (h->p.precision == HMC_FP32) {
+            std::vector<float> t((size_t)R.N);
+            HMC_CK(h, cudaMemcpyAsync(t.data(), A.w, t.size() * 4, cudaMemcpyDeviceToHost, h->stream), "download");
+            HMC_CK(h, cudaStreamSynchronize(h->stream), "sync");
+            for (long long i = 0; i < R.N; ++i) w_field[i] = t[i];
+        } else {
+            HMC_CK(h, cudaMemcpyAsync(w_field, A.w, (size_t)R.N * 8, cudaMemcpyDeviceToHost, h->stream), "download");
+        }
+    }
+    HMC_CK(h, cudaStreamSynchronize(h->stream), "sync");
+    ++h->state_version;
+    A.state_version = h->state_version;
+    A.have_forward = true;
+    return HMC_OK;
+}
+
+hmc_status hmc_adjoint_backward(hmc_handle *h, double gW, const double *g_field, double *grad) {
+    hmc_status s = need_oriented(h);
+    if (s != HMC_OK) return s;
+    if (!grad) return fail(h, HMC_ERR_ARG, "NULL grad");
+    if (!std::isfinite(gW)) return fail(h, HMC_ERR_ARG, "non-finite gW");
+    if (!h->adj.have_forward || h->adj.state_version != h->state_version || h->adj.rtab_version != h->orient_version)
+        return fail(h, HMC_ERR_STATE, "hmc_adjoint_backward needs the state left by hmc_adjoint_forward");
+    return h->p.precision == HMC_FP32 ? adj_backward_t<float>(h, gW, g_field, grad)
+                                      : adj_backward_t<double>(h, gW, g_field, grad);
+}
 
 }  // extern "C"
