@@ -363,10 +363,57 @@ def run_ours(args):
     return 0
 
 
+def run_ensemble(args):
+    """The batched ensemble: 64 replicas of uneven size in one handle, every
+    phase one launch over all replicas, one CUDA graph per MCS; prints one
+    JSON line (site-updates/s over all replicas)."""
+    import torch
+    torch.cuda.set_device(0)
+    import hmc_synth as S
+    import paper_1009_0457_gb300 as G
+    specs, euler, fields = S.ensemble_inputs()
+    stream = torch.cuda.Stream()
+    per = [dict(load_axis=sp["axis"], strain=sp["strain"], seed=sp["mc_seed"], replica=r)
+           for r, sp in enumerate(specs)]
+    b = G.HMCBatch([sp["shape"] for sp in specs], specs[0]["Q"], per, precision=G.HMC_FP32,
+                   mpm_steps_per_mcs=50, stream=stream.cuda_stream, **S.COMMON)
+    b.set_orientations(euler, fields)
+    G.lib.hmc_mc_sweeps(b.h, args.warmup, None)
+    b.synchronize()
+    N = sum(int(np.prod(sp["shape"])) for sp in specs)
+    clocks = Clocks(0)
+    torch.cuda.synchronize()
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    st = G.lib.hmc_mc_sweeps(b.h, args.steps, None)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    assert st == 0, G.hmc_last_error(b.h)
+    t = e0.elapsed_time(e1) / 1e3
+    shape, grid = b.tuning()
+    line = {"metric": METRIC, "value": N * args.steps / t, "unit": "site-updates/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"ensemble: {len(specs)} replicas, cubic edges from {S.ENSEMBLE_EDGES}, "
+                                   f"Q={specs[0]['Q']}, axis uniform on S2, strain U[5e-4, 3e-3], "
+                                   f"50 MPM steps per MCS, FP32, one launch per phase over all replicas",
+                       "sites": N, "replicas": len(specs),
+                       "edges": [sp["shape"][0] for sp in specs]},
+            "mpm_shape": ["16x16", "32x8", "8x32"][shape], "mpm_grid": grid,
+            "gpu_launches": args.steps * (50 + 4), "clocks": clk}
+    print(json.dumps(line), flush=True)
+    b.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "ensemble":
+        return run_ensemble(args)
     return run_ours(args)
 
 

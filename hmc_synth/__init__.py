@@ -167,3 +167,30 @@ def ensemble_specs(n_replicas: int = 64, seed: int = 4, Q: int = 256, grain_volu
                         voronoi_seed=int(rng.integers(1 << 31)), mc_seed=int(rng.integers(1 << 62)),
                         euler_seed=4))
     return out
+
+
+def ensemble_inputs(n_replicas: int = 64, seed: int = 4, Q: int = 256):
+    """(specs, euler (Q,3), [spins per replica]) of the batched ensemble; the
+    Voronoi fields are cached like ``workload_inputs`` when HMC_SYNTH_CACHE is set."""
+    import os
+    specs = ensemble_specs(n_replicas, seed, Q)
+    euler = euler_uniform_so3(Q, specs[0]["euler_seed"])
+    cache = os.environ.get("HMC_SYNTH_CACHE")
+    fields = []
+    for sp in specs:
+        path = None
+        if cache:
+            os.makedirs(cache, exist_ok=True)
+            e = sp["shape"][0]
+            path = os.path.join(cache, f"ens_{e}_{sp['n_seeds']}_{sp['voronoi_seed']}.npy")
+            if os.path.exists(path):
+                f = np.load(path)
+                if f.shape == tuple(sp["shape"]):
+                    fields.append(f)
+                    continue
+        f = voronoi_spins(sp["shape"], sp["n_seeds"], Q, sp["voronoi_seed"])
+        if path:
+            np.save(path + ".tmp.npy", f)
+            os.replace(path + ".tmp.npy", path)
+        fields.append(f)
+    return specs, euler, fields

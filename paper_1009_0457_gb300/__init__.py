@@ -325,6 +325,12 @@ class HMC:
     def tuning(self):
         return hmc_get_tuning(self.h)
 
+    def adjoint_forward(self, nsteps, checkpoint_every, want_field=True):
+        return hmc_adjoint_forward(self.h, nsteps, checkpoint_every, self.n_sites if want_field else None)
+
+    def adjoint_backward(self, gW, g_field=None):
+        return hmc_adjoint_backward(self.h, gW, g_field)
+
     def close(self):
         if self.h:
             hmc_destroy(self.h)
