@@ -22,14 +22,18 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import internal_force, strain_field, tables
+from . import euler_to_A, internal_force, rotated_stiffness, strain_field, tables
 
 N_PARAMS = 9
 
 
 def basis_tables(euler):
-    """Rotated basis tensors R1, R2, R3 (Q,6,6) with C' = C11 R1 + C12 R2 + C44 R3."""
-    return [tables(euler, *c)[1] for c in ((1.0, 0.0, 0.0), (0.0, 1.0, 0.0), (0.0, 0.0, 1.0))]
+    """Rotated basis tensors R1, R2, R3 (Q,6,6) with C' = C11 R1 + C12 R2 + C44 R3
+    (the rotation of Eq. 17 is linear in the tensor; the basis tensors are singular,
+    so no compliance is formed)."""
+    euler = np.asarray(euler, dtype=np.float64).reshape(-1, 3)
+    A = [euler_to_A(*e) for e in euler]
+    return [np.stack([rotated_stiffness(*c, a) for a in A]) for c in ((1.0, 0.0, 0.0), (0.0, 1.0, 0.0), (0.0, 0.0, 1.0))]
 
 
 def forward(spins, Ct, Ebar, u0, v0, nsteps, dt, damping):
