@@ -141,6 +141,10 @@ def kernel_traffic(kernel):
     return None
 
 
+def mpm_variant_name(v):
+    return ["16x16", "32x8", "8x32"][v % 3] + (" paired-FMA Hooke" if v >= 3 else "")
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -354,6 +358,7 @@ def run_ours(args):
             "stress_ms": t_stress * 1e3, "half_sweep_ms": t_sweep * 1e3,
             "roofline": roofline, "roofline_sweep": roofline_sweep,
             "e2e": e2e, "gpu_launches": launches, "clocks": clk, "fp64_form": fp64, "cpu_baseline": cpu,
+            "mpm_variant": mpm_variant_name(h.tuning()[0]), "mpm_grid": h.tuning()[1],
         }
         print(json.dumps(line), flush=True)
     h.close()
@@ -401,7 +406,7 @@ def run_ensemble(args):
                                    f"50 MPM steps per MCS, FP32, one launch per phase over all replicas",
                        "sites": N, "replicas": len(specs),
                        "edges": [sp["shape"][0] for sp in specs]},
-            "mpm_shape": ["16x16", "32x8", "8x32"][shape], "mpm_grid": grid,
+            "mpm_variant": mpm_variant_name(shape), "mpm_grid": grid,
             "gpu_launches": args.steps * (50 + 4), "clocks": clk}
     print(json.dumps(line), flush=True)
     b.close()

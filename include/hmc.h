@@ -127,11 +127,12 @@ hmc_status hmc_batch_create(const hmc_params *params, int32_t n_replicas, hmc_ha
 hmc_status hmc_select_replica(hmc_handle *h, int32_t r);
 
 /* Launch configuration chosen by the autotuner at the first MPM step (or the
- * default before it): MPM patch shape (0: 16x16 cells, 1: 32x8, 2: 8x32) and
- * the number of persistent MPM CTAs.  The autotuner times every candidate on
- * scratch copies of the nodal state; all candidates give bit-identical
- * results.  Environment variable HMC_AUTOTUNE=0 keeps the 16x16 default;
- * HMC_MPM_SHAPE=0|1|2 forces one shape. */
+ * default before it): MPM variant v (patch shape v % 3 -- 0: 16x16 cells,
+ * 1: 32x8, 2: 8x32 -- with, for v >= 3 (FP32 only), the Hooke product as
+ * paired FP32 FMAs) and the number of persistent MPM CTAs.  The autotuner
+ * times every candidate on scratch copies of the nodal state; all patch
+ * shapes of one Hooke variant give bit-identical results.  Environment
+ * variable HMC_AUTOTUNE=0 keeps variant 0; HMC_MPM_SHAPE=<v> forces one. */
 hmc_status hmc_get_tuning(hmc_handle *h, int32_t *mpm_shape, int32_t *mpm_grid);
 
 /* Release the handle and all its device memory (NULL is a no-op). */

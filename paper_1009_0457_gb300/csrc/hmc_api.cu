@@ -69,6 +69,7 @@ struct hmc_handle {
     void *v = nullptr;
     int cur = 0;
     void *sig = nullptr, *ctab = nullptr, *wtab = nullptr;
+    float *ctab_pairs = nullptr;          // FP32 MPM stiffness rows as component pairs
     unsigned long long *thr = nullptr, *counts = nullptr, *bins = nullptr;
     double *partials = nullptr, *fractions = nullptr;
     int32_t *binmap = nullptr;
@@ -216,6 +217,7 @@ hmc::MpmArgs<T> mpm_args(hmc_handle *h, const void *u_in, void *u_out, void *v) 
     a.u_out = static_cast<T *>(u_out);
     a.v = static_cast<T *>(v);
     a.ctab = static_cast<const T *>(h->ctab);
+    a.ctab_pairs = h->ctab_pairs;   // FP32 paired-FMA variants
     a.dt = (T)h->dt;
     a.dt_over_m = (T)(h->dt / 8.0);  // lumped mass rho * V * sum_p N_I(x_p) = 8 voxels
     a.keep = (T)(1.0 - h->damping);
@@ -387,7 +389,7 @@ void destroy_buffers(hmc_handle *h) {
     free_adjoint(h);
     for (int i = 0; i < 2; ++i)
         if (h->gexec[i]) cudaGraphExecDestroy(h->gexec[i]);
-    void *bufs[] = {h->spins, h->stage16, h->u[0], h->u[1], h->v, h->sig, h->ctab, h->wtab, h->thr, h->counts,
+    void *bufs[] = {h->spins, h->stage16, h->u[0], h->u[1], h->v, h->sig, h->ctab, h->ctab_pairs, h->wtab, h->thr, h->counts,
                     h->bins, h->partials, h->fractions, h->binmap, h->st, h->d_reps, h->d_cta_rep, h->d_sched};
     for (void *b : bufs)
         if (b) cudaFree(b);
@@ -429,7 +431,8 @@ void pack_stress_host(const RepHost &R, const double *in, std::vector<T> &packed
 
 // ---- MPM schedule and autotuner --------------------------------------------
 
-hmc_status upload_sched(hmc_handle *h, int shape) {
+hmc_status upload_sched(hmc_handle *h, int variant) {
+    const int shape = variant % hmc::MPM_NSHAPES;
     const int ox = hmc::mpm_shape_cx(shape) - 1, oy = hmc::mpm_shape_cy(shape) - 1;
     std::vector<hmc::MpmSched> sc(h->R + 1);
     long long off = 0;
@@ -476,9 +479,10 @@ hmc_status ensure_tuned(hmc_handle *h) {
     hmc_status s = HMC_OK;
     const char *env = std::getenv("HMC_AUTOTUNE");
     const bool enabled = !(env && env[0] == '0');
-    // HMC_MPM_SHAPE=0|1|2 forces a patch shape (with its default grid), bypassing the tuner
+    // HMC_MPM_SHAPE=<variant> forces an MPM variant (with its default grid), bypassing the tuner
     const char *forced = std::getenv("HMC_MPM_SHAPE");
-    if (forced && forced[0] >= '0' && forced[0] < '0' + hmc::MPM_NSHAPES && forced[1] == 0) {
+    const int nvar = h->p.precision == HMC_FP32 ? 2 * hmc::MPM_NSHAPES : hmc::MPM_NSHAPES;
+    if (forced && forced[0] >= '0' && forced[0] < '0' + nvar && forced[1] == 0) {
         const int shape = forced[0] - '0';
         if ((s = upload_sched(h, shape)) != HMC_OK) return s;
         h->mpm_shape = shape;
@@ -514,7 +518,8 @@ hmc_status ensure_tuned(hmc_handle *h) {
         cudaEventCreate(&e1);
         float best = 1e30f;
         cudaError_t err = cudaMemcpyAsync(vs, h->v, nb, cudaMemcpyDeviceToDevice, h->stream);
-        for (int shape = 0; shape < hmc::MPM_NSHAPES && err == cudaSuccess && s == HMC_OK; ++shape) {
+        const int nvariants = h->p.precision == HMC_FP32 ? 2 * hmc::MPM_NSHAPES : hmc::MPM_NSHAPES;
+        for (int shape = 0; shape < nvariants && err == cudaSuccess && s == HMC_OK; ++shape) {
             if ((s = upload_sched(h, shape)) != HMC_OK) break;
             for (int lim : {0, 1}) {
                 const int grid = grid_for_shape(h, shape, lim);
@@ -710,6 +715,7 @@ hmc_status hmc_batch_create(const hmc_params *params, int32_t n_replicas, hmc_ha
         {&h->u[0], nodes_b, "u0"}, {&h->u[1], nodes_b, "u1"}, {&h->v, nodes_b, "v"},
         {&h->sig, h->tsize * 48 * (size_t)h->nblk_total, "stress"},
         {&h->ctab, h->tsize * 24 * (size_t)p->n_orient, "stiffness table"},
+        {(void **)&h->ctab_pairs, sizeof(float) * 36 * (size_t)p->n_orient, "stiffness pair table"},
         {&h->wtab, h->tsize * 20 * (size_t)p->n_orient, "zone table"},
         {(void **)&h->thr, sizeof(unsigned long long) * 8, "threshold table"},
         {(void **)&h->counts, sizeof(unsigned long long) * (size_t)p->n_orient, "orientation counts"},
@@ -863,6 +869,15 @@ hmc_status hmc_set_orientations(hmc_handle *h, const double *euler, const uint16
         auto w = pack_wtab<float>(h->A, Q);
         HMC_CK(h, cudaMemcpy(h->ctab, c.data(), c.size() * sizeof(float), cudaMemcpyHostToDevice), "table upload");
         HMC_CK(h, cudaMemcpy(h->wtab, w.data(), w.size() * sizeof(float), cudaMemcpyHostToDevice), "table upload");
+        std::vector<float> cp((size_t)Q * 36);
+        for (int q = 0; q < Q; ++q)
+            for (int k = 0; k < 3; ++k)
+                for (int j = 0; j < 6; ++j) {
+                    cp[(size_t)q * 36 + 12 * k + 2 * j] = (float)h->Cv[(size_t)q * 36 + 6 * (2 * k) + j];
+                    cp[(size_t)q * 36 + 12 * k + 2 * j + 1] = (float)h->Cv[(size_t)q * 36 + 6 * (2 * k + 1) + j];
+                }
+        HMC_CK(h, cudaMemcpy(h->ctab_pairs, cp.data(), cp.size() * sizeof(float), cudaMemcpyHostToDevice),
+               "table upload");
     } else {
         auto c = pack_ctab<double>(h->Cv, Q);
         auto w = pack_wtab<double>(h->A, Q);

@@ -77,6 +77,7 @@ struct MpmArgs {
     T *u_out;
     T *v;
     const T *ctab;
+    const float *ctab_pairs; // FP32 stiffness rows as component pairs (paired-FMA variant)
     T dt, dt_over_m, keep;   // keep = 1 - damping
     int grid;                // persistent CTAs
 };
@@ -106,7 +107,9 @@ struct SweepArgs {
     int nctas;
 };
 
-// MPM patch shapes (cells per patch edge; owned nodes = cells - 1).
+// MPM patch shapes (cells per patch edge; owned nodes = cells - 1).  A variant
+// index v in [0, 2 * MPM_NSHAPES) selects shape v % MPM_NSHAPES; v >= MPM_NSHAPES
+// selects the paired-FMA Hooke product (FP32 only).
 enum MpmShape { MPM_16x16 = 0, MPM_32x8 = 1, MPM_8x32 = 2, MPM_NSHAPES = 3 };
 int mpm_shape_cx(int shape);
 int mpm_shape_cy(int shape);
@@ -120,7 +123,7 @@ template <typename T>
 cudaError_t launch_sweep(const SweepArgs<T> &a, int colour, bool elastic, cudaStream_t s);
 cudaError_t mpm_prepare();  // opt the MPM kernels into their dynamic shared memory (once, before any capture)
 template <typename T>
-int mpm_per_sm(int shape);  // resident MPM CTAs per SM
+int mpm_per_sm(int variant);  // resident MPM CTAs per SM
 
 // One CTA per replica: fixed-order FP64 sum of its stress partials, loading
 // update (update_strain) and MCS counter (advance).

@@ -81,6 +81,41 @@ struct PlaneLoad {
     }
 };
 
+// Hooke's law for the MPM step.  FP64: the 21-entry symmetric row.  FP32: the
+// full 6x6 matrix stored as row pairs ((C0j,C1j), (C2j,C3j), (C4j,C5j)), so
+// that each pair of stress components is one chain of paired FMAs
+// (__ffma2_rn: two FP32 FMAs per instruction on sm_100 and later).
+template <typename T, bool PAIR>
+struct HookeRow {
+    Row24<T> r;
+    __device__ __forceinline__ void load(const T *tab, const float *, uint32_t q) { r.load(tab + 24ll * q); }
+    __device__ __forceinline__ void apply(const T (&e)[6], T (&s)[6]) const { hooke21<T>(r.v, e, s); }
+};
+template <>
+struct HookeRow<float, true> {
+    float2 p[3][6];   // p[k][j] = (C_{2k,j}, C_{2k+1,j})
+    __device__ __forceinline__ void load(const float *, const float *pairs, uint32_t q) {
+        const float4 *t = reinterpret_cast<const float4 *>(pairs + 36ll * q);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const float4 v = __ldg(t + i);
+            const int k = (2 * i) / 6, j = (2 * i) % 6;
+            p[k][j] = make_float2(v.x, v.y);
+            p[k][j + 1] = make_float2(v.z, v.w);
+        }
+    }
+    __device__ __forceinline__ void apply(const float (&e)[6], float (&s)[6]) const {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            float2 acc = __fmul2_rn(p[k][0], make_float2(e[0], e[0]));
+#pragma unroll
+            for (int j = 1; j < 6; ++j) acc = __ffma2_rn(p[k][j], make_float2(e[j], e[j]), acc);
+            s[2 * k] = acc.x;
+            s[2 * k + 1] = acc.y;
+        }
+    }
+};
+
 // 2x2 -> 2x2 transform with weights 3 (same side) and 1 (other side) in both
 // indices: o[b][c] = sum_J sum_K W(J,b) W(K,c) d[J][K], eight FMAs.
 template <typename T>
@@ -124,9 +159,9 @@ __device__ __forceinline__ void cell_gradients31(const T (&u)[8][3], CellGrad<T>
 // Eight points of one cell: F[corner] = (2I-1) X'[J][K] + (2J-1) Y'[I][K] +
 // (2K-1) Z'[I][J] with X', Y', Z' the 3/1-weighted sums of the traction
 // columns of sigma; the nodal force is -(V/h)/16 F = -F/32 (V = 1 voxel, h = 2).
-template <typename T>
+template <typename T, bool PAIR>
 __device__ __forceinline__ void cell_forces(const T (&u)[8][3], const uint4 &sp, const T *__restrict__ ctab,
-                                            const T (&eb)[6], T (&f)[8][3]) {
+                                            const float *__restrict__ cpairs, const T (&eb)[6], T (&f)[8][3]) {
     CellGrad<T> g;
     cell_gradients31<T>(u, g);
     T tx[2][2][3], ty[2][2][3], tz[2][2][3];  // traction sums over a, b, c respectively
@@ -136,7 +171,7 @@ __device__ __forceinline__ void cell_forces(const T (&u)[8][3], const uint4 &sp,
         for (int j = 0; j < 2; ++j)
 #pragma unroll
             for (int d = 0; d < 3; ++d) tx[i][j][d] = ty[i][j][d] = tz[i][j][d] = T(0);
-    Row24<T> row;
+    HookeRow<T, PAIR> row;
     uint32_t qprev = 0xffffffffu;
 #pragma unroll
     for (int L = 0; L < 8; ++L) {
@@ -146,10 +181,10 @@ __device__ __forceinline__ void cell_forces(const T (&u)[8][3], const uint4 &sp,
         // points of one cell mostly share one orientation: fetch the row only when it changes
         const uint32_t q = spin_of(sp, local_slot(L));
         if (q != qprev) {
-            row.load(ctab + 24ll * q);
+            row.load(ctab, cpairs, q);
             qprev = q;
         }
-        hooke21<T>(row.v, e, s);
+        row.apply(e, s);
         // columns of sigma: x = (s0,s5,s4), y = (s5,s1,s3), z = (s4,s3,s2)
         tx[b][c][0] += s[0]; tx[b][c][1] += s[5]; tx[b][c][2] += s[4];
         ty[a][c][0] += s[5]; ty[a][c][1] += s[1]; ty[a][c][2] += s[3];
@@ -175,7 +210,7 @@ __device__ __forceinline__ void cell_forces(const T (&u)[8][3], const uint4 &sp,
     }
 }
 
-template <typename T, int CX, int CY>
+template <typename T, int CX, int CY, bool PAIR>
 __global__ void __launch_bounds__(CX *CY, (sizeof(T) == 4 ? 2 : 1)) k_mpm_step(MpmArgs<T> a) {
     constexpr int OX = CX - 1, OY = CY - 1;
     using Smem = typename MpmSmem<CX, CY>::template S<T>;
@@ -243,7 +278,7 @@ __global__ void __launch_bounds__(CX *CY, (sizeof(T) == 4 ? 2 : 1)) k_mpm_step(M
 #pragma unroll
                             for (int d = 0; d < 3; ++d) u[corner(I, J, K)][d] = sm.us[K ? b1 : b0][d][lcj + J][lci + I];
                 T f[8][3];
-                cell_forces<T>(u, sp, a.ctab, eb, f);
+                cell_forces<T, PAIR>(u, sp, a.ctab, a.ctab_pairs, eb, f);
 #pragma unroll
                 for (int J = 0; J < 2; ++J)
 #pragma unroll
@@ -293,51 +328,70 @@ size_t smem_of() {
 int mpm_shape_cx(int shape) { return shape == MPM_32x8 ? 32 : shape == MPM_8x32 ? 8 : 16; }
 int mpm_shape_cy(int shape) { return shape == MPM_32x8 ? 8 : shape == MPM_8x32 ? 32 : 16; }
 
-template <typename T>
-static cudaError_t prepare_t() {
-    cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_mpm_step<T, 16, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem_of<T, 16, 16>())) != cudaSuccess)
-        return e;
-    if ((e = cudaFuncSetAttribute(k_mpm_step<T, 32, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem_of<T, 32, 8>())) != cudaSuccess)
-        return e;
-    return cudaFuncSetAttribute(k_mpm_step<T, 8, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem_of<T, 8, 32>());
+template <typename T, int CX, int CY, bool PAIR>
+static cudaError_t set_attr() {
+    return cudaFuncSetAttribute(k_mpm_step<T, CX, CY, PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem_of<T, CX, CY>());
 }
 
 cudaError_t mpm_prepare() {
-    cudaError_t e = prepare_t<float>();
-    return e != cudaSuccess ? e : prepare_t<double>();
+    cudaError_t e;
+    if ((e = set_attr<float, 16, 16, false>()) != cudaSuccess || (e = set_attr<float, 32, 8, false>()) != cudaSuccess ||
+        (e = set_attr<float, 8, 32, false>()) != cudaSuccess || (e = set_attr<float, 16, 16, true>()) != cudaSuccess ||
+        (e = set_attr<float, 32, 8, true>()) != cudaSuccess || (e = set_attr<float, 8, 32, true>()) != cudaSuccess ||
+        (e = set_attr<double, 16, 16, false>()) != cudaSuccess ||
+        (e = set_attr<double, 32, 8, false>()) != cudaSuccess || (e = set_attr<double, 8, 32, false>()) != cudaSuccess)
+        return e;
+    return cudaSuccess;
 }
 
-template <typename T>
-int mpm_per_sm(int shape) {
+template <typename T, bool PAIR>
+static int per_sm_t(int shape) {
     int n = 1;
     cudaError_t e;
     if (shape == MPM_32x8)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_mpm_step<T, 32, 8>, 256, smem_of<T, 32, 8>());
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_mpm_step<T, 32, 8, PAIR>, 256, smem_of<T, 32, 8>());
     else if (shape == MPM_8x32)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_mpm_step<T, 8, 32>, 256, smem_of<T, 8, 32>());
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_mpm_step<T, 8, 32, PAIR>, 256, smem_of<T, 8, 32>());
     else
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_mpm_step<T, 16, 16>, 256, smem_of<T, 16, 16>());
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_mpm_step<T, 16, 16, PAIR>, 256, smem_of<T, 16, 16>());
     return (e != cudaSuccess || n < 1) ? 1 : n;
 }
-template int mpm_per_sm<float>(int);
-template int mpm_per_sm<double>(int);
 
-template <typename T>
-cudaError_t launch_mpm_step(const MpmArgs<T> &a, int shape, cudaStream_t s) {
-    if (shape == MPM_32x8)
-        k_mpm_step<T, 32, 8><<<a.grid, 256, smem_of<T, 32, 8>(), s>>>(a);
-    else if (shape == MPM_8x32)
-        k_mpm_step<T, 8, 32><<<a.grid, 256, smem_of<T, 8, 32>(), s>>>(a);
-    else
-        k_mpm_step<T, 16, 16><<<a.grid, 256, smem_of<T, 16, 16>(), s>>>(a);
-    return cudaGetLastError();
+template <>
+int mpm_per_sm<float>(int shape) {
+    return per_sm_t<float, false>(shape % MPM_NSHAPES) < per_sm_t<float, true>(shape % MPM_NSHAPES)
+               ? per_sm_t<float, false>(shape % MPM_NSHAPES)
+               : per_sm_t<float, true>(shape % MPM_NSHAPES);
+}
+template <>
+int mpm_per_sm<double>(int shape) {
+    return per_sm_t<double, false>(shape % MPM_NSHAPES);
 }
 
-template cudaError_t launch_mpm_step<float>(const MpmArgs<float> &, int, cudaStream_t);
-template cudaError_t launch_mpm_step<double>(const MpmArgs<double> &, int, cudaStream_t);
+template <typename T, bool PAIR>
+static void launch_t(const MpmArgs<T> &a, int shape, cudaStream_t s) {
+    if (shape == MPM_32x8)
+        k_mpm_step<T, 32, 8, PAIR><<<a.grid, 256, smem_of<T, 32, 8>(), s>>>(a);
+    else if (shape == MPM_8x32)
+        k_mpm_step<T, 8, 32, PAIR><<<a.grid, 256, smem_of<T, 8, 32>(), s>>>(a);
+    else
+        k_mpm_step<T, 16, 16, PAIR><<<a.grid, 256, smem_of<T, 16, 16>(), s>>>(a);
+}
+
+// shape in 0..2: scalar Hooke; shape + MPM_NSHAPES: paired-FMA Hooke (FP32 only)
+template <>
+cudaError_t launch_mpm_step<float>(const MpmArgs<float> &a, int shape, cudaStream_t s) {
+    if (shape >= MPM_NSHAPES)
+        launch_t<float, true>(a, shape - MPM_NSHAPES, s);
+    else
+        launch_t<float, false>(a, shape, s);
+    return cudaGetLastError();
+}
+template <>
+cudaError_t launch_mpm_step<double>(const MpmArgs<double> &a, int shape, cudaStream_t s) {
+    launch_t<double, false>(a, shape % MPM_NSHAPES, s);
+    return cudaGetLastError();
+}
 
 }  // namespace hmc

@@ -54,7 +54,8 @@ def test_batch_replicas_equal_solo_runs(G, precision):
     b.close()
 
 
-def test_patch_shapes_are_bitwise_equal(G):
+@pytest.mark.parametrize("variants", [("0", "1", "2"), ("3", "4", "5")])
+def test_patch_shapes_are_bitwise_equal(G, variants):
     shape = (10, 40, 50)
     eul = S.euler_uniform_so3(9, 2)
     sp = S.voronoi_spins(shape, 20, 9, 4)
@@ -63,7 +64,7 @@ def test_patch_shapes_are_bitwise_equal(G):
     out = []
     old = os.environ.get("HMC_MPM_SHAPE")
     try:
-        for shp in ("0", "1", "2"):
+        for shp in variants:
             os.environ["HMC_MPM_SHAPE"] = shp
             g = G.HMC(shape, 9, load_axis=(1, 2, 3.0), strain=2e-3, **C3)
             g.set_orientations(eul, sp)
@@ -96,3 +97,28 @@ def test_batch_mpm_matches_oracle_fp64(G):
         u = b.nodal(i)[0]
         assert np.linalg.norm(u - o.u) < 1e-12 * np.linalg.norm(o.u)
     b.close()
+
+
+def test_paired_hooke_close_to_scalar(G):
+    shape = (10, 40, 50)
+    eul = S.euler_uniform_so3(9, 2)
+    sp = S.voronoi_spins(shape, 20, 9, 4)
+    rng = np.random.default_rng(3)
+    u0 = rng.normal(size=(np.prod(shape) // 8, 3)) * 1e-3
+    out = []
+    old = os.environ.get("HMC_MPM_SHAPE")
+    try:
+        for shp in ("0", "3"):
+            os.environ["HMC_MPM_SHAPE"] = shp
+            g = G.HMC(shape, 9, load_axis=(1, 2, 3.0), strain=2e-3, **C3)
+            g.set_orientations(eul, sp)
+            g.set_nodal(u0, None)
+            g.mpm_steps(15)
+            out.append(g.nodal()[0])
+            g.close()
+    finally:
+        if old is None:
+            os.environ.pop("HMC_MPM_SHAPE", None)
+        else:
+            os.environ["HMC_MPM_SHAPE"] = old
+    assert np.linalg.norm(out[1] - out[0]) < 1e-6 * np.linalg.norm(out[0] - u0)
