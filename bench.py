@@ -145,6 +145,19 @@ def mpm_variant_name(v):
     return ["16x16", "32x8", "8x32"][v % 3] + (" paired-FMA Hooke" if v >= 3 else "")
 
 
+def dist_reduce(t_local, units_local, device="cpu"):
+    """(max time over ranks, total work units over ranks); identity without a process group."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return float(t_local), float(units_local)
+    x = torch.tensor([float(t_local)], dtype=torch.float64, device=device)
+    y = torch.tensor([float(units_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(x, op=dist.ReduceOp.MAX)
+    dist.all_reduce(y, op=dist.ReduceOp.SUM)
+    return float(x.item()), float(y.item())
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -240,12 +253,7 @@ def run_ours(args):
             dist.barrier()
 
     def tmax(t):
-        if ws > 1:
-            import torch.distributed as dist
-            x = torch.tensor([t], device="cuda", dtype=torch.float64)
-            dist.all_reduce(x, op=dist.ReduceOp.MAX)
-            return float(x.item())
-        return t
+        return dist_reduce(t, 0, "cuda")[0]
 
     def timed(fn):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -274,8 +282,8 @@ def run_ours(args):
     clk = clocks.stop()
     assert st == 0, G.hmc_last_error(h.h)
     t_local = e0.elapsed_time(e1) / 1e3
-    t = tmax(t_local)
-    value = N * args.steps * ws / t
+    t, units = dist_reduce(t_local, N * args.steps, "cuda")
+    value = units / t
     launches = args.steps * (spec["mpm_steps"] + 4)
 
     # ---- per-kernel timing on the same stream (roofline) ----------------------

@@ -27,7 +27,14 @@
  *  - Every call returns an hmc_status; no C++ exception crosses the ABI.  A
  *    failed call leaves the handle valid; hmc_last_error() describes the
  *    failure.  CUDA errors map to HMC_ERR_CUDA, allocation failures to
- *    HMC_ERR_OOM, calls before hmc_set_orientations to HMC_ERR_STATE.
+ *    HMC_ERR_OOM, calls before hmc_set_orientations to HMC_ERR_STATE; a
+ *    non-finite FP64 reduction (mean stress, energy) sets a per-replica flag
+ *    reported as HMC_ERR_NONFINITE by the calls that read statistics or the
+ *    accepted count, until hmc_set_nodal / hmc_set_state load a new state.
+ *  - Host-side fault injection for tests (environment variable HMC_FAULT):
+ *    "alloc" fails handle creation before any CUDA call, "launch" fails
+ *    hmc_mpm_steps / hmc_mc_sweeps before anything is enqueued, "nan" writes a
+ *    NaN into the first nodal displacement before the next stress pass.
  */
 #ifndef HMC_H_
 #define HMC_H_

@@ -126,6 +126,16 @@ hmc_status cuda_fail(hmc_handle *h, cudaError_t e, const char *what) {
         if (e_ != cudaSuccess) return cuda_fail(h, e_, what); \
     } while (0)
 
+// Host-side fault injection for tests of the failure paths (no GPU fault is
+// ever produced): HMC_FAULT=alloc fails the next handle creation before any
+// CUDA call, =launch fails the next MPM / Monte Carlo launch sequence before it
+// is enqueued, =nan writes a NaN into the first nodal displacement before the
+// next stress pass, so the FP64 reductions report HMC_ERR_NONFINITE.
+bool fault(const char *what) {
+    const char *f = std::getenv("HMC_FAULT");
+    return f && std::strcmp(f, what) == 0;
+}
+
 RepHost &selr(hmc_handle *h) { return h->reps[h->sel]; }
 DevState *sel_st(hmc_handle *h) { return h->st + h->sel; }
 size_t node_bytes(const hmc_handle *h) { return h->tsize * 3 * (size_t)h->nblk_total; }
@@ -293,10 +303,16 @@ hmc_status read_accepted(hmc_handle *h, int64_t *acc) {
     HMC_CK(h, cudaMemcpy2DAsync(a.data(), sizeof(unsigned long long), &h->st->accepted, sizeof(DevState),
                                 sizeof(unsigned long long), h->R, cudaMemcpyDeviceToHost, h->stream),
            "download");
+    std::vector<int32_t> bad(h->R);
+    HMC_CK(h, cudaMemcpy2DAsync(bad.data(), sizeof(int32_t), &h->st->nonfinite, sizeof(DevState), sizeof(int32_t),
+                                h->R, cudaMemcpyDeviceToHost, h->stream),
+           "download");
     HMC_CK(h, cudaStreamSynchronize(h->stream), "sync");
     int64_t s = 0;
     for (auto x : a) s += (int64_t)x;
     *acc = s;
+    for (int r = 0; r < h->R; ++r)
+        if (bad[r]) return fail(h, HMC_ERR_NONFINITE, "non-finite stress or energy in replica " + std::to_string(r));
     return HMC_OK;
 }
 
@@ -639,6 +655,7 @@ hmc_status hmc_batch_create(const hmc_params *params, int32_t n_replicas, hmc_ha
     if (!out) return fail(nullptr, HMC_ERR_ARG, "out is NULL");
     *out = nullptr;
     if (!params || n_replicas < 1) return fail(nullptr, HMC_ERR_ARG, "need params for at least one replica");
+    if (fault("alloc")) return fail(nullptr, HMC_ERR_OOM, "injected allocation failure (HMC_FAULT=alloc)");
     for (int r = 0; r < n_replicas; ++r) {
         std::string msg = validate(params + r);
         if (msg.empty() && r > 0) msg = validate_shared(params, params + r);
@@ -928,6 +945,12 @@ hmc_status hmc_get_spins(hmc_handle *h, uint16_t *spins) {
 hmc_status hmc_compute_stress(hmc_handle *h, double *mean, double *energy) {
     hmc_status s = need_oriented(h);
     if (s != HMC_OK) return s;
+    if (fault("nan")) {
+        HMC_CK(h, cudaMemsetAsync(static_cast<char *>(h->u[h->cur]) + h->tsize * 3 * (size_t)selr(h).blk_off, 0xff,
+                                  h->tsize, h->stream),
+               "fault injection");
+        ++h->state_version;
+    }
     HMC_CK(h, enq_stress(h, h->stream), "stress launch");
     HMC_CK(h, hmc::launch_end_mcs(h->d_reps, h->R, h->partials, 0, 0, h->stream), "reduction launch");
     if (mean || energy) return read_stats(h, mean, energy);
@@ -939,6 +962,7 @@ hmc_status hmc_mpm_steps(hmc_handle *h, int32_t nsteps, double *energy) {
     hmc_status s = need_oriented(h);
     if (s != HMC_OK) return s;
     if (nsteps < 0) return fail(h, HMC_ERR_ARG, "nsteps < 0");
+    if (fault("launch")) return fail(h, HMC_ERR_CUDA, "injected launch failure (HMC_FAULT=launch)");
     if (nsteps > 0 && (s = ensure_tuned(h)) != HMC_OK) return s;
     for (int k = 0; k < nsteps; ++k) HMC_CK(h, enq_mpm(h, h->stream), "MPM launch");
     if (energy) return hmc_compute_stress(h, nullptr, energy);
@@ -969,6 +993,7 @@ hmc_status hmc_mc_sweeps(hmc_handle *h, int32_t n_mcs, int64_t *accepted) {
     hmc_status s = need_oriented(h);
     if (s != HMC_OK) return s;
     if (n_mcs < 0) return fail(h, HMC_ERR_ARG, "n_mcs < 0");
+    if (fault("launch")) return fail(h, HMC_ERR_CUDA, "injected launch failure (HMC_FAULT=launch)");
     if (n_mcs > 0 && h->p.mpm_steps_per_mcs > 0 && (s = ensure_tuned(h)) != HMC_OK) return s;
     HMC_CK(h, reset_accepted(h), "memset");
     for (int m = 0; m < n_mcs; ++m) {
@@ -1151,6 +1176,9 @@ hmc_status hmc_set_nodal(hmc_handle *h, const double *u, const double *v) {
                 if (!std::isfinite(a[i])) return fail(h, HMC_ERR_ARG, "non-finite nodal value");
     if (u && (s = nodal_io(h, h->u[h->cur], const_cast<double *>(u), false)) != HMC_OK) return s;
     if (v && (s = nodal_io(h, h->v, const_cast<double *>(v), false)) != HMC_OK) return s;
+    // a finite nodal state clears the replica's non-finite flag
+    HMC_CK(h, cudaMemsetAsync(&sel_st(h)->nonfinite, 0, sizeof(int32_t), h->stream), "memset");
+    HMC_CK(h, cudaStreamSynchronize(h->stream), "sync");
     return HMC_OK;
 }
 

@@ -34,12 +34,18 @@ namespace hmc {
 
 namespace {
 
+// Row stride of the node tiles in shared memory: a warp covers 32 / CX rows of
+// the patch, and the stride puts those rows in disjoint banks (16 wide: 48,
+// 8 wide: 40, 32 wide: 33).
+__host__ __device__ constexpr int node_stride(int cx) { return cx == 16 ? 48 : cx == 8 ? 40 : cx + 1; }
+
 template <int CX, int CY>
 struct MpmSmem {
     static constexpr int NX = CX + 1, NY = CY + 1;   // node tile (one node of halo each side)
+    static constexpr int NXP = node_stride(CX);
     template <typename T>
     struct S {
-        T us[3][3][NY][NX];   // node planes (buffer, component, j, i), held as u/32
+        T us[3][3][NY][NXP];  // node planes (buffer, component, j, i), held as u/32
         T fb[4][3][CY][CX];   // cell contributions to their lower corner nodes (corner I+2J, component)
         T ft[4][3][CY][CX];   // ... to their upper corner nodes
     };
@@ -68,7 +74,7 @@ struct PlaneLoad {
             }
         }
     }
-    __device__ __forceinline__ void store(T (&us)[3][NY][NX]) const {
+    __device__ __forceinline__ void store(T (&us)[3][NY][node_stride(CX)]) const {
 #pragma unroll
         for (int m = 0; m < PER; ++m) {
             const int t = threadIdx.x + m * NTHR;
