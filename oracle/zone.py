@@ -140,3 +140,68 @@ def zone_shift(spins, Ct, Ebar, u0, p, q_new, r, Bs=None):
     u1[dofs] = du
     W_new = energy(Bs, Cp2, Ebar, u1, pts) - g @ u1
     return W_new - W_old
+
+
+# ---------------------------------------------------------------------------
+# Red/black half sweep with the zone energy of Eq. 6 (zone half-width r)
+# ---------------------------------------------------------------------------
+
+def site_trial_zone(spins, x, y, z, seed, mcs, replica, J, kT, trial, Q, lam, Ct, Ebar, u0, r, Bs):
+    """One Metropolis trial (Eq. 5) at voxel (x, y, z): the trial orientation
+    and the bond-energy change as in the one-point sweep (Philox counter
+    (site, mcs, replica, 0), neighbour order -x,+x,-y,+y,-z,+z), the elastic
+    term lam * zone_shift over the zone of half-width r about the current
+    displacement u0.  Returns (accepted, q_new, dH, threshold)."""
+    from . import TRIAL_NEIGHBOR, accept_threshold, philox4x32_10
+    nz, ny, nx = spins.shape
+    p = x + nx * (y + ny * z)
+    w = philox4x32_10([p, mcs, replica, 0], [seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF])
+    nb = [int(spins[z, y, (x - 1) % nx]), int(spins[z, y, (x + 1) % nx]),
+          int(spins[z, (y - 1) % ny, x]), int(spins[z, (y + 1) % ny, x]),
+          int(spins[(z - 1) % nz, y, x]), int(spins[(z + 1) % nz, y, x])]
+    q = int(spins[z, y, x])
+    if trial == TRIAL_NEIGHBOR:
+        qn = nb[(int(w[0]) * 6) >> 32]
+    else:
+        qn = (int(w[0]) * int(Q)) >> 32
+    if qn == q:
+        return False, qn, 0.0, -1.0
+    dE = sum(1 for v in nb if v == q) - sum(1 for v in nb if v == qn)
+    dHe = lam * zone_shift(spins, Ct, Ebar, u0, p, qn, r, Bs)
+    if dHe == 0.0:
+        return (dE <= 0 or float(w[1]) < accept_threshold(dE, J, kT)), qn, J * dE, -1.0
+    H = J * dE + dHe
+    t = -kT * np.log((float(w[1]) + 0.5) / 4294967296.0) if kT > 0 else 0.0
+    return bool(H <= t), qn, H, t
+
+
+def half_sweep_zone(spins, colour, seed, mcs, replica, J, kT, trial, Q, lam, Ct, Ebar, u0, r, Bs=None):
+    """Red/black half step (Sec. "Microstructural Evolution") with the zone
+    energy: every site of one colour ((x+y+z) even = red = 0) is tried against
+    the orientations at the start of the half step, then the accepted trials
+    are applied together.  A zone of half-width r >= 1 contains sites of the
+    same colour, so the trials read the start-of-step copy.  In place; returns
+    (accepted, changed[N] u8, dH[N], thresh[N]) in natural site order."""
+    nz, ny, nx = spins.shape
+    Bs = all_strain_matrices(spins.shape) if Bs is None else Bs
+    start = spins.copy()
+    N = nx * ny * nz
+    changed = np.zeros(N, dtype=np.uint8)
+    dH = np.zeros(N)
+    thr = np.zeros(N)
+    flips = []
+    for z in range(nz):
+        for y in range(ny):
+            for x in range(nx):
+                if ((x + y + z) & 1) != colour:
+                    continue
+                p = x + nx * (y + ny * z)
+                acc, qn, h, t = site_trial_zone(start, x, y, z, seed, mcs, replica, J, kT, trial, Q, lam,
+                                                Ct, Ebar, u0, r, Bs)
+                dH[p], thr[p] = h, t
+                if acc:
+                    changed[p] = 1
+                    flips.append((z, y, x, qn))
+    for z, y, x, qn in flips:
+        spins[z, y, x] = qn
+    return len(flips), changed, dH, thr
