@@ -63,9 +63,19 @@ typedef enum {
  * Monte Carlo step (traction-free sides of a periodic cell).  STRAIN6: all six
  * mean strain components are prescribed by `strain6`. */
 enum { HMC_BC_UNIAXIAL = 0, HMC_BC_STRAIN6 = 1 };
-/* Elastic term of the trial energy: off (pure Potts) or the one-point
- * constant-traction zone shift w(q_old) - w(q_new), w(q) = 1/2 s.S'(q).s. */
-enum { HMC_ELASTIC_OFF = 0, HMC_ELASTIC_TRACTION = 1 };
+/* Elastic term of the trial energy: off (pure Potts); the one-point
+ * constant-traction zone shift w(q_old) - w(q_new), w(q) = 1/2 s.S'(q).s
+ * (Eqs. 6-8), from the stress of the last stress pass; or the zone of the 27
+ * points around the site (Eq. 6 over a zone of half-width one point, the larger
+ * zone proposed in Sec. "Conclusions"): the zone is re-equilibrated with the
+ * forces of the rest of the body on its nodes held at their current values, and
+ * the shift is the change of its minimum potential energy,
+ * 1/2 e0.dC (I + G dC)^-1 e0 with e0 the site's strain from the current nodal
+ * displacement and mean strain, dC = C'(q_new) - C'(q_old), G the compliance of
+ * the zone seen at the site.  ZONE1 evaluates every trial against the spins as
+ * they were at the start of the half step (the zone holds sites of the sweep's
+ * own colour) and needs nx, ny, nz >= 6; it does not read the stored stress. */
+enum { HMC_ELASTIC_OFF = 0, HMC_ELASTIC_TRACTION = 1, HMC_ELASTIC_ZONE1 = 2 };
 /* Trial orientation: copy a random one of the six neighbours, or draw
  * uniformly from 0..Q-1. */
 enum { HMC_TRIAL_NEIGHBOR = 0, HMC_TRIAL_UNIFORM_Q = 1 };
@@ -206,6 +216,15 @@ hmc_status hmc_mc_sweeps(hmc_handle *h, int32_t n_mcs, int64_t *accepted);
  * between the <100> and <111> moduli.  Counts are int64, fractions FP64. */
 hmc_status hmc_texture_histogram(hmc_handle *h, int32_t kind, int32_t nbins, double *fractions,
                                  int64_t *counts_per_q);
+
+/* Grain count of the selected replica (Sec. "Microstructural Evolution": a
+ * grain's volume is the number of grid sites it holds; the mean grain volume
+ * of the grain-growth law V^(3/2) = c2 t is N / *n_grains).  A grain is a set of
+ * sites of one orientation connected through face neighbours on the periodic
+ * lattice.  Synchronous; union-find on the device in a buffer of 4 bytes per
+ * site of the largest replica, allocated by the first call.  HMC_ERR_TIMEOUT if
+ * a union-find loop reached its iteration cap (no result). */
+hmc_status hmc_grain_count(hmc_handle *h, int64_t *n_grains);
 
 /* Statistics of the current state: number of unlike nearest-neighbour bonds
  * (each counted once, int64; the bond energy is J times it), elastic energy and

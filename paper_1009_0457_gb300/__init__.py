@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libhmc.so")
 
 HMC_OK, HMC_ERR_ARG, HMC_ERR_CUDA, HMC_ERR_OOM, HMC_ERR_STATE, HMC_ERR_NONFINITE, HMC_ERR_TIMEOUT = 0, -1, -2, -3, -4, -5, -6
 HMC_BC_UNIAXIAL, HMC_BC_STRAIN6 = 0, 1
-HMC_ELASTIC_OFF, HMC_ELASTIC_TRACTION = 0, 1
+HMC_ELASTIC_OFF, HMC_ELASTIC_TRACTION, HMC_ELASTIC_ZONE1 = 0, 1, 2
 HMC_TRIAL_NEIGHBOR, HMC_TRIAL_UNIFORM_Q = 0, 1
 HMC_FP64, HMC_FP32 = 0, 1
 HMC_HIST_PER_Q, HMC_HIST_ANGLE_100, HMC_HIST_YOUNG = 0, 1, 2
@@ -87,6 +87,7 @@ def _load():
         "hmc_mc_sweeps": (st, [H, C.c_int32, i64p]),
         "hmc_texture_histogram": (st, [H, C.c_int32, C.c_int32, dp, i64p]),
         "hmc_energy": (st, [H, i64p, dp, dp]),
+        "hmc_grain_count": (st, [H, i64p]),
         "hmc_get_stress": (st, [H, dp]),
         "hmc_set_stress": (st, [H, dp]),
         "hmc_get_nodal": (st, [H, dp, dp]),
@@ -223,6 +224,12 @@ def hmc_energy(h):
     m = np.zeros(6)
     _check(h, lib.hmc_energy(h, _ptr(u, C.c_int64), _ptr(e, C.c_double), _ptr(m, C.c_double)))
     return int(u[0]), float(e[0]), m
+
+
+def hmc_grain_count(h):
+    n = np.zeros(1, dtype=np.int64)
+    _check(h, lib.hmc_grain_count(h, _ptr(n, C.c_int64)))
+    return int(n[0])
 
 
 def hmc_get_stress(h, n_sites):
@@ -377,6 +384,9 @@ class HMC:
 
     def energy(self):
         return hmc_energy(self.h)
+
+    def grain_count(self):
+        return hmc_grain_count(self.h)
 
     def stress(self):
         return hmc_get_stress(self.h, self.n_sites)

@@ -70,6 +70,15 @@ struct hmc_handle {
     int cur = 0;
     void *sig = nullptr, *ctab = nullptr, *wtab = nullptr;
     float *ctab_pairs = nullptr;          // FP32 MPM stiffness rows as component pairs
+    // 27-point zone (HMC_ELASTIC_ZONE1): trial list, start-of-step spins, element tables, schedule
+    uint4 *zone_work = nullptr, *snap = nullptr;
+    unsigned *zone_count = nullptr;
+    void *ktab = nullptr;
+    uint16_t *zone_sched = nullptr;
+    int zone_nsched = 0, zone_grid = 1;
+    // grain count: union-find parents of the largest replica, root count and error word
+    unsigned *cc_parent = nullptr;
+    unsigned long long *cc_count = nullptr;
     unsigned long long *thr = nullptr, *counts = nullptr, *bins = nullptr;
     double *partials = nullptr, *fractions = nullptr;
     int32_t *binmap = nullptr;
@@ -273,7 +282,34 @@ cudaError_t enqueue_sweep(hmc_handle *h, int colour, cudaStream_t s) {
     a.J = (T)h->p.J;
     a.kT = (T)h->p.kT;
     a.nctas = h->nctas;
-    return hmc::launch_sweep<T>(a, colour, h->p.elastic == HMC_ELASTIC_TRACTION, s);
+    a.work = h->zone_work;
+    a.count = h->zone_count;
+    if (h->p.elastic != HMC_ELASTIC_ZONE1)
+        return hmc::launch_sweep<T>(a, colour, h->p.elastic == HMC_ELASTIC_TRACTION ? hmc::SWEEP_POINT
+                                                                                     : hmc::SWEEP_POTTS, s);
+    // 27-point zone: list the trials, copy the spins as they are at the start of the half step,
+    // then decide every listed trial against that copy
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(h->zone_count, 0, sizeof(unsigned), s)) != cudaSuccess) return e;
+    if ((e = hmc::launch_sweep<T>(a, colour, hmc::SWEEP_ZONE_LIST, s)) != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(h->snap, h->spins, sizeof(uint4) * (size_t)h->nblk_total, cudaMemcpyDeviceToDevice,
+                             s)) != cudaSuccess)
+        return e;
+    hmc::ZoneArgs<T> z;
+    z.reps = h->d_reps;
+    z.snap = h->snap;
+    z.spins = h->spins;
+    z.u = static_cast<const T *>(h->u[h->cur]);
+    z.ctab = static_cast<const T *>(h->ctab);
+    z.ktab = static_cast<const T *>(h->ktab);
+    z.work = h->zone_work;
+    z.count = h->zone_count;
+    z.thr = h->thr;
+    z.sched = h->zone_sched;
+    z.nsched = h->zone_nsched;
+    z.J = (T)h->p.J;
+    z.kT = (T)h->p.kT;
+    return hmc::launch_zone<T>(z, h->zone_grid, s);
 }
 
 cudaError_t enq_stress(hmc_handle *h, cudaStream_t s) {
@@ -357,7 +393,10 @@ std::string validate(const hmc_params *p) {
         if (!std::isfinite(x)) return "non-finite parameter";
     if (p->kT < 0) return "kT must be >= 0";
     if (p->bc != HMC_BC_UNIAXIAL && p->bc != HMC_BC_STRAIN6) return "bad bc";
-    if (p->elastic != HMC_ELASTIC_OFF && p->elastic != HMC_ELASTIC_TRACTION) return "bad elastic";
+    if (p->elastic != HMC_ELASTIC_OFF && p->elastic != HMC_ELASTIC_TRACTION && p->elastic != HMC_ELASTIC_ZONE1)
+        return "bad elastic";
+    if (p->elastic == HMC_ELASTIC_ZONE1 && (p->nx < 6 || p->ny < 6 || p->nz < 6))
+        return "the 27-point zone needs grid edges >= 6";
     if (p->trial != HMC_TRIAL_NEIGHBOR && p->trial != HMC_TRIAL_UNIFORM_Q) return "bad trial";
     if (p->precision != HMC_FP32 && p->precision != HMC_FP64) return "bad precision";
     if (p->mpm_steps_per_mcs < 0) return "mpm_steps_per_mcs must be >= 0";
@@ -406,7 +445,8 @@ void destroy_buffers(hmc_handle *h) {
     for (int i = 0; i < 2; ++i)
         if (h->gexec[i]) cudaGraphExecDestroy(h->gexec[i]);
     void *bufs[] = {h->spins, h->stage16, h->u[0], h->u[1], h->v, h->sig, h->ctab, h->ctab_pairs, h->wtab, h->thr, h->counts,
-                    h->bins, h->partials, h->fractions, h->binmap, h->st, h->d_reps, h->d_cta_rep, h->d_sched};
+                    h->bins, h->partials, h->fractions, h->binmap, h->st, h->d_reps, h->d_cta_rep, h->d_sched,
+                    h->zone_work, h->snap, h->zone_count, h->ktab, h->zone_sched, h->cc_parent, h->cc_count};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (h->cap) cudaStreamDestroy(h->cap);
@@ -777,6 +817,7 @@ hmc_status hmc_batch_create(const hmc_params *params, int32_t n_replicas, hmc_ha
         rd[r].key1 = (uint32_t)(R.p.seed >> 32);
         rd[r].replica = R.p.replica;
         rd[r].lam_sd_half = R.lam_sd_half;
+        rd[r].lam = R.lam;
         rd[r].st = h->st + r;
         for (int c = 0; c < R.ncta; ++c) ctarep[R.cta_off + c] = r;
     }
@@ -789,6 +830,26 @@ hmc_status hmc_batch_create(const hmc_params *params, int32_t n_replicas, hmc_ha
     void *zero_ptrs[] = {h->u[0], h->u[1], h->v};
     for (void *z : zero_ptrs)
         if ((e = cudaMemset(z, 0, nodes_b)) != cudaSuccess) return bail(cuda_fail(h, e, "memset"));
+    if (p->elastic == HMC_ELASTIC_ZONE1) {
+        std::vector<uint16_t> zs = hmc::zone_schedule();
+        if (zs.empty()) return bail(fail(h, HMC_ERR_CUDA, "zone schedule does not fit"));
+        h->zone_nsched = (int)zs.size();
+        Alloc za[] = {
+            {(void **)&h->zone_work, sizeof(uint4) * 4 * (size_t)h->nblk_total, "zone trial list"},
+            {(void **)&h->snap, sizeof(uint4) * (size_t)h->nblk_total, "spin copy"},
+            {(void **)&h->zone_count, sizeof(unsigned), "zone trial count"},
+            {&h->ktab, h->tsize * 8 * 300 * (size_t)p->n_orient, "zone element tables"},
+            {(void **)&h->zone_sched, sizeof(uint16_t) * zs.size(), "zone schedule"},
+        };
+        for (auto &a : za)
+            if ((e = cudaMalloc(a.ptr, a.bytes)) != cudaSuccess) return bail(cuda_fail(h, e, a.what));
+        if ((e = cudaMemcpy(h->zone_sched, zs.data(), sizeof(uint16_t) * zs.size(), cudaMemcpyHostToDevice)) !=
+            cudaSuccess)
+            return bail(cuda_fail(h, e, "zone schedule upload"));
+        if ((e = hmc::zone_prepare()) != cudaSuccess) return bail(cuda_fail(h, e, "zone kernel attribute"));
+        const int per_sm = p->precision == HMC_FP32 ? hmc::zone_per_sm<float>() : hmc::zone_per_sm<double>();
+        h->zone_grid = h->num_sms * per_sm;
+    }
     hmc_status s = upload_sched(h, h->mpm_shape);
     if (s != HMC_OK) return bail(s);
     h->mpm_grid = grid_for_shape(h, h->mpm_shape, 0);
@@ -900,6 +961,18 @@ hmc_status hmc_set_orientations(hmc_handle *h, const double *euler, const uint16
         auto w = pack_wtab<double>(h->A, Q);
         HMC_CK(h, cudaMemcpy(h->ctab, c.data(), c.size() * sizeof(double), cudaMemcpyHostToDevice), "table upload");
         HMC_CK(h, cudaMemcpy(h->wtab, w.data(), w.size() * sizeof(double), cudaMemcpyHostToDevice), "table upload");
+    }
+    if (h->p.elastic == HMC_ELASTIC_ZONE1) {
+        std::vector<double> kt;
+        hmc::zone_element_tables(h->Cv.data(), Q, kt);
+        if (h->p.precision == HMC_FP32) {
+            std::vector<float> kf(kt.begin(), kt.end());
+            HMC_CK(h, cudaMemcpy(h->ktab, kf.data(), kf.size() * sizeof(float), cudaMemcpyHostToDevice),
+                   "zone table upload");
+        } else {
+            HMC_CK(h, cudaMemcpy(h->ktab, kt.data(), kt.size() * sizeof(double), cudaMemcpyHostToDevice),
+                   "zone table upload");
+        }
     }
     const size_t nodes_b = node_bytes(h);
     HMC_CK(h, cudaMemsetAsync(h->u[0], 0, nodes_b, h->stream), "memset u");
@@ -1021,6 +1094,26 @@ hmc_status hmc_mc_sweeps(hmc_handle *h, int32_t n_mcs, int64_t *accepted) {
         if (h->p.mpm_steps_per_mcs & 1) h->cur ^= 1;
     }
     if (accepted) return read_accepted(h, accepted);
+    return HMC_OK;
+}
+
+hmc_status hmc_grain_count(hmc_handle *h, int64_t *n_grains) {
+    hmc_status s = need_oriented(h);
+    if (s != HMC_OK) return s;
+    if (!n_grains) return fail(h, HMC_ERR_ARG, "NULL n_grains");
+    const RepHost &R = selr(h);
+    if (R.N > 0xffffffffll) return fail(h, HMC_ERR_ARG, "replica too large for 32-bit grain labels");
+    if (!h->cc_parent) HMC_CK(h, cudaMalloc(&h->cc_parent, sizeof(unsigned) * (size_t)h->N_max), "grain labels");
+    if (!h->cc_count) HMC_CK(h, cudaMalloc(&h->cc_count, 2 * sizeof(unsigned long long)), "grain count");
+    int *err = reinterpret_cast<int *>(h->cc_count + 1);
+    HMC_CK(h, hmc::launch_grain_count(h->spins + R.blk_off, R.nbx, R.nby, R.nbz, h->cc_parent, h->cc_count, err,
+                                      h->stream),
+           "grain count launch");
+    unsigned long long host[2] = {0, 0};
+    HMC_CK(h, cudaMemcpyAsync(host, h->cc_count, sizeof(host), cudaMemcpyDeviceToHost, h->stream), "grain count read");
+    HMC_CK(h, cudaStreamSynchronize(h->stream), "sync");
+    if ((int)(host[1] & 0xffffffffu) != 0) return fail(h, HMC_ERR_TIMEOUT, "grain union-find exceeded its iteration cap");
+    *n_grains = (int64_t)host[0];
     return HMC_OK;
 }
 

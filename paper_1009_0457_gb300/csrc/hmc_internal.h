@@ -18,6 +18,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 namespace hmc {
 
 // Scalars that kernels read or update on the device, so that a Monte Carlo
@@ -54,6 +56,7 @@ struct Replica {
     long long blk_off;
     uint32_t key0, key1, replica, pad2;
     double lam_sd_half;       // lambda * (S11 - S12 - S44/2) / 2
+    double lam;               // lambda: MC energy per GPa of elastic energy density
     DevState *st;
 };
 
@@ -105,6 +108,28 @@ struct SweepArgs {
     int trial, nq;
     T J, kT;
     int nctas;
+    uint4 *work;                     // zone mode: trial list {site, replica, q_new | q_old << 16, r1}
+    unsigned *count;                 // zone mode: entries in the list
+};
+
+// Elastic term of a sweep: none, one-point zone from the stored stress, or the
+// 27-point zone (trials listed by the sweep, decided by the zone kernel).
+enum SweepMode { SWEEP_POTTS = 0, SWEEP_POINT = 1, SWEEP_ZONE_LIST = 2 };
+
+template <typename T>
+struct ZoneArgs {
+    const Replica *reps;
+    const uint4 *snap;               // spins at the start of the half step
+    uint4 *spins;                    // live spins: accepted trials are XOR-ed in
+    const T *u;                      // nodal displacement
+    const T *ctab;                   // Q x 24 rotated stiffness
+    const T *ktab;                   // Q x 8 x 300 element stiffness of a point per position in its cell
+    const uint4 *work;
+    const unsigned *count;
+    const unsigned long long *thr;
+    const uint16_t *sched;           // elimination schedule (zone_schedule)
+    int nsched;
+    T J, kT;
 };
 
 // MPM patch shapes (cells per patch edge; owned nodes = cells - 1).  A variant
@@ -120,7 +145,14 @@ cudaError_t launch_mpm_step(const MpmArgs<T> &a, int shape, cudaStream_t s);
 template <typename T>
 cudaError_t launch_stress(const StressArgs<T> &a, cudaStream_t s);
 template <typename T>
-cudaError_t launch_sweep(const SweepArgs<T> &a, int colour, bool elastic, cudaStream_t s);
+cudaError_t launch_sweep(const SweepArgs<T> &a, int colour, int mode, cudaStream_t s);
+template <typename T>
+cudaError_t launch_zone(const ZoneArgs<T> &a, int grid, cudaStream_t s);
+template <typename T>
+int zone_per_sm();                 // resident zone CTAs per SM
+cudaError_t zone_prepare();        // opt the zone kernels into their dynamic shared memory
+std::vector<uint16_t> zone_schedule();   // empty if it does not fit the kernel's table
+void zone_element_tables(const double *Cv, int Q, std::vector<double> &out);
 cudaError_t mpm_prepare();  // opt the MPM kernels into their dynamic shared memory (once, before any capture)
 template <typename T>
 int mpm_per_sm(int variant);  // resident MPM CTAs per SM
@@ -134,6 +166,8 @@ cudaError_t launch_pack_spins(const uint16_t *nat, uint4 *blk, int nx, int ny, i
 cudaError_t launch_unpack_spins(const uint4 *blk, uint16_t *nat, int nx, int ny, int nz, cudaStream_t s);
 cudaError_t launch_bonds_counts(const uint4 *blk, int nbx, int nby, int nbz, int nq,
                                 unsigned long long *counts, DevState *st, cudaStream_t s);
+cudaError_t launch_grain_count(const uint4 *spins, int nbx, int nby, int nbz, unsigned *parent,
+                               unsigned long long *count, int *err, cudaStream_t s);
 cudaError_t launch_bins(const unsigned long long *counts, const int32_t *binmap, int nq, int nbins,
                         unsigned long long *bins, double *fractions, long long n_sites, cudaStream_t s);
 

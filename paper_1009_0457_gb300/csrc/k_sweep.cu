@@ -4,11 +4,15 @@
 // constant-traction zone shift (Eqs. 6-8 and 13) from the stored stress.
 //
 // One thread per 2x2x2 block: it tries the block's four sites of the sweep's
-// colour.  A CTA covers 256 blocks of one replica of the batch.  Loads per block: the block's 16 B of spins, the other colour's
-// 8 B quad of the six face neighbours (cache hits: every quad is some other
-// thread's own), and six 16 B stress vectors (FP32).  Writes: the colour's
-// 8 B quad when a site changed.  Same-colour sites share no neighbour, so the
-// in-place update is race free.
+// colour.  A CTA covers 256 blocks of one replica of the batch.  Loads per
+// block: the block's 16 B of spins, the other colour's 8 B quad of the six face
+// neighbours (cache hits: every quad is some other thread's own), and six 16 B
+// stress vectors (FP32).  Writes: the colour's 8 B quad when a site changed.
+// Same-colour sites share no neighbour, so the in-place update is race free.
+//
+// With the 27-point zone the sweep only lists its non-trivial trials (site,
+// replica, old and new orientation, the acceptance draw) with one atomic per
+// warp; the zone kernel decides them.
 #include "hmc_device.cuh"
 
 namespace hmc {
@@ -83,12 +87,16 @@ __device__ __forceinline__ T zone_phi(const T *__restrict__ w, const T (&s)[6]) 
 __device__ __forceinline__ float log_t(float x) { return logf(x); }
 __device__ __forceinline__ double log_t(double x) { return log(x); }
 
-template <typename T, bool ELASTIC>
+template <typename T, int MODE>
 __global__ void __launch_bounds__(BLOCK_THREADS, (sizeof(T) == 4 ? 3 : 2)) k_sweep(SweepArgs<T> a, int colour) {
+    constexpr bool ELASTIC = MODE == SWEEP_POINT;
+    constexpr bool LIST = MODE == SWEEP_ZONE_LIST;
     const int r = __ldg(a.cta_rep + blockIdx.x);
     const Replica &R = a.reps[r];
     const int blk = (blockIdx.x - R.cta_off) * BLOCK_THREADS + threadIdx.x;  // block within the replica
     int nacc = 0;
+    uint4 ent[4];   // zone mode: this thread's trials for the list
+    int nent = 0;
     if (blk < R.nblk) {
         const int nbx = R.nbx, nby = R.nby, nbz = R.nbz;
         const int bx = blk % nbx, rr = blk / nbx;
@@ -155,6 +163,16 @@ __global__ void __launch_bounds__(BLOCK_THREADS, (sizeof(T) == 4 ? 3 : 2)) k_swe
             }
             out[i] = q;
             if (qn == q) continue;
+            if (LIST) {
+                const uint32_t x = 2u * bx + lx, y = 2u * by + ly, z = 2u * bz + lz;
+                const uint4 en = make_uint4(x + (uint32_t)R.nx * (y + (uint32_t)R.ny * z), (uint32_t)r,
+                                            (uint32_t)qn | ((uint32_t)q << 16), rn.y);
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (j == nent) ent[j] = en;
+                ++nent;
+                continue;
+            }
             int dE = 0;
 #pragma unroll
             for (int j = 0; j < 6; ++j) dE += (nb[j] == q) - (nb[j] == qn);
@@ -186,6 +204,25 @@ __global__ void __launch_bounds__(BLOCK_THREADS, (sizeof(T) == 4 ? 3 : 2)) k_swe
             reinterpret_cast<uint2 *>(spins)[2 * blk + colour] = w;
         }
     }
+    if (LIST) {
+        // warp-aggregated append: one atomic per warp, entries in lane order
+        const int lane = threadIdx.x & 31;
+        int incl = nent;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        unsigned base = 0;
+        if (lane == 31 && total) base = atomicAdd(a.count, (unsigned)total);
+        base = __shfl_sync(0xffffffffu, base, 31);
+        const unsigned first = base + (unsigned)(incl - nent);
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (j < nent) a.work[first + j] = ent[j];
+        return;
+    }
     // a CTA belongs to one replica: warp totals go to that replica's counter
     const unsigned tot = __reduce_add_sync(0xffffffffu, (unsigned)nacc);
     if ((threadIdx.x & 31) == 0 && tot) atomicAdd(&R.st->accepted, (unsigned long long)tot);
@@ -194,15 +231,17 @@ __global__ void __launch_bounds__(BLOCK_THREADS, (sizeof(T) == 4 ? 3 : 2)) k_swe
 }  // namespace
 
 template <typename T>
-cudaError_t launch_sweep(const SweepArgs<T> &a, int colour, bool elastic, cudaStream_t s) {
-    if (elastic)
-        k_sweep<T, true><<<a.nctas, BLOCK_THREADS, 0, s>>>(a, colour);
+cudaError_t launch_sweep(const SweepArgs<T> &a, int colour, int mode, cudaStream_t s) {
+    if (mode == SWEEP_POINT)
+        k_sweep<T, SWEEP_POINT><<<a.nctas, BLOCK_THREADS, 0, s>>>(a, colour);
+    else if (mode == SWEEP_ZONE_LIST)
+        k_sweep<T, SWEEP_ZONE_LIST><<<a.nctas, BLOCK_THREADS, 0, s>>>(a, colour);
     else
-        k_sweep<T, false><<<a.nctas, BLOCK_THREADS, 0, s>>>(a, colour);
+        k_sweep<T, SWEEP_POTTS><<<a.nctas, BLOCK_THREADS, 0, s>>>(a, colour);
     return cudaGetLastError();
 }
 
-template cudaError_t launch_sweep<float>(const SweepArgs<float> &, int, bool, cudaStream_t);
-template cudaError_t launch_sweep<double>(const SweepArgs<double> &, int, bool, cudaStream_t);
+template cudaError_t launch_sweep<float>(const SweepArgs<float> &, int, int, cudaStream_t);
+template cudaError_t launch_sweep<double>(const SweepArgs<double> &, int, int, cudaStream_t);
 
 }  // namespace hmc
