@@ -69,6 +69,11 @@ def lib():
         L.orc_unlike_bonds.argtypes = [i, i, i, u16p]
         L.orc_unlike_bonds.restype = C.c_int64
         L.orc_orientation_counts.argtypes = [C.c_int64, u16p, i, i64p]
+        L.orc_gs_sweep.argtypes = [i, i, i, u16p, C.c_uint64, C.c_uint32, C.c_uint32, C.c_double, C.c_double,
+                                   i, i, i64p]
+        L.orc_gs_sweep.restype = C.c_int64
+        L.orc_grain_count.argtypes = [i, i, i, u16p, i64p]
+        L.orc_grain_count.restype = C.c_int64
         _lib = L
     return _lib
 
@@ -358,6 +363,28 @@ def half_sweep(spins, colour, seed, mcs, replica, J, kT, trial, Q, elastic, lam,
                                _p(Sf, C.c_double), _p(sg, C.c_double), _p(changed, C.c_uint8),
                                _p(dH, C.c_double), _p(t, C.c_double))
     return int(acc), changed, dH, t
+
+
+def gs_sweep(spins, seed, mcs, replica, J, kT, trial, Q):
+    """In-place Gauss-Seidel Monte Carlo step (sequential random sites, each
+    accepted trial applied at once); returns (accepted, summed bond-count change)."""
+    nz, ny, nx = spins.shape
+    assert spins.dtype == np.uint16 and spins.flags.c_contiguous
+    de = np.zeros(1, dtype=np.int64)
+    acc = lib().orc_gs_sweep(nx, ny, nz, _p(spins, C.c_uint16), int(seed), int(mcs), int(replica), float(J),
+                             float(kT), int(trial), int(Q), _p(de, C.c_int64))
+    return int(acc), int(de[0])
+
+
+def grain_count(spins, want_labels=False):
+    """Grains = face-connected sets of one orientation on the periodic lattice."""
+    nz, ny, nx = spins.shape
+    s = np.ascontiguousarray(spins, dtype=np.uint16)
+    lab = np.zeros(s.size, dtype=np.int64) if want_labels else None
+    n = lib().orc_grain_count(nx, ny, nz, _p(s, C.c_uint16), _p(lab, C.c_int64) if want_labels else None)
+    if n < 0:
+        raise MemoryError("grain count")
+    return (int(n), lab.reshape(s.shape)) if want_labels else int(n)
 
 
 def unlike_bonds(spins):

@@ -527,3 +527,89 @@ void orc_orientation_counts(int64_t N, const uint16_t *spin, int Q, int64_t *cou
     memset(counts, 0, sizeof(int64_t) * Q);
     for (int64_t p = 0; p < N; ++p) counts[spin[p]] += 1;
 }
+
+/* Gauss-Seidel Monte Carlo step (Sec. "Microstructural Evolution"): N = nx ny nz
+ * trials in sequence, each at a site drawn uniformly, each accepted trial applied
+ * at once so that later trials see it.  Pure Potts energy (Eq. 4) and Metropolis
+ * rule (Eq. 5) with the integer thresholds.  Trial t draws Philox4x32-10 with
+ * counter (t, mcs, replica, 1) and key (seed lo, seed hi): word 0 picks the site
+ * floor(r0 N / 2^32), word 1 the trial orientation (neighbour k = floor(6 r1 / 2^32)
+ * in the order -x,+x,-y,+y,-z,+z, or floor(r1 Q / 2^32)), word 2 the acceptance.
+ * Returns the accepted count; *dE_sum (optional) receives the summed bond-count
+ * change of the accepted trials. */
+int64_t orc_gs_sweep(int nx, int ny, int nz, uint16_t *spin, uint64_t seed, uint32_t mcs, uint32_t replica,
+                     double J, double kT, int trial_mode, int Q, int64_t *dE_sum)
+{
+    const int64_t N = (int64_t)nx * ny * nz;
+    const uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+    int64_t accepted = 0, esum = 0;
+    for (int64_t t = 0; t < N; ++t) {
+        uint32_t ctr[4] = {(uint32_t)t, mcs, replica, 1u};
+        uint32_t r[4];
+        orc_philox4x32_10(ctr, key, r);
+        const int64_t p = (int64_t)(((uint64_t)r[0] * (uint64_t)N) >> 32);
+        const int x = (int)(p % nx), y = (int)((p / nx) % ny), z = (int)(p / ((int64_t)nx * ny));
+        uint16_t nb[6];
+        nb[0] = spin[wrap(x - 1, nx) + (int64_t)nx * (y + (int64_t)ny * z)];
+        nb[1] = spin[wrap(x + 1, nx) + (int64_t)nx * (y + (int64_t)ny * z)];
+        nb[2] = spin[x + (int64_t)nx * (wrap(y - 1, ny) + (int64_t)ny * z)];
+        nb[3] = spin[x + (int64_t)nx * (wrap(y + 1, ny) + (int64_t)ny * z)];
+        nb[4] = spin[x + (int64_t)nx * (y + (int64_t)ny * wrap(z - 1, nz))];
+        nb[5] = spin[x + (int64_t)nx * (y + (int64_t)ny * wrap(z + 1, nz))];
+        const uint16_t q = spin[p];
+        const uint16_t qt = trial_mode == ORC_TRIAL_NEIGHBOR ? nb[(int)(((uint64_t)r[1] * 6u) >> 32)]
+                                                            : (uint16_t)(((uint64_t)r[1] * (uint64_t)Q) >> 32);
+        if (qt == q) continue;
+        int dE = 0;
+        for (int k = 0; k < 6; ++k) dE += (nb[k] == q) - (nb[k] == qt);
+        if (dE <= 0 || (double)r[2] < orc_accept_threshold(dE, J, kT)) {
+            spin[p] = qt;
+            ++accepted;
+            esum += dE;
+        }
+    }
+    if (dE_sum) *dE_sum = esum;
+    return accepted;
+}
+
+/* Number of grains: connected sets of sites of one orientation, face neighbours
+ * (6-connectivity) on the periodic lattice, by breadth-first search.  label
+ * (optional, N entries) receives each site's grain index in order of discovery. */
+int64_t orc_grain_count(int nx, int ny, int nz, const uint16_t *spin, int64_t *label)
+{
+    const int64_t N = (int64_t)nx * ny * nz;
+    int64_t *lab = label ? label : (int64_t *)malloc(sizeof(int64_t) * (size_t)N);
+    int64_t *queue = (int64_t *)malloc(sizeof(int64_t) * (size_t)N);
+    if (!lab || !queue) {
+        if (!label) free(lab);
+        free(queue);
+        return -1;
+    }
+    for (int64_t p = 0; p < N; ++p) lab[p] = -1;
+    int64_t grains = 0;
+    for (int64_t s = 0; s < N; ++s) {
+        if (lab[s] >= 0) continue;
+        int64_t head = 0, tail = 0;
+        queue[tail++] = s;
+        lab[s] = grains;
+        while (head < tail) {
+            const int64_t p = queue[head++];
+            const int x = (int)(p % nx), y = (int)((p / nx) % ny), z = (int)(p / ((int64_t)nx * ny));
+            const int64_t nbr[6] = {wrap(x - 1, nx) + (int64_t)nx * (y + (int64_t)ny * z),
+                                    wrap(x + 1, nx) + (int64_t)nx * (y + (int64_t)ny * z),
+                                    x + (int64_t)nx * (wrap(y - 1, ny) + (int64_t)ny * z),
+                                    x + (int64_t)nx * (wrap(y + 1, ny) + (int64_t)ny * z),
+                                    x + (int64_t)nx * (y + (int64_t)ny * wrap(z - 1, nz)),
+                                    x + (int64_t)nx * (y + (int64_t)ny * wrap(z + 1, nz))};
+            for (int k = 0; k < 6; ++k)
+                if (lab[nbr[k]] < 0 && spin[nbr[k]] == spin[s]) {
+                    lab[nbr[k]] = grains;
+                    queue[tail++] = nbr[k];
+                }
+        }
+        ++grains;
+    }
+    if (!label) free(lab);
+    free(queue);
+    return grains;
+}
