@@ -36,27 +36,34 @@ namespace hmc {
 
 namespace {
 
-constexpr int ZS = 81;                       // row stride of the zone matrix (odd: rows in distinct banks)
-constexpr int ZK = 6564;                     // 81 x 81 elements rounded up to a multiple of 4
-constexpr int ZSCHED_CAP = 1280;             // u16 entries of the elimination schedule
-constexpr int ZS_NBOFF = 27, ZS_PROFF = 55;  // schedule header: node order, then the two offset arrays
+// Schedule table (uint16, built by zone_schedule):
+//   [0, 27)        elimination order of reflected node rx + 3 ry + 9 rz
+//   [27, 55)       per step k: first column-block entry (slot of block (I, k))
+//   [55, 83)       per step k: first update entry (slots of (I,J), (I,k), (J,k))
+//   [83, 110)      slot of the diagonal block of order k
+//   [110, 839)     slot of block (I, J), I >= J, in the filled pattern (0xffff: always zero)
+//   then the column-block entries, then the update triples.
+constexpr int ZS_NBOFF = 27, ZS_UPOFF = 55, ZS_DIAG = 83, ZS_BIDX = 110, ZS_HDR = 839;
+constexpr int ZSCHED_CAP = 4096;
+constexpr int ZSLOT_CAP = 232;   // 3x3 blocks of the filled lower triangle (226 for this pattern)
+constexpr int ZBLK = 12;         // a block: 3 rows of 4 values (the 4th pads a row to 16 B)
 
 template <typename T>
 struct ZoneCfg;
 template <>
 struct ZoneCfg<float> {
-    static constexpr int WARPS = 4;
+    static constexpr int WARPS = 8;
 };
 template <>
 struct ZoneCfg<double> {
-    static constexpr int WARPS = 2;
+    static constexpr int WARPS = 4;
 };
 
 __host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
 __host__ __device__ constexpr size_t zone_cta_bytes() { return align16((ZSCHED_CAP + 300) * sizeof(uint16_t)); }
 template <typename T>
 __host__ __device__ constexpr size_t zone_warp_bytes() {
-    return align16((ZK + 144 + 36) * sizeof(T) + 64 + 8);
+    return align16((ZSLOT_CAP * ZBLK + 144 + 72) * sizeof(T) + 64 + 8 + 32 + 8);
 }
 template <typename T>
 __host__ __device__ constexpr size_t zone_smem() {
@@ -65,6 +72,22 @@ __host__ __device__ constexpr size_t zone_smem() {
 
 __device__ __forceinline__ float zlog(float x) { return logf(x); }
 __device__ __forceinline__ double zlog(double x) { return log(x); }
+
+__device__ __forceinline__ void ld4(const float *p, float (&v)[4]) {
+    const float4 t = *reinterpret_cast<const float4 *>(p);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ __forceinline__ void ld4(const double *p, double (&v)[4]) {
+    const double2 a = reinterpret_cast<const double2 *>(p)[0], b = reinterpret_cast<const double2 *>(p)[1];
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+__device__ __forceinline__ void st4(float *p, const float (&v)[4]) {
+    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void st4(double *p, const double (&v)[4]) {
+    reinterpret_cast<double2 *>(p)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
+}
 
 // Gradient of the trilinear shape function of cell corner (I,J,K) at the point
 // of local position (a,b,c) in {0,1}^3 (coordinates 1/4, 3/4 of the edge h = 2).
@@ -78,32 +101,38 @@ __device__ __forceinline__ void corner_grad(int a, int b, int c, int I, int J, i
     g[2] = Na * Nb * sc;
 }
 
-// Row (corner, alpha) of B_p^T: strain (Voigt, engineering shear) per unit
-// displacement component alpha of that corner.
+// Component v of row (corner, alpha) of B_p^T: strain (Voigt, engineering
+// shear) per unit displacement component alpha of that corner.
 template <typename T>
-__device__ __forceinline__ void bt_row(const T (&g)[3], int alpha, T (&b)[6]) {
-    b[0] = alpha == 0 ? g[0] : T(0);
-    b[1] = alpha == 1 ? g[1] : T(0);
-    b[2] = alpha == 2 ? g[2] : T(0);
-    b[3] = alpha == 1 ? g[2] : alpha == 2 ? g[1] : T(0);
-    b[4] = alpha == 0 ? g[2] : alpha == 2 ? g[0] : T(0);
-    b[5] = alpha == 0 ? g[1] : alpha == 1 ? g[0] : T(0);
+__device__ __forceinline__ T bt_entry(const T (&g)[3], int alpha, int v) {
+    switch (v) {
+        case 0: return alpha == 0 ? g[0] : T(0);
+        case 1: return alpha == 1 ? g[1] : T(0);
+        case 2: return alpha == 2 ? g[2] : T(0);
+        case 3: return alpha == 1 ? g[2] : alpha == 2 ? g[1] : T(0);
+        case 4: return alpha == 0 ? g[2] : alpha == 2 ? g[0] : T(0);
+        default: return alpha == 0 ? g[1] : alpha == 1 ? g[0] : T(0);
+    }
 }
 
 template <typename T>
-__global__ void __launch_bounds__(32 * ZoneCfg<T>::WARPS) k_zone(ZoneArgs<T> a) {
+__global__ void __launch_bounds__(32 * ZoneCfg<T>::WARPS, 2) k_zone(ZoneArgs<T> a) {
     constexpr int W = ZoneCfg<T>::WARPS;
+    constexpr int NJ = 10;   // element-matrix entries per lane: t = lane + 32 j < 300
     constexpr unsigned FULL = 0xffffffffu;
     extern __shared__ __align__(16) unsigned char smem[];
     uint16_t *sch = reinterpret_cast<uint16_t *>(smem);
     uint16_t *ep = sch + ZSCHED_CAP;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned char *wb = smem + zone_cta_bytes() + warp * zone_warp_bytes<T>();
-    T *Kz = reinterpret_cast<T *>(wb);
-    T *Ys = Kz + ZK;          // Y = L22^-1 B_p^T, 24 x 6
-    T *Gs = Ys + 144;         // G, 6 x 6
-    uint8_t *dmap = reinterpret_cast<uint8_t *>(Gs + 36);   // (zone cell, corner) -> node order
-    uint8_t *inv = dmap + 64;                               // order - 19 -> corner of the site's cell
+    T *Kb = reinterpret_cast<T *>(wb);                     // block slots of the zone matrix
+    T *Ys = Kb + ZSLOT_CAP * ZBLK;                         // Y = L22^-1 B_p^T, 24 x 6
+    T *Gs = Ys + 144;                                      // G, 6 x 6
+    T *dCs = Gs + 36;                                      // C'(q_new) - C'(q_old), 6 x 6
+    uint8_t *dmap = reinterpret_cast<uint8_t *>(dCs + 36); // (zone cell, corner) -> node order
+    uint8_t *inv = dmap + 64;                              // order - 19 -> corner of the site's cell
+    uint8_t *plist = inv + 8;                              // zone points grouped by zone cell
+    uint8_t *cend = plist + 32;                            // end of each cell's group in plist
 
     for (int i = threadIdx.x; i < a.nsched; i += blockDim.x) sch[i] = a.sched[i];
     // element-matrix entry t (upper triangle of the 24 x 24, row-major) -> corners and components
@@ -117,9 +146,11 @@ __global__ void __launch_bounds__(32 * ZoneCfg<T>::WARPS) k_zone(ZoneArgs<T> a) 
         ep[t] = (uint16_t)((e1 / 3) | ((e1 % 3) << 3) | ((e2 / 3) << 5) | ((e2 % 3) << 8));
     }
     __syncthreads();
+    uint32_t epl[NJ];
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) epl[j] = lane + 32 * j < 300 ? ep[lane + 32 * j] : 0u;
     // fixed DOFs: all of node A (order 0), y and z of node B, z of node C
     const int ordB = sch[1], ordC = sch[3];
-    const int fB1 = 3 * ordB + 1, fB2 = 3 * ordB + 2, fC2 = 3 * ordC + 2;
     const unsigned n = *a.count;
 
     for (unsigned e = blockIdx.x * W + warp; e < n; e += gridDim.x * W) {
@@ -132,16 +163,16 @@ __global__ void __launch_bounds__(32 * ZoneCfg<T>::WARPS) k_zone(ZoneArgs<T> a) 
         const int lox = (x - 1) >> 1, loy = (y - 1) >> 1, loz = (z - 1) >> 1;   // lowest zone node (may be -1)
         const int pcx = (x >> 1) - lox, pcy = (y >> 1) - loy, pcz = (z >> 1) - loz;   // site's zone cell
 
-        // the zone's 27 points: orientation (start-of-step copy), position in its cell, zone cell
-        uint32_t my_q = 0, my_pos = 0, my_cell = 0;
+        // the zone's 27 points: orientation (start-of-step copy) and position in its cell
+        uint32_t my_q = 0, my_pos = 0;
         if (lane < 27) {
-            const int X = x + lane % 3 - 1, Yv = y + (lane / 3) % 3 - 1, Z = z + lane / 9 - 1;
-            const int Xw = wrapi(X, nx), Yw = wrapi(Yv, ny), Zw = wrapi(Z, nz);
+            const int Xw = wrapi(x + lane % 3 - 1, nx), Yw = wrapi(y + (lane / 3) % 3 - 1, ny);
+            const int Zw = wrapi(z + lane / 9 - 1, nz);
             const uint4 b = a.snap[R.blk_off + (Xw >> 1) + (long long)R.nbx * ((Yw >> 1) + (long long)R.nby * (Zw >> 1))];
-            my_q = spin_of(b, local_slot((Xw & 1) + 2 * (Yw & 1) + 4 * (Zw & 1)));
             my_pos = (Xw & 1) + 2 * (Yw & 1) + 4 * (Zw & 1);
-            my_cell = ((X >> 1) - lox) + 2 * ((Yv >> 1) - loy) + 4 * ((Z >> 1) - loz);
+            my_q = spin_of(b, local_slot(my_pos));
         }
+        // node orders of each zone cell's corners, and the zone points grouped by cell
         for (int l = lane; l < 64; l += 32) {
             const int c = l >> 3, k = l & 7;
             const int lx = (c & 1) + (k & 1), ly = ((c >> 1) & 1) + ((k >> 1) & 1), lz = (c >> 2) + (k >> 2);
@@ -150,92 +181,145 @@ __global__ void __launch_bounds__(32 * ZoneCfg<T>::WARPS) k_zone(ZoneArgs<T> a) 
             dmap[l] = o;
             if (c == pcx + 2 * pcy + 4 * pcz) inv[o - 19] = (uint8_t)k;
         }
+        if (lane < 8) {
+            // offsets of cell c along one axis: the site's own cell (1 in the zone when the
+            // coordinate is even) holds offsets {0,+1} or {-1,0}; the other holds the rest
+            const int cx = lane & 1, cy = (lane >> 1) & 1, cz = lane >> 2;
+            const int x0 = cx ? (pcx ? 0 : 1) : -1, x1 = cx ? 1 : (pcx ? -1 : 0);
+            const int y0 = cy ? (pcy ? 0 : 1) : -1, y1 = cy ? 1 : (pcy ? -1 : 0);
+            const int z0 = cz ? (pcz ? 0 : 1) : -1, z1 = cz ? 1 : (pcz ? -1 : 0);
+            const int cnt = (x1 - x0 + 1) * (y1 - y0 + 1) * (z1 - z0 + 1);
+            int incl = cnt;
+#pragma unroll
+            for (int o = 1; o < 8; o <<= 1) {
+                const int v = __shfl_up_sync(0xffu, incl, o);
+                if (lane >= o) incl += v;
+            }
+            int w = incl - cnt;
+            for (int dz = z0; dz <= z1; ++dz)
+                for (int dy = y0; dy <= y1; ++dy)
+                    for (int dx = x0; dx <= x1; ++dx) plist[w++] = (uint8_t)((dx + 1) + 3 * (dy + 1) + 9 * (dz + 1));
+            cend[lane] = (uint8_t)incl;
+        }
         {
             using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
-            V *kv = reinterpret_cast<V *>(Kz);
+            V *kv = reinterpret_cast<V *>(Kb);
             const V zero{};
-            for (int i = lane; i < (int)(ZK * sizeof(T) / 16); i += 32) kv[i] = zero;
+            for (int i = lane; i < (int)(ZSLOT_CAP * ZBLK * sizeof(T) / 16); i += 32) kv[i] = zero;
         }
         __syncwarp();
         if (lane < 6) {
-            const int d = lane < 3 ? lane : lane == 3 ? fB1 : lane == 4 ? fB2 : fC2;
-            Kz[d * ZS + d] = T(1);
+            const int o = lane < 3 ? 0 : lane < 5 ? ordB : ordC, r = lane < 3 ? lane : lane == 3 ? 1 : 2;
+            Kb[sch[ZS_DIAG + o] * ZBLK + 5 * r] = T(1);   // (r, r) of the diagonal block
         }
 
-        // assembly: K = sum over the zone's points of B^T C' B (element tables per orientation and position)
-        for (int s = 0; s < 27; ++s) {
-            const uint32_t qs = __shfl_sync(FULL, my_q, s), pos = __shfl_sync(FULL, my_pos, s);
-            const uint32_t cell = __shfl_sync(FULL, my_cell, s);
-            const T *ke = a.ktab + ((size_t)qs * 8 + pos) * 300;
-            const uint8_t *dm = dmap + 8 * cell;
-            for (int t = lane; t < 300; t += 32) {
-                const uint32_t pr = ep[t];
-                const int d1 = 3 * dm[pr & 7] + ((pr >> 3) & 3), d2 = 3 * dm[(pr >> 5) & 7] + (pr >> 8);
-                const bool fx = d1 < 3 || d2 < 3 || d1 == fB1 || d1 == fB2 || d1 == fC2 || d2 == fB1 || d2 == fB2 ||
-                                d2 == fC2;
-                if (fx) continue;
-                const int i = max(d1, d2), j = min(d1, d2);
-                Kz[i * ZS + j] += __ldg(ke + t);
+        // assembly: K = sum of B^T C' B over the zone's points (element tables per orientation and
+        // position); the points of one zone cell share its DOF map, so they are summed in registers
+        // and scattered once per cell.  Loads of the next point are issued before the current sum.
+        {
+            T acc[NJ], cur[NJ], nxt[NJ];
+#pragma unroll
+            for (int j = 0; j < NJ; ++j) acc[j] = T(0);
+            auto fetch = [&](int s, T(&v)[NJ]) {
+                const uint32_t qs = __shfl_sync(FULL, my_q, s), pos = __shfl_sync(FULL, my_pos, s);
+                const T *ke = a.ktab + ((size_t)qs * 8 + pos) * 300 + lane;
+#pragma unroll
+                for (int j = 0; j < NJ; ++j) v[j] = (j < NJ - 1 || lane < 300 - 32 * (NJ - 1)) ? __ldg(ke + 32 * j) : T(0);
+            };
+            fetch(plist[0], cur);
+            int c = 0, cn = cend[0];
+            for (int u = 0; u < 27; ++u) {
+                if (u + 1 < 27) fetch(plist[u + 1], nxt);
+#pragma unroll
+                for (int j = 0; j < NJ; ++j) acc[j] += cur[j];
+                if (u + 1 == cn) {
+                    const uint8_t *dm = dmap + 8 * c;
+#pragma unroll
+                    for (int j = 0; j < NJ; ++j) {
+                        if (lane + 32 * j >= 300) continue;
+                        const uint32_t pr = epl[j];
+                        int o1 = dm[pr & 7], a1 = (pr >> 3) & 3, o2 = dm[(pr >> 5) & 7], a2 = pr >> 8;
+                        const bool f1 = o1 == 0 || (o1 == ordB && a1 >= 1) || (o1 == ordC && a1 == 2);
+                        const bool f2 = o2 == 0 || (o2 == ordB && a2 >= 1) || (o2 == ordC && a2 == 2);
+                        if (f1 || f2) continue;
+                        if (o1 < o2 || (o1 == o2 && a1 < a2)) {
+                            const int to = o1, ta = a1;
+                            o1 = o2; a1 = a2; o2 = to; a2 = ta;
+                        }
+                        Kb[sch[ZS_BIDX + 27 * o1 + o2] * ZBLK + 4 * a1 + a2] += acc[j];
+                        acc[j] = T(0);
+                    }
+#pragma unroll
+                    for (int j = 0; j < NJ; ++j) acc[j] = T(0);
+                    __syncwarp();
+                    ++c;
+                    cn = c < 8 ? cend[c] : 27;
+                }
+#pragma unroll
+                for (int j = 0; j < NJ; ++j) cur[j] = nxt[j];
             }
-            __syncwarp();
         }
+        __syncwarp();
 
         // block Cholesky in the static order; a non-positive pivot marks the trial as failed
         bool ok = true;
         for (int k = 0; k < 27; ++k) {
-            T *Kk = Kz + 3 * k * ZS + 3 * k;
-            const T c00 = Kk[0], c10 = Kk[ZS], c11 = Kk[ZS + 1], c20 = Kk[2 * ZS], c21 = Kk[2 * ZS + 1],
-                    c22 = Kk[2 * ZS + 2];
-            const T l00 = sqrt(c00), i00 = T(1) / l00;
-            const T l10 = c10 * i00, l20 = c20 * i00;
-            const T l11 = sqrt(c11 - l10 * l10), i11 = T(1) / l11;
-            const T l21 = (c21 - l20 * l10) * i11;
-            const T l22 = sqrt(c22 - l20 * l20 - l21 * l21), i22 = T(1) / l22;
+            T *Dk = Kb + sch[ZS_DIAG + k] * ZBLK;
+            T r0[4], r1v[4], r2[4];
+            ld4(Dk, r0);
+            ld4(Dk + 4, r1v);
+            ld4(Dk + 8, r2);
+            const T l00 = sqrt(r0[0]), i00 = T(1) / l00;
+            const T l10 = r1v[0] * i00, l20 = r2[0] * i00;
+            const T l11 = sqrt(r1v[1] - l10 * l10), i11 = T(1) / l11;
+            const T l21 = (r2[1] - l20 * l10) * i11;
+            const T l22 = sqrt(r2[2] - l20 * l20 - l21 * l21), i22 = T(1) / l22;
             ok = ok && (l00 > T(0)) && (l11 > T(0)) && (l22 > T(0)) && (i00 < T(3.0e38)) && (i11 < T(3.0e38)) &&
                  (i22 < T(3.0e38));
             __syncwarp();
             if (lane == 0) {
-                Kk[0] = l00;
-                Kk[ZS] = l10;
-                Kk[ZS + 1] = l11;
-                Kk[2 * ZS] = l20;
-                Kk[2 * ZS + 1] = l21;
-                Kk[2 * ZS + 2] = l22;
+                Dk[0] = l00;
+                Dk[4] = l10;
+                Dk[5] = l11;
+                Dk[8] = l20;
+                Dk[9] = l21;
+                Dk[10] = l22;
             }
             const int nb0 = sch[ZS_NBOFF + k], nb1 = sch[ZS_NBOFF + k + 1];
             for (int t = nb0 + lane; t < nb1; t += 32) {
-                T *B = Kz + 3 * sch[t] * ZS + 3 * k;   // block (I, k): L_Ik = C_Ik L_kk^-T
+                T *B = Kb + sch[t] * ZBLK;   // block (I, k): L_Ik = C_Ik L_kk^-T
 #pragma unroll
                 for (int r = 0; r < 3; ++r) {
-                    T *row = B + r * ZS;
-                    const T x0 = row[0] * i00;
-                    const T x1 = (row[1] - x0 * l10) * i11;
-                    const T x2 = (row[2] - x0 * l20 - x1 * l21) * i22;
-                    row[0] = x0;
-                    row[1] = x1;
-                    row[2] = x2;
+                    T v[4];
+                    ld4(B + 4 * r, v);
+                    const T x0 = v[0] * i00;
+                    const T x1 = (v[1] - x0 * l10) * i11;
+                    const T x2 = (v[2] - x0 * l20 - x1 * l21) * i22;
+                    v[0] = x0;
+                    v[1] = x1;
+                    v[2] = x2;
+                    st4(B + 4 * r, v);
                 }
             }
             __syncwarp();
-            const int pr0 = sch[ZS_PROFF + k], pr1 = sch[ZS_PROFF + k + 1];
-            for (int t = pr0 + lane; t < pr1; t += 32) {
-                const int I = sch[t] & 0xff, J = sch[t] >> 8;
-                const T *LI = Kz + 3 * I * ZS + 3 * k, *LJ = Kz + 3 * J * ZS + 3 * k;
-                T li[3][3], lj[3][3];
+            const int up0 = sch[ZS_UPOFF + k], up1 = sch[ZS_UPOFF + k + 1];
+            for (int t = up0 + 3 * lane; t < up1; t += 96) {
+                T *C = Kb + sch[t] * ZBLK;
+                const T *LI = Kb + sch[t + 1] * ZBLK, *LJ = Kb + sch[t + 2] * ZBLK;
+                T li[3][4], lj[3][4];
 #pragma unroll
-                for (int r = 0; r < 3; ++r)
+                for (int r = 0; r < 3; ++r) {
+                    ld4(LI + 4 * r, li[r]);
+                    ld4(LJ + 4 * r, lj[r]);
+                }
 #pragma unroll
-                    for (int m = 0; m < 3; ++m) {
-                        li[r][m] = LI[r * ZS + m];
-                        lj[r][m] = LJ[r * ZS + m];
-                    }
-                T *C = Kz + 3 * I * ZS + 3 * J;
+                for (int r = 0; r < 3; ++r) {
+                    T v[4];
+                    ld4(C + 4 * r, v);
 #pragma unroll
-                for (int r = 0; r < 3; ++r)
-#pragma unroll
-                    for (int c = 0; c < 3; ++c)
-                        if (I != J || c <= r)
-                            C[r * ZS + c] -= li[r][0] * lj[c][0] + li[r][1] * lj[c][1] + li[r][2] * lj[c][2];
+                    for (int c = 0; c < 3; ++c) v[c] -= li[r][0] * lj[c][0] + li[r][1] * lj[c][1] + li[r][2] * lj[c][2];
+                    st4(C + 4 * r, v);
+                }
             }
             __syncwarp();
         }
@@ -243,36 +327,36 @@ __global__ void __launch_bounds__(32 * ZoneCfg<T>::WARPS) k_zone(ZoneArgs<T> a) 
         // Y = L22^-1 B_p^T on the site's cell (orders 19..26): lane v < 6 takes column v
         const int pa = x & 1, pb = y & 1, pcq = z & 1;
         if (lane < 6) {
-            for (int nn = 19; nn < 27; ++nn) {
-                const int cr = inv[nn - 19];
+            T yv[24];
+#pragma unroll
+            for (int nn = 0; nn < 8; ++nn) {
+                const int cr = inv[nn];
                 T g[3];
                 corner_grad<T>(pa, pb, pcq, cr & 1, (cr >> 1) & 1, cr >> 2, g);
                 T rhs[3];
 #pragma unroll
-                for (int al = 0; al < 3; ++al) {
-                    T b[6];
-                    bt_row<T>(g, al, b);
-                    T v = b[0];
+                for (int al = 0; al < 3; ++al) rhs[al] = bt_entry<T>(g, al, lane);
 #pragma unroll
-                    for (int w = 1; w < 6; ++w)
-                        if (lane == w) v = b[w];
-                    rhs[al] = v;
-                }
-                for (int m = 19; m < nn; ++m) {
-                    const T *L = Kz + 3 * nn * ZS + 3 * m;
+                for (int m = 0; m < nn; ++m) {
+                    const T *L = Kb + sch[ZS_BIDX + 27 * (19 + nn) + 19 + m] * ZBLK;
 #pragma unroll
-                    for (int r = 0; r < 3; ++r)
-                        rhs[r] -= L[r * ZS] * Ys[(3 * (m - 19)) * 6 + lane] + L[r * ZS + 1] * Ys[(3 * (m - 19) + 1) * 6 + lane] +
-                                  L[r * ZS + 2] * Ys[(3 * (m - 19) + 2) * 6 + lane];
+                    for (int r = 0; r < 3; ++r) {
+                        T v[4];
+                        ld4(L + 4 * r, v);
+                        rhs[r] -= v[0] * yv[3 * m] + v[1] * yv[3 * m + 1] + v[2] * yv[3 * m + 2];
+                    }
                 }
-                const T *Ln = Kz + 3 * nn * ZS + 3 * nn;
-                const T y0 = rhs[0] / Ln[0];
-                const T y1 = (rhs[1] - Ln[ZS] * y0) / Ln[ZS + 1];
-                const T y2 = (rhs[2] - Ln[2 * ZS] * y0 - Ln[2 * ZS + 1] * y1) / Ln[2 * ZS + 2];
-                Ys[(3 * (nn - 19)) * 6 + lane] = y0;
-                Ys[(3 * (nn - 19) + 1) * 6 + lane] = y1;
-                Ys[(3 * (nn - 19) + 2) * 6 + lane] = y2;
+                const T *Ln = Kb + sch[ZS_DIAG + 19 + nn] * ZBLK;
+                T d0[4], d1[4], d2[4];
+                ld4(Ln, d0);
+                ld4(Ln + 4, d1);
+                ld4(Ln + 8, d2);
+                yv[3 * nn] = rhs[0] / d0[0];
+                yv[3 * nn + 1] = (rhs[1] - d1[0] * yv[3 * nn]) / d1[1];
+                yv[3 * nn + 2] = (rhs[2] - d2[0] * yv[3 * nn] - d2[1] * yv[3 * nn + 1]) / d2[2];
             }
+#pragma unroll
+            for (int rrow = 0; rrow < 24; ++rrow) Ys[rrow * 6 + lane] = yv[rrow];
         }
         __syncwarp();
         if (lane < 21) {
@@ -283,6 +367,7 @@ __global__ void __launch_bounds__(32 * ZoneCfg<T>::WARPS) k_zone(ZoneArgs<T> a) 
             }
             const int w = v + rem;
             T s = T(0);
+#pragma unroll
             for (int rrow = 0; rrow < 24; ++rrow) s += Ys[rrow * 6 + v] * Ys[rrow * 6 + w];
             Gs[6 * v + w] = s;
             Gs[6 * w + v] = s;
@@ -296,10 +381,8 @@ __global__ void __launch_bounds__(32 * ZoneCfg<T>::WARPS) k_zone(ZoneArgs<T> a) 
             const T uv = a.u[3 * (R.blk_off + gi + (long long)R.nbx * (gj + (long long)R.nby * gk)) + al];
             T g[3];
             corner_grad<T>(pa, pb, pcq, cr & 1, (cr >> 1) & 1, cr >> 2, g);
-            T b[6];
-            bt_row<T>(g, al, b);
 #pragma unroll
-            for (int k = 0; k < 6; ++k) eps[k] = b[k] * uv;
+            for (int k = 0; k < 6; ++k) eps[k] = bt_entry<T>(g, al, k) * uv;
         }
 #pragma unroll
         for (int k = 0; k < 6; ++k)
@@ -315,85 +398,87 @@ __global__ void __launch_bounds__(32 * ZoneCfg<T>::WARPS) k_zone(ZoneArgs<T> a) 
                 dE += (v == q) - (v == qn);
             }
         }
+        if (lane < 21) {
+            int i = 0, rem = lane;
+            while (rem >= 6 - i) {
+                rem -= 6 - i;
+                ++i;
+            }
+            const int j = i + rem;
+            const T d = __ldg(a.ctab + 24 * (size_t)qn + lane) - __ldg(a.ctab + 24 * (size_t)q + lane);
+            dCs[6 * i + j] = d;
+            dCs[6 * j + i] = d;
+        }
         __syncwarp();
         ok = __all_sync(FULL, ok);
-        if (lane == 0) {
+        T e0[6];
+        {
             T eb[6];
             load_ebar<T>(R.st, eb);
-            T e0[6];
 #pragma unroll
             for (int k = 0; k < 6; ++k) e0[k] = eb[k] + eps[k];
-            // dC = C'(q_new) - C'(q_old), symmetric from the 21 stored entries
-            T dC[6][6];
-            {
-                const T *cn = a.ctab + 24 * (size_t)qn, *co = a.ctab + 24 * (size_t)q;
-                int t = 0;
+        }
+        // (I + G dC) eta = e0: lane i < 6 holds row i; partial pivoting across the lanes
+        T mrow[7];
 #pragma unroll
-                for (int i = 0; i < 6; ++i)
+        for (int j = 0; j < 6; ++j) {
+            T s = (lane == j) ? T(1) : T(0);
+            if (lane < 6) {
 #pragma unroll
-                    for (int j = i; j < 6; ++j) {
-                        const T d = __ldg(cn + t) - __ldg(co + t);
-                        dC[i][j] = d;
-                        dC[j][i] = d;
-                        ++t;
-                    }
+                for (int k = 0; k < 6; ++k) s += Gs[6 * lane + k] * dCs[6 * k + j];
             }
-            // solve (I + G dC) eta = e0 by Gaussian elimination with partial pivoting
-            T M[6][7];
+            mrow[j] = s;
+        }
+        mrow[6] = T(0);
 #pragma unroll
-            for (int i = 0; i < 6; ++i) {
+        for (int k = 0; k < 6; ++k)
+            if (lane == k) mrow[6] = e0[k];
 #pragma unroll
-                for (int j = 0; j < 6; ++j) {
-                    T s = i == j ? T(1) : T(0);
+        for (int c = 0; c < 6; ++c) {
+            T v = (lane >= c && lane < 6) ? fabs(mrow[c]) : T(-1);
+            int piv = lane;
 #pragma unroll
-                    for (int k = 0; k < 6; ++k) s += Gs[6 * i + k] * dC[k][j];
-                    M[i][j] = s;
-                }
-                M[i][6] = e0[i];
-            }
-#pragma unroll
-            for (int c = 0; c < 6; ++c) {
-                int piv = c;
-                T best = fabs(M[c][c]);
-#pragma unroll
-                for (int r = c + 1; r < 6; ++r)
-                    if (fabs(M[r][c]) > best) {
-                        best = fabs(M[r][c]);
-                        piv = r;
-                    }
-                ok = ok && best > T(0);
-#pragma unroll
-                for (int j = 0; j < 7; ++j) {
-                    T tmp = M[c][j];
-#pragma unroll
-                    for (int r = c + 1; r < 6; ++r)
-                        if (r == piv) {
-                            M[c][j] = M[r][j];
-                            M[r][j] = tmp;
-                        }
-                }
-                const T ip = T(1) / M[c][c];
-#pragma unroll
-                for (int r = c + 1; r < 6; ++r) {
-                    const T f = M[r][c] * ip;
-#pragma unroll
-                    for (int j = c; j < 7; ++j) M[r][j] -= f * M[c][j];
+            for (int o = 16; o > 0; o >>= 1) {
+                const T ov = __shfl_xor_sync(FULL, v, o);
+                const int op = __shfl_xor_sync(FULL, piv, o);
+                if (ov > v || (ov == v && op < piv)) {
+                    v = ov;
+                    piv = op;
                 }
             }
-            T eta[6];
+            ok = ok && v > T(0);
 #pragma unroll
-            for (int i = 5; i >= 0; --i) {
-                T s = M[i][6];
-#pragma unroll
-                for (int j = i + 1; j < 6; ++j) s -= M[i][j] * eta[j];
-                eta[i] = s / M[i][i];
+            for (int j = 0; j < 7; ++j) {
+                const T rc = __shfl_sync(FULL, mrow[j], c), rp = __shfl_sync(FULL, mrow[j], piv);
+                if (lane == c)
+                    mrow[j] = rp;
+                else if (lane == piv)
+                    mrow[j] = rc;
             }
+            T prow[7];
+#pragma unroll
+            for (int j = 0; j < 7; ++j) prow[j] = __shfl_sync(FULL, mrow[j], c);
+            if (lane > c && lane < 6) {
+                const T f = mrow[c] / prow[c];
+#pragma unroll
+                for (int j = c; j < 7; ++j) mrow[j] -= f * prow[j];
+            }
+        }
+        T eta[6];
+#pragma unroll
+        for (int i = 5; i >= 0; --i) {
+            T s = __shfl_sync(FULL, mrow[6], i);
+#pragma unroll
+            for (int j = i + 1; j < 6; ++j) s -= __shfl_sync(FULL, mrow[j], i) * eta[j];
+            eta[i] = s / __shfl_sync(FULL, mrow[i], i);
+        }
+        if (lane == 0) {
             T f = T(0);
 #pragma unroll
             for (int i = 0; i < 6; ++i) {
                 T s = T(0);
 #pragma unroll
-                for (int j = 0; j < 6; ++j) s += dC[i][j] * eta[j];
+                for (int j = 0; j < 6; ++j) s += dCs[6 * i + j] * eta[j];
                 f += e0[i] * s;
             }
             const T dHe = (T)R.lam * T(0.5) * f;
@@ -462,13 +547,10 @@ template cudaError_t launch_zone<double>(const ZoneArgs<double> &, int, cudaStre
 // ---- host tables --------------------------------------------------------------
 
 // Elimination schedule of the zone's 27 nodes in the reflected frame (the
-// site's cell = nodes with all coordinates in {1,2}).  Layout (uint16):
-//   [0, 27)   order of node rx + 3 ry + 9 rz
-//   [27, 55)  nb_off[k]: first entry of step k's column blocks (node orders > k)
-//   [55, 83)  pr_off[k]: first entry of step k's block updates (I | J << 8, I >= J)
-//   then the column-block entries, then the block-update entries.
-// Nodes share a block of K when they lie in a common zone cell (Chebyshev
-// distance <= 1); the symbolic factorisation adds the fill of each step.
+// site's cell = nodes with all coordinates in {1,2}); layout at the top of this
+// file.  Nodes share a block of K when they lie in a common zone cell
+// (Chebyshev distance <= 1); the symbolic factorisation adds the fill of each
+// step, and every block of the filled lower triangle gets a storage slot.
 std::vector<uint16_t> zone_schedule() {
     auto co = [](int n, int d) { return d == 0 ? n % 3 : d == 1 ? (n / 3) % 3 : n / 9; };
     auto cls = [&](int n) {
@@ -487,8 +569,6 @@ std::vector<uint16_t> zone_schedule() {
     for (int c = 2; c <= 3; ++c)
         for (int n = 0; n < 27; ++n)
             if (cls(n) == c) order.push_back(n);
-    std::vector<uint16_t> t(83, 0);
-    for (int i = 0; i < 27; ++i) t[order[i]] = (uint16_t)i;
     bool pat[27][27];
     for (int i = 0; i < 27; ++i)
         for (int j = 0; j < 27; ++j) {
@@ -497,31 +577,45 @@ std::vector<uint16_t> zone_schedule() {
             pat[i][j] = dmax <= 1;
         }
     std::vector<std::vector<int>> nb(27);
-    std::vector<std::vector<uint16_t>> pr(27);
+    std::vector<std::vector<std::pair<int, int>>> up(27);
     for (int k = 0; k < 27; ++k) {
         for (int i = k + 1; i < 27; ++i)
             if (pat[i][k]) nb[k].push_back(i);
         for (int I : nb[k])
             for (int J : nb[k])
                 if (J <= I) {
-                    pr[k].push_back((uint16_t)(I | (J << 8)));
+                    up[k].push_back({I, J});
                     pat[I][J] = pat[J][I] = true;
                 }
     }
-    size_t off = 83;
+    std::vector<uint16_t> t(ZS_HDR, 0);
+    for (int i = 0; i < 27; ++i) t[order[i]] = (uint16_t)i;
+    int slots = 0;
+    for (int I = 0; I < 27; ++I)
+        for (int J = 0; J < 27; ++J) t[ZS_BIDX + 27 * I + J] = 0xffff;
+    for (int I = 0; I < 27; ++I)
+        for (int J = 0; J <= I; ++J)
+            if (pat[I][J]) t[ZS_BIDX + 27 * I + J] = (uint16_t)slots++;
+    if (slots > ZSLOT_CAP) return {};
+    for (int k = 0; k < 27; ++k) t[ZS_DIAG + k] = t[ZS_BIDX + 28 * k];
+    size_t off = ZS_HDR;
     for (int k = 0; k <= 27; ++k) {
         t[ZS_NBOFF + k] = (uint16_t)off;
         if (k < 27) off += nb[k].size();
     }
     for (int k = 0; k <= 27; ++k) {
-        t[ZS_PROFF + k] = (uint16_t)off;
-        if (k < 27) off += pr[k].size();
+        t[ZS_UPOFF + k] = (uint16_t)off;
+        if (k < 27) off += 3 * up[k].size();
     }
     for (int k = 0; k < 27; ++k)
-        for (int i : nb[k]) t.push_back((uint16_t)i);
+        for (int I : nb[k]) t.push_back(t[ZS_BIDX + 27 * I + k]);
     for (int k = 0; k < 27; ++k)
-        for (uint16_t v : pr[k]) t.push_back(v);
-    if (t.size() > (size_t)ZSCHED_CAP) t.clear();
+        for (auto &ij : up[k]) {
+            t.push_back(t[ZS_BIDX + 27 * ij.first + ij.second]);
+            t.push_back(t[ZS_BIDX + 27 * ij.first + k]);
+            t.push_back(t[ZS_BIDX + 27 * ij.second + k]);
+        }
+    if (t.size() > (size_t)ZSCHED_CAP) return {};
     return t;
 }
 
