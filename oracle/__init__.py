@@ -201,6 +201,19 @@ def initial_uniaxial_strain(S_R, n, eps0):
     return eps0 / (N @ b) * b
 
 
+def initial_traction_strain(S_R, n, s0):
+    """Mean strain whose Reuss stress is the uniaxial stress s0 n(x)n."""
+    _, N, _ = axis_vectors(n)
+    return S_R @ (s0 * N)
+
+
+def update_traction_strain(E, mean_sig, S_R, n, s0):
+    """Stress control: move the mean strain by the Reuss compliance times the gap
+    between the prescribed uniaxial stress s0 n(x)n and the mean stress."""
+    _, N, _ = axis_vectors(n)
+    return E + S_R @ (s0 * N - mean_sig)
+
+
 def update_uniaxial_strain(E, mean_sig, S_R, n, eps0):
     """Remove the lateral part of the mean stress with the Reuss compliance, then
     put the axial strain n.E.n back to eps0 along the uniaxial-stress direction."""
@@ -444,7 +457,7 @@ def texture_histogram(kind, nbins, counts, A, St, n, c11, c12, c44):
 # The Monte Carlo step schedule (Sec. "Results": equilibrate, then one MC step)
 # ---------------------------------------------------------------------------
 
-BC_UNIAXIAL, BC_STRAIN6 = 0, 1
+BC_UNIAXIAL, BC_STRAIN6, BC_TRACTION = 0, 1, 2
 ELASTIC_OFF, ELASTIC_TRACTION = 0, 1
 
 
@@ -455,7 +468,7 @@ class OracleHMC:
     frozen, and (uniaxial control) one update of the mean strain."""
 
     def __init__(self, shape, Q, *, J=1.0, kT=0.7, c11=246.5, c12=147.3, c44=124.7,
-                 bc=BC_UNIAXIAL, load_axis=(0, 0, 1), strain=1e-3, strain6=None,
+                 bc=BC_UNIAXIAL, load_axis=(0, 0, 1), strain=1e-3, strain6=None, stress=0.0,
                  elastic_scale_=None, elastic=ELASTIC_TRACTION, trial=TRIAL_NEIGHBOR,
                  mpm_steps_per_mcs=50, dt=None, damping=None, seed=0, replica=0):
         self.shape = tuple(shape)  # (nz, ny, nx)
@@ -464,6 +477,7 @@ class OracleHMC:
         self.Q, self.J, self.kT = Q, J, kT
         self.c = (c11, c12, c44)
         self.bc, self.axis, self.eps0 = bc, np.asarray(load_axis, dtype=np.float64), strain
+        self.sig0 = stress
         self.strain6 = np.zeros(6) if strain6 is None else np.asarray(strain6, dtype=np.float64)
         self.lam = elastic_scale(max(nx, ny, nz)) if elastic_scale_ is None or elastic_scale_ < 0 else elastic_scale_
         self.elastic, self.trial = elastic, trial
@@ -480,6 +494,8 @@ class OracleHMC:
         self.S_R = reuss_compliance(self.St, orientation_counts(self.spins, self.Q))
         if self.bc == BC_UNIAXIAL:
             self.Ebar = initial_uniaxial_strain(self.S_R, self.axis, self.eps0)
+        elif self.bc == BC_TRACTION:
+            self.Ebar = initial_traction_strain(self.S_R, self.axis, self.sig0)
         else:
             self.Ebar = self.strain6.copy()
         self.u = np.zeros((self.nnodes, 3))
@@ -501,7 +517,23 @@ class OracleHMC:
     def end_mcs(self):
         if self.bc == BC_UNIAXIAL:
             self.Ebar = update_uniaxial_strain(self.Ebar, self.mean_sig, self.S_R, self.axis, self.eps0)
+        elif self.bc == BC_TRACTION:
+            self.Ebar = update_traction_strain(self.Ebar, self.mean_sig, self.S_R, self.axis, self.sig0)
         self.mcs += 1
+
+    def set_load(self, value):
+        """New uniaxial strain (UNIAXIAL) or stress (TRACTION); the mean strain
+        moves at once by the Reuss response to the change."""
+        _, N, _ = axis_vectors(self.axis)
+        if self.bc == BC_UNIAXIAL:
+            b = self.S_R @ N
+            self.Ebar = self.Ebar + (value - self.eps0) / (N @ b) * b
+            self.eps0 = value
+        elif self.bc == BC_TRACTION:
+            self.Ebar = self.Ebar + self.S_R @ ((value - self.sig0) * N)
+            self.sig0 = value
+        else:
+            raise ValueError("STRAIN6 has no scalar load")
 
     def mc_sweeps(self, n):
         total = 0
