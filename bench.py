@@ -421,12 +421,79 @@ def run_ensemble(args):
     return 0
 
 
+ZONE_FLOP_PER_TRIAL = 70_000   # assembly 8.1k adds, block Cholesky 56k, forward solve and G 4.6k, 6x6 solve 1k
+
+
+def run_zone(args):
+    """The 27-point constant-traction zone (HMC_ELASTIC_ZONE1) on the 128^3
+    microstructure: whole MCS timed with CUDA events, plus the zone half sweep
+    alone (trial list, spin copy, zone kernel) against the ALU roofline."""
+    import torch
+    torch.cuda.set_device(0)
+    import hmc_synth as S
+    import paper_1009_0457_gb300 as G
+    spec, euler, spins = S.workload_inputs("ni128")
+    stream = torch.cuda.Stream()
+    nz, ny, nx = spec["shape"]
+    kw = dict(S.COMMON)
+    g = G.HMC(spec["shape"], spec["Q"], precision=G.HMC_FP32, bc=G.HMC_BC_UNIAXIAL, load_axis=spec["axis"],
+              strain=spec["strain"], elastic=G.HMC_ELASTIC_ZONE1, mpm_steps_per_mcs=spec["mpm_steps"],
+              stream=stream.cuda_stream, **kw)
+    g.set_orientations(euler, spins)
+    G.lib.hmc_mc_sweeps(g.h, args.warmup, None)
+    g.synchronize()
+    N = nx * ny * nz
+    clocks = Clocks(0)
+    torch.cuda.synchronize()
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    st = G.lib.hmc_mc_sweeps(g.h, args.steps, None)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    assert st == 0, G.hmc_last_error(g.h)
+    t = e0.elapsed_time(e1) / 1e3
+    # the zone half sweep alone, both colours, on the current state
+    half_ms, trials = [], []
+    for c in (0, 1, 0, 1):
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        assert G.lib.hmc_sweep_half(g.h, c, None) == 0
+        a1.record(stream)
+        torch.cuda.synchronize()
+        half_ms.append(a0.elapsed_time(a1))
+        trials.append(g.info().zone_trials)
+    ms = float(np.mean(half_ms))
+    ntr = float(np.mean(trials))
+    achieved = ZONE_FLOP_PER_TRIAL * ntr / (ms * 1e-3) / 1e12
+    peak = 152 * 128 * 2 * 2.070e3 / 1e6
+    line = {"metric": METRIC, "value": N * args.steps / t, "unit": "site-updates/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "zone128: the 128^3 Ni polycrystal (Q=256, 5000 Voronoi grains, uniaxial 2e-3 "
+                                   "along [001]) with the 27-point constant-traction zone, 50 MPM steps per MCS",
+                       "sites": N},
+            "zone_half_sweep_ms": ms, "zone_trials_per_half_sweep": ntr,
+            "roofline": {"kernel": "k_zone<float> (27-point zone, one warp per trial)", "bound": "alu",
+                         "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                         "traffic": None,
+                         "algorithmic": f"{ZONE_FLOP_PER_TRIAL} flop/trial x {ntr:.0f} trials per half sweep",
+                         "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"},
+            "gpu_launches": args.steps * (spec["mpm_steps"] + 2 + 2 * 2), "clocks": clk}
+    print(json.dumps(line), flush=True)
+    g.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "ensemble":
         return run_ensemble(args)
+    if args.workload == "zone128":
+        return run_zone(args)
     return run_ours(args)
 
 

@@ -61,8 +61,13 @@ typedef enum {
 /* Loading control.  UNIAXIAL: the mean strain along load_axis is held at
  * `strain` and the other five mean stresses are driven to zero once per
  * Monte Carlo step (traction-free sides of a periodic cell).  STRAIN6: all six
- * mean strain components are prescribed by `strain6`. */
-enum { HMC_BC_UNIAXIAL = 0, HMC_BC_STRAIN6 = 1 };
+ * mean strain components are prescribed by `strain6`.  TRACTION: uniaxial
+ * stress `stress` (GPa) along load_axis, the loading of Sec. "Results" (a cube
+ * under a uniaxial tension): once per Monte Carlo step the mean strain moves by
+ * the Reuss compliance of the initial volume fractions times the gap between
+ * the prescribed and the mean stress; it starts at the Reuss strain of the
+ * prescribed stress. */
+enum { HMC_BC_UNIAXIAL = 0, HMC_BC_STRAIN6 = 1, HMC_BC_TRACTION = 2 };
 /* Elastic term of the trial energy: off (pure Potts); the one-point
  * constant-traction zone shift w(q_old) - w(q_new), w(q) = 1/2 s.S'(q).s
  * (Eqs. 6-8), from the stress of the last stress pass; or the zone of the 27
@@ -105,6 +110,7 @@ typedef struct {
     uint64_t seed;               /* Philox key of the trial stream                    */
     uint32_t replica;            /* third Philox counter word (ensemble member)       */
     void *stream;                /* cudaStream_t for all work; NULL = library-owned   */
+    double stress;               /* TRACTION stress along load_axis, GPa               */
 } hmc_params;
 
 /* Scalars the library derived from the parameters, and its counters. */
@@ -114,6 +120,7 @@ typedef struct {
     uint32_t mcs;                /* Monte Carlo steps completed (Philox word 1)       */
     int32_t u_buffer;            /* which displacement buffer holds the current state */
     int64_t n_sites, n_nodes;
+    int64_t zone_trials;         /* ZONE1: trials the last half sweep listed (all replicas) */
 } hmc_info;
 
 /* Fill *p with defaults: 32^3, Q = 64, J = 1, kT = 0.7, Ni constants
@@ -240,6 +247,15 @@ hmc_status hmc_set_stress(hmc_handle *h, const double *sigma);
 /* Nodal displacement and velocity (nnodes x 3 doubles each; either NULL). */
 hmc_status hmc_get_nodal(hmc_handle *h, double *u, double *v);
 hmc_status hmc_set_nodal(hmc_handle *h, const double *u, const double *v);
+
+/* New scalar load of the selected replica, e.g. one substep of a loading
+ * ramp: the uniaxial strain (UNIAXIAL) or stress in GPa (TRACTION).  The mean
+ * strain moves at once by the Reuss response to the change (UNIAXIAL: along
+ * S_R n(x)n to the new axial strain; TRACTION: by S_R (change) n(x)n); the
+ * control loop then acts at the end of each Monte Carlo step.  HMC_ERR_ARG for
+ * STRAIN6 (use hmc_set_strain) or a non-finite value.  The load is a parameter,
+ * not part of hmc_get_state. */
+hmc_status hmc_set_load(hmc_handle *h, double value);
 
 /* Mean strain Ebar (6, Voigt engineering). */
 hmc_status hmc_get_strain(hmc_handle *h, double *strain_bar);

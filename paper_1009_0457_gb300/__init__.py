@@ -18,7 +18,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libhmc.so")
 
 HMC_OK, HMC_ERR_ARG, HMC_ERR_CUDA, HMC_ERR_OOM, HMC_ERR_STATE, HMC_ERR_NONFINITE, HMC_ERR_TIMEOUT = 0, -1, -2, -3, -4, -5, -6
-HMC_BC_UNIAXIAL, HMC_BC_STRAIN6 = 0, 1
+HMC_BC_UNIAXIAL, HMC_BC_STRAIN6, HMC_BC_TRACTION = 0, 1, 2
 HMC_ELASTIC_OFF, HMC_ELASTIC_TRACTION, HMC_ELASTIC_ZONE1 = 0, 1, 2
 HMC_TRIAL_NEIGHBOR, HMC_TRIAL_UNIFORM_Q = 0, 1
 HMC_FP64, HMC_FP32 = 0, 1
@@ -44,6 +44,7 @@ class hmc_params(C.Structure):
         ("seed", C.c_uint64),
         ("replica", C.c_uint32),
         ("stream", C.c_void_p),
+        ("stress", C.c_double),
     ]
 
 
@@ -53,6 +54,7 @@ class hmc_info(C.Structure):
         ("strain_bar", C.c_double * 6),
         ("mcs", C.c_uint32), ("u_buffer", C.c_int32),
         ("n_sites", C.c_int64), ("n_nodes", C.c_int64),
+        ("zone_trials", C.c_int64),
     ]
 
 
@@ -94,6 +96,7 @@ def _load():
         "hmc_set_nodal": (st, [H, dp, dp]),
         "hmc_get_strain": (st, [H, dp]),
         "hmc_set_strain": (st, [H, dp]),
+        "hmc_set_load": (st, [H, C.c_double]),
         "hmc_get_info": (st, [H, C.POINTER(hmc_info)]),
         "hmc_get_state": (st, [H, C.c_void_p, C.POINTER(C.c_size_t)]),
         "hmc_set_state": (st, [H, C.c_void_p, C.c_size_t]),
@@ -266,6 +269,10 @@ def hmc_set_strain(h, e):
     _check(h, lib.hmc_set_strain(h, _ptr(e, C.c_double)))
 
 
+def hmc_set_load(h, value):
+    _check(h, lib.hmc_set_load(h, float(value)))
+
+
 def hmc_get_info(h) -> hmc_info:
     i = hmc_info()
     _check(h, lib.hmc_get_info(h, C.byref(i)))
@@ -405,6 +412,9 @@ class HMC:
 
     def set_strain(self, e):
         hmc_set_strain(self.h, e)
+
+    def set_load(self, value):
+        hmc_set_load(self.h, value)
 
     def info(self):
         return hmc_get_info(self.h)

@@ -392,7 +392,8 @@ std::string validate(const hmc_params *p) {
     for (double x : vals)
         if (!std::isfinite(x)) return "non-finite parameter";
     if (p->kT < 0) return "kT must be >= 0";
-    if (p->bc != HMC_BC_UNIAXIAL && p->bc != HMC_BC_STRAIN6) return "bad bc";
+    if (p->bc != HMC_BC_UNIAXIAL && p->bc != HMC_BC_STRAIN6 && p->bc != HMC_BC_TRACTION) return "bad bc";
+    if (!std::isfinite(p->stress)) return "non-finite stress";
     if (p->elastic != HMC_ELASTIC_OFF && p->elastic != HMC_ELASTIC_TRACTION && p->elastic != HMC_ELASTIC_ZONE1)
         return "bad elastic";
     if (p->elastic == HMC_ELASTIC_ZONE1 && (p->nx < 6 || p->ny < 6 || p->nz < 6))
@@ -403,7 +404,7 @@ std::string validate(const hmc_params *p) {
     if (p->damping >= 1.0) return "damping must be < 1";
     // cubic stability: C11 - C12 > 0, C11 + 2 C12 > 0, C44 > 0
     if (!(p->c11 - p->c12 > 0 && p->c11 + 2 * p->c12 > 0 && p->c44 > 0)) return "stiffness not positive definite";
-    if (p->bc == HMC_BC_UNIAXIAL) {
+    if (p->bc == HMC_BC_UNIAXIAL || p->bc == HMC_BC_TRACTION) {
         const double n2 = p->load_axis[0] * p->load_axis[0] + p->load_axis[1] * p->load_axis[1] +
                           p->load_axis[2] * p->load_axis[2];
         if (!(n2 > 0) || !std::isfinite(n2)) return "load_axis must be a non-zero finite vector";
@@ -732,7 +733,7 @@ hmc_status hmc_batch_create(const hmc_params *params, int32_t n_replicas, hmc_ha
         const int K = std::max(R.p.nx, std::max(R.p.ny, R.p.nz));
         R.lam = R.p.elastic_scale >= 0 ? R.p.elastic_scale : 1e9 * (1.0 / K) * kL0 * kGammaStar / (2.0 * kGammaS);
         R.lam_sd_half = 0.5 * R.lam * (h->S11 - h->S12 - 0.5 * h->S44);
-        if (R.p.bc == HMC_BC_UNIAXIAL) {
+        if (R.p.bc == HMC_BC_UNIAXIAL || R.p.bc == HMC_BC_TRACTION) {
             const double n = std::sqrt(R.p.load_axis[0] * R.p.load_axis[0] + R.p.load_axis[1] * R.p.load_axis[1] +
                                        R.p.load_axis[2] * R.p.load_axis[2]);
             for (int i = 0; i < 3; ++i) R.axis[i] = R.p.load_axis[i] / n;
@@ -935,6 +936,14 @@ hmc_status hmc_set_orientations(hmc_handle *h, const double *euler, const uint16
             d.axNB = 0;
             for (int i = 0; i < 6; ++i) d.axNB += d.axN[i] * d.axB[i];
             for (int i = 0; i < 6; ++i) d.ebar[i] = R.p.strain / d.axNB * d.axB[i];
+        } else if (R.p.bc == HMC_BC_TRACTION) {
+            axis_vectors(R.axis, d.axN, d.axNs);
+            d.sig0 = R.p.stress;
+            for (int i = 0; i < 6; ++i) {
+                double e = 0;
+                for (int j = 0; j < 6; ++j) e += d.sr[6 * i + j] * d.sig0 * d.axN[j];
+                d.ebar[i] = e;
+            }
         } else {
             for (int i = 0; i < 6; ++i) d.ebar[i] = R.p.strain6[i];
         }
@@ -1300,6 +1309,39 @@ hmc_status hmc_set_strain(hmc_handle *h, const double *e) {
     return HMC_OK;
 }
 
+hmc_status hmc_set_load(hmc_handle *h, double value) {
+    if (h) ++h->state_version;
+    hmc_status s = need_oriented(h);
+    if (s != HMC_OK) return s;
+    if (!std::isfinite(value)) return fail(h, HMC_ERR_ARG, "non-finite load");
+    const int bc = selr(h).p.bc;
+    if (bc != HMC_BC_UNIAXIAL && bc != HMC_BC_TRACTION) return fail(h, HMC_ERR_ARG, "STRAIN6 has no scalar load");
+    DevState st;
+    HMC_CK(h, cudaMemcpyAsync(&st, sel_st(h), sizeof(st), cudaMemcpyDeviceToHost, h->stream), "download");
+    HMC_CK(h, cudaStreamSynchronize(h->stream), "sync");
+    if (bc == HMC_BC_UNIAXIAL) {
+        for (int i = 0; i < 6; ++i) st.ebar[i] += (value - st.eps0) / st.axNB * st.axB[i];
+        st.eps0 = value;
+    } else {
+        double e[6];
+        for (int i = 0; i < 6; ++i) {
+            double d = 0;
+            for (int j = 0; j < 6; ++j) d += st.sr[6 * i + j] * (value - st.sig0) * st.axN[j];
+            e[i] = st.ebar[i] + d;
+        }
+        for (int i = 0; i < 6; ++i) st.ebar[i] = e[i];
+        st.sig0 = value;
+    }
+    for (int i = 0; i < 6; ++i) st.ebar_f[i] = (float)st.ebar[i];
+    DevState *d = sel_st(h);
+    HMC_CK(h, cudaMemcpyAsync(d->ebar, st.ebar, sizeof(st.ebar), cudaMemcpyHostToDevice, h->stream), "upload");
+    HMC_CK(h, cudaMemcpyAsync(d->ebar_f, st.ebar_f, sizeof(st.ebar_f), cudaMemcpyHostToDevice, h->stream), "upload");
+    HMC_CK(h, cudaMemcpyAsync(&d->eps0, &st.eps0, sizeof(double), cudaMemcpyHostToDevice, h->stream), "upload");
+    HMC_CK(h, cudaMemcpyAsync(&d->sig0, &st.sig0, sizeof(double), cudaMemcpyHostToDevice, h->stream), "upload");
+    HMC_CK(h, cudaStreamSynchronize(h->stream), "sync");
+    return HMC_OK;
+}
+
 hmc_status hmc_get_info(hmc_handle *h, hmc_info *info) {
     if (!h) return HMC_ERR_ARG;
     if (!info) return fail(h, HMC_ERR_ARG, "NULL info");
@@ -1315,6 +1357,12 @@ hmc_status hmc_get_info(hmc_handle *h, hmc_info *info) {
     info->u_buffer = h->cur;
     info->n_sites = R.N;
     info->n_nodes = R.nblk;
+    info->zone_trials = 0;
+    if (h->zone_count) {
+        unsigned n = 0;
+        HMC_CK(h, cudaMemcpy(&n, h->zone_count, sizeof(n), cudaMemcpyDeviceToHost), "download");
+        info->zone_trials = n;
+    }
     return HMC_OK;
 }
 

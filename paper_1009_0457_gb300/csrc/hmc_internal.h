@@ -42,6 +42,7 @@ struct DevState {
     unsigned long long unlike;     // unlike-bond count of the last statistics pass
     int32_t nonfinite;       // set when a reduction produced a non-finite value
     int32_t bad_spin;        // set by the upload check when a spin is >= Q
+    double sig0;             // prescribed uniaxial stress (traction control)
 };
 
 // One replica of a batch (a single handle is a batch of one).  Replica r's

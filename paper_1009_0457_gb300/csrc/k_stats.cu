@@ -201,6 +201,19 @@ __global__ void __launch_bounds__(256) k_end_mcs(const Replica *reps, const doub
                 st->ebar_f[i] = (float)st->ebar[i];
             }
         }
+        if (update_strain && st->bc == 2 && !bad) {
+            // stress control: Ebar += S_R (sig0 n(x)n - <sigma>)
+            double e[6];
+            for (int i = 0; i < 6; ++i) {
+                double d = 0.0;
+                for (int j = 0; j < 6; ++j) d += st->sr[6 * i + j] * (st->sig0 * st->axN[j] - mean[j]);
+                e[i] = st->ebar[i] + d;
+            }
+            for (int i = 0; i < 6; ++i) {
+                st->ebar[i] = e[i];
+                st->ebar_f[i] = (float)e[i];
+            }
+        }
         if (advance) st->mcs += 1;
     }
 }
