@@ -161,15 +161,35 @@ struct Row24<double> {
     }
 };
 
+// Explicitly rounded product and fused multiply-add, so that every kernel and
+// variant evaluates a dot product in the same order with the same roundings.
+__device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double rmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float rfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double rfma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// Row i of sigma = C e: C_i0 e0, then C_ij e_j added by fused multiply-adds in
+// j order (the order of the paired-FMA variant of the MPM step, which is
+// therefore bit-identical).
+template <typename T>
+__device__ __forceinline__ T hooke_row(T c0, T c1, T c2, T c3, T c4, T c5, const T (&e)[6]) {
+    T s = rmul(c0, e[0]);
+    s = rfma(c1, e[1], s);
+    s = rfma(c2, e[2], s);
+    s = rfma(c3, e[3], s);
+    s = rfma(c4, e[4], s);
+    return rfma(c5, e[5], s);
+}
+
 // sigma = C e with the 21 upper-triangle entries c00 c01 .. c05 c11 .. c55.
 template <typename T>
 __device__ __forceinline__ void hooke21(const T *c, const T (&e)[6], T (&s)[6]) {
-    s[0] = c[0] * e[0] + c[1] * e[1] + c[2] * e[2] + c[3] * e[3] + c[4] * e[4] + c[5] * e[5];
-    s[1] = c[1] * e[0] + c[6] * e[1] + c[7] * e[2] + c[8] * e[3] + c[9] * e[4] + c[10] * e[5];
-    s[2] = c[2] * e[0] + c[7] * e[1] + c[11] * e[2] + c[12] * e[3] + c[13] * e[4] + c[14] * e[5];
-    s[3] = c[3] * e[0] + c[8] * e[1] + c[12] * e[2] + c[15] * e[3] + c[16] * e[4] + c[17] * e[5];
-    s[4] = c[4] * e[0] + c[9] * e[1] + c[13] * e[2] + c[16] * e[3] + c[18] * e[4] + c[19] * e[5];
-    s[5] = c[5] * e[0] + c[10] * e[1] + c[14] * e[2] + c[17] * e[3] + c[19] * e[4] + c[20] * e[5];
+    s[0] = hooke_row<T>(c[0], c[1], c[2], c[3], c[4], c[5], e);
+    s[1] = hooke_row<T>(c[1], c[6], c[7], c[8], c[9], c[10], e);
+    s[2] = hooke_row<T>(c[2], c[7], c[11], c[12], c[13], c[14], e);
+    s[3] = hooke_row<T>(c[3], c[8], c[12], c[15], c[16], c[17], e);
+    s[4] = hooke_row<T>(c[4], c[9], c[13], c[16], c[18], c[19], e);
+    s[5] = hooke_row<T>(c[5], c[10], c[14], c[17], c[19], c[20], e);
 }
 
 template <typename T>

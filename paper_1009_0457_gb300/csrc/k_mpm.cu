@@ -168,6 +168,11 @@ __device__ __forceinline__ void cell_gradients31(const T (&u)[8][3], CellGrad<T>
 template <typename T, bool PAIR>
 __device__ __forceinline__ void cell_forces(const T (&u)[8][3], const uint4 &sp, const T *__restrict__ ctab,
                                             const float *__restrict__ cpairs, const T (&eb)[6], T (&f)[8][3]) {
+    // the first point's stiffness row is requested before the gradients are formed, so that
+    // its load latency overlaps them
+    HookeRow<T, PAIR> row;
+    uint32_t qprev = spin_of(sp, local_slot(0));
+    row.load(ctab, cpairs, qprev);
     CellGrad<T> g;
     cell_gradients31<T>(u, g);
     T tx[2][2][3], ty[2][2][3], tz[2][2][3];  // traction sums over a, b, c respectively
@@ -177,8 +182,6 @@ __device__ __forceinline__ void cell_forces(const T (&u)[8][3], const uint4 &sp,
         for (int j = 0; j < 2; ++j)
 #pragma unroll
             for (int d = 0; d < 3; ++d) tx[i][j][d] = ty[i][j][d] = tz[i][j][d] = T(0);
-    HookeRow<T, PAIR> row;
-    uint32_t qprev = 0xffffffffu;
 #pragma unroll
     for (int L = 0; L < 8; ++L) {
         const int a = L & 1, b = (L >> 1) & 1, c = L >> 2;
