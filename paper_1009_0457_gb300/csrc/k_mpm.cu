@@ -20,7 +20,8 @@
 // one contiguous range per resident CTA (a persistent grid of occupancy x
 // SMs), so every CTA marches about the same number of planes, over replicas of
 // any size, and pays the one-plane restart only where its range enters a new
-// tile.  The next node plane is read into registers before the cells of the
+// tile.  In a tile cut by a replica's high edges the needed cells are numbered
+// so that the active threads fill whole warps.  The next node plane is read into registers before the cells of the
 // current plane are computed and stored to shared memory after them.
 //
 // Scaling: the interpolation weights 3/4 and 1/4 of the trilinear shape
@@ -226,7 +227,6 @@ __global__ void __launch_bounds__(CX *CY, (sizeof(T) == 4 ? 2 : 1)) k_mpm_step(M
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
     const int tid = threadIdx.x;
-    const int lci = tid % CX, lcj = tid / CX;            // this thread's cell in the patch
     const T fscale = -a.dt_over_m * T(0.03125);          // -dt / (32 m)
     // this CTA's contiguous range of the linear (replica, tile, plane) index
     long long w = a.total * blockIdx.x / gridDim.x;
@@ -244,10 +244,13 @@ __global__ void __launch_bounds__(CX *CY, (sizeof(T) == 4 ? 2 : 1)) k_mpm_step(M
         const int kend = (int)min((long long)nbz, (long long)k0 + rem);
         w += kend - k0;
         const int i0 = (tile % SC.tiles_x) * OX, j0 = (tile / SC.tiles_x) * OY;
+        // cells needed by the tile's owned nodes: W x H (fewer at the high edges of the replica);
+        // they are numbered W-wide so that the active threads fill whole warps
+        const int W = min(CX, nbx - i0 + 1), H = min(CY, nby - j0 + 1);
+        const int lci = tid % W, lcj = tid / W;               // this thread's cell in the patch
+        const bool need = tid < W * H;
         const int ni = i0 - 1 + lci, nj = j0 - 1 + lcj;      // node at the cell's lower corner
-        const bool own = lci >= 1 && lcj >= 1 && ni < nbx && nj < nby;
-        // a cell is needed when some owned node uses it: local index <= last owned local index
-        const bool need = lci <= min(OX, nbx - i0) && lcj <= min(OY, nby - j0);
+        const bool own = need && lci >= 1 && lcj >= 1;
         const int gi = wrapi(ni, nbx), gj = wrapi(nj, nby);
         const int plane = nbx * nby;
         const long long col = R.blk_off + gi + nbx * gj;    // (i, j) column of this cell and node in the batch

@@ -77,8 +77,9 @@ __device__ __forceinline__ void store4<double>(double *p, const double (&v)[4]) 
 // Stress of the eight points of each cell from the current displacement; the
 // colour-packed stress array is what the half sweeps read.  Each CTA covers 256
 // blocks of one replica and writes its partial sums of sigma and of
-// 1/2 sigma.eps (FP64 across warps; within a warp FP32 TwoSum pairs or FP64,
-// by T) for a fixed-order final reduction.
+// 1/2 sigma.eps (a cell's eight points summed plainly, then FP32 TwoSum pairs or
+// FP64 within a warp, by T, and FP64 across warps) for a fixed-order final
+// reduction.
 template <typename T>
 __global__ void __launch_bounds__(BLOCK_THREADS) k_stress(StressArgs<T> a) {
     __shared__ double red[BLOCK_THREADS / 32][7];
@@ -112,6 +113,7 @@ __global__ void __launch_bounds__(BLOCK_THREADS) k_stress(StressArgs<T> a) {
         cell_gradients<T>(uc, g);
         const uint4 sp = __ldg(a.spins + R.blk_off + blk);
         T out[2][6][4];
+        T csum[7] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0)};   // this cell's eight points, plain sums
         Row24<T> row;
         uint32_t qprev = 0xffffffffu;
 #pragma unroll
@@ -129,11 +131,13 @@ __global__ void __launch_bounds__(BLOCK_THREADS) k_stress(StressArgs<T> a) {
 #pragma unroll
             for (int k = 0; k < 6; ++k) {
                 out[slot >> 2][k][slot & 3] = s[k];
-                acc.add(k, s[k]);
+                csum[k] += s[k];
                 w += s[k] * e[k];
             }
-            acc.add(6, T(0.5) * w);
+            csum[6] += T(0.5) * w;
         }
+#pragma unroll
+        for (int k = 0; k < 7; ++k) acc.add(k, csum[k]);
         T *sig = a.sig + 48ll * R.blk_off;
 #pragma unroll
         for (int c = 0; c < 2; ++c)
