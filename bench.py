@@ -129,9 +129,11 @@ def kernel_traffic(kernel):
     """Per-launch DRAM bytes from the committed ncu summary, if the kernel's
     source is unchanged since the capture (else None)."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
-    src = {"mpm": "k_mpm.cu", "sweep": "k_sweep.cu"}[kernel]
+    src = {"mpm": "k_mpm.cu", "sweep": "k_sweep.cu", "zone": "k_zone.cu"}[kernel]
     try:
-        sha = hashlib.sha256(open(os.path.join(ROOT, "paper_1009_0457_gb300", "csrc", src), "rb").read()).hexdigest()[:16]
+        csrc = os.path.join(ROOT, "paper_1009_0457_gb300", "csrc")
+        blob = b"".join(open(os.path.join(csrc, f), "rb").read() for f in (src, "hmc_device.cuh", "hmc_internal.h"))
+        sha = hashlib.sha256(blob).hexdigest()[:16]
         for line in open(path):
             f = line.split()
             if len(f) >= 4 and not line.startswith("#") and f[0] == kernel and f[1] == sha:
@@ -477,7 +479,7 @@ def run_zone(args):
             "zone_half_sweep_ms": ms, "zone_trials_per_half_sweep": ntr,
             "roofline": {"kernel": "k_zone<float> (27-point zone, one warp per trial)", "bound": "alu",
                          "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                         "traffic": None,
+                         "traffic": kernel_traffic("zone"),
                          "algorithmic": f"{ZONE_FLOP_PER_TRIAL} flop/trial x {ntr:.0f} trials per half sweep",
                          "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"},
             "gpu_launches": args.steps * (spec["mpm_steps"] + 2 + 2 * 2), "clocks": clk}
