@@ -87,7 +87,7 @@ class Clocks:
 
     def start(self):
         try:
-            d = os.path.join(ROOT, "gpurun_out") if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else None
+            d = os.environ.get("HMC_CLOCKS_DIR") or None   # where to keep the sampled clock log
             fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv", dir=d)
             os.close(fd)
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",

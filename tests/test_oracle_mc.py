@@ -35,7 +35,7 @@ def test_integer_threshold_equals_float_rule():
             assert not ((Fraction(T) + Fraction(1, 2)) / 2 ** 32 < p)
     assert O.accept_threshold(3, 1.0, 0.0) == 0.0
     assert O.accept_threshold(0, 1.0, 0.7) == 2 ** 32
-    # the SURVEY-quoted acceptances at kT = 0.7
+    # acceptance probabilities e^(-k / 0.7) for k = 1..5, to four digits
     for k, pk in zip(range(1, 6), (0.2397, 0.0574, 0.0138, 0.0033, 0.00079)):
         assert abs(O.accept_threshold(k, 1.0, 0.7) / 2 ** 32 - pk) < 0.0005 * max(1, pk * 100)
 
