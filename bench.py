@@ -144,6 +144,8 @@ def kernel_traffic(kernel):
 
 
 def mpm_variant_name(v):
+    if v == 6:
+        return "16x16 two cells per thread (paired FP32)"
     return ["16x16", "32x8", "8x32"][v % 3] + (" paired-FMA Hooke" if v >= 3 else "")
 
 

@@ -528,9 +528,9 @@ std::string tune_signature(const hmc_handle *h) {
 // Pick the MPM patch shape and persistent-grid size by timing every candidate
 // on scratch copies of the nodal state (the simulation state is not touched),
 // once per batch signature; HMC_AUTOTUNE=0 keeps the 16x16 default and
-// HMC_MPM_SHAPE forces one shape.  Every
-// candidate computes bit-identical results: the per-cell arithmetic and the
-// order of each node's force sum do not depend on the tiling.
+// HMC_MPM_SHAPE forces one variant.  Every candidate computes bit-identical
+// results: the per-cell arithmetic (explicitly rounded, in one order, paired or
+// not) and the order of each node's force sum do not depend on the variant.
 hmc_status ensure_tuned(hmc_handle *h) {
     if (h->tuned) return HMC_OK;
     hmc_status s = HMC_OK;
@@ -538,7 +538,7 @@ hmc_status ensure_tuned(hmc_handle *h) {
     const bool enabled = !(env && env[0] == '0');
     // HMC_MPM_SHAPE=<variant> forces an MPM variant (with its default grid), bypassing the tuner
     const char *forced = std::getenv("HMC_MPM_SHAPE");
-    const int nvar = h->p.precision == HMC_FP32 ? 2 * hmc::MPM_NSHAPES : hmc::MPM_NSHAPES;
+    const int nvar = hmc::mpm_nvariants(h->p.precision == HMC_FP32);
     if (forced && forced[0] >= '0' && forced[0] < '0' + nvar && forced[1] == 0) {
         const int shape = forced[0] - '0';
         if ((s = upload_sched(h, shape)) != HMC_OK) return s;
@@ -575,7 +575,7 @@ hmc_status ensure_tuned(hmc_handle *h) {
         cudaEventCreate(&e1);
         float best = 1e30f;
         cudaError_t err = cudaMemcpyAsync(vs, h->v, nb, cudaMemcpyDeviceToDevice, h->stream);
-        const int nvariants = h->p.precision == HMC_FP32 ? 2 * hmc::MPM_NSHAPES : hmc::MPM_NSHAPES;
+        const int nvariants = hmc::mpm_nvariants(h->p.precision == HMC_FP32);
         for (int shape = 0; shape < nvariants && err == cudaSuccess && s == HMC_OK; ++shape) {
             if ((s = upload_sched(h, shape)) != HMC_OK) break;
             for (int lim : {0, 1}) {

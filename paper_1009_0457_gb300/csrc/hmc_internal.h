@@ -135,8 +135,10 @@ struct ZoneArgs {
 
 // MPM patch shapes (cells per patch edge; owned nodes = cells - 1).  A variant
 // index v in [0, 2 * MPM_NSHAPES) selects shape v % MPM_NSHAPES; v >= MPM_NSHAPES
-// selects the paired-FMA Hooke product (FP32 only).
-enum MpmShape { MPM_16x16 = 0, MPM_32x8 = 1, MPM_8x32 = 2, MPM_NSHAPES = 3 };
+// selects the paired-FMA Hooke product (FP32 only); v = MPM_TWO_CELL is the
+// 16x16 shape with two cells per thread in paired FP32 registers (FP32 only).
+enum MpmShape { MPM_16x16 = 0, MPM_32x8 = 1, MPM_8x32 = 2, MPM_NSHAPES = 3, MPM_TWO_CELL = 6 };
+inline int mpm_nvariants(bool fp32) { return fp32 ? MPM_TWO_CELL + 1 : MPM_NSHAPES; }
 int mpm_shape_cx(int shape);
 int mpm_shape_cy(int shape);
 

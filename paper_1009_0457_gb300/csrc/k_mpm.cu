@@ -59,19 +59,28 @@ struct PlaneLoad {
     static constexpr int NX = CX + 1, NY = CY + 1, NN = NX * NY, NTHR = CX * CY;
     static constexpr int PER = (NN + NTHR - 1) / NTHR;
     T r[PER][3];
-    __device__ __forceinline__ void fetch(const T *__restrict__ u, long long node0, int i0, int j0, int k, int nbx,
-                                          int nby, int nbz) {
-        const int gk = wrapi(k, nbz);
+    int col[PER];   // this thread's tile nodes as (i + nbx j) in the replica's node plane
+    // once per tile: the periodic (i, j) of each node this thread loads
+    __device__ __forceinline__ void prepare(int i0, int j0, int nbx, int nby) {
+#pragma unroll
+        for (int m = 0; m < PER; ++m) {
+            const int t = threadIdx.x + m * NTHR;
+            const int li = t % NX, lj = t / NX;
+            col[m] = wrapi(i0 - 1 + li, nbx) + nbx * wrapi(j0 - 1 + lj, nby);
+        }
+    }
+    // node plane k, -1 <= k <= nbz (periodic in z)
+    __device__ __forceinline__ void fetch(const T *__restrict__ u, long long node0, int k, int nbz, int plane) {
+        const int gk = k < 0 ? k + nbz : (k >= nbz ? k - nbz : k);
+        const T *base = u + 3 * (node0 + (long long)plane * gk);
 #pragma unroll
         for (int m = 0; m < PER; ++m) {
             const int t = threadIdx.x + m * NTHR;
             if (t < NN) {
-                const int li = t % NX, lj = t / NX;
-                const int gi = wrapi(i0 - 1 + li, nbx), gj = wrapi(j0 - 1 + lj, nby);
-                const long long n = 3ll * (node0 + gi + nbx * (gj + nby * gk));
-                r[m][0] = __ldg(u + n);
-                r[m][1] = __ldg(u + n + 1);
-                r[m][2] = __ldg(u + n + 2);
+                const T *p = base + 3 * col[m];
+                r[m][0] = __ldg(p);
+                r[m][1] = __ldg(p + 1);
+                r[m][2] = __ldg(p + 2);
             }
         }
     }
@@ -176,6 +185,16 @@ __device__ __forceinline__ void cell_forces(const T (&u)[8][3], const uint4 &sp,
     row.load(ctab, cpairs, qprev);
     CellGrad<T> g;
     cell_gradients31<T>(u, g);
+    // the normal strains of a point are eb_k plus one gradient entry that two points share:
+    // add eb_k to those entries once
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            g.gx[i][j][0] = eb[0] + g.gx[i][j][0];
+            g.gy[i][j][1] = eb[1] + g.gy[i][j][1];
+            g.gz[i][j][2] = eb[2] + g.gz[i][j][2];
+        }
     T tx[2][2][3], ty[2][2][3], tz[2][2][3];  // traction sums over a, b, c respectively
 #pragma unroll
     for (int i = 0; i < 2; ++i)
@@ -187,7 +206,12 @@ __device__ __forceinline__ void cell_forces(const T (&u)[8][3], const uint4 &sp,
     for (int L = 0; L < 8; ++L) {
         const int a = L & 1, b = (L >> 1) & 1, c = L >> 2;
         T e[6], s[6];
-        point_strain<T>(g, eb, a, b, c, e);
+        e[0] = g.gx[b][c][0];
+        e[1] = g.gy[a][c][1];
+        e[2] = g.gz[a][b][2];
+        e[3] = eb[3] + (g.gz[a][b][1] + g.gy[a][c][2]);
+        e[4] = eb[4] + (g.gz[a][b][0] + g.gx[b][c][2]);
+        e[5] = eb[5] + (g.gy[a][c][0] + g.gx[b][c][1]);
         // points of one cell mostly share one orientation: fetch the row only when it changes
         const uint32_t q = spin_of(sp, local_slot(L));
         if (q != qprev) {
@@ -259,9 +283,10 @@ __global__ void __launch_bounds__(CX *CY, (sizeof(T) == 4 ? 2 : 1)) k_mpm_step(M
 
         PlaneLoad<T, CX, CY> pl;
         int b0 = 0, b1 = 1, b2 = 2;
-        pl.fetch(a.u_in, R.blk_off, i0, j0, k0 - 1, nbx, nby, nbz);
+        pl.prepare(i0, j0, nbx, nby);
+        pl.fetch(a.u_in, R.blk_off, k0 - 1, nbz, plane);
         pl.store(sm.us[b0]);
-        pl.fetch(a.u_in, R.blk_off, i0, j0, k0, nbx, nby, nbz);
+        pl.fetch(a.u_in, R.blk_off, k0, nbz, plane);
         pl.store(sm.us[b1]);
         uint4 sp = need ? __ldg(a.spins + col + (long long)plane * wrapi(k0 - 1, nbz)) : make_uint4(0, 0, 0, 0);
         __syncthreads();
@@ -278,7 +303,7 @@ __global__ void __launch_bounds__(CX *CY, (sizeof(T) == 4 ? 2 : 1)) k_mpm_step(M
                 for (int d = 0; d < 3; ++d) vold[d] = a.v[nidx + d];
             }
             const bool more = kk + 1 < kend;
-            if (more) pl.fetch(a.u_in, R.blk_off, i0, j0, kk + 2, nbx, nby, nbz);
+            if (more) pl.fetch(a.u_in, R.blk_off, kk + 2, nbz, plane);
             if (need) {
                 T u[8][3];
 #pragma unroll
@@ -310,9 +335,9 @@ __global__ void __launch_bounds__(CX *CY, (sizeof(T) == 4 ? 2 : 1)) k_mpm_step(M
                     for (int d = 0; d < 3; ++d) {
                         const T F = acc[d] + sm.fb[3][d][lcj - 1][lci - 1] + sm.fb[2][d][lcj - 1][lci] +
                                     sm.fb[1][d][lcj][lci - 1] + sm.fb[0][d][lcj][lci];
-                        const T vn = a.keep * vold[d] + fscale * F;
+                        const T vn = rfma(fscale, F, rmul(a.keep, vold[d]));
                         a.v[nidx + d] = vn;
-                        a.u_out[nidx + d] = sm.us[b0][d][lcj][lci] * T(32) + a.dt * vn;
+                        a.u_out[nidx + d] = rfma(a.dt, vn, sm.us[b0][d][lcj][lci] * T(32));
                     }
                 }
 #pragma unroll
@@ -326,6 +351,325 @@ __global__ void __launch_bounds__(CX *CY, (sizeof(T) == 4 ? 2 : 1)) k_mpm_step(M
             b1 = b2;
             b2 = t;
             sp = sp_next;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Two cells per thread.  Cells x and x+8 of a 16 x 16 patch are the two lanes of
+// float2 registers, and every floating-point step of the cell is one paired
+// instruction (__ffma2_rn, __fadd2_rn, __fmul2_rn) in the order and with the
+// roundings of the one-cell kernel above, so the two kernels give the same
+// bits.  128 threads per 16 x 16 patch, same tiles and schedule as the 16x16
+// shape; node planes are held as pairs (u(k), u(k+8)) for k = 0..8.
+// ---------------------------------------------------------------------------
+struct MpmSmem2 {
+    static constexpr int NY = 17, S2 = 24;   // node rows; pair columns (9 used), padded so that a
+                                             // half-warp's two rows fall in disjoint banks
+    float2 us[3][3][NY][S2];
+    float2 fb[4][3][16][8];   // cell contributions (cell k, cell k+8) to their lower corner nodes
+    float2 ft[4][3][16][8];   // ... to their upper corner nodes
+};
+
+__device__ __forceinline__ float2 p_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 p_neg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 p_sub(float2 a, float2 b) { return __fadd2_rn(a, p_neg(b)); }
+__device__ __forceinline__ float2 p_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 p_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+
+__device__ __forceinline__ void interp31_2(float2 d00, float2 d10, float2 d01, float2 d11, float2 (&o)[2][2]) {
+    const float2 three = make_float2(3.f, 3.f);
+    const float2 e00 = p_fma(three, d00, d10), e10 = p_fma(three, d10, d00);
+    const float2 e01 = p_fma(three, d01, d11), e11 = p_fma(three, d11, d01);
+    o[0][0] = p_fma(three, e00, e01);
+    o[0][1] = p_fma(three, e01, e00);
+    o[1][0] = p_fma(three, e10, e11);
+    o[1][1] = p_fma(three, e11, e10);
+}
+
+__device__ __forceinline__ float2 hooke_row2(const float2 (&c)[21], int i0, int i1, int i2, int i3, int i4, int i5,
+                                             const float2 (&e)[6]) {
+    float2 s = p_mul(c[i0], e[0]);
+    s = p_fma(c[i1], e[1], s);
+    s = p_fma(c[i2], e[2], s);
+    s = p_fma(c[i3], e[3], s);
+    s = p_fma(c[i4], e[4], s);
+    return p_fma(c[i5], e[5], s);
+}
+
+__device__ __forceinline__ void load_row_pair(const float *ctab, uint32_t qa, uint32_t qb, float2 (&c)[21]) {
+    Row24<float> ra, rb;
+    ra.load(ctab + 24ll * qa);
+    rb.load(ctab + 24ll * qb);
+#pragma unroll
+    for (int k = 0; k < 21; ++k) c[k] = make_float2(ra.v[k], rb.v[k]);
+}
+
+__device__ __forceinline__ void cell_forces2(const float2 (&u)[8][3], const uint4 &spa, const uint4 &spb,
+                                             const float *__restrict__ ctab, const float2 (&eb)[6],
+                                             float2 (&f)[8][3]) {
+    float2 row[21];
+    uint32_t qa = spin_of(spa, local_slot(0)), qb = spin_of(spb, local_slot(0));
+    load_row_pair(ctab, qa, qb, row);
+    float2 gx[2][2][3], gy[2][2][3], gz[2][2][3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        float2 o[2][2];
+        interp31_2(p_sub(u[corner(1, 0, 0)][d], u[corner(0, 0, 0)][d]), p_sub(u[corner(1, 1, 0)][d], u[corner(0, 1, 0)][d]),
+                   p_sub(u[corner(1, 0, 1)][d], u[corner(0, 0, 1)][d]), p_sub(u[corner(1, 1, 1)][d], u[corner(0, 1, 1)][d]), o);
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int c = 0; c < 2; ++c) gx[b][c][d] = o[b][c];
+        interp31_2(p_sub(u[corner(0, 1, 0)][d], u[corner(0, 0, 0)][d]), p_sub(u[corner(1, 1, 0)][d], u[corner(1, 0, 0)][d]),
+                   p_sub(u[corner(0, 1, 1)][d], u[corner(0, 0, 1)][d]), p_sub(u[corner(1, 1, 1)][d], u[corner(1, 0, 1)][d]), o);
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int c = 0; c < 2; ++c) gy[a][c][d] = o[a][c];
+        interp31_2(p_sub(u[corner(0, 0, 1)][d], u[corner(0, 0, 0)][d]), p_sub(u[corner(1, 0, 1)][d], u[corner(1, 0, 0)][d]),
+                   p_sub(u[corner(0, 1, 1)][d], u[corner(0, 1, 0)][d]), p_sub(u[corner(1, 1, 1)][d], u[corner(1, 1, 0)][d]), o);
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int b = 0; b < 2; ++b) gz[a][b][d] = o[a][b];
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            gx[i][j][0] = p_add(eb[0], gx[i][j][0]);
+            gy[i][j][1] = p_add(eb[1], gy[i][j][1]);
+            gz[i][j][2] = p_add(eb[2], gz[i][j][2]);
+        }
+    float2 tx[2][2][3], ty[2][2][3], tz[2][2][3];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+#pragma unroll
+            for (int d = 0; d < 3; ++d) tx[i][j][d] = ty[i][j][d] = tz[i][j][d] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int L = 0; L < 8; ++L) {
+        const int a = L & 1, b = (L >> 1) & 1, c = L >> 2;
+        float2 e[6], s[6];
+        e[0] = gx[b][c][0];
+        e[1] = gy[a][c][1];
+        e[2] = gz[a][b][2];
+        e[3] = p_add(eb[3], p_add(gz[a][b][1], gy[a][c][2]));
+        e[4] = p_add(eb[4], p_add(gz[a][b][0], gx[b][c][2]));
+        e[5] = p_add(eb[5], p_add(gy[a][c][0], gx[b][c][1]));
+        const uint32_t na = spin_of(spa, local_slot(L)), nb = spin_of(spb, local_slot(L));
+        if (na != qa || nb != qb) {
+            load_row_pair(ctab, na, nb, row);
+            qa = na;
+            qb = nb;
+        }
+        s[0] = hooke_row2(row, 0, 1, 2, 3, 4, 5, e);
+        s[1] = hooke_row2(row, 1, 6, 7, 8, 9, 10, e);
+        s[2] = hooke_row2(row, 2, 7, 11, 12, 13, 14, e);
+        s[3] = hooke_row2(row, 3, 8, 12, 15, 16, 17, e);
+        s[4] = hooke_row2(row, 4, 9, 13, 16, 18, 19, e);
+        s[5] = hooke_row2(row, 5, 10, 14, 17, 19, 20, e);
+        tx[b][c][0] = p_add(tx[b][c][0], s[0]); tx[b][c][1] = p_add(tx[b][c][1], s[5]); tx[b][c][2] = p_add(tx[b][c][2], s[4]);
+        ty[a][c][0] = p_add(ty[a][c][0], s[5]); ty[a][c][1] = p_add(ty[a][c][1], s[1]); ty[a][c][2] = p_add(ty[a][c][2], s[3]);
+        tz[a][b][0] = p_add(tz[a][b][0], s[4]); tz[a][b][1] = p_add(tz[a][b][1], s[3]); tz[a][b][2] = p_add(tz[a][b][2], s[2]);
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        float2 X[2][2], Y[2][2], Z[2][2];
+        interp31_2(tx[0][0][d], tx[1][0][d], tx[0][1][d], tx[1][1][d], X);
+        interp31_2(ty[0][0][d], ty[1][0][d], ty[0][1][d], ty[1][1][d], Y);
+        interp31_2(tz[0][0][d], tz[1][0][d], tz[0][1][d], tz[1][1][d], Z);
+#pragma unroll
+        for (int K = 0; K < 2; ++K)
+#pragma unroll
+            for (int J = 0; J < 2; ++J)
+#pragma unroll
+                for (int I = 0; I < 2; ++I) {
+                    const float2 fx = I ? X[J][K] : p_neg(X[J][K]);
+                    const float2 fy = J ? Y[I][K] : p_neg(Y[I][K]);
+                    const float2 fz = K ? Z[I][J] : p_neg(Z[I][J]);
+                    f[corner(I, J, K)][d] = p_add(p_add(fx, fy), fz);
+                }
+    }
+}
+
+// float index of cell or node k (0..16) in a row of pairs (k, k+8)
+__device__ __forceinline__ int pair_slot(int k) { return k < 8 ? 2 * k : 2 * (k - 8) + 1; }
+
+// 4-byte global -> shared copies that complete asynchronously (no register staging)
+__device__ __forceinline__ void cp_async4(float *smem_dst, const float *gsrc) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+__global__ void __launch_bounds__(128, 2) k_mpm_step2(MpmArgs<float> a) {
+    constexpr int CX = 16, CY = 16, OX = CX - 1, OY = CY - 1, NX = 17, NN = NX * NX, NT = 128;
+    constexpr int PER = (NN + NT - 1) / NT;
+    using S2 = MpmSmem2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    S2 &sm = *reinterpret_cast<S2 *>(smem_raw);
+    const int tid = threadIdx.x;
+    const int tx = tid & 7, ty = tid >> 3;   // cells (tx, ty) and (tx + 8, ty) of the patch
+    // The node planes hold u itself (the one-cell kernel holds u/32): strains, stresses and
+    // forces here are 32 times those of the one-cell kernel, the mean strain is taken times 32
+    // and the force constant over 32 -- exact powers of two, so every rounding is the same.
+    const float fscale = -a.dt_over_m * 0.03125f * 0.03125f;
+    long long w = a.total * blockIdx.x / gridDim.x;
+    const long long wend = a.total * (blockIdx.x + 1) / gridDim.x;
+    int r = 0;
+    while (w < wend) {
+        while (a.sched[r + 1].plane_off <= w) ++r;
+        const Replica &R = a.reps[r];
+        const MpmSched &SC = a.sched[r];
+        const int nbx = R.nbx, nby = R.nby, nbz = R.nbz;
+        const long long lw = w - SC.plane_off;
+        const int tile = (int)(lw / nbz);
+        const int k0 = (int)(lw - (long long)tile * nbz);
+        const long long rem = min(wend, a.sched[r + 1].plane_off) - w;
+        const int kend = (int)min((long long)nbz, (long long)k0 + rem);
+        w += kend - k0;
+        const int i0 = (tile % SC.tiles_x) * OX, j0 = (tile / SC.tiles_x) * OY;
+        const int W = min(CX, nbx - i0 + 1), H = min(CY, nby - j0 + 1);
+        const bool needa = tx < W && ty < H, needb = tx + 8 < W && ty < H;
+        const int plane = nbx * nby;
+        const long long cola = R.blk_off + wrapi(i0 - 1 + tx, nbx) + nbx * wrapi(j0 - 1 + ty, nby);
+        const long long colb = R.blk_off + wrapi(i0 + 7 + tx, nbx) + nbx * wrapi(j0 - 1 + ty, nby);
+        // owned nodes: (W-1) x (H-1), two per thread at most
+        const int ow = W - 1, no = (W - 1) * (H - 1);
+        int oi[2], oj[2];
+        long long ocol[2];
+#pragma unroll
+        for (int m = 0; m < 2; ++m) {
+            const int n = tid + m * NT;
+            oi[m] = 1 + n % ow;
+            oj[m] = 1 + n / ow;
+            ocol[m] = R.blk_off + wrapi(i0 - 1 + oi[m], nbx) + nbx * wrapi(j0 - 1 + oj[m], nby);
+        }
+        float2 eb[6];
+        {
+            float e1[6];
+            load_ebar<float>(R.st, e1);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) eb[k] = make_float2(32.f * e1[k], 32.f * e1[k]);
+        }
+        // node tile loads: node (li, lj) -> pair column li (lane x) and/or li - 8 (lane y)
+        int pcol[PER];
+#pragma unroll
+        for (int m = 0; m < PER; ++m) {
+            const int t = tid + m * NT;
+            pcol[m] = wrapi(i0 - 1 + t % NX, nbx) + nbx * wrapi(j0 - 1 + t / NX, nby);
+        }
+        // node plane k (-1 <= k <= nbz, periodic) into buffer b: node (li, lj) goes to pair li
+        // (lane x) and/or pair li - 8 (lane y)
+        auto fetch = [&](int k, int b) {
+            const int gk = k < 0 ? k + nbz : (k >= nbz ? k - nbz : k);
+            const float *base = a.u_in + 3 * (R.blk_off + (long long)plane * gk);
+#pragma unroll
+            for (int m = 0; m < PER; ++m) {
+                const int t = tid + m * NT;
+                if (t < NN) {
+                    const int li = t % NX, lj = t / NX;
+                    const float *src = base + 3 * pcol[m];
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        float *row = reinterpret_cast<float *>(&sm.us[b][d][lj][0]);
+                        if (li <= 8) cp_async4(row + 2 * li, src + d);
+                        if (li >= 8) cp_async4(row + 2 * (li - 8) + 1, src + d);
+                    }
+                }
+            }
+            cp_async_commit();
+        };
+        int b0 = 0, b1 = 1, b2 = 2;
+        fetch(k0 - 1, b0);
+        fetch(k0, b1);
+        cp_async_wait_all();
+        uint4 spa = needa ? __ldg(a.spins + cola + (long long)plane * wrapi(k0 - 1, nbz)) : make_uint4(0, 0, 0, 0);
+        uint4 spb = needb ? __ldg(a.spins + colb + (long long)plane * wrapi(k0 - 1, nbz)) : make_uint4(0, 0, 0, 0);
+        __syncthreads();
+
+        float acc[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+        for (int kk = k0 - 1; kk < kend; ++kk) {
+            uint4 spa_n = make_uint4(0, 0, 0, 0), spb_n = make_uint4(0, 0, 0, 0);
+            if (kk + 1 < kend) {
+                if (needa) spa_n = __ldg(a.spins + cola + (long long)plane * (kk + 1));
+                if (needb) spb_n = __ldg(a.spins + colb + (long long)plane * (kk + 1));
+            }
+            float vold[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+            const long long poff = (long long)plane * (kk < 0 ? 0 : kk);
+            if (kk >= k0) {
+#pragma unroll
+                for (int m = 0; m < 2; ++m)
+                    if (tid + m * NT < no)
+#pragma unroll
+                        for (int d = 0; d < 3; ++d) vold[m][d] = a.v[3 * (ocol[m] + poff) + d];
+            }
+            const bool more = kk + 1 < kend;
+            if (more) fetch(kk + 2, b2);   // b2 was last read before the previous plane's second barrier
+            if (needa || needb) {
+                float2 u[8][3];
+#pragma unroll
+                for (int K = 0; K < 2; ++K)
+#pragma unroll
+                    for (int J = 0; J < 2; ++J)
+#pragma unroll
+                        for (int I = 0; I < 2; ++I)
+#pragma unroll
+                            for (int d = 0; d < 3; ++d) u[corner(I, J, K)][d] = sm.us[K ? b1 : b0][d][ty + J][tx + I];
+                float2 f[8][3];
+                cell_forces2(u, spa, spb, a.ctab, eb, f);
+#pragma unroll
+                for (int J = 0; J < 2; ++J)
+#pragma unroll
+                    for (int I = 0; I < 2; ++I)
+#pragma unroll
+                        for (int d = 0; d < 3; ++d) {
+                            sm.fb[I + 2 * J][d][ty][tx] = f[corner(I, J, 0)][d];
+                            sm.ft[I + 2 * J][d][ty][tx] = f[corner(I, J, 1)][d];
+                        }
+            }
+            cp_async_wait_all();
+            __syncthreads();
+#pragma unroll
+            for (int m = 0; m < 2; ++m) {
+                if (tid + m * NT >= no) continue;
+                const int i = oi[m], j = oj[m];
+                const int sl = pair_slot(i - 1), sr = pair_slot(i);
+                if (kk >= k0) {
+                    const long long nidx = 3 * (ocol[m] + poff);
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        const float *f3 = reinterpret_cast<const float *>(&sm.fb[3][d][j - 1][0]);
+                        const float *f2 = reinterpret_cast<const float *>(&sm.fb[2][d][j - 1][0]);
+                        const float *f1 = reinterpret_cast<const float *>(&sm.fb[1][d][j][0]);
+                        const float *f0 = reinterpret_cast<const float *>(&sm.fb[0][d][j][0]);
+                        const float F = acc[m][d] + f3[sl] + f2[sr] + f1[sl] + f0[sr];
+                        const float vn = rfma(fscale, F, rmul(a.keep, vold[m][d]));
+                        a.v[nidx + d] = vn;
+                        const float *ur = reinterpret_cast<const float *>(&sm.us[b0][d][j][0]);
+                        a.u_out[nidx + d] = rfma(a.dt, vn, ur[i <= 8 ? 2 * i : 2 * (i - 8) + 1]);
+                    }
+                }
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    const float *f3 = reinterpret_cast<const float *>(&sm.ft[3][d][j - 1][0]);
+                    const float *f2 = reinterpret_cast<const float *>(&sm.ft[2][d][j - 1][0]);
+                    const float *f1 = reinterpret_cast<const float *>(&sm.ft[1][d][j][0]);
+                    const float *f0 = reinterpret_cast<const float *>(&sm.ft[0][d][j][0]);
+                    acc[m][d] = f3[sl] + f2[sr] + f1[sl] + f0[sr];
+                }
+            }
+            __syncthreads();
+            const int t = b0;
+            b0 = b1;
+            b1 = b2;
+            b2 = t;
+            spa = spa_n;
+            spb = spb_n;
         }
     }
 }
@@ -348,6 +692,9 @@ static cudaError_t set_attr() {
 
 cudaError_t mpm_prepare() {
     cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_mpm_step2, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)sizeof(MpmSmem2))) != cudaSuccess)
+        return e;
     if ((e = set_attr<float, 16, 16, false>()) != cudaSuccess || (e = set_attr<float, 32, 8, false>()) != cudaSuccess ||
         (e = set_attr<float, 8, 32, false>()) != cudaSuccess || (e = set_attr<float, 16, 16, true>()) != cudaSuccess ||
         (e = set_attr<float, 32, 8, true>()) != cudaSuccess || (e = set_attr<float, 8, 32, true>()) != cudaSuccess ||
@@ -372,6 +719,12 @@ static int per_sm_t(int shape) {
 
 template <>
 int mpm_per_sm<float>(int shape) {
+    if (shape == MPM_TWO_CELL) {
+        int n = 1;
+        const cudaError_t e =
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_mpm_step2, 128, sizeof(MpmSmem2));
+        return (e != cudaSuccess || n < 1) ? 1 : n;
+    }
     return per_sm_t<float, false>(shape % MPM_NSHAPES) < per_sm_t<float, true>(shape % MPM_NSHAPES)
                ? per_sm_t<float, false>(shape % MPM_NSHAPES)
                : per_sm_t<float, true>(shape % MPM_NSHAPES);
@@ -391,10 +744,13 @@ static void launch_t(const MpmArgs<T> &a, int shape, cudaStream_t s) {
         k_mpm_step<T, 16, 16, PAIR><<<a.grid, 256, smem_of<T, 16, 16>(), s>>>(a);
 }
 
-// shape in 0..2: scalar Hooke; shape + MPM_NSHAPES: paired-FMA Hooke (FP32 only)
+// shape in 0..2: scalar Hooke; shape + MPM_NSHAPES: paired-FMA Hooke (FP32 only);
+// MPM_TWO_CELL: two cells per thread (FP32 only)
 template <>
 cudaError_t launch_mpm_step<float>(const MpmArgs<float> &a, int shape, cudaStream_t s) {
-    if (shape >= MPM_NSHAPES)
+    if (shape == MPM_TWO_CELL)
+        k_mpm_step2<<<a.grid, 128, sizeof(MpmSmem2), s>>>(a);
+    else if (shape >= MPM_NSHAPES)
         launch_t<float, true>(a, shape - MPM_NSHAPES, s);
     else
         launch_t<float, false>(a, shape, s);

@@ -54,7 +54,7 @@ def test_batch_replicas_equal_solo_runs(G, precision):
     b.close()
 
 
-@pytest.mark.parametrize("variants", [("0", "1", "2"), ("3", "4", "5")])
+@pytest.mark.parametrize("variants", [("0", "1", "2"), ("3", "4", "5"), ("0", "6")])
 def test_patch_shapes_are_bitwise_equal(G, variants):
     shape = (10, 40, 50)
     eul = S.euler_uniform_so3(9, 2)
