@@ -54,16 +54,18 @@ def lib():
         L.orc_stress_field.argtypes = [i, i, i, u16p, dp, dp, dp, dp, dp, dp]
         L.orc_point_zone_shift.argtypes = [dp, dp, dp]
         L.orc_point_zone_shift.restype = C.c_double
+        L.orc_point_strain_shift.argtypes = [dp, dp, dp, dp]
+        L.orc_point_strain_shift.restype = C.c_double
         L.orc_accept_threshold.argtypes = [i, C.c_double, C.c_double]
         L.orc_accept_threshold.restype = C.c_double
         L.orc_site_trial.argtypes = [i, i, i, u16p, i, i, i, C.c_uint64, C.c_uint32, C.c_uint32,
-                                     C.c_double, C.c_double, i, i, i, C.c_double, dp, dp,
+                                     C.c_double, C.c_double, i, i, i, C.c_double, dp, dp, dp,
                                      u16p, dp, dp]
         L.orc_site_trial.restype = C.c_int
         L.orc_site_trial_at.argtypes = L.orc_site_trial.argtypes
         L.orc_site_trial_at.restype = C.c_int
         L.orc_half_sweep.argtypes = [i, i, i, u16p, i, C.c_uint64, C.c_uint32, C.c_uint32,
-                                     C.c_double, C.c_double, i, i, i, C.c_double, dp, dp,
+                                     C.c_double, C.c_double, i, i, i, C.c_double, dp, dp, dp,
                                      u8p, dp, dp]
         L.orc_half_sweep.restype = C.c_int64
         L.orc_unlike_bonds.argtypes = [i, i, i, u16p]
@@ -321,59 +323,73 @@ def stress_field(spins, Ct, u, Ebar):
 TRIAL_NEIGHBOR, TRIAL_UNIFORM_Q = 0, 1
 
 
+ELASTIC_OFF, ELASTIC_TRACTION, ELASTIC_ZONE1, ELASTIC_STRAIN = 0, 1, 2, 3
+
+
 def point_zone_shift(S_old, S_new, sig):
     a, b, s = _f64(S_old), _f64(S_new), _f64(sig)
     return lib().orc_point_zone_shift(_p(a, C.c_double), _p(b, C.c_double), _p(s, C.c_double))
+
+
+def point_strain_shift(S_old, C_old, C_new, sig):
+    """Constant-strain one-point shift 1/2 e.(C_new - C_old).e with e = S_old sig."""
+    a, b, c, s = _f64(S_old), _f64(C_old), _f64(C_new), _f64(sig)
+    return lib().orc_point_strain_shift(_p(a, C.c_double), _p(b, C.c_double), _p(c, C.c_double),
+                                        _p(s, C.c_double))
 
 
 def accept_threshold(k, J, kT):
     return lib().orc_accept_threshold(int(k), float(J), float(kT))
 
 
-def site_trial(spins, x, y, z, seed, mcs, replica, J, kT, trial, Q, elastic, lam, St, sig):
+def site_trial(spins, x, y, z, seed, mcs, replica, J, kT, trial, Q, elastic, lam, St, sig, Ct=None):
     nz, ny, nx = spins.shape
     s = np.ascontiguousarray(spins, dtype=np.uint16)
     Sf = _f64(St) if St is not None else np.zeros(36)
+    Cf = _f64(Ct) if Ct is not None else np.zeros_like(Sf)
     sg = _f64(sig) if sig is not None else np.zeros(6 * nx * ny * nz)
     qn = np.zeros(1, dtype=np.uint16)
     dH = np.zeros(1)
     t = np.zeros(1)
     acc = lib().orc_site_trial(nx, ny, nz, _p(s, C.c_uint16), x, y, z, int(seed), int(mcs), int(replica),
                                float(J), float(kT), int(trial), int(Q), int(elastic), float(lam),
-                               _p(Sf, C.c_double), _p(sg, C.c_double), _p(qn, C.c_uint16),
+                               _p(Sf, C.c_double), _p(Cf, C.c_double), _p(sg, C.c_double), _p(qn, C.c_uint16),
                                _p(dH, C.c_double), _p(t, C.c_double))
     return bool(acc), int(qn[0]), float(dH[0]), float(t[0])
 
 
-def site_trial_at(spins, x, y, z, seed, mcs, replica, J, kT, trial, Q, elastic, lam, St, sig_p):
+def site_trial_at(spins, x, y, z, seed, mcs, replica, J, kT, trial, Q, elastic, lam, St, sig_p, Ct=None):
     """One trial with the site's own stress sig_p (6 values) instead of a whole field."""
     nz, ny, nx = spins.shape
     s = np.ascontiguousarray(spins, dtype=np.uint16)
     Sf = _f64(St) if St is not None else np.zeros(36)
+    Cf = _f64(Ct) if Ct is not None else np.zeros_like(Sf)
     sg = _f64(sig_p) if sig_p is not None else np.zeros(6)
     qn = np.zeros(1, dtype=np.uint16)
     dH = np.zeros(1)
     t = np.zeros(1)
     acc = lib().orc_site_trial_at(nx, ny, nz, _p(s, C.c_uint16), x, y, z, int(seed), int(mcs), int(replica),
                                   float(J), float(kT), int(trial), int(Q), int(elastic), float(lam),
-                                  _p(Sf, C.c_double), _p(sg, C.c_double), _p(qn, C.c_uint16),
+                                  _p(Sf, C.c_double), _p(Cf, C.c_double), _p(sg, C.c_double), _p(qn, C.c_uint16),
                                   _p(dH, C.c_double), _p(t, C.c_double))
     return bool(acc), int(qn[0]), float(dH[0]), float(t[0])
 
 
-def half_sweep(spins, colour, seed, mcs, replica, J, kT, trial, Q, elastic, lam, St, sig):
-    """In-place red/black half sweep; returns (accepted, changed[N] u8, dH[N], thresh[N])."""
+def half_sweep(spins, colour, seed, mcs, replica, J, kT, trial, Q, elastic, lam, St, sig, Ct=None):
+    """In-place red/black half sweep; returns (accepted, changed[N] u8, dH[N], thresh[N]).
+    elastic: 0 off, 1 constant-traction point zone (St), 3 constant-strain point zone (St, Ct)."""
     nz, ny, nx = spins.shape
     assert spins.dtype == np.uint16 and spins.flags.c_contiguous
     N = nx * ny * nz
     Sf = _f64(St) if St is not None else np.zeros(36)
+    Cf = _f64(Ct) if Ct is not None else np.zeros_like(Sf)
     sg = _f64(sig) if sig is not None else np.zeros(1)
     changed = np.zeros(N, dtype=np.uint8)
     dH = np.zeros(N)
     t = np.zeros(N)
     acc = lib().orc_half_sweep(nx, ny, nz, _p(spins, C.c_uint16), int(colour), int(seed), int(mcs), int(replica),
                                float(J), float(kT), int(trial), int(Q), int(elastic), float(lam),
-                               _p(Sf, C.c_double), _p(sg, C.c_double), _p(changed, C.c_uint8),
+                               _p(Sf, C.c_double), _p(Cf, C.c_double), _p(sg, C.c_double), _p(changed, C.c_uint8),
                                _p(dH, C.c_double), _p(t, C.c_double))
     return int(acc), changed, dH, t
 
@@ -458,7 +474,7 @@ def texture_histogram(kind, nbins, counts, A, St, n, c11, c12, c44):
 # ---------------------------------------------------------------------------
 
 BC_UNIAXIAL, BC_STRAIN6, BC_TRACTION = 0, 1, 2
-ELASTIC_OFF, ELASTIC_TRACTION = 0, 1
+# ELASTIC_* and TRIAL_* are defined with the Monte Carlo functions above
 
 
 class OracleHMC:
@@ -512,7 +528,7 @@ class OracleHMC:
     def half_sweep(self, colour):
         return half_sweep(self.spins, colour, self.seed, self.mcs, self.replica, self.J, self.kT,
                           self.trial, self.Q, self.elastic, self.lam, self.St,
-                          self.sig if self.elastic else None)
+                          self.sig if self.elastic else None, self.Ct)
 
     def end_mcs(self):
         if self.bc == BC_UNIAXIAL:

@@ -389,6 +389,24 @@ double orc_point_zone_shift(const double *S_old, const double *S_new, const doub
     return w_old - w_new;
 }
 
+/* Elastic shift of the single-point constant-strain zone (Eq. 8 read with the
+ * point's strain held fixed, e = S_old s): the change of its energy density,
+ * 1/2 e.(C_new - C_old).e. */
+double orc_point_strain_shift(const double *S_old, const double *C_old, const double *C_new, const double sig[6])
+{
+    double e[6];
+    for (int I = 0; I < 6; ++I) {
+        e[I] = 0.0;
+        for (int J = 0; J < 6; ++J) e[I] += S_old[6 * I + J] * sig[J];
+    }
+    double d = 0.0;
+    for (int I = 0; I < 6; ++I)
+        for (int J = 0; J < 6; ++J) d += 0.5 * e[I] * (C_new[6 * I + J] - C_old[6 * I + J]) * e[J];
+    return d;
+}
+
+enum { ORC_ELASTIC_OFF = 0, ORC_ELASTIC_TRACTION = 1, ORC_ELASTIC_STRAIN = 3 };
+
 /* Integer acceptance threshold of the Metropolis rule (Eq. 5) for an integer
  * bond-energy change k > 0: accept iff r1 < T(k), equivalent to
  * (r1 + 1/2) 2^-32 < exp(-k J / kT) for every 32-bit r1. */
@@ -410,7 +428,7 @@ enum { ORC_TRIAL_NEIGHBOR = 0, ORC_TRIAL_UNIFORM_Q = 1 };
 int orc_site_trial_at(int nx, int ny, int nz, const uint16_t *spin, int x, int y, int z,
                       uint64_t seed, uint32_t mcs, uint32_t replica, double J, double kT,
                       int trial_mode, int Q, int elastic, double lambda, const double *Stab,
-                      const double *sig_p, uint16_t *q_new, double *dH, double *thresh)
+                      const double *Ctab, const double *sig_p, uint16_t *q_new, double *dH, double *thresh)
 {
     int64_t p = (int64_t)x + (int64_t)nx * ((int64_t)y + (int64_t)ny * z);
     uint32_t ctr[4] = {(uint32_t)p, mcs, replica, 0u};
@@ -446,7 +464,11 @@ int orc_site_trial_at(int nx, int ny, int nz, const uint16_t *spin, int x, int y
     }
     int dE = n_old - n_new;
     double dHe = 0.0;
-    if (elastic) dHe = lambda * orc_point_zone_shift(Stab + 36 * (int64_t)q, Stab + 36 * (int64_t)qt, sig_p);
+    if (elastic == ORC_ELASTIC_TRACTION)
+        dHe = lambda * orc_point_zone_shift(Stab + 36 * (int64_t)q, Stab + 36 * (int64_t)qt, sig_p);
+    else if (elastic == ORC_ELASTIC_STRAIN)
+        dHe = lambda * orc_point_strain_shift(Stab + 36 * (int64_t)q, Ctab + 36 * (int64_t)q,
+                                              Ctab + 36 * (int64_t)qt, sig_p);
     if (dHe == 0.0) {
         *dH = J * dE;
         if (dE <= 0) return 1;
@@ -464,11 +486,11 @@ int orc_site_trial_at(int nx, int ny, int nz, const uint16_t *spin, int x, int y
 int orc_site_trial(int nx, int ny, int nz, const uint16_t *spin, int x, int y, int z,
                    uint64_t seed, uint32_t mcs, uint32_t replica, double J, double kT,
                    int trial_mode, int Q, int elastic, double lambda, const double *Stab,
-                   const double *sig, uint16_t *q_new, double *dH, double *thresh)
+                   const double *Ctab, const double *sig, uint16_t *q_new, double *dH, double *thresh)
 {
     int64_t p = (int64_t)x + (int64_t)nx * ((int64_t)y + (int64_t)ny * z);
     return orc_site_trial_at(nx, ny, nz, spin, x, y, z, seed, mcs, replica, J, kT, trial_mode, Q, elastic,
-                             lambda, Stab, elastic ? sig + 6 * p : NULL, q_new, dH, thresh);
+                             lambda, Stab, Ctab, elastic ? sig + 6 * p : NULL, q_new, dH, thresh);
 }
 
 /* Red/black half sweep (Sec. "Microstructural Evolution"): every site of one
@@ -478,7 +500,7 @@ int orc_site_trial(int nx, int ny, int nz, const uint16_t *spin, int x, int y, i
  * only this colour's sites written): changed flag, dH and threshold. */
 int64_t orc_half_sweep(int nx, int ny, int nz, uint16_t *spin, int colour, uint64_t seed,
                        uint32_t mcs, uint32_t replica, double J, double kT, int trial_mode, int Q,
-                       int elastic, double lambda, const double *Stab, const double *sig,
+                       int elastic, double lambda, const double *Stab, const double *Ctab, const double *sig,
                        uint8_t *changed, double *dH_out, double *thresh_out)
 {
     int64_t accepted = 0;
@@ -490,7 +512,7 @@ int64_t orc_half_sweep(int nx, int ny, int nz, uint16_t *spin, int colour, uint6
                 uint16_t qn;
                 double dH, t;
                 int acc = orc_site_trial(nx, ny, nz, spin, x, y, z, seed, mcs, replica, J, kT, trial_mode,
-                                         Q, elastic, lambda, Stab, sig, &qn, &dH, &t);
+                                         Q, elastic, lambda, Stab, Ctab, sig, &qn, &dH, &t);
                 if (changed) changed[p] = (uint8_t)acc;
                 if (dH_out) dH_out[p] = dH;
                 if (thresh_out) thresh_out[p] = t;
