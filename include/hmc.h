@@ -80,7 +80,11 @@ enum { HMC_BC_UNIAXIAL = 0, HMC_BC_STRAIN6 = 1, HMC_BC_TRACTION = 2 };
  * the zone seen at the site.  ZONE1 evaluates every trial against the spins as
  * they were at the start of the half step (the zone holds sites of the sweep's
  * own colour) and needs nx, ny, nz >= 6; it does not read the stored stress. */
-enum { HMC_ELASTIC_OFF = 0, HMC_ELASTIC_TRACTION = 1, HMC_ELASTIC_ZONE1 = 2 };
+enum { HMC_ELASTIC_OFF = 0, HMC_ELASTIC_TRACTION = 1, HMC_ELASTIC_ZONE1 = 2, HMC_ELASTIC_STRAIN = 3 };
+/* HMC_ELASTIC_STRAIN: the one-point zone with the point's strain held fixed
+ * instead of its stress (Eq. 8 read with the strain e = S'(q_old) s of the
+ * stored stress): 1/2 e.(C'(q_new) - C'(q_old)).e.  It also favours the softer
+ * orientation, with a different magnitude. */
 /* Trial orientation: copy a random one of the six neighbours, or draw
  * uniformly from 0..Q-1. */
 enum { HMC_TRIAL_NEIGHBOR = 0, HMC_TRIAL_UNIFORM_Q = 1 };
@@ -141,8 +145,8 @@ hmc_status hmc_create(const hmc_params *p, hmc_handle **out);
  * in nx, ny, nz, load_axis, strain, strain6, elastic_scale, seed and replica;
  * all other fields must be equal (HMC_ERR_ARG otherwise).  Each replica's
  * spins, stress and Monte Carlo stream are exactly those of the same
- * replica run alone.  hmc_create(p, out) is hmc_batch_create(p, 1, out). */
-hmc_status hmc_batch_create(const hmc_params *params, int32_t n_replicas, hmc_handle **out);
+ * replica run alone.  hmc_create(p, out) is hmc_create_batch(p, 1, out). */
+hmc_status hmc_create_batch(const hmc_params *params, int32_t n_replicas, hmc_handle **out);
 
 /* Select the replica that the per-replica accessors act on (hmc_set_spins,
  * hmc_get_spins, hmc_get/set_stress, hmc_get/set_nodal, hmc_get/set_strain,
@@ -182,6 +186,22 @@ hmc_status hmc_set_spins(hmc_handle *h, const uint16_t *spins);
 
 /* Copy the spin field out (N values, natural order). */
 hmc_status hmc_get_spins(hmc_handle *h, uint16_t *spins);
+
+/* Device-pointer forms for zero-copy exchange with other device code (for
+ * example a tensor's data pointer).  The pointer must be memory of the current
+ * device (device or managed), 16-byte aligned, and hold N uint16 values of the
+ * selected replica in natural order; it is read or written on the handle's
+ * stream and not retained.  HMC_ERR_ARG (nothing launched) for NULL, a
+ * misaligned pointer or one that is not device memory of this device.
+ * hmc_set_spins_dev validates the values on the device (HMC_ERR_ARG if one is
+ * >= Q, spins unchanged) and packs them; hmc_get_spins_dev unpacks into the
+ * buffer.  Both return after the copy has completed.
+ * hmc_set_orientations_dev is hmc_set_orientations with the spins of all
+ * replicas (back to back) in device memory; they pass through the host once,
+ * since the Reuss compliance is formed from their volume fractions there. */
+hmc_status hmc_set_spins_dev(hmc_handle *h, const uint16_t *d_spins);
+hmc_status hmc_get_spins_dev(hmc_handle *h, uint16_t *d_spins);
+hmc_status hmc_set_orientations_dev(hmc_handle *h, const double *euler_zyz, const uint16_t *d_spins);
 
 /* nsteps explicit MPM steps (Sec. "Elastic Deformation"): per material point
  * strain = Ebar + sym(grad u) from the trilinear nodal field, stress =

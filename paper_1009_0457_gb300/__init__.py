@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libhmc.so")
 
 HMC_OK, HMC_ERR_ARG, HMC_ERR_CUDA, HMC_ERR_OOM, HMC_ERR_STATE, HMC_ERR_NONFINITE, HMC_ERR_TIMEOUT = 0, -1, -2, -3, -4, -5, -6
 HMC_BC_UNIAXIAL, HMC_BC_STRAIN6, HMC_BC_TRACTION = 0, 1, 2
-HMC_ELASTIC_OFF, HMC_ELASTIC_TRACTION, HMC_ELASTIC_ZONE1 = 0, 1, 2
+HMC_ELASTIC_OFF, HMC_ELASTIC_TRACTION, HMC_ELASTIC_ZONE1, HMC_ELASTIC_STRAIN = 0, 1, 2, 3
 HMC_TRIAL_NEIGHBOR, HMC_TRIAL_UNIFORM_Q = 0, 1
 HMC_FP64, HMC_FP32 = 0, 1
 HMC_HIST_PER_Q, HMC_HIST_ANGLE_100, HMC_HIST_YOUNG = 0, 1, 2
@@ -75,7 +75,7 @@ def _load():
     sig = {
         "hmc_default_params": (None, [C.POINTER(hmc_params)]),
         "hmc_create": (st, [C.POINTER(hmc_params), C.POINTER(H)]),
-        "hmc_batch_create": (st, [C.POINTER(hmc_params), C.c_int32, C.POINTER(H)]),
+        "hmc_create_batch": (st, [C.POINTER(hmc_params), C.c_int32, C.POINTER(H)]),
         "hmc_select_replica": (st, [H, C.c_int32]),
         "hmc_get_tuning": (st, [H, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
         "hmc_destroy": (None, [H]),
@@ -96,6 +96,9 @@ def _load():
         "hmc_set_nodal": (st, [H, dp, dp]),
         "hmc_get_strain": (st, [H, dp]),
         "hmc_set_strain": (st, [H, dp]),
+        "hmc_set_spins_dev": (st, [H, C.c_void_p]),
+        "hmc_get_spins_dev": (st, [H, C.c_void_p]),
+        "hmc_set_orientations_dev": (st, [H, dp, C.c_void_p]),
         "hmc_set_load": (st, [H, C.c_double]),
         "hmc_get_info": (st, [H, C.POINTER(hmc_info)]),
         "hmc_get_state": (st, [H, C.c_void_p, C.POINTER(C.c_size_t)]),
@@ -147,11 +150,11 @@ def hmc_create(p: hmc_params):
     return h
 
 
-def hmc_batch_create(params):
+def hmc_create_batch(params):
     """One handle over len(params) replicas (a sequence of hmc_params)."""
     arr = (hmc_params * len(params))(*params)
     h = C.c_void_p()
-    _check(None, lib.hmc_batch_create(arr, len(params), C.byref(h)))
+    _check(None, lib.hmc_create_batch(arr, len(params), C.byref(h)))
     return h
 
 
@@ -178,6 +181,20 @@ def hmc_set_orientations(h, euler, spins):
 def hmc_set_spins(h, spins):
     s = np.ascontiguousarray(spins, dtype=np.uint16)
     _check(h, lib.hmc_set_spins(h, _ptr(s, C.c_uint16)))
+
+
+def hmc_set_spins_dev(h, d_spins):
+    """d_spins: device address (int) of N uint16 values, e.g. a tensor's data_ptr()."""
+    _check(h, lib.hmc_set_spins_dev(h, C.c_void_p(int(d_spins))))
+
+
+def hmc_get_spins_dev(h, d_spins):
+    _check(h, lib.hmc_get_spins_dev(h, C.c_void_p(int(d_spins))))
+
+
+def hmc_set_orientations_dev(h, euler, d_spins):
+    e = np.ascontiguousarray(euler, dtype=np.float64)
+    _check(h, lib.hmc_set_orientations_dev(h, _ptr(e, C.c_double), C.c_void_p(int(d_spins))))
 
 
 def hmc_get_spins(h, out):
@@ -442,7 +459,7 @@ class HMCBatch:
             d = dict(common)
             d.update(kw)
             self.params.append(hmc_default_params(nx=nx, ny=ny, nz=nz, n_orient=n_orient, **d))
-        self.h = hmc_batch_create(self.params)
+        self.h = hmc_create_batch(self.params)
         self.sel = 0
 
     def close(self):

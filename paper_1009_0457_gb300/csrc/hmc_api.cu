@@ -6,6 +6,7 @@
 // the kernels live in k_*.cu.
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -74,6 +75,7 @@ struct hmc_handle {
     uint4 *zone_work = nullptr, *snap = nullptr;
     unsigned *zone_count = nullptr;
     void *ktab = nullptr;
+    void *stab = nullptr;                 // compliance rows (constant-strain zone)
     uint16_t *zone_sched = nullptr;
     int zone_nsched = 0, zone_grid = 1;
     // grain count: union-find parents of the largest replica, root count and error word
@@ -284,9 +286,14 @@ cudaError_t enqueue_sweep(hmc_handle *h, int colour, cudaStream_t s) {
     a.nctas = h->nctas;
     a.work = h->zone_work;
     a.count = h->zone_count;
+    a.ctab = static_cast<const T *>(h->ctab);
+    a.stab = static_cast<const T *>(h->stab);
     if (h->p.elastic != HMC_ELASTIC_ZONE1)
-        return hmc::launch_sweep<T>(a, colour, h->p.elastic == HMC_ELASTIC_TRACTION ? hmc::SWEEP_POINT
-                                                                                     : hmc::SWEEP_POTTS, s);
+        return hmc::launch_sweep<T>(a, colour,
+                                    h->p.elastic == HMC_ELASTIC_TRACTION ? hmc::SWEEP_POINT
+                                    : h->p.elastic == HMC_ELASTIC_STRAIN ? hmc::SWEEP_STRAIN
+                                                                         : hmc::SWEEP_POTTS,
+                                    s);
     // 27-point zone: list the trials, copy the spins as they are at the start of the half step,
     // then decide every listed trial against that copy
     cudaError_t e;
@@ -394,7 +401,8 @@ std::string validate(const hmc_params *p) {
     if (p->kT < 0) return "kT must be >= 0";
     if (p->bc != HMC_BC_UNIAXIAL && p->bc != HMC_BC_STRAIN6 && p->bc != HMC_BC_TRACTION) return "bad bc";
     if (!std::isfinite(p->stress)) return "non-finite stress";
-    if (p->elastic != HMC_ELASTIC_OFF && p->elastic != HMC_ELASTIC_TRACTION && p->elastic != HMC_ELASTIC_ZONE1)
+    if (p->elastic != HMC_ELASTIC_OFF && p->elastic != HMC_ELASTIC_TRACTION && p->elastic != HMC_ELASTIC_ZONE1 &&
+        p->elastic != HMC_ELASTIC_STRAIN)
         return "bad elastic";
     if (p->elastic == HMC_ELASTIC_ZONE1 && (p->nx < 6 || p->ny < 6 || p->nz < 6))
         return "the 27-point zone needs grid edges >= 6";
@@ -447,7 +455,8 @@ void destroy_buffers(hmc_handle *h) {
         if (h->gexec[i]) cudaGraphExecDestroy(h->gexec[i]);
     void *bufs[] = {h->spins, h->stage16, h->u[0], h->u[1], h->v, h->sig, h->ctab, h->ctab_pairs, h->wtab, h->thr, h->counts,
                     h->bins, h->partials, h->fractions, h->binmap, h->st, h->d_reps, h->d_cta_rep, h->d_sched,
-                    h->zone_work, h->snap, h->zone_count, h->ktab, h->zone_sched, h->cc_parent, h->cc_count};
+                    h->zone_work, h->snap, h->zone_count, h->ktab, h->zone_sched, h->cc_parent, h->cc_count,
+                    h->stab};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (h->cap) cudaStreamDestroy(h->cap);
@@ -692,7 +701,7 @@ void hmc_default_params(hmc_params *p) {
     p->stream = nullptr;
 }
 
-hmc_status hmc_batch_create(const hmc_params *params, int32_t n_replicas, hmc_handle **out) {
+hmc_status hmc_create_batch(const hmc_params *params, int32_t n_replicas, hmc_handle **out) {
     if (!out) return fail(nullptr, HMC_ERR_ARG, "out is NULL");
     *out = nullptr;
     if (!params || n_replicas < 1) return fail(nullptr, HMC_ERR_ARG, "need params for at least one replica");
@@ -831,6 +840,9 @@ hmc_status hmc_batch_create(const hmc_params *params, int32_t n_replicas, hmc_ha
     void *zero_ptrs[] = {h->u[0], h->u[1], h->v};
     for (void *z : zero_ptrs)
         if ((e = cudaMemset(z, 0, nodes_b)) != cudaSuccess) return bail(cuda_fail(h, e, "memset"));
+    if (p->elastic == HMC_ELASTIC_STRAIN &&
+        (e = cudaMalloc(&h->stab, h->tsize * 24 * (size_t)p->n_orient)) != cudaSuccess)
+        return bail(cuda_fail(h, e, "compliance table"));
     if (p->elastic == HMC_ELASTIC_ZONE1) {
         std::vector<uint16_t> zs = hmc::zone_schedule();
         if (zs.empty()) return bail(fail(h, HMC_ERR_CUDA, "zone schedule does not fit"));
@@ -858,7 +870,7 @@ hmc_status hmc_batch_create(const hmc_params *params, int32_t n_replicas, hmc_ha
     return HMC_OK;
 }
 
-hmc_status hmc_create(const hmc_params *p, hmc_handle **out) { return hmc_batch_create(p, 1, out); }
+hmc_status hmc_create(const hmc_params *p, hmc_handle **out) { return hmc_create_batch(p, 1, out); }
 
 void hmc_destroy(hmc_handle *h) {
     if (!h) return;
@@ -971,6 +983,17 @@ hmc_status hmc_set_orientations(hmc_handle *h, const double *euler, const uint16
         HMC_CK(h, cudaMemcpy(h->ctab, c.data(), c.size() * sizeof(double), cudaMemcpyHostToDevice), "table upload");
         HMC_CK(h, cudaMemcpy(h->wtab, w.data(), w.size() * sizeof(double), cudaMemcpyHostToDevice), "table upload");
     }
+    if (h->p.elastic == HMC_ELASTIC_STRAIN) {
+        if (h->p.precision == HMC_FP32) {
+            auto st32 = pack_ctab<float>(h->Sv, Q);
+            HMC_CK(h, cudaMemcpy(h->stab, st32.data(), st32.size() * sizeof(float), cudaMemcpyHostToDevice),
+                   "table upload");
+        } else {
+            auto st64 = pack_ctab<double>(h->Sv, Q);
+            HMC_CK(h, cudaMemcpy(h->stab, st64.data(), st64.size() * sizeof(double), cudaMemcpyHostToDevice),
+                   "table upload");
+        }
+    }
     if (h->p.elastic == HMC_ELASTIC_ZONE1) {
         std::vector<double> kt;
         hmc::zone_element_tables(h->Cv.data(), Q, kt);
@@ -1009,6 +1032,64 @@ hmc_status hmc_set_spins(hmc_handle *h, const uint16_t *spins) {
     if ((s = upload_spins(h, h->sel, spins)) != HMC_OK) return s;
     HMC_CK(h, cudaStreamSynchronize(h->stream), "sync");
     return HMC_OK;
+}
+
+namespace {
+// Device pointers handed in by the caller: memory of the current device, 16-byte aligned.
+hmc_status check_dev_ptr(hmc_handle *h, const void *p, const char *what) {
+    if (!p) return fail(h, HMC_ERR_ARG, std::string("NULL ") + what);
+    if (reinterpret_cast<uintptr_t>(p) & 15) return fail(h, HMC_ERR_ARG, std::string(what) + " must be 16-byte aligned");
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(h, HMC_ERR_ARG, std::string(what) + " is not a CUDA pointer");
+    }
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return fail(h, HMC_ERR_CUDA, "cudaGetDevice");
+    if (!((at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) && at.device == dev))
+        return fail(h, HMC_ERR_ARG, std::string(what) + " is not device memory of the current device");
+    return HMC_OK;
+}
+}  // namespace
+
+hmc_status hmc_set_spins_dev(hmc_handle *h, const uint16_t *d_spins) {
+    if (h) ++h->state_version;
+    hmc_status s = need_oriented(h);
+    if (s != HMC_OK) return s;
+    if ((s = check_dev_ptr(h, d_spins, "device spins")) != HMC_OK) return s;
+    const RepHost &R = selr(h);
+    int bad = 0;
+    HMC_CK(h, cudaMemsetAsync(&sel_st(h)->bad_spin, 0, sizeof(int32_t), h->stream), "memset");
+    HMC_CK(h, hmc::launch_check_spins(d_spins, R.N, h->p.n_orient, sel_st(h), h->stream), "spin check");
+    HMC_CK(h, cudaMemcpyAsync(&bad, &sel_st(h)->bad_spin, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream),
+           "download");
+    HMC_CK(h, cudaStreamSynchronize(h->stream), "sync");
+    if (bad) return fail(h, HMC_ERR_ARG, "spin value >= n_orient");
+    HMC_CK(h, hmc::launch_pack_spins(d_spins, h->spins + R.blk_off, R.p.nx, R.p.ny, R.p.nz, h->stream),
+           "pack spins");
+    HMC_CK(h, cudaStreamSynchronize(h->stream), "sync");
+    return HMC_OK;
+}
+
+hmc_status hmc_get_spins_dev(hmc_handle *h, uint16_t *d_spins) {
+    hmc_status s = need_oriented(h);
+    if (s != HMC_OK) return s;
+    if ((s = check_dev_ptr(h, d_spins, "device spins")) != HMC_OK) return s;
+    const RepHost &R = selr(h);
+    HMC_CK(h, hmc::launch_unpack_spins(h->spins + R.blk_off, d_spins, R.p.nx, R.p.ny, R.p.nz, h->stream),
+           "unpack spins");
+    HMC_CK(h, cudaStreamSynchronize(h->stream), "sync");
+    return HMC_OK;
+}
+
+hmc_status hmc_set_orientations_dev(hmc_handle *h, const double *euler, const uint16_t *d_spins) {
+    if (!h) return HMC_ERR_ARG;
+    hmc_status s = check_dev_ptr(h, d_spins, "device spins");
+    if (s != HMC_OK) return s;
+    std::vector<uint16_t> host((size_t)h->N_total);
+    HMC_CK(h, cudaMemcpy(host.data(), d_spins, sizeof(uint16_t) * host.size(), cudaMemcpyDeviceToHost),
+           "spin download");
+    return hmc_set_orientations(h, euler, host.data());
 }
 
 hmc_status hmc_get_spins(hmc_handle *h, uint16_t *spins) {

@@ -111,11 +111,13 @@ struct SweepArgs {
     int nctas;
     uint4 *work;                     // zone mode: trial list {site, replica, q_new | q_old << 16, r1}
     unsigned *count;                 // zone mode: entries in the list
+    const T *ctab, *stab;            // constant-strain mode: stiffness and compliance rows (Q x 24)
 };
 
-// Elastic term of a sweep: none, one-point zone from the stored stress, or the
-// 27-point zone (trials listed by the sweep, decided by the zone kernel).
-enum SweepMode { SWEEP_POTTS = 0, SWEEP_POINT = 1, SWEEP_ZONE_LIST = 2 };
+// Elastic term of a sweep: none, one-point zone from the stored stress (constant
+// traction or constant strain), or the 27-point zone (trials listed by the
+// sweep, decided by the zone kernel).
+enum SweepMode { SWEEP_POTTS = 0, SWEEP_POINT = 1, SWEEP_ZONE_LIST = 2, SWEEP_STRAIN = 3 };
 
 template <typename T>
 struct ZoneArgs {

@@ -1,7 +1,8 @@
 // Red/black checkerboard half sweep (Sec. "Microstructural Evolution") with the
 // Metropolis rule (Eq. 5) on the bond-energy change of the Potts Hamiltonian
 // (Eq. 4, bonds counted once, 6 neighbours, periodic) plus the one-point
-// constant-traction zone shift (Eqs. 6-8 and 13) from the stored stress.
+// constant-traction zone shift (Eqs. 6-8 and 13) from the stored stress, or its
+// constant-strain reading.
 //
 // One thread per 2x2x2 block: it tries the block's four sites of the sweep's
 // colour.  A CTA covers 256 blocks of one replica of the batch.  Loads per
@@ -89,7 +90,7 @@ __device__ __forceinline__ double log_t(double x) { return log(x); }
 
 template <typename T, int MODE>
 __global__ void __launch_bounds__(BLOCK_THREADS, (sizeof(T) == 4 ? 3 : 2)) k_sweep(SweepArgs<T> a, int colour) {
-    constexpr bool ELASTIC = MODE == SWEEP_POINT;
+    constexpr bool ELASTIC = MODE == SWEEP_POINT || MODE == SWEEP_STRAIN;   // reads the stored stress
     constexpr bool LIST = MODE == SWEEP_ZONE_LIST;
     const int r = __ldg(a.cta_rep + blockIdx.x);
     const Replica &R = a.reps[r];
@@ -177,11 +178,35 @@ __global__ void __launch_bounds__(BLOCK_THREADS, (sizeof(T) == 4 ? 3 : 2)) k_swe
 #pragma unroll
             for (int j = 0; j < 6; ++j) dE += (nb[j] == q) - (nb[j] == qn);
             T dHe = T(0);
-            if (ELASTIC) {
+            if (MODE == SWEEP_POINT) {
                 T s[6];
 #pragma unroll
                 for (int k = 0; k < 6; ++k) s[k] = sg[k][i];
                 dHe = lam_sd_half * (zone_phi<T>(a.wtab + 20ll * q, s) - zone_phi<T>(a.wtab + 20ll * qn, s));
+            } else if (MODE == SWEEP_STRAIN) {
+                // e = S'(q) s held fixed: 1/2 (e.C'(q_new)e - e.C'(q)e)
+                T s[6], e[6], sn[6], so[6];
+#pragma unroll
+                for (int k = 0; k < 6; ++k) s[k] = sg[k][i];
+                {
+                    Row24<T> r;
+                    r.load(a.stab + 24ll * q);
+                    hooke21<T>(r.v, s, e);
+                }
+                {
+                    Row24<T> r;
+                    r.load(a.ctab + 24ll * qn);
+                    hooke21<T>(r.v, e, sn);
+                }
+                {
+                    Row24<T> r;
+                    r.load(a.ctab + 24ll * q);
+                    hooke21<T>(r.v, e, so);
+                }
+                T d = T(0);
+#pragma unroll
+                for (int k = 0; k < 6; ++k) d += e[k] * (sn[k] - so[k]);
+                dHe = T(0.5) * (T)R.lam * d;
             }
             bool acc;
             if (!ELASTIC || dHe == T(0)) {
@@ -234,6 +259,8 @@ template <typename T>
 cudaError_t launch_sweep(const SweepArgs<T> &a, int colour, int mode, cudaStream_t s) {
     if (mode == SWEEP_POINT)
         k_sweep<T, SWEEP_POINT><<<a.nctas, BLOCK_THREADS, 0, s>>>(a, colour);
+    else if (mode == SWEEP_STRAIN)
+        k_sweep<T, SWEEP_STRAIN><<<a.nctas, BLOCK_THREADS, 0, s>>>(a, colour);
     else if (mode == SWEEP_ZONE_LIST)
         k_sweep<T, SWEEP_ZONE_LIST><<<a.nctas, BLOCK_THREADS, 0, s>>>(a, colour);
     else

@@ -116,12 +116,13 @@ def test_stress_parity_ragged_tiles(G, precision):
     assert rel(g.nodal()[0], o.u) < (1e-12 if precision == 0 else 1e-5)
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_hybrid_lockstep_decisions(G, precision):
+@pytest.mark.parametrize("precision,elastic", [(0, 1), (1, 1), (0, 3), (1, 3)])
+def test_hybrid_lockstep_decisions(G, precision, elastic):
     """Both sides sweep the same spins with the same stress (the oracle's, pushed
-    to the device); decisions may differ only where |dH - t| is within 1e-6."""
+    to the device); decisions may differ only where |dH - t| is within 1e-6.
+    elastic 1: constant-traction point zone; 3: constant-strain point zone."""
     shape = (16, 34, 36)
-    g, o = make_pair(G, shape, 16, precision, axis=(1, 1, 1.0), n_mpm=10, n_seeds=20)
+    g, o = make_pair(G, shape, 16, precision, axis=(1, 1, 1.0), n_mpm=10, n_seeds=20, elastic=elastic)
     o.mpm_steps(10)
     sig = o.stress()
     n_site = n_mis = 0
