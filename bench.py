@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--workload", default="ni256")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--store-stress", type=int, default=1, choices=[0, 1],
+                    help="1: the stress pass stores every point's stress for the sweeps; 0: sweeps recompute it")
     return ap.parse_args()
 
 
@@ -247,7 +249,7 @@ def run_ours(args):
     stream = torch.cuda.Stream()
     common = dict(J=spec["J"], kT=spec["kT"], c11=spec["c11"], c12=spec["c12"], c44=spec["c44"],
                   load_axis=spec["axis"], strain=spec["strain"], mpm_steps_per_mcs=spec["mpm_steps"],
-                  seed=0x5EED0000 + 3, replica=rank, stream=stream.cuda_stream)
+                  seed=0x5EED0000 + 3, replica=rank, stream=stream.cuda_stream, store_stress=args.store_stress)
     h = G.HMC(spec["shape"], spec["Q"], precision=G.HMC_FP32, **common)
     h.set_orientations(euler, spins)
 
@@ -365,7 +367,7 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": "site-updates/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": workload_config(spec, args.workload),
+            "config": dict(workload_config(spec, args.workload), store_stress=args.store_stress),
             "mpm_cell_steps_per_s": N * ws / t_mpm, "mpm_ms_per_step": t_mpm * 1e3,
             "stress_ms": t_stress * 1e3, "half_sweep_ms": t_sweep * 1e3,
             "roofline": roofline, "roofline_sweep": roofline_sweep,

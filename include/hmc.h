@@ -115,6 +115,14 @@ typedef struct {
     uint32_t replica;            /* third Philox counter word (ensemble member)       */
     void *stream;                /* cudaStream_t for all work; NULL = library-owned   */
     double stress;               /* TRACTION stress along load_axis, GPa               */
+    int32_t store_stress;        /* 1: the stress pass of each MC step stores every
+                                    point's stress and the point-zone sweeps read it;
+                                    0: the step's stress pass only forms the mean
+                                    stress and energy, and the sweeps recompute the
+                                    stress of each non-trivial trial site from the
+                                    nodal displacement (same arithmetic, same bits).
+                                    The stored field is then refreshed only by
+                                    hmc_compute_stress.                              */
 } hmc_params;
 
 /* Scalars the library derived from the parameters, and its counters. */
@@ -258,9 +266,11 @@ hmc_status hmc_grain_count(hmc_handle *h, int64_t *n_grains);
  * mean stress (6) from the stored stress (FP64).  Any pointer may be NULL. */
 hmc_status hmc_energy(hmc_handle *h, int64_t *unlike_bonds, double *elastic_energy, double *mean_stress);
 
-/* Stored stress of every point (N x 6 doubles, natural order), i.e. the
- * stress the next half sweeps read.  hmc_set_stress replaces it (rounded to
- * the handle's precision), so that a sweep can be run on a given stress. */
+/* Stored stress of every point (N x 6 doubles, natural order): the stress of
+ * the last pass that stored it -- hmc_compute_stress always, a Monte Carlo step
+ * only when its sweeps read it (point-zone elastic term and store_stress = 1).
+ * hmc_set_stress replaces it (rounded to the handle's precision), so that a
+ * stored-stress sweep can be run on a given stress. */
 hmc_status hmc_get_stress(hmc_handle *h, double *sigma);
 hmc_status hmc_set_stress(hmc_handle *h, const double *sigma);
 

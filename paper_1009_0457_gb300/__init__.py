@@ -45,6 +45,7 @@ class hmc_params(C.Structure):
         ("replica", C.c_uint32),
         ("stream", C.c_void_p),
         ("stress", C.c_double),
+        ("store_stress", C.c_int32),
     ]
 
 

@@ -257,7 +257,7 @@ cudaError_t enq_mpm(hmc_handle *h, cudaStream_t s) {
 }
 
 template <typename T>
-cudaError_t enqueue_stress(hmc_handle *h, cudaStream_t s) {
+cudaError_t enqueue_stress(hmc_handle *h, bool store, cudaStream_t s) {
     hmc::StressArgs<T> a;
     a.reps = h->d_reps;
     a.cta_rep = h->d_cta_rep;
@@ -267,7 +267,7 @@ cudaError_t enqueue_stress(hmc_handle *h, cudaStream_t s) {
     a.sig = static_cast<T *>(h->sig);
     a.partials = h->partials;
     a.nctas = h->nctas;
-    return hmc::launch_stress<T>(a, s);
+    return hmc::launch_stress<T>(a, store, s);
 }
 
 template <typename T>
@@ -288,17 +288,19 @@ cudaError_t enqueue_sweep(hmc_handle *h, int colour, cudaStream_t s) {
     a.count = h->zone_count;
     a.ctab = static_cast<const T *>(h->ctab);
     a.stab = static_cast<const T *>(h->stab);
+    a.u = static_cast<const T *>(h->u[h->cur]);
+    const bool point = h->p.elastic == HMC_ELASTIC_TRACTION || h->p.elastic == HMC_ELASTIC_STRAIN;
     if (h->p.elastic != HMC_ELASTIC_ZONE1)
         return hmc::launch_sweep<T>(a, colour,
                                     h->p.elastic == HMC_ELASTIC_TRACTION ? hmc::SWEEP_POINT
                                     : h->p.elastic == HMC_ELASTIC_STRAIN ? hmc::SWEEP_STRAIN
                                                                          : hmc::SWEEP_POTTS,
-                                    s);
+                                    point && !h->p.store_stress, s);
     // 27-point zone: list the trials, copy the spins as they are at the start of the half step,
     // then decide every listed trial against that copy
     cudaError_t e;
     if ((e = cudaMemsetAsync(h->zone_count, 0, sizeof(unsigned), s)) != cudaSuccess) return e;
-    if ((e = hmc::launch_sweep<T>(a, colour, hmc::SWEEP_ZONE_LIST, s)) != cudaSuccess) return e;
+    if ((e = hmc::launch_sweep<T>(a, colour, hmc::SWEEP_ZONE_LIST, false, s)) != cudaSuccess) return e;
     if ((e = cudaMemcpyAsync(h->snap, h->spins, sizeof(uint4) * (size_t)h->nblk_total, cudaMemcpyDeviceToDevice,
                              s)) != cudaSuccess)
         return e;
@@ -319,11 +321,18 @@ cudaError_t enqueue_sweep(hmc_handle *h, int colour, cudaStream_t s) {
     return hmc::launch_zone<T>(z, h->zone_grid, s);
 }
 
-cudaError_t enq_stress(hmc_handle *h, cudaStream_t s) {
-    return h->p.precision == HMC_FP32 ? enqueue_stress<float>(h, s) : enqueue_stress<double>(h, s);
+// store: write every point's stress (the explicit stress pass, and the Monte Carlo step when the
+// sweeps read it); otherwise only the reductions of the end of the step
+cudaError_t enq_stress(hmc_handle *h, bool store, cudaStream_t s) {
+    return h->p.precision == HMC_FP32 ? enqueue_stress<float>(h, store, s) : enqueue_stress<double>(h, store, s);
 }
 cudaError_t enq_sweep(hmc_handle *h, int c, cudaStream_t s) {
     return h->p.precision == HMC_FP32 ? enqueue_sweep<float>(h, c, s) : enqueue_sweep<double>(h, c, s);
+}
+
+// The sweeps read the stored stress only with a point-zone elastic term and store_stress set.
+bool sweeps_read_stress(const hmc_handle *h) {
+    return (h->p.elastic == HMC_ELASTIC_TRACTION || h->p.elastic == HMC_ELASTIC_STRAIN) && h->p.store_stress;
 }
 
 // One Monte Carlo step of every replica on stream s (also used while capturing the graph).
@@ -331,7 +340,7 @@ cudaError_t enqueue_mcs(hmc_handle *h, cudaStream_t s) {
     cudaError_t e;
     for (int k = 0; k < h->p.mpm_steps_per_mcs; ++k)
         if ((e = enq_mpm(h, s)) != cudaSuccess) return e;
-    if ((e = enq_stress(h, s)) != cudaSuccess) return e;
+    if ((e = enq_stress(h, sweeps_read_stress(h), s)) != cudaSuccess) return e;
     if ((e = enq_sweep(h, 0, s)) != cudaSuccess) return e;
     if ((e = enq_sweep(h, 1, s)) != cudaSuccess) return e;
     return hmc::launch_end_mcs(h->d_reps, h->R, h->partials, 1, 1, s);
@@ -401,6 +410,7 @@ std::string validate(const hmc_params *p) {
     if (p->kT < 0) return "kT must be >= 0";
     if (p->bc != HMC_BC_UNIAXIAL && p->bc != HMC_BC_STRAIN6 && p->bc != HMC_BC_TRACTION) return "bad bc";
     if (!std::isfinite(p->stress)) return "non-finite stress";
+    if (p->store_stress != 0 && p->store_stress != 1) return "store_stress must be 0 or 1";
     if (p->elastic != HMC_ELASTIC_OFF && p->elastic != HMC_ELASTIC_TRACTION && p->elastic != HMC_ELASTIC_ZONE1 &&
         p->elastic != HMC_ELASTIC_STRAIN)
         return "bad elastic";
@@ -427,9 +437,9 @@ std::string validate_shared(const hmc_params *a, const hmc_params *b) {
     if (a->n_orient != b->n_orient || a->J != b->J || a->kT != b->kT || a->c11 != b->c11 || a->c12 != b->c12 ||
         a->c44 != b->c44 || a->bc != b->bc || a->elastic != b->elastic || a->trial != b->trial ||
         a->mpm_steps_per_mcs != b->mpm_steps_per_mcs || a->dt != b->dt || a->damping != b->damping ||
-        a->precision != b->precision || a->stream != b->stream)
+        a->precision != b->precision || a->stream != b->stream || a->store_stress != b->store_stress)
         return "replicas of a batch must share n_orient, J, kT, c11, c12, c44, bc, elastic, trial, "
-               "mpm_steps_per_mcs, dt, damping, precision and stream";
+               "mpm_steps_per_mcs, dt, damping, precision, stream and store_stress";
     return "";
 }
 
@@ -691,6 +701,7 @@ void hmc_default_params(hmc_params *p) {
     p->strain = 1e-3;
     p->elastic_scale = -1.0;
     p->elastic = HMC_ELASTIC_TRACTION;
+    p->store_stress = 1;
     p->trial = HMC_TRIAL_NEIGHBOR;
     p->mpm_steps_per_mcs = 50;
     p->dt = -1.0;
@@ -1114,7 +1125,7 @@ hmc_status hmc_compute_stress(hmc_handle *h, double *mean, double *energy) {
                "fault injection");
         ++h->state_version;
     }
-    HMC_CK(h, enq_stress(h, h->stream), "stress launch");
+    HMC_CK(h, enq_stress(h, true, h->stream), "stress launch");
     HMC_CK(h, hmc::launch_end_mcs(h->d_reps, h->R, h->partials, 0, 0, h->stream), "reduction launch");
     if (mean || energy) return read_stats(h, mean, energy);
     return HMC_OK;

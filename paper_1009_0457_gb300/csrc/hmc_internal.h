@@ -112,6 +112,8 @@ struct SweepArgs {
     uint4 *work;                     // zone mode: trial list {site, replica, q_new | q_old << 16, r1}
     unsigned *count;                 // zone mode: entries in the list
     const T *ctab, *stab;            // constant-strain mode: stiffness and compliance rows (Q x 24)
+    const T *u;                      // recompute mode: nodal displacement (the stress of a trial site
+                                     // is formed from it as the stress pass would)
 };
 
 // Elastic term of a sweep: none, one-point zone from the stored stress (constant
@@ -148,9 +150,9 @@ int mpm_shape_cy(int shape);
 template <typename T>
 cudaError_t launch_mpm_step(const MpmArgs<T> &a, int shape, cudaStream_t s);
 template <typename T>
-cudaError_t launch_stress(const StressArgs<T> &a, cudaStream_t s);
+cudaError_t launch_stress(const StressArgs<T> &a, bool store, cudaStream_t s);   // store = 0: reductions only
 template <typename T>
-cudaError_t launch_sweep(const SweepArgs<T> &a, int colour, int mode, cudaStream_t s);
+cudaError_t launch_sweep(const SweepArgs<T> &a, int colour, int mode, bool recompute, cudaStream_t s);
 template <typename T>
 cudaError_t launch_zone(const ZoneArgs<T> &a, int grid, cudaStream_t s);
 template <typename T>

@@ -80,7 +80,7 @@ __device__ __forceinline__ void store4<double>(double *p, const double (&v)[4]) 
 // 1/2 sigma.eps (a cell's eight points summed plainly, then FP32 TwoSum pairs or
 // FP64 within a warp, by T, and FP64 across warps) for a fixed-order final
 // reduction.
-template <typename T>
+template <typename T, bool STORE>
 __global__ void __launch_bounds__(BLOCK_THREADS) k_stress(StressArgs<T> a) {
     __shared__ double red[BLOCK_THREADS / 32][7];
     const int rep = __ldg(a.cta_rep + blockIdx.x);
@@ -138,11 +138,13 @@ __global__ void __launch_bounds__(BLOCK_THREADS) k_stress(StressArgs<T> a) {
         }
 #pragma unroll
         for (int k = 0; k < 7; ++k) acc.add(k, csum[k]);
-        T *sig = a.sig + 48ll * R.blk_off;
+        if (STORE) {
+            T *sig = a.sig + 48ll * R.blk_off;
 #pragma unroll
-        for (int c = 0; c < 2; ++c)
+            for (int c = 0; c < 2; ++c)
 #pragma unroll
-            for (int k = 0; k < 6; ++k) store4<T>(sig + 4ll * ((long long)(c * 6 + k) * R.nblk + blk), out[c][k]);
+                for (int k = 0; k < 6; ++k) store4<T>(sig + 4ll * ((long long)(c * 6 + k) * R.nblk + blk), out[c][k]);
+        }
     }
     acc.warp_reduce();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -324,12 +326,15 @@ __global__ void k_bins(const unsigned long long *counts, const int32_t *binmap, 
 }  // namespace
 
 template <typename T>
-cudaError_t launch_stress(const StressArgs<T> &a, cudaStream_t s) {
-    k_stress<T><<<a.nctas, BLOCK_THREADS, 0, s>>>(a);
+cudaError_t launch_stress(const StressArgs<T> &a, bool store, cudaStream_t s) {
+    if (store)
+        k_stress<T, true><<<a.nctas, BLOCK_THREADS, 0, s>>>(a);
+    else
+        k_stress<T, false><<<a.nctas, BLOCK_THREADS, 0, s>>>(a);
     return cudaGetLastError();
 }
-template cudaError_t launch_stress<float>(const StressArgs<float> &, cudaStream_t);
-template cudaError_t launch_stress<double>(const StressArgs<double> &, cudaStream_t);
+template cudaError_t launch_stress<float>(const StressArgs<float> &, bool, cudaStream_t);
+template cudaError_t launch_stress<double>(const StressArgs<double> &, bool, cudaStream_t);
 
 cudaError_t launch_end_mcs(const Replica *reps, int nrep, const double *partials, int update_strain, int advance,
                            cudaStream_t s) {

@@ -88,9 +88,10 @@ __device__ __forceinline__ T zone_phi(const T *__restrict__ w, const T (&s)[6]) 
 __device__ __forceinline__ float log_t(float x) { return logf(x); }
 __device__ __forceinline__ double log_t(double x) { return log(x); }
 
-template <typename T, int MODE>
+template <typename T, int MODE, bool RECOMP>
 __global__ void __launch_bounds__(BLOCK_THREADS, (sizeof(T) == 4 ? 3 : 2)) k_sweep(SweepArgs<T> a, int colour) {
-    constexpr bool ELASTIC = MODE == SWEEP_POINT || MODE == SWEEP_STRAIN;   // reads the stored stress
+    constexpr bool ELASTIC = MODE == SWEEP_POINT || MODE == SWEEP_STRAIN;   // a point-zone elastic term
+    constexpr bool STORED = ELASTIC && !RECOMP;                               // ... from the stored stress
     constexpr bool LIST = MODE == SWEEP_ZONE_LIST;
     const int r = __ldg(a.cta_rep + blockIdx.x);
     const Replica &R = a.reps[r];
@@ -118,7 +119,7 @@ __global__ void __launch_bounds__(BLOCK_THREADS, (sizeof(T) == 4 ? 3 : 2)) k_swe
         const uint2 Oym = __ldg(q2 + 2 * bym + oc), Oyp = __ldg(q2 + 2 * byp + oc);
         const uint2 Ozm = __ldg(q2 + 2 * bzm + oc), Ozp = __ldg(q2 + 2 * bzp + oc);
         T sg[6][4];
-        if (ELASTIC) {
+        if (STORED) {
             const T *sig = a.sig + 48ll * R.blk_off;
 #pragma unroll
             for (int k = 0; k < 6; ++k) {
@@ -138,6 +139,10 @@ __global__ void __launch_bounds__(BLOCK_THREADS, (sizeof(T) == 4 ? 3 : 2)) k_swe
             rnd[i] = philox_r01(x + (uint32_t)R.nx * (y + (uint32_t)R.ny * z), mcs, R.replica, 0u, R.key0, R.key1);
         }
         const T lam_sd_half = (T)R.lam_sd_half;
+        // recompute mode: the cell's displacement gradients, formed at the first non-trivial trial
+        CellGrad<T> g;
+        T ebv[6];
+        bool have_g = false;
         uint16_t out[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
@@ -178,17 +183,52 @@ __global__ void __launch_bounds__(BLOCK_THREADS, (sizeof(T) == 4 ? 3 : 2)) k_swe
 #pragma unroll
             for (int j = 0; j < 6; ++j) dE += (nb[j] == q) - (nb[j] == qn);
             T dHe = T(0);
+            T er[6];   // recompute mode: the site's strain
+            if (RECOMP && ELASTIC) {
+                if (!have_g) {
+                    // the cell's eight corner displacements, as the stress pass reads them
+                    const T *u = a.u + 3 * R.blk_off;
+                    T uc[8][3];
+#pragma unroll
+                    for (int K = 0; K < 2; ++K)
+#pragma unroll
+                        for (int J = 0; J < 2; ++J)
+#pragma unroll
+                            for (int I = 0; I < 2; ++I) {
+                                const int gi = bx + I == nbx ? 0 : bx + I;
+                                const int gj = by + J == nby ? 0 : by + J;
+                                const int gk = bz + K == nbz ? 0 : bz + K;
+                                const int n = 3 * (gi + nbx * (gj + nby * gk));
+#pragma unroll
+                                for (int d = 0; d < 3; ++d) uc[corner(I, J, K)][d] = __ldg(u + n + d);
+                            }
+                    cell_gradients<T>(uc, g);
+                    load_ebar<T>(R.st, ebv);
+                    have_g = true;
+                }
+                point_strain<T>(g, ebv, lx, ly, lz, er);
+            }
             if (MODE == SWEEP_POINT) {
                 T s[6];
+                if (RECOMP) {
+                    Row24<T> r;
+                    r.load(a.ctab + 24ll * q);
+                    hooke21<T>(r.v, er, s);
+                } else {
 #pragma unroll
-                for (int k = 0; k < 6; ++k) s[k] = sg[k][i];
+                    for (int k = 0; k < 6; ++k) s[k] = sg[k][i];
+                }
                 dHe = lam_sd_half * (zone_phi<T>(a.wtab + 20ll * q, s) - zone_phi<T>(a.wtab + 20ll * qn, s));
             } else if (MODE == SWEEP_STRAIN) {
-                // e = S'(q) s held fixed: 1/2 (e.C'(q_new)e - e.C'(q)e)
-                T s[6], e[6], sn[6], so[6];
+                // e held fixed (stored mode: e = S'(q) s): 1/2 (e.C'(q_new)e - e.C'(q)e)
+                T e[6], sn[6], so[6];
+                if (RECOMP) {
 #pragma unroll
-                for (int k = 0; k < 6; ++k) s[k] = sg[k][i];
-                {
+                    for (int k = 0; k < 6; ++k) e[k] = er[k];
+                } else {
+                    T s[6];
+#pragma unroll
+                    for (int k = 0; k < 6; ++k) s[k] = sg[k][i];
                     Row24<T> r;
                     r.load(a.stab + 24ll * q);
                     hooke21<T>(r.v, s, e);
@@ -256,19 +296,23 @@ __global__ void __launch_bounds__(BLOCK_THREADS, (sizeof(T) == 4 ? 3 : 2)) k_swe
 }  // namespace
 
 template <typename T>
-cudaError_t launch_sweep(const SweepArgs<T> &a, int colour, int mode, cudaStream_t s) {
-    if (mode == SWEEP_POINT)
-        k_sweep<T, SWEEP_POINT><<<a.nctas, BLOCK_THREADS, 0, s>>>(a, colour);
+cudaError_t launch_sweep(const SweepArgs<T> &a, int colour, int mode, bool recompute, cudaStream_t s) {
+    if (mode == SWEEP_POINT && recompute)
+        k_sweep<T, SWEEP_POINT, true><<<a.nctas, BLOCK_THREADS, 0, s>>>(a, colour);
+    else if (mode == SWEEP_POINT)
+        k_sweep<T, SWEEP_POINT, false><<<a.nctas, BLOCK_THREADS, 0, s>>>(a, colour);
+    else if (mode == SWEEP_STRAIN && recompute)
+        k_sweep<T, SWEEP_STRAIN, true><<<a.nctas, BLOCK_THREADS, 0, s>>>(a, colour);
     else if (mode == SWEEP_STRAIN)
-        k_sweep<T, SWEEP_STRAIN><<<a.nctas, BLOCK_THREADS, 0, s>>>(a, colour);
+        k_sweep<T, SWEEP_STRAIN, false><<<a.nctas, BLOCK_THREADS, 0, s>>>(a, colour);
     else if (mode == SWEEP_ZONE_LIST)
-        k_sweep<T, SWEEP_ZONE_LIST><<<a.nctas, BLOCK_THREADS, 0, s>>>(a, colour);
+        k_sweep<T, SWEEP_ZONE_LIST, false><<<a.nctas, BLOCK_THREADS, 0, s>>>(a, colour);
     else
-        k_sweep<T, SWEEP_POTTS><<<a.nctas, BLOCK_THREADS, 0, s>>>(a, colour);
+        k_sweep<T, SWEEP_POTTS, false><<<a.nctas, BLOCK_THREADS, 0, s>>>(a, colour);
     return cudaGetLastError();
 }
 
-template cudaError_t launch_sweep<float>(const SweepArgs<float> &, int, int, cudaStream_t);
-template cudaError_t launch_sweep<double>(const SweepArgs<double> &, int, int, cudaStream_t);
+template cudaError_t launch_sweep<float>(const SweepArgs<float> &, int, int, bool, cudaStream_t);
+template cudaError_t launch_sweep<double>(const SweepArgs<double> &, int, int, bool, cudaStream_t);
 
 }  // namespace hmc

@@ -230,3 +230,42 @@ def test_errors_leave_handle_usable(G):
         g.set_orientations(np.zeros((2, 3)), np.full(64, 5, dtype=np.uint16))
     g.set_orientations(np.zeros((2, 3)), np.zeros(64, dtype=np.uint16))
     g.mc_sweeps(1)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_recomputed_stress_sweeps_are_bit_identical(G, precision):
+    """store_stress = 0: the sweeps form each trial site's stress from the nodal
+    displacement with the stress pass's arithmetic, so whole Monte Carlo steps give
+    the same bits as with the stored field."""
+    shape = (12, 18, 34)
+    out = []
+    for store in (1, 0):
+        eul = S.euler_uniform_so3(12, 4)
+        sp = S.voronoi_spins(shape, 15, 12, 4)
+        g = G.HMC(shape, 12, precision=precision, load_axis=(1, 1, 1.0), strain=2e-3, mpm_steps_per_mcs=8,
+                  elastic_scale=2e3, store_stress=store, seed=77, **C3)
+        g.set_orientations(eul, sp)
+        acc = g.mc_sweeps(3)
+        out.append((acc, g.spins().copy(), g.nodal()[0], g.strain()))
+        g.close()
+    assert out[0][0] == out[1][0] and out[0][0] > 0
+    assert np.array_equal(out[0][1], out[1][1])
+    assert np.array_equal(out[0][2], out[1][2]) and np.array_equal(out[0][3], out[1][3])
+
+
+def test_recomputed_strain_zone_matches_stored(G):
+    """Constant-strain zone: the recomputed strain is the point strain itself, the
+    stored form S'(q) sigma rounds through the stress; decisions agree but for
+    trials within rounding of their threshold."""
+    shape = (12, 18, 34)
+    res = []
+    for store in (1, 0):
+        eul = S.euler_uniform_so3(12, 4)
+        sp = S.voronoi_spins(shape, 15, 12, 4)
+        g = G.HMC(shape, 12, precision=0, load_axis=(1, 1, 1.0), strain=2e-3, mpm_steps_per_mcs=8,
+                  elastic=G.HMC_ELASTIC_STRAIN, elastic_scale=2e3, store_stress=store, seed=78, **C3)
+        g.set_orientations(eul, sp)
+        g.mc_sweeps(1)
+        res.append(g.spins().copy())
+        g.close()
+    assert (res[0] != res[1]).mean() <= 1e-4
