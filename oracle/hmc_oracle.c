@@ -425,16 +425,32 @@ enum { ORC_TRIAL_NEIGHBOR = 0, ORC_TRIAL_UNIFORM_Q = 1 };
  * total change in MC energy units, *thresh the Metropolis threshold
  * -kT ln u (or -1 when the integer table decided).  sig_p is the site's
  * stress (6 values; unused when the elastic term is off). */
+/* The two draws of the trial at site (x, y, z) of Monte Carlo step mcs.  Sites
+ * (x, y, z) with x even and (x + 1, y ^ 1, z) -- same colour, same 2x2x2 block --
+ * share one Philox4x32-10 block: counter (index of the even-x site, mcs,
+ * replica, 0), key (seed lo, seed hi); words 0, 1 go to the even-x site and
+ * words 2, 3 to its partner.  out[0] picks the trial state, out[1] decides. */
+void orc_site_draws(int nx, int ny, int x, int y, int z, uint64_t seed, uint32_t mcs, uint32_t replica,
+                    uint32_t out[2])
+{
+    const int odd = x & 1;
+    const int xl = x - odd, yl = odd ? (y ^ 1) : y;
+    uint32_t ctr[4] = {(uint32_t)((int64_t)xl + (int64_t)nx * ((int64_t)yl + (int64_t)ny * z)), mcs, replica, 0u};
+    uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+    uint32_t r[4];
+    orc_philox4x32_10(ctr, key, r);
+    out[0] = r[2 * odd];
+    out[1] = r[2 * odd + 1];
+}
+
 int orc_site_trial_at(int nx, int ny, int nz, const uint16_t *spin, int x, int y, int z,
                       uint64_t seed, uint32_t mcs, uint32_t replica, double J, double kT,
                       int trial_mode, int Q, int elastic, double lambda, const double *Stab,
                       const double *Ctab, const double *sig_p, uint16_t *q_new, double *dH, double *thresh)
 {
     int64_t p = (int64_t)x + (int64_t)nx * ((int64_t)y + (int64_t)ny * z);
-    uint32_t ctr[4] = {(uint32_t)p, mcs, replica, 0u};
-    uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
-    uint32_t r[4];
-    orc_philox4x32_10(ctr, key, r);
+    uint32_t r[2];
+    orc_site_draws(nx, ny, x, y, z, seed, mcs, replica, r);
 
     /* neighbours in the order -x, +x, -y, +y, -z, +z (periodic lattice) */
     uint16_t nb[6];

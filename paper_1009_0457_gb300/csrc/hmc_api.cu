@@ -785,6 +785,7 @@ hmc_status hmc_create_batch(const hmc_params *params, int32_t n_replicas, hmc_ha
     if ((e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking)) != cudaSuccess)
         return bail(cuda_fail(h, e, "capture stream create"));
     if ((e = hmc::mpm_prepare()) != cudaSuccess) return bail(cuda_fail(h, e, "MPM kernel attribute"));
+    if ((e = hmc::sweep_prepare()) != cudaSuccess) return bail(cuda_fail(h, e, "sweep kernel attribute"));
     struct Alloc { void **ptr; size_t bytes; const char *what; };
     const size_t nodes_b = node_bytes(h);
     Alloc allocs[] = {

@@ -13,8 +13,8 @@ namespace hmc {
 // Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds of two
 // 32x32 -> 64-bit products with the Weyl key increments between rounds.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint2 philox_r01(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
-                                            uint32_t k0, uint32_t k1) {
+__device__ __forceinline__ uint4 philox4(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
+                                         uint32_t k1) {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
         const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
@@ -27,7 +27,7 @@ __device__ __forceinline__ uint2 philox_r01(uint32_t c0, uint32_t c1, uint32_t c
         k0 += 0x9E3779B9u;
         k1 += 0xBB67AE85u;
     }
-    return make_uint2(c0, c1);
+    return make_uint4(c0, c1, c2, c3);
 }
 
 // ---------------------------------------------------------------------------

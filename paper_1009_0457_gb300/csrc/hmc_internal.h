@@ -161,6 +161,7 @@ cudaError_t zone_prepare();        // opt the zone kernels into their dynamic sh
 std::vector<uint16_t> zone_schedule();   // empty if it does not fit the kernel's table
 void zone_element_tables(const double *Cv, int Q, std::vector<double> &out);
 cudaError_t mpm_prepare();  // opt the MPM kernels into their dynamic shared memory (once, before any capture)
+cudaError_t sweep_prepare();  // opt the elastic sweeps into their trial list in shared memory
 template <typename T>
 int mpm_per_sm(int variant);  // resident MPM CTAs per SM
 

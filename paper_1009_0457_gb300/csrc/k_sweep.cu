@@ -4,21 +4,31 @@
 // constant-traction zone shift (Eqs. 6-8 and 13) from the stored stress, or its
 // constant-strain reading.
 //
-// One thread per 2x2x2 block: it tries the block's four sites of the sweep's
-// colour.  A CTA covers 256 blocks of one replica of the batch.  Loads per
-// block: the block's 16 B of spins, the other colour's 8 B quad of the six face
-// neighbours (cache hits: every quad is some other thread's own), and six 16 B
-// stress vectors (FP32).  Writes: the colour's 8 B quad when a site changed.
-// Same-colour sites share no neighbour, so the in-place update is race free.
+// One thread per 2x2x2 block: it draws the trials of the block's four sites of
+// the sweep's colour.  A CTA covers 256 blocks of one replica of the batch.
+// Loads per block: the block's 16 B of spins, the other colour's 8 B quad of
+// the six face neighbours (cache hits: every quad is some other thread's own),
+// and six 16 B stress vectors (FP32).  Writes: the colour's 8 B quad when a site
+// changed.  Same-colour sites share no neighbour, so the in-place update is race
+// free.  Two sites of a colour share one Philox4x32-10 block (four words, two
+// per site).
+//
+// With an elastic term, the trials that change the orientation (a minority:
+// interior sites copy their own orientation) are listed in shared memory with
+// their stress, and the CTA's threads then evaluate the listed trials densely,
+// so that the zone energies and the logarithm of the Metropolis threshold run
+// with full warps rather than on the few lanes whose site needs them.
 //
 // With the 27-point zone the sweep only lists its non-trivial trials (site,
-// replica, old and new orientation, the acceptance draw) with one atomic per
-// warp; the zone kernel decides them.
+// replica, old and new orientation, the acceptance draw) in global memory with
+// one atomic per warp; the zone kernel decides them.
 #include "hmc_device.cuh"
 
 namespace hmc {
 
 namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
 
 template <typename T>
 struct Vec4;
@@ -71,6 +81,7 @@ struct Row20<double> {
     }
 };
 
+// explicitly rounded, so that every mode evaluates it identically
 template <typename T>
 __device__ __forceinline__ T zone_phi(const T *__restrict__ w, const T (&s)[6]) {
     Row20<T> r;
@@ -78,9 +89,10 @@ __device__ __forceinline__ T zone_phi(const T *__restrict__ w, const T (&s)[6]) 
     T acc = T(0);
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
-        const T p = r.v[6 * m] * s[0] + r.v[6 * m + 1] * s[1] + r.v[6 * m + 2] * s[2] + r.v[6 * m + 3] * s[3] +
-                    r.v[6 * m + 4] * s[4] + r.v[6 * m + 5] * s[5];
-        acc += p * p;
+        T p = rmul(r.v[6 * m], s[0]);
+#pragma unroll
+        for (int k = 1; k < 6; ++k) p = rfma(r.v[6 * m + k], s[k], p);
+        acc = rfma(p, p, acc);
     }
     return acc;
 }
@@ -88,18 +100,58 @@ __device__ __forceinline__ T zone_phi(const T *__restrict__ w, const T (&s)[6]) 
 __device__ __forceinline__ float log_t(float x) { return logf(x); }
 __device__ __forceinline__ double log_t(double x) { return log(x); }
 
+// Shared-memory list of a CTA's trials that change the orientation (elastic modes):
+// the site's stress (stored mode) or strain (recompute mode), the old and new
+// orientation, the bond-count change, the acceptance draw and the owning thread and slot.
+template <typename T>
+struct SweepList {
+    T sig[6][4 * BLOCK_THREADS];
+    uint32_t qq[4 * BLOCK_THREADS];    // q | q_new << 16
+    uint32_t r1[4 * BLOCK_THREADS];
+    uint32_t own[4 * BLOCK_THREADS];   // thread << 2 | slot, bond change + 8 in bits 16..23
+    uint8_t acc[4 * BLOCK_THREADS];    // decision by (thread, slot)
+    unsigned count;
+};
+
+// warp-aggregated reservation of n entries: returns this lane's first index
+__device__ __forceinline__ unsigned warp_reserve(unsigned *counter, int n, int lane) {
+    int incl = n;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += v;
+    }
+    const int total = __shfl_sync(FULL, incl, 31);
+    unsigned base = 0;
+    if (lane == 31 && total) base = atomicAdd(counter, (unsigned)total);
+    return __shfl_sync(FULL, base, 31) + (unsigned)(incl - n);
+}
+
 template <typename T, int MODE, bool RECOMP>
 __global__ void __launch_bounds__(BLOCK_THREADS, (sizeof(T) == 4 ? 3 : 2)) k_sweep(SweepArgs<T> a, int colour) {
     constexpr bool ELASTIC = MODE == SWEEP_POINT || MODE == SWEEP_STRAIN;   // a point-zone elastic term
     constexpr bool STORED = ELASTIC && !RECOMP;                               // ... from the stored stress
     constexpr bool LIST = MODE == SWEEP_ZONE_LIST;
+    extern __shared__ __align__(16) unsigned char sweep_smem[];
+    SweepList<T> &sl = *reinterpret_cast<SweepList<T> *>(sweep_smem);
     const int r = __ldg(a.cta_rep + blockIdx.x);
     const Replica &R = a.reps[r];
-    const int blk = (blockIdx.x - R.cta_off) * BLOCK_THREADS + threadIdx.x;  // block within the replica
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int blk = (blockIdx.x - R.cta_off) * BLOCK_THREADS + tid;  // block within the replica
+    if (ELASTIC) {
+        if (tid == 0) sl.count = 0;
+        __syncthreads();
+    }
     int nacc = 0;
     uint4 ent[4];   // zone mode: this thread's trials for the list
     int nent = 0;
-    if (blk < R.nblk) {
+    uint16_t out[4] = {0, 0, 0, 0}, qnew[4] = {0, 0, 0, 0};
+    uint32_t pend = 0;   // elastic modes: slots with a listed trial
+    T sg[6][4];          // elastic modes: stress (stored) or strain (recompute) of the colour's four sites
+    uint2 rnd[4];
+    int dEs[4] = {0, 0, 0, 0};
+    const bool live = blk < R.nblk;
+    if (live) {
         const int nbx = R.nbx, nby = R.nby, nbz = R.nbz;
         const int bx = blk % nbx, rr = blk / nbx;
         const int by = rr % nby, bz = rr / nby;
@@ -109,7 +161,7 @@ __global__ void __launch_bounds__(BLOCK_THREADS, (sizeof(T) == 4 ? 3 : 2)) k_swe
         const int byp = blk + (by == nby - 1 ? -(nby - 1) * sxy : sxy);
         const int bzm = blk + (bz == 0 ? (nbz - 1) * sxz : -sxz);
         const int bzp = blk + (bz == nbz - 1 ? -(nbz - 1) * sxz : sxz);
-        uint4 *spins = a.spins + R.blk_off;
+        const uint4 *spins = a.spins + R.blk_off;
         const uint2 *q2 = reinterpret_cast<const uint2 *>(spins);
         const int oc = colour ^ 1;
         const uint4 own4 = spins[blk];
@@ -118,7 +170,6 @@ __global__ void __launch_bounds__(BLOCK_THREADS, (sizeof(T) == 4 ? 3 : 2)) k_swe
         const uint2 Oxm = __ldg(q2 + 2 * bxm + oc), Oxp = __ldg(q2 + 2 * bxp + oc);
         const uint2 Oym = __ldg(q2 + 2 * bym + oc), Oyp = __ldg(q2 + 2 * byp + oc);
         const uint2 Ozm = __ldg(q2 + 2 * bzm + oc), Ozp = __ldg(q2 + 2 * bzp + oc);
-        T sg[6][4];
         if (STORED) {
             const T *sig = a.sig + 48ll * R.blk_off;
 #pragma unroll
@@ -130,20 +181,29 @@ __global__ void __launch_bounds__(BLOCK_THREADS, (sizeof(T) == 4 ? 3 : 2)) k_swe
             }
         }
         const uint32_t mcs = R.st->mcs;
-        // the four sites' Philox draws first: four independent chains for the scheduler
-        uint2 rnd[4];
+        // Two Philox blocks per thread.  The colour's sites pair up as (even-x site, its
+        // partner at x+1, y^1): red slots (0, 1) and (3, 2), black (1, 0) and (2, 3),
+        // leader first; the leader takes words 0 and 1, the partner words 2 and 3.
+        {
+            const int la = colour ? 1 : 0, pa = colour ? 0 : 1, lb = colour ? 2 : 3;
+            const int LA = slot_local(4 * colour + la), LB = slot_local(4 * colour + lb);
+            const uint32_t xa = 2u * bx + (LA & 1), ya = 2u * by + ((LA >> 1) & 1), za = 2u * bz + (LA >> 2);
+            const uint32_t xb = 2u * bx + (LB & 1), yb = 2u * by + ((LB >> 1) & 1), zb = 2u * bz + (LB >> 2);
+            const uint4 wa = philox4(xa + (uint32_t)R.nx * (ya + (uint32_t)R.ny * za), mcs, R.replica, 0u, R.key0,
+                                     R.key1);
+            const uint4 wb = philox4(xb + (uint32_t)R.nx * (yb + (uint32_t)R.ny * zb), mcs, R.replica, 0u, R.key0,
+                                     R.key1);
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int L = slot_local(4 * colour + i);
-            const uint32_t x = 2u * bx + (L & 1), y = 2u * by + ((L >> 1) & 1), z = 2u * bz + (L >> 2);
-            rnd[i] = philox_r01(x + (uint32_t)R.nx * (y + (uint32_t)R.ny * z), mcs, R.replica, 0u, R.key0, R.key1);
+            for (int i = 0; i < 4; ++i)
+                rnd[i] = i == la ? make_uint2(wa.x, wa.y)
+                         : i == pa ? make_uint2(wa.z, wa.w)
+                         : i == lb ? make_uint2(wb.x, wb.y)
+                                   : make_uint2(wb.z, wb.w);
         }
-        const T lam_sd_half = (T)R.lam_sd_half;
-        // recompute mode: the cell's displacement gradients, formed at the first non-trivial trial
+        // recompute mode: the cell's displacement gradients, formed at the first listed trial
         CellGrad<T> g;
         T ebv[6];
         bool have_g = false;
-        uint16_t out[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const int L = slot_local(4 * colour + i);
@@ -168,6 +228,7 @@ __global__ void __launch_bounds__(BLOCK_THREADS, (sizeof(T) == 4 ? 3 : 2)) k_swe
                 qn = (uint16_t)__umulhi(rn.x, (uint32_t)a.nq);
             }
             out[i] = q;
+            qnew[i] = qn;
             if (qn == q) continue;
             if (LIST) {
                 const uint32_t x = 2u * bx + lx, y = 2u * by + ly, z = 2u * bz + lz;
@@ -182,9 +243,16 @@ __global__ void __launch_bounds__(BLOCK_THREADS, (sizeof(T) == 4 ? 3 : 2)) k_swe
             int dE = 0;
 #pragma unroll
             for (int j = 0; j < 6; ++j) dE += (nb[j] == q) - (nb[j] == qn);
-            T dHe = T(0);
-            T er[6];   // recompute mode: the site's strain
-            if (RECOMP && ELASTIC) {
+            if (!ELASTIC) {
+                if (dE <= 0 || (unsigned long long)rn.y < __ldg(a.thr + dE)) {
+                    out[i] = qn;
+                    ++nacc;
+                }
+                continue;
+            }
+            dEs[i] = dE;
+            pend |= 1u << i;
+            if (RECOMP) {
                 if (!have_g) {
                     // the cell's eight corner displacements, as the stress pass reads them
                     const T *u = a.u + 3 * R.blk_off;
@@ -206,109 +274,155 @@ __global__ void __launch_bounds__(BLOCK_THREADS, (sizeof(T) == 4 ? 3 : 2)) k_swe
                     load_ebar<T>(R.st, ebv);
                     have_g = true;
                 }
+                T er[6];
                 point_strain<T>(g, ebv, lx, ly, lz, er);
-            }
-            if (MODE == SWEEP_POINT) {
-                T s[6];
-                if (RECOMP) {
-                    Row24<T> r;
-                    r.load(a.ctab + 24ll * q);
-                    hooke21<T>(r.v, er, s);
-                } else {
 #pragma unroll
-                    for (int k = 0; k < 6; ++k) s[k] = sg[k][i];
+                for (int k = 0; k < 6; ++k) sg[k][i] = er[k];
+            }
+        }
+    }
+
+    if (ELASTIC) {
+        // list the pending trials (every lane of the warp takes part in the reservation)
+        unsigned idx = warp_reserve(&sl.count, __popc(pend), lane);
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            if (pend & (1u << i)) {
+#pragma unroll
+                for (int k = 0; k < 6; ++k) sl.sig[k][idx] = sg[k][i];
+                sl.qq[idx] = (uint32_t)out[i] | ((uint32_t)qnew[i] << 16);
+                sl.r1[idx] = rnd[i].y;
+                sl.own[idx] = (uint32_t)(tid << 2 | i) | ((uint32_t)(dEs[i] + 8) << 16);
+                ++idx;
+            }
+        __syncthreads();
+        // the listed trials, evaluated densely by all threads of the CTA
+        const unsigned n = sl.count;
+        const T lam_sd_half = (T)R.lam_sd_half;
+        for (unsigned e = tid; e < n; e += BLOCK_THREADS) {
+            const uint32_t qq = sl.qq[e], ow = sl.own[e];
+            const uint32_t q = qq & 0xffffu, qn = qq >> 16, r1 = sl.r1[e];
+            const int dE = (int)((ow >> 16) & 0xffu) - 8;
+            T s[6];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) s[k] = sl.sig[k][e];
+            T dHe = T(0);
+            if (MODE == SWEEP_POINT) {
+                if (RECOMP) {
+                    // the entry holds the strain: the stress with the site's stiffness, as the stress pass forms it
+                    T e6[6];
+#pragma unroll
+                    for (int k = 0; k < 6; ++k) e6[k] = s[k];
+                    Row24<T> rw;
+                    rw.load(a.ctab + 24ll * q);
+                    hooke21<T>(rw.v, e6, s);
                 }
                 dHe = lam_sd_half * (zone_phi<T>(a.wtab + 20ll * q, s) - zone_phi<T>(a.wtab + 20ll * qn, s));
-            } else if (MODE == SWEEP_STRAIN) {
-                // e held fixed (stored mode: e = S'(q) s): 1/2 (e.C'(q_new)e - e.C'(q)e)
-                T e[6], sn[6], so[6];
+            } else {
+                // constant strain: e (stored mode: S'(q) s) held fixed, 1/2 (e.C'(q_new)e - e.C'(q)e)
+                T e6[6], sn[6], so[6];
                 if (RECOMP) {
 #pragma unroll
-                    for (int k = 0; k < 6; ++k) e[k] = er[k];
+                    for (int k = 0; k < 6; ++k) e6[k] = s[k];
                 } else {
-                    T s[6];
-#pragma unroll
-                    for (int k = 0; k < 6; ++k) s[k] = sg[k][i];
-                    Row24<T> r;
-                    r.load(a.stab + 24ll * q);
-                    hooke21<T>(r.v, s, e);
+                    Row24<T> rw;
+                    rw.load(a.stab + 24ll * q);
+                    hooke21<T>(rw.v, s, e6);
                 }
                 {
-                    Row24<T> r;
-                    r.load(a.ctab + 24ll * qn);
-                    hooke21<T>(r.v, e, sn);
+                    Row24<T> rw;
+                    rw.load(a.ctab + 24ll * qn);
+                    hooke21<T>(rw.v, e6, sn);
                 }
                 {
-                    Row24<T> r;
-                    r.load(a.ctab + 24ll * q);
-                    hooke21<T>(r.v, e, so);
+                    Row24<T> rw;
+                    rw.load(a.ctab + 24ll * q);
+                    hooke21<T>(rw.v, e6, so);
                 }
                 T d = T(0);
 #pragma unroll
-                for (int k = 0; k < 6; ++k) d += e[k] * (sn[k] - so[k]);
+                for (int k = 0; k < 6; ++k) d = rfma(e6[k], sn[k] - so[k], d);
                 dHe = T(0.5) * (T)R.lam * d;
             }
             bool acc;
-            if (!ELASTIC || dHe == T(0)) {
-                acc = dE <= 0 || (unsigned long long)rn.y < __ldg(a.thr + dE);
+            if (dHe == T(0)) {
+                acc = dE <= 0 || (unsigned long long)r1 < __ldg(a.thr + dE);
             } else {
-                const T H = a.J * (T)dE + dHe;
-                const T u01 = ((T)rn.y + T(0.5)) * T(2.3283064365386963e-10);
+                const T H = rfma(a.J, (T)dE, dHe);
+                const T u01 = ((T)r1 + T(0.5)) * T(2.3283064365386963e-10);
                 const T t = a.kT > T(0) ? -a.kT * log_t(u01) : T(0);
                 acc = H <= t;
             }
-            if (acc) {
-                out[i] = qn;
-                ++nacc;
-            }
+            sl.acc[ow & 0xffffu] = acc ? 1 : 0;
         }
-        if (nacc) {
-            uint2 w;
-            w.x = (uint32_t)out[0] | ((uint32_t)out[1] << 16);
-            w.y = (uint32_t)out[2] | ((uint32_t)out[3] << 16);
-            reinterpret_cast<uint2 *>(spins)[2 * blk + colour] = w;
+        __syncthreads();
+        if (pend) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if ((pend & (1u << i)) && sl.acc[tid << 2 | i]) {
+                    out[i] = qnew[i];
+                    ++nacc;
+                }
         }
     }
+    if (live && nacc) {
+        uint2 w;
+        w.x = (uint32_t)out[0] | ((uint32_t)out[1] << 16);
+        w.y = (uint32_t)out[2] | ((uint32_t)out[3] << 16);
+        reinterpret_cast<uint2 *>(a.spins + R.blk_off)[2 * blk + colour] = w;
+    }
     if (LIST) {
-        // warp-aggregated append: one atomic per warp, entries in lane order
-        const int lane = threadIdx.x & 31;
-        int incl = nent;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int v = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += v;
-        }
-        const int total = __shfl_sync(0xffffffffu, incl, 31);
-        unsigned base = 0;
-        if (lane == 31 && total) base = atomicAdd(a.count, (unsigned)total);
-        base = __shfl_sync(0xffffffffu, base, 31);
-        const unsigned first = base + (unsigned)(incl - nent);
+        const unsigned first = warp_reserve(a.count, nent, lane);
 #pragma unroll
         for (int j = 0; j < 4; ++j)
             if (j < nent) a.work[first + j] = ent[j];
         return;
     }
     // a CTA belongs to one replica: warp totals go to that replica's counter
-    const unsigned tot = __reduce_add_sync(0xffffffffu, (unsigned)nacc);
-    if ((threadIdx.x & 31) == 0 && tot) atomicAdd(&R.st->accepted, (unsigned long long)tot);
+    const unsigned tot = __reduce_add_sync(FULL, (unsigned)nacc);
+    if (lane == 0 && tot) atomicAdd(&R.st->accepted, (unsigned long long)tot);
+}
+
+template <typename T, int MODE, bool RECOMP>
+void launch_one(const SweepArgs<T> &a, int colour, cudaStream_t s) {
+    constexpr bool ELASTIC = MODE == SWEEP_POINT || MODE == SWEEP_STRAIN;
+    k_sweep<T, MODE, RECOMP><<<a.nctas, BLOCK_THREADS, ELASTIC ? sizeof(SweepList<T>) : 0, s>>>(a, colour);
+}
+
+template <typename T, int MODE, bool RECOMP>
+cudaError_t set_smem() {
+    return cudaFuncSetAttribute(k_sweep<T, MODE, RECOMP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sizeof(SweepList<T>));
 }
 
 }  // namespace
 
+cudaError_t sweep_prepare() {
+    cudaError_t e;
+    if ((e = set_smem<float, SWEEP_POINT, false>()) != cudaSuccess) return e;
+    if ((e = set_smem<float, SWEEP_POINT, true>()) != cudaSuccess) return e;
+    if ((e = set_smem<float, SWEEP_STRAIN, false>()) != cudaSuccess) return e;
+    if ((e = set_smem<float, SWEEP_STRAIN, true>()) != cudaSuccess) return e;
+    if ((e = set_smem<double, SWEEP_POINT, false>()) != cudaSuccess) return e;
+    if ((e = set_smem<double, SWEEP_POINT, true>()) != cudaSuccess) return e;
+    if ((e = set_smem<double, SWEEP_STRAIN, false>()) != cudaSuccess) return e;
+    return set_smem<double, SWEEP_STRAIN, true>();
+}
+
 template <typename T>
 cudaError_t launch_sweep(const SweepArgs<T> &a, int colour, int mode, bool recompute, cudaStream_t s) {
     if (mode == SWEEP_POINT && recompute)
-        k_sweep<T, SWEEP_POINT, true><<<a.nctas, BLOCK_THREADS, 0, s>>>(a, colour);
+        launch_one<T, SWEEP_POINT, true>(a, colour, s);
     else if (mode == SWEEP_POINT)
-        k_sweep<T, SWEEP_POINT, false><<<a.nctas, BLOCK_THREADS, 0, s>>>(a, colour);
+        launch_one<T, SWEEP_POINT, false>(a, colour, s);
     else if (mode == SWEEP_STRAIN && recompute)
-        k_sweep<T, SWEEP_STRAIN, true><<<a.nctas, BLOCK_THREADS, 0, s>>>(a, colour);
+        launch_one<T, SWEEP_STRAIN, true>(a, colour, s);
     else if (mode == SWEEP_STRAIN)
-        k_sweep<T, SWEEP_STRAIN, false><<<a.nctas, BLOCK_THREADS, 0, s>>>(a, colour);
+        launch_one<T, SWEEP_STRAIN, false>(a, colour, s);
     else if (mode == SWEEP_ZONE_LIST)
-        k_sweep<T, SWEEP_ZONE_LIST, false><<<a.nctas, BLOCK_THREADS, 0, s>>>(a, colour);
+        launch_one<T, SWEEP_ZONE_LIST, false>(a, colour, s);
     else
-        k_sweep<T, SWEEP_POTTS, false><<<a.nctas, BLOCK_THREADS, 0, s>>>(a, colour);
+        launch_one<T, SWEEP_POTTS, false>(a, colour, s);
     return cudaGetLastError();
 }
 

@@ -210,3 +210,15 @@ def test_polycrystal_modulus_within_uniform_bounds():
     Ev = O.young_modulus_along(np.linalg.inv(Ct.mean(axis=0))[None], n)[0]
     Er = O.young_modulus_along(St.mean(axis=0)[None], n)[0]
     assert abs(Ev - E_V) < 0.01 * E_V and abs(Er - E_R) < 0.01 * E_R
+
+
+def test_paired_site_draws():
+    """Sites (x, y, z), x even, and (x+1, y^1, z) share one Philox4x32-10 block:
+    words 0, 1 and 2, 3 of the block keyed by the even-x site's index."""
+    nx, ny = 10, 6
+    for (x, y, z) in [(0, 0, 0), (4, 3, 2), (8, 5, 1)]:
+        p = x + nx * (y + ny * z)
+        w = O.philox4x32_10([p, 7, 2, 0], [0x12345678, 0x9ABCDEF0])
+        assert O.site_draws(nx, ny, x, y, z, 0x9ABCDEF012345678, 7, 2) == (int(w[0]), int(w[1]))
+        assert O.site_draws(nx, ny, x + 1, y ^ 1, z, 0x9ABCDEF012345678, 7, 2) == (int(w[2]), int(w[3]))
+        assert (x + y + z) % 2 == (x + 1 + (y ^ 1) + z) % 2   # same colour
