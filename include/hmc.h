@@ -34,7 +34,9 @@
  *  - Host-side fault injection for tests (environment variable HMC_FAULT):
  *    "alloc" fails handle creation before any CUDA call, "launch" fails
  *    hmc_mpm_steps / hmc_mc_sweeps before anything is enqueued, "nan" writes a
- *    NaN into the first nodal displacement before the next stress pass.
+ *    NaN into the first nodal displacement before the next stress pass,
+ *    "sweep_wait" makes stored-stress sweeps skip their stress copy so that
+ *    their bounded (1 s per CTA) wait for it runs out: HMC_ERR_TIMEOUT.
  */
 #ifndef HMC_H_
 #define HMC_H_
@@ -226,11 +228,16 @@ hmc_status hmc_mpm_steps(hmc_handle *h, int32_t nsteps, double *elastic_energy);
 hmc_status hmc_compute_stress(hmc_handle *h, double *mean_stress, double *elastic_energy);
 
 /* One red/black half sweep (Sec. "Microstructural Evolution"): every site of
- * `colour` ((x+y+z) even = 0 = red) draws Philox4x32-10 with counter
- * (site, mcs, replica, 0) and key seed, picks a trial orientation, and is
+ * `colour` ((x+y+z) even = 0 = red) takes two words of a Philox4x32-10 block
+ * with counter (s, mcs, replica, 0) and key seed, s the index of the site at
+ * even x of the pair {(x even, y, z), (x+1, y^1, z)} (the even-x site takes
+ * words 0-1, its partner words 2-3), picks a trial orientation, and is
  * accepted by Eq. 5 on J*(change of unlike-neighbour count) plus lambda times
  * the stored-stress zone shift.  The MC step counter is not advanced.
- * *accepted (nullable) receives the number of sites that changed. */
+ * *accepted (nullable) receives the number of sites that changed.  A
+ * stored-stress sweep waits for its asynchronous stress copy with a 1 s limit
+ * per CTA; a CTA whose wait ran out changes no spin, and the next call that
+ * reads the accepted count or the statistics reports HMC_ERR_TIMEOUT once. */
 hmc_status hmc_sweep_half(hmc_handle *h, int32_t colour, int64_t *accepted);
 
 /* Close a Monte Carlo step: with UNIAXIAL control update the mean strain from

@@ -141,7 +141,10 @@ hmc_status cuda_fail(hmc_handle *h, cudaError_t e, const char *what) {
 // ever produced): HMC_FAULT=alloc fails the next handle creation before any
 // CUDA call, =launch fails the next MPM / Monte Carlo launch sequence before it
 // is enqueued, =nan writes a NaN into the first nodal displacement before the
-// next stress pass, so the FP64 reductions report HMC_ERR_NONFINITE.
+// next stress pass, so the FP64 reductions report HMC_ERR_NONFINITE, and
+// =sweep_wait makes the stored-stress sweeps enqueued from then on skip their
+// stress copy, so that each CTA's bounded wait for it runs out (1 s) and the
+// sweep reports HMC_ERR_TIMEOUT.
 bool fault(const char *what) {
     const char *f = std::getenv("HMC_FAULT");
     return f && std::strcmp(f, what) == 0;
@@ -289,13 +292,15 @@ cudaError_t enqueue_sweep(hmc_handle *h, int colour, cudaStream_t s) {
     a.ctab = static_cast<const T *>(h->ctab);
     a.stab = static_cast<const T *>(h->stab);
     a.u = static_cast<const T *>(h->u[h->cur]);
+    a.skip_copy = fault("sweep_wait") ? 1 : 0;
     const bool point = h->p.elastic == HMC_ELASTIC_TRACTION || h->p.elastic == HMC_ELASTIC_STRAIN;
-    if (h->p.elastic != HMC_ELASTIC_ZONE1)
-        return hmc::launch_sweep<T>(a, colour,
-                                    h->p.elastic == HMC_ELASTIC_TRACTION ? hmc::SWEEP_POINT
-                                    : h->p.elastic == HMC_ELASTIC_STRAIN ? hmc::SWEEP_STRAIN
-                                                                         : hmc::SWEEP_POTTS,
-                                    point && !h->p.store_stress, s);
+    if (h->p.elastic != HMC_ELASTIC_ZONE1) {
+        const int mode = h->p.elastic == HMC_ELASTIC_TRACTION ? hmc::SWEEP_POINT
+                         : h->p.elastic == HMC_ELASTIC_STRAIN ? hmc::SWEEP_STRAIN
+                                                              : hmc::SWEEP_POTTS;
+        const bool recompute = point && !h->p.store_stress;
+        return hmc::launch_sweep<T>(a, colour, mode, recompute, s);
+    }
     // 27-point zone: list the trials, copy the spins as they are at the start of the half step,
     // then decide every listed trial against that copy
     cudaError_t e;
@@ -359,10 +364,21 @@ hmc_status read_accepted(hmc_handle *h, int64_t *acc) {
     HMC_CK(h, cudaMemcpy2DAsync(bad.data(), sizeof(int32_t), &h->st->nonfinite, sizeof(DevState), sizeof(int32_t),
                                 h->R, cudaMemcpyDeviceToHost, h->stream),
            "download");
+    std::vector<int32_t> late(h->R);
+    HMC_CK(h, cudaMemcpy2DAsync(late.data(), sizeof(int32_t), &h->st->wait_timeout, sizeof(DevState),
+                                sizeof(int32_t), h->R, cudaMemcpyDeviceToHost, h->stream),
+           "download");
     HMC_CK(h, cudaStreamSynchronize(h->stream), "sync");
     int64_t s = 0;
     for (auto x : a) s += (int64_t)x;
     *acc = s;
+    for (int r = 0; r < h->R; ++r)
+        if (late[r]) {
+            // reported once: the sweep that gave up changed nothing, and later sweeps start clean
+            HMC_CK(h, cudaMemset2DAsync(&h->st->wait_timeout, sizeof(DevState), 0, sizeof(int32_t), h->R, h->stream),
+                   "memset");
+            return fail(h, HMC_ERR_TIMEOUT, "a sweep's stress copy did not complete in replica " + std::to_string(r));
+        }
     for (int r = 0; r < h->R; ++r)
         if (bad[r]) return fail(h, HMC_ERR_NONFINITE, "non-finite stress or energy in replica " + std::to_string(r));
     return HMC_OK;
@@ -645,6 +661,10 @@ hmc_status read_stats(hmc_handle *h, double *mean, double *energy) {
     DevState st;
     HMC_CK(h, cudaMemcpyAsync(&st, sel_st(h), sizeof(st), cudaMemcpyDeviceToHost, h->stream), "state download");
     HMC_CK(h, cudaStreamSynchronize(h->stream), "sync");
+    if (st.wait_timeout) {
+        HMC_CK(h, cudaMemsetAsync(&sel_st(h)->wait_timeout, 0, sizeof(int32_t), h->stream), "memset");
+        return fail(h, HMC_ERR_TIMEOUT, "a sweep's stress copy did not complete");
+    }
     if (st.nonfinite) return fail(h, HMC_ERR_NONFINITE, "non-finite stress or energy");
     if (mean)
         for (int i = 0; i < 6; ++i) mean[i] = st.mean_sigma[i];
@@ -841,6 +861,8 @@ hmc_status hmc_create_batch(const hmc_params *params, int32_t n_replicas, hmc_ha
         rd[r].lam_sd_half = R.lam_sd_half;
         rd[r].lam = R.lam;
         rd[r].st = h->st + r;
+        rd[r].divx = hmc::make_udiv((uint32_t)R.nbx);
+        rd[r].divy = hmc::make_udiv((uint32_t)R.nby);
         for (int c = 0; c < R.ncta; ++c) ctarep[R.cta_off + c] = r;
     }
     if ((e = cudaMemcpy(h->st, st.data(), sizeof(DevState) * st.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||

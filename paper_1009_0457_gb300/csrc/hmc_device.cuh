@@ -52,6 +52,19 @@ __device__ __forceinline__ uint16_t quad_get(const uint2 &q, int i) {
     return (uint16_t)((i & 1) ? (w >> 16) : (w & 0xffffu));
 }
 
+__device__ __forceinline__ uint32_t udiv(const UDiv &D, uint32_t n) {
+    const uint32_t t = __umulhi(D.m, n);
+    return (t + ((n - t) >> D.s1)) >> D.s2;
+}
+
+// block coordinates of block `blk` of a replica
+__device__ __forceinline__ void block_xyz(const Replica &R, int blk, int &bx, int &by, int &bz) {
+    const uint32_t rr = udiv(R.divx, (uint32_t)blk), zz = udiv(R.divy, rr);
+    bx = blk - (int)rr * R.nbx;
+    by = (int)rr - (int)zz * R.nby;
+    bz = (int)zz;
+}
+
 __host__ __device__ __forceinline__ int wrapi(int a, int n) {
     a %= n;
     return a < 0 ? a + n : a;

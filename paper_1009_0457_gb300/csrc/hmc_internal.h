@@ -43,13 +43,29 @@ struct DevState {
     int32_t nonfinite;       // set when a reduction produced a non-finite value
     int32_t bad_spin;        // set by the upload check when a spin is >= Q
     double sig0;             // prescribed uniaxial stress (traction control)
+    int32_t wait_timeout;    // set when a sweep gave up waiting for a tile copy
+    int32_t pad1;
 };
+
+// Division by an invariant 32-bit divisor d >= 1 with one high multiply
+// (Granlund & Montgomery, PLDI'94, Sec. 4): l = ceil(log2 d),
+// m = floor(2^32 (2^l - d) / d) + 1, t = mulhi(m, n), n / d = (t + ((n - t) >> s1)) >> s2
+// with s1 = min(l, 1), s2 = max(l - 1, 0).  Exact for every 32-bit n.
+struct UDiv {
+    uint32_t m, s1, s2;
+};
+inline UDiv make_udiv(uint32_t d) {
+    uint32_t l = 0;
+    while (l < 31 && (1u << l) < d) ++l;
+    const unsigned long long m = ((((unsigned long long)1 << l) - d) << 32) / d + 1;
+    return UDiv{(uint32_t)m, l < 1 ? l : 1u, l > 0 ? l - 1 : 0u};
+}
 
 // One replica of a batch (a single handle is a batch of one).  Replica r's
 // blocks, nodes and stress occupy [blk_off, blk_off + nblk) of the batch
 // arrays (nodes are indexed like blocks, 3 values each; the stress of a
 // replica is its own [2][6][nblk][4] array at 48 * blk_off).
-struct Replica {
+struct alignas(16) Replica {   // 16 B aligned: the pipelined sweep stages it with a bulk copy
     int nx, ny, nz, nbx, nby, nbz;
     int nblk;                 // 2x2x2 blocks = MPM cells = background nodes
     int cta_off, ncta;        // its CTAs in the block-parallel grids (BLOCK_THREADS each)
@@ -59,7 +75,10 @@ struct Replica {
     double lam_sd_half;       // lambda * (S11 - S12 - S44/2) / 2
     double lam;               // lambda: MC energy per GPa of elastic energy density
     DevState *st;
+    UDiv divx, divy;          // division by nbx and by nby
+    uint32_t pad3;
 };
+static_assert(sizeof(Replica) % 16 == 0, "Replica must be a whole number of 16 B units");
 
 constexpr int BLOCK_THREADS = 256;   // threads of the sweep and stress CTAs
 
@@ -114,6 +133,8 @@ struct SweepArgs {
     const T *ctab, *stab;            // constant-strain mode: stiffness and compliance rows (Q x 24)
     const T *u;                      // recompute mode: nodal displacement (the stress of a trial site
                                      // is formed from it as the stress pass would)
+    int skip_copy;                   // fault injection: the stored-stress copy is never started, so its
+                                     // bounded wait runs out (HMC_FAULT=sweep_wait)
 };
 
 // Elastic term of a sweep: none, one-point zone from the stored stress (constant
@@ -161,7 +182,7 @@ cudaError_t zone_prepare();        // opt the zone kernels into their dynamic sh
 std::vector<uint16_t> zone_schedule();   // empty if it does not fit the kernel's table
 void zone_element_tables(const double *Cv, int Q, std::vector<double> &out);
 cudaError_t mpm_prepare();  // opt the MPM kernels into their dynamic shared memory (once, before any capture)
-cudaError_t sweep_prepare();  // opt the elastic sweeps into their trial list in shared memory
+cudaError_t sweep_prepare();  // opt the elastic sweeps into their shared memory
 template <typename T>
 int mpm_per_sm(int variant);  // resident MPM CTAs per SM
 

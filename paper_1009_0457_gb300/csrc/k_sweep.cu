@@ -5,19 +5,25 @@
 // constant-strain reading.
 //
 // One thread per 2x2x2 block: it draws the trials of the block's four sites of
-// the sweep's colour.  A CTA covers 256 blocks of one replica of the batch.
-// Loads per block: the block's 16 B of spins, the other colour's 8 B quad of
-// the six face neighbours (cache hits: every quad is some other thread's own),
-// and six 16 B stress vectors (FP32).  Writes: the colour's 8 B quad when a site
-// changed.  Same-colour sites share no neighbour, so the in-place update is race
-// free.  Two sites of a colour share one Philox4x32-10 block (four words, two
-// per site).
+// the sweep's colour; a tile of 256 blocks of one replica is one CTA's work.
+// Per block the sweep reads the block's 16 B of spins, the other colour's 8 B
+// quad of the six face neighbours and (stored-stress elastic forms) the colour's
+// 96 B of stress (FP32), and writes the colour's 8 B quad when a site changed.
+// Same-colour sites share no neighbour, so the in-place update is race free.
+// Two sites of a colour share one Philox4x32-10 block (four words, two per site).
+//
+// Five CTAs per SM (FP32).  With the stored
+// stress, thread 0 starts a bulk asynchronous copy of the tile's stress of the
+// colour into shared memory (completing on an mbarrier) as the CTA begins; the
+// threads meanwhile load their spins and neighbours and run the Philox and
+// bond arithmetic, and only the listed trials read the staged stress.  The
+// acceptance count is reduced per CTA before its one atomic.
 //
 // With an elastic term, the trials that change the orientation (a minority:
-// interior sites copy their own orientation) are listed in shared memory with
-// their stress, and the CTA's threads then evaluate the listed trials densely,
-// so that the zone energies and the logarithm of the Metropolis threshold run
-// with full warps rather than on the few lanes whose site needs them.
+// interior sites copy their own orientation) are listed in shared memory, and
+// the CTA's threads then evaluate the listed trials densely, so that the zone
+// energies and the logarithm of the Metropolis threshold run with full warps
+// rather than on the few lanes whose site needs them.
 //
 // With the 27-point zone the sweep only lists its non-trivial trials (site,
 // replica, old and new orientation, the acceptance draw) in global memory with
@@ -29,26 +35,6 @@ namespace hmc {
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
-
-template <typename T>
-struct Vec4;
-template <>
-struct Vec4<float> {
-    float v[4];
-    __device__ __forceinline__ void load(const float *p) {
-        const float4 t = __ldcs(reinterpret_cast<const float4 *>(p));  // streamed once per sweep
-        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
-    }
-};
-template <>
-struct Vec4<double> {
-    double v[4];
-    __device__ __forceinline__ void load(const double *p) {
-        const double2 a = __ldcs(reinterpret_cast<const double2 *>(p));
-        const double2 b = __ldcs(reinterpret_cast<const double2 *>(p) + 1);
-        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
-    }
-};
 
 // Phi(q; sigma) = sum over the three crystal axes of (a_m . sigma . a_m)^2, from
 // the Voigt weight vectors of the axes.  For one cubic material the zone energy
@@ -103,11 +89,11 @@ __device__ __forceinline__ float log_t(float x) { return __logf(x); }
 __device__ __forceinline__ double log_t(double x) { return log(x); }
 
 // Shared-memory list of a CTA's trials that change the orientation (elastic modes):
-// the site's stress (stored mode) or strain (recompute mode), the old and new
-// orientation, the bond-count change, the acceptance draw and the owning thread and slot.
-template <typename T>
+// the old and new orientation, the acceptance draw, the owning thread and slot with
+// the bond-count change, and (flat kernel) the site's stress or strain.
+template <typename T, bool SIG>
 struct SweepList {
-    T sig[6][4 * BLOCK_THREADS];
+    T sig[SIG ? 6 : 1][SIG ? 4 * BLOCK_THREADS : 1];
     uint32_t qq[4 * BLOCK_THREADS];    // q | q_new << 16
     uint32_t r1[4 * BLOCK_THREADS];
     uint32_t own[4 * BLOCK_THREADS];   // thread << 2 | slot, bond change + 8 in bits 16..23
@@ -129,130 +115,278 @@ __device__ __forceinline__ unsigned warp_reserve(unsigned *counter, int n, int l
     return __shfl_sync(FULL, base, 31) + (unsigned)(incl - n);
 }
 
+// The Philox words of the colour's four sites of block (bx, by, bz).  The colour's
+// sites pair up as (even-x site, its partner at x+1, y^1): red slots (0, 1) and
+// (3, 2), black (1, 0) and (2, 3), leader first; one Philox4x32-10 block per pair,
+// counter (leader's site index, Monte Carlo step, replica, 0); the leader takes
+// words 0 and 1, the partner words 2 and 3.
+template <int COL>
+__device__ __forceinline__ void block_draws(const Replica &R, int bx, int by, int bz, uint32_t mcs,
+                                            uint2 (&rnd)[4]) {
+    constexpr int la = COL ? 1 : 0, lb = COL ? 2 : 3;
+    constexpr int LA = slot_local(4 * COL + la), LB = slot_local(4 * COL + lb);
+    const uint32_t x0 = 2u * (uint32_t)bx, y0 = 2u * (uint32_t)by, z0 = 2u * (uint32_t)bz;
+    const uint32_t nx = (uint32_t)R.nx, ny = (uint32_t)R.ny;
+    const uint32_t sa = x0 + (LA & 1) + nx * (y0 + ((LA >> 1) & 1) + ny * (z0 + (LA >> 2)));
+    const uint32_t sb = x0 + (LB & 1) + nx * (y0 + ((LB >> 1) & 1) + ny * (z0 + (LB >> 2)));
+    const uint4 wa = philox4(sa, mcs, R.replica, 0u, R.key0, R.key1);
+    const uint4 wb = philox4(sb, mcs, R.replica, 0u, R.key0, R.key1);
+    rnd[la] = make_uint2(wa.x, wa.y);
+    rnd[la ^ 1] = make_uint2(wa.z, wa.w);
+    rnd[lb] = make_uint2(wb.x, wb.y);
+    rnd[lb ^ 1] = make_uint2(wb.z, wb.w);
+}
+
+// The colour's four trials of a block: current and proposed orientation and the
+// bond-count change dE = (like bonds lost) - (like bonds gained), zero when the
+// proposal keeps the orientation.  O is the block's own quad of the other colour,
+// N its -x, +x, -y, +y, -z, +z neighbours' quads of the other colour.
+template <int COL>
+__device__ __forceinline__ void block_trials(int trial, int nq, const uint2 &mine, const uint2 &O,
+                                             const uint2 (&N)[6], const uint2 (&rnd)[4], uint16_t (&q)[4],
+                                             uint16_t (&qn)[4], int (&dE)[4]) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int L = slot_local(4 * COL + i);
+        const int lx = L & 1, ly = (L >> 1) & 1, lz = L >> 2;
+        uint16_t nb[6];
+        nb[0] = quad_get(lx ? O : N[0], i);
+        nb[1] = quad_get(lx ? N[1] : O, i);
+        nb[2] = quad_get(ly ? O : N[2], i ^ 1);
+        nb[3] = quad_get(ly ? N[3] : O, i ^ 1);
+        nb[4] = quad_get(lz ? O : N[4], i ^ 2);
+        nb[5] = quad_get(lz ? N[5] : O, i ^ 2);
+        const uint16_t qo = quad_get(mine, i);
+        uint16_t qnew;
+        if (trial == 0) {
+            const uint32_t k = __umulhi(rnd[i].x, 6u);
+            qnew = nb[0];
+#pragma unroll
+            for (int j = 1; j < 6; ++j)
+                if (k == (uint32_t)j) qnew = nb[j];
+        } else {
+            qnew = (uint16_t)__umulhi(rnd[i].x, (uint32_t)nq);
+        }
+        int d = 0;
+#pragma unroll
+        for (int j = 0; j < 6; ++j) d += (int)(nb[j] == qo) - (int)(nb[j] == qnew);
+        q[i] = qo;
+        qn[i] = qnew;
+        dE[i] = d;
+    }
+}
+
+// Elastic energy change of a listed trial from the site's stress s (stored forms)
+// or, for the recomputing point form, from its strain (then s is overwritten with
+// the stress the stress pass would form).
 template <typename T, int MODE, bool RECOMP>
-__global__ void __launch_bounds__(BLOCK_THREADS, (sizeof(T) == 4 ? 4 : 2)) k_sweep(SweepArgs<T> a, int colour) {
+__device__ __forceinline__ T trial_dhe(const SweepArgs<T> &a, const Replica &R, uint32_t q, uint32_t qn, T (&s)[6]) {
+    if (MODE == SWEEP_POINT) {
+        if (RECOMP) {
+            T e6[6];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) e6[k] = s[k];
+            Row24<T> rw;
+            rw.load(a.ctab + 24ll * q);
+            hooke21<T>(rw.v, e6, s);
+        }
+        return (T)R.lam_sd_half * (zone_phi<T>(a.wtab + 20ll * q, s) - zone_phi<T>(a.wtab + 20ll * qn, s));
+    }
+    // constant strain: e (stored forms: S'(q) s) held fixed, 1/2 (e.C'(q_new)e - e.C'(q)e)
+    T e6[6], sn[6], so[6];
+    if (RECOMP) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) e6[k] = s[k];
+    } else {
+        Row24<T> rw;
+        rw.load(a.stab + 24ll * q);
+        hooke21<T>(rw.v, s, e6);
+    }
+    {
+        Row24<T> rw;
+        rw.load(a.ctab + 24ll * qn);
+        hooke21<T>(rw.v, e6, sn);
+    }
+    {
+        Row24<T> rw;
+        rw.load(a.ctab + 24ll * q);
+        hooke21<T>(rw.v, e6, so);
+    }
+    T d = T(0);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) d = rfma(e6[k], sn[k] - so[k], d);
+    return T(0.5) * (T)R.lam * d;
+}
+
+// Metropolis decision (Eq. 5): the integer threshold table when the elastic term
+// vanishes, otherwise H <= -kT ln u with u = (r1 + 1/2) 2^-32.
+template <typename T>
+__device__ __forceinline__ bool metropolis(const SweepArgs<T> &a, int dE, T dHe, uint32_t r1) {
+    if (dHe == T(0)) return dE <= 0 || (unsigned long long)r1 < __ldg(a.thr + dE);
+    const T H = rfma(a.J, (T)dE, dHe);
+    const T u01 = ((T)r1 + T(0.5)) * T(2.3283064365386963e-10);
+    const T t = a.kT > T(0) ? -a.kT * log_t(u01) : T(0);
+    return H <= t;
+}
+
+// ---------------------------------------------------------------------------
+// mbarrier and asynchronous-copy primitives (inline PTX)
+// ---------------------------------------------------------------------------
+constexpr long long WAIT_NS = 1000000000ll;      // a wait not over after 1 s is a failure
+constexpr int WAIT_POLLS = 1 << 24;              // backstop on the number of polls
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long *b, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *b, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_test(unsigned long long *b, unsigned parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return (long long)t;
+}
+// wait for the phase of the given parity to complete; false after the time limit
+__device__ __forceinline__ bool mbar_wait(unsigned long long *b, unsigned parity) {
+    if (mbar_test(b, parity)) return true;
+    const long long t0 = global_ns();
+    for (int i = 0; i < WAIT_POLLS; ++i) {
+        if (mbar_test(b, parity)) return true;
+        if (global_ns() - t0 > WAIT_NS) break;
+    }
+    return false;
+}
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes, unsigned long long *b) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(b))
+                 : "memory");
+}
+// ---------------------------------------------------------------------------
+// Flat kernel: one CTA per tile.  With the stored stress, thread 0 starts a bulk
+// copy of the tile's stress of the colour into shared memory as the CTA begins;
+// only the listed trials read it, after the threads' own loads and arithmetic.
+// ---------------------------------------------------------------------------
+template <typename T, bool STORED>
+struct FlatSmem;
+template <typename T>
+struct FlatSmem<T, false> {
+    SweepList<T, true> list;
+};
+template <typename T>
+struct FlatSmem<T, true> {
+    T sig[6][4 * BLOCK_THREADS];
+    SweepList<T, false> list;
+    unsigned long long bar;
+};
+
+template <typename T, int MODE, bool RECOMP>
+constexpr int flat_min_ctas() {
+    return sizeof(T) == 8 ? 2 : RECOMP ? 3 : MODE == SWEEP_ZONE_LIST ? 4 : 5;
+}
+
+template <typename T, int MODE, bool RECOMP, int COL>
+__global__ void __launch_bounds__(BLOCK_THREADS, flat_min_ctas<T, MODE, RECOMP>()) k_sweep(SweepArgs<T> a) {
     constexpr bool ELASTIC = MODE == SWEEP_POINT || MODE == SWEEP_STRAIN;   // a point-zone elastic term
     constexpr bool STORED = ELASTIC && !RECOMP;                               // ... from the stored stress
     constexpr bool LIST = MODE == SWEEP_ZONE_LIST;
-    extern __shared__ __align__(16) unsigned char sweep_smem[];
-    SweepList<T> &sl = *reinterpret_cast<SweepList<T> *>(sweep_smem);
+    extern __shared__ __align__(128) unsigned char sweep_smem[];
+    FlatSmem<T, STORED> &fs = *reinterpret_cast<FlatSmem<T, STORED> *>(sweep_smem);
+    auto &sl = fs.list;
     const int r = __ldg(a.cta_rep + blockIdx.x);
     const Replica &R = a.reps[r];
     const int tid = threadIdx.x, lane = tid & 31;
-    const int blk = (blockIdx.x - R.cta_off) * BLOCK_THREADS + tid;  // block within the replica
+    const int t0 = (blockIdx.x - R.cta_off) * BLOCK_THREADS;
+    const int blk = t0 + tid;  // block within the replica
     if (ELASTIC) {
-        if (tid == 0) sl.count = 0;
+        if (tid == 0) {
+            sl.count = 0;
+            if constexpr (STORED) {
+                // the colour's stress of the tile: six components, four values per block, each
+                // source a multiple of 16 B in address and size
+                const unsigned nb = (unsigned)min(BLOCK_THREADS, R.nblk - t0);
+                mbar_init(&fs.bar, 1);
+                mbar_init_fence();
+                if (!a.skip_copy) {
+                    mbar_expect_tx(&fs.bar, nb * 24u * (unsigned)sizeof(T));
+                    const T *sig = a.sig + 48ll * R.blk_off + 4ll * ((long long)(COL * 6) * R.nblk + t0);
+#pragma unroll
+                    for (int k = 0; k < 6; ++k)
+                        bulk_load(&fs.sig[k][0], sig + 4ll * k * R.nblk, nb * 4u * (unsigned)sizeof(T), &fs.bar);
+                }
+            }
+        }
         __syncthreads();
     }
     int nacc = 0;
     uint4 ent[4];   // zone mode: this thread's trials for the list
     int nent = 0;
-    uint16_t out[4] = {0, 0, 0, 0}, qnew[4] = {0, 0, 0, 0};
+    uint16_t out[4] = {0, 0, 0, 0}, qn[4] = {0, 0, 0, 0};
     uint32_t pend = 0;   // elastic modes: slots with a listed trial
-    T sg[6][4];          // elastic modes: stress (stored) or strain (recompute) of the colour's four sites
+    T sg[6][4];          // recompute mode: strain of the colour's four sites
     uint2 rnd[4];
-    int dEs[4] = {0, 0, 0, 0};
+    int dE[4] = {0, 0, 0, 0};
     const bool live = blk < R.nblk;
     if (live) {
         const int nbx = R.nbx, nby = R.nby, nbz = R.nbz;
-        const int bx = blk % nbx, rr = blk / nbx;
-        const int by = rr % nby, bz = rr / nby;
+        int bx, by, bz;
+        block_xyz(R, blk, bx, by, bz);
         const int sxy = nbx, sxz = nbx * nby;
-        const int bxm = blk + (bx == 0 ? nbx - 1 : -1), bxp = blk + (bx == nbx - 1 ? 1 - nbx : 1);
-        const int bym = blk + (by == 0 ? (nby - 1) * sxy : -sxy);
-        const int byp = blk + (by == nby - 1 ? -(nby - 1) * sxy : sxy);
-        const int bzm = blk + (bz == 0 ? (nbz - 1) * sxz : -sxz);
-        const int bzp = blk + (bz == nbz - 1 ? -(nbz - 1) * sxz : sxz);
         const uint4 *spins = a.spins + R.blk_off;
         const uint2 *q2 = reinterpret_cast<const uint2 *>(spins);
-        const int oc = colour ^ 1;
+        constexpr int oc = COL ^ 1;
         const uint4 own4 = spins[blk];
-        const uint2 mine = colour ? make_uint2(own4.z, own4.w) : make_uint2(own4.x, own4.y);
+        const uint2 mine = COL ? make_uint2(own4.z, own4.w) : make_uint2(own4.x, own4.y);
         const uint2 O = oc ? make_uint2(own4.z, own4.w) : make_uint2(own4.x, own4.y);
-        const uint2 Oxm = __ldg(q2 + 2 * bxm + oc), Oxp = __ldg(q2 + 2 * bxp + oc);
-        const uint2 Oym = __ldg(q2 + 2 * bym + oc), Oyp = __ldg(q2 + 2 * byp + oc);
-        const uint2 Ozm = __ldg(q2 + 2 * bzm + oc), Ozp = __ldg(q2 + 2 * bzp + oc);
-        if (STORED) {
-            const T *sig = a.sig + 48ll * R.blk_off;
-#pragma unroll
-            for (int k = 0; k < 6; ++k) {
-                Vec4<T> t;
-                t.load(sig + 4ll * ((long long)(colour * 6 + k) * R.nblk + blk));
-#pragma unroll
-                for (int i = 0; i < 4; ++i) sg[k][i] = t.v[i];
-            }
-        }
-        const uint32_t mcs = R.st->mcs;
-        // Two Philox blocks per thread.  The colour's sites pair up as (even-x site, its
-        // partner at x+1, y^1): red slots (0, 1) and (3, 2), black (1, 0) and (2, 3),
-        // leader first; the leader takes words 0 and 1, the partner words 2 and 3.
-        {
-            const int la = colour ? 1 : 0, pa = colour ? 0 : 1, lb = colour ? 2 : 3;
-            const int LA = slot_local(4 * colour + la), LB = slot_local(4 * colour + lb);
-            const uint32_t xa = 2u * bx + (LA & 1), ya = 2u * by + ((LA >> 1) & 1), za = 2u * bz + (LA >> 2);
-            const uint32_t xb = 2u * bx + (LB & 1), yb = 2u * by + ((LB >> 1) & 1), zb = 2u * bz + (LB >> 2);
-            const uint4 wa = philox4(xa + (uint32_t)R.nx * (ya + (uint32_t)R.ny * za), mcs, R.replica, 0u, R.key0,
-                                     R.key1);
-            const uint4 wb = philox4(xb + (uint32_t)R.nx * (yb + (uint32_t)R.ny * zb), mcs, R.replica, 0u, R.key0,
-                                     R.key1);
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-                rnd[i] = i == la ? make_uint2(wa.x, wa.y)
-                         : i == pa ? make_uint2(wa.z, wa.w)
-                         : i == lb ? make_uint2(wb.x, wb.y)
-                                   : make_uint2(wb.z, wb.w);
-        }
+        uint2 N[6];
+        N[0] = __ldg(q2 + 2 * (blk + (bx == 0 ? nbx - 1 : -1)) + oc);
+        N[1] = __ldg(q2 + 2 * (blk + (bx == nbx - 1 ? 1 - nbx : 1)) + oc);
+        N[2] = __ldg(q2 + 2 * (blk + (by == 0 ? (nby - 1) * sxy : -sxy)) + oc);
+        N[3] = __ldg(q2 + 2 * (blk + (by == nby - 1 ? -(nby - 1) * sxy : sxy)) + oc);
+        N[4] = __ldg(q2 + 2 * (blk + (bz == 0 ? (nbz - 1) * sxz : -sxz)) + oc);
+        N[5] = __ldg(q2 + 2 * (blk + (bz == nbz - 1 ? -(nbz - 1) * sxz : sxz)) + oc);
+        block_draws<COL>(R, bx, by, bz, R.st->mcs, rnd);
+        uint16_t q[4];
+        block_trials<COL>(a.trial, a.nq, mine, O, N, rnd, q, qn, dE);
         // recompute mode: the cell's displacement gradients, formed at the first listed trial
         CellGrad<T> g;
         T ebv[6];
         bool have_g = false;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            const int L = slot_local(4 * colour + i);
+            out[i] = q[i];
+            if (qn[i] == q[i]) continue;
+            const int L = slot_local(4 * COL + i);
             const int lx = L & 1, ly = (L >> 1) & 1, lz = L >> 2;
-            const uint16_t q = quad_get(mine, i);
-            uint16_t nb[6];
-            nb[0] = quad_get(lx ? O : Oxm, i);
-            nb[1] = quad_get(lx ? Oxp : O, i);
-            nb[2] = quad_get(ly ? O : Oym, i ^ 1);
-            nb[3] = quad_get(ly ? Oyp : O, i ^ 1);
-            nb[4] = quad_get(lz ? O : Ozm, i ^ 2);
-            nb[5] = quad_get(lz ? Ozp : O, i ^ 2);
-            const uint2 rn = rnd[i];
-            uint16_t qn;
-            if (a.trial == 0) {
-                const uint32_t k = __umulhi(rn.x, 6u);
-                qn = nb[0];
-#pragma unroll
-                for (int j = 1; j < 6; ++j)
-                    if (k == (uint32_t)j) qn = nb[j];
-            } else {
-                qn = (uint16_t)__umulhi(rn.x, (uint32_t)a.nq);
-            }
-            out[i] = q;
-            qnew[i] = qn;
-            if (qn == q) continue;
             if (LIST) {
                 const uint32_t x = 2u * bx + lx, y = 2u * by + ly, z = 2u * bz + lz;
                 const uint4 en = make_uint4(x + (uint32_t)R.nx * (y + (uint32_t)R.ny * z), (uint32_t)r,
-                                            (uint32_t)qn | ((uint32_t)q << 16), rn.y);
+                                            (uint32_t)qn[i] | ((uint32_t)q[i] << 16), rnd[i].y);
 #pragma unroll
                 for (int j = 0; j < 4; ++j)
                     if (j == nent) ent[j] = en;
                 ++nent;
                 continue;
             }
-            int dE = 0;
-#pragma unroll
-            for (int j = 0; j < 6; ++j) dE += (nb[j] == q) - (nb[j] == qn);
             if (!ELASTIC) {
-                if (dE <= 0 || (unsigned long long)rn.y < __ldg(a.thr + dE)) {
-                    out[i] = qn;
+                if (dE[i] <= 0 || (unsigned long long)rnd[i].y < __ldg(a.thr + dE[i])) {
+                    out[i] = qn[i];
                     ++nacc;
                 }
                 continue;
             }
-            dEs[i] = dE;
             pend |= 1u << i;
             if (RECOMP) {
                 if (!have_g) {
@@ -290,79 +424,46 @@ __global__ void __launch_bounds__(BLOCK_THREADS, (sizeof(T) == 4 ? 4 : 2)) k_swe
 #pragma unroll
         for (int i = 0; i < 4; ++i)
             if (pend & (1u << i)) {
+                if constexpr (!STORED) {
 #pragma unroll
-                for (int k = 0; k < 6; ++k) sl.sig[k][idx] = sg[k][i];
-                sl.qq[idx] = (uint32_t)out[i] | ((uint32_t)qnew[i] << 16);
+                    for (int k = 0; k < 6; ++k) sl.sig[k][idx] = sg[k][i];
+                }
+                sl.qq[idx] = (uint32_t)out[i] | ((uint32_t)qn[i] << 16);
                 sl.r1[idx] = rnd[i].y;
-                sl.own[idx] = (uint32_t)(tid << 2 | i) | ((uint32_t)(dEs[i] + 8) << 16);
+                sl.own[idx] = (uint32_t)(tid << 2 | i) | ((uint32_t)(dE[i] + 8) << 16);
                 ++idx;
             }
-        __syncthreads();
+        bool ok = true;
+        if constexpr (STORED) ok = mbar_wait(&fs.bar, 0u);   // the tile's stress has landed
+        if (__syncthreads_or(!ok)) {
+            // the copy did not complete: report, wait once more (bounded) for it, decide nothing
+            if (tid == 0) {
+                atomicExch(&R.st->wait_timeout, 1);
+                if constexpr (STORED) mbar_wait(&fs.bar, 0u);
+            }
+            return;
+        }
         // the listed trials, evaluated densely by all threads of the CTA
         const unsigned n = sl.count;
-        const T lam_sd_half = (T)R.lam_sd_half;
         for (unsigned e = tid; e < n; e += BLOCK_THREADS) {
             const uint32_t qq = sl.qq[e], ow = sl.own[e];
-            const uint32_t q = qq & 0xffffu, qn = qq >> 16, r1 = sl.r1[e];
-            const int dE = (int)((ow >> 16) & 0xffu) - 8;
             T s[6];
 #pragma unroll
-            for (int k = 0; k < 6; ++k) s[k] = sl.sig[k][e];
-            T dHe = T(0);
-            if (MODE == SWEEP_POINT) {
-                if (RECOMP) {
-                    // the entry holds the strain: the stress with the site's stiffness, as the stress pass forms it
-                    T e6[6];
-#pragma unroll
-                    for (int k = 0; k < 6; ++k) e6[k] = s[k];
-                    Row24<T> rw;
-                    rw.load(a.ctab + 24ll * q);
-                    hooke21<T>(rw.v, e6, s);
-                }
-                dHe = lam_sd_half * (zone_phi<T>(a.wtab + 20ll * q, s) - zone_phi<T>(a.wtab + 20ll * qn, s));
-            } else {
-                // constant strain: e (stored mode: S'(q) s) held fixed, 1/2 (e.C'(q_new)e - e.C'(q)e)
-                T e6[6], sn[6], so[6];
-                if (RECOMP) {
-#pragma unroll
-                    for (int k = 0; k < 6; ++k) e6[k] = s[k];
-                } else {
-                    Row24<T> rw;
-                    rw.load(a.stab + 24ll * q);
-                    hooke21<T>(rw.v, s, e6);
-                }
-                {
-                    Row24<T> rw;
-                    rw.load(a.ctab + 24ll * qn);
-                    hooke21<T>(rw.v, e6, sn);
-                }
-                {
-                    Row24<T> rw;
-                    rw.load(a.ctab + 24ll * q);
-                    hooke21<T>(rw.v, e6, so);
-                }
-                T d = T(0);
-#pragma unroll
-                for (int k = 0; k < 6; ++k) d = rfma(e6[k], sn[k] - so[k], d);
-                dHe = T(0.5) * (T)R.lam * d;
+            for (int k = 0; k < 6; ++k) {
+                if constexpr (STORED)
+                    s[k] = fs.sig[k][ow & 0x3ffu];
+                else
+                    s[k] = sl.sig[k][e];
             }
-            bool acc;
-            if (dHe == T(0)) {
-                acc = dE <= 0 || (unsigned long long)r1 < __ldg(a.thr + dE);
-            } else {
-                const T H = rfma(a.J, (T)dE, dHe);
-                const T u01 = ((T)r1 + T(0.5)) * T(2.3283064365386963e-10);
-                const T t = a.kT > T(0) ? -a.kT * log_t(u01) : T(0);
-                acc = H <= t;
-            }
-            sl.acc[ow & 0xffffu] = acc ? 1 : 0;
+            const T dHe = trial_dhe<T, MODE, RECOMP>(a, R, qq & 0xffffu, qq >> 16, s);
+            sl.acc[ow & 0xffffu] = metropolis<T>(a, (int)((ow >> 16) & 0xffu) - 8, dHe, sl.r1[e]) ? 1 : 0;
         }
         __syncthreads();
         if (pend) {
 #pragma unroll
             for (int i = 0; i < 4; ++i)
                 if ((pend & (1u << i)) && sl.acc[tid << 2 | i]) {
-                    out[i] = qnew[i];
+                    out[i] = qn[i];
                     ++nacc;
                 }
         }
@@ -371,7 +472,7 @@ __global__ void __launch_bounds__(BLOCK_THREADS, (sizeof(T) == 4 ? 4 : 2)) k_swe
         uint2 w;
         w.x = (uint32_t)out[0] | ((uint32_t)out[1] << 16);
         w.y = (uint32_t)out[2] | ((uint32_t)out[3] << 16);
-        reinterpret_cast<uint2 *>(a.spins + R.blk_off)[2 * blk + colour] = w;
+        reinterpret_cast<uint2 *>(a.spins + R.blk_off)[2 * blk + COL] = w;
     }
     if (LIST) {
         const unsigned first = warp_reserve(a.count, nent, lane);
@@ -380,51 +481,76 @@ __global__ void __launch_bounds__(BLOCK_THREADS, (sizeof(T) == 4 ? 4 : 2)) k_swe
             if (j < nent) a.work[first + j] = ent[j];
         return;
     }
-    // a CTA belongs to one replica: warp totals go to that replica's counter
+    // a CTA belongs to one replica: one atomic per CTA on that replica's counter (warps of every
+    // CTA adding to one address directly would serialise at its L2 slice)
+    __shared__ unsigned warp_tot[BLOCK_THREADS / 32];
     const unsigned tot = __reduce_add_sync(FULL, (unsigned)nacc);
-    if (lane == 0 && tot) atomicAdd(&R.st->accepted, (unsigned long long)tot);
+    if (lane == 0) warp_tot[tid >> 5] = tot;
+    __syncthreads();
+    if (tid == 0) {
+        unsigned c = 0;
+#pragma unroll
+        for (int w = 0; w < BLOCK_THREADS / 32; ++w) c += warp_tot[w];
+        if (c) atomicAdd(&R.st->accepted, (unsigned long long)c);
+    }
 }
 
 template <typename T, int MODE, bool RECOMP>
-void launch_one(const SweepArgs<T> &a, int colour, cudaStream_t s) {
+constexpr size_t flat_smem_bytes() {
     constexpr bool ELASTIC = MODE == SWEEP_POINT || MODE == SWEEP_STRAIN;
-    k_sweep<T, MODE, RECOMP><<<a.nctas, BLOCK_THREADS, ELASTIC ? sizeof(SweepList<T>) : 0, s>>>(a, colour);
+    return ELASTIC ? sizeof(FlatSmem<T, !RECOMP>) : 0;
+}
+
+template <typename T, int MODE, bool RECOMP, int COL>
+void launch_flat(const SweepArgs<T> &a, cudaStream_t s) {
+    k_sweep<T, MODE, RECOMP, COL><<<a.nctas, BLOCK_THREADS, flat_smem_bytes<T, MODE, RECOMP>(), s>>>(a);
 }
 
 template <typename T, int MODE, bool RECOMP>
-cudaError_t set_smem() {
-    return cudaFuncSetAttribute(k_sweep<T, MODE, RECOMP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)sizeof(SweepList<T>));
+void launch_form(const SweepArgs<T> &a, int colour, cudaStream_t s) {
+    if (colour)
+        launch_flat<T, MODE, RECOMP, 1>(a, s);
+    else
+        launch_flat<T, MODE, RECOMP, 0>(a, s);
+}
+
+template <typename T, int MODE, bool RECOMP>
+cudaError_t set_flat_smem() {
+    const int bytes = (int)flat_smem_bytes<T, MODE, RECOMP>();
+    cudaError_t e = cudaFuncSetAttribute(k_sweep<T, MODE, RECOMP, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_sweep<T, MODE, RECOMP, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
 }  // namespace
 
 cudaError_t sweep_prepare() {
     cudaError_t e;
-    if ((e = set_smem<float, SWEEP_POINT, false>()) != cudaSuccess) return e;
-    if ((e = set_smem<float, SWEEP_POINT, true>()) != cudaSuccess) return e;
-    if ((e = set_smem<float, SWEEP_STRAIN, false>()) != cudaSuccess) return e;
-    if ((e = set_smem<float, SWEEP_STRAIN, true>()) != cudaSuccess) return e;
-    if ((e = set_smem<double, SWEEP_POINT, false>()) != cudaSuccess) return e;
-    if ((e = set_smem<double, SWEEP_POINT, true>()) != cudaSuccess) return e;
-    if ((e = set_smem<double, SWEEP_STRAIN, false>()) != cudaSuccess) return e;
-    return set_smem<double, SWEEP_STRAIN, true>();
+    if ((e = set_flat_smem<float, SWEEP_POINT, false>()) != cudaSuccess) return e;
+    if ((e = set_flat_smem<float, SWEEP_POINT, true>()) != cudaSuccess) return e;
+    if ((e = set_flat_smem<float, SWEEP_STRAIN, false>()) != cudaSuccess) return e;
+    if ((e = set_flat_smem<float, SWEEP_STRAIN, true>()) != cudaSuccess) return e;
+    if ((e = set_flat_smem<double, SWEEP_POINT, false>()) != cudaSuccess) return e;
+    if ((e = set_flat_smem<double, SWEEP_POINT, true>()) != cudaSuccess) return e;
+    if ((e = set_flat_smem<double, SWEEP_STRAIN, false>()) != cudaSuccess) return e;
+    if ((e = set_flat_smem<double, SWEEP_STRAIN, true>()) != cudaSuccess) return e;
+    return cudaSuccess;
 }
 
 template <typename T>
 cudaError_t launch_sweep(const SweepArgs<T> &a, int colour, int mode, bool recompute, cudaStream_t s) {
     if (mode == SWEEP_POINT && recompute)
-        launch_one<T, SWEEP_POINT, true>(a, colour, s);
+        launch_form<T, SWEEP_POINT, true>(a, colour, s);
     else if (mode == SWEEP_POINT)
-        launch_one<T, SWEEP_POINT, false>(a, colour, s);
+        launch_form<T, SWEEP_POINT, false>(a, colour, s);
     else if (mode == SWEEP_STRAIN && recompute)
-        launch_one<T, SWEEP_STRAIN, true>(a, colour, s);
+        launch_form<T, SWEEP_STRAIN, true>(a, colour, s);
     else if (mode == SWEEP_STRAIN)
-        launch_one<T, SWEEP_STRAIN, false>(a, colour, s);
+        launch_form<T, SWEEP_STRAIN, false>(a, colour, s);
     else if (mode == SWEEP_ZONE_LIST)
-        launch_one<T, SWEEP_ZONE_LIST, false>(a, colour, s);
+        launch_form<T, SWEEP_ZONE_LIST, false>(a, colour, s);
     else
-        launch_one<T, SWEEP_POTTS, false>(a, colour, s);
+        launch_form<T, SWEEP_POTTS, false>(a, colour, s);
     return cudaGetLastError();
 }
 

@@ -64,3 +64,21 @@ def test_injected_nan_is_detected_and_cleared(G):
     g.set_nodal(np.zeros((64, 3)), np.zeros((64, 3)))
     mean, W = g.compute_stress()
     assert np.isfinite(W) and np.isfinite(mean).all()
+
+
+@pytest.mark.gpu
+def test_injected_copy_wait_runs_out_and_is_reported(G):
+    """HMC_FAULT=sweep_wait: the stored-stress sweep never starts its stress copy,
+    so the CTA's bounded wait (1 s) runs out; the CTA changes nothing, the call
+    reports HMC_ERR_TIMEOUT once, and the handle sweeps normally afterwards."""
+    from hmc_synth import voronoi_spins, euler_uniform_so3
+    g = G.HMC((8, 8, 8), 4, mpm_steps_per_mcs=2, elastic_scale=3e3)
+    sp = voronoi_spins((8, 8, 8), 6, 4, 1)
+    g.set_orientations(euler_uniform_so3(4, 1), sp)
+    g.compute_stress()
+    with _with_fault("sweep_wait"):
+        with pytest.raises(G.HMCError) as e:
+            g.sweep_half(0)
+    assert e.value.status == G.HMC_ERR_TIMEOUT
+    assert (g.spins() == sp).all()
+    assert g.sweep_half(0) > 0

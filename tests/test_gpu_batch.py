@@ -122,3 +122,31 @@ def test_paired_hooke_bitwise_equal_to_scalar(G):
         else:
             os.environ["HMC_MPM_SHAPE"] = old
     assert np.array_equal(out[1], out[0])   # same products and fused adds in the same order
+
+
+@pytest.mark.parametrize("precision,elastic", [(1, 1), (1, 3), (1, 0), (0, 0)])
+def test_large_uneven_batch_equals_solo_runs(G, precision, elastic):
+    """Replicas of uneven size, the largest spanning several waves of sweep CTAs:
+    each replica of the batch equals its own single-replica run bit for bit
+    (spins, accepted count, nodal state), for the stored-stress elastic forms and
+    pure Potts."""
+    shapes = [(128, 128, 96), (34, 18, 8), (64, 50, 46)]
+    eul = S.euler_uniform_so3(64, 3)
+    fields = [S.voronoi_spins(sh, 40, 64, 50 + i) for i, sh in enumerate(shapes)]
+    per = [dict(seed=11 + r, load_axis=(0.2 * r, 0.3, 1.0), strain=1e-3 * (r + 1), replica=r) for r in range(3)]
+    common = dict(precision=precision, mpm_steps_per_mcs=4, elastic=elastic, elastic_scale=3e3, **C3)
+    b = G.HMCBatch(shapes, 64, per, **common)
+    b.set_orientations(eul, fields)
+    acc_b = b.mc_sweeps(3)
+    acc_s = 0
+    for r, sh in enumerate(shapes):
+        kw = dict(common)
+        kw.update(per[r])
+        g = G.HMC(sh, 64, **kw)
+        g.set_orientations(eul, fields[r])
+        acc_s += g.mc_sweeps(3)
+        assert np.array_equal(b.spins(r), g.spins()), r
+        assert np.array_equal(b.nodal(r)[0], g.nodal()[0]), r
+        g.close()
+    b.close()
+    assert acc_b == acc_s and acc_b > 0
