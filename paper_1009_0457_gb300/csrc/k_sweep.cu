@@ -35,6 +35,12 @@ namespace hmc {
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
+// threads (= blocks) of a sweep CTA: a tile of BLOCK_THREADS blocks may be split over SPLIT
+// CTAs (measured on the 256^3 workload: 256 threads 0.073 ms, 128 0.078 ms, 64 0.088 ms
+// per half sweep; the per-CTA costs outweigh the shorter barriers)
+constexpr int SWEEP_CTA = 256;
+constexpr int SPLIT = BLOCK_THREADS / SWEEP_CTA;
+static_assert(BLOCK_THREADS % SWEEP_CTA == 0, "tiles split evenly");
 
 // Phi(q; sigma) = sum over the three crystal axes of (a_m . sigma . a_m)^2, from
 // the Voigt weight vectors of the axes.  For one cubic material the zone energy
@@ -93,11 +99,11 @@ __device__ __forceinline__ double log_t(double x) { return log(x); }
 // the bond-count change, and (flat kernel) the site's stress or strain.
 template <typename T, bool SIG>
 struct SweepList {
-    T sig[SIG ? 6 : 1][SIG ? 4 * BLOCK_THREADS : 1];
-    uint32_t qq[4 * BLOCK_THREADS];    // q | q_new << 16
-    uint32_t r1[4 * BLOCK_THREADS];
-    uint32_t own[4 * BLOCK_THREADS];   // thread << 2 | slot, bond change + 8 in bits 16..23
-    uint8_t acc[4 * BLOCK_THREADS];    // decision by (thread, slot)
+    T sig[SIG ? 6 : 1][SIG ? 4 * SWEEP_CTA : 1];
+    uint32_t qq[4 * SWEEP_CTA];    // q | q_new << 16
+    uint32_t r1[4 * SWEEP_CTA];
+    uint32_t own[4 * SWEEP_CTA];   // thread << 2 | slot, bond change + 8 in bits 16..23
+    uint8_t acc[4 * SWEEP_CTA];    // decision by (thread, slot)
     unsigned count;
 };
 
@@ -287,28 +293,30 @@ struct FlatSmem<T, false> {
 };
 template <typename T>
 struct FlatSmem<T, true> {
-    T sig[6][4 * BLOCK_THREADS];
+    T sig[6][4 * SWEEP_CTA];
     SweepList<T, false> list;
     unsigned long long bar;
 };
 
 template <typename T, int MODE, bool RECOMP>
 constexpr int flat_min_ctas() {
-    return sizeof(T) == 8 ? 2 : RECOMP ? 3 : MODE == SWEEP_ZONE_LIST ? 4 : 5;
+    return SPLIT * (sizeof(T) == 8 ? 2 : RECOMP ? 3 : MODE == SWEEP_ZONE_LIST ? 4 : 5);
 }
 
 template <typename T, int MODE, bool RECOMP, int COL>
-__global__ void __launch_bounds__(BLOCK_THREADS, flat_min_ctas<T, MODE, RECOMP>()) k_sweep(SweepArgs<T> a) {
+__global__ void __launch_bounds__(SWEEP_CTA, flat_min_ctas<T, MODE, RECOMP>()) k_sweep(SweepArgs<T> a) {
     constexpr bool ELASTIC = MODE == SWEEP_POINT || MODE == SWEEP_STRAIN;   // a point-zone elastic term
     constexpr bool STORED = ELASTIC && !RECOMP;                               // ... from the stored stress
     constexpr bool LIST = MODE == SWEEP_ZONE_LIST;
     extern __shared__ __align__(128) unsigned char sweep_smem[];
     FlatSmem<T, STORED> &fs = *reinterpret_cast<FlatSmem<T, STORED> *>(sweep_smem);
     auto &sl = fs.list;
-    const int r = __ldg(a.cta_rep + blockIdx.x);
+    const int tile = blockIdx.x / SPLIT;
+    const int r = __ldg(a.cta_rep + tile);
     const Replica &R = a.reps[r];
     const int tid = threadIdx.x, lane = tid & 31;
-    const int t0 = (blockIdx.x - R.cta_off) * BLOCK_THREADS;
+    const int t0 = (tile - R.cta_off) * BLOCK_THREADS + (blockIdx.x % SPLIT) * SWEEP_CTA;
+    if (t0 >= R.nblk) return;  // the empty part of a replica's last tile
     const int blk = t0 + tid;  // block within the replica
     if (ELASTIC) {
         if (tid == 0) {
@@ -316,7 +324,7 @@ __global__ void __launch_bounds__(BLOCK_THREADS, flat_min_ctas<T, MODE, RECOMP>(
             if constexpr (STORED) {
                 // the colour's stress of the tile: six components, four values per block, each
                 // source a multiple of 16 B in address and size
-                const unsigned nb = (unsigned)min(BLOCK_THREADS, R.nblk - t0);
+                const unsigned nb = (unsigned)min(SWEEP_CTA, R.nblk - t0);
                 mbar_init(&fs.bar, 1);
                 mbar_init_fence();
                 if (!a.skip_copy) {
@@ -445,7 +453,7 @@ __global__ void __launch_bounds__(BLOCK_THREADS, flat_min_ctas<T, MODE, RECOMP>(
         }
         // the listed trials, evaluated densely by all threads of the CTA
         const unsigned n = sl.count;
-        for (unsigned e = tid; e < n; e += BLOCK_THREADS) {
+        for (unsigned e = tid; e < n; e += SWEEP_CTA) {
             const uint32_t qq = sl.qq[e], ow = sl.own[e];
             T s[6];
 #pragma unroll
@@ -483,14 +491,14 @@ __global__ void __launch_bounds__(BLOCK_THREADS, flat_min_ctas<T, MODE, RECOMP>(
     }
     // a CTA belongs to one replica: one atomic per CTA on that replica's counter (warps of every
     // CTA adding to one address directly would serialise at its L2 slice)
-    __shared__ unsigned warp_tot[BLOCK_THREADS / 32];
+    __shared__ unsigned warp_tot[SWEEP_CTA / 32];
     const unsigned tot = __reduce_add_sync(FULL, (unsigned)nacc);
     if (lane == 0) warp_tot[tid >> 5] = tot;
     __syncthreads();
     if (tid == 0) {
         unsigned c = 0;
 #pragma unroll
-        for (int w = 0; w < BLOCK_THREADS / 32; ++w) c += warp_tot[w];
+        for (int w = 0; w < SWEEP_CTA / 32; ++w) c += warp_tot[w];
         if (c) atomicAdd(&R.st->accepted, (unsigned long long)c);
     }
 }
@@ -503,7 +511,7 @@ constexpr size_t flat_smem_bytes() {
 
 template <typename T, int MODE, bool RECOMP, int COL>
 void launch_flat(const SweepArgs<T> &a, cudaStream_t s) {
-    k_sweep<T, MODE, RECOMP, COL><<<a.nctas, BLOCK_THREADS, flat_smem_bytes<T, MODE, RECOMP>(), s>>>(a);
+    k_sweep<T, MODE, RECOMP, COL><<<a.nctas * SPLIT, SWEEP_CTA, flat_smem_bytes<T, MODE, RECOMP>(), s>>>(a);
 }
 
 template <typename T, int MODE, bool RECOMP>
