@@ -54,7 +54,7 @@ def lib():
         L.orc_stress_field.argtypes = [i, i, i, u16p, dp, dp, dp, dp, dp, dp]
         L.orc_point_zone_shift.argtypes = [dp, dp, dp]
         L.orc_point_zone_shift.restype = C.c_double
-        L.orc_site_draws.argtypes = [i, i, i, i, i, C.c_uint64, C.c_uint32, C.c_uint32, u32p]
+        L.orc_site_draws.argtypes = [i, i, i, i, i, C.c_uint64, C.c_uint32, C.c_uint32, i, u32p]
         L.orc_point_strain_shift.argtypes = [dp, dp, dp, dp]
         L.orc_point_strain_shift.restype = C.c_double
         L.orc_accept_threshold.argtypes = [i, C.c_double, C.c_double]
@@ -327,12 +327,15 @@ TRIAL_NEIGHBOR, TRIAL_UNIFORM_Q = 0, 1
 ELASTIC_OFF, ELASTIC_TRACTION, ELASTIC_ZONE1, ELASTIC_STRAIN = 0, 1, 2, 3
 
 
-def site_draws(nx, ny, x, y, z, seed, mcs, replica):
-    """(r0, r1) of the trial at (x, y, z): the Philox block of the even-x site of the pair
-    {(x, y, z), (x^1, y^1, z)}; words 0, 1 for the even-x site, 2, 3 for its partner."""
+def site_draws(nx, ny, x, y, z, seed, mcs, replica, trial=0):
+    """(r0, r1) of the trial at (x, y, z): r0 picks the trial state, r1 decides.  The
+    colour's four sites of a 2x2x2 block share the Philox block with counter (block
+    origin index, mcs, replica, 2 + colour); the site with the j-th smallest local corner
+    index takes word j.  Neighbour trials (trial 0): r1 = low 32 bits of 6 r0; trials over
+    all orientations: r1 = word j of the block with counter word 3 = 4 + colour."""
     out = np.zeros(2, dtype=np.uint32)
     lib().orc_site_draws(int(nx), int(ny), int(x), int(y), int(z), int(seed), int(mcs), int(replica),
-                         _p(out, C.c_uint32))
+                         int(trial), _p(out, C.c_uint32))
     return int(out[0]), int(out[1])
 
 

@@ -425,22 +425,36 @@ enum { ORC_TRIAL_NEIGHBOR = 0, ORC_TRIAL_UNIFORM_Q = 1 };
  * total change in MC energy units, *thresh the Metropolis threshold
  * -kT ln u (or -1 when the integer table decided).  sig_p is the site's
  * stress (6 values; unused when the elastic term is off). */
-/* The two draws of the trial at site (x, y, z) of Monte Carlo step mcs.  Sites
- * (x, y, z) with x even and (x + 1, y ^ 1, z) -- same colour, same 2x2x2 block --
- * share one Philox4x32-10 block: counter (index of the even-x site, mcs,
- * replica, 0), key (seed lo, seed hi); words 0, 1 go to the even-x site and
- * words 2, 3 to its partner.  out[0] picks the trial state, out[1] decides. */
+/* The two draws of the trial at site (x, y, z) of Monte Carlo step mcs: out[0]
+ * picks the trial state, out[1] decides.  The four sites of one colour in the
+ * same 2x2x2 block (origin x, y, z all even) share one Philox4x32-10 block:
+ * counter (index of the block origin, mcs, replica, 2 + colour), key (seed lo,
+ * seed hi); the site whose local corner index lx + 2 ly + 4 lz is the j-th
+ * smallest among its colour's four takes word j.  Neighbour trials: out[0] is that
+ * word w and out[1] the low 32 bits of 6 w (the neighbour index is the high
+ * bits).  Trials over all orientations: out[1] is word j of a second block with
+ * counter word 3 = 4 + colour. */
 void orc_site_draws(int nx, int ny, int x, int y, int z, uint64_t seed, uint32_t mcs, uint32_t replica,
-                    uint32_t out[2])
+                    int trial_mode, uint32_t out[2])
 {
-    const int odd = x & 1;
-    const int xl = x - odd, yl = odd ? (y ^ 1) : y;
-    uint32_t ctr[4] = {(uint32_t)((int64_t)xl + (int64_t)nx * ((int64_t)yl + (int64_t)ny * z)), mcs, replica, 0u};
+    const int colour = (x + y + z) & 1;
+    const int L = (x & 1) + 2 * (y & 1) + 4 * (z & 1);
+    int j = 0;   /* corners of the same colour with a smaller local index */
+    for (int m = 0; m < L; ++m)
+        if ((((m & 1) + ((m >> 1) & 1) + (m >> 2)) & 1) == colour) ++j;
+    const int64_t origin = (int64_t)(x & ~1) + (int64_t)nx * ((int64_t)(y & ~1) + (int64_t)ny * (z & ~1));
+    uint32_t ctr[4] = {(uint32_t)origin, mcs, replica, 2u + (uint32_t)colour};
     uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
     uint32_t r[4];
     orc_philox4x32_10(ctr, key, r);
-    out[0] = r[2 * odd];
-    out[1] = r[2 * odd + 1];
+    out[0] = r[j];
+    if (trial_mode == ORC_TRIAL_NEIGHBOR) {
+        out[1] = (uint32_t)((uint64_t)r[j] * 6u);   /* mod 2^32 */
+    } else {
+        ctr[3] = 4u + (uint32_t)colour;
+        orc_philox4x32_10(ctr, key, r);
+        out[1] = r[j];
+    }
 }
 
 int orc_site_trial_at(int nx, int ny, int nz, const uint16_t *spin, int x, int y, int z,
@@ -450,7 +464,7 @@ int orc_site_trial_at(int nx, int ny, int nz, const uint16_t *spin, int x, int y
 {
     int64_t p = (int64_t)x + (int64_t)nx * ((int64_t)y + (int64_t)ny * z);
     uint32_t r[2];
-    orc_site_draws(nx, ny, x, y, z, seed, mcs, replica, r);
+    orc_site_draws(nx, ny, x, y, z, seed, mcs, replica, trial_mode, r);
 
     /* neighbours in the order -x, +x, -y, +y, -z, +z (periodic lattice) */
     uint16_t nb[6];

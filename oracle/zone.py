@@ -148,14 +148,14 @@ def zone_shift(spins, Ct, Ebar, u0, p, q_new, r, Bs=None):
 
 def site_trial_zone(spins, x, y, z, seed, mcs, replica, J, kT, trial, Q, lam, Ct, Ebar, u0, r, Bs):
     """One Metropolis trial (Eq. 5) at voxel (x, y, z): the trial orientation
-    and the bond-energy change as in the one-point sweep (the site's two Philox
+    and the bond-energy change as in the one-point sweep (the site's Philox
     draws, neighbour order -x,+x,-y,+y,-z,+z), the elastic
     term lam * zone_shift over the zone of half-width r about the current
     displacement u0.  Returns (accepted, q_new, dH, threshold)."""
     from . import TRIAL_NEIGHBOR, accept_threshold, site_draws
     nz, ny, nx = spins.shape
     p = x + nx * (y + ny * z)
-    w = site_draws(nx, ny, x, y, z, seed, mcs, replica)
+    w = site_draws(nx, ny, x, y, z, seed, mcs, replica, trial)
     nb = [int(spins[z, y, (x - 1) % nx]), int(spins[z, y, (x + 1) % nx]),
           int(spins[z, (y - 1) % ny, x]), int(spins[z, (y + 1) % ny, x]),
           int(spins[(z - 1) % nz, y, x]), int(spins[(z + 1) % nz, y, x])]

@@ -87,6 +87,7 @@ struct hmc_handle {
     int bins_cap = 0;
     DevState *st = nullptr;               // R device states
     hmc::Replica *d_reps = nullptr;       // R descriptors
+    hmc::Replica rep0{};                  // host copy of descriptor 0 (kernel argument of one-replica sweeps)
     int *d_cta_rep = nullptr;             // replica of every sweep / stress CTA
     hmc::MpmSched *d_sched = nullptr;     // R + 1 MPM schedules for the chosen shape
     // MPM launch configuration (autotuned)
@@ -293,6 +294,8 @@ cudaError_t enqueue_sweep(hmc_handle *h, int colour, cudaStream_t s) {
     a.stab = static_cast<const T *>(h->stab);
     a.u = static_cast<const T *>(h->u[h->cur]);
     a.skip_copy = fault("sweep_wait") ? 1 : 0;
+    a.nrep = h->R;
+    a.rep0 = h->rep0;
     const bool point = h->p.elastic == HMC_ELASTIC_TRACTION || h->p.elastic == HMC_ELASTIC_STRAIN;
     if (h->p.elastic != HMC_ELASTIC_ZONE1) {
         const int mode = h->p.elastic == HMC_ELASTIC_TRACTION ? hmc::SWEEP_POINT
@@ -860,11 +863,14 @@ hmc_status hmc_create_batch(const hmc_params *params, int32_t n_replicas, hmc_ha
         rd[r].replica = R.p.replica;
         rd[r].lam_sd_half = R.lam_sd_half;
         rd[r].lam = R.lam;
+        rd[r].lam_sd_half_f = (float)R.lam_sd_half;
+        rd[r].lam_f = (float)R.lam;
         rd[r].st = h->st + r;
         rd[r].divx = hmc::make_udiv((uint32_t)R.nbx);
         rd[r].divy = hmc::make_udiv((uint32_t)R.nby);
         for (int c = 0; c < R.ncta; ++c) ctarep[R.cta_off + c] = r;
     }
+    h->rep0 = rd[0];
     if ((e = cudaMemcpy(h->st, st.data(), sizeof(DevState) * st.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(h->d_reps, rd.data(), sizeof(hmc::Replica) * rd.size(), cudaMemcpyHostToDevice)) !=
             cudaSuccess ||

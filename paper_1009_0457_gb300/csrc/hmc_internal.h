@@ -77,6 +77,7 @@ struct alignas(16) Replica {   // 16 B aligned: the pipelined sweep stages it wi
     DevState *st;
     UDiv divx, divy;          // division by nbx and by nby
     uint32_t pad3;
+    float lam_sd_half_f, lam_f;   // FP32 copies of the two scales
 };
 static_assert(sizeof(Replica) % 16 == 0, "Replica must be a whole number of 16 B units");
 
@@ -135,6 +136,8 @@ struct SweepArgs {
                                      // is formed from it as the stress pass would)
     int skip_copy;                   // fault injection: the stored-stress copy is never started, so its
                                      // bounded wait runs out (HMC_FAULT=sweep_wait)
+    int nrep;                        // replicas; with one, the kernels read rep0 below
+    Replica rep0;                    // replica 0's descriptor, passed by value
 };
 
 // Elastic term of a sweep: none, one-point zone from the stored stress (constant

@@ -10,7 +10,7 @@
 // quad of the six face neighbours and (stored-stress elastic forms) the colour's
 // 96 B of stress (FP32), and writes the colour's 8 B quad when a site changed.
 // Same-colour sites share no neighbour, so the in-place update is race free.
-// Two sites of a colour share one Philox4x32-10 block (four words, two per site).
+// The colour's four sites of a block share one Philox4x32-10 block (a word each).
 //
 // Five CTAs per SM (FP32).  With the stored
 // stress, thread 0 starts a bulk asynchronous copy of the tile's stress of the
@@ -41,6 +41,7 @@ constexpr unsigned FULL = 0xffffffffu;
 constexpr int SWEEP_CTA = 256;
 constexpr int SPLIT = BLOCK_THREADS / SWEEP_CTA;
 static_assert(BLOCK_THREADS % SWEEP_CTA == 0, "tiles split evenly");
+static_assert(4 * SWEEP_CTA <= 1024, "a trial's thread and slot fit ten bits");
 
 // Phi(q; sigma) = sum over the three crystal axes of (a_m . sigma . a_m)^2, from
 // the Voigt weight vectors of the axes.  For one cubic material the zone energy
@@ -102,7 +103,7 @@ struct SweepList {
     T sig[SIG ? 6 : 1][SIG ? 4 * SWEEP_CTA : 1];
     uint32_t qq[4 * SWEEP_CTA];    // q | q_new << 16
     uint32_t r1[4 * SWEEP_CTA];
-    uint32_t own[4 * SWEEP_CTA];   // thread << 2 | slot, bond change + 8 in bits 16..23
+    uint16_t own[4 * SWEEP_CTA];   // thread << 2 | slot, bond change + 8 in bits 10..13
     uint8_t acc[4 * SWEEP_CTA];    // decision by (thread, slot)
     unsigned count;
 };
@@ -121,26 +122,30 @@ __device__ __forceinline__ unsigned warp_reserve(unsigned *counter, int n, int l
     return __shfl_sync(FULL, base, 31) + (unsigned)(incl - n);
 }
 
-// The Philox words of the colour's four sites of block (bx, by, bz).  The colour's
-// sites pair up as (even-x site, its partner at x+1, y^1): red slots (0, 1) and
-// (3, 2), black (1, 0) and (2, 3), leader first; one Philox4x32-10 block per pair,
-// counter (leader's site index, Monte Carlo step, replica, 0); the leader takes
-// words 0 and 1, the partner words 2 and 3.
+// The draws of the colour's four sites of block (bx, by, bz), rnd[i] = (trial word,
+// acceptance word) of slot i (slots in increasing local corner index).  One
+// Philox4x32-10 block per block and colour: counter (index of the block's origin
+// site, Monte Carlo step, replica, 2 + colour), key (seed lo, seed hi); word i
+// belongs to slot i.  Neighbour trials take the acceptance word from the same
+// word w, as the low half of 6 w (the high half picks the neighbour); trials over
+// all orientations take it from a second block, counter word 3 = 4 + colour.
 template <int COL>
-__device__ __forceinline__ void block_draws(const Replica &R, int bx, int by, int bz, uint32_t mcs,
+__device__ __forceinline__ void block_draws(const Replica &R, int trial, int bx, int by, int bz, uint32_t mcs,
                                             uint2 (&rnd)[4]) {
-    constexpr int la = COL ? 1 : 0, lb = COL ? 2 : 3;
-    constexpr int LA = slot_local(4 * COL + la), LB = slot_local(4 * COL + lb);
-    const uint32_t x0 = 2u * (uint32_t)bx, y0 = 2u * (uint32_t)by, z0 = 2u * (uint32_t)bz;
-    const uint32_t nx = (uint32_t)R.nx, ny = (uint32_t)R.ny;
-    const uint32_t sa = x0 + (LA & 1) + nx * (y0 + ((LA >> 1) & 1) + ny * (z0 + (LA >> 2)));
-    const uint32_t sb = x0 + (LB & 1) + nx * (y0 + ((LB >> 1) & 1) + ny * (z0 + (LB >> 2)));
-    const uint4 wa = philox4(sa, mcs, R.replica, 0u, R.key0, R.key1);
-    const uint4 wb = philox4(sb, mcs, R.replica, 0u, R.key0, R.key1);
-    rnd[la] = make_uint2(wa.x, wa.y);
-    rnd[la ^ 1] = make_uint2(wa.z, wa.w);
-    rnd[lb] = make_uint2(wb.x, wb.y);
-    rnd[lb ^ 1] = make_uint2(wb.z, wb.w);
+    const uint32_t s0 = 2u * ((uint32_t)bx + (uint32_t)R.nx * ((uint32_t)by + (uint32_t)R.ny * (uint32_t)bz));
+    const uint4 w = philox4(s0, mcs, R.replica, 2u + COL, R.key0, R.key1);
+    if (trial == 0) {
+        rnd[0] = make_uint2(w.x, 6u * w.x);
+        rnd[1] = make_uint2(w.y, 6u * w.y);
+        rnd[2] = make_uint2(w.z, 6u * w.z);
+        rnd[3] = make_uint2(w.w, 6u * w.w);
+    } else {
+        const uint4 v = philox4(s0, mcs, R.replica, 4u + COL, R.key0, R.key1);
+        rnd[0] = make_uint2(w.x, v.x);
+        rnd[1] = make_uint2(w.y, v.y);
+        rnd[2] = make_uint2(w.z, v.z);
+        rnd[3] = make_uint2(w.w, v.w);
+    }
 }
 
 // The colour's four trials of a block: current and proposed orientation and the
@@ -182,6 +187,14 @@ __device__ __forceinline__ void block_trials(int trial, int nq, const uint2 &min
     }
 }
 
+// a replica's scale in the kernel's precision (FP32 kernels read the FP32 copy)
+template <typename T>
+__device__ __forceinline__ T rep_scale(double d, float f);
+template <>
+__device__ __forceinline__ float rep_scale<float>(double, float f) { return f; }
+template <>
+__device__ __forceinline__ double rep_scale<double>(double d, float) { return d; }
+
 // Elastic energy change of a listed trial from the site's stress s (stored forms)
 // or, for the recomputing point form, from its strain (then s is overwritten with
 // the stress the stress pass would form).
@@ -196,7 +209,7 @@ __device__ __forceinline__ T trial_dhe(const SweepArgs<T> &a, const Replica &R, 
             rw.load(a.ctab + 24ll * q);
             hooke21<T>(rw.v, e6, s);
         }
-        return (T)R.lam_sd_half * (zone_phi<T>(a.wtab + 20ll * q, s) - zone_phi<T>(a.wtab + 20ll * qn, s));
+        return rep_scale<T>(R.lam_sd_half, R.lam_sd_half_f) * (zone_phi<T>(a.wtab + 20ll * q, s) - zone_phi<T>(a.wtab + 20ll * qn, s));
     }
     // constant strain: e (stored forms: S'(q) s) held fixed, 1/2 (e.C'(q_new)e - e.C'(q)e)
     T e6[6], sn[6], so[6];
@@ -221,7 +234,7 @@ __device__ __forceinline__ T trial_dhe(const SweepArgs<T> &a, const Replica &R, 
     T d = T(0);
 #pragma unroll
     for (int k = 0; k < 6; ++k) d = rfma(e6[k], sn[k] - so[k], d);
-    return T(0.5) * (T)R.lam * d;
+    return T(0.5) * rep_scale<T>(R.lam, R.lam_f) * d;
 }
 
 // Metropolis decision (Eq. 5): the integer threshold table when the elastic term
@@ -298,13 +311,21 @@ struct FlatSmem<T, true> {
     unsigned long long bar;
 };
 
+// resident CTAs per SM the kernels are compiled for (measured on the 256^3 workload: six FP32
+// one-point-zone CTAs fit registers and shared memory but sweep slower than five)
 template <typename T, int MODE, bool RECOMP>
 constexpr int flat_min_ctas() {
-    return SPLIT * (sizeof(T) == 8 ? 2 : RECOMP ? 3 : MODE == SWEEP_ZONE_LIST ? 4 : 5);
+    return SPLIT * (sizeof(T) == 8 ? 2
+                    : RECOMP ? 3
+                    : MODE == SWEEP_ZONE_LIST ? 4
+                    : 5);
 }
 
-template <typename T, int MODE, bool RECOMP, int COL>
-__global__ void __launch_bounds__(SWEEP_CTA, flat_min_ctas<T, MODE, RECOMP>()) k_sweep(SweepArgs<T> a) {
+// ONE: a single replica, whose descriptor is read from the kernel argument (no dependent
+// loads before the tile's copy and spin loads can start)
+template <typename T, int MODE, bool RECOMP, int COL, bool ONE>
+__global__ void __launch_bounds__(SWEEP_CTA, flat_min_ctas<T, MODE, RECOMP>())
+    k_sweep(const __grid_constant__ SweepArgs<T> a) {
     constexpr bool ELASTIC = MODE == SWEEP_POINT || MODE == SWEEP_STRAIN;   // a point-zone elastic term
     constexpr bool STORED = ELASTIC && !RECOMP;                               // ... from the stored stress
     constexpr bool LIST = MODE == SWEEP_ZONE_LIST;
@@ -312,8 +333,8 @@ __global__ void __launch_bounds__(SWEEP_CTA, flat_min_ctas<T, MODE, RECOMP>()) k
     FlatSmem<T, STORED> &fs = *reinterpret_cast<FlatSmem<T, STORED> *>(sweep_smem);
     auto &sl = fs.list;
     const int tile = blockIdx.x / SPLIT;
-    const int r = __ldg(a.cta_rep + tile);
-    const Replica &R = a.reps[r];
+    const int r = ONE ? 0 : __ldg(a.cta_rep + tile);
+    const Replica &R = ONE ? a.rep0 : a.reps[r];
     const int tid = threadIdx.x, lane = tid & 31;
     const int t0 = (tile - R.cta_off) * BLOCK_THREADS + (blockIdx.x % SPLIT) * SWEEP_CTA;
     if (t0 >= R.nblk) return;  // the empty part of a replica's last tile
@@ -365,7 +386,7 @@ __global__ void __launch_bounds__(SWEEP_CTA, flat_min_ctas<T, MODE, RECOMP>()) k
         N[3] = __ldg(q2 + 2 * (blk + (by == nby - 1 ? -(nby - 1) * sxy : sxy)) + oc);
         N[4] = __ldg(q2 + 2 * (blk + (bz == 0 ? (nbz - 1) * sxz : -sxz)) + oc);
         N[5] = __ldg(q2 + 2 * (blk + (bz == nbz - 1 ? -(nbz - 1) * sxz : sxz)) + oc);
-        block_draws<COL>(R, bx, by, bz, R.st->mcs, rnd);
+        block_draws<COL>(R, a.trial, bx, by, bz, R.st->mcs, rnd);
         uint16_t q[4];
         block_trials<COL>(a.trial, a.nq, mine, O, N, rnd, q, qn, dE);
         // recompute mode: the cell's displacement gradients, formed at the first listed trial
@@ -438,7 +459,7 @@ __global__ void __launch_bounds__(SWEEP_CTA, flat_min_ctas<T, MODE, RECOMP>()) k
                 }
                 sl.qq[idx] = (uint32_t)out[i] | ((uint32_t)qn[i] << 16);
                 sl.r1[idx] = rnd[i].y;
-                sl.own[idx] = (uint32_t)(tid << 2 | i) | ((uint32_t)(dE[i] + 8) << 16);
+                sl.own[idx] = (uint16_t)((tid << 2 | i) | ((dE[i] + 8) << 10));
                 ++idx;
             }
         bool ok = true;
@@ -464,7 +485,7 @@ __global__ void __launch_bounds__(SWEEP_CTA, flat_min_ctas<T, MODE, RECOMP>()) k
                     s[k] = sl.sig[k][e];
             }
             const T dHe = trial_dhe<T, MODE, RECOMP>(a, R, qq & 0xffffu, qq >> 16, s);
-            sl.acc[ow & 0xffffu] = metropolis<T>(a, (int)((ow >> 16) & 0xffu) - 8, dHe, sl.r1[e]) ? 1 : 0;
+            sl.acc[ow & 0x3ffu] = metropolis<T>(a, (int)(ow >> 10) - 8, dHe, sl.r1[e]) ? 1 : 0;
         }
         __syncthreads();
         if (pend) {
@@ -511,7 +532,10 @@ constexpr size_t flat_smem_bytes() {
 
 template <typename T, int MODE, bool RECOMP, int COL>
 void launch_flat(const SweepArgs<T> &a, cudaStream_t s) {
-    k_sweep<T, MODE, RECOMP, COL><<<a.nctas * SPLIT, SWEEP_CTA, flat_smem_bytes<T, MODE, RECOMP>(), s>>>(a);
+    if (a.nrep == 1)
+        k_sweep<T, MODE, RECOMP, COL, true><<<a.nctas * SPLIT, SWEEP_CTA, flat_smem_bytes<T, MODE, RECOMP>(), s>>>(a);
+    else
+        k_sweep<T, MODE, RECOMP, COL, false><<<a.nctas * SPLIT, SWEEP_CTA, flat_smem_bytes<T, MODE, RECOMP>(), s>>>(a);
 }
 
 template <typename T, int MODE, bool RECOMP>
@@ -525,9 +549,12 @@ void launch_form(const SweepArgs<T> &a, int colour, cudaStream_t s) {
 template <typename T, int MODE, bool RECOMP>
 cudaError_t set_flat_smem() {
     const int bytes = (int)flat_smem_bytes<T, MODE, RECOMP>();
-    cudaError_t e = cudaFuncSetAttribute(k_sweep<T, MODE, RECOMP, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_sweep<T, MODE, RECOMP, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_sweep<T, MODE, RECOMP, 0, false>, at, bytes)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_sweep<T, MODE, RECOMP, 1, false>, at, bytes)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_sweep<T, MODE, RECOMP, 0, true>, at, bytes)) != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_sweep<T, MODE, RECOMP, 1, true>, at, bytes);
 }
 
 }  // namespace

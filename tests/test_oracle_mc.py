@@ -144,7 +144,7 @@ def test_elastic_threshold_rule():
         if qn == s[z, y, x]:
             continue
         p = x + 8 * (y + 8 * z)
-        r = O.site_draws(8, 8, x, y, z, 9, m, 0)
+        r = O.site_draws(8, 8, x, y, z, 9, m, 0, O.TRIAL_NEIGHBOR)
         u = (float(r[1]) + 0.5) / 2 ** 32
         assert abs(t + 0.7 * math.log(u)) < 1e-15
         assert acc == (dH <= t)

@@ -212,13 +212,41 @@ def test_polycrystal_modulus_within_uniform_bounds():
     assert abs(Ev - E_V) < 0.01 * E_V and abs(Er - E_R) < 0.01 * E_R
 
 
-def test_paired_site_draws():
-    """Sites (x, y, z), x even, and (x+1, y^1, z) share one Philox4x32-10 block:
-    words 0, 1 and 2, 3 of the block keyed by the even-x site's index."""
+def test_block_site_draws():
+    """The four same-colour sites of a 2x2x2 block share one Philox4x32-10 block keyed
+    by the block origin's index: the j-th site in increasing local corner index takes
+    word j.  Neighbour trials derive the acceptance word as the low half of 6 w;
+    trials over all orientations take it from the block with counter word 3 = 4 + colour."""
     nx, ny = 10, 6
-    for (x, y, z) in [(0, 0, 0), (4, 3, 2), (8, 5, 1)]:
-        p = x + nx * (y + ny * z)
-        w = O.philox4x32_10([p, 7, 2, 0], [0x12345678, 0x9ABCDEF0])
-        assert O.site_draws(nx, ny, x, y, z, 0x9ABCDEF012345678, 7, 2) == (int(w[0]), int(w[1]))
-        assert O.site_draws(nx, ny, x + 1, y ^ 1, z, 0x9ABCDEF012345678, 7, 2) == (int(w[2]), int(w[3]))
-        assert (x + y + z) % 2 == (x + 1 + (y ^ 1) + z) % 2   # same colour
+    seed = 0x9ABCDEF012345678
+    key = [seed & 0xffffffff, seed >> 32]
+    red, black = [0, 3, 5, 6], [1, 2, 4, 7]
+    for (bx, by, bz) in [(0, 0, 0), (2, 1, 1), (4, 2, 3)]:
+        origin = 2 * bx + nx * (2 * by + ny * 2 * bz)
+        for colour, corners in ((0, red), (1, black)):
+            w = O.philox4x32_10([origin, 7, 2, 2 + colour], key)
+            v = O.philox4x32_10([origin, 7, 2, 4 + colour], key)
+            for j, L in enumerate(corners):
+                x, y, z = 2 * bx + (L & 1), 2 * by + ((L >> 1) & 1), 2 * bz + (L >> 2)
+                assert (x + y + z) % 2 == colour
+                assert O.site_draws(nx, ny, x, y, z, seed, 7, 2, O.TRIAL_NEIGHBOR) == \
+                    (int(w[j]), (6 * int(w[j])) % 2 ** 32)
+                assert O.site_draws(nx, ny, x, y, z, seed, 7, 2, O.TRIAL_UNIFORM_Q) == (int(w[j]), int(v[j]))
+
+
+def test_neighbour_trial_and_acceptance_draws_are_independent():
+    """For neighbour trials the neighbour index k = floor(6 w / 2^32) and the acceptance
+    draw r1 = 6 w mod 2^32 come from one word: k is uniform on 0..5 and, given k, r1 is
+    uniform on [0, 2^32) (chi-square over 6 x 8 cells of 48 000 draws)."""
+    cnt = np.zeros((6, 8))
+    n = 0
+    for m in range(125):
+        for z in range(4):
+            for y in range(8):
+                for x in range(12):
+                    r0, r1 = O.site_draws(12, 8, x, y, z, 77, m, 1, O.TRIAL_NEIGHBOR)
+                    cnt[(r0 * 6) >> 32, r1 >> 29] += 1
+                    n += 1
+    e = n / 48.0
+    chi2 = ((cnt - e) ** 2 / e).sum()
+    assert chi2 < 47 + 5 * math.sqrt(2 * 47)   # 47 degrees of freedom, five standard deviations
