@@ -12,18 +12,18 @@
 // Same-colour sites share no neighbour, so the in-place update is race free.
 // The colour's four sites of a block share one Philox4x32-10 block (a word each).
 //
-// Five CTAs per SM (FP32).  With the stored
-// stress, thread 0 starts a bulk asynchronous copy of the tile's stress of the
-// colour into shared memory (completing on an mbarrier) as the CTA begins; the
-// threads meanwhile load their spins and neighbours and run the Philox and
-// bond arithmetic, and only the listed trials read the staged stress.  The
-// acceptance count is reduced per CTA before its one atomic.
-//
-// With an elastic term, the trials that change the orientation (a minority:
-// interior sites copy their own orientation) are listed in shared memory, and
-// the CTA's threads then evaluate the listed trials densely, so that the zone
-// energies and the logarithm of the Metropolis threshold run with full warps
-// rather than on the few lanes whose site needs them.
+// Five CTAs per SM (FP32).  With the stored stress, thread 0 starts a bulk
+// asynchronous copy of the tile's stress of the colour into shared memory
+// (completing on an mbarrier) as the CTA begins; the threads meanwhile load their
+// spins and neighbours and run the Philox and bond arithmetic.  With an elastic
+// term, the trials that change the orientation (a minority: interior sites copy
+// their own orientation) are listed in shared memory, each warp in its own region
+// (positions from ballots, no shared counter), and only thread 0 waits for the
+// copy: one CTA barrier then publishes the staged stress, after which each warp
+// evaluates its listed trials densely with its 32 lanes (zone energies and the
+// logarithm of the Metropolis threshold on full lanes rather than on the few whose
+// site needs them) and its lanes apply their decisions after a warp barrier.  The
+// last warp to finish adds the CTA's acceptances to the replica's count.
 //
 // With the 27-point zone the sweep only lists its non-trivial trials (site,
 // replica, old and new orientation, the acceptance draw) in global memory with
@@ -103,9 +103,9 @@ struct SweepList {
     T sig[SIG ? 6 : 1][SIG ? 4 * SWEEP_CTA : 1];
     uint32_t qq[4 * SWEEP_CTA];    // q | q_new << 16
     uint32_t r1[4 * SWEEP_CTA];
-    uint16_t own[4 * SWEEP_CTA];   // thread << 2 | slot, bond change + 8 in bits 10..13
+    uint16_t own[4 * SWEEP_CTA];   // lane << 2 | slot, bond change + 8 in bits 8..11
     uint8_t acc[4 * SWEEP_CTA];    // decision by (thread, slot)
-    unsigned count;
+    unsigned nacc, done;           // acceptances of the CTA; warps finished
 };
 
 // warp-aggregated reservation of n entries: returns this lane's first index
@@ -341,7 +341,8 @@ __global__ void __launch_bounds__(SWEEP_CTA, flat_min_ctas<T, MODE, RECOMP>())
     const int blk = t0 + tid;  // block within the replica
     if (ELASTIC) {
         if (tid == 0) {
-            sl.count = 0;
+            sl.nacc = 0;
+            sl.done = 0;
             if constexpr (STORED) {
                 // the colour's stress of the tile: six components, four values per block, each
                 // source a multiple of 16 B in address and size
@@ -357,7 +358,6 @@ __global__ void __launch_bounds__(SWEEP_CTA, flat_min_ctas<T, MODE, RECOMP>())
                 }
             }
         }
-        __syncthreads();
     }
     int nacc = 0;
     uint4 ent[4];   // zone mode: this thread's trials for the list
@@ -447,23 +447,32 @@ __global__ void __launch_bounds__(SWEEP_CTA, flat_min_ctas<T, MODE, RECOMP>())
         }
     }
 
+    unsigned dacc = 0;   // elastic forms: acceptances decided by this thread
     if (ELASTIC) {
-        // list the pending trials (every lane of the warp takes part in the reservation)
-        unsigned idx = warp_reserve(&sl.count, __popc(pend), lane);
+        // each warp lists its pending trials in its own region of the list: slot 0 trials of
+        // lanes 0..31, then slot 1, ...
+        const unsigned below = (1u << lane) - 1u;
+        const int wb = (tid >> 5) * 128;
+        unsigned n = 0;
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
-            if (pend & (1u << i)) {
+        for (int i = 0; i < 4; ++i) {
+            const bool pi = (pend >> i) & 1u;
+            const unsigned m = __ballot_sync(FULL, pi);
+            if (pi) {
+                const unsigned idx = wb + n + __popc(m & below);
                 if constexpr (!STORED) {
 #pragma unroll
                     for (int k = 0; k < 6; ++k) sl.sig[k][idx] = sg[k][i];
                 }
                 sl.qq[idx] = (uint32_t)out[i] | ((uint32_t)qn[i] << 16);
                 sl.r1[idx] = rnd[i].y;
-                sl.own[idx] = (uint16_t)((tid << 2 | i) | ((dE[i] + 8) << 10));
-                ++idx;
+                sl.own[idx] = (uint16_t)((lane << 2 | i) | ((dE[i] + 8) << 8));
             }
+            n += __popc(m);
+        }
         bool ok = true;
-        if constexpr (STORED) ok = mbar_wait(&fs.bar, 0u);   // the tile's stress has landed
+        if constexpr (STORED)
+            if (tid == 0) ok = mbar_wait(&fs.bar, 0u);   // the tile's stress has landed
         if (__syncthreads_or(!ok)) {
             // the copy did not complete: report, wait once more (bounded) for it, decide nothing
             if (tid == 0) {
@@ -472,22 +481,24 @@ __global__ void __launch_bounds__(SWEEP_CTA, flat_min_ctas<T, MODE, RECOMP>())
             }
             return;
         }
-        // the listed trials, evaluated densely by all threads of the CTA
-        const unsigned n = sl.count;
-        for (unsigned e = tid; e < n; e += SWEEP_CTA) {
-            const uint32_t qq = sl.qq[e], ow = sl.own[e];
+        // the warp's listed trials, evaluated densely by its lanes
+        for (unsigned e = lane; e < n; e += 32) {
+            const uint32_t qq = sl.qq[wb + e], ow = sl.own[wb + e];
+            const int site = wb + (int)(ow & 0x7fu);   // thread << 2 | slot
             T s[6];
 #pragma unroll
             for (int k = 0; k < 6; ++k) {
                 if constexpr (STORED)
-                    s[k] = fs.sig[k][ow & 0x3ffu];
+                    s[k] = fs.sig[k][site];
                 else
-                    s[k] = sl.sig[k][e];
+                    s[k] = sl.sig[k][wb + e];
             }
             const T dHe = trial_dhe<T, MODE, RECOMP>(a, R, qq & 0xffffu, qq >> 16, s);
-            sl.acc[ow & 0x3ffu] = metropolis<T>(a, (int)(ow >> 10) - 8, dHe, sl.r1[e]) ? 1 : 0;
+            const bool acc = metropolis<T>(a, (int)(ow >> 8) - 8, dHe, sl.r1[wb + e]);
+            sl.acc[site] = acc ? 1 : 0;
+            dacc += acc ? 1u : 0u;
         }
-        __syncthreads();
+        __syncwarp();
         if (pend) {
 #pragma unroll
             for (int i = 0; i < 4; ++i)
@@ -512,6 +523,20 @@ __global__ void __launch_bounds__(SWEEP_CTA, flat_min_ctas<T, MODE, RECOMP>())
     }
     // a CTA belongs to one replica: one atomic per CTA on that replica's counter (warps of every
     // CTA adding to one address directly would serialise at its L2 slice)
+    if constexpr (ELASTIC) {
+        // the last warp to finish adds the CTA's acceptances
+        const unsigned wt = __reduce_add_sync(FULL, dacc);
+        if (lane == 0) {
+            if (wt) atomicAdd(&sl.nacc, wt);
+            __threadfence_block();
+            if (atomicAdd(&sl.done, 1u) == SWEEP_CTA / 32 - 1) {
+                __threadfence_block();
+                const unsigned c = atomicAdd(&sl.nacc, 0u);
+                if (c) atomicAdd(&R.st->accepted, (unsigned long long)c);
+            }
+        }
+        return;
+    }
     __shared__ unsigned warp_tot[SWEEP_CTA / 32];
     const unsigned tot = __reduce_add_sync(FULL, (unsigned)nacc);
     if (lane == 0) warp_tot[tid >> 5] = tot;
