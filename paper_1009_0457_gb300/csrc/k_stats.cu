@@ -75,26 +75,38 @@ __device__ __forceinline__ void store4<double>(double *p, const double (&v)[4]) 
 }
 
 // Stress of the eight points of each cell from the current displacement; the
-// colour-packed stress array is what the half sweeps read.  Each CTA covers 256
-// blocks of one replica and writes its partial sums of sigma and of
-// 1/2 sigma.eps (a cell's eight points summed plainly, then FP32 TwoSum pairs or
-// FP64 within a warp, by T, and FP64 across warps) for a fixed-order final
+// colour-packed stress array is what the half sweeps read.  Each CTA covers the
+// 256 blocks of one replica's tile with STRESS_THREADS threads, each taking
+// STRESS_CELLS blocks in turn (the warp reduction below is then paid once per
+// STRESS_CELLS cells), and writes its partial sums of sigma and of 1/2 sigma.eps
+// (a cell's eight points summed plainly, then FP32 TwoSum pairs or FP64 within a
+// thread and a warp, by T, and FP64 across warps) for a fixed-order final
 // reduction.
+// threads of a stress CTA (measured on the 256^3 workload: 256 threads, one block each, 0.244 ms;
+// 128 threads 0.180 ms; 64 threads 0.156 ms; 32 threads 0.156 ms)
+constexpr int STRESS_THREADS = 64;
+constexpr int STRESS_CELLS = BLOCK_THREADS / STRESS_THREADS;
+static_assert(BLOCK_THREADS % STRESS_THREADS == 0, "a tile splits evenly over the threads");
+
 template <typename T, bool STORE>
-__global__ void __launch_bounds__(BLOCK_THREADS) k_stress(StressArgs<T> a) {
-    __shared__ double red[BLOCK_THREADS / 32][7];
+__global__ void __launch_bounds__(STRESS_THREADS) k_stress(StressArgs<T> a) {
+    __shared__ double red[STRESS_THREADS / 32][7];
     const int rep = __ldg(a.cta_rep + blockIdx.x);
     const Replica &R = a.reps[rep];
-    const int blk = (blockIdx.x - R.cta_off) * BLOCK_THREADS + threadIdx.x;
+    const int t0 = (blockIdx.x - R.cta_off) * BLOCK_THREADS;
     Acc7<T> acc;
     acc.zero();
-    if (blk < R.nblk) {
-        T eb[6];
-        load_ebar<T>(R.st, eb);
-        const int nbx = R.nbx, nby = R.nby, nbz = R.nbz;
+    T eb[6];
+    load_ebar<T>(R.st, eb);
+    const int nbx = R.nbx, nby = R.nby, nbz = R.nbz;
+    const T *u = a.u + 3 * R.blk_off;
+    T *sig = a.sig + 48ll * R.blk_off;
+#pragma unroll 1
+    for (int c8 = 0; c8 < STRESS_CELLS; ++c8) {
+        const int blk = t0 + c8 * STRESS_THREADS + threadIdx.x;
+        if (blk >= R.nblk) break;
         const int bx = blk % nbx, rr = blk / nbx;
         const int by = rr % nby, bz = rr / nby;
-        const T *u = a.u + 3 * R.blk_off;
         T uc[8][3];
 #pragma unroll
         for (int K = 0; K < 2; ++K)
@@ -112,39 +124,40 @@ __global__ void __launch_bounds__(BLOCK_THREADS) k_stress(StressArgs<T> a) {
         CellGrad<T> g;
         cell_gradients<T>(uc, g);
         const uint4 sp = __ldg(a.spins + R.blk_off + blk);
-        T out[2][6][4];
         T csum[7] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0)};   // this cell's eight points, plain sums
         Row24<T> row;
         uint32_t qprev = 0xffffffffu;
+        // red slots 0..3, then black 4..7: each colour's stress is stored as soon as it is formed
 #pragma unroll
-        for (int slot = 0; slot < 8; ++slot) {
-            const int L = slot_local(slot);
-            T e[6], s[6];
-            point_strain<T>(g, eb, L & 1, (L >> 1) & 1, L >> 2, e);
-            const uint32_t q = spin_of(sp, slot);  // points of a cell mostly share one orientation
-            if (q != qprev) {
-                row.load(a.ctab + 24ll * q);
-                qprev = q;
-            }
-            hooke21<T>(row.v, e, s);
-            T w = T(0);
+        for (int c = 0; c < 2; ++c) {
+            T out[6][4];
 #pragma unroll
-            for (int k = 0; k < 6; ++k) {
-                out[slot >> 2][k][slot & 3] = s[k];
-                csum[k] += s[k];
-                w += s[k] * e[k];
+            for (int j = 0; j < 4; ++j) {
+                const int slot = 4 * c + j, L = slot_local(slot);
+                T e[6], st[6];
+                point_strain<T>(g, eb, L & 1, (L >> 1) & 1, L >> 2, e);
+                const uint32_t q = spin_of(sp, slot);  // points of a cell mostly share one orientation
+                if (q != qprev) {
+                    row.load(a.ctab + 24ll * q);
+                    qprev = q;
+                }
+                hooke21<T>(row.v, e, st);
+                T w = T(0);
+#pragma unroll
+                for (int k = 0; k < 6; ++k) {
+                    out[k][j] = st[k];
+                    csum[k] += st[k];
+                    w += st[k] * e[k];
+                }
+                csum[6] += T(0.5) * w;
             }
-            csum[6] += T(0.5) * w;
+            if (STORE) {
+#pragma unroll
+                for (int k = 0; k < 6; ++k) store4<T>(sig + 4ll * ((long long)(c * 6 + k) * R.nblk + blk), out[k]);
+            }
         }
 #pragma unroll
         for (int k = 0; k < 7; ++k) acc.add(k, csum[k]);
-        if (STORE) {
-            T *sig = a.sig + 48ll * R.blk_off;
-#pragma unroll
-            for (int c = 0; c < 2; ++c)
-#pragma unroll
-                for (int k = 0; k < 6; ++k) store4<T>(sig + 4ll * ((long long)(c * 6 + k) * R.nblk + blk), out[c][k]);
-        }
     }
     acc.warp_reduce();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -153,7 +166,7 @@ __global__ void __launch_bounds__(BLOCK_THREADS) k_stress(StressArgs<T> a) {
     __syncthreads();
     if (threadIdx.x < 7) {
         double s = 0.0;
-        for (int w = 0; w < BLOCK_THREADS / 32; ++w) s += red[w][threadIdx.x];
+        for (int w = 0; w < STRESS_THREADS / 32; ++w) s += red[w][threadIdx.x];
         a.partials[7ll * blockIdx.x + threadIdx.x] = s;
     }
 }
@@ -328,9 +341,9 @@ __global__ void k_bins(const unsigned long long *counts, const int32_t *binmap, 
 template <typename T>
 cudaError_t launch_stress(const StressArgs<T> &a, bool store, cudaStream_t s) {
     if (store)
-        k_stress<T, true><<<a.nctas, BLOCK_THREADS, 0, s>>>(a);
+        k_stress<T, true><<<a.nctas, STRESS_THREADS, 0, s>>>(a);
     else
-        k_stress<T, false><<<a.nctas, BLOCK_THREADS, 0, s>>>(a);
+        k_stress<T, false><<<a.nctas, STRESS_THREADS, 0, s>>>(a);
     return cudaGetLastError();
 }
 template cudaError_t launch_stress<float>(const StressArgs<float> &, bool, cudaStream_t);
