@@ -492,6 +492,69 @@ def run_zone(args):
     return 0
 
 
+ADJ_STEPS, ADJ_EVERY = 200, 20
+
+
+def run_adjoint(args):
+    """The adjoint of the explicit MPM solve (the differentiation form) on the 128^3
+    microstructure: spins frozen, Ebar = the library's initial mixed-control strain for
+    2e-3 along [001], 200 FP32 steps with a checkpoint every 20.  One step = the forward
+    map (W and the w field) plus the reverse sweep giving d(gW W + g.w)/d(C11, C12, C44,
+    Ebar_1..6); CUDA events around each, on the library's stream."""
+    import torch
+    torch.cuda.set_device(0)
+    import hmc_synth as S
+    import paper_1009_0457_gb300 as G
+    spec, euler, spins = S.workload_inputs("ni128")
+    nz, ny, nx = spec["shape"]
+    N = nx * ny * nz
+    stream = torch.cuda.Stream()
+    kw = dict(c11=spec["c11"], c12=spec["c12"], c44=spec["c44"], stream=stream.cuda_stream)
+    u = G.HMC(spec["shape"], spec["Q"], precision=G.HMC_FP32, load_axis=(0.0, 0.0, 1.0), strain=2e-3,
+              mpm_steps_per_mcs=0, **kw)
+    u.set_orientations(euler, spins)
+    E = u.strain()
+    u.close()
+    g = G.HMC(spec["shape"], spec["Q"], precision=G.HMC_FP32, bc=G.HMC_BC_STRAIN6, strain6=tuple(E),
+              mpm_steps_per_mcs=0, **kw)
+    g.set_orientations(euler, spins)
+    g_field = np.random.default_rng(5).random(N)
+    nodal0 = g.nodal()
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        r = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3, r
+
+    fw, bw = [], []
+    for it in range(args.warmup + args.steps):
+        g.set_nodal(*nodal0)
+        tf, _ = timed(lambda: g.adjoint_forward(ADJ_STEPS, ADJ_EVERY))
+        tb, grad = timed(lambda: g.adjoint_backward(0.5, g_field))
+        if it >= args.warmup:
+            fw.append(tf)
+            bw.append(tb)
+    t_mpm, _ = timed(lambda: G.lib.hmc_mpm_steps(g.h, ADJ_STEPS, None))
+    tf, tb = float(np.median(fw)), float(np.median(bw))
+    line = {"metric": METRIC, "value": N * ADJ_STEPS / (tf + tb), "unit": "cell-steps/s (forward + reverse)",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * (tf + tb),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "adjoint128: the 128^3 Ni polycrystal (Q=256, 5000 Voronoi grains) with frozen spins, "
+                                   "mean strain = the initial mixed-control strain for 2e-3 along [001], 200 explicit "
+                                   "FP32 MPM steps, checkpoint every 20, gradient of 0.5 W + g.w w.r.t. C11, C12, C44 "
+                                   "and the 6 mean-strain components", "sites": N},
+            "forward_ms": 1e3 * tf, "reverse_ms": 1e3 * tb, "plain_mpm_ms": 1e3 * t_mpm,
+            "adjoint_cost_in_forward_steps": (tf + tb) / (t_mpm / ADJ_STEPS) / ADJ_STEPS,
+            "gradient": [float(x) for x in grad]}
+    print(json.dumps(line), flush=True)
+    g.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -500,6 +563,8 @@ def main():
         return run_ensemble(args)
     if args.workload == "zone128":
         return run_zone(args)
+    if args.workload == "adjoint128":
+        return run_adjoint(args)
     return run_ours(args)
 
 

@@ -11,6 +11,7 @@ struct AdjArgs {
     const uint4 *spins;   // block layout
     const T *ctab;        // C'(q), 21 entries padded to 24
     const T *rtab;        // rotated basis tensors R_1, R_2, R_3 per orientation, 3 x 24
+    const T *wtab;        // Voigt weights of the three crystal axes a_m (a_m.x.a_m = w_m.x), 20 per orientation
     double *partials;     // per-CTA partial sums
     T ebar[6];            // mean strain of the forward state
     int nx, ny, nz, nbx, nby, nbz, nblk;

@@ -1575,6 +1575,7 @@ hmc::AdjArgs<T> adj_args(hmc_handle *h) {
     a.spins = h->spins;
     a.ctab = static_cast<const T *>(h->ctab);
     a.rtab = static_cast<const T *>(h->adj.rtab);
+    a.wtab = static_cast<const T *>(h->wtab);
     a.partials = h->adj.partials;
     for (int i = 0; i < 6; ++i) a.ebar[i] = (T)h->adj.ebar[i];
     a.nx = R.p.nx; a.ny = R.p.ny; a.nz = R.p.nz;
@@ -1698,6 +1699,8 @@ hmc_status adj_backward_t(hmc_handle *h, double gW, const double *g_field, doubl
                                         h->stream),
            "gather launch");
     const size_t nb = node_bytes(h);
+    // every reverse step adds its parameter terms to its CTA's partials; one reduction at the end
+    HMC_CK(h, cudaMemsetAsync(A.partials, 0, sizeof(double) * 9 * (size_t)A.nctas, h->stream), "memset");
     for (int s = A.nseg - 1; s >= 0; --s) {
         const int n0 = s * A.ck, len = std::min(A.ck, A.steps - n0);
         // recompute the segment's forward states u^{n0} .. u^{n0+len-1} from its checkpoint
@@ -1713,7 +1716,6 @@ hmc_status adj_backward_t(hmc_handle *h, double gW, const double *g_field, doubl
             HMC_CK(h, hmc::launch_adj_params<T>(aa, static_cast<const T *>(A.lam),
                                                 reinterpret_cast<const T *>(seg_ptr(h, A.seg, j)), h->stream),
                    "parameter launch");
-            HMC_CK(h, hmc::launch_adj_reduce(A.partials, A.nctas, 9, 9, -c, A.grad + 1, h->stream), "reduce launch");
             // ubar^n = ubar^{n+1} + c F(lambda^{n+1}; 0); tmp = lambda^{n+1} + dt ubar^n
             HMC_CK(h, mpm_custom<T>(h, A.lam, A.tmp, A.ubar, A.reps0, 1.0), "adjoint step launch");
             HMC_CK(h, hmc::launch_adj_lambda<T>(3ll * R.nblk, static_cast<const T *>(A.tmp), (T)h->damping,
@@ -1721,6 +1723,7 @@ hmc_status adj_backward_t(hmc_handle *h, double gW, const double *g_field, doubl
                    "lambda launch");
         }
     }
+    HMC_CK(h, hmc::launch_adj_reduce(A.partials, A.nctas, 9, 9, -c, A.grad + 1, h->stream), "reduce launch");
     double out[10];
     HMC_CK(h, cudaMemcpyAsync(out, A.grad, sizeof(out), cudaMemcpyDeviceToHost, h->stream), "download");
     HMC_CK(h, cudaStreamSynchronize(h->stream), "sync");

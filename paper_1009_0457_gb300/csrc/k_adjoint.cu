@@ -12,10 +12,11 @@
 // plus the terminal terms sum_p alpha_p [1/2 eps.R_i.eps, (C' eps)_k].  R_i are
 // the rotated basis tensors with C' = C11 R_1 + C12 R_2 + C44 R_3.
 //
-// These kernels: the per-step parameter reduction, the terminal pass (field
-// w, W, alpha-weighted nodal vector through a per-cell buffer and a node
-// gather, terminal parameter terms), the lambda update, and the fixed-order
-// FP64 reduction of per-CTA partials.  Single replica; one thread per cell.
+// These kernels: the per-step parameter terms (added to per-CTA partials that
+// are reduced once per reverse sweep), the terminal pass (field w, W,
+// alpha-weighted nodal vector through a per-cell buffer and a node gather,
+// terminal parameter terms), the lambda update, and the fixed-order FP64
+// reduction of per-CTA partials.  Single replica; one thread per cell.
 #include "hmc_device.cuh"
 #include "hmc_adjoint.h"
 
@@ -49,31 +50,122 @@ __device__ __forceinline__ T quad21(const T *c, const T (&a)[6], const T (&b)[6]
     return a[0] * s[0] + a[1] * s[1] + a[2] * s[2] + a[3] * s[3] + a[4] * s[4] + a[5] * s[5];
 }
 
-// Sum the NV values of every thread into one FP64 partial per CTA.
+// Error-free sum of two floats (Knuth's TwoSum): a + b = s + e exactly.
+struct TwoSumF {
+    float hi, lo;
+    __device__ __forceinline__ void add(float x) {
+        const float s = hi + x;
+        const float bb = s - hi;
+        const float e = (hi - (s - bb)) + (x - bb);
+        hi = s;
+        lo += e;
+    }
+};
+
+// Per-thread accumulators of NV reduced quantities: FP32 values are summed as
+// TwoSum pairs (no FP64 arithmetic per point or per cell), FP64 values plainly.
+template <typename T, int NV>
+struct AdjAcc;
 template <int NV>
-__device__ __forceinline__ void cta_partials(double (&v)[NV], double *partials) {
+struct AdjAcc<float, NV> {
+    TwoSumF v[NV];
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) v[i].hi = v[i].lo = 0.f;
+    }
+    __device__ __forceinline__ void add(int i, float x) { v[i].add(x); }
+    __device__ __forceinline__ void warp_reduce() {
+#pragma unroll
+        for (int off = 16; off; off >>= 1)
+#pragma unroll
+            for (int i = 0; i < NV; ++i) {
+                const float hi = __shfl_down_sync(0xffffffffu, v[i].hi, off);
+                const float lo = __shfl_down_sync(0xffffffffu, v[i].lo, off);
+                v[i].add(hi);
+                v[i].lo += lo;
+            }
+    }
+    __device__ __forceinline__ double get(int i) const { return (double)v[i].hi + (double)v[i].lo; }
+};
+template <int NV>
+struct AdjAcc<double, NV> {
+    double v[NV];
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) v[i] = 0.0;
+    }
+    __device__ __forceinline__ void add(int i, double x) { v[i] += x; }
+    __device__ __forceinline__ void warp_reduce() {
+#pragma unroll
+        for (int off = 16; off; off >>= 1)
+#pragma unroll
+            for (int i = 0; i < NV; ++i) v[i] += __shfl_down_sync(0xffffffffu, v[i], off);
+    }
+    __device__ __forceinline__ double get(int i) const { return v[i]; }
+};
+
+// Sum the NV values of every thread into one FP64 partial per CTA, stored, or
+// added to the CTA's partial (accumulate: the reverse sweep sums its steps per CTA
+// and reduces across CTAs once).
+template <typename T, int NV>
+__device__ __forceinline__ void cta_partials(AdjAcc<T, NV> &acc, double *partials, bool accumulate) {
     __shared__ double red[8][NV];
-#pragma unroll
-    for (int off = 16; off; off >>= 1)
-#pragma unroll
-        for (int i = 0; i < NV; ++i) v[i] += __shfl_down_sync(0xffffffffu, v[i], off);
+    acc.warp_reduce();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (lane == 0)
-        for (int i = 0; i < NV; ++i) red[warp][i] = v[i];
+        for (int i = 0; i < NV; ++i) red[warp][i] = acc.get(i);
     __syncthreads();
     if (threadIdx.x < NV) {
         double s = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w][threadIdx.x];
-        partials[NV * (long long)blockIdx.x + threadIdx.x] = s;
+        double *p = partials + NV * (long long)blockIdx.x + threadIdx.x;
+        *p = accumulate ? *p + s : s;
     }
 }
 
-// One reverse step's parameter terms: per point epsbar.R_i.eps (i = 1..3) and
-// C' epsbar (6), summed per CTA.
+// The basis quadratic forms of a rotated cubic crystal from the crystal-axis
+// projections p_m(x) = a_m.x.a_m (x a strain, engineering shear):
+//   x.R_1.y = P,  x.R_2.y = tr x tr y - P,  x.R_3.y = 2 (x:y - P),  P = sum_m p_m(x) p_m(y),
+// since R_1 holds the crystal-frame normal-normal diagonal, R_2 its off-diagonal
+// and R_3 the engineering-shear diagonal.  w holds the Voigt weights of the three
+// axes for tensor-shear components, so the shear strains enter halved.
 template <typename T>
-__global__ void __launch_bounds__(256) k_adj_params(AdjArgs<T> a, const T *__restrict__ lam,
+__device__ __forceinline__ void basis_forms(const T (&w)[18], const T (&x)[6], const T (&y)[6], T (&r)[3]) {
+    const T xh[6] = {x[0], x[1], x[2], T(0.5) * x[3], T(0.5) * x[4], T(0.5) * x[5]};
+    const T yh[6] = {y[0], y[1], y[2], T(0.5) * y[3], T(0.5) * y[4], T(0.5) * y[5]};
+    T P = T(0);
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+        T px = T(0), py = T(0);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            px += w[6 * m + k] * xh[k];
+            py += w[6 * m + k] * yh[k];
+        }
+        P += px * py;
+    }
+    const T tr = (x[0] + x[1] + x[2]) * (y[0] + y[1] + y[2]);
+    const T dd = x[0] * y[0] + x[1] * y[1] + x[2] * y[2] + x[3] * yh[3] + x[4] * yh[4] + x[5] * yh[5];
+    r[0] = P;
+    r[1] = tr - P;
+    r[2] = T(2) * (dd - P);
+}
+
+template <typename T>
+__device__ __forceinline__ void load_row(const T *__restrict__ p, int n, T *out) {
+#pragma unroll
+    for (int k = 0; k < n; ++k) out[k] = __ldg(p + k);
+}
+
+// One reverse step's parameter terms: per point epsbar.R_i.eps (i = 1..3) and
+// C' epsbar (6); a cell's eight points are summed plainly, cells by the
+// accumulator, and the CTA's sums are added to its partials.  The axis weights and
+// the stiffness row are loaded when the orientation changes from one point to the next.
+template <typename T>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adj_params(AdjArgs<T> a, const T *__restrict__ lam,
                                                     const T *__restrict__ u) {
-    double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    AdjAcc<T, 9> acc;
+    acc.zero();
     const int blk = blockIdx.x * blockDim.x + threadIdx.x;
     if (blk < a.nblk) {
         const int bx = blk % a.nbx, r = blk / a.nbx;
@@ -86,22 +178,33 @@ __global__ void __launch_bounds__(256) k_adj_params(AdjArgs<T> a, const T *__res
         cell_gradients<T>(cu, gu);
         const uint4 sp = __ldg(a.spins + blk);
         const T zero[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+        T csum[9] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
+        T w[18];
+        Row24<T> crow;
+        uint32_t qprev = 0xffffffffu;
 #pragma unroll
         for (int L = 0; L < 8; ++L) {
             const int x = L & 1, y = (L >> 1) & 1, z = L >> 2;
-            T eb[6], e[6], s[6];
+            T eb[6], e[6], s[6], rf[3];
             point_strain<T>(gl, zero, x, y, z, eb);
             point_strain<T>(gu, a.ebar, x, y, z, e);
             const uint32_t q = spin_of(sp, local_slot(L));
-            const T *rq = a.rtab + 72ll * q;
+            if (q != qprev) {
+                load_row<T>(a.wtab + 20ll * q, 18, w);
+                crow.load(a.ctab + 24ll * q);
+                qprev = q;
+            }
+            basis_forms<T>(w, eb, e, rf);
 #pragma unroll
-            for (int i = 0; i < 3; ++i) acc[i] += (double)quad21<T>(rq + 24 * i, eb, e);
-            hooke21<T>(a.ctab + 24ll * q, eb, s);
+            for (int i = 0; i < 3; ++i) csum[i] += rf[i];
+            hooke21<T>(crow.v, eb, s);
 #pragma unroll
-            for (int k = 0; k < 6; ++k) acc[3 + k] += (double)s[k];
+            for (int k = 0; k < 6; ++k) csum[3 + k] += s[k];
         }
+#pragma unroll
+        for (int i = 0; i < 9; ++i) acc.add(i, csum[i]);
     }
-    cta_partials<9>(acc, a.partials);
+    cta_partials<T, 9>(acc, a.partials, true);
 }
 
 // Terminal pass at u^T: field w (natural order), per-CTA partials of
@@ -111,11 +214,13 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_adj_terminal(AdjArgs<T> a, const T *__restrict__ u,
                                                       const T *__restrict__ g, T gW, T *__restrict__ w,
                                                       T *__restrict__ fcell) {
-    double acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    AdjAcc<T, 10> acc;
+    acc.zero();
     const int blk = blockIdx.x * blockDim.x + threadIdx.x;
     if (blk < a.nblk) {
         const int bx = blk % a.nbx, r = blk / a.nbx;
         const int by = r % a.nby, bz = r / a.nby;
+        T csum[10] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
         T cu[8][3];
         load_corners<T>(u, bx, by, bz, a.nbx, a.nby, a.nbz, cu);
         CellGrad<T> gu;
@@ -139,13 +244,13 @@ __global__ void __launch_bounds__(256) k_adj_terminal(AdjArgs<T> a, const T *__r
             const T wp = T(0.5) * (s[0] * e[0] + s[1] * e[1] + s[2] * e[2] + s[3] * e[3] + s[4] * e[4] + s[5] * e[5]);
             if (w) w[p] = wp;
             const T al = gW + (g ? g[p] : T(0));
-            acc[0] += (double)wp;
+            csum[0] += wp;
             const T *rq = a.rtab + 72ll * q;
 #pragma unroll
-            for (int i = 0; i < 3; ++i) acc[1 + i] += (double)(al * T(0.5) * quad21<T>(rq + 24 * i, e, e));
+            for (int i = 0; i < 3; ++i) csum[1 + i] += al * T(0.5) * quad21<T>(rq + 24 * i, e, e);
 #pragma unroll
             for (int k = 0; k < 6; ++k) {
-                acc[4 + k] += (double)(al * s[k]);
+                csum[4 + k] += al * s[k];
                 s[k] *= al;
             }
             tx[y][z][0] += s[0]; tx[y][z][1] += s[5]; tx[y][z][2] += s[4];
@@ -172,8 +277,10 @@ __global__ void __launch_bounds__(256) k_adj_terminal(AdjArgs<T> a, const T *__r
                         fc[3 * corner(I, J, K) + d] = fx + fy + fz;
                     }
         }
+#pragma unroll
+        for (int i = 0; i < 10; ++i) acc.add(i, csum[i]);
     }
-    cta_partials<10>(acc, a.partials);
+    cta_partials<T, 10>(acc, a.partials, false);
 }
 
 // Node gather of the per-cell corner contributions (fixed order): out = scale * sum.
