@@ -227,13 +227,16 @@ hmc_status hmc_mpm_steps(hmc_handle *h, int32_t nsteps, double *elastic_energy);
  * in FP64 across the domain.  Either pointer may be NULL. */
 hmc_status hmc_compute_stress(hmc_handle *h, double *mean_stress, double *elastic_energy);
 
-/* One red/black half sweep (Sec. "Microstructural Evolution"): every site of
- * `colour` ((x+y+z) even = 0 = red) takes two words of a Philox4x32-10 block
- * with counter (s, mcs, replica, 0) and key seed, s the index of the site at
- * even x of the pair {(x even, y, z), (x+1, y^1, z)} (the even-x site takes
- * words 0-1, its partner words 2-3), picks a trial orientation, and is
- * accepted by Eq. 5 on J*(change of unlike-neighbour count) plus lambda times
- * the stored-stress zone shift.  The MC step counter is not advanced.
+/* One red/black half sweep (Sec. "Microstructural Evolution"): the four sites
+ * of `colour` ((x+y+z) even = 0 = red) in each 2x2x2 block share one
+ * Philox4x32-10 block with counter (s, mcs, replica, 2 + colour) and key seed,
+ * s the index of the block's origin site; the site with the j-th smallest local
+ * corner index lx + 2 ly + 4 lz takes word w = word j.  A neighbour trial picks
+ * neighbour floor(6 w / 2^32) (order -x, +x, -y, +y, -z, +z) and takes the low
+ * 32 bits of 6 w as its acceptance draw; a trial over all orientations picks
+ * floor(Q w / 2^32) and takes word j of a second block (counter word 3 =
+ * 4 + colour).  The trial is accepted by Eq. 5 on J*(change of unlike-neighbour
+ * count) plus lambda times the stored-stress zone shift.  The MC step counter is not advanced.
  * *accepted (nullable) receives the number of sites that changed.  A
  * stored-stress sweep waits for its asynchronous stress copy with a 1 s limit
  * per CTA; a CTA whose wait ran out changes no spin, and the next call that
