@@ -69,7 +69,7 @@ struct hmc_handle {
     void *u[2] = {nullptr, nullptr};
     void *v = nullptr;
     int cur = 0;
-    void *sig = nullptr, *ctab = nullptr, *wtab = nullptr;
+    void *sig = nullptr, *ctab = nullptr, *wtab = nullptr, *atab = nullptr;
     float *ctab_pairs = nullptr;          // FP32 MPM stiffness rows as component pairs
     // 27-point zone (HMC_ELASTIC_ZONE1): trial list, start-of-step spins, element tables, schedule
     uint4 *zone_work = nullptr, *snap = nullptr;
@@ -222,6 +222,16 @@ std::vector<T> pack_wtab(const std::vector<double> &A, int Q) {
     return out;
 }
 
+// the first two crystal axes (columns 0 and 1 of A) of every orientation, padded to 8
+template <typename T>
+std::vector<T> pack_atab(const std::vector<double> &A, int Q) {
+    std::vector<T> out((size_t)Q * 8, T(0));
+    for (int q = 0; q < Q; ++q)
+        for (int m = 0; m < 2; ++m)
+            for (int r = 0; r < 3; ++r) out[(size_t)q * 8 + 3 * m + r] = (T)A[(size_t)q * 9 + r * 3 + m];
+    return out;
+}
+
 void axis_vectors(const double *n, double *N, double *Nsv) {
     N[0] = n[0] * n[0]; N[1] = n[1] * n[1]; N[2] = n[2] * n[2];
     N[3] = n[1] * n[2]; N[4] = n[0] * n[2]; N[5] = n[0] * n[1];
@@ -281,7 +291,7 @@ cudaError_t enqueue_sweep(hmc_handle *h, int colour, cudaStream_t s) {
     a.cta_rep = h->d_cta_rep;
     a.spins = h->spins;
     a.sig = static_cast<const T *>(h->sig);
-    a.wtab = static_cast<const T *>(h->wtab);
+    a.atab = static_cast<const T *>(h->atab);
     a.thr = h->thr;
     a.trial = h->p.trial;
     a.nq = h->p.n_orient;
@@ -482,7 +492,7 @@ void destroy_buffers(hmc_handle *h) {
     free_adjoint(h);
     for (int i = 0; i < 2; ++i)
         if (h->gexec[i]) cudaGraphExecDestroy(h->gexec[i]);
-    void *bufs[] = {h->spins, h->stage16, h->u[0], h->u[1], h->v, h->sig, h->ctab, h->ctab_pairs, h->wtab, h->thr, h->counts,
+    void *bufs[] = {h->spins, h->stage16, h->u[0], h->u[1], h->v, h->sig, h->ctab, h->ctab_pairs, h->wtab, h->atab, h->thr, h->counts,
                     h->bins, h->partials, h->fractions, h->binmap, h->st, h->d_reps, h->d_cta_rep, h->d_sched,
                     h->zone_work, h->snap, h->zone_count, h->ktab, h->zone_sched, h->cc_parent, h->cc_count,
                     h->stab};
@@ -818,7 +828,8 @@ hmc_status hmc_create_batch(const hmc_params *params, int32_t n_replicas, hmc_ha
         {&h->sig, h->tsize * 48 * (size_t)h->nblk_total, "stress"},
         {&h->ctab, h->tsize * 24 * (size_t)p->n_orient, "stiffness table"},
         {(void **)&h->ctab_pairs, sizeof(float) * 36 * (size_t)p->n_orient, "stiffness pair table"},
-        {&h->wtab, h->tsize * 20 * (size_t)p->n_orient, "zone table"},
+        {&h->wtab, h->tsize * 20 * (size_t)p->n_orient, "axis weight table"},
+        {&h->atab, h->tsize * 8 * (size_t)p->n_orient, "axis table"},
         {(void **)&h->thr, sizeof(unsigned long long) * 8, "threshold table"},
         {(void **)&h->counts, sizeof(unsigned long long) * (size_t)p->n_orient, "orientation counts"},
         {(void **)&h->partials, sizeof(double) * 7 * (size_t)h->nctas, "partials"},
@@ -1006,8 +1017,10 @@ hmc_status hmc_set_orientations(hmc_handle *h, const double *euler, const uint16
     if (h->p.precision == HMC_FP32) {
         auto c = pack_ctab<float>(h->Cv, Q);
         auto w = pack_wtab<float>(h->A, Q);
+        auto ax = pack_atab<float>(h->A, Q);
         HMC_CK(h, cudaMemcpy(h->ctab, c.data(), c.size() * sizeof(float), cudaMemcpyHostToDevice), "table upload");
         HMC_CK(h, cudaMemcpy(h->wtab, w.data(), w.size() * sizeof(float), cudaMemcpyHostToDevice), "table upload");
+        HMC_CK(h, cudaMemcpy(h->atab, ax.data(), ax.size() * sizeof(float), cudaMemcpyHostToDevice), "table upload");
         std::vector<float> cp((size_t)Q * 36);
         for (int q = 0; q < Q; ++q)
             for (int k = 0; k < 3; ++k)
@@ -1020,8 +1033,10 @@ hmc_status hmc_set_orientations(hmc_handle *h, const double *euler, const uint16
     } else {
         auto c = pack_ctab<double>(h->Cv, Q);
         auto w = pack_wtab<double>(h->A, Q);
+        auto ax = pack_atab<double>(h->A, Q);
         HMC_CK(h, cudaMemcpy(h->ctab, c.data(), c.size() * sizeof(double), cudaMemcpyHostToDevice), "table upload");
         HMC_CK(h, cudaMemcpy(h->wtab, w.data(), w.size() * sizeof(double), cudaMemcpyHostToDevice), "table upload");
+        HMC_CK(h, cudaMemcpy(h->atab, ax.data(), ax.size() * sizeof(double), cudaMemcpyHostToDevice), "table upload");
     }
     if (h->p.elastic == HMC_ELASTIC_STRAIN) {
         if (h->p.precision == HMC_FP32) {

@@ -10,9 +10,12 @@
 //                               component of a block is one 16 B (FP32) load
 //   ctab    T[Q][24]            rotated stiffness C'(q), 21 upper-triangle Voigt
 //                               entries (row-major) padded to 24
-//   wtab    T[Q][20]            zone-energy weights: for each crystal axis a_m the
-//                               Voigt vector (a1^2,a2^2,a3^2,2a2a3,2a1a3,2a1a2),
-//                               18 values padded to 20
+//   wtab    T[Q][20]            for each crystal axis a_m the Voigt vector
+//                               (a1^2,a2^2,a3^2,2a2a3,2a1a3,2a1a2), 18 values padded
+//                               to 20 (the adjoint's basis forms)
+//   atab    T[Q][8]             the first two crystal axes a_0, a_1 in the sample
+//                               frame (columns of A), padded to 8 (the sweep's zone
+//                               energy)
 #pragma once
 
 #include <cuda_runtime.h>
@@ -124,7 +127,7 @@ struct SweepArgs {
     const int *cta_rep;
     uint4 *spins;
     const T *sig;
-    const T *wtab;
+    const T *atab;                   // the first two crystal axes per orientation (8 values)
     const unsigned long long *thr;   // integer Metropolis thresholds for dE = 0..7
     int trial, nq;
     T J, kT;

@@ -43,31 +43,31 @@ constexpr int SPLIT = BLOCK_THREADS / SWEEP_CTA;
 static_assert(BLOCK_THREADS % SWEEP_CTA == 0, "tiles split evenly");
 static_assert(4 * SWEEP_CTA <= 1024, "a trial's thread and slot fit ten bits");
 
-// Phi(q; sigma) = sum over the three crystal axes of (a_m . sigma . a_m)^2, from
-// the Voigt weight vectors of the axes.  For one cubic material the zone energy
-// w(q) = 1/2 sigma.S'(q).sigma = 1/2 [S12 tr^2 + S44/2 |sigma|^2 + s_d Phi(q)], so
-// w(q_old) - w(q_new) = s_d / 2 (Phi(q_old) - Phi(q_new)).
+// Phi(q; sigma) = sum over the three crystal axes of p_m^2, p_m = a_m . sigma . a_m.
+// For one cubic material the zone energy w(q) = 1/2 sigma.S'(q).sigma =
+// 1/2 [S12 tr^2 + S44/2 |sigma|^2 + s_d Phi(q)], so
+// w(q_old) - w(q_new) = s_d / 2 (Phi(q_old) - Phi(q_new)).  The axes are orthonormal,
+// so p_2 = tr sigma - p_0 - p_1 and two axes per orientation suffice (an 8-value
+// row, two 16-byte loads).
 template <typename T>
-struct Row20;
+struct AxisRow;
 template <>
-struct Row20<float> {
-    float v[20];
+struct AxisRow<float> {
+    float v[8];
     __device__ __forceinline__ void load(const float *p) {
         const float4 *q = reinterpret_cast<const float4 *>(p);
-#pragma unroll
-        for (int i = 0; i < 5; ++i) {
-            const float4 t = __ldg(q + i);
-            v[4 * i] = t.x; v[4 * i + 1] = t.y; v[4 * i + 2] = t.z; v[4 * i + 3] = t.w;
-        }
+        const float4 t0 = __ldg(q), t1 = __ldg(q + 1);
+        v[0] = t0.x; v[1] = t0.y; v[2] = t0.z; v[3] = t0.w;
+        v[4] = t1.x; v[5] = t1.y; v[6] = t1.z; v[7] = t1.w;
     }
 };
 template <>
-struct Row20<double> {
-    double v[20];
+struct AxisRow<double> {
+    double v[8];
     __device__ __forceinline__ void load(const double *p) {
         const double2 *q = reinterpret_cast<const double2 *>(p);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) {
+        for (int i = 0; i < 3; ++i) {
             const double2 t = __ldg(q + i);
             v[2 * i] = t.x; v[2 * i + 1] = t.y;
         }
@@ -76,18 +76,20 @@ struct Row20<double> {
 
 // explicitly rounded, so that every mode evaluates it identically
 template <typename T>
-__device__ __forceinline__ T zone_phi(const T *__restrict__ w, const T (&s)[6]) {
-    Row20<T> r;
-    r.load(w);
-    T acc = T(0);
+__device__ __forceinline__ T zone_phi(const T *__restrict__ ax, const T (&s)[6]) {
+    AxisRow<T> a;
+    a.load(ax);
+    const T s3 = s[3] + s[3], s4 = s[4] + s[4], s5 = s[5] + s[5];
+    T p[2];
 #pragma unroll
-    for (int m = 0; m < 3; ++m) {
-        T p = rmul(r.v[6 * m], s[0]);
-#pragma unroll
-        for (int k = 1; k < 6; ++k) p = rfma(r.v[6 * m + k], s[k], p);
-        acc = rfma(p, p, acc);
+    for (int m = 0; m < 2; ++m) {
+        const T x = a.v[3 * m], y = a.v[3 * m + 1], z = a.v[3 * m + 2];
+        const T t1 = rfma(z, s4, rfma(y, s5, rmul(x, s[0])));   // x s11 + 2 y s12 + 2 z s13
+        const T t2 = rfma(z, s3, rmul(y, s[1]));               // y s22 + 2 z s23
+        p[m] = rfma(rmul(z, s[2]), z, rfma(y, t2, rmul(x, t1)));
     }
-    return acc;
+    const T p2 = ((s[0] + s[1]) + s[2]) - p[0] - p[1];
+    return rfma(p[0], p[0], rfma(p[1], p[1], rmul(p2, p2)));
 }
 
 // FP32: the hardware logarithm (relative error ~1e-7, inside the decision margin the parity
@@ -209,7 +211,7 @@ __device__ __forceinline__ T trial_dhe(const SweepArgs<T> &a, const Replica &R, 
             rw.load(a.ctab + 24ll * q);
             hooke21<T>(rw.v, e6, s);
         }
-        return rep_scale<T>(R.lam_sd_half, R.lam_sd_half_f) * (zone_phi<T>(a.wtab + 20ll * q, s) - zone_phi<T>(a.wtab + 20ll * qn, s));
+        return rep_scale<T>(R.lam_sd_half, R.lam_sd_half_f) * (zone_phi<T>(a.atab + 8ll * q, s) - zone_phi<T>(a.atab + 8ll * qn, s));
     }
     // constant strain: e (stored forms: S'(q) s) held fixed, 1/2 (e.C'(q_new)e - e.C'(q)e)
     T e6[6], sn[6], so[6];
