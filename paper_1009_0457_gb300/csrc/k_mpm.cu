@@ -172,6 +172,15 @@ __device__ __forceinline__ void cell_gradients31(const T (&u)[8][3], CellGrad<T>
     }
 }
 
+// The point visited n-th in a cell: the corners in a Gray-code order, one coordinate
+// changing per step.  A cell split by a grain boundary reloads its stiffness row
+// whenever the orientation changes from one point to the next: 4, 2 and 1 times for a
+// boundary plane normal to x, y and z (7, 3 and 1 in plain corner order).  Every MPM
+// variant visits the points in this order, so their results stay bit-identical.
+__host__ __device__ constexpr int gray_point(int n) {
+    return n == 0 ? 0 : n == 1 ? 1 : n == 2 ? 3 : n == 3 ? 2 : n == 4 ? 6 : n == 5 ? 7 : n == 6 ? 5 : 4;
+}
+
 // Eight points of one cell: F[corner] = (2I-1) X'[J][K] + (2J-1) Y'[I][K] +
 // (2K-1) Z'[I][J] with X', Y', Z' the 3/1-weighted sums of the traction
 // columns of sigma; the nodal force is -(V/h)/16 F = -F/32 (V = 1 voxel, h = 2).
@@ -203,7 +212,8 @@ __device__ __forceinline__ void cell_forces(const T (&u)[8][3], const uint4 &sp,
 #pragma unroll
             for (int d = 0; d < 3; ++d) tx[i][j][d] = ty[i][j][d] = tz[i][j][d] = T(0);
 #pragma unroll
-    for (int L = 0; L < 8; ++L) {
+    for (int n = 0; n < 8; ++n) {
+        const int L = gray_point(n);
         const int a = L & 1, b = (L >> 1) & 1, c = L >> 2;
         T e[6], s[6];
         e[0] = g.gx[b][c][0];
@@ -450,7 +460,8 @@ __device__ __forceinline__ void cell_forces2(const float2 (&u)[8][3], const uint
 #pragma unroll
             for (int d = 0; d < 3; ++d) tx[i][j][d] = ty[i][j][d] = tz[i][j][d] = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int L = 0; L < 8; ++L) {
+    for (int n = 0; n < 8; ++n) {
+        const int L = gray_point(n);
         const int a = L & 1, b = (L >> 1) & 1, c = L >> 2;
         float2 e[6], s[6];
         e[0] = gx[b][c][0];
