@@ -70,7 +70,7 @@ struct hmc_handle {
     void *v = nullptr;
     int cur = 0;
     void *sig = nullptr, *ctab = nullptr, *wtab = nullptr, *atab = nullptr;
-    float *ctab_pairs = nullptr;          // FP32 MPM stiffness rows as component pairs
+    float *cubw = nullptr;                // FP32 MPM step: Voigt weights of two crystal axes per orientation
     // 27-point zone (HMC_ELASTIC_ZONE1): trial list, start-of-step spins, element tables, schedule
     uint4 *zone_work = nullptr, *snap = nullptr;
     unsigned *zone_count = nullptr;
@@ -252,7 +252,12 @@ hmc::MpmArgs<T> mpm_args(hmc_handle *h, const void *u_in, void *u_out, void *v) 
     a.u_out = static_cast<T *>(u_out);
     a.v = static_cast<T *>(v);
     a.ctab = static_cast<const T *>(h->ctab);
-    a.ctab_pairs = h->ctab_pairs;   // FP32 paired-FMA variants
+    a.cubw = h->cubw;               // FP32 step: cubic form of Hooke's law
+    a.cub[0] = (float)h->p.c12;
+    a.cub[1] = (float)(2.0 * h->p.c44);
+    a.cub[2] = (float)h->p.c44;
+    a.cub[3] = (float)(h->p.c11 - h->p.c12 - 2.0 * h->p.c44);
+    a.nq = h->p.n_orient;
     a.dt = (T)h->dt;
     a.dt_over_m = (T)(h->dt / 8.0);  // lumped mass rho * V * sum_p N_I(x_p) = 8 voxels
     a.keep = (T)(1.0 - h->damping);
@@ -492,7 +497,7 @@ void destroy_buffers(hmc_handle *h) {
     free_adjoint(h);
     for (int i = 0; i < 2; ++i)
         if (h->gexec[i]) cudaGraphExecDestroy(h->gexec[i]);
-    void *bufs[] = {h->spins, h->stage16, h->u[0], h->u[1], h->v, h->sig, h->ctab, h->ctab_pairs, h->wtab, h->atab, h->thr, h->counts,
+    void *bufs[] = {h->spins, h->stage16, h->u[0], h->u[1], h->v, h->sig, h->ctab, h->cubw, h->wtab, h->atab, h->thr, h->counts,
                     h->bins, h->partials, h->fractions, h->binmap, h->st, h->d_reps, h->d_cta_rep, h->d_sched,
                     h->zone_work, h->snap, h->zone_count, h->ktab, h->zone_sched, h->cc_parent, h->cc_count,
                     h->stab};
@@ -558,7 +563,8 @@ hmc_status upload_sched(hmc_handle *h, int variant) {
 }
 
 int grid_for_shape(hmc_handle *h, int shape, int per_sm_limit) {
-    int per_sm = h->p.precision == HMC_FP32 ? hmc::mpm_per_sm<float>(shape) : hmc::mpm_per_sm<double>(shape);
+    int per_sm = h->p.precision == HMC_FP32 ? hmc::mpm_per_sm<float>(shape, h->p.n_orient)
+                                            : hmc::mpm_per_sm<double>(shape, h->p.n_orient);
     if (per_sm_limit > 0 && per_sm > per_sm_limit) per_sm = per_sm_limit;
     long long g = (long long)per_sm * h->num_sms;
     const long long cap = (h->mpm_total + 3) / 4;  // at least four planes per CTA
@@ -827,7 +833,7 @@ hmc_status hmc_create_batch(const hmc_params *params, int32_t n_replicas, hmc_ha
         {&h->u[0], nodes_b, "u0"}, {&h->u[1], nodes_b, "u1"}, {&h->v, nodes_b, "v"},
         {&h->sig, h->tsize * 48 * (size_t)h->nblk_total, "stress"},
         {&h->ctab, h->tsize * 24 * (size_t)p->n_orient, "stiffness table"},
-        {(void **)&h->ctab_pairs, sizeof(float) * 36 * (size_t)p->n_orient, "stiffness pair table"},
+        {(void **)&h->cubw, sizeof(float) * 12 * (size_t)p->n_orient, "cubic axis table"},
         {&h->wtab, h->tsize * 20 * (size_t)p->n_orient, "axis weight table"},
         {&h->atab, h->tsize * 8 * (size_t)p->n_orient, "axis table"},
         {(void **)&h->thr, sizeof(unsigned long long) * 8, "threshold table"},
@@ -1021,14 +1027,18 @@ hmc_status hmc_set_orientations(hmc_handle *h, const double *euler, const uint16
         HMC_CK(h, cudaMemcpy(h->ctab, c.data(), c.size() * sizeof(float), cudaMemcpyHostToDevice), "table upload");
         HMC_CK(h, cudaMemcpy(h->wtab, w.data(), w.size() * sizeof(float), cudaMemcpyHostToDevice), "table upload");
         HMC_CK(h, cudaMemcpy(h->atab, ax.data(), ax.size() * sizeof(float), cudaMemcpyHostToDevice), "table upload");
-        std::vector<float> cp((size_t)Q * 36);
+        // the FP32 MPM step's cubic form: Voigt weights (x^2, y^2, z^2, yz, xz, xy) of the crystal
+        // axes a_0 and a_1 (columns 0 and 1 of A) of every orientation
+        std::vector<float> cw((size_t)Q * 12);
         for (int q = 0; q < Q; ++q)
-            for (int k = 0; k < 3; ++k)
-                for (int j = 0; j < 6; ++j) {
-                    cp[(size_t)q * 36 + 12 * k + 2 * j] = (float)h->Cv[(size_t)q * 36 + 6 * (2 * k) + j];
-                    cp[(size_t)q * 36 + 12 * k + 2 * j + 1] = (float)h->Cv[(size_t)q * 36 + 6 * (2 * k + 1) + j];
-                }
-        HMC_CK(h, cudaMemcpy(h->ctab_pairs, cp.data(), cp.size() * sizeof(float), cudaMemcpyHostToDevice),
+            for (int m = 0; m < 2; ++m) {
+                const double *A = &h->A[(size_t)q * 9];
+                const double x = A[0 * 3 + m], y = A[1 * 3 + m], z = A[2 * 3 + m];
+                float *w = &cw[(size_t)q * 12 + 6 * m];
+                w[0] = (float)(x * x); w[1] = (float)(y * y); w[2] = (float)(z * z);
+                w[3] = (float)(y * z); w[4] = (float)(x * z); w[5] = (float)(x * y);
+            }
+        HMC_CK(h, cudaMemcpy(h->cubw, cw.data(), cw.size() * sizeof(float), cudaMemcpyHostToDevice),
                "table upload");
     } else {
         auto c = pack_ctab<double>(h->Cv, Q);

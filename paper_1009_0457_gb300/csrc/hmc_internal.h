@@ -16,6 +16,8 @@
 //   atab    T[Q][8]             the first two crystal axes a_0, a_1 in the sample
 //                               frame (columns of A), padded to 8 (the sweep's zone
 //                               energy)
+//   cubw    float[Q][12]        FP32 MPM step: the Voigt weights (x^2, y^2, z^2, yz,
+//                               xz, xy) of the first two crystal axes a_0, a_1
 #pragma once
 
 #include <cuda_runtime.h>
@@ -103,11 +105,15 @@ struct MpmArgs {
     const T *u_in;
     T *u_out;
     T *v;
-    const T *ctab;
-    const float *ctab_pairs; // FP32 stiffness rows as component pairs (paired-FMA variant)
+    const T *ctab;           // FP64 step: rotated stiffness rows
+    const float *cubw;       // FP32 step: Voigt weights of two crystal axes per orientation (12 each)
+    float cub[4];            // FP32 step: C12, 2 C44, C44 and C11 - C12 - 2 C44
+    int nq;                  // orientations (the FP32 step stages cubw in shared memory up to MPM_STAB_MAX)
     T dt, dt_over_m, keep;   // keep = 1 - damping
     int grid;                // persistent CTAs
 };
+
+constexpr int MPM_STAB_MAX = 1024;   // orientations whose FP32 table the MPM step holds in shared memory
 
 template <typename T>
 struct StressArgs {
@@ -190,7 +196,7 @@ void zone_element_tables(const double *Cv, int Q, std::vector<double> &out);
 cudaError_t mpm_prepare();  // opt the MPM kernels into their dynamic shared memory (once, before any capture)
 cudaError_t sweep_prepare();  // opt the elastic sweeps into their shared memory
 template <typename T>
-int mpm_per_sm(int variant);  // resident MPM CTAs per SM
+int mpm_per_sm(int variant, int nq);  // resident MPM CTAs per SM
 
 // One CTA per replica: fixed-order FP64 sum of its stress partials, loading
 // update (update_strain) and MCS counter (advance).

@@ -52,6 +52,12 @@ struct MpmSmem {
     };
 };
 
+// byte offset of the FP32 orientation table behind a CTA's tiles (16-byte aligned)
+template <int CX, int CY, typename T>
+__host__ __device__ constexpr size_t mpm_table_offset() {
+    return (sizeof(typename MpmSmem<CX, CY>::template S<T>) + 15) & ~size_t(15);
+}
+
 // Node plane k of the tile with origin (i0, j0) (one node of halo on each side),
 // read from global memory into registers / written to shared memory.
 template <typename T, int CX, int CY>
@@ -97,38 +103,88 @@ struct PlaneLoad {
     }
 };
 
-// Hooke's law for the MPM step.  FP64: the 21-entry symmetric row.  FP32: the
-// full 6x6 matrix stored as row pairs ((C0j,C1j), (C2j,C3j), (C4j,C5j)), so
-// that each pair of stress components is one chain of paired FMAs
-// (__ffma2_rn: two FP32 FMAs per instruction on sm_100 and later).
-template <typename T, bool PAIR>
+// Hooke's law for the MPM step.  FP64: the 21-entry symmetric row of C'(q).  FP32:
+// the cubic form of one rotated cubic material,
+//   sigma = (C12 tr + Ad p2) I + 2 C44 eps + Ad (p0 - p2) a0 a0 + Ad (p1 - p2) a1 a1,
+//   p_m = a_m.eps.a_m = W_m.e,  p2 = tr - p0 - p1,  Ad = C11 - C12 - 2 C44,
+// with e the Voigt strain (engineering shear), sigma in tensor shear and W_m the Voigt
+// weights (x^2, y^2, z^2, yz, xz, xy) of crystal axis a_m = (x, y, z); the third axis
+// drops out because the axes are orthonormal.  12 values per orientation instead of
+// 21, so the table of up to MPM_STAB_MAX orientations sits in shared memory (STAB) and
+// a cell whose points change orientation reloads from there.  Every operation is
+// explicitly rounded, in one order, in the scalar form and in the paired forms
+// (__ffma2_rn: two FP32 FMAs per instruction), which therefore give the same bits.
+__device__ __forceinline__ void cubic_hooke(const float (&w)[12], const float (&cub)[4], const float (&e)[6],
+                                            float (&s)[6]) {
+    float p0 = __fmul_rn(w[0], e[0]), p1 = __fmul_rn(w[6], e[0]);
+#pragma unroll
+    for (int k = 1; k < 6; ++k) {
+        p0 = __fmaf_rn(w[k], e[k], p0);
+        p1 = __fmaf_rn(w[6 + k], e[k], p1);
+    }
+    const float tr = __fadd_rn(__fadd_rn(e[0], e[1]), e[2]);
+    const float p2 = __fsub_rn(__fsub_rn(tr, p0), p1);
+    const float c = __fmaf_rn(cub[3], p2, __fmul_rn(cub[0], tr));
+    const float d0 = __fmul_rn(cub[3], __fsub_rn(p0, p2)), d1 = __fmul_rn(cub[3], __fsub_rn(p1, p2));
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const float base = k < 3 ? __fmaf_rn(cub[1], e[k], c) : __fmul_rn(cub[2], e[k]);
+        s[k] = __fmaf_rn(d1, w[6 + k], __fmaf_rn(d0, w[k], base));
+    }
+}
+
+// the same with the two axis products and the stress components formed in pairs
+__device__ __forceinline__ void cubic_hooke_paired(const float (&w)[12], const float (&cub)[4], const float (&e)[6],
+                                                   float (&s)[6]) {
+    float2 pp = __fmul2_rn(make_float2(w[0], w[6]), make_float2(e[0], e[0]));
+#pragma unroll
+    for (int k = 1; k < 6; ++k) pp = __ffma2_rn(make_float2(w[k], w[6 + k]), make_float2(e[k], e[k]), pp);
+    const float p0 = pp.x, p1 = pp.y;
+    const float tr = __fadd_rn(__fadd_rn(e[0], e[1]), e[2]);
+    const float p2 = __fsub_rn(__fsub_rn(tr, p0), p1);
+    const float c = __fmaf_rn(cub[3], p2, __fmul_rn(cub[0], tr));
+    const float d0 = __fmul_rn(cub[3], __fsub_rn(p0, p2)), d1 = __fmul_rn(cub[3], __fsub_rn(p1, p2));
+    const float2 D0 = make_float2(d0, d0), D1 = make_float2(d1, d1);
+    float2 base[3];
+    base[0] = __ffma2_rn(make_float2(cub[1], cub[1]), make_float2(e[0], e[1]), make_float2(c, c));
+    base[1] = make_float2(__fmaf_rn(cub[1], e[2], c), __fmul_rn(cub[2], e[3]));
+    base[2] = __fmul2_rn(make_float2(cub[2], cub[2]), make_float2(e[4], e[5]));
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const float2 t = __ffma2_rn(D0, make_float2(w[2 * j], w[2 * j + 1]), base[j]);
+        const float2 r = __ffma2_rn(D1, make_float2(w[6 + 2 * j], w[7 + 2 * j]), t);
+        s[2 * j] = r.x;
+        s[2 * j + 1] = r.y;
+    }
+}
+
+template <typename T, bool PAIR, bool STAB>
 struct HookeRow {
     Row24<T> r;
     __device__ __forceinline__ void load(const T *tab, const float *, uint32_t q) { r.load(tab + 24ll * q); }
-    __device__ __forceinline__ void apply(const T (&e)[6], T (&s)[6]) const { hooke21<T>(r.v, e, s); }
+    __device__ __forceinline__ void apply(const T (&e)[6], T (&s)[6], const float (&)[4]) const {
+        hooke21<T>(r.v, e, s);
+    }
 };
-template <>
-struct HookeRow<float, true> {
-    float2 p[3][6];   // p[k][j] = (C_{2k,j}, C_{2k+1,j})
-    __device__ __forceinline__ void load(const float *, const float *pairs, uint32_t q) {
-        const float4 *t = reinterpret_cast<const float4 *>(pairs + 36ll * q);
+template <bool PAIR, bool STAB>
+struct HookeRow<float, PAIR, STAB> {
+    float w[12];
+    // cw: the table in shared memory (STAB) or in global memory
+    __device__ __forceinline__ void load(const float *, const float *cw, uint32_t q) {
+        const float4 *p = reinterpret_cast<const float4 *>(cw + 12 * q);
+        float4 v[3];
 #pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            const float4 v = __ldg(t + i);
-            const int k = (2 * i) / 6, j = (2 * i) % 6;
-            p[k][j] = make_float2(v.x, v.y);
-            p[k][j + 1] = make_float2(v.z, v.w);
+        for (int i = 0; i < 3; ++i) v[i] = STAB ? p[i] : __ldg(p + i);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            w[4 * i] = v[i].x; w[4 * i + 1] = v[i].y; w[4 * i + 2] = v[i].z; w[4 * i + 3] = v[i].w;
         }
     }
-    __device__ __forceinline__ void apply(const float (&e)[6], float (&s)[6]) const {
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            float2 acc = __fmul2_rn(p[k][0], make_float2(e[0], e[0]));
-#pragma unroll
-            for (int j = 1; j < 6; ++j) acc = __ffma2_rn(p[k][j], make_float2(e[j], e[j]), acc);
-            s[2 * k] = acc.x;
-            s[2 * k + 1] = acc.y;
-        }
+    __device__ __forceinline__ void apply(const float (&e)[6], float (&s)[6], const float (&cub)[4]) const {
+        if (PAIR)
+            cubic_hooke_paired(w, cub, e, s);
+        else
+            cubic_hooke(w, cub, e, s);
     }
 };
 
@@ -184,14 +240,15 @@ __host__ __device__ constexpr int gray_point(int n) {
 // Eight points of one cell: F[corner] = (2I-1) X'[J][K] + (2J-1) Y'[I][K] +
 // (2K-1) Z'[I][J] with X', Y', Z' the 3/1-weighted sums of the traction
 // columns of sigma; the nodal force is -(V/h)/16 F = -F/32 (V = 1 voxel, h = 2).
-template <typename T, bool PAIR>
+template <typename T, bool PAIR, bool STAB>
 __device__ __forceinline__ void cell_forces(const T (&u)[8][3], const uint4 &sp, const T *__restrict__ ctab,
-                                            const float *__restrict__ cpairs, const T (&eb)[6], T (&f)[8][3]) {
+                                            const float *cw, const float (&cub)[4], const T (&eb)[6],
+                                            T (&f)[8][3]) {
     // the first point's stiffness row is requested before the gradients are formed, so that
     // its load latency overlaps them
-    HookeRow<T, PAIR> row;
+    HookeRow<T, PAIR, STAB> row;
     uint32_t qprev = spin_of(sp, local_slot(0));
-    row.load(ctab, cpairs, qprev);
+    row.load(ctab, cw, qprev);
     CellGrad<T> g;
     cell_gradients31<T>(u, g);
     // the normal strains of a point are eb_k plus one gradient entry that two points share:
@@ -225,10 +282,10 @@ __device__ __forceinline__ void cell_forces(const T (&u)[8][3], const uint4 &sp,
         // points of one cell mostly share one orientation: fetch the row only when it changes
         const uint32_t q = spin_of(sp, local_slot(L));
         if (q != qprev) {
-            row.load(ctab, cpairs, q);
+            row.load(ctab, cw, q);
             qprev = q;
         }
-        row.apply(e, s);
+        row.apply(e, s, cub);
         // columns of sigma: x = (s0,s5,s4), y = (s5,s1,s3), z = (s4,s3,s2)
         tx[b][c][0] += s[0]; tx[b][c][1] += s[5]; tx[b][c][2] += s[4];
         ty[a][c][0] += s[5]; ty[a][c][1] += s[1]; ty[a][c][2] += s[3];
@@ -254,7 +311,7 @@ __device__ __forceinline__ void cell_forces(const T (&u)[8][3], const uint4 &sp,
     }
 }
 
-template <typename T, int CX, int CY, bool PAIR>
+template <typename T, int CX, int CY, bool PAIR, bool STAB>
 __global__ void __launch_bounds__(CX *CY, (sizeof(T) == 4 ? 2 : 1)) k_mpm_step(MpmArgs<T> a) {
     constexpr int OX = CX - 1, OY = CY - 1;
     using Smem = typename MpmSmem<CX, CY>::template S<T>;
@@ -262,6 +319,18 @@ __global__ void __launch_bounds__(CX *CY, (sizeof(T) == 4 ? 2 : 1)) k_mpm_step(M
     Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
     const int tid = threadIdx.x;
     const T fscale = -a.dt_over_m * T(0.03125);          // -dt / (32 m)
+    // FP32: the orientation table of the cubic form, staged in shared memory behind the tiles
+    const float *cw = a.cubw;
+    if constexpr (STAB) {
+        float *ts = reinterpret_cast<float *>(smem_raw + mpm_table_offset<CX, CY, T>());
+        for (int i = tid; i < 3 * a.nq; i += CX * CY)
+            reinterpret_cast<float4 *>(ts)[i] = __ldg(reinterpret_cast<const float4 *>(a.cubw) + i);
+        __syncthreads();
+        cw = ts;
+    }
+    float cub[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) cub[i] = a.cub[i];
     // this CTA's contiguous range of the linear (replica, tile, plane) index
     long long w = a.total * blockIdx.x / gridDim.x;
     const long long wend = a.total * (blockIdx.x + 1) / gridDim.x;
@@ -325,7 +394,7 @@ __global__ void __launch_bounds__(CX *CY, (sizeof(T) == 4 ? 2 : 1)) k_mpm_step(M
 #pragma unroll
                             for (int d = 0; d < 3; ++d) u[corner(I, J, K)][d] = sm.us[K ? b1 : b0][d][lcj + J][lci + I];
                 T f[8][3];
-                cell_forces<T, PAIR>(u, sp, a.ctab, a.ctab_pairs, eb, f);
+                cell_forces<T, PAIR, STAB>(u, sp, a.ctab, cw, cub, eb, f);
 #pragma unroll
                 for (int J = 0; J < 2; ++J)
 #pragma unroll
@@ -397,30 +466,47 @@ __device__ __forceinline__ void interp31_2(float2 d00, float2 d10, float2 d01, f
     o[1][1] = p_fma(three, e11, e10);
 }
 
-__device__ __forceinline__ float2 hooke_row2(const float2 (&c)[21], int i0, int i1, int i2, int i3, int i4, int i5,
-                                             const float2 (&e)[6]) {
-    float2 s = p_mul(c[i0], e[0]);
-    s = p_fma(c[i1], e[1], s);
-    s = p_fma(c[i2], e[2], s);
-    s = p_fma(c[i3], e[3], s);
-    s = p_fma(c[i4], e[4], s);
-    return p_fma(c[i5], e[5], s);
+// The cubic form of Hooke's law (cubic_hooke) on two cells at once, every
+// operation one paired instruction with the scalar form's rounding.
+__device__ __forceinline__ void cubic_hooke2(const float2 (&w)[12], const float (&cub)[4], const float2 (&e)[6],
+                                             float2 (&s)[6]) {
+    float2 p0 = p_mul(w[0], e[0]), p1 = p_mul(w[6], e[0]);
+#pragma unroll
+    for (int k = 1; k < 6; ++k) {
+        p0 = p_fma(w[k], e[k], p0);
+        p1 = p_fma(w[6 + k], e[k], p1);
+    }
+    const float2 C12 = make_float2(cub[0], cub[0]), C44x2 = make_float2(cub[1], cub[1]);
+    const float2 C44 = make_float2(cub[2], cub[2]), Ad = make_float2(cub[3], cub[3]);
+    const float2 tr = p_add(p_add(e[0], e[1]), e[2]);
+    const float2 p2 = p_sub(p_sub(tr, p0), p1);
+    const float2 c = p_fma(Ad, p2, p_mul(C12, tr));
+    const float2 d0 = p_mul(Ad, p_sub(p0, p2)), d1 = p_mul(Ad, p_sub(p1, p2));
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const float2 base = k < 3 ? p_fma(C44x2, e[k], c) : p_mul(C44, e[k]);
+        s[k] = p_fma(d1, w[6 + k], p_fma(d0, w[k], base));
+    }
 }
 
-__device__ __forceinline__ void load_row_pair(const float *ctab, uint32_t qa, uint32_t qb, float2 (&c)[21]) {
-    Row24<float> ra, rb;
-    ra.load(ctab + 24ll * qa);
-    rb.load(ctab + 24ll * qb);
+__device__ __forceinline__ void load_w_pair(const float *cw, uint32_t qa, uint32_t qb, float2 (&w)[12]) {
+    const float4 *pa = reinterpret_cast<const float4 *>(cw + 12 * qa), *pb = reinterpret_cast<const float4 *>(cw + 12 * qb);
 #pragma unroll
-    for (int k = 0; k < 21; ++k) c[k] = make_float2(ra.v[k], rb.v[k]);
+    for (int i = 0; i < 3; ++i) {
+        const float4 x = __ldg(pa + i), y = __ldg(pb + i);
+        w[4 * i] = make_float2(x.x, y.x);
+        w[4 * i + 1] = make_float2(x.y, y.y);
+        w[4 * i + 2] = make_float2(x.z, y.z);
+        w[4 * i + 3] = make_float2(x.w, y.w);
+    }
 }
 
 __device__ __forceinline__ void cell_forces2(const float2 (&u)[8][3], const uint4 &spa, const uint4 &spb,
-                                             const float *__restrict__ ctab, const float2 (&eb)[6],
-                                             float2 (&f)[8][3]) {
-    float2 row[21];
+                                             const float *__restrict__ cw, const float (&cub)[4],
+                                             const float2 (&eb)[6], float2 (&f)[8][3]) {
+    float2 row[12];
     uint32_t qa = spin_of(spa, local_slot(0)), qb = spin_of(spb, local_slot(0));
-    load_row_pair(ctab, qa, qb, row);
+    load_w_pair(cw, qa, qb, row);
     float2 gx[2][2][3], gy[2][2][3], gz[2][2][3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
@@ -472,16 +558,11 @@ __device__ __forceinline__ void cell_forces2(const float2 (&u)[8][3], const uint
         e[5] = p_add(eb[5], p_add(gy[a][c][0], gx[b][c][1]));
         const uint32_t na = spin_of(spa, local_slot(L)), nb = spin_of(spb, local_slot(L));
         if (na != qa || nb != qb) {
-            load_row_pair(ctab, na, nb, row);
+            load_w_pair(cw, na, nb, row);
             qa = na;
             qb = nb;
         }
-        s[0] = hooke_row2(row, 0, 1, 2, 3, 4, 5, e);
-        s[1] = hooke_row2(row, 1, 6, 7, 8, 9, 10, e);
-        s[2] = hooke_row2(row, 2, 7, 11, 12, 13, 14, e);
-        s[3] = hooke_row2(row, 3, 8, 12, 15, 16, 17, e);
-        s[4] = hooke_row2(row, 4, 9, 13, 16, 18, 19, e);
-        s[5] = hooke_row2(row, 5, 10, 14, 17, 19, 20, e);
+        cubic_hooke2(row, cub, e, s);
         tx[b][c][0] = p_add(tx[b][c][0], s[0]); tx[b][c][1] = p_add(tx[b][c][1], s[5]); tx[b][c][2] = p_add(tx[b][c][2], s[4]);
         ty[a][c][0] = p_add(ty[a][c][0], s[5]); ty[a][c][1] = p_add(ty[a][c][1], s[1]); ty[a][c][2] = p_add(ty[a][c][2], s[3]);
         tz[a][b][0] = p_add(tz[a][b][0], s[4]); tz[a][b][1] = p_add(tz[a][b][1], s[3]); tz[a][b][2] = p_add(tz[a][b][2], s[2]);
@@ -632,7 +713,7 @@ __global__ void __launch_bounds__(128, 2) k_mpm_step2(MpmArgs<float> a) {
 #pragma unroll
                             for (int d = 0; d < 3; ++d) u[corner(I, J, K)][d] = sm.us[K ? b1 : b0][d][ty + J][tx + I];
                 float2 f[8][3];
-                cell_forces2(u, spa, spb, a.ctab, eb, f);
+                cell_forces2(u, spa, spb, a.cubw, a.cub, eb, f);
 #pragma unroll
                 for (int J = 0; J < 2; ++J)
 #pragma unroll
@@ -686,8 +767,9 @@ __global__ void __launch_bounds__(128, 2) k_mpm_step2(MpmArgs<float> a) {
 }
 
 template <typename T, int CX, int CY>
-size_t smem_of() {
-    return sizeof(typename MpmSmem<CX, CY>::template S<T>);
+size_t smem_of(bool stab, int nq) {
+    return stab ? mpm_table_offset<CX, CY, T>() + sizeof(float) * 12 * (size_t)nq
+                : sizeof(typename MpmSmem<CX, CY>::template S<T>);
 }
 
 }  // namespace
@@ -695,10 +777,18 @@ size_t smem_of() {
 int mpm_shape_cx(int shape) { return shape == MPM_32x8 ? 32 : shape == MPM_8x32 ? 8 : 16; }
 int mpm_shape_cy(int shape) { return shape == MPM_32x8 ? 8 : shape == MPM_8x32 ? 32 : 16; }
 
-template <typename T, int CX, int CY, bool PAIR>
+template <typename T, int CX, int CY, bool PAIR, bool STAB>
 static cudaError_t set_attr() {
-    return cudaFuncSetAttribute(k_mpm_step<T, CX, CY, PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem_of<T, CX, CY>());
+    return cudaFuncSetAttribute(k_mpm_step<T, CX, CY, PAIR, STAB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem_of<T, CX, CY>(STAB, MPM_STAB_MAX));
+}
+
+template <bool PAIR, bool STAB>
+static cudaError_t set_attr_f32() {
+    cudaError_t e;
+    if ((e = set_attr<float, 16, 16, PAIR, STAB>()) != cudaSuccess) return e;
+    if ((e = set_attr<float, 32, 8, PAIR, STAB>()) != cudaSuccess) return e;
+    return set_attr<float, 8, 32, PAIR, STAB>();
 }
 
 cudaError_t mpm_prepare() {
@@ -706,70 +796,82 @@ cudaError_t mpm_prepare() {
     if ((e = cudaFuncSetAttribute(k_mpm_step2, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)sizeof(MpmSmem2))) != cudaSuccess)
         return e;
-    if ((e = set_attr<float, 16, 16, false>()) != cudaSuccess || (e = set_attr<float, 32, 8, false>()) != cudaSuccess ||
-        (e = set_attr<float, 8, 32, false>()) != cudaSuccess || (e = set_attr<float, 16, 16, true>()) != cudaSuccess ||
-        (e = set_attr<float, 32, 8, true>()) != cudaSuccess || (e = set_attr<float, 8, 32, true>()) != cudaSuccess ||
-        (e = set_attr<double, 16, 16, false>()) != cudaSuccess ||
-        (e = set_attr<double, 32, 8, false>()) != cudaSuccess || (e = set_attr<double, 8, 32, false>()) != cudaSuccess)
+    if ((e = set_attr_f32<false, false>()) != cudaSuccess || (e = set_attr_f32<false, true>()) != cudaSuccess ||
+        (e = set_attr_f32<true, false>()) != cudaSuccess || (e = set_attr_f32<true, true>()) != cudaSuccess ||
+        (e = set_attr<double, 16, 16, false, false>()) != cudaSuccess ||
+        (e = set_attr<double, 32, 8, false, false>()) != cudaSuccess ||
+        (e = set_attr<double, 8, 32, false, false>()) != cudaSuccess)
         return e;
     return cudaSuccess;
 }
 
-template <typename T, bool PAIR>
-static int per_sm_t(int shape) {
+template <typename T, bool PAIR, bool STAB>
+static int per_sm_t(int shape, int nq) {
     int n = 1;
     cudaError_t e;
     if (shape == MPM_32x8)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_mpm_step<T, 32, 8, PAIR>, 256, smem_of<T, 32, 8>());
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_mpm_step<T, 32, 8, PAIR, STAB>, 256,
+                                                          smem_of<T, 32, 8>(STAB, nq));
     else if (shape == MPM_8x32)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_mpm_step<T, 8, 32, PAIR>, 256, smem_of<T, 8, 32>());
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_mpm_step<T, 8, 32, PAIR, STAB>, 256,
+                                                          smem_of<T, 8, 32>(STAB, nq));
     else
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_mpm_step<T, 16, 16, PAIR>, 256, smem_of<T, 16, 16>());
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_mpm_step<T, 16, 16, PAIR, STAB>, 256,
+                                                          smem_of<T, 16, 16>(STAB, nq));
     return (e != cudaSuccess || n < 1) ? 1 : n;
 }
 
 template <>
-int mpm_per_sm<float>(int shape) {
+int mpm_per_sm<float>(int shape, int nq) {
     if (shape == MPM_TWO_CELL) {
         int n = 1;
         const cudaError_t e =
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_mpm_step2, 128, sizeof(MpmSmem2));
         return (e != cudaSuccess || n < 1) ? 1 : n;
     }
-    return per_sm_t<float, false>(shape % MPM_NSHAPES) < per_sm_t<float, true>(shape % MPM_NSHAPES)
-               ? per_sm_t<float, false>(shape % MPM_NSHAPES)
-               : per_sm_t<float, true>(shape % MPM_NSHAPES);
+    const int sh = shape % MPM_NSHAPES;
+    int a, b;
+    if (nq <= MPM_STAB_MAX) {
+        a = per_sm_t<float, false, true>(sh, nq);
+        b = per_sm_t<float, true, true>(sh, nq);
+    } else {
+        a = per_sm_t<float, false, false>(sh, nq);
+        b = per_sm_t<float, true, false>(sh, nq);
+    }
+    return a < b ? a : b;
 }
 template <>
-int mpm_per_sm<double>(int shape) {
-    return per_sm_t<double, false>(shape % MPM_NSHAPES);
+int mpm_per_sm<double>(int shape, int nq) {
+    return per_sm_t<double, false, false>(shape % MPM_NSHAPES, nq);
 }
 
-template <typename T, bool PAIR>
+template <typename T, bool PAIR, bool STAB>
 static void launch_t(const MpmArgs<T> &a, int shape, cudaStream_t s) {
     if (shape == MPM_32x8)
-        k_mpm_step<T, 32, 8, PAIR><<<a.grid, 256, smem_of<T, 32, 8>(), s>>>(a);
+        k_mpm_step<T, 32, 8, PAIR, STAB><<<a.grid, 256, smem_of<T, 32, 8>(STAB, a.nq), s>>>(a);
     else if (shape == MPM_8x32)
-        k_mpm_step<T, 8, 32, PAIR><<<a.grid, 256, smem_of<T, 8, 32>(), s>>>(a);
+        k_mpm_step<T, 8, 32, PAIR, STAB><<<a.grid, 256, smem_of<T, 8, 32>(STAB, a.nq), s>>>(a);
     else
-        k_mpm_step<T, 16, 16, PAIR><<<a.grid, 256, smem_of<T, 16, 16>(), s>>>(a);
+        k_mpm_step<T, 16, 16, PAIR, STAB><<<a.grid, 256, smem_of<T, 16, 16>(STAB, a.nq), s>>>(a);
 }
 
 // shape in 0..2: scalar Hooke; shape + MPM_NSHAPES: paired-FMA Hooke (FP32 only);
-// MPM_TWO_CELL: two cells per thread (FP32 only)
+// MPM_TWO_CELL: two cells per thread (FP32 only).  FP32 steps of up to MPM_STAB_MAX
+// orientations hold the orientation table in shared memory.
 template <>
 cudaError_t launch_mpm_step<float>(const MpmArgs<float> &a, int shape, cudaStream_t s) {
+    const bool stab = a.nq <= MPM_STAB_MAX;
     if (shape == MPM_TWO_CELL)
         k_mpm_step2<<<a.grid, 128, sizeof(MpmSmem2), s>>>(a);
     else if (shape >= MPM_NSHAPES)
-        launch_t<float, true>(a, shape - MPM_NSHAPES, s);
+        stab ? launch_t<float, true, true>(a, shape - MPM_NSHAPES, s) : launch_t<float, true, false>(a, shape - MPM_NSHAPES, s);
     else
-        launch_t<float, false>(a, shape, s);
+        stab ? launch_t<float, false, true>(a, shape, s) : launch_t<float, false, false>(a, shape, s);
     return cudaGetLastError();
 }
 template <>
 cudaError_t launch_mpm_step<double>(const MpmArgs<double> &a, int shape, cudaStream_t s) {
-    launch_t<double, false>(a, shape % MPM_NSHAPES, s);
+    launch_t<double, false, false>(a, shape % MPM_NSHAPES, s);
     return cudaGetLastError();
 }
 
