@@ -42,10 +42,10 @@ sys.path.insert(0, ROOT)
 
 # FP32 peak of the ALU roofline: 152 SMs x 128 FP32 lanes x 2 flop per FMA x clock
 GB300_SMS, FP32_LANES = 152, 128
-# algorithmic flops of one point in one fused MPM step, separable trilinear form
-# (corner differences, gradient interpolation, strain, 6x6 Hooke, traction sums,
-# force interpolation, corner assembly, node update), FMA = 2 flop
-MPM_FLOP_PER_POINT = 138
+# algorithmic flops of one point in one fused FP32 MPM step, separable trilinear form
+# (corner differences, gradient interpolation, strain, Hooke's law in the cubic form
+# (66 flop), traction sums, force interpolation, corner assembly, node update), FMA = 2 flop
+MPM_FLOP_PER_POINT = 132
 MPM_BYTES_PER_POINT = {"f32": 8, "f64": 14}      # spin 2 + (u,v) read + (u,v) write, per point
 SWEEP_BYTES_PER_SITE = {"f32": 28, "f64": 52}    # spin read + write + stored stress read
 STRESS_BYTES_PER_SITE = {"f32": 27.5, "f64": 53}  # spin 2 + u read (per point) + stress write

@@ -100,6 +100,25 @@ def test_mpm_parity(G, precision, steps, tol):
     assert abs(W_g - o.W) < tol * abs(o.W)
 
 
+@pytest.mark.parametrize("Q", [1024, 1100])
+def test_mpm_parity_large_orientation_sets(G, Q):
+    """The FP32 step holds the orientation table of its cubic form in shared memory up to
+    1024 orientations and reads it from global memory beyond: both paths against the
+    FP64 oracle after 200 steps, with orientation indices drawn over the whole table."""
+    shape = (10, 18, 34)
+    E6 = [-4e-4, -3e-4, 1e-3, 1e-4, -2e-4, 5e-5]
+    g, o = make_pair(G, shape, Q, 1, bc=1, strain6=E6, n_mpm=0, n_seeds=40, seed=13)
+    assert int(o.spins.max()) > 700
+    rng = np.random.default_rng(6)
+    u, v = _random_state(o, rng)
+    g.set_nodal(u, v)
+    o.u, o.v = u.copy(), v.copy()
+    g.mpm_steps(200)
+    o.mpm_steps(200)
+    ug, vg = g.nodal()
+    assert rel(ug, o.u) < 1e-4 and rel(vg, o.v) < 1e-4
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_stress_parity_ragged_tiles(G, precision):
     shape = (6, 34, 66)  # 17 x 33 cells in y, x: partial 16x16 tiles
