@@ -1587,11 +1587,6 @@ cudaError_t mpm_custom(hmc_handle *h, const void *uin, void *uout, void *v, cons
     return hmc::launch_mpm_step<T>(a, h->mpm_shape, h->stream);
 }
 
-cudaError_t mpm_custom_any(hmc_handle *h, const void *uin, void *uout, void *v, const hmc::Replica *reps,
-                           double keep) {
-    return h->p.precision == HMC_FP32 ? mpm_custom<float>(h, uin, uout, v, reps, keep)
-                                      : mpm_custom<double>(h, uin, uout, v, reps, keep);
-}
 
 template <typename T>
 hmc::AdjArgs<T> adj_args(hmc_handle *h) {
