@@ -35,20 +35,22 @@ namespace hmc {
 
 namespace {
 
-// Row stride of the node tiles in shared memory: a warp covers 32 / CX rows of
-// the patch, and the stride puts those rows in disjoint banks (16 wide: 48,
-// 8 wide: 40, 32 wide: 33).
-__host__ __device__ constexpr int node_stride(int cx) { return cx == 16 ? 48 : cx == 8 ? 40 : cx + 1; }
+// A node's or a cell corner's three components and a pad: one 16-byte shared-memory access
+// in FP32 (eight consecutive lanes read 128 contiguous bytes, free of bank conflicts)
+// instead of three 4-byte ones.
+template <typename T>
+struct alignas(16) Vec4 {
+    T x, y, z, p;
+};
 
 template <int CX, int CY>
 struct MpmSmem {
     static constexpr int NX = CX + 1, NY = CY + 1;   // node tile (one node of halo each side)
-    static constexpr int NXP = node_stride(CX);
     template <typename T>
     struct S {
-        T us[3][3][NY][NXP];  // node planes (buffer, component, j, i), held as u/32
-        T fb[4][3][CY][CX];   // cell contributions to their lower corner nodes (corner I+2J, component)
-        T ft[4][3][CY][CX];   // ... to their upper corner nodes
+        Vec4<T> us[3][NY][NX];  // node planes (buffer, j, i), held as u/32
+        Vec4<T> fb[4][CY][CX];  // cell contributions to their lower corner nodes (corner I+2J)
+        Vec4<T> ft[4][CY][CX];  // ... to their upper corner nodes
     };
 };
 
@@ -90,15 +92,12 @@ struct PlaneLoad {
             }
         }
     }
-    __device__ __forceinline__ void store(T (&us)[3][NY][node_stride(CX)]) const {
+    __device__ __forceinline__ void store(Vec4<T> (&us)[NY][NX]) const {
 #pragma unroll
         for (int m = 0; m < PER; ++m) {
             const int t = threadIdx.x + m * NTHR;
-            if (t < NN) {
-                const int li = t % NX, lj = t / NX;
-#pragma unroll
-                for (int d = 0; d < 3; ++d) us[d][lj][li] = r[m][d] * T(0.03125);
-            }
+            if (t < NN)
+                us[t / NX][t % NX] = Vec4<T>{r[m][0] * T(0.03125), r[m][1] * T(0.03125), r[m][2] * T(0.03125), T(0)};
         }
     }
 };
@@ -390,39 +389,46 @@ __global__ void __launch_bounds__(CX *CY, (sizeof(T) == 4 ? 2 : 1)) k_mpm_step(M
 #pragma unroll
                     for (int J = 0; J < 2; ++J)
 #pragma unroll
-                        for (int I = 0; I < 2; ++I)
-#pragma unroll
-                            for (int d = 0; d < 3; ++d) u[corner(I, J, K)][d] = sm.us[K ? b1 : b0][d][lcj + J][lci + I];
+                        for (int I = 0; I < 2; ++I) {
+                            const Vec4<T> n = sm.us[K ? b1 : b0][lcj + J][lci + I];
+                            u[corner(I, J, K)][0] = n.x;
+                            u[corner(I, J, K)][1] = n.y;
+                            u[corner(I, J, K)][2] = n.z;
+                        }
                 T f[8][3];
                 cell_forces<T, PAIR, STAB>(u, sp, a.ctab, cw, cub, eb, f);
 #pragma unroll
                 for (int J = 0; J < 2; ++J)
 #pragma unroll
-                    for (int I = 0; I < 2; ++I)
-#pragma unroll
-                        for (int d = 0; d < 3; ++d) {
-                            sm.fb[I + 2 * J][d][lcj][lci] = f[corner(I, J, 0)][d];
-                            sm.ft[I + 2 * J][d][lcj][lci] = f[corner(I, J, 1)][d];
-                        }
+                    for (int I = 0; I < 2; ++I) {
+                        const T *fl = f[corner(I, J, 0)], *fu = f[corner(I, J, 1)];
+                        sm.fb[I + 2 * J][lcj][lci] = Vec4<T>{fl[0], fl[1], fl[2], T(0)};
+                        sm.ft[I + 2 * J][lcj][lci] = Vec4<T>{fu[0], fu[1], fu[2], T(0)};
+                    }
             }
             if (more) pl.store(sm.us[b2]);   // buffer b2 was last read before the previous barrier
             __syncthreads();
             if (own) {
                 // cells (lci-1, lcj-1), (lci, lcj-1), (lci-1, lcj), (lci, lcj) see this node as corner 3, 2, 1, 0
                 if (kk >= k0) {
+                    const Vec4<T> c3 = sm.fb[3][lcj - 1][lci - 1], c2 = sm.fb[2][lcj - 1][lci];
+                    const Vec4<T> c1 = sm.fb[1][lcj][lci - 1], c0 = sm.fb[0][lcj][lci];
+                    const Vec4<T> un = sm.us[b0][lcj][lci];
+                    const T F[3] = {acc[0] + c3.x + c2.x + c1.x + c0.x, acc[1] + c3.y + c2.y + c1.y + c0.y,
+                                    acc[2] + c3.z + c2.z + c1.z + c0.z};
+                    const T uc[3] = {un.x, un.y, un.z};
 #pragma unroll
                     for (int d = 0; d < 3; ++d) {
-                        const T F = acc[d] + sm.fb[3][d][lcj - 1][lci - 1] + sm.fb[2][d][lcj - 1][lci] +
-                                    sm.fb[1][d][lcj][lci - 1] + sm.fb[0][d][lcj][lci];
-                        const T vn = rfma(fscale, F, rmul(a.keep, vold[d]));
+                        const T vn = rfma(fscale, F[d], rmul(a.keep, vold[d]));
                         a.v[nidx + d] = vn;
-                        a.u_out[nidx + d] = rfma(a.dt, vn, sm.us[b0][d][lcj][lci] * T(32));
+                        a.u_out[nidx + d] = rfma(a.dt, vn, uc[d] * T(32));
                     }
                 }
-#pragma unroll
-                for (int d = 0; d < 3; ++d)
-                    acc[d] = sm.ft[3][d][lcj - 1][lci - 1] + sm.ft[2][d][lcj - 1][lci] + sm.ft[1][d][lcj][lci - 1] +
-                             sm.ft[0][d][lcj][lci];
+                const Vec4<T> c3 = sm.ft[3][lcj - 1][lci - 1], c2 = sm.ft[2][lcj - 1][lci];
+                const Vec4<T> c1 = sm.ft[1][lcj][lci - 1], c0 = sm.ft[0][lcj][lci];
+                acc[0] = c3.x + c2.x + c1.x + c0.x;
+                acc[1] = c3.y + c2.y + c1.y + c0.y;
+                acc[2] = c3.z + c2.z + c1.z + c0.z;
             }
             __syncthreads();
             const int t = b0;
