@@ -11,6 +11,8 @@
 // 96 B of stress (FP32), and writes the colour's 8 B quad when a site changed.
 // Same-colour sites share no neighbour, so the in-place update is race free.
 // The colour's four sites of a block share one Philox4x32-10 block (a word each).
+// The bond counts compare the six neighbours as three pairs of 16-bit halves with
+// per-half SIMD minima: six minima in place of twelve compares, the same integers.
 //
 // Five CTAs per SM (FP32).  With the stored stress, thread 0 starts a bulk
 // asynchronous copy of the tile's stress of the colour into shared memory
@@ -154,6 +156,16 @@ __device__ __forceinline__ void block_draws(const Replica &R, int trial, int bx,
 // bond-count change dE = (like bonds lost) - (like bonds gained), zero when the
 // proposal keeps the orientation.  O is the block's own quad of the other colour,
 // N its -x, +x, -y, +y, -z, +z neighbours' quads of the other colour.
+// halves ia of a and ib of b (16-bit orientations of uint2 quads) as one 32-bit pair
+__device__ __forceinline__ uint32_t quad_pair(const uint2 &a, int ia, const uint2 &b, int ib) {
+    const uint32_t wa = ia < 2 ? a.x : a.y, wb = ib < 2 ? b.x : b.y;
+    const uint32_t sel = ((ia & 1) ? 0x32u : 0x10u) | ((ib & 1) ? 0x7600u : 0x5400u);
+    return __byte_perm(wa, wb, sel);
+}
+
+// number of halves of x that are not zero, per half (0 or 1 each)
+__device__ __forceinline__ uint32_t nonzero2(uint32_t x) { return __vminu2(x, 0x00010001u); }
+
 template <int COL>
 __device__ __forceinline__ void block_trials(int trial, int nq, const uint2 &mine, const uint2 &O,
                                              const uint2 (&N)[6], const uint2 (&rnd)[4], uint16_t (&q)[4],
@@ -162,30 +174,28 @@ __device__ __forceinline__ void block_trials(int trial, int nq, const uint2 &min
     for (int i = 0; i < 4; ++i) {
         const int L = slot_local(4 * COL + i);
         const int lx = L & 1, ly = (L >> 1) & 1, lz = L >> 2;
-        uint16_t nb[6];
-        nb[0] = quad_get(lx ? O : N[0], i);
-        nb[1] = quad_get(lx ? N[1] : O, i);
-        nb[2] = quad_get(ly ? O : N[2], i ^ 1);
-        nb[3] = quad_get(ly ? N[3] : O, i ^ 1);
-        nb[4] = quad_get(lz ? O : N[4], i ^ 2);
-        nb[5] = quad_get(lz ? N[5] : O, i ^ 2);
-        const uint16_t qo = quad_get(mine, i);
-        uint16_t qnew;
+        // the six neighbours -x, +x, -y, +y, -z, +z as three pairs of 16-bit halves
+        const uint32_t P0 = quad_pair(lx ? O : N[0], i, lx ? N[1] : O, i);
+        const uint32_t P1 = quad_pair(ly ? O : N[2], i ^ 1, ly ? N[3] : O, i ^ 1);
+        const uint32_t P2 = quad_pair(lz ? O : N[4], i ^ 2, lz ? N[5] : O, i ^ 2);
+        const uint32_t qo = quad_get(mine, i);
+        uint32_t qnew;
         if (trial == 0) {
-            const uint32_t k = __umulhi(rnd[i].x, 6u);
-            qnew = nb[0];
-#pragma unroll
-            for (int j = 1; j < 6; ++j)
-                if (k == (uint32_t)j) qnew = nb[j];
+            const uint32_t k = __umulhi(rnd[i].x, 6u);   // neighbour k: pair k / 2, half k % 2
+            const uint32_t w = k < 2 ? P0 : k < 4 ? P1 : P2;
+            qnew = (k & 1) ? w >> 16 : w & 0xffffu;
         } else {
-            qnew = (uint16_t)__umulhi(rnd[i].x, (uint32_t)nq);
+            qnew = __umulhi(rnd[i].x, (uint32_t)nq);
         }
-        int d = 0;
-#pragma unroll
-        for (int j = 0; j < 6; ++j) d += (int)(nb[j] == qo) - (int)(nb[j] == qnew);
-        q[i] = qo;
-        qn[i] = qnew;
-        dE[i] = d;
+        // dE = (neighbours equal to q) - (neighbours equal to q_new) = (halves differing from
+        // q_new) - (halves differing from q), counted per half (at most 3 each) and then summed
+        const uint32_t Qo = qo * 0x00010001u, Qn = qnew * 0x00010001u;
+        const uint32_t So = nonzero2(P0 ^ Qo) + nonzero2(P1 ^ Qo) + nonzero2(P2 ^ Qo);
+        const uint32_t Sn = nonzero2(P0 ^ Qn) + nonzero2(P1 ^ Qn) + nonzero2(P2 ^ Qn);
+        const uint32_t U = Sn + 0x00030003u - So;   // per half in 0..6: no borrow between halves
+        q[i] = (uint16_t)qo;
+        qn[i] = (uint16_t)qnew;
+        dE[i] = (int)((U * 0x00010001u) >> 16) - 6;
     }
 }
 
@@ -334,11 +344,14 @@ __global__ void __launch_bounds__(SWEEP_CTA, flat_min_ctas<T, MODE, RECOMP>())
     extern __shared__ __align__(128) unsigned char sweep_smem[];
     FlatSmem<T, STORED> &fs = *reinterpret_cast<FlatSmem<T, STORED> *>(sweep_smem);
     auto &sl = fs.list;
-    const int tile = blockIdx.x / SPLIT;
+    // the red half sweep follows the stress pass: its CTAs take the tiles in reverse order, so
+    // that the first to run read the stress the pass wrote last, still in L2
+    const int bid = COL == 0 ? (int)gridDim.x - 1 - (int)blockIdx.x : (int)blockIdx.x;
+    const int tile = bid / SPLIT;
     const int r = ONE ? 0 : __ldg(a.cta_rep + tile);
     const Replica &R = ONE ? a.rep0 : a.reps[r];
     const int tid = threadIdx.x, lane = tid & 31;
-    const int t0 = (tile - R.cta_off) * BLOCK_THREADS + (blockIdx.x % SPLIT) * SWEEP_CTA;
+    const int t0 = (tile - R.cta_off) * BLOCK_THREADS + (bid % SPLIT) * SWEEP_CTA;
     if (t0 >= R.nblk) return;  // the empty part of a replica's last tile
     const int blk = t0 + tid;  // block within the replica
     if (ELASTIC) {
