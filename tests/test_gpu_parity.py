@@ -53,6 +53,19 @@ def test_pure_potts_bit_exact(G, shape, trial):
     assert g.info().mcs == 4
 
 
+@pytest.mark.parametrize("trial", [0, 1])
+def test_pure_potts_bit_exact_16bit_orientations(G, trial):
+    """Orientation indices over the whole 16-bit range (Q = 65535, grains on both sides of
+    32768): the bond counts compare orientations as 16-bit halves of packed pairs, so no
+    high bit may leak between halves."""
+    shape = (8, 12, 34)
+    g, o = make_pair(G, shape, 65535, G.HMC_FP32, elastic=0, trial=trial, n_mpm=0, n_seeds=16)
+    assert (o.spins >= 32768).any() and (o.spins < 32768).any()
+    for m in range(3):
+        assert g.mc_sweeps(1) == o.mc_sweeps(1)
+        assert (g.spins() == o.spins).all(), f"MCS {m}"
+
+
 def test_defaults_agree_with_oracle(G):
     g = G.HMC((32, 32, 32), 4)
     i = g.info()
