@@ -366,7 +366,7 @@ cudaError_t enqueue_mcs(hmc_handle *h, cudaStream_t s) {
     if ((e = enq_stress(h, sweeps_read_stress(h), s)) != cudaSuccess) return e;
     if ((e = enq_sweep(h, 0, s)) != cudaSuccess) return e;
     if ((e = enq_sweep(h, 1, s)) != cudaSuccess) return e;
-    return hmc::launch_end_mcs(h->d_reps, h->R, h->partials, 1, 1, s);
+    return hmc::launch_end_mcs(h->d_reps, h->R, h->partials, h->nctas, 1, 1, s);
 }
 
 cudaError_t reset_accepted(hmc_handle *h) {
@@ -838,7 +838,7 @@ hmc_status hmc_create_batch(const hmc_params *params, int32_t n_replicas, hmc_ha
         {&h->atab, h->tsize * 8 * (size_t)p->n_orient, "axis table"},
         {(void **)&h->thr, sizeof(unsigned long long) * 8, "threshold table"},
         {(void **)&h->counts, sizeof(unsigned long long) * (size_t)p->n_orient, "orientation counts"},
-        {(void **)&h->partials, sizeof(double) * 7 * (size_t)h->nctas, "partials"},
+        {(void **)&h->partials, sizeof(double) * (7 * (size_t)h->nctas + hmc::end_scratch_doubles(h->R)), "partials"},
         {(void **)&h->st, sizeof(DevState) * (size_t)h->R, "device state"},
         {(void **)&h->d_reps, sizeof(hmc::Replica) * (size_t)h->R, "replica table"},
         {(void **)&h->d_cta_rep, sizeof(int) * (size_t)h->nctas, "CTA table"},
@@ -897,6 +897,10 @@ hmc_status hmc_create_batch(const hmc_params *params, int32_t n_replicas, hmc_ha
     void *zero_ptrs[] = {h->u[0], h->u[1], h->v};
     for (void *z : zero_ptrs)
         if ((e = cudaMemset(z, 0, nodes_b)) != cudaSuccess) return bail(cuda_fail(h, e, "memset"));
+    // the end-of-step reduction's arrival counters start at zero
+    if ((e = cudaMemset(h->partials, 0, sizeof(double) * (7 * (size_t)h->nctas + hmc::end_scratch_doubles(h->R)))) !=
+        cudaSuccess)
+        return bail(cuda_fail(h, e, "memset"));
     if (p->elastic == HMC_ELASTIC_STRAIN &&
         (e = cudaMalloc(&h->stab, h->tsize * 24 * (size_t)p->n_orient)) != cudaSuccess)
         return bail(cuda_fail(h, e, "compliance table"));
@@ -1180,7 +1184,7 @@ hmc_status hmc_compute_stress(hmc_handle *h, double *mean, double *energy) {
         ++h->state_version;
     }
     HMC_CK(h, enq_stress(h, true, h->stream), "stress launch");
-    HMC_CK(h, hmc::launch_end_mcs(h->d_reps, h->R, h->partials, 0, 0, h->stream), "reduction launch");
+    HMC_CK(h, hmc::launch_end_mcs(h->d_reps, h->R, h->partials, h->nctas, 0, 0, h->stream), "reduction launch");
     if (mean || energy) return read_stats(h, mean, energy);
     return HMC_OK;
 }
@@ -1212,7 +1216,7 @@ hmc_status hmc_end_mcs(hmc_handle *h) {
     if (h) ++h->state_version;
     hmc_status s = need_oriented(h);
     if (s != HMC_OK) return s;
-    HMC_CK(h, hmc::launch_end_mcs(h->d_reps, h->R, h->partials, 1, 1, h->stream), "end-of-step launch");
+    HMC_CK(h, hmc::launch_end_mcs(h->d_reps, h->R, h->partials, h->nctas, 1, 1, h->stream), "end-of-step launch");
     return HMC_OK;
 }
 

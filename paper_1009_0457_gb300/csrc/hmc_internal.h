@@ -200,7 +200,13 @@ int mpm_per_sm(int variant, int nq);  // resident MPM CTAs per SM
 
 // One CTA per replica: fixed-order FP64 sum of its stress partials, loading
 // update (update_strain) and MCS counter (advance).
-cudaError_t launch_end_mcs(const Replica *reps, int nrep, const double *partials, int update_strain, int advance,
+// End-of-step reduction: END_GROUPS CTAs per replica sum the stress partials in a fixed
+// order in FP64; the last to finish sums their group sums in group order and finishes the
+// step.  Its scratch lies behind the nctas x 7 stress partials: END_GROUPS x 7 group sums
+// per replica, then one arrival counter per replica (zero between launches).
+constexpr int END_GROUPS = 32;
+inline size_t end_scratch_doubles(int nrep) { return (size_t)nrep * END_GROUPS * 7 + (size_t)(nrep + 1) / 2; }
+cudaError_t launch_end_mcs(const Replica *reps, int nrep, double *partials, int nctas, int update_strain, int advance,
                            cudaStream_t s);
 cudaError_t launch_check_spins(const uint16_t *nat, long long n, int nq, DevState *st, cudaStream_t s);
 cudaError_t launch_pack_spins(const uint16_t *nat, uint4 *blk, int nx, int ny, int nz, cudaStream_t s);

@@ -171,15 +171,24 @@ __global__ void __launch_bounds__(STRESS_THREADS) k_stress(StressArgs<T> a) {
     }
 }
 
-// One CTA per replica: fixed-order FP64 reduction of its stress partials,
+// End of a step: fixed-order FP64 reduction of each replica's stress partials,
 // uniaxial control update of its mean strain, and its Monte Carlo step counter.
-__global__ void __launch_bounds__(256) k_end_mcs(const Replica *reps, const double *partials, int update_strain,
+// GB300 retires few FP64 operations per SM, so the partials (one set of seven per
+// stress CTA) are summed by END_GROUPS CTAs per replica: group g takes the CTAs
+// g, g + END_GROUPS, ... (each thread in that order, then a tree over the threads),
+// and the last group to arrive sums the group sums in group order and finishes.
+__global__ void __launch_bounds__(256) k_end_mcs(const Replica *reps, double *partials, int nctas, int update_strain,
                                                   int advance) {
     __shared__ double red[256][7];
-    const Replica &R = reps[blockIdx.x];
+    __shared__ int last;
+    const int r = blockIdx.x / END_GROUPS, grp = blockIdx.x % END_GROUPS;
+    const Replica &R = reps[r];
     DevState *st = R.st;
+    double *gsum = partials + 7ll * nctas + 7ll * END_GROUPS * r;   // this replica's group sums
+    // the arrival counters follow the group sums of all replicas (gridDim.x = replicas x END_GROUPS)
+    unsigned *arrive = reinterpret_cast<unsigned *>(partials + 7ll * nctas + 7ll * gridDim.x) + r;
     double s[7] = {0, 0, 0, 0, 0, 0, 0};
-    for (int p = threadIdx.x; p < R.ncta; p += 256)
+    for (int p = grp + END_GROUPS * threadIdx.x; p < R.ncta; p += END_GROUPS * 256)
         for (int i = 0; i < 7; ++i) s[i] += partials[7ll * (R.cta_off + p) + i];
     for (int i = 0; i < 7; ++i) red[threadIdx.x][i] = s[i];
     __syncthreads();
@@ -188,6 +197,21 @@ __global__ void __launch_bounds__(256) k_end_mcs(const Replica *reps, const doub
             for (int i = 0; i < 7; ++i) red[threadIdx.x][i] += red[threadIdx.x + w][i];
         __syncthreads();
     }
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < 7; ++i) gsum[7 * grp + i] = red[0][i];
+        __threadfence();
+        last = atomicAdd(arrive, 1u) == END_GROUPS - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    // the last group of the replica: the group sums in group order
+    __threadfence();
+    if (threadIdx.x < 7) {
+        double t = 0.0;
+        for (int g = 0; g < END_GROUPS; ++g) t += __ldcg(gsum + 7 * g + threadIdx.x);
+        red[0][threadIdx.x] = t;
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
         const double n_sites = 8.0 * (double)R.nblk;
         double mean[6];
@@ -234,6 +258,7 @@ __global__ void __launch_bounds__(256) k_end_mcs(const Replica *reps, const doub
             }
         }
         if (advance) st->mcs += 1;
+        *arrive = 0u;   // ready for the next launch
     }
 }
 
@@ -349,9 +374,9 @@ cudaError_t launch_stress(const StressArgs<T> &a, bool store, cudaStream_t s) {
 template cudaError_t launch_stress<float>(const StressArgs<float> &, bool, cudaStream_t);
 template cudaError_t launch_stress<double>(const StressArgs<double> &, bool, cudaStream_t);
 
-cudaError_t launch_end_mcs(const Replica *reps, int nrep, const double *partials, int update_strain, int advance,
+cudaError_t launch_end_mcs(const Replica *reps, int nrep, double *partials, int nctas, int update_strain, int advance,
                            cudaStream_t s) {
-    k_end_mcs<<<nrep, 256, 0, s>>>(reps, partials, update_strain, advance);
+    k_end_mcs<<<nrep * END_GROUPS, 256, 0, s>>>(reps, partials, nctas, update_strain, advance);
     return cudaGetLastError();
 }
 
