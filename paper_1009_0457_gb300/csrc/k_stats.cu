@@ -83,13 +83,15 @@ __device__ __forceinline__ void store4<double>(double *p, const double (&v)[4]) 
 // thread and a warp, by T, and FP64 across warps) for a fixed-order final
 // reduction.
 // threads of a stress CTA (measured on the 256^3 workload: 256 threads, one block each, 0.244 ms;
-// 128 threads 0.180 ms; 64 threads 0.156 ms; 32 threads 0.156 ms)
+// 128 threads 0.180 ms; 64 threads 0.156 ms; 32 threads 0.156 ms).  Each thread loads its next
+// block's corners and spins while it works on the current one (0.156 -> 0.150 ms), held to
+// 128 registers in FP32 (eight CTAs per SM).
 constexpr int STRESS_THREADS = 64;
 constexpr int STRESS_CELLS = BLOCK_THREADS / STRESS_THREADS;
 static_assert(BLOCK_THREADS % STRESS_THREADS == 0, "a tile splits evenly over the threads");
 
 template <typename T, bool STORE>
-__global__ void __launch_bounds__(STRESS_THREADS) k_stress(StressArgs<T> a) {
+__global__ void __launch_bounds__(STRESS_THREADS, sizeof(T) == 4 ? 8 : 1) k_stress(StressArgs<T> a) {
     __shared__ double red[STRESS_THREADS / 32][7];
     const int rep = __ldg(a.cta_rep + blockIdx.x);
     const Replica &R = a.reps[rep];
@@ -101,13 +103,10 @@ __global__ void __launch_bounds__(STRESS_THREADS) k_stress(StressArgs<T> a) {
     const int nbx = R.nbx, nby = R.nby, nbz = R.nbz;
     const T *u = a.u + 3 * R.blk_off;
     T *sig = a.sig + 48ll * R.blk_off;
-#pragma unroll 1
-    for (int c8 = 0; c8 < STRESS_CELLS; ++c8) {
-        const int blk = t0 + c8 * STRESS_THREADS + threadIdx.x;
-        if (blk >= R.nblk) break;
+    // a cell's corner displacements and spins, loaded one cell ahead of its arithmetic
+    auto load_cell = [&](int blk, T (&uc)[8][3], uint4 &sp) {
         const int bx = blk % nbx, rr = blk / nbx;
         const int by = rr % nby, bz = rr / nby;
-        T uc[8][3];
 #pragma unroll
         for (int K = 0; K < 2; ++K)
 #pragma unroll
@@ -121,9 +120,25 @@ __global__ void __launch_bounds__(STRESS_THREADS) k_stress(StressArgs<T> a) {
 #pragma unroll
                     for (int d = 0; d < 3; ++d) uc[corner(I, J, K)][d] = __ldg(u + n + d);
                 }
+        sp = __ldg(a.spins + R.blk_off + blk);
+    };
+    T un[8][3];
+    uint4 spn = make_uint4(0, 0, 0, 0);
+    int blk = t0 + threadIdx.x;
+    if (blk < R.nblk) load_cell(blk, un, spn);
+#pragma unroll 1
+    for (int c8 = 0; c8 < STRESS_CELLS; ++c8) {
+        if (blk >= R.nblk) break;
+        T uc[8][3];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int d = 0; d < 3; ++d) uc[i][d] = un[i][d];
+        const uint4 sp = spn;
+        const int blk_next = blk + STRESS_THREADS;
+        if (c8 + 1 < STRESS_CELLS && blk_next < R.nblk) load_cell(blk_next, un, spn);
         CellGrad<T> g;
         cell_gradients<T>(uc, g);
-        const uint4 sp = __ldg(a.spins + R.blk_off + blk);
         T csum[7] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0)};   // this cell's eight points, plain sums
         Row24<T> row;
         uint32_t qprev = 0xffffffffu;
@@ -158,6 +173,7 @@ __global__ void __launch_bounds__(STRESS_THREADS) k_stress(StressArgs<T> a) {
         }
 #pragma unroll
         for (int k = 0; k < 7; ++k) acc.add(k, csum[k]);
+        blk = blk_next;
     }
     acc.warp_reduce();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
