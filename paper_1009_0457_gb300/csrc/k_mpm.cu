@@ -318,6 +318,9 @@ __global__ void __launch_bounds__(CX *CY, (sizeof(T) == 4 ? 2 : 1)) k_mpm_step(M
     Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
     const int tid = threadIdx.x;
     const T fscale = -a.dt_over_m * T(0.03125);          // -dt / (32 m)
+    // the next step may be launched now: its CTAs take the SM slots this grid's CTAs free
+    // and stage their table while this grid finishes
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     // FP32: the orientation table of the cubic form, staged in shared memory behind the tiles
     const float *cw = a.cubw;
     if constexpr (STAB) {
@@ -330,6 +333,9 @@ __global__ void __launch_bounds__(CX *CY, (sizeof(T) == 4 ? 2 : 1)) k_mpm_step(M
     float cub[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) cub[i] = a.cub[i];
+    // everything above reads only constant tables; u, v, the spins and the mean strain come
+    // from the kernels before this one
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     // this CTA's contiguous range of the linear (replica, tile, plane) index
     long long w = a.total * blockIdx.x / gridDim.x;
     const long long wend = a.total * (blockIdx.x + 1) / gridDim.x;
@@ -851,14 +857,30 @@ int mpm_per_sm<double>(int shape, int nq) {
     return per_sm_t<double, false, false>(shape % MPM_NSHAPES, nq);
 }
 
+// launched with programmatic stream serialisation: the kernel waits for the grid before it
+// (griddepcontrol.wait) only after its prologue
+template <typename T, int CX, int CY, bool PAIR, bool STAB>
+static void launch_pdl(const MpmArgs<T> &a, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(a.grid);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = smem_of<T, CX, CY>(STAB, a.nq);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k_mpm_step<T, CX, CY, PAIR, STAB>, a);
+}
 template <typename T, bool PAIR, bool STAB>
 static void launch_t(const MpmArgs<T> &a, int shape, cudaStream_t s) {
     if (shape == MPM_32x8)
-        k_mpm_step<T, 32, 8, PAIR, STAB><<<a.grid, 256, smem_of<T, 32, 8>(STAB, a.nq), s>>>(a);
+        launch_pdl<T, 32, 8, PAIR, STAB>(a, s);
     else if (shape == MPM_8x32)
-        k_mpm_step<T, 8, 32, PAIR, STAB><<<a.grid, 256, smem_of<T, 8, 32>(STAB, a.nq), s>>>(a);
+        launch_pdl<T, 8, 32, PAIR, STAB>(a, s);
     else
-        k_mpm_step<T, 16, 16, PAIR, STAB><<<a.grid, 256, smem_of<T, 16, 16>(STAB, a.nq), s>>>(a);
+        launch_pdl<T, 16, 16, PAIR, STAB>(a, s);
 }
 
 // shape in 0..2: scalar Hooke; shape + MPM_NSHAPES: paired-FMA Hooke (FP32 only);
