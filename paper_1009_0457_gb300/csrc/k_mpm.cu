@@ -250,8 +250,9 @@ __device__ __forceinline__ void cell_forces(const T (&u)[8][3], const uint4 &sp,
     row.load(ctab, cw, qprev);
     CellGrad<T> g;
     cell_gradients31<T>(u, g);
-    // the normal strains of a point are eb_k plus one gradient entry that two points share:
-    // add eb_k to those entries once
+    // each strain component of a point is eb_k plus gradient entries that two points share:
+    // add eb_k once to the one entry of each component that only that component uses (the
+    // normal entries, and one of the two entries of each shear)
 #pragma unroll
     for (int i = 0; i < 2; ++i)
 #pragma unroll
@@ -259,6 +260,9 @@ __device__ __forceinline__ void cell_forces(const T (&u)[8][3], const uint4 &sp,
             g.gx[i][j][0] = eb[0] + g.gx[i][j][0];
             g.gy[i][j][1] = eb[1] + g.gy[i][j][1];
             g.gz[i][j][2] = eb[2] + g.gz[i][j][2];
+            g.gz[i][j][1] = eb[3] + g.gz[i][j][1];
+            g.gz[i][j][0] = eb[4] + g.gz[i][j][0];
+            g.gy[i][j][0] = eb[5] + g.gy[i][j][0];
         }
     T tx[2][2][3], ty[2][2][3], tz[2][2][3];  // traction sums over a, b, c respectively
 #pragma unroll
@@ -275,9 +279,9 @@ __device__ __forceinline__ void cell_forces(const T (&u)[8][3], const uint4 &sp,
         e[0] = g.gx[b][c][0];
         e[1] = g.gy[a][c][1];
         e[2] = g.gz[a][b][2];
-        e[3] = eb[3] + (g.gz[a][b][1] + g.gy[a][c][2]);
-        e[4] = eb[4] + (g.gz[a][b][0] + g.gx[b][c][2]);
-        e[5] = eb[5] + (g.gy[a][c][0] + g.gx[b][c][1]);
+        e[3] = g.gz[a][b][1] + g.gy[a][c][2];
+        e[4] = g.gz[a][b][0] + g.gx[b][c][2];
+        e[5] = g.gy[a][c][0] + g.gx[b][c][1];
         // points of one cell mostly share one orientation: fetch the row only when it changes
         const uint32_t q = spin_of(sp, local_slot(L));
         if (q != qprev) {
@@ -549,6 +553,9 @@ __device__ __forceinline__ void cell_forces2(const float2 (&u)[8][3], const uint
             gx[i][j][0] = p_add(eb[0], gx[i][j][0]);
             gy[i][j][1] = p_add(eb[1], gy[i][j][1]);
             gz[i][j][2] = p_add(eb[2], gz[i][j][2]);
+            gz[i][j][1] = p_add(eb[3], gz[i][j][1]);
+            gz[i][j][0] = p_add(eb[4], gz[i][j][0]);
+            gy[i][j][0] = p_add(eb[5], gy[i][j][0]);
         }
     float2 tx[2][2][3], ty[2][2][3], tz[2][2][3];
 #pragma unroll
@@ -565,9 +572,9 @@ __device__ __forceinline__ void cell_forces2(const float2 (&u)[8][3], const uint
         e[0] = gx[b][c][0];
         e[1] = gy[a][c][1];
         e[2] = gz[a][b][2];
-        e[3] = p_add(eb[3], p_add(gz[a][b][1], gy[a][c][2]));
-        e[4] = p_add(eb[4], p_add(gz[a][b][0], gx[b][c][2]));
-        e[5] = p_add(eb[5], p_add(gy[a][c][0], gx[b][c][1]));
+        e[3] = p_add(gz[a][b][1], gy[a][c][2]);
+        e[4] = p_add(gz[a][b][0], gx[b][c][2]);
+        e[5] = p_add(gy[a][c][0], gx[b][c][1]);
         const uint32_t na = spin_of(spa, local_slot(L)), nb = spin_of(spb, local_slot(L));
         if (na != qa || nb != qb) {
             load_w_pair(cw, na, nb, row);

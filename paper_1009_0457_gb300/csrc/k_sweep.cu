@@ -515,9 +515,10 @@ __global__ void __launch_bounds__(SWEEP_CTA, flat_min_ctas<T, MODE, RECOMP>())
         }
         __syncwarp();
         if (pend) {
+            const uint32_t acc4 = *reinterpret_cast<const uint32_t *>(&sl.acc[tid << 2]);   // slots 0..3
 #pragma unroll
             for (int i = 0; i < 4; ++i)
-                if ((pend & (1u << i)) && sl.acc[tid << 2 | i]) {
+                if ((pend & (1u << i)) && ((acc4 >> (8 * i)) & 0xffu)) {
                     out[i] = qn[i];
                     ++nacc;
                 }
