@@ -867,7 +867,7 @@ int mpm_per_sm<double>(int shape, int nq) {
 // launched with programmatic stream serialisation: the kernel waits for the grid before it
 // (griddepcontrol.wait) only after its prologue
 template <typename T, int CX, int CY, bool PAIR, bool STAB>
-static void launch_pdl(const MpmArgs<T> &a, cudaStream_t s) {
+static cudaError_t launch_pdl(const MpmArgs<T> &a, cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(a.grid);
     cfg.blockDim = dim3(256);
@@ -878,16 +878,13 @@ static void launch_pdl(const MpmArgs<T> &a, cudaStream_t s) {
     at[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, k_mpm_step<T, CX, CY, PAIR, STAB>, a);
+    return cudaLaunchKernelEx(&cfg, k_mpm_step<T, CX, CY, PAIR, STAB>, a);
 }
 template <typename T, bool PAIR, bool STAB>
-static void launch_t(const MpmArgs<T> &a, int shape, cudaStream_t s) {
-    if (shape == MPM_32x8)
-        launch_pdl<T, 32, 8, PAIR, STAB>(a, s);
-    else if (shape == MPM_8x32)
-        launch_pdl<T, 8, 32, PAIR, STAB>(a, s);
-    else
-        launch_pdl<T, 16, 16, PAIR, STAB>(a, s);
+static cudaError_t launch_t(const MpmArgs<T> &a, int shape, cudaStream_t s) {
+    if (shape == MPM_32x8) return launch_pdl<T, 32, 8, PAIR, STAB>(a, s);
+    if (shape == MPM_8x32) return launch_pdl<T, 8, 32, PAIR, STAB>(a, s);
+    return launch_pdl<T, 16, 16, PAIR, STAB>(a, s);
 }
 
 // shape in 0..2: scalar Hooke; shape + MPM_NSHAPES: paired-FMA Hooke (FP32 only);
@@ -896,18 +893,18 @@ static void launch_t(const MpmArgs<T> &a, int shape, cudaStream_t s) {
 template <>
 cudaError_t launch_mpm_step<float>(const MpmArgs<float> &a, int shape, cudaStream_t s) {
     const bool stab = a.nq <= MPM_STAB_MAX;
-    if (shape == MPM_TWO_CELL)
+    if (shape == MPM_TWO_CELL) {
         k_mpm_step2<<<a.grid, 128, sizeof(MpmSmem2), s>>>(a);
-    else if (shape >= MPM_NSHAPES)
-        stab ? launch_t<float, true, true>(a, shape - MPM_NSHAPES, s) : launch_t<float, true, false>(a, shape - MPM_NSHAPES, s);
-    else
-        stab ? launch_t<float, false, true>(a, shape, s) : launch_t<float, false, false>(a, shape, s);
-    return cudaGetLastError();
+        return cudaGetLastError();
+    }
+    if (shape >= MPM_NSHAPES)
+        return stab ? launch_t<float, true, true>(a, shape - MPM_NSHAPES, s)
+                    : launch_t<float, true, false>(a, shape - MPM_NSHAPES, s);
+    return stab ? launch_t<float, false, true>(a, shape, s) : launch_t<float, false, false>(a, shape, s);
 }
 template <>
 cudaError_t launch_mpm_step<double>(const MpmArgs<double> &a, int shape, cudaStream_t s) {
-    launch_t<double, false, false>(a, shape % MPM_NSHAPES, s);
-    return cudaGetLastError();
+    return launch_t<double, false, false>(a, shape % MPM_NSHAPES, s);
 }
 
 }  // namespace hmc
