@@ -40,8 +40,8 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# FP32 peak of the ALU roofline: 152 SMs x 128 FP32 lanes x 2 flop per FMA x clock
-GB300_SMS, FP32_LANES = 152, 128
+# FP32 peak of the ALU roofline: SMs (read from the device) x 128 FP32 lanes x 2 flop per FMA x clock
+FP32_LANES = 128
 # algorithmic flops of one point in one fused FP32 MPM step, separable trilinear form
 # (corner differences, gradient interpolation, strain, Hooke's law in the cubic form
 # (66 flop), traction sums, force interpolation, corner assembly, node update), FMA = 2 flop
@@ -50,6 +50,7 @@ MPM_BYTES_PER_POINT = {"f32": 8, "f64": 14}      # spin 2 + (u,v) read + (u,v) w
 SWEEP_BYTES_PER_SITE = {"f32": 28, "f64": 52}    # spin read + write + stored stress read
 STRESS_BYTES_PER_SITE = {"f32": 27.5, "f64": 53}  # spin 2 + u read (per point) + stress write
 CROP = 64
+ENSEMBLE_STEPS = 10
 
 
 def parse():
@@ -61,6 +62,7 @@ def parse():
     ap.add_argument("--workload", default="ni256")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--store-stress", type=int, default=1, choices=[0, 1],
                     help="1: the stress pass stores every point's stress for the sweeps; 0: sweeps recompute it")
     return ap.parse_args()
@@ -171,22 +173,66 @@ def dist_env():
     return ws, rank, local
 
 
-def crop_spec(spins, euler):
-    return spins[:CROP, :CROP, :CROP].copy(), euler
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
 
 
-def oracle_mcs_rate(spec, euler, spins, n_mcs):
-    """site-updates/s of the oracle (FP64, 1 thread) over n_mcs full MCS on a crop."""
+def crops(spins, n):
+    """n disjoint CROP^3 crops of the field (as many as it holds, at most n)."""
+    nz, ny, nx = spins.shape
+    out = []
+    for z in range(0, nz - CROP + 1, CROP):
+        for y in range(0, ny - CROP + 1, CROP):
+            for x in range(0, nx - CROP + 1, CROP):
+                if len(out) < n:
+                    out.append(np.ascontiguousarray(spins[z:z + CROP, y:y + CROP, x:x + CROP]))
+    return out
+
+
+def _oracle_crop_worker(spec, euler, crop, warmup, n_mcs, barrier, out):
+    """One host process: the unchanged FP64 oracle (single-threaded C) on one crop; the
+    timed part starts when every process has finished its set-up and warm-up."""
+    sys.path.insert(0, ROOT)
     import oracle as O
-    sp, eul = crop_spec(spins, euler)
-    o = O.OracleHMC(sp.shape, spec["Q"], J=spec["J"], kT=spec["kT"], c11=spec["c11"], c12=spec["c12"],
-                    c44=spec["c44"], load_axis=spec["axis"], strain=spec["strain"],
-                    mpm_steps_per_mcs=spec["mpm_steps"], seed=12345)
-    o.set_orientations(eul, sp)
-    t0 = time.perf_counter()
-    o.mc_sweeps(n_mcs)
-    t = time.perf_counter() - t0
-    return sp.size * n_mcs / t, t, sp.size
+    try:
+        o = O.OracleHMC(crop.shape, spec["Q"], J=spec["J"], kT=spec["kT"], c11=spec["c11"], c12=spec["c12"],
+                        c44=spec["c44"], load_axis=spec["axis"], strain=spec["strain"],
+                        mpm_steps_per_mcs=spec["mpm_steps"], seed=12345)
+        o.set_orientations(euler, crop)
+        o.mc_sweeps(warmup)
+        barrier.wait(timeout=600)
+        t0 = time.time()
+        o.mc_sweeps(n_mcs)
+        out.put((crop.size * n_mcs, t0, time.time()))
+    except Exception as e:  # reported by the parent
+        out.put(("error", repr(e), 0.0))
+
+
+def oracle_rate(spec, euler, spins, n_mcs, procs, warmup=0):
+    """site-updates/s of the oracle over n_mcs full MCS in each of `procs` host processes,
+    each on its own disjoint CROP^3 crop (one process per core; spawned, never forked,
+    since the parent may already hold a CUDA context).  Returns (rate, seconds, sites, procs)."""
+    import multiprocessing as mp
+    parts = crops(spins, procs)
+    ctx = mp.get_context("spawn")
+    barrier = ctx.Barrier(len(parts))
+    q = ctx.Queue()
+    ps = [ctx.Process(target=_oracle_crop_worker, args=(spec, euler, c, warmup, n_mcs, barrier, q), daemon=True)
+          for c in parts]
+    for p in ps:
+        p.start()
+    res = [q.get(timeout=1800) for _ in ps]
+    for p in ps:
+        p.join(timeout=60)
+    bad = [r for r in res if r[0] == "error"]
+    if bad:
+        raise RuntimeError(f"oracle worker failed: {bad[0][1]}")
+    units = sum(r[0] for r in res)
+    t = max(r[2] for r in res) - min(r[1] for r in res)
+    return units / t, t, sum(c.size for c in parts), len(parts)
 
 
 def run_reference(args):
@@ -195,24 +241,17 @@ def run_reference(args):
         return 0
     import hmc_synth as S
     spec, euler, spins = S.workload_inputs(args.workload)
-    import oracle as O
-    sp, eul = crop_spec(spins, euler)
-    o = O.OracleHMC(sp.shape, spec["Q"], J=spec["J"], kT=spec["kT"], c11=spec["c11"], c12=spec["c12"],
-                    c44=spec["c44"], load_axis=spec["axis"], strain=spec["strain"],
-                    mpm_steps_per_mcs=spec["mpm_steps"], seed=12345)
-    o.set_orientations(eul, sp)
-    o.mc_sweeps(args.warmup)
-    t0 = time.perf_counter()
-    o.mc_sweeps(args.steps)
-    t = time.perf_counter() - t0
-    value = sp.size * args.steps / t
-    sample = (f"{CROP}^3 crop ({sp.size} sites) of the {args.workload} microstructure; each step one full "
-              f"oracle MCS ({spec['mpm_steps']} MPM steps, stress, red+black sweep), FP64, 1 thread")
+    cores = host_cores()
+    value, t, sites, nproc = oracle_rate(spec, euler, spins, args.steps, cores, warmup=args.warmup)
+    sample = (f"{nproc} disjoint {CROP}^3 crops ({sites} sites) of the {args.workload} microstructure, one "
+              f"single-threaded oracle process per host core; each step one full oracle MCS in every crop "
+              f"({spec['mpm_steps']} MPM steps, stress, red+black sweep), FP64")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "site-updates/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(spec, args.workload),
-            "cpu_baseline": {"kind": "oracle", "value": value, "unit": "site-updates/s", "cores": 1, "sample": sample},
+            "cpu_baseline": {"kind": "oracle", "value": value, "unit": "site-updates/s", "cores": nproc,
+                             "sample": sample},
             "e2e": {"value": value, "unit": "site-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -273,6 +312,23 @@ def run_ours(args):
     # warm-up (captures the graph)
     G.lib.hmc_mc_sweeps(h.h, args.warmup, None)
     h.synchronize()
+    # the workload logs the texture (angle to the nearest <100>, 10-degree bins) every hist_every MCS
+    hist_every = int(spec.get("hist_every", 0))
+    hist = np.zeros(9)
+    hist_p = hist.ctypes.data_as(G.C.POINTER(G.C.c_double))
+
+    def run_mcs(n):
+        done, nh = 0, 0
+        while done < n:
+            k = min(n - done, hist_every) if hist_every else n
+            st = G.lib.hmc_mc_sweeps(h.h, k, None)
+            assert st == 0, G.hmc_last_error(h.h)
+            done += k
+            if hist_every and k == hist_every:
+                st = G.lib.hmc_texture_histogram(h.h, G.HMC_HIST_ANGLE_100, 9, hist_p, None)
+                assert st == 0, G.hmc_last_error(h.h)
+                nh += 1
+        return nh
 
     # ---- timed region: K MCS --------------------------------------------------
     clocks = Clocks(local)
@@ -281,16 +337,16 @@ def run_ours(args):
     clocks.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    st = G.lib.hmc_mc_sweeps(h.h, args.steps, None)
+    n_hist = run_mcs(args.steps)
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
-    assert st == 0, G.hmc_last_error(h.h)
     t_local = e0.elapsed_time(e1) / 1e3
     t, units = dist_reduce(t_local, N * args.steps, "cuda")
     value = units / t
-    launches = args.steps * (spec["mpm_steps"] + 4)
+    launches = args.steps * (spec["mpm_steps"] + 4) + 2 * n_hist
+    texture = [float(x) for x in hist] if n_hist else None
 
     # ---- per-kernel timing on the same stream (roofline) ----------------------
     n_mpm = 50
@@ -302,15 +358,21 @@ def run_ours(args):
         assert G.lib.hmc_compute_stress(h.h, None, None) == 0
         t_sweep += [timed(lambda c=c: G.lib.hmc_sweep_half(h.h, c, None)) for c in (0, 1)]
     t_sweep = statistics.median(t_sweep)
+    mcs_ms = 1e3 * t / args.steps
+    sum_ms = 1e3 * (spec["mpm_steps"] * t_mpm + t_stress + 2 * t_sweep)
+    mcs_phases = {"mpm_ms": 1e3 * spec["mpm_steps"] * t_mpm, "stress_and_reduction_ms": 1e3 * t_stress,
+                  "half_sweeps_ms": 2e3 * t_sweep, "sum_ms": sum_ms, "mcs_ms": mcs_ms,
+                  "graph_minus_phases_fraction": (mcs_ms - sum_ms) / mcs_ms}
     hbm, sm_max, peak_src = peaks()
-    fp32_peak = GB300_SMS * FP32_LANES * 2 * sm_max * 1e6 / 1e12
+    n_sms = torch.cuda.get_device_properties(local).multi_processor_count
+    fp32_peak = n_sms * FP32_LANES * 2 * sm_max * 1e6 / 1e12
     mpm_tflops = MPM_FLOP_PER_POINT * N / t_mpm / 1e12
     sweep_gbs = SWEEP_BYTES_PER_SITE["f32"] * (N / 2) / t_sweep / 1e9
     roofline = {"kernel": "k_mpm_step<float> (fused explicit MPM step)", "bound": "alu",
                 "achieved": mpm_tflops, "peak": fp32_peak, "unit": "TFLOP/s", "frac": mpm_tflops / fp32_peak,
                 "traffic": kernel_traffic("mpm"),
                 "algorithmic": f"{MPM_FLOP_PER_POINT} flop/point x {N} points per launch",
-                "peak_source": f"derived: {GB300_SMS} SMs x {FP32_LANES} FP32 lanes x 2 flop x {sm_max:.0f} MHz "
+                "peak_source": f"derived: {n_sms} SMs x {FP32_LANES} FP32 lanes x 2 flop x {sm_max:.0f} MHz "
                                f"(max SM clock, {peak_src})",
                 "hbm_view": {"achieved_gbs": MPM_BYTES_PER_POINT["f32"] * N / t_mpm / 1e9, "peak": hbm,
                              "frac": MPM_BYTES_PER_POINT["f32"] * N / t_mpm / 1e9 / hbm}}
@@ -354,17 +416,34 @@ def run_ours(args):
         t64 = timed(lambda: G.lib.hmc_mc_sweeps(h64.h, k64, None))
         t64_mpm = timed(lambda: G.lib.hmc_mpm_steps(h64.h, 5, None)) / 5
         v64 = N * k64 / t64
-        fp64 = {"value": v64, "unit": "site-updates/s", "steps": k64, "speedup_fp32_over_fp64": value / ws / v64,
+        fp64 = {"form": "the fused kernels instantiated in FP64 (not the unfused incremental form)",
+                "value": v64, "unit": "site-updates/s", "steps": k64, "speedup_fp32_over_fp64": value / ws / v64,
                 "mpm_cell_steps_per_s": N / t64_mpm, "mpm_ms_per_step": t64_mpm * 1e3}
         h64.close()
+
+    # ---- error of the FP32 path against the FP64 path (outside the timed region) ----
+    err32 = None
+    if rank == 0 and ws == 1 and not args.no_fp64:
+        err32 = fp32_error(G, spec, euler, spins, common)
 
     # ---- CPU oracle on the host cores (rank 0, one GPU only) ------------------
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        v, tt, n = oracle_mcs_rate(spec, euler, spins, 1)
-        cpu = {"kind": "oracle", "value": v, "unit": "site-updates/s", "cores": 1,
-               "sample": f"{CROP}^3 crop ({n} sites) of the workload's microstructure, one full MCS "
-                         f"({spec['mpm_steps']} MPM steps, stress, red+black sweep), FP64, {tt:.1f} s"}
+        v1, t1, n1, _ = oracle_rate(spec, euler, spins, 1, 1)
+        cores = host_cores()
+        v, tt, n, nproc = oracle_rate(spec, euler, spins, 1, cores)
+        cpu = {"kind": "oracle", "value": v, "unit": "site-updates/s", "cores": nproc,
+               "sample": f"{nproc} disjoint {CROP}^3 crops ({n} sites) of the workload's microstructure, one "
+                         f"single-threaded oracle process per host core, one full MCS each ({spec['mpm_steps']} "
+                         f"MPM steps, stress, red+black sweep), FP64, {tt:.1f} s wall",
+               "one_core": {"value": v1, "unit": "site-updates/s", "cores": 1,
+                            "sample": f"one {CROP}^3 crop ({n1} sites), one full MCS, {t1:.1f} s"}}
+
+    # ---- the batched ensemble (64 uneven replicas in one handle), one GPU only ----
+    ens = None
+    if rank == 0 and ws == 1 and not args.no_ensemble:
+        ens = ensemble_measure(torch, G, S, ENSEMBLE_STEPS, 3, local)
+        ens["workload"] = ENSEMBLE_WORKLOAD(S, ens)
 
     if rank == 0:
         line = {
@@ -375,7 +454,8 @@ def run_ours(args):
             "mpm_cell_steps_per_s": N * ws / t_mpm, "mpm_ms_per_step": t_mpm * 1e3,
             "stress_ms": t_stress * 1e3, "half_sweep_ms": t_sweep * 1e3,
             "roofline": roofline, "roofline_sweep": roofline_sweep,
-            "e2e": e2e, "gpu_launches": launches, "clocks": clk, "fp64_form": fp64, "cpu_baseline": cpu,
+            "e2e": e2e, "gpu_launches": launches, "clocks": clk, "fp64_form": fp64, "fp32_error": err32,
+            "texture_angle100_10deg": texture, "ensemble": ens, "mcs_phases": mcs_phases, "cpu_baseline": cpu,
             "mpm_variant": mpm_variant_name(h.tuning()[0]), "mpm_grid": h.tuning()[1],
         }
         print(json.dumps(line), flush=True)
@@ -386,49 +466,129 @@ def run_ours(args):
     return 0
 
 
-def run_ensemble(args):
-    """The batched ensemble: 64 replicas of uneven size in one handle, every
-    phase one launch over all replicas, one CUDA graph per MCS; prints one
-    JSON line (site-updates/s over all replicas)."""
-    import torch
-    torch.cuda.set_device(0)
-    import hmc_synth as S
-    import paper_1009_0457_gb300 as G
+FP32_ERR_STEPS = 200
+
+
+def fp32_error(G, spec, euler, spins, common):
+    """The error of the FP32 path against the FP64 path of the same library (which the
+    oracle parity tests pin to the oracle), on the workload itself:
+      * stress: relative L2 of the FP32 stress after 200 explicit MPM steps from the same
+        state (zero displacement, the initial mean strain);
+      * decisions: one red and one black half sweep in FP32 and in FP64 on the same spins
+        and the same stress (the FP64 stress, rounded for the FP32 handle); the fraction
+        of the colour's sites whose decision differs, and how many of those differing
+        decisions lie outside the 1e-6 margin |H - t| <= 1e-6 max(1, |t|) of the FP64 sweep."""
+    kw = dict(common)
+    kw["store_stress"] = 1
+    h64 = G.HMC(spec["shape"], spec["Q"], precision=G.HMC_FP64, **kw)
+    h32 = G.HMC(spec["shape"], spec["Q"], precision=G.HMC_FP32, **kw)
+    try:
+        for h in (h64, h32):
+            h.set_orientations(euler, spins)
+            h.mpm_steps(FP32_ERR_STEPS)
+            h.compute_stress()
+        s64 = h64.stress()
+        s32 = h32.stress()
+        rel_l2 = float(np.linalg.norm(s32 - s64) / np.linalg.norm(s64))
+        del s32
+        h32.set_stress(s64)
+        del s64
+        nz, ny, nx = spec["shape"]
+        par = (np.arange(nz)[:, None, None] + np.arange(ny)[None, :, None] + np.arange(nx)[None, None, :]) & 1
+        halves = []
+        for colour in (0, 1):
+            h32.set_spins(h64.spins())
+            _, m64 = h64.sweep_half_margins(colour)
+            h32.sweep_half(colour)
+            mis = (h64.spins() != h32.spins()) & (par == colour)
+            n_mis = int(mis.sum())
+            gaps = np.abs(m64[mis])
+            halves.append({"colour": colour, "sites": int((par == colour).sum()), "mismatched": n_mis,
+                           "mismatch_fraction": n_mis / int((par == colour).sum()),
+                           "outside_1e-6_margin": int((gaps > 1e-6).sum()),
+                           "largest_margin_of_a_mismatch": float(gaps.max()) if n_mis else 0.0,
+                           "evaluated_trials": int((~np.isnan(m64) & (par == colour)).sum())})
+        return {"stress_rel_l2": rel_l2, "stress_steps": FP32_ERR_STEPS, "half_sweeps": halves,
+                "reference": "the library's FP64 path from the same state (pinned to the FP64 oracle by the "
+                             "parity tests)"}
+    finally:
+        h64.close()
+        h32.close()
+
+
+def ensemble_measure(torch, G, S, steps, warmup, clocks_index=0):
+    """The batched ensemble (64 replicas of uneven size in one handle, every phase one
+    launch over all replicas, one CUDA graph per MCS): site-updates/s over all replicas,
+    the time of each phase launched on its own (50 MPM steps, stress pass with the
+    end-of-step reduction, red and black half sweep) and what the graph saves or loses
+    against their sum (launch gaps)."""
     specs, euler, fields = S.ensemble_inputs()
     stream = torch.cuda.Stream()
     per = [dict(load_axis=sp["axis"], strain=sp["strain"], seed=sp["mc_seed"], replica=r)
            for r, sp in enumerate(specs)]
     b = G.HMCBatch([sp["shape"] for sp in specs], specs[0]["Q"], per, precision=G.HMC_FP32,
                    mpm_steps_per_mcs=50, stream=stream.cuda_stream, **S.COMMON)
-    b.set_orientations(euler, fields)
-    G.lib.hmc_mc_sweeps(b.h, args.warmup, None)
-    b.synchronize()
-    N = sum(int(np.prod(sp["shape"])) for sp in specs)
-    clocks = Clocks(0)
-    torch.cuda.synchronize()
-    clocks.start()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    st = G.lib.hmc_mc_sweeps(b.h, args.steps, None)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    clk = clocks.stop()
-    assert st == 0, G.hmc_last_error(b.h)
-    t = e0.elapsed_time(e1) / 1e3
-    shape, grid = b.tuning()
-    line = {"metric": METRIC, "value": N * args.steps / t, "unit": "site-updates/s", "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+    try:
+        b.set_orientations(euler, fields)
+        G.lib.hmc_mc_sweeps(b.h, warmup, None)
+        b.synchronize()
+        N = sum(int(np.prod(sp["shape"])) for sp in specs)
+
+        def timed(fn):
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a0.record(stream)
+            st = fn()
+            a1.record(stream)
+            torch.cuda.synchronize()
+            assert st == 0, G.hmc_last_error(b.h)
+            return a0.elapsed_time(a1)
+
+        clocks = Clocks(clocks_index)
+        torch.cuda.synchronize()
+        clocks.start()
+        ms = timed(lambda: G.lib.hmc_mc_sweeps(b.h, steps, None))
+        clk = clocks.stop()
+        phases = {"mpm_50_steps_ms": timed(lambda: G.lib.hmc_mpm_steps(b.h, 50, None)),
+                  "stress_and_reduction_ms": timed(lambda: G.lib.hmc_compute_stress(b.h, None, None)),
+                  "red_half_sweep_ms": timed(lambda: G.lib.hmc_sweep_half(b.h, 0, None)),
+                  "black_half_sweep_ms": timed(lambda: G.lib.hmc_sweep_half(b.h, 1, None))}
+        mcs_ms = ms / steps
+        tot = sum(phases.values())
+        shape, grid = b.tuning()
+        return {"value": N * steps / (ms / 1e3), "unit": "site-updates/s", "steps": steps, "warmup": warmup,
+                "ms_per_mcs": mcs_ms, "sites": N, "replicas": len(specs),
+                "edges": [sp["shape"][0] for sp in specs],
+                "phases_ms": phases, "phase_fractions": {k: v / tot for k, v in phases.items()},
+                "sum_of_phases_ms": tot, "graph_minus_phases_fraction": (mcs_ms - tot) / mcs_ms,
+                "mpm_variant": mpm_variant_name(shape), "mpm_grid": grid,
+                "gpu_launches": steps * (50 + 4), "clocks": clk}
+    finally:
+        b.close()
+
+
+def run_ensemble(args):
+    """The batched ensemble on its own: one JSON line (site-updates/s over all replicas)."""
+    import torch
+    torch.cuda.set_device(0)
+    import hmc_synth as S
+    import paper_1009_0457_gb300 as G
+    e = ensemble_measure(torch, G, S, args.steps, args.warmup)
+    line = {"metric": METRIC, "value": e["value"], "unit": "site-updates/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": e["ms_per_mcs"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"ensemble: {len(specs)} replicas, cubic edges from {S.ENSEMBLE_EDGES}, "
-                                   f"Q={specs[0]['Q']}, axis uniform on S2, strain U[5e-4, 3e-3], "
-                                   f"50 MPM steps per MCS, FP32, one launch per phase over all replicas",
-                       "sites": N, "replicas": len(specs),
-                       "edges": [sp["shape"][0] for sp in specs]},
-            "mpm_variant": mpm_variant_name(shape), "mpm_grid": grid,
-            "gpu_launches": args.steps * (50 + 4), "clocks": clk}
+            "config": {"workload": ENSEMBLE_WORKLOAD(S, e), "sites": e["sites"], "replicas": e["replicas"],
+                       "edges": e["edges"]},
+            "phases_ms": e["phases_ms"], "graph_minus_phases_fraction": e["graph_minus_phases_fraction"],
+            "mpm_variant": e["mpm_variant"], "mpm_grid": e["mpm_grid"], "gpu_launches": e["gpu_launches"],
+            "clocks": e["clocks"]}
     print(json.dumps(line), flush=True)
-    b.close()
     return 0
+
+
+def ENSEMBLE_WORKLOAD(S, e):
+    return (f"ensemble: {e['replicas']} replicas, cubic edges from {S.ENSEMBLE_EDGES}, Q=256, axis uniform on S2, "
+            f"strain U[5e-4, 3e-3], 50 MPM steps per MCS, FP32, one launch per phase over all replicas")
 
 
 ZONE_FLOP_PER_TRIAL = 70_000   # assembly 8.1k adds, block Cholesky 56k, forward solve and G 4.6k, 6x6 solve 1k
@@ -477,7 +637,9 @@ def run_zone(args):
     ms = float(np.mean(half_ms))
     ntr = float(np.mean(trials))
     achieved = ZONE_FLOP_PER_TRIAL * ntr / (ms * 1e-3) / 1e12
-    peak = 152 * 128 * 2 * 2.070e3 / 1e6
+    _, sm_max, _ = peaks()
+    n_sms = torch.cuda.get_device_properties(0).multi_processor_count
+    peak = n_sms * FP32_LANES * 2 * sm_max / 1e6
     line = {"metric": METRIC, "value": N * args.steps / t, "unit": "site-updates/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -489,7 +651,7 @@ def run_zone(args):
                          "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                          "traffic": kernel_traffic("zone"),
                          "algorithmic": f"{ZONE_FLOP_PER_TRIAL} flop/trial x {ntr:.0f} trials per half sweep",
-                         "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"},
+                         "peak_source": f"derived: {n_sms} SMs x {FP32_LANES} FP32 lanes x 2 flop x {sm_max:.0f} MHz"},
             "gpu_launches": args.steps * (spec["mpm_steps"] + 2 + 2 * 2), "clocks": clk}
     print(json.dumps(line), flush=True)
     g.close()

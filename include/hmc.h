@@ -239,9 +239,26 @@ hmc_status hmc_compute_stress(hmc_handle *h, double *mean_stress, double *elasti
  * count) plus lambda times the stored-stress zone shift.  The MC step counter is not advanced.
  * *accepted (nullable) receives the number of sites that changed.  A
  * stored-stress sweep waits for its asynchronous stress copy with a 1 s limit
- * per CTA; a CTA whose wait ran out changes no spin, and the next call that
- * reads the accepted count or the statistics reports HMC_ERR_TIMEOUT once. */
+ * per CTA; a CTA whose wait ran out changes no spin and, before it returns,
+ * waits (bounded, 20 further limits) for the copy to land, so that no copy
+ * outlives it.  The next call that reads the accepted count or the statistics
+ * reports HMC_ERR_TIMEOUT once, and later sweeps run normally.  Should a copy
+ * still be outstanding after those limits (valid device memory always
+ * arrives, so only a failing device gets there), HMC_ERR_TIMEOUT says so and
+ * every later call on the handle returns HMC_ERR_STATE: destroy it. */
 hmc_status hmc_sweep_half(hmc_handle *h, int32_t colour, int64_t *accepted);
+
+/* The same half sweep (single-replica handle, point-zone elastic term, stored
+ * stress), which also reports how close each decision was: margin (N doubles,
+ * HOST, natural order) receives (H - t) / max(1, |t|) for every trial that was
+ * evaluated with the elastic term -- H = J dE + dH_e the energy change and
+ * t = -kT ln u the threshold of Eq. 5 in the handle's precision, accepted iff
+ * H <= t -- and NaN for every other site.  A diagnostic for stating the error
+ * of the FP32 path: a decision that differs between precisions is one whose
+ * margin is within that precision's rounding.  Allocates and frees a device
+ * buffer of N doubles per call and synchronises.  HMC_ERR_ARG for a batch, a
+ * NULL margin, or a handle whose sweeps do not read the stored stress. */
+hmc_status hmc_sweep_half_margins(hmc_handle *h, int32_t colour, double *margin, int64_t *accepted);
 
 /* Close a Monte Carlo step: with UNIAXIAL control update the mean strain from
  * the mean stress of the last hmc_compute_stress, then advance the counter. */
@@ -249,8 +266,15 @@ hmc_status hmc_end_mcs(hmc_handle *h);
 
 /* n_mcs Monte Carlo steps, each: mpm_steps_per_mcs MPM steps, stress, red
  * half sweep, black half sweep (stress frozen over the step), end of step.
- * Replayed from a captured CUDA graph.  *accepted (nullable) receives the
- * number of spin changes over all n_mcs steps and all replicas. */
+ * This is the loading schedule of Sec. "Results" (in every load sub-step the
+ * quasi-static elastic state is obtained by the explicit MPM of Sec. "Elastic
+ * Deformation", then one Monte Carlo step follows) with the red/black update of
+ * Sec. "Microstructural Evolution".  Replayed from a captured CUDA graph (the
+ * first call on each displacement buffer captures it; make that call before any
+ * capture of your own).  *accepted (nullable) receives the number of spin
+ * changes over all n_mcs steps and all replicas.  HMC_ERR_STATE before
+ * hmc_set_orientations; HMC_ERR_ARG for n_mcs < 0; HMC_ERR_NONFINITE or
+ * HMC_ERR_TIMEOUT as described at hmc_sweep_half and hmc_compute_stress. */
 hmc_status hmc_mc_sweeps(hmc_handle *h, int32_t n_mcs, int64_t *accepted);
 
 /* Texture of the current spin field (Sec. "Results").  counts_per_q (Q int64,
@@ -271,9 +295,13 @@ hmc_status hmc_texture_histogram(hmc_handle *h, int32_t kind, int32_t nbins, dou
  * a union-find loop reached its iteration cap (no result). */
 hmc_status hmc_grain_count(hmc_handle *h, int64_t *n_grains);
 
-/* Statistics of the current state: number of unlike nearest-neighbour bonds
- * (each counted once, int64; the bond energy is J times it), elastic energy and
- * mean stress (6) from the stored stress (FP64).  Any pointer may be NULL. */
+/* Statistics of the current state.  unlike_bonds: the number of unlike
+ * nearest-neighbour bonds of the periodic lattice, each bond counted once
+ * (int64), so that the boundary energy of the Potts Hamiltonian (Eq. 4, read
+ * as J (1 - delta) per bond) is J times it.  elastic_energy: sum over the points
+ * of 1/2 sigma.eps (Eq. 1, V = one voxel) and mean_stress (6, Voigt) from the
+ * last stored stress pass, both reduced in FP64 in a fixed order.  Any pointer
+ * may be NULL.  HMC_ERR_NONFINITE if the reduction was not finite. */
 hmc_status hmc_energy(hmc_handle *h, int64_t *unlike_bonds, double *elastic_energy, double *mean_stress);
 
 /* Stored stress of every point (N x 6 doubles, natural order): the stress of
@@ -327,12 +355,16 @@ hmc_status hmc_set_state(hmc_handle *h, const void *buf, size_t bytes);
  *   d_sigma   N x 6 FP32 output, natural order (device)
  *   d_mean    6 doubles output (device);  d_energy  1 double output (device)
  *   stream    cudaStream_t, NULL = legacy default stream
- * Grids above 16,777,216 points (2,097,152 cells) are rejected with
- * HMC_ERR_ARG.  Work is enqueued on `stream` and not waited for.  The first
- * call on a device looks up the scratch array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  All calls share the scratch array: calls whose
- * work overlaps on the GPU race.  Errors are reported through
+ * Grids of at most 16,777,216 points (2,097,152 cells; 256^3 is the largest
+ * cube accepted) are served; larger ones are rejected with HMC_ERR_ARG.  Work
+ * is enqueued on `stream` and not waited for.  The first call on a device
+ * looks up the scratch array's device address (cudaGetSymbolAddress) with that
+ * device current and keeps it for the life of the process: make that first
+ * call before any stream capture, in the device's primary context, and do not
+ * call cudaDeviceReset afterwards (the kept address would be stale).  All
+ * calls share the one scratch array, which keeps the last call's partial sums:
+ * calls whose work can overlap on the GPU (different streams with no ordering
+ * between them) race, so order them.  Errors are reported through
  * hmc_last_error(NULL). */
 hmc_status hmc_stress_noalloc(const uint16_t *d_spins, const float *d_u, const float *d_ctab,
                               const double *strain_bar, int32_t nx, int32_t ny, int32_t nz, float *d_sigma,

@@ -86,6 +86,7 @@ def _load():
         "hmc_mpm_steps": (st, [H, C.c_int32, dp]),
         "hmc_compute_stress": (st, [H, dp, dp]),
         "hmc_sweep_half": (st, [H, C.c_int32, i64p]),
+        "hmc_sweep_half_margins": (st, [H, C.c_int32, dp, i64p]),
         "hmc_end_mcs": (st, [H]),
         "hmc_mc_sweeps": (st, [H, C.c_int32, i64p]),
         "hmc_texture_histogram": (st, [H, C.c_int32, C.c_int32, dp, i64p]),
@@ -220,6 +221,14 @@ def hmc_sweep_half(h, colour):
     a = np.zeros(1, dtype=np.int64)
     _check(h, lib.hmc_sweep_half(h, int(colour), _ptr(a, C.c_int64)))
     return int(a[0])
+
+
+def hmc_sweep_half_margins(h, colour, n_sites):
+    """(accepted, margin): margin[i] = (H - t) / max(1, |t|) of site i's elastic trial, NaN elsewhere."""
+    a = np.zeros(1, dtype=np.int64)
+    m = np.empty(n_sites)
+    _check(h, lib.hmc_sweep_half_margins(h, int(colour), _ptr(m, C.c_double), _ptr(a, C.c_int64)))
+    return int(a[0]), m
 
 
 def hmc_end_mcs(h):
@@ -397,6 +406,10 @@ class HMC:
 
     def sweep_half(self, colour):
         return hmc_sweep_half(self.h, colour)
+
+    def sweep_half_margins(self, colour):
+        acc, m = hmc_sweep_half_margins(self.h, colour, self.n_sites)
+        return acc, m.reshape(self.shape)
 
     def end_mcs(self):
         hmc_end_mcs(self.h)

@@ -61,6 +61,7 @@ struct hmc_handle {
     int nctas = 0;
     cudaStream_t stream = nullptr, cap = nullptr;
     bool own_stream = false, oriented = false;
+    bool lost = false;    // a sweep returned with its stress copy outstanding: every later call is refused
     int num_sms = 0;
     size_t tsize = 4;
     // device buffers
@@ -290,7 +291,7 @@ cudaError_t enqueue_stress(hmc_handle *h, bool store, cudaStream_t s) {
 }
 
 template <typename T>
-cudaError_t enqueue_sweep(hmc_handle *h, int colour, cudaStream_t s) {
+hmc::SweepArgs<T> sweep_args(hmc_handle *h) {
     hmc::SweepArgs<T> a;
     a.reps = h->d_reps;
     a.cta_rep = h->d_cta_rep;
@@ -310,7 +311,14 @@ cudaError_t enqueue_sweep(hmc_handle *h, int colour, cudaStream_t s) {
     a.u = static_cast<const T *>(h->u[h->cur]);
     a.skip_copy = fault("sweep_wait") ? 1 : 0;
     a.nrep = h->R;
+    a.margin = nullptr;
     a.rep0 = h->rep0;
+    return a;
+}
+
+template <typename T>
+cudaError_t enqueue_sweep(hmc_handle *h, int colour, cudaStream_t s) {
+    hmc::SweepArgs<T> a = sweep_args<T>(h);
     const bool point = h->p.elastic == HMC_ELASTIC_TRACTION || h->p.elastic == HMC_ELASTIC_STRAIN;
     if (h->p.elastic != HMC_ELASTIC_ZONE1) {
         const int mode = h->p.elastic == HMC_ELASTIC_TRACTION ? hmc::SWEEP_POINT
@@ -391,6 +399,13 @@ hmc_status read_accepted(hmc_handle *h, int64_t *acc) {
     for (auto x : a) s += (int64_t)x;
     *acc = s;
     for (int r = 0; r < h->R; ++r)
+        if (late[r] == 2) {
+            h->lost = true;
+            return fail(h, HMC_ERR_TIMEOUT, "a sweep's stress copy never completed in replica " + std::to_string(r) +
+                                                "; shared memory of later kernels may have been overwritten, so the "
+                                                "handle refuses every further call: destroy it");
+        }
+    for (int r = 0; r < h->R; ++r)
         if (late[r]) {
             // reported once: the sweep that gave up changed nothing, and later sweeps start clean
             HMC_CK(h, cudaMemset2DAsync(&h->st->wait_timeout, sizeof(DevState), 0, sizeof(int32_t), h->R, h->stream),
@@ -404,6 +419,7 @@ hmc_status read_accepted(hmc_handle *h, int64_t *acc) {
 
 hmc_status need_oriented(hmc_handle *h) {
     if (!h) return HMC_ERR_ARG;
+    if (h->lost) return fail(h, HMC_ERR_STATE, "a sweep returned with its stress copy outstanding; destroy the handle");
     if (!h->oriented) return fail(h, HMC_ERR_STATE, "hmc_set_orientations has not been called");
     return HMC_OK;
 }
@@ -680,6 +696,10 @@ hmc_status read_stats(hmc_handle *h, double *mean, double *energy) {
     DevState st;
     HMC_CK(h, cudaMemcpyAsync(&st, sel_st(h), sizeof(st), cudaMemcpyDeviceToHost, h->stream), "state download");
     HMC_CK(h, cudaStreamSynchronize(h->stream), "sync");
+    if (st.wait_timeout == 2) {
+        h->lost = true;
+        return fail(h, HMC_ERR_TIMEOUT, "a sweep's stress copy never completed; the handle refuses every further call");
+    }
     if (st.wait_timeout) {
         HMC_CK(h, cudaMemsetAsync(&sel_st(h)->wait_timeout, 0, sizeof(int32_t), h->stream), "memset");
         return fail(h, HMC_ERR_TIMEOUT, "a sweep's stress copy did not complete");
@@ -1209,6 +1229,42 @@ hmc_status hmc_sweep_half(hmc_handle *h, int32_t colour, int64_t *accepted) {
     HMC_CK(h, reset_accepted(h), "memset");
     HMC_CK(h, enq_sweep(h, colour, h->stream), "sweep launch");
     if (accepted) return read_accepted(h, accepted);
+    return HMC_OK;
+}
+
+hmc_status hmc_sweep_half_margins(hmc_handle *h, int32_t colour, double *margin, int64_t *accepted) {
+    if (h) ++h->state_version;
+    hmc_status s = need_oriented(h);
+    if (s != HMC_OK) return s;
+    if (colour != 0 && colour != 1) return fail(h, HMC_ERR_ARG, "colour must be 0 or 1");
+    if (!margin) return fail(h, HMC_ERR_ARG, "NULL margin");
+    if (h->R != 1) return fail(h, HMC_ERR_ARG, "hmc_sweep_half_margins takes a single-replica handle");
+    if (!sweeps_read_stress(h))
+        return fail(h, HMC_ERR_ARG, "hmc_sweep_half_margins needs a point-zone elastic term and store_stress = 1");
+    const size_t bytes = sizeof(double) * (size_t)h->N_total;
+    double *d = nullptr;
+    HMC_CK(h, cudaMalloc(&d, bytes), "margin buffer");
+    cudaError_t e = cudaMemsetAsync(d, 0xff, bytes, h->stream);   // all-ones words: NaN
+    if (e == cudaSuccess) e = reset_accepted(h);
+    if (e == cudaSuccess) {
+        const int mode = h->p.elastic == HMC_ELASTIC_STRAIN ? hmc::SWEEP_STRAIN : hmc::SWEEP_POINT;
+        if (h->p.precision == HMC_FP32) {
+            hmc::SweepArgs<float> a = sweep_args<float>(h);
+            a.margin = d;
+            e = hmc::launch_sweep_margin<float>(a, colour, mode, h->stream);
+        } else {
+            hmc::SweepArgs<double> a = sweep_args<double>(h);
+            a.margin = d;
+            e = hmc::launch_sweep_margin<double>(a, colour, mode, h->stream);
+        }
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(margin, d, bytes, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(d);
+    if (e != cudaSuccess) return cuda_fail(h, e, "margin sweep");
+    int64_t acc = 0;
+    if ((s = read_accepted(h, &acc)) != HMC_OK) return s;
+    if (accepted) *accepted = acc;
     return HMC_OK;
 }
 

@@ -146,6 +146,8 @@ struct SweepArgs {
     int skip_copy;                   // fault injection: the stored-stress copy is never started, so its
                                      // bounded wait runs out (HMC_FAULT=sweep_wait)
     int nrep;                        // replicas; with one, the kernels read rep0 below
+    double *margin;                  // margin form: (H - t) / max(1, |t|) of every trial evaluated with
+                                     // the elastic term, natural site order (others untouched)
     Replica rep0;                    // replica 0's descriptor, passed by value
 };
 
@@ -186,6 +188,10 @@ template <typename T>
 cudaError_t launch_stress(const StressArgs<T> &a, bool store, cudaStream_t s);   // store = 0: reductions only
 template <typename T>
 cudaError_t launch_sweep(const SweepArgs<T> &a, int colour, int mode, bool recompute, cudaStream_t s);
+// the stored-stress point-zone sweep of a single replica that also writes every evaluated
+// trial's distance to its Metropolis threshold to a.margin (mode SWEEP_POINT or SWEEP_STRAIN)
+template <typename T>
+cudaError_t launch_sweep_margin(const SweepArgs<T> &a, int colour, int mode, cudaStream_t s);
 template <typename T>
 cudaError_t launch_zone(const ZoneArgs<T> &a, int grid, cudaStream_t s);
 template <typename T>

@@ -11,11 +11,15 @@
 //
 // Limits and sharing: the array holds NOALLOC_MAX_CTAS partial-sum slots of
 // 8 doubles (512 KiB, resident on every GPU that loads the library until the
-// process exits); one CTA covers 256 cells of 2x2x2 points, so grids above
-// 2,097,152 cells (16,777,216 points, e.g. 256^3) are rejected.  Every call
-// uses the same array and leaves its partial sums there; each call overwrites
-// every slot it reads, so nothing has to start at zero, but two calls whose
-// work overlaps on the GPU (different streams, no ordering) race on the array.
+// process exits); one CTA covers 256 cells of 2x2x2 points, so grids of up to
+// 2,097,152 cells (16,777,216 points) are served -- 256^3 is the largest cube
+// accepted -- and larger ones are rejected.  Every call uses the same array and
+// leaves its partial sums there; each call overwrites every slot it reads, so
+// nothing has to start at zero, but two calls whose work overlaps on the GPU
+// (different streams, no ordering) race on the array.  The array's device
+// address is looked up once per device and kept for the life of the process,
+// which assumes the device's primary context and no cudaDeviceReset after the
+// first call.
 #include <cmath>
 #include <mutex>
 #include <string>

@@ -265,6 +265,7 @@ __device__ __forceinline__ bool metropolis(const SweepArgs<T> &a, int dE, T dHe,
 // ---------------------------------------------------------------------------
 constexpr long long WAIT_NS = 1000000000ll;      // a wait not over after 1 s is a failure
 constexpr int WAIT_POLLS = 1 << 24;              // backstop on the number of polls
+constexpr int DRAIN_WAITS = 20;                  // further limits a timed-out CTA waits for its copy
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ void mbar_init(unsigned long long *b, unsigned count) {
@@ -334,8 +335,9 @@ constexpr int flat_min_ctas() {
 }
 
 // ONE: a single replica, whose descriptor is read from the kernel argument (no dependent
-// loads before the tile's copy and spin loads can start)
-template <typename T, int MODE, bool RECOMP, int COL, bool ONE>
+// loads before the tile's copy and spin loads can start).  MARGIN: also write each elastic
+// trial's (H - t) / max(1, |t|) to a.margin (a diagnostic form; the decisions are the same).
+template <typename T, int MODE, bool RECOMP, int COL, bool ONE, bool MARGIN = false>
 __global__ void __launch_bounds__(SWEEP_CTA, flat_min_ctas<T, MODE, RECOMP>())
     k_sweep(const __grid_constant__ SweepArgs<T> a) {
     constexpr bool ELASTIC = MODE == SWEEP_POINT || MODE == SWEEP_STRAIN;   // a point-zone elastic term
@@ -489,10 +491,24 @@ __global__ void __launch_bounds__(SWEEP_CTA, flat_min_ctas<T, MODE, RECOMP>())
         if constexpr (STORED)
             if (tid == 0) ok = mbar_wait(&fs.bar, 0u);   // the tile's stress has landed
         if (__syncthreads_or(!ok)) {
-            // the copy did not complete: report, wait once more (bounded) for it, decide nothing
+            // The copy did not complete within the limit: report it and decide nothing.  No bulk
+            // copy may still be writing this CTA's shared memory when the CTA returns, or it
+            // would land in the shared memory of whichever CTA the SM runs next.  Either no copy
+            // was started (the injected fault, skip_copy), or thread 0 keeps waiting until the
+            // copy's mbarrier phase completes, which happens exactly when all its bytes have
+            // landed.  A copy of valid device memory always completes; only if it has not after
+            // DRAIN_WAITS further limits does the CTA return with it outstanding, and then it
+            // records wait_timeout = 2, which the host reports as a lost context (the handle
+            // refuses every later call).
             if (tid == 0) {
                 atomicExch(&R.st->wait_timeout, 1);
-                if constexpr (STORED) mbar_wait(&fs.bar, 0u);
+                if constexpr (STORED) {
+                    if (!a.skip_copy) {
+                        bool landed = false;
+                        for (int k = 0; k < DRAIN_WAITS && !landed; ++k) landed = mbar_wait(&fs.bar, 0u);
+                        if (!landed) atomicExch(&R.st->wait_timeout, 2);
+                    }
+                }
             }
             return;
         }
@@ -510,6 +526,18 @@ __global__ void __launch_bounds__(SWEEP_CTA, flat_min_ctas<T, MODE, RECOMP>())
             }
             const T dHe = trial_dhe<T, MODE, RECOMP>(a, R, qq & 0xffffu, qq >> 16, s);
             const bool acc = metropolis<T>(a, (int)(ow >> 8) - 8, dHe, sl.r1[wb + e]);
+            if constexpr (MARGIN) {
+                // the trial's site: block t0 + (owning thread), slot ow & 3 of the colour
+                int bx, by, bz;
+                block_xyz(R, t0 + (site >> 2), bx, by, bz);
+                const int L = slot_local(4 * COL + (int)(ow & 3u));
+                const long long x = 2 * bx + (L & 1), y = 2 * by + ((L >> 1) & 1), z = 2 * bz + (L >> 2);
+                const T H = rfma(a.J, (T)((int)(ow >> 8) - 8), dHe);
+                const T u01 = ((T)sl.r1[wb + e] + T(0.5)) * T(2.3283064365386963e-10);
+                const T t = a.kT > T(0) ? -a.kT * log_t(u01) : T(0);
+                const T den = fabs(t) > T(1) ? fabs(t) : T(1);
+                a.margin[x + (long long)R.nx * (y + (long long)R.ny * z)] = (double)((H - t) / den);
+            }
             sl.acc[site] = acc ? 1 : 0;
             dacc += acc ? 1u : 0u;
         }
@@ -612,6 +640,38 @@ cudaError_t sweep_prepare() {
     if ((e = set_flat_smem<double, SWEEP_STRAIN, true>()) != cudaSuccess) return e;
     return cudaSuccess;
 }
+
+template <typename T, int MODE, int COL>
+void launch_margin_form(const SweepArgs<T> &a, cudaStream_t s) {
+    k_sweep<T, MODE, false, COL, true, true><<<a.nctas * SPLIT, SWEEP_CTA, flat_smem_bytes<T, MODE, false>(), s>>>(a);
+}
+
+template <typename T, int MODE>
+cudaError_t set_margin_smem() {
+    const int bytes = (int)flat_smem_bytes<T, MODE, false>();
+    const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_sweep<T, MODE, false, 0, true, true>, at, bytes)) != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_sweep<T, MODE, false, 1, true, true>, at, bytes);
+}
+
+template <typename T>
+cudaError_t launch_sweep_margin(const SweepArgs<T> &a, int colour, int mode, cudaStream_t s) {
+    cudaError_t e;
+    if (mode == SWEEP_STRAIN) {
+        if ((e = set_margin_smem<T, SWEEP_STRAIN>()) != cudaSuccess) return e;
+        if (colour) launch_margin_form<T, SWEEP_STRAIN, 1>(a, s);
+        else launch_margin_form<T, SWEEP_STRAIN, 0>(a, s);
+    } else {
+        if ((e = set_margin_smem<T, SWEEP_POINT>()) != cudaSuccess) return e;
+        if (colour) launch_margin_form<T, SWEEP_POINT, 1>(a, s);
+        else launch_margin_form<T, SWEEP_POINT, 0>(a, s);
+    }
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_sweep_margin<float>(const SweepArgs<float> &, int, int, cudaStream_t);
+template cudaError_t launch_sweep_margin<double>(const SweepArgs<double> &, int, int, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_sweep(const SweepArgs<T> &a, int colour, int mode, bool recompute, cudaStream_t s) {

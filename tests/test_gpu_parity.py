@@ -301,3 +301,30 @@ def test_recomputed_strain_zone_matches_stored(G):
         res.append(g.spins().copy())
         g.close()
     assert (res[0] != res[1]).mean() <= 1e-4
+
+
+@pytest.mark.parametrize("elastic", [1, 3])
+def test_sweep_margins_match_the_oracle(G, elastic):
+    """hmc_sweep_half_margins (FP64): the same decisions as the plain half sweep, and for
+    every trial evaluated with the elastic term its (H - t) / max(1, |t|) equals the
+    oracle's to rounding; a trial is accepted exactly when that margin is <= 0."""
+    shape = (10, 18, 34)
+    g, o = make_pair(G, shape, 16, G.HMC_FP64, axis=(1, 1, 1.0), n_mpm=6, n_seeds=20, elastic=elastic)
+    o.mpm_steps(6)
+    sig = o.stress()
+    z, y, x = np.meshgrid(*[np.arange(n) for n in shape], indexing="ij")
+    for colour in (0, 1):
+        g.set_spins(o.spins)
+        g.set_stress(sig)
+        pre = o.spins.copy()
+        acc, m = g.sweep_half_margins(colour)
+        acc_o, changed, dH, t = o.half_sweep(colour)
+        assert acc == acc_o and (g.spins() == o.spins).all()
+        mask = ((x + y + z) & 1) == colour
+        ev = ~np.isnan(m)
+        assert ev.sum() > 0 and not (ev & ~mask).any()
+        want = (dH - t) / np.maximum(1.0, np.abs(t))
+        assert np.abs(m[ev] - want[ev]).max() < 1e-12
+        moved = o.spins != pre
+        assert (moved <= ev).all()                 # every change came from an evaluated trial
+        assert ((m[ev] <= 0) == moved[ev]).all()   # accepted exactly when the margin is <= 0

@@ -45,3 +45,61 @@ def test_texture_histograms():
     d = (246.5 - 147.3) * (246.5 + 2 * 147.3)
     S11 = (246.5 + 147.3) / d
     assert E.min() >= 1 / S11 - 1e-9
+
+
+def _rz(a):
+    c, s = np.cos(a), np.sin(a)
+    return np.array([[c, -s, 0.0], [s, c, 0.0], [0.0, 0.0, 1.0]])
+
+
+def _ry(b):
+    c, s = np.cos(b), np.sin(b)
+    return np.array([[c, 0.0, s], [0.0, 1.0, 0.0], [-s, 0.0, c]])
+
+
+def test_angle_to_nearest_100_rotation_about_z():
+    """Sec. "Results" (single-angle orientation set, load along x): a crystal turned by phi
+    about z has its [100] axis at phi and its [010] axis at 90 - phi from x, so the angle
+    to the nearest <100> is min(phi, 90 - phi)."""
+    phi = np.radians(np.arange(0, 90, 3) + 0.25)
+    A = np.stack([O.euler_to_A(p, 0.0, 0.0) for p in phi])
+    want = np.minimum(np.degrees(phi), 90.0 - np.degrees(phi))
+    assert np.allclose(O.angle_to_nearest_100(A, (1, 0, 0)), want, rtol=0, atol=1e-9)
+    assert np.allclose(O.angle_to_nearest_100(A, (0, 1, 0)), want, rtol=0, atol=1e-9)
+    # the z axis is a crystal <100> axis for every rotation about z
+    assert np.allclose(O.angle_to_nearest_100(A, (0, 0, 1)), 0.0, rtol=0, atol=1e-6)
+
+
+def test_angle_to_nearest_100_uses_crystal_axes_as_columns():
+    """A maps crystal-frame vectors to the sample frame (Eq. 18, z-y-z), so the crystal
+    axes in the sample frame are the columns of A: the cosine of the angle between the
+    load axis x and crystal axis j is A[0, j], the first ROW of A.  For Euler angles
+    (0.3, 0.7, 1.1) the first row and the first column give different angles (38.3
+    against 17.5 degrees), so taking rows for columns fails here."""
+    f, t, p = 0.3, 0.7, 1.1
+    cf, sf, ct, st, cp, sp = np.cos(f), np.sin(f), np.cos(t), np.sin(t), np.cos(p), np.sin(p)
+    # Rz(f) Ry(t) Rz(p) multiplied out by hand: first row and first column
+    row0 = np.array([cf * ct * cp - sf * sp, -cf * ct * sp - sf * cp, cf * st])
+    col0 = np.array([cf * ct * cp - sf * sp, sf * ct * cp + cf * sp, -st * cp])
+    A = _rz(f) @ _ry(t) @ _rz(p)
+    assert np.allclose(A[0], row0) and np.allclose(A[:, 0], col0)
+    want = np.degrees(np.arccos(np.abs(row0).max()))
+    wrong = np.degrees(np.arccos(np.abs(col0).max()))
+    assert abs(want - 38.2575) < 1e-3 and abs(wrong - 17.4598) < 1e-3
+    got = O.angle_to_nearest_100(O.euler_to_A(f, t, p)[None], (1, 0, 0))[0]
+    assert abs(got - want) < 1e-9
+    # the same angle from the crystal-frame direction cosines of the load axis, A^T x
+    l = A.T @ np.array([1.0, 0.0, 0.0])
+    assert abs(np.degrees(np.arccos(np.abs(l).max())) - got) < 1e-9
+
+
+def test_angle_histogram_of_the_z_rotation_set():
+    """ANGLE_100 fractions of 90 equal-volume orientations at phi = k + 1/2 degrees about
+    z, load along x: the angles are min(k + 1/2, 89.5 - k), so each 10-degree bin below
+    40 degrees holds 20 of them, the 40-50 bin 10, and the bins above 45 degrees none."""
+    eul = np.stack([np.radians(np.arange(90) + 0.5), np.zeros(90), np.zeros(90)], axis=1)
+    A, Ct, St = O.tables(eul, 246.5, 147.3, 124.7)
+    counts = np.full(90, 7, dtype=np.int64)
+    f = O.texture_histogram(1, 9, counts, A, St, (1, 0, 0), 246.5, 147.3, 124.7)
+    want = np.array([20, 20, 20, 20, 10, 0, 0, 0, 0]) / 90.0
+    assert np.array_equal(f, want)

@@ -71,3 +71,47 @@ def test_noalloc_stress_matches_handle_on_two_calls():
     assert e.value.status == G.HMC_ERR_ARG
     assert "limit" in G.hmc_last_error(None)
     g.close()
+
+
+def test_noalloc_stress_at_its_largest_grid():
+    """256^3 points fill every one of the 8 192 partial-sum slots of the fixed scratch
+    array: the call is accepted and equals the handle's stress pass on the same state."""
+    from conftest import build_libhmc
+    build_libhmc()
+    torch = pytest.importorskip("torch")
+    import hmc_synth as S
+    import oracle as O
+    import paper_1009_0457_gb300 as G
+
+    shape, Q = (256, 256, 256), 12
+    nz, ny, nx = shape
+    eul = S.euler_uniform_so3(Q, 5)
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    spins = ((x // 12 + 3 * (y // 20) + 5 * (z // 28)) % Q).astype(np.uint16)
+    g = G.HMC(shape, Q, precision=G.HMC_FP32, load_axis=(0.3, 0.4, 1.0), strain=2e-3, mpm_steps_per_mcs=0, **C3)
+    g.set_orientations(eul, spins)
+    rng = np.random.default_rng(8)
+    nn = (nx // 2) * (ny // 2) * (nz // 2)
+    u = (rng.standard_normal((nn, 3)) * 1e-3).astype(np.float32).astype(np.float64)
+    g.set_nodal(u, np.zeros_like(u))
+    mean_ref, W_ref = g.compute_stress()
+    sig_ref = g.stress()
+    E = g.strain()
+    _, Ct, _ = O.tables(eul, **C3)
+    dev = torch.device("cuda", 0)
+    N = spins.size
+    d_spins = torch.from_numpy(spins.reshape(-1).view(np.int16).copy()).to(dev)
+    d_ctab = torch.from_numpy(Ct.reshape(-1).astype(np.float32)).to(dev)
+    d_u = torch.from_numpy(u.reshape(-1).astype(np.float32)).to(dev)
+    d_sigma = torch.full((N * 6,), float("nan"), dtype=torch.float32, device=dev)
+    d_mean = torch.full((6,), float("nan"), dtype=torch.float64, device=dev)
+    d_energy = torch.full((1,), float("nan"), dtype=torch.float64, device=dev)
+    torch.cuda.synchronize()
+    G.hmc_stress_noalloc(d_spins.data_ptr(), d_u.data_ptr(), d_ctab.data_ptr(), E, nx, ny, nz,
+                         d_sigma.data_ptr(), d_mean.data_ptr(), d_energy.data_ptr(), None)
+    torch.cuda.synchronize()
+    sig = d_sigma.cpu().numpy().astype(np.float64).reshape(N, 6)
+    assert rel(sig, sig_ref) < 2e-6
+    assert rel(d_mean.cpu().numpy(), mean_ref) < 2e-6
+    assert abs(d_energy.item() - W_ref) < 2e-6 * abs(W_ref)
+    g.close()
