@@ -357,6 +357,7 @@ def run_ours(args):
     for _ in range(3):
         assert G.lib.hmc_compute_stress(h.h, None, None) == 0
         t_sweep += [timed(lambda c=c: G.lib.hmc_sweep_half(h.h, c, None)) for c in (0, 1)]
+    t_red, t_black = statistics.median(t_sweep[0::2]), statistics.median(t_sweep[1::2])
     t_sweep = statistics.median(t_sweep)
     mcs_ms = 1e3 * t / args.steps
     sum_ms = 1e3 * (spec["mpm_steps"] * t_mpm + t_stress + 2 * t_sweep)
@@ -453,6 +454,7 @@ def run_ours(args):
             "config": dict(workload_config(spec, args.workload), store_stress=args.store_stress),
             "mpm_cell_steps_per_s": N * ws / t_mpm, "mpm_ms_per_step": t_mpm * 1e3,
             "stress_ms": t_stress * 1e3, "half_sweep_ms": t_sweep * 1e3,
+            "red_half_sweep_ms": t_red * 1e3, "black_half_sweep_ms": t_black * 1e3,
             "roofline": roofline, "roofline_sweep": roofline_sweep,
             "e2e": e2e, "gpu_launches": launches, "clocks": clk, "fp64_form": fp64, "fp32_error": err32,
             "texture_angle100_10deg": texture, "ensemble": ens, "mcs_phases": mcs_phases, "cpu_baseline": cpu,

@@ -323,6 +323,7 @@ def test_sweep_margins_match_the_oracle(G, elastic):
         mask = ((x + y + z) & 1) == colour
         ev = ~np.isnan(m)
         assert ev.sum() > 0 and not (ev & ~mask).any()
+        dH, t = dH.reshape(shape), t.reshape(shape)
         want = (dH - t) / np.maximum(1.0, np.abs(t))
         assert np.abs(m[ev] - want[ev]).max() < 1e-12
         moved = o.spins != pre

@@ -42,7 +42,7 @@ def _pair_args(spec):
 def _oracle(spec, euler, spins):
     kw = _pair_args(spec)
     o = O.OracleHMC(spec["shape"], spec["Q"], **kw)
-    o.set_orientations(euler, spins)
+    o.set_orientations(euler, spins.copy())   # the oracle sweeps its spin array in place
     return o
 
 
@@ -80,7 +80,8 @@ def ni128():
         for colour in (0, 1):
             pre = o.spins.copy()
             acc, changed, dH, t = o.half_sweep(colour)
-            halves.append(dict(pre=pre, post=o.spins.copy(), acc=acc, dH=dH.copy(), t=t.copy()))
+            halves.append(dict(pre=pre, post=o.spins.copy(), acc=acc, dH=dH.reshape(spec["shape"]).copy(),
+                               t=t.reshape(spec["shape"]).copy()))
         o.end_mcs()
         rec.append(dict(sig=sig, halves=halves, ebar=o.Ebar.copy(), u=o.u.copy()))
     return spec, euler, spins, rec
