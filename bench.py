@@ -459,6 +459,7 @@ def run_ours(args):
             "e2e": e2e, "gpu_launches": launches, "clocks": clk, "fp64_form": fp64, "fp32_error": err32,
             "texture_angle100_10deg": texture, "ensemble": ens, "mcs_phases": mcs_phases, "cpu_baseline": cpu,
             "mpm_variant": mpm_variant_name(h.tuning()[0]), "mpm_grid": h.tuning()[1],
+            "sweep_cta": h.sweep_tuning()[0], "sweeps_read_stored_stress": h.sweep_tuning()[1],
         }
         print(json.dumps(line), flush=True)
     h.close()

@@ -124,7 +124,10 @@ typedef struct {
                                     stress of each non-trivial trial site from the
                                     nodal displacement (same arithmetic, same bits).
                                     The stored field is then refreshed only by
-                                    hmc_compute_stress.                              */
+                                    hmc_compute_stress.  2 (constant-traction point
+                                    zone): the autotuner picks 1 or 0 by timing both
+                                    forms at the first MPM use (the same bits either
+                                    way); other elastic terms treat 2 as 1.          */
 } hmc_params;
 
 /* Scalars the library derived from the parameters, and its counters. */
@@ -172,6 +175,15 @@ hmc_status hmc_select_replica(hmc_handle *h, int32_t r);
  * shapes of one Hooke variant give bit-identical results.  Environment
  * variable HMC_AUTOTUNE=0 keeps variant 0; HMC_MPM_SHAPE=<v> forces one. */
 hmc_status hmc_get_tuning(hmc_handle *h, int32_t *mpm_shape, int32_t *mpm_grid);
+
+/* The sweep choices of the autotuner, made at the same time (a library service with
+ * no counterpart in the paper): *sweep_cta (nullable) the threads per half-sweep CTA,
+ * 256 (one CTA per 256-block tile) or 128 (the tile split over two CTAs; the
+ * stored-stress point-zone and pure Potts forms); *stored (nullable) 1 if the stress
+ * pass of a Monte Carlo step stores the stress for the sweeps, 0 if the sweeps
+ * recompute it (store_stress = 2 lets the tuner choose).  Every choice gives the same
+ * results.  HMC_SWEEP_CTA=128|256 forces the CTA size. */
+hmc_status hmc_get_sweep_tuning(hmc_handle *h, int32_t *sweep_cta, int32_t *stored);
 
 /* Release the handle and all its device memory (NULL is a no-op). */
 void hmc_destroy(hmc_handle *h);

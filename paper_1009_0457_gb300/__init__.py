@@ -79,6 +79,7 @@ def _load():
         "hmc_create_batch": (st, [C.POINTER(hmc_params), C.c_int32, C.POINTER(H)]),
         "hmc_select_replica": (st, [H, C.c_int32]),
         "hmc_get_tuning": (st, [H, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+        "hmc_get_sweep_tuning": (st, [H, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
         "hmc_destroy": (None, [H]),
         "hmc_set_orientations": (st, [H, dp, u16p]),
         "hmc_set_spins": (st, [H, u16p]),
@@ -162,6 +163,13 @@ def hmc_create_batch(params):
 
 def hmc_select_replica(h, r):
     _check(h, lib.hmc_select_replica(h, int(r)))
+
+
+def hmc_get_sweep_tuning(h):
+    """(threads per sweep CTA, 1 if the sweeps read stored stress else 0)."""
+    c, st_ = C.c_int32(0), C.c_int32(0)
+    _check(h, lib.hmc_get_sweep_tuning(h, C.byref(c), C.byref(st_)))
+    return c.value, st_.value
 
 
 def hmc_get_tuning(h):
@@ -366,6 +374,9 @@ class HMC:
     def tuning(self):
         return hmc_get_tuning(self.h)
 
+    def sweep_tuning(self):
+        return hmc_get_sweep_tuning(self.h)
+
     def adjoint_forward(self, nsteps, checkpoint_every, want_field=True):
         return hmc_adjoint_forward(self.h, nsteps, checkpoint_every, self.n_sites if want_field else None)
 
@@ -516,6 +527,9 @@ class HMCBatch:
 
     def tuning(self):
         return hmc_get_tuning(self.h)
+
+    def sweep_tuning(self):
+        return hmc_get_sweep_tuning(self.h)
 
     def synchronize(self):
         hmc_synchronize(self.h)

@@ -34,7 +34,11 @@ int slot_local_h(int s) { static const int t[8] = {0, 3, 5, 6, 1, 2, 4, 7}; retu
 
 // Autotuner results, per batch signature, for the life of the process.
 std::mutex g_tune_mutex;
-std::map<std::string, std::pair<int, int>> g_tune_cache;
+struct TuneResult {
+    int mpm_shape, mpm_grid, sweep_cta;
+    bool store;
+};
+std::map<std::string, TuneResult> g_tune_cache;
 
 // Host view of one replica.
 struct RepHost {
@@ -95,6 +99,9 @@ struct hmc_handle {
     int mpm_shape = hmc::MPM_16x16, mpm_grid = 1;
     long long mpm_total = 0;
     bool tuned = false;
+    int sweep_cta = 256;                  // sweep threads per CTA (tuned)
+    bool store_eff = true;                // the step's stress pass stores the stress for the sweeps (tuned
+                                          // when store_stress = 2)
     // derived scalars
     double dt = 0, damping = 0, S11 = 0, S12 = 0, S44 = 0;
     // host tables (FP64)
@@ -311,6 +318,7 @@ hmc::SweepArgs<T> sweep_args(hmc_handle *h) {
     a.u = static_cast<const T *>(h->u[h->cur]);
     a.skip_copy = fault("sweep_wait") ? 1 : 0;
     a.nrep = h->R;
+    a.cta = h->sweep_cta;
     a.margin = nullptr;
     a.rep0 = h->rep0;
     return a;
@@ -324,7 +332,7 @@ cudaError_t enqueue_sweep(hmc_handle *h, int colour, cudaStream_t s) {
         const int mode = h->p.elastic == HMC_ELASTIC_TRACTION ? hmc::SWEEP_POINT
                          : h->p.elastic == HMC_ELASTIC_STRAIN ? hmc::SWEEP_STRAIN
                                                               : hmc::SWEEP_POTTS;
-        const bool recompute = point && !h->p.store_stress;
+        const bool recompute = point && !h->store_eff;
         return hmc::launch_sweep<T>(a, colour, mode, recompute, s);
     }
     // 27-point zone: list the trials, copy the spins as they are at the start of the half step,
@@ -363,7 +371,7 @@ cudaError_t enq_sweep(hmc_handle *h, int c, cudaStream_t s) {
 
 // The sweeps read the stored stress only with a point-zone elastic term and store_stress set.
 bool sweeps_read_stress(const hmc_handle *h) {
-    return (h->p.elastic == HMC_ELASTIC_TRACTION || h->p.elastic == HMC_ELASTIC_STRAIN) && h->p.store_stress;
+    return (h->p.elastic == HMC_ELASTIC_TRACTION || h->p.elastic == HMC_ELASTIC_STRAIN) && h->store_eff;
 }
 
 // One Monte Carlo step of every replica on stream s (also used while capturing the graph).
@@ -460,7 +468,7 @@ std::string validate(const hmc_params *p) {
     if (p->kT < 0) return "kT must be >= 0";
     if (p->bc != HMC_BC_UNIAXIAL && p->bc != HMC_BC_STRAIN6 && p->bc != HMC_BC_TRACTION) return "bad bc";
     if (!std::isfinite(p->stress)) return "non-finite stress";
-    if (p->store_stress != 0 && p->store_stress != 1) return "store_stress must be 0 or 1";
+    if (p->store_stress < 0 || p->store_stress > 2) return "store_stress must be 0, 1 or 2";
     if (p->elastic != HMC_ELASTIC_OFF && p->elastic != HMC_ELASTIC_TRACTION && p->elastic != HMC_ELASTIC_ZONE1 &&
         p->elastic != HMC_ELASTIC_STRAIN)
         return "bad elastic";
@@ -589,106 +597,215 @@ int grid_for_shape(hmc_handle *h, int shape, int per_sm_limit) {
 }
 
 std::string tune_signature(const hmc_handle *h) {
-    std::string s = std::to_string(h->p.precision) + ":" + std::to_string(h->num_sms);
+    std::string s = std::to_string(h->p.precision) + ":" + std::to_string(h->num_sms) + ":" +
+                    std::to_string(h->p.elastic) + ":" + std::to_string(h->p.store_stress) + ":" +
+                    std::to_string(h->p.n_orient);
     for (const auto &R : h->reps)
         s += ":" + std::to_string(R.nbx) + "x" + std::to_string(R.nby) + "x" + std::to_string(R.nbz);
     return s;
 }
 
 // Pick the MPM patch shape and persistent-grid size by timing every candidate
-// on scratch copies of the nodal state (the simulation state is not touched),
-// once per batch signature; HMC_AUTOTUNE=0 keeps the 16x16 default and
-// HMC_MPM_SHAPE forces one variant.  Every candidate computes bit-identical
-// results: the per-cell arithmetic (explicitly rounded, in one order, paired or
-// not) and the order of each node's force sum do not depend on the variant.
+// on scratch copies of the nodal state (the simulation state is not touched).
+// Every candidate computes bit-identical results: the per-cell arithmetic
+// (explicitly rounded, in one order, paired or not) and the order of each
+// node's force sum do not depend on the variant.
+hmc_status tune_mpm(hmc_handle *h, bool enabled, int &best_shape, int &best_grid) {
+    hmc_status s = HMC_OK;
+    best_shape = hmc::MPM_16x16;
+    if ((s = upload_sched(h, best_shape)) != HMC_OK) return s;
+    best_grid = grid_for_shape(h, best_shape, 0);
+    if (!enabled) return HMC_OK;
+    const size_t nb = node_bytes(h);
+    void *uo = nullptr, *vs = nullptr;
+    HMC_CK(h, cudaMalloc(&uo, nb), "autotune scratch");
+    if (cudaMalloc(&vs, nb) != cudaSuccess) {
+        cudaFree(uo);
+        return fail(h, HMC_ERR_OOM, "autotune scratch");
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    cudaError_t err = cudaMemcpyAsync(vs, h->v, nb, cudaMemcpyDeviceToDevice, h->stream);
+    const int nvariants = hmc::mpm_nvariants(h->p.precision == HMC_FP32);
+    for (int shape = 0; shape < nvariants && err == cudaSuccess && s == HMC_OK; ++shape) {
+        if ((s = upload_sched(h, shape)) != HMC_OK) break;
+        for (int lim : {0, 1}) {
+            const int grid = grid_for_shape(h, shape, lim);
+            if (lim == 1 && grid == grid_for_shape(h, shape, 0)) continue;
+            const int saved_grid = h->mpm_grid;
+            h->mpm_grid = grid;
+            auto launch = [&]() {
+                return h->p.precision == HMC_FP32
+                           ? hmc::launch_mpm_step<float>(mpm_args<float>(h, h->u[h->cur], uo, vs), shape, h->stream)
+                           : hmc::launch_mpm_step<double>(mpm_args<double>(h, h->u[h->cur], uo, vs), shape,
+                                                          h->stream);
+            };
+            err = launch();
+            if (err == cudaSuccess) err = cudaEventRecord(e0, h->stream);
+            for (int k = 0; k < 3 && err == cudaSuccess; ++k) err = launch();
+            if (err == cudaSuccess) err = cudaEventRecord(e1, h->stream);
+            if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+            float ms = 0;
+            if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+            h->mpm_grid = saved_grid;
+            if (err == cudaSuccess && ms < best) {
+                best = ms;
+                best_shape = shape;
+                best_grid = grid;
+            }
+            if (err != cudaSuccess) break;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamSynchronize(h->stream);
+    cudaFree(uo);
+    cudaFree(vs);
+    if (s != HMC_OK) return s;
+    if (err != cudaSuccess) return cuda_fail(h, err, "autotune");
+    return upload_sched(h, best_shape);
+}
+
+// Pick the sweep CTA size (256 threads per 256-block tile, or the tile split over two
+// CTAs of 128) and, with store_stress = 2 and the constant-traction point zone,
+// whether a Monte Carlo step stores every point's stress for the sweeps or the
+// sweeps recompute each trial site's stress from the nodal displacement.  Every
+// candidate gives the same decisions (the stored and recomputed forms evaluate the
+// same rounded arithmetic; the CTA size only changes which CTA decides a site), so
+// the choice never changes a result.  Each candidate is timed as a step runs it --
+// the stress pass (storing or not), the red and the black half sweep -- on a scratch
+// copy of the spins, with the stress written to scratch memory, so the simulation
+// state is not touched (only the acceptance counter, which every sweep resets).
+hmc_status tune_sweeps(hmc_handle *h, bool enabled) {
+    const bool point = h->p.elastic == HMC_ELASTIC_TRACTION || h->p.elastic == HMC_ELASTIC_STRAIN;
+    h->sweep_cta = 256;
+    h->store_eff = h->p.store_stress != 0;
+    if (!(point || h->p.elastic == HMC_ELASTIC_OFF)) return HMC_OK;   // the zone form lists trials
+    const bool auto_store = h->p.store_stress == 2 && h->p.elastic == HMC_ELASTIC_TRACTION;
+    if (!enabled || h->nblk_total < 256) return HMC_OK;
+    const size_t nsp = sizeof(uint4) * (size_t)h->nblk_total;
+    const size_t nsig = (size_t)48 * h->tsize * (size_t)h->nblk_total;
+    void *spn = nullptr, *sig = nullptr, *part = nullptr;
+    HMC_CK(h, cudaMalloc(&spn, nsp), "autotune scratch");
+    cudaError_t err = cudaMalloc(&sig, point ? nsig : 16);
+    if (err == cudaSuccess) err = cudaMalloc(&part, sizeof(double) * 7 * (size_t)h->nctas);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (err == cudaSuccess) err = cudaEventCreate(&e0);
+    if (err == cudaSuccess) err = cudaEventCreate(&e1);
+    float best = 1e30f;
+    int best_cta = 256;
+    bool best_store = h->store_eff;
+    for (int store = 1; store >= 0 && err == cudaSuccess; --store) {
+        if (!auto_store && store != (int)h->store_eff) continue;
+        for (int cta : {256, 128}) {
+            if (cta == 128 && point && !store) continue;   // the recomputing form has one CTA size
+            float t = 1e30f;
+            for (int rep = 0; rep < 3 && err == cudaSuccess; ++rep) {
+                err = cudaMemcpyAsync(spn, h->spins, nsp, cudaMemcpyDeviceToDevice, h->stream);
+                if (err == cudaSuccess) err = cudaEventRecord(e0, h->stream);
+                if (point && err == cudaSuccess) {
+                    auto stress = [&](auto tag) {
+                        using T = decltype(tag);
+                        hmc::StressArgs<T> a;
+                        a.reps = h->d_reps;
+                        a.cta_rep = h->d_cta_rep;
+                        a.spins = static_cast<const uint4 *>(spn);
+                        a.u = static_cast<const T *>(h->u[h->cur]);
+                        a.ctab = static_cast<const T *>(h->ctab);
+                        a.sig = static_cast<T *>(sig);
+                        a.partials = static_cast<double *>(part);
+                        a.nctas = h->nctas;
+                        return hmc::launch_stress<T>(a, store != 0, h->stream);
+                    };
+                    err = h->p.precision == HMC_FP32 ? stress(float()) : stress(double());
+                }
+                for (int c = 0; c < 2 && err == cudaSuccess; ++c) {
+                    auto sweep = [&](auto tag) {
+                        using T = decltype(tag);
+                        hmc::SweepArgs<T> a = sweep_args<T>(h);
+                        a.spins = static_cast<uint4 *>(spn);
+                        a.sig = static_cast<const T *>(sig);
+                        a.cta = cta;
+                        a.skip_copy = 0;
+                        const int mode = h->p.elastic == HMC_ELASTIC_TRACTION ? hmc::SWEEP_POINT
+                                         : h->p.elastic == HMC_ELASTIC_STRAIN ? hmc::SWEEP_STRAIN
+                                                                              : hmc::SWEEP_POTTS;
+                        return hmc::launch_sweep<T>(a, c, mode, point && !store, h->stream);
+                    };
+                    err = h->p.precision == HMC_FP32 ? sweep(float()) : sweep(double());
+                }
+                if (err == cudaSuccess) err = cudaEventRecord(e1, h->stream);
+                if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+                float ms = 0;
+                if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+                if (err == cudaSuccess && ms < t) t = ms;
+            }
+            if (err == cudaSuccess && t < best) {
+                best = t;
+                best_cta = cta;
+                best_store = store != 0;
+            }
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaStreamSynchronize(h->stream);
+    cudaFree(spn);
+    cudaFree(sig);
+    cudaFree(part);
+    if (err != cudaSuccess) return cuda_fail(h, err, "sweep autotune");
+    h->sweep_cta = best_cta;
+    h->store_eff = best_store;
+    return HMC_OK;
+}
+
+// The tuned launch configuration, once per handle at its first MPM use (before any graph
+// capture): cached per batch signature for the life of the process.  HMC_AUTOTUNE=0 keeps
+// the defaults (16x16 MPM patches, 256-thread sweep CTAs, stored stress in auto mode);
+// HMC_MPM_SHAPE=<variant> and HMC_SWEEP_CTA=128|256 force a choice.
 hmc_status ensure_tuned(hmc_handle *h) {
     if (h->tuned) return HMC_OK;
     hmc_status s = HMC_OK;
     const char *env = std::getenv("HMC_AUTOTUNE");
     const bool enabled = !(env && env[0] == '0');
-    // HMC_MPM_SHAPE=<variant> forces an MPM variant (with its default grid), bypassing the tuner
     const char *forced = std::getenv("HMC_MPM_SHAPE");
+    const char *forced_cta = std::getenv("HMC_SWEEP_CTA");
     const int nvar = hmc::mpm_nvariants(h->p.precision == HMC_FP32);
-    if (forced && forced[0] >= '0' && forced[0] < '0' + nvar && forced[1] == 0) {
-        const int shape = forced[0] - '0';
-        if ((s = upload_sched(h, shape)) != HMC_OK) return s;
-        h->mpm_shape = shape;
-        h->mpm_grid = grid_for_shape(h, shape, 0);
-        h->tuned = true;
-        return HMC_OK;
-    }
+    const bool force_mpm = forced && forced[0] >= '0' && forced[0] < '0' + nvar && forced[1] == 0;
+    const bool force_cta = forced_cta && (std::string(forced_cta) == "128" || std::string(forced_cta) == "256");
     const std::string sig = tune_signature(h);
-    {
+    if (!force_mpm && !force_cta) {
         std::lock_guard<std::mutex> lock(g_tune_mutex);
         auto it = g_tune_cache.find(sig);
         if (it != g_tune_cache.end()) {
-            if ((s = upload_sched(h, it->second.first)) != HMC_OK) return s;
-            h->mpm_shape = it->second.first;
-            h->mpm_grid = it->second.second;
+            if ((s = upload_sched(h, it->second.mpm_shape)) != HMC_OK) return s;
+            h->mpm_shape = it->second.mpm_shape;
+            h->mpm_grid = it->second.mpm_grid;
+            h->sweep_cta = it->second.sweep_cta;
+            h->store_eff = it->second.store;
             h->tuned = true;
             return HMC_OK;
         }
     }
-    int best_shape = hmc::MPM_16x16;
-    if ((s = upload_sched(h, best_shape)) != HMC_OK) return s;
-    int best_grid = grid_for_shape(h, best_shape, 0);
-    if (enabled) {
-        const size_t nb = node_bytes(h);
-        void *uo = nullptr, *vs = nullptr;
-        HMC_CK(h, cudaMalloc(&uo, nb), "autotune scratch");
-        if (cudaMalloc(&vs, nb) != cudaSuccess) {
-            cudaFree(uo);
-            return fail(h, HMC_ERR_OOM, "autotune scratch");
-        }
-        cudaEvent_t e0, e1;
-        cudaEventCreate(&e0);
-        cudaEventCreate(&e1);
-        float best = 1e30f;
-        cudaError_t err = cudaMemcpyAsync(vs, h->v, nb, cudaMemcpyDeviceToDevice, h->stream);
-        const int nvariants = hmc::mpm_nvariants(h->p.precision == HMC_FP32);
-        for (int shape = 0; shape < nvariants && err == cudaSuccess && s == HMC_OK; ++shape) {
-            if ((s = upload_sched(h, shape)) != HMC_OK) break;
-            for (int lim : {0, 1}) {
-                const int grid = grid_for_shape(h, shape, lim);
-                if (lim == 1 && grid == grid_for_shape(h, shape, 0)) continue;
-                const int saved_grid = h->mpm_grid;
-                h->mpm_grid = grid;
-                auto launch = [&]() {
-                    return h->p.precision == HMC_FP32
-                               ? hmc::launch_mpm_step<float>(mpm_args<float>(h, h->u[h->cur], uo, vs), shape, h->stream)
-                               : hmc::launch_mpm_step<double>(mpm_args<double>(h, h->u[h->cur], uo, vs), shape,
-                                                              h->stream);
-                };
-                err = launch();
-                if (err == cudaSuccess) err = cudaEventRecord(e0, h->stream);
-                for (int k = 0; k < 3 && err == cudaSuccess; ++k) err = launch();
-                if (err == cudaSuccess) err = cudaEventRecord(e1, h->stream);
-                if (err == cudaSuccess) err = cudaEventSynchronize(e1);
-                float ms = 0;
-                if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
-                h->mpm_grid = saved_grid;
-                if (err == cudaSuccess && ms < best) {
-                    best = ms;
-                    best_shape = shape;
-                    best_grid = grid;
-                }
-                if (err != cudaSuccess) break;
-            }
-        }
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
-        cudaStreamSynchronize(h->stream);
-        cudaFree(uo);
-        cudaFree(vs);
-        if (s != HMC_OK) return s;
-        if (err != cudaSuccess) return cuda_fail(h, err, "autotune");
-        if ((s = upload_sched(h, best_shape)) != HMC_OK) return s;
+    int shape = 0, grid = 1;
+    if (force_mpm) {
+        shape = forced[0] - '0';
+        if ((s = upload_sched(h, shape)) != HMC_OK) return s;
+        grid = grid_for_shape(h, shape, 0);
+    } else if ((s = tune_mpm(h, enabled, shape, grid)) != HMC_OK) {
+        return s;
     }
-    h->mpm_shape = best_shape;
-    h->mpm_grid = best_grid;
+    h->mpm_shape = shape;
+    h->mpm_grid = grid;
+    if ((s = tune_sweeps(h, enabled && !force_cta)) != HMC_OK) return s;
+    if (force_cta) h->sweep_cta = std::atoi(forced_cta);
     h->tuned = true;
-    std::lock_guard<std::mutex> lock(g_tune_mutex);
-    g_tune_cache[sig] = {best_shape, best_grid};
+    if (!force_mpm && !force_cta) {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        g_tune_cache[sig] = TuneResult{h->mpm_shape, h->mpm_grid, h->sweep_cta, h->store_eff};
+    }
     return HMC_OK;
 }
 
@@ -786,6 +903,7 @@ hmc_status hmc_create_batch(const hmc_params *params, int32_t n_replicas, hmc_ha
     if (!h) return fail(nullptr, HMC_ERR_OOM, "host allocation failed");
     const hmc_params *p = params;
     h->p = *p;
+    h->store_eff = p->store_stress != 0;   // auto (2) starts stored; the tuner may switch it
     h->R = n_replicas;
     h->tsize = p->precision == HMC_FP32 ? 4 : 8;
     const double lam_max = std::fmax(std::fmax(p->c11 + 2 * p->c12, p->c11 - p->c12), 2 * p->c44);
@@ -971,6 +1089,13 @@ hmc_status hmc_get_tuning(hmc_handle *h, int32_t *mpm_shape, int32_t *mpm_grid) 
     if (!h) return HMC_ERR_ARG;
     if (mpm_shape) *mpm_shape = h->mpm_shape;
     if (mpm_grid) *mpm_grid = h->mpm_grid;
+    return HMC_OK;
+}
+
+hmc_status hmc_get_sweep_tuning(hmc_handle *h, int32_t *sweep_cta, int32_t *stored) {
+    if (!h) return HMC_ERR_ARG;
+    if (sweep_cta) *sweep_cta = h->sweep_cta;
+    if (stored) *stored = h->store_eff ? 1 : 0;
     return HMC_OK;
 }
 

@@ -146,6 +146,8 @@ struct SweepArgs {
     int skip_copy;                   // fault injection: the stored-stress copy is never started, so its
                                      // bounded wait runs out (HMC_FAULT=sweep_wait)
     int nrep;                        // replicas; with one, the kernels read rep0 below
+    int cta;                         // threads per CTA: 256, or 128 (a tile split over two CTAs; the
+                                     // stored-stress point-zone and pure Potts forms)
     double *margin;                  // margin form: (H - t) / max(1, |t|) of every trial evaluated with
                                      // the elastic term, natural site order (others untouched)
     Replica rep0;                    // replica 0's descriptor, passed by value

@@ -37,13 +37,17 @@ namespace hmc {
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
-// threads (= blocks) of a sweep CTA: a tile of BLOCK_THREADS blocks may be split over SPLIT
-// CTAs (measured on the 256^3 workload: 256 threads 0.073 ms, 128 0.078 ms, 64 0.088 ms
-// per half sweep; the per-CTA costs outweigh the shorter barriers)
+// threads (= blocks) of a sweep CTA: a tile of BLOCK_THREADS blocks is one CTA of 256 threads
+// or split over two of 128 (a tuning knob of the stored-stress point-zone and pure Potts forms;
+// measured on the 256^3 workload: 256 threads 0.073 ms, 128 0.078 ms, 64 0.088 ms per half
+// sweep, the per-CTA costs outweighing the shorter barriers).  Decisions do not depend on it.
 constexpr int SWEEP_CTA = 256;
-constexpr int SPLIT = BLOCK_THREADS / SWEEP_CTA;
-static_assert(BLOCK_THREADS % SWEEP_CTA == 0, "tiles split evenly");
-static_assert(4 * SWEEP_CTA <= 1024, "a trial's thread and slot fit ten bits");
+template <int CTA>
+__host__ __device__ constexpr int split_of() {
+    static_assert(BLOCK_THREADS % CTA == 0, "tiles split evenly");
+    static_assert(4 * CTA <= 1024, "a trial's thread and slot fit ten bits");
+    return BLOCK_THREADS / CTA;
+}
 
 // Phi(q; sigma) = sum over the three crystal axes of p_m^2, p_m = a_m . sigma . a_m.
 // For one cubic material the zone energy w(q) = 1/2 sigma.S'(q).sigma =
@@ -102,13 +106,13 @@ __device__ __forceinline__ double log_t(double x) { return log(x); }
 // Shared-memory list of a CTA's trials that change the orientation (elastic modes):
 // the old and new orientation, the acceptance draw, the owning thread and slot with
 // the bond-count change, and (flat kernel) the site's stress or strain.
-template <typename T, bool SIG>
+template <typename T, bool SIG, int CTA>
 struct SweepList {
-    T sig[SIG ? 6 : 1][SIG ? 4 * SWEEP_CTA : 1];
-    uint32_t qq[4 * SWEEP_CTA];    // q | q_new << 16
-    uint32_t r1[4 * SWEEP_CTA];
-    uint16_t own[4 * SWEEP_CTA];   // lane << 2 | slot, bond change + 8 in bits 8..11
-    uint8_t acc[4 * SWEEP_CTA];    // decision by (thread, slot)
+    T sig[SIG ? 6 : 1][SIG ? 4 * CTA : 1];
+    uint32_t qq[4 * CTA];    // q | q_new << 16
+    uint32_t r1[4 * CTA];
+    uint16_t own[4 * CTA];   // lane << 2 | slot, bond change + 8 in bits 8..11
+    uint8_t acc[4 * CTA];    // decision by (thread, slot)
     unsigned nacc, done;           // acceptances of the CTA; warps finished
 };
 
@@ -311,24 +315,24 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned b
 // copy of the tile's stress of the colour into shared memory as the CTA begins;
 // only the listed trials read it, after the threads' own loads and arithmetic.
 // ---------------------------------------------------------------------------
-template <typename T, bool STORED>
+template <typename T, bool STORED, int CTA>
 struct FlatSmem;
-template <typename T>
-struct FlatSmem<T, false> {
-    SweepList<T, true> list;
+template <typename T, int CTA>
+struct FlatSmem<T, false, CTA> {
+    SweepList<T, true, CTA> list;
 };
-template <typename T>
-struct FlatSmem<T, true> {
-    T sig[6][4 * SWEEP_CTA];
-    SweepList<T, false> list;
+template <typename T, int CTA>
+struct FlatSmem<T, true, CTA> {
+    T sig[6][4 * CTA];
+    SweepList<T, false, CTA> list;
     unsigned long long bar;
 };
 
 // resident CTAs per SM the kernels are compiled for (measured on the 256^3 workload: six FP32
 // one-point-zone CTAs fit registers and shared memory but sweep slower than five)
-template <typename T, int MODE, bool RECOMP>
-constexpr int flat_min_ctas() {
-    return SPLIT * (sizeof(T) == 8 ? 2
+template <typename T, int MODE, bool RECOMP, int CTA>
+__host__ __device__ constexpr int flat_min_ctas() {
+    return split_of<CTA>() * (sizeof(T) == 8 ? 2
                     : RECOMP ? 3
                     : MODE == SWEEP_ZONE_LIST ? 4
                     : 5);
@@ -337,14 +341,15 @@ constexpr int flat_min_ctas() {
 // ONE: a single replica, whose descriptor is read from the kernel argument (no dependent
 // loads before the tile's copy and spin loads can start).  MARGIN: also write each elastic
 // trial's (H - t) / max(1, |t|) to a.margin (a diagnostic form; the decisions are the same).
-template <typename T, int MODE, bool RECOMP, int COL, bool ONE, bool MARGIN = false>
-__global__ void __launch_bounds__(SWEEP_CTA, flat_min_ctas<T, MODE, RECOMP>())
+template <typename T, int MODE, bool RECOMP, int COL, bool ONE, bool MARGIN = false, int CTA = SWEEP_CTA>
+__global__ void __launch_bounds__(CTA, flat_min_ctas<T, MODE, RECOMP, CTA>())
     k_sweep(const __grid_constant__ SweepArgs<T> a) {
+    constexpr int SPLIT = split_of<CTA>();
     constexpr bool ELASTIC = MODE == SWEEP_POINT || MODE == SWEEP_STRAIN;   // a point-zone elastic term
     constexpr bool STORED = ELASTIC && !RECOMP;                               // ... from the stored stress
     constexpr bool LIST = MODE == SWEEP_ZONE_LIST;
     extern __shared__ __align__(128) unsigned char sweep_smem[];
-    FlatSmem<T, STORED> &fs = *reinterpret_cast<FlatSmem<T, STORED> *>(sweep_smem);
+    FlatSmem<T, STORED, CTA> &fs = *reinterpret_cast<FlatSmem<T, STORED, CTA> *>(sweep_smem);
     auto &sl = fs.list;
     // the red half sweep follows the stress pass: its CTAs take the tiles in reverse order, so
     // that the first to run read the stress the pass wrote last, still in L2
@@ -353,7 +358,7 @@ __global__ void __launch_bounds__(SWEEP_CTA, flat_min_ctas<T, MODE, RECOMP>())
     const int r = ONE ? 0 : __ldg(a.cta_rep + tile);
     const Replica &R = ONE ? a.rep0 : a.reps[r];
     const int tid = threadIdx.x, lane = tid & 31;
-    const int t0 = (tile - R.cta_off) * BLOCK_THREADS + (bid % SPLIT) * SWEEP_CTA;
+    const int t0 = (tile - R.cta_off) * BLOCK_THREADS + (bid % SPLIT) * CTA;
     if (t0 >= R.nblk) return;  // the empty part of a replica's last tile
     const int blk = t0 + tid;  // block within the replica
     if (ELASTIC) {
@@ -363,7 +368,7 @@ __global__ void __launch_bounds__(SWEEP_CTA, flat_min_ctas<T, MODE, RECOMP>())
             if constexpr (STORED) {
                 // the colour's stress of the tile: six components, four values per block, each
                 // source a multiple of 16 B in address and size
-                const unsigned nb = (unsigned)min(SWEEP_CTA, R.nblk - t0);
+                const unsigned nb = (unsigned)min(CTA, R.nblk - t0);
                 mbar_init(&fs.bar, 1);
                 mbar_init_fence();
                 if (!a.skip_copy) {
@@ -573,7 +578,7 @@ __global__ void __launch_bounds__(SWEEP_CTA, flat_min_ctas<T, MODE, RECOMP>())
         if (lane == 0) {
             if (wt) atomicAdd(&sl.nacc, wt);
             __threadfence_block();
-            if (atomicAdd(&sl.done, 1u) == SWEEP_CTA / 32 - 1) {
+            if (atomicAdd(&sl.done, 1u) == CTA / 32 - 1) {
                 __threadfence_block();
                 const unsigned c = atomicAdd(&sl.nacc, 0u);
                 if (c) atomicAdd(&R.st->accepted, (unsigned long long)c);
@@ -581,30 +586,49 @@ __global__ void __launch_bounds__(SWEEP_CTA, flat_min_ctas<T, MODE, RECOMP>())
         }
         return;
     }
-    __shared__ unsigned warp_tot[SWEEP_CTA / 32];
+    __shared__ unsigned warp_tot[CTA / 32];
     const unsigned tot = __reduce_add_sync(FULL, (unsigned)nacc);
     if (lane == 0) warp_tot[tid >> 5] = tot;
     __syncthreads();
     if (tid == 0) {
         unsigned c = 0;
 #pragma unroll
-        for (int w = 0; w < SWEEP_CTA / 32; ++w) c += warp_tot[w];
+        for (int w = 0; w < CTA / 32; ++w) c += warp_tot[w];
         if (c) atomicAdd(&R.st->accepted, (unsigned long long)c);
     }
 }
 
-template <typename T, int MODE, bool RECOMP>
+template <typename T, int MODE, bool RECOMP, int CTA = SWEEP_CTA>
 constexpr size_t flat_smem_bytes() {
     constexpr bool ELASTIC = MODE == SWEEP_POINT || MODE == SWEEP_STRAIN;
-    return ELASTIC ? sizeof(FlatSmem<T, !RECOMP>) : 0;
+    return ELASTIC ? sizeof(FlatSmem<T, !RECOMP, CTA>) : 0;
+}
+
+// forms with the 128-thread CTA (a tile split over two CTAs) as a tuning choice
+template <int MODE, bool RECOMP>
+constexpr bool has_half_cta() {
+    return (MODE == SWEEP_POINT && !RECOMP) || MODE == SWEEP_POTTS;
+}
+
+template <typename T, int MODE, bool RECOMP, int COL, int CTA>
+void launch_flat_cta(const SweepArgs<T> &a, cudaStream_t s) {
+    constexpr int SPLIT = split_of<CTA>();
+    constexpr size_t smem = flat_smem_bytes<T, MODE, RECOMP, CTA>();
+    if (a.nrep == 1)
+        k_sweep<T, MODE, RECOMP, COL, true, false, CTA><<<a.nctas * SPLIT, CTA, smem, s>>>(a);
+    else
+        k_sweep<T, MODE, RECOMP, COL, false, false, CTA><<<a.nctas * SPLIT, CTA, smem, s>>>(a);
 }
 
 template <typename T, int MODE, bool RECOMP, int COL>
 void launch_flat(const SweepArgs<T> &a, cudaStream_t s) {
-    if (a.nrep == 1)
-        k_sweep<T, MODE, RECOMP, COL, true><<<a.nctas * SPLIT, SWEEP_CTA, flat_smem_bytes<T, MODE, RECOMP>(), s>>>(a);
-    else
-        k_sweep<T, MODE, RECOMP, COL, false><<<a.nctas * SPLIT, SWEEP_CTA, flat_smem_bytes<T, MODE, RECOMP>(), s>>>(a);
+    if constexpr (has_half_cta<MODE, RECOMP>()) {
+        if (a.cta == 128) {
+            launch_flat_cta<T, MODE, RECOMP, COL, 128>(a, s);
+            return;
+        }
+    }
+    launch_flat_cta<T, MODE, RECOMP, COL, SWEEP_CTA>(a, s);
 }
 
 template <typename T, int MODE, bool RECOMP>
@@ -615,15 +639,23 @@ void launch_form(const SweepArgs<T> &a, int colour, cudaStream_t s) {
         launch_flat<T, MODE, RECOMP, 0>(a, s);
 }
 
-template <typename T, int MODE, bool RECOMP>
-cudaError_t set_flat_smem() {
-    const int bytes = (int)flat_smem_bytes<T, MODE, RECOMP>();
+template <typename T, int MODE, bool RECOMP, int CTA>
+cudaError_t set_flat_smem_cta() {
+    const int bytes = (int)flat_smem_bytes<T, MODE, RECOMP, CTA>();
     const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_sweep<T, MODE, RECOMP, 0, false>, at, bytes)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(k_sweep<T, MODE, RECOMP, 1, false>, at, bytes)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(k_sweep<T, MODE, RECOMP, 0, true>, at, bytes)) != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_sweep<T, MODE, RECOMP, 1, true>, at, bytes);
+    if ((e = cudaFuncSetAttribute(k_sweep<T, MODE, RECOMP, 0, false, false, CTA>, at, bytes)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_sweep<T, MODE, RECOMP, 1, false, false, CTA>, at, bytes)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_sweep<T, MODE, RECOMP, 0, true, false, CTA>, at, bytes)) != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_sweep<T, MODE, RECOMP, 1, true, false, CTA>, at, bytes);
+}
+
+template <typename T, int MODE, bool RECOMP>
+cudaError_t set_flat_smem() {
+    cudaError_t e = set_flat_smem_cta<T, MODE, RECOMP, SWEEP_CTA>();
+    if constexpr (has_half_cta<MODE, RECOMP>())
+        if (e == cudaSuccess) e = set_flat_smem_cta<T, MODE, RECOMP, 128>();
+    return e;
 }
 
 }  // namespace
@@ -643,7 +675,8 @@ cudaError_t sweep_prepare() {
 
 template <typename T, int MODE, int COL>
 void launch_margin_form(const SweepArgs<T> &a, cudaStream_t s) {
-    k_sweep<T, MODE, false, COL, true, true><<<a.nctas * SPLIT, SWEEP_CTA, flat_smem_bytes<T, MODE, false>(), s>>>(a);
+    k_sweep<T, MODE, false, COL, true, true><<<a.nctas * split_of<SWEEP_CTA>(), SWEEP_CTA,
+                                               flat_smem_bytes<T, MODE, false>(), s>>>(a);
 }
 
 template <typename T, int MODE>
