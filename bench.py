@@ -649,7 +649,7 @@ def run_zone(args):
             "config": {"workload": "zone128: the 128^3 Ni polycrystal (Q=256, 5000 Voronoi grains, uniaxial 2e-3 "
                                    "along [001]) with the 27-point constant-traction zone, 50 MPM steps per MCS",
                        "sites": N},
-            "zone_half_sweep_ms": ms, "zone_trials_per_half_sweep": ntr,
+            "zone_half_sweep_ms": ms, "zone_trials_per_half_sweep": ntr, "zone_ns_per_trial": ms * 1e6 / ntr,
             "roofline": {"kernel": "k_zone<float> (27-point zone, one warp per trial)", "bound": "alu",
                          "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                          "traffic": kernel_traffic("zone"),

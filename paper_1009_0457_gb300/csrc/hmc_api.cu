@@ -82,7 +82,7 @@ struct hmc_handle {
     void *ktab = nullptr;
     void *stab = nullptr;                 // compliance rows (constant-strain zone)
     uint16_t *zone_sched = nullptr;
-    int zone_nsched = 0, zone_grid = 1;
+    int zone_nsched = 0, zone_grid = 1, zone_scatter_off = 0;
     // grain count: union-find parents of the largest replica, root count and error word
     unsigned *cc_parent = nullptr;
     unsigned long long *cc_count = nullptr;
@@ -354,6 +354,7 @@ cudaError_t enqueue_sweep(hmc_handle *h, int colour, cudaStream_t s) {
     z.count = h->zone_count;
     z.thr = h->thr;
     z.sched = h->zone_sched;
+    z.scatter = h->zone_sched + h->zone_scatter_off;
     z.nsched = h->zone_nsched;
     z.J = (T)h->p.J;
     z.kT = (T)h->p.kT;
@@ -1046,6 +1047,10 @@ hmc_status hmc_create_batch(const hmc_params *params, int32_t n_replicas, hmc_ha
         std::vector<uint16_t> zs = hmc::zone_schedule();
         if (zs.empty()) return bail(fail(h, HMC_ERR_CUDA, "zone schedule does not fit"));
         h->zone_nsched = (int)zs.size();
+        const std::vector<uint16_t> scat = hmc::zone_scatter_table(zs);
+        zs.resize((zs.size() + 7) & ~size_t(7), 0);   // the scatter table starts 16-byte aligned
+        h->zone_scatter_off = (int)zs.size();
+        zs.insert(zs.end(), scat.begin(), scat.end());
         Alloc za[] = {
             {(void **)&h->zone_work, sizeof(uint4) * 4 * (size_t)h->nblk_total, "zone trial list"},
             {(void **)&h->snap, sizeof(uint4) * (size_t)h->nblk_total, "spin copy"},

@@ -170,6 +170,7 @@ struct ZoneArgs {
     const unsigned *count;
     const unsigned long long *thr;
     const uint16_t *sched;           // elimination schedule (zone_schedule)
+    const uint16_t *scatter;         // element-matrix places per reflection and zone cell (zone_scatter_table)
     int nsched;
     T J, kT;
 };
@@ -200,6 +201,7 @@ template <typename T>
 int zone_per_sm();                 // resident zone CTAs per SM
 cudaError_t zone_prepare();        // opt the zone kernels into their dynamic shared memory
 std::vector<uint16_t> zone_schedule();   // empty if it does not fit the kernel's table
+std::vector<uint16_t> zone_scatter_table(const std::vector<uint16_t> &schedule);
 void zone_element_tables(const double *Cv, int Q, std::vector<double> &out);
 cudaError_t mpm_prepare();  // opt the MPM kernels into their dynamic shared memory (once, before any capture)
 cudaError_t sweep_prepare();  // opt the elastic sweeps into their shared memory

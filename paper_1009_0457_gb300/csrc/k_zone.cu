@@ -28,6 +28,8 @@
 // are read from the copy of the spins taken at the start of the half step, and
 // accepted trials are XOR-ed into the live spins (the old value is known).
 #include <algorithm>
+#include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "hmc_device.cuh"
@@ -60,7 +62,7 @@ struct ZoneCfg<double> {
 };
 
 __host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
-__host__ __device__ constexpr size_t zone_cta_bytes() { return align16((ZSCHED_CAP + 300) * sizeof(uint16_t)); }
+__host__ __device__ constexpr size_t zone_cta_bytes() { return align16(ZSCHED_CAP * sizeof(uint16_t)); }
 template <typename T>
 __host__ __device__ constexpr size_t zone_warp_bytes() {
     return align16((ZSLOT_CAP * ZBLK + 144 + 72) * sizeof(T) + 64 + 8 + 32 + 8);
@@ -70,6 +72,8 @@ __host__ __device__ constexpr size_t zone_smem() {
     return zone_cta_bytes() + ZoneCfg<T>::WARPS * zone_warp_bytes<T>();
 }
 
+__device__ __forceinline__ float zrsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double zrsqrt(double x) { return rsqrt(x); }
 __device__ __forceinline__ float zlog(float x) { return logf(x); }
 __device__ __forceinline__ double zlog(double x) { return log(x); }
 
@@ -122,7 +126,6 @@ __global__ void __launch_bounds__(32 * ZoneCfg<T>::WARPS, 2) k_zone(ZoneArgs<T> 
     constexpr unsigned FULL = 0xffffffffu;
     extern __shared__ __align__(16) unsigned char smem[];
     uint16_t *sch = reinterpret_cast<uint16_t *>(smem);
-    uint16_t *ep = sch + ZSCHED_CAP;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned char *wb = smem + zone_cta_bytes() + warp * zone_warp_bytes<T>();
     T *Kb = reinterpret_cast<T *>(wb);                     // block slots of the zone matrix
@@ -135,20 +138,7 @@ __global__ void __launch_bounds__(32 * ZoneCfg<T>::WARPS, 2) k_zone(ZoneArgs<T> 
     uint8_t *cend = plist + 32;                            // end of each cell's group in plist
 
     for (int i = threadIdx.x; i < a.nsched; i += blockDim.x) sch[i] = a.sched[i];
-    // element-matrix entry t (upper triangle of the 24 x 24, row-major) -> corners and components
-    for (int t = threadIdx.x; t < 300; t += blockDim.x) {
-        int e1 = 0, rem = t;
-        while (rem >= 24 - e1) {
-            rem -= 24 - e1;
-            ++e1;
-        }
-        const int e2 = e1 + rem;
-        ep[t] = (uint16_t)((e1 / 3) | ((e1 % 3) << 3) | ((e2 / 3) << 5) | ((e2 % 3) << 8));
-    }
     __syncthreads();
-    uint32_t epl[NJ];
-#pragma unroll
-    for (int j = 0; j < NJ; ++j) epl[j] = lane + 32 * j < 300 ? ep[lane + 32 * j] : 0u;
     // fixed DOFs: all of node A (order 0), y and z of node B, z of node C
     const int ordB = sch[1], ordC = sch[3];
     const unsigned n = *a.count;
@@ -162,6 +152,7 @@ __global__ void __launch_bounds__(32 * ZoneCfg<T>::WARPS, 2) k_zone(ZoneArgs<T> 
         const int x = p % nx, yz = p / nx, y = yz % ny, z = yz / ny;
         const int lox = (x - 1) >> 1, loy = (y - 1) >> 1, loz = (z - 1) >> 1;   // lowest zone node (may be -1)
         const int pcx = (x >> 1) - lox, pcy = (y >> 1) - loy, pcz = (z >> 1) - loz;   // site's zone cell
+        const int refl = pcx + 2 * pcy + 4 * pcz;                                      // its reflection
 
         // the zone's 27 points: orientation (start-of-step copy) and position in its cell
         uint32_t my_q = 0, my_pos = 0;
@@ -233,21 +224,14 @@ __global__ void __launch_bounds__(32 * ZoneCfg<T>::WARPS, 2) k_zone(ZoneArgs<T> 
 #pragma unroll
                 for (int j = 0; j < NJ; ++j) acc[j] += cur[j];
                 if (u + 1 == cn) {
-                    const uint8_t *dm = dmap + 8 * c;
+                    // the entries' places in the block slots for this reflection and zone cell
+                    // (zone_scatter_table; 0xffff: a fixed DOF)
+                    const uint16_t *sc = a.scatter + (size_t)(refl * 8 + c) * 320 + lane;
 #pragma unroll
                     for (int j = 0; j < NJ; ++j) {
                         if (lane + 32 * j >= 300) continue;
-                        const uint32_t pr = epl[j];
-                        int o1 = dm[pr & 7], a1 = (pr >> 3) & 3, o2 = dm[(pr >> 5) & 7], a2 = pr >> 8;
-                        const bool f1 = o1 == 0 || (o1 == ordB && a1 >= 1) || (o1 == ordC && a1 == 2);
-                        const bool f2 = o2 == 0 || (o2 == ordB && a2 >= 1) || (o2 == ordC && a2 == 2);
-                        if (f1 || f2) continue;
-                        if (o1 < o2 || (o1 == o2 && a1 < a2)) {
-                            const int to = o1, ta = a1;
-                            o1 = o2; a1 = a2; o2 = to; a2 = ta;
-                        }
-                        Kb[sch[ZS_BIDX + 27 * o1 + o2] * ZBLK + 4 * a1 + a2] += acc[j];
-                        acc[j] = T(0);
+                        const uint32_t off = __ldg(sc + 32 * j);
+                        if (off != 0xffffu) Kb[off] += acc[j];
                     }
 #pragma unroll
                     for (int j = 0; j < NJ; ++j) acc[j] = T(0);
@@ -269,21 +253,27 @@ __global__ void __launch_bounds__(32 * ZoneCfg<T>::WARPS, 2) k_zone(ZoneArgs<T> 
             ld4(Dk, r0);
             ld4(Dk + 4, r1v);
             ld4(Dk + 8, r2);
-            const T l00 = sqrt(r0[0]), i00 = T(1) / l00;
+            // the 3x3 diagonal factor from reciprocal square roots (one special-function
+            // operation per pivot instead of a square root and a division); the reciprocal
+            // pivots go to the rows' pad entries for the triangular solves below
+            const T a00 = r0[0], i00 = zrsqrt(a00), l00 = a00 * i00;
             const T l10 = r1v[0] * i00, l20 = r2[0] * i00;
-            const T l11 = sqrt(r1v[1] - l10 * l10), i11 = T(1) / l11;
+            const T a11 = r1v[1] - l10 * l10, i11 = zrsqrt(a11), l11 = a11 * i11;
             const T l21 = (r2[1] - l20 * l10) * i11;
-            const T l22 = sqrt(r2[2] - l20 * l20 - l21 * l21), i22 = T(1) / l22;
-            ok = ok && (l00 > T(0)) && (l11 > T(0)) && (l22 > T(0)) && (i00 < T(3.0e38)) && (i11 < T(3.0e38)) &&
+            const T a22 = r2[2] - l20 * l20 - l21 * l21, i22 = zrsqrt(a22), l22 = a22 * i22;
+            ok = ok && (a00 > T(0)) && (a11 > T(0)) && (a22 > T(0)) && (i00 < T(3.0e38)) && (i11 < T(3.0e38)) &&
                  (i22 < T(3.0e38));
             __syncwarp();
             if (lane == 0) {
                 Dk[0] = l00;
+                Dk[3] = i00;
                 Dk[4] = l10;
                 Dk[5] = l11;
+                Dk[7] = i11;
                 Dk[8] = l20;
                 Dk[9] = l21;
                 Dk[10] = l22;
+                Dk[11] = i22;
             }
             const int nb0 = sch[ZS_NBOFF + k], nb1 = sch[ZS_NBOFF + k + 1];
             for (int t = nb0 + lane; t < nb1; t += 32) {
@@ -317,7 +307,11 @@ __global__ void __launch_bounds__(32 * ZoneCfg<T>::WARPS, 2) k_zone(ZoneArgs<T> 
                     T v[4];
                     ld4(C + 4 * r, v);
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) v[c] -= li[r][0] * lj[c][0] + li[r][1] * lj[c][1] + li[r][2] * lj[c][2];
+                    for (int c = 0; c < 3; ++c) {
+                        v[c] = fma(-li[r][0], lj[c][0], v[c]);
+                        v[c] = fma(-li[r][1], lj[c][1], v[c]);
+                        v[c] = fma(-li[r][2], lj[c][2], v[c]);
+                    }
                     st4(C + 4 * r, v);
                 }
             }
@@ -351,9 +345,9 @@ __global__ void __launch_bounds__(32 * ZoneCfg<T>::WARPS, 2) k_zone(ZoneArgs<T> 
                 ld4(Ln, d0);
                 ld4(Ln + 4, d1);
                 ld4(Ln + 8, d2);
-                yv[3 * nn] = rhs[0] / d0[0];
-                yv[3 * nn + 1] = (rhs[1] - d1[0] * yv[3 * nn]) / d1[1];
-                yv[3 * nn + 2] = (rhs[2] - d2[0] * yv[3 * nn] - d2[1] * yv[3 * nn + 1]) / d2[2];
+                yv[3 * nn] = rhs[0] * d0[3];   // row pads hold the reciprocal pivots
+                yv[3 * nn + 1] = (rhs[1] - d1[0] * yv[3 * nn]) * d1[3];
+                yv[3 * nn + 2] = (rhs[2] - d2[0] * yv[3 * nn] - d2[1] * yv[3 * nn + 1]) * d2[3];
             }
 #pragma unroll
             for (int rrow = 0; rrow < 24; ++rrow) Ys[rrow * 6 + lane] = yv[rrow];
@@ -546,12 +540,146 @@ template cudaError_t launch_zone<double>(const ZoneArgs<double> &, int, cudaStre
 
 // ---- host tables --------------------------------------------------------------
 
+namespace {
+
+// Shared-memory layout of the factorisation.  A block's row r of slot s is the 16-byte
+// unit 3 s + r of the warp's block area, so the eight lanes of a quarter warp that load
+// row r of distinct blocks s hit distinct bank groups exactly when their s are distinct
+// mod 8 (3 is odd); lanes loading the same block share the access.  The cost of a layout
+// is the number of shared-memory wavefronts of the block loads and stores of the column
+// solves and the updates (32 lanes, four quarters per 16-byte access), with the slots of
+// the blocks and the order of each step's updates as the free choices; neither changes
+// any arithmetic (each block gets one update per step, and where it is stored does not
+// matter), so every layout gives the same bits.
+struct ZoneLayout {
+    std::vector<std::vector<int>> nb;                    // per step: column-block rows I
+    std::vector<std::vector<std::pair<int, int>>> up;    // per step: update blocks (I, J)
+    std::vector<int> slot_of;                            // 27 * I + J -> slot (-1 if structurally zero)
+};
+
+int quarter_wavefronts(const int *s, int n) {
+    // distinct slots per residue mod 8 among the quarter's lanes; the largest count
+    int cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0}, w = 0;
+    for (int i = 0; i < n; ++i) {
+        bool seen = false;
+        for (int j = 0; j < i; ++j) seen = seen || s[j] == s[i];
+        if (!seen) w = std::max(w, ++cnt[s[i] & 7]);
+    }
+    return w;
+}
+
+long step_cost(const ZoneLayout &L, int k) {
+    long c = 0;
+    int s[8];
+    const auto &u = L.up[k];
+    for (size_t q = 0; q < u.size(); q += 8) {
+        const int n = (int)std::min<size_t>(8, u.size() - q);
+        for (int which = 0; which < 3; ++which) {
+            for (int i = 0; i < n; ++i) {
+                const int I = u[q + i].first, J = u[q + i].second;
+                s[i] = L.slot_of[which == 0 ? 27 * I + J : which == 1 ? 27 * I + k : 27 * J + k];
+            }
+            c += quarter_wavefronts(s, n) * (which == 0 ? 4 : 3);   // C: 3 loads + 3 stores
+        }
+    }
+    const auto &b = L.nb[k];
+    for (size_t q = 0; q < b.size(); q += 8) {
+        const int n = (int)std::min<size_t>(8, b.size() - q);
+        for (int i = 0; i < n; ++i) s[i] = L.slot_of[27 * b[q + i] + k];
+        c += quarter_wavefronts(s, n) * 6;
+    }
+    return c;
+}
+
+// Simulated annealing over slot swaps and swaps of two updates of one step (fixed seed,
+// splitmix64; a few tenths of a second, once per process).
+void optimise_layout(ZoneLayout &L, int nslots) {
+    uint64_t st = 0x5EEDC0DE12345ull;
+    auto rnd = [&]() {
+        uint64_t z = (st += 0x9E3779B97F4A7C15ull);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return z ^ (z >> 31);
+    };
+    std::vector<std::vector<int>> steps_of(nslots);   // steps whose cost involves a slot
+    auto rebuild = [&]() {
+        for (auto &v : steps_of) v.clear();
+        for (int k = 0; k < 27; ++k) {
+            std::vector<int> ss;
+            for (auto &ij : L.up[k]) {
+                ss.push_back(L.slot_of[27 * ij.first + ij.second]);
+                ss.push_back(L.slot_of[27 * ij.first + k]);
+                ss.push_back(L.slot_of[27 * ij.second + k]);
+            }
+            for (int I : L.nb[k]) ss.push_back(L.slot_of[27 * I + k]);
+            std::sort(ss.begin(), ss.end());
+            ss.erase(std::unique(ss.begin(), ss.end()), ss.end());
+            for (int x : ss) steps_of[x].push_back(k);
+        }
+    };
+    rebuild();
+    std::vector<int> owner(nslots, -1);   // slot -> 27 I + J
+    for (int b = 0; b < 27 * 27; ++b)
+        if (L.slot_of[b] >= 0) owner[L.slot_of[b]] = b;
+    std::vector<long> cost(27);
+    for (int k = 0; k < 27; ++k) cost[k] = step_cost(L, k);
+    double T = 2.0;
+    for (int it = 0; it < 120000; ++it) {
+        if (rnd() & 1) {
+            const int a = (int)(rnd() % nslots), b = (int)(rnd() % nslots);
+            if (a == b || owner[a] < 0 || owner[b] < 0) continue;
+            std::vector<int> ks = steps_of[a];
+            ks.insert(ks.end(), steps_of[b].begin(), steps_of[b].end());
+            std::sort(ks.begin(), ks.end());
+            ks.erase(std::unique(ks.begin(), ks.end()), ks.end());
+            long before = 0, after = 0;
+            for (int k : ks) before += cost[k];
+            std::swap(L.slot_of[owner[a]], L.slot_of[owner[b]]);
+            std::vector<long> nc(ks.size());
+            for (size_t i = 0; i < ks.size(); ++i) after += (nc[i] = step_cost(L, ks[i]));
+            if (after <= before || (double)(rnd() >> 11) * 0x1.0p-53 < std::exp((before - after) / T)) {
+                std::swap(owner[a], owner[b]);
+                std::swap(steps_of[a], steps_of[b]);
+                for (size_t i = 0; i < ks.size(); ++i) cost[ks[i]] = nc[i];
+            } else {
+                std::swap(L.slot_of[owner[a]], L.slot_of[owner[b]]);
+            }
+        } else {
+            const int k = (int)(rnd() % 27);
+            const int n = (int)L.up[k].size();
+            if (n < 2) continue;
+            const int a = (int)(rnd() % n), b = (int)(rnd() % n);
+            if (a == b) continue;
+            std::swap(L.up[k][a], L.up[k][b]);
+            const long nc = step_cost(L, k);
+            if (nc <= cost[k] || (double)(rnd() >> 11) * 0x1.0p-53 < std::exp((cost[k] - nc) / T))
+                cost[k] = nc;
+            else
+                std::swap(L.up[k][a], L.up[k][b]);
+        }
+        T = std::max(0.05, T * 0.99995);
+    }
+}
+
+}  // namespace
+
 // Elimination schedule of the zone's 27 nodes in the reflected frame (the
 // site's cell = nodes with all coordinates in {1,2}); layout at the top of this
 // file.  Nodes share a block of K when they lie in a common zone cell
 // (Chebyshev distance <= 1); the symbolic factorisation adds the fill of each
-// step, and every block of the filled lower triangle gets a storage slot.
+// step, and every block of the filled lower triangle gets a storage slot, placed
+// (with the order of each step's updates) by optimise_layout to spread the lanes'
+// block accesses over the shared-memory banks.  Built once per process.
+std::vector<uint16_t> zone_schedule_build();
+
 std::vector<uint16_t> zone_schedule() {
+    static std::once_flag once;
+    static std::vector<uint16_t> table;
+    std::call_once(once, [] { table = zone_schedule_build(); });
+    return table;
+}
+
+std::vector<uint16_t> zone_schedule_build() {
     auto co = [](int n, int d) { return d == 0 ? n % 3 : d == 1 ? (n / 3) % 3 : n / 9; };
     auto cls = [&](int n) {
         const int a = co(n, 0), b = co(n, 1), c = co(n, 2);
@@ -590,13 +718,20 @@ std::vector<uint16_t> zone_schedule() {
     }
     std::vector<uint16_t> t(ZS_HDR, 0);
     for (int i = 0; i < 27; ++i) t[order[i]] = (uint16_t)i;
+    ZoneLayout L;
+    L.nb = nb;
+    L.up = up;
+    L.slot_of.assign(27 * 27, -1);
     int slots = 0;
     for (int I = 0; I < 27; ++I)
-        for (int J = 0; J < 27; ++J) t[ZS_BIDX + 27 * I + J] = 0xffff;
-    for (int I = 0; I < 27; ++I)
         for (int J = 0; J <= I; ++J)
-            if (pat[I][J]) t[ZS_BIDX + 27 * I + J] = (uint16_t)slots++;
+            if (pat[I][J]) L.slot_of[27 * I + J] = slots++;
     if (slots > ZSLOT_CAP) return {};
+    optimise_layout(L, slots);
+    up = L.up;
+    for (int I = 0; I < 27; ++I)
+        for (int J = 0; J < 27; ++J)
+            t[ZS_BIDX + 27 * I + J] = L.slot_of[27 * I + J] >= 0 ? (uint16_t)L.slot_of[27 * I + J] : (uint16_t)0xffff;
     for (int k = 0; k < 27; ++k) t[ZS_DIAG + k] = t[ZS_BIDX + 28 * k];
     size_t off = ZS_HDR;
     for (int k = 0; k <= 27; ++k) {
@@ -617,6 +752,40 @@ std::vector<uint16_t> zone_schedule() {
         }
     if (t.size() > (size_t)ZSCHED_CAP) return {};
     return t;
+}
+
+// Where each entry of a zone cell's summed element matrix goes in the block slots:
+// for reflection rf = pcx + 2 pcy + 4 pcz (the site's zone cell), zone cell c and
+// upper-triangle entry t of the 24 x 24 element matrix (element DOF 3 corner + alpha),
+// the float offset slot(o1, o2) * 12 + 4 a1 + a2 of its lower-triangle place, or 0xffff
+// when either DOF is one of the six held fixed.  Rows padded to 320 entries.
+std::vector<uint16_t> zone_scatter_table(const std::vector<uint16_t> &t) {
+    std::vector<uint16_t> out((size_t)64 * 320, 0xffff);
+    const int ordB = t[1], ordC = t[3];
+    for (int rf = 0; rf < 8; ++rf) {
+        const int pcx = rf & 1, pcy = (rf >> 1) & 1, pcz = rf >> 2;
+        for (int c = 0; c < 8; ++c) {
+            auto order_of = [&](int k) {
+                const int lx = (c & 1) + (k & 1), ly = ((c >> 1) & 1) + ((k >> 1) & 1), lz = (c >> 2) + (k >> 2);
+                const int rx = pcx ? lx : 2 - lx, ry = pcy ? ly : 2 - ly, rz = pcz ? lz : 2 - lz;
+                return (int)t[rx + 3 * ry + 9 * rz];
+            };
+            int e = 0;
+            for (int e1 = 0; e1 < 24; ++e1)
+                for (int e2 = e1; e2 < 24; ++e2, ++e) {
+                    int o1 = order_of(e1 / 3), a1 = e1 % 3, o2 = order_of(e2 / 3), a2 = e2 % 3;
+                    const bool f1 = o1 == 0 || (o1 == ordB && a1 >= 1) || (o1 == ordC && a1 == 2);
+                    const bool f2 = o2 == 0 || (o2 == ordB && a2 >= 1) || (o2 == ordC && a2 == 2);
+                    if (f1 || f2) continue;
+                    if (o1 < o2 || (o1 == o2 && a1 < a2)) {
+                        std::swap(o1, o2);
+                        std::swap(a1, a2);
+                    }
+                    out[(size_t)(rf * 8 + c) * 320 + e] = (uint16_t)(t[ZS_BIDX + 27 * o1 + o2] * ZBLK + 4 * a1 + a2);
+                }
+        }
+    }
+    return out;
 }
 
 // Element stiffness V B^T C'(q) B (V = 1 voxel) of a point at local position
