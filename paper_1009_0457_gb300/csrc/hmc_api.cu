@@ -1055,7 +1055,7 @@ hmc_status hmc_create_batch(const hmc_params *params, int32_t n_replicas, hmc_ha
             {(void **)&h->zone_work, sizeof(uint4) * 4 * (size_t)h->nblk_total, "zone trial list"},
             {(void **)&h->snap, sizeof(uint4) * (size_t)h->nblk_total, "spin copy"},
             {(void **)&h->zone_count, sizeof(unsigned), "zone trial count"},
-            {&h->ktab, h->tsize * 8 * 300 * (size_t)p->n_orient, "zone element tables"},
+            {&h->ktab, h->tsize * 8 * 320 * (size_t)p->n_orient, "zone element tables"},
             {(void **)&h->zone_sched, sizeof(uint16_t) * zs.size(), "zone schedule"},
         };
         for (auto &a : za)

@@ -49,6 +49,8 @@ constexpr int ZS_NBOFF = 27, ZS_UPOFF = 55, ZS_DIAG = 83, ZS_BIDX = 110, ZS_HDR 
 constexpr int ZSCHED_CAP = 4096;
 constexpr int ZSLOT_CAP = 232;   // 3x3 blocks of the filled lower triangle (226 for this pattern)
 constexpr int ZBLK = 12;         // a block: 3 rows of 4 values (the 4th pads a row to 16 B)
+constexpr int ZROW = 320;        // an element matrix's 300 upper-triangle entries, padded to 10 x 32
+constexpr int ZTRASH = (ZSLOT_CAP - 1) * ZBLK;   // an unused slot: target of the scatter's padding
 
 template <typename T>
 struct ZoneCfg;
@@ -206,41 +208,46 @@ __global__ void __launch_bounds__(32 * ZoneCfg<T>::WARPS, 2) k_zone(ZoneArgs<T> 
 
         // assembly: K = sum of B^T C' B over the zone's points (element tables per orientation and
         // position); the points of one zone cell share its DOF map, so they are summed in registers
-        // and scattered once per cell.  Loads of the next point are issued before the current sum.
+        // and scattered once per cell.  The element rows are read from L2 three points ahead of
+        // their sum (three register buffers in rotation), so that the loads overlap.
         {
-            T acc[NJ], cur[NJ], nxt[NJ];
+            T acc[NJ], b0[NJ], b1[NJ], b2[NJ];
 #pragma unroll
             for (int j = 0; j < NJ; ++j) acc[j] = T(0);
+            // element rows are padded with zeros to 320 entries, so every lane loads NJ of them
             auto fetch = [&](int s, T(&v)[NJ]) {
                 const uint32_t qs = __shfl_sync(FULL, my_q, s), pos = __shfl_sync(FULL, my_pos, s);
-                const T *ke = a.ktab + ((size_t)qs * 8 + pos) * 300 + lane;
+                const T *ke = a.ktab + ((size_t)qs * 8 + pos) * ZROW + lane;
 #pragma unroll
-                for (int j = 0; j < NJ; ++j) v[j] = (j < NJ - 1 || lane < 300 - 32 * (NJ - 1)) ? __ldg(ke + 32 * j) : T(0);
+                for (int j = 0; j < NJ; ++j) v[j] = __ldg(ke + 32 * j);
             };
-            fetch(plist[0], cur);
+            fetch(plist[0], b0);
+            fetch(plist[1], b1);
+            fetch(plist[2], b2);
             int c = 0, cn = cend[0];
-            for (int u = 0; u < 27; ++u) {
-                if (u + 1 < 27) fetch(plist[u + 1], nxt);
+            // add point u (held in buf), scatter when it closes its zone cell, refill buf with point u + 3
+            auto step = [&](int u, T(&buf)[NJ]) {
 #pragma unroll
-                for (int j = 0; j < NJ; ++j) acc[j] += cur[j];
+                for (int j = 0; j < NJ; ++j) acc[j] += buf[j];
+                if (u + 3 < 27) fetch(plist[u + 3], buf);
                 if (u + 1 == cn) {
                     // the entries' places in the block slots for this reflection and zone cell
-                    // (zone_scatter_table; 0xffff: a fixed DOF)
-                    const uint16_t *sc = a.scatter + (size_t)(refl * 8 + c) * 320 + lane;
+                    // (zone_scatter_table): padding entries and those of fixed DOFs go to the
+                    // unused last slot, so the scatter has no branches
+                    const uint16_t *sc = a.scatter + (size_t)(refl * 8 + c) * ZROW + lane;
 #pragma unroll
-                    for (int j = 0; j < NJ; ++j) {
-                        if (lane + 32 * j >= 300) continue;
-                        const uint32_t off = __ldg(sc + 32 * j);
-                        if (off != 0xffffu) Kb[off] += acc[j];
-                    }
+                    for (int j = 0; j < NJ; ++j) Kb[__ldg(sc + 32 * j)] += acc[j];
 #pragma unroll
                     for (int j = 0; j < NJ; ++j) acc[j] = T(0);
                     __syncwarp();
                     ++c;
                     cn = c < 8 ? cend[c] : 27;
                 }
-#pragma unroll
-                for (int j = 0; j < NJ; ++j) cur[j] = nxt[j];
+            };
+            for (int u = 0; u < 27; u += 3) {
+                step(u, b0);
+                step(u + 1, b1);
+                step(u + 2, b2);
             }
         }
         __syncwarp();
@@ -726,7 +733,7 @@ std::vector<uint16_t> zone_schedule_build() {
     for (int I = 0; I < 27; ++I)
         for (int J = 0; J <= I; ++J)
             if (pat[I][J]) L.slot_of[27 * I + J] = slots++;
-    if (slots > ZSLOT_CAP) return {};
+    if (slots > ZSLOT_CAP - 1) return {};   // the last slot stays free (ZTRASH)
     optimise_layout(L, slots);
     up = L.up;
     for (int I = 0; I < 27; ++I)
@@ -757,10 +764,11 @@ std::vector<uint16_t> zone_schedule_build() {
 // Where each entry of a zone cell's summed element matrix goes in the block slots:
 // for reflection rf = pcx + 2 pcy + 4 pcz (the site's zone cell), zone cell c and
 // upper-triangle entry t of the 24 x 24 element matrix (element DOF 3 corner + alpha),
-// the float offset slot(o1, o2) * 12 + 4 a1 + a2 of its lower-triangle place, or 0xffff
-// when either DOF is one of the six held fixed.  Rows padded to 320 entries.
+// the float offset slot(o1, o2) * 12 + 4 a1 + a2 of its lower-triangle place, or the
+// unused last slot when either DOF is one of the six held fixed.  Rows padded to 320
+// entries, the padding pointing at the unused slot as well.
 std::vector<uint16_t> zone_scatter_table(const std::vector<uint16_t> &t) {
-    std::vector<uint16_t> out((size_t)64 * 320, 0xffff);
+    std::vector<uint16_t> out((size_t)64 * ZROW, (uint16_t)ZTRASH);
     const int ordB = t[1], ordC = t[3];
     for (int rf = 0; rf < 8; ++rf) {
         const int pcx = rf & 1, pcy = (rf >> 1) & 1, pcz = rf >> 2;
@@ -781,7 +789,7 @@ std::vector<uint16_t> zone_scatter_table(const std::vector<uint16_t> &t) {
                         std::swap(o1, o2);
                         std::swap(a1, a2);
                     }
-                    out[(size_t)(rf * 8 + c) * 320 + e] = (uint16_t)(t[ZS_BIDX + 27 * o1 + o2] * ZBLK + 4 * a1 + a2);
+                    out[(size_t)(rf * 8 + c) * ZROW + e] = (uint16_t)(t[ZS_BIDX + 27 * o1 + o2] * ZBLK + 4 * a1 + a2);
                 }
         }
     }
@@ -790,9 +798,9 @@ std::vector<uint16_t> zone_scatter_table(const std::vector<uint16_t> &t) {
 
 // Element stiffness V B^T C'(q) B (V = 1 voxel) of a point at local position
 // pos = a + 2b + 4c of its cell, in element DOF order 3 corner + alpha, upper
-// triangle row-major (300 values), for every orientation.
+// triangle row-major (300 values, padded with zeros to ZROW), for every orientation.
 void zone_element_tables(const double *Cv, int Q, std::vector<double> &out) {
-    out.assign((size_t)Q * 8 * 300, 0.0);
+    out.assign((size_t)Q * 8 * ZROW, 0.0);
     for (int pos = 0; pos < 8; ++pos) {
         const int a = pos & 1, b = (pos >> 1) & 1, c = pos >> 2;
         double B[6][24] = {};
@@ -815,7 +823,7 @@ void zone_element_tables(const double *Cv, int Q, std::vector<double> &out) {
                     for (int k = 0; k < 6; ++k) s += C[6 * i + k] * B[k][e];
                     CB[i][e] = s;
                 }
-            double *o = &out[((size_t)q * 8 + pos) * 300];
+            double *o = &out[((size_t)q * 8 + pos) * ZROW];
             int t = 0;
             for (int e1 = 0; e1 < 24; ++e1)
                 for (int e2 = e1; e2 < 24; ++e2) {
