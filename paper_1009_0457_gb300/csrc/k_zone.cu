@@ -270,21 +270,10 @@ __global__ void __launch_bounds__(32 * ZoneCfg<T>::WARPS, 2) k_zone(ZoneArgs<T> 
             const T a22 = r2[2] - l20 * l20 - l21 * l21, i22 = zrsqrt(a22), l22 = a22 * i22;
             ok = ok && (a00 > T(0)) && (a11 > T(0)) && (a22 > T(0)) && (i00 < T(3.0e38)) && (i11 < T(3.0e38)) &&
                  (i22 < T(3.0e38));
-            __syncwarp();
-            if (lane == 0) {
-                Dk[0] = l00;
-                Dk[3] = i00;
-                Dk[4] = l10;
-                Dk[5] = l11;
-                Dk[7] = i11;
-                Dk[8] = l20;
-                Dk[9] = l21;
-                Dk[10] = l22;
-                Dk[11] = i22;
-            }
+            // column blocks (I, k): L_Ik = C_Ik L_kk^-T, from the factor each lane holds in registers
             const int nb0 = sch[ZS_NBOFF + k], nb1 = sch[ZS_NBOFF + k + 1];
             for (int t = nb0 + lane; t < nb1; t += 32) {
-                T *B = Kb + sch[t] * ZBLK;   // block (I, k): L_Ik = C_Ik L_kk^-T
+                T *B = Kb + sch[t] * ZBLK;
 #pragma unroll
                 for (int r = 0; r < 3; ++r) {
                     T v[4];
@@ -298,9 +287,29 @@ __global__ void __launch_bounds__(32 * ZoneCfg<T>::WARPS, 2) k_zone(ZoneArgs<T> 
                     st4(B + 4 * r, v);
                 }
             }
-            __syncwarp();
+            // the first update's target block is not touched by the column solves: read it now
             const int up0 = sch[ZS_UPOFF + k], up1 = sch[ZS_UPOFF + k + 1];
-            for (int t = up0 + 3 * lane; t < up1; t += 96) {
+            T cv[3][4];
+            if (up0 + 3 * lane < up1) {
+                const T *C = Kb + sch[up0 + 3 * lane] * ZBLK;
+#pragma unroll
+                for (int r = 0; r < 3; ++r) ld4(C + 4 * r, cv[r]);
+            }
+            __syncwarp();
+            // every lane has read the diagonal block: lane 0 stores its factor and reciprocal
+            // pivots (read again only by the triangular solve of Y, after the factorisation)
+            if (lane == 0) {
+                Dk[0] = l00;
+                Dk[3] = i00;
+                Dk[4] = l10;
+                Dk[5] = l11;
+                Dk[7] = i11;
+                Dk[8] = l20;
+                Dk[9] = l21;
+                Dk[10] = l22;
+                Dk[11] = i22;
+            }
+            for (int t = up0 + 3 * lane, first = 1; t < up1; t += 96, first = 0) {
                 T *C = Kb + sch[t] * ZBLK;
                 const T *LI = Kb + sch[t + 1] * ZBLK, *LJ = Kb + sch[t + 2] * ZBLK;
                 T li[3][4], lj[3][4];
@@ -309,17 +318,19 @@ __global__ void __launch_bounds__(32 * ZoneCfg<T>::WARPS, 2) k_zone(ZoneArgs<T> 
                     ld4(LI + 4 * r, li[r]);
                     ld4(LJ + 4 * r, lj[r]);
                 }
+                if (!first) {
+#pragma unroll
+                    for (int r = 0; r < 3; ++r) ld4(C + 4 * r, cv[r]);
+                }
 #pragma unroll
                 for (int r = 0; r < 3; ++r) {
-                    T v[4];
-                    ld4(C + 4 * r, v);
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
-                        v[c] = fma(-li[r][0], lj[c][0], v[c]);
-                        v[c] = fma(-li[r][1], lj[c][1], v[c]);
-                        v[c] = fma(-li[r][2], lj[c][2], v[c]);
+                        cv[r][c] = fma(-li[r][0], lj[c][0], cv[r][c]);
+                        cv[r][c] = fma(-li[r][1], lj[c][1], cv[r][c]);
+                        cv[r][c] = fma(-li[r][2], lj[c][2], cv[r][c]);
                     }
-                    st4(C + 4 * r, v);
+                    st4(C + 4 * r, cv[r]);
                 }
             }
             __syncwarp();
@@ -436,10 +447,12 @@ __global__ void __launch_bounds__(32 * ZoneCfg<T>::WARPS, 2) k_zone(ZoneArgs<T> 
             if (lane == k) mrow[6] = e0[k];
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
+            // pivot: the largest |entry| of column c in rows c..5, lowest row on ties; the rows live
+            // in lanes 0..5, so a butterfly over each group of eight lanes finds it in lanes 0..7
             T v = (lane >= c && lane < 6) ? fabs(mrow[c]) : T(-1);
             int piv = lane;
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
+            for (int o = 4; o > 0; o >>= 1) {
                 const T ov = __shfl_xor_sync(FULL, v, o);
                 const int op = __shfl_xor_sync(FULL, piv, o);
                 if (ov > v || (ov == v && op < piv)) {
@@ -448,17 +461,17 @@ __global__ void __launch_bounds__(32 * ZoneCfg<T>::WARPS, 2) k_zone(ZoneArgs<T> 
                 }
             }
             ok = ok && v > T(0);
+            // swap rows c and piv; the pivot row (now row c) is the one just read from lane piv
+            T prow[7];
 #pragma unroll
             for (int j = 0; j < 7; ++j) {
                 const T rc = __shfl_sync(FULL, mrow[j], c), rp = __shfl_sync(FULL, mrow[j], piv);
+                prow[j] = rp;
                 if (lane == c)
                     mrow[j] = rp;
                 else if (lane == piv)
                     mrow[j] = rc;
             }
-            T prow[7];
-#pragma unroll
-            for (int j = 0; j < 7; ++j) prow[j] = __shfl_sync(FULL, mrow[j], c);
             if (lane > c && lane < 6) {
                 const T f = mrow[c] / prow[c];
 #pragma unroll
