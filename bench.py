@@ -519,16 +519,24 @@ def fp32_error(G, spec, euler, spins, common):
         h32.close()
 
 
-def ensemble_measure(torch, G, S, steps, warmup, clocks_index=0):
+def ensemble_measure(torch, G, S, steps, warmup, clocks_index=0, rank=0, ws=1):
     """The batched ensemble (64 replicas of uneven size in one handle, every phase one
     launch over all replicas, one CUDA graph per MCS): site-updates/s over all replicas,
     the time of each phase launched on its own (50 MPM steps, stress pass with the
     end-of-step reduction, red and black half sweep) and what the graph saves or loses
-    against their sum (launch gaps)."""
+    against their sum (launch gaps).  With ws ranks, this rank takes its share of the
+    replicas (balanced by sites, replica ids kept) and the rates are this rank's."""
+    from paper_1009_0457_gb300.shard import balance_replicas
     specs, euler, fields = S.ensemble_inputs()
+    if ws > 1:
+        mine = balance_replicas([int(np.prod(sp["shape"])) for sp in specs], ws)[rank]
+        specs = [dict(sp, replica=r) for r, sp in enumerate(specs)]
+        specs, fields = [specs[r] for r in mine], [fields[r] for r in mine]
+    else:
+        specs = [dict(sp, replica=r) for r, sp in enumerate(specs)]
     stream = torch.cuda.Stream()
-    per = [dict(load_axis=sp["axis"], strain=sp["strain"], seed=sp["mc_seed"], replica=r)
-           for r, sp in enumerate(specs)]
+    per = [dict(load_axis=sp["axis"], strain=sp["strain"], seed=sp["mc_seed"], replica=sp["replica"])
+           for sp in specs]
     b = G.HMCBatch([sp["shape"] for sp in specs], specs[0]["Q"], per, precision=G.HMC_FP32,
                    mpm_steps_per_mcs=50, stream=stream.cuda_stream, **S.COMMON)
     try:
@@ -571,26 +579,45 @@ def ensemble_measure(torch, G, S, steps, warmup, clocks_index=0):
 
 
 def run_ensemble(args):
-    """The batched ensemble on its own: one JSON line (site-updates/s over all replicas)."""
+    """The batched ensemble on its own: one JSON line (site-updates/s over all replicas).
+    Under torchrun the replicas are shared out over the ranks (replicas only, no
+    collective on the data path): the job's rate is all ranks' site-updates over the
+    slowest rank's time, and the ensemble is the same 64 replicas at every N (strong
+    scaling)."""
     import torch
-    torch.cuda.set_device(0)
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
     import hmc_synth as S
     import paper_1009_0457_gb300 as G
-    e = ensemble_measure(torch, G, S, args.steps, args.warmup)
-    line = {"metric": METRIC, "value": e["value"], "unit": "site-updates/s", "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": e["ms_per_mcs"],
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": ENSEMBLE_WORKLOAD(S, e), "sites": e["sites"], "replicas": e["replicas"],
-                       "edges": e["edges"]},
-            "phases_ms": e["phases_ms"], "graph_minus_phases_fraction": e["graph_minus_phases_fraction"],
-            "mpm_variant": e["mpm_variant"], "mpm_grid": e["mpm_grid"], "gpu_launches": e["gpu_launches"],
-            "clocks": e["clocks"]}
-    print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    e = ensemble_measure(torch, G, S, args.steps, args.warmup, local, rank, ws)
+    t, units = dist_reduce(e["ms_per_mcs"] * args.steps / 1e3, e["sites"] * args.steps, "cuda")
+    if rank == 0:
+        line = {"metric": METRIC, "value": units / t, "unit": "site-updates/s", "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+                "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": ENSEMBLE_WORKLOAD(S, e), "sites": int(units / args.steps), "replicas": 64,
+                           "replicas_on_rank0": e["replicas"], "parallelism": f"replicas over {ws} ranks"},
+                "phases_ms": e["phases_ms"], "graph_minus_phases_fraction": e["graph_minus_phases_fraction"],
+                "mpm_variant": e["mpm_variant"], "mpm_grid": e["mpm_grid"], "gpu_launches": e["gpu_launches"],
+                "clocks": e["clocks"]}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
     return 0
 
 
 def ENSEMBLE_WORKLOAD(S, e):
-    return (f"ensemble: {e['replicas']} replicas, cubic edges from {S.ENSEMBLE_EDGES}, Q=256, axis uniform on S2, "
+    return (f"ensemble: 64 replicas, cubic edges from {S.ENSEMBLE_EDGES}, Q=256, axis uniform on S2, "
             f"strain U[5e-4, 3e-3], 50 MPM steps per MCS, FP32, one launch per phase over all replicas")
 
 

@@ -96,8 +96,8 @@ struct PlaneLoad {
 #pragma unroll
         for (int m = 0; m < PER; ++m) {
             const int t = threadIdx.x + m * NTHR;
-            if (t < NN)
-                us[t / NX][t % NX] = Vec4<T>{r[m][0] * T(0.03125), r[m][1] * T(0.03125), r[m][2] * T(0.03125), T(0)};
+            if (t < NN)   // node (t % NX, t / NX) of the row-major tile
+                (&us[0][0])[t] = Vec4<T>{r[m][0] * T(0.03125), r[m][1] * T(0.03125), r[m][2] * T(0.03125), T(0)};
         }
     }
 };
@@ -380,15 +380,21 @@ __global__ void __launch_bounds__(CX *CY, (sizeof(T) == 4 ? 2 : 1)) k_mpm_step(M
         __syncthreads();
 
         T acc[3] = {T(0), T(0), T(0)};
+        // this column's spins of the next plane, and its node's velocity and new displacement in
+        // the current plane, advanced by one plane per iteration
+        const uint4 *spn = a.spins + col + (long long)plane * k0;
+        T *vp = a.v + 3 * (col + (long long)plane * k0);
+        T *up = a.u_out + 3 * (col + (long long)plane * k0);
+        const long long pstride = 3ll * plane;
         for (int kk = k0 - 1; kk < kend; ++kk) {
             // one plane ahead: next plane's spins and u, this plane's owned velocity
             uint4 sp_next = make_uint4(0, 0, 0, 0);
-            if (need && kk + 1 < kend) sp_next = __ldg(a.spins + col + (long long)plane * (kk + 1));
+            if (need && kk + 1 < kend) sp_next = __ldg(spn);
+            spn += plane;
             T vold[3] = {T(0), T(0), T(0)};
-            const long long nidx = 3ll * (col + (long long)plane * (kk < 0 ? 0 : kk));
             if (own && kk >= k0) {
 #pragma unroll
-                for (int d = 0; d < 3; ++d) vold[d] = a.v[nidx + d];
+                for (int d = 0; d < 3; ++d) vold[d] = vp[d];
             }
             const bool more = kk + 1 < kend;
             if (more) pl.fetch(a.u_in, R.blk_off, kk + 2, nbz, plane);
@@ -430,9 +436,11 @@ __global__ void __launch_bounds__(CX *CY, (sizeof(T) == 4 ? 2 : 1)) k_mpm_step(M
 #pragma unroll
                     for (int d = 0; d < 3; ++d) {
                         const T vn = rfma(fscale, F[d], rmul(a.keep, vold[d]));
-                        a.v[nidx + d] = vn;
-                        a.u_out[nidx + d] = rfma(a.dt, vn, uc[d] * T(32));
+                        vp[d] = vn;
+                        up[d] = rfma(a.dt, vn, uc[d] * T(32));
                     }
+                    vp += pstride;
+                    up += pstride;
                 }
                 const Vec4<T> c3 = sm.ft[3][lcj - 1][lci - 1], c2 = sm.ft[2][lcj - 1][lci];
                 const Vec4<T> c1 = sm.ft[1][lcj][lci - 1], c0 = sm.ft[0][lcj][lci];

@@ -49,3 +49,44 @@ def test_two_gloo_ranks_reduce_time_and_work():
 def test_single_process_reduce_is_identity():
     import bench
     assert bench.dist_reduce(3.5, 7) == (3.5, 7.0)
+
+
+def _shard_worker(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import numpy as np
+    import hmc_synth as S
+    from paper_1009_0457_gb300.shard import balance_replicas
+    sites = [int(np.prod(sp["shape"])) for sp in S.ensemble_specs()]
+    mine = balance_replicas(sites, world)[rank]
+    parts = [None] * world
+    dist.all_gather_object(parts, mine)
+    loads = [None] * world
+    dist.all_gather_object(loads, sum(sites[r] for r in mine))
+    out[rank] = (parts, loads, max(sites), len(sites))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_ensemble_replicas_shared_out_over_gloo_ranks(world):
+    """Every rank computes its own share of the 64-replica ensemble; gathered, the shares
+    are disjoint, cover every replica once, agree between ranks and differ in sites by
+    at most one replica's."""
+    mgr = mp.Manager()
+    out = mgr.dict()
+    mp.spawn(_shard_worker, args=(world, _free_port(), out), nprocs=world, join=True)
+    parts, loads, biggest, n = out[0]
+    for r in range(world):
+        assert out[r][0] == parts and out[r][1] == loads
+    flat = sorted(x for p in parts for x in p)
+    assert flat == list(range(n))
+    assert max(loads) - min(loads) <= biggest
+
+
+def test_balance_replicas_single_rank_and_empty():
+    from paper_1009_0457_gb300.shard import balance_replicas
+    assert balance_replicas([5, 3, 9], 1) == [[0, 1, 2]]
+    assert balance_replicas([4, 4], 3) == [[0], [1], []]
+    with pytest.raises(ValueError):
+        balance_replicas([1], 0)
