@@ -49,6 +49,9 @@ MPM_FLOP_PER_POINT = 132
 MPM_BYTES_PER_POINT = {"f32": 8, "f64": 14}      # spin 2 + (u,v) read + (u,v) write, per point
 SWEEP_BYTES_PER_SITE = {"f32": 28, "f64": 52}    # spin read + write + stored stress read
 STRESS_BYTES_PER_SITE = {"f32": 27.5, "f64": 53}  # spin 2 + u read (per point) + stress write
+# plain FP64 step, per point: stress read (P2G) 48 + cell forces written and read 2 x 24 + node
+# u, v read and written 4 x 3 + stress read and written (G2P) 96 + spins 2 (once per kernel pair)
+PLAIN_BYTES_PER_POINT = 48 + 2 * 24 + 12 + 96 + 2
 CROP = 64
 ENSEMBLE_STEPS = 10
 
@@ -417,9 +420,26 @@ def run_ours(args):
         t64 = timed(lambda: G.lib.hmc_mc_sweeps(h64.h, k64, None))
         t64_mpm = timed(lambda: G.lib.hmc_mpm_steps(h64.h, 5, None)) / 5
         v64 = N * k64 / t64
-        fp64 = {"form": "the fused kernels instantiated in FP64 (not the unfused incremental form)",
-                "value": v64, "unit": "site-updates/s", "steps": k64, "speedup_fp32_over_fp64": value / ws / v64,
-                "mpm_cell_steps_per_s": N / t64_mpm, "mpm_ms_per_step": t64_mpm * 1e3}
+        # the plain form of the explicit step: unfused, incremental, FP64 (one call of 5 steps
+        # includes its total-form stress start, a sixth of a step's work)
+        G.lib.hmc_mpm_steps_plain(h64.h, 1)
+        h64.synchronize()
+        t_plain = timed(lambda: G.lib.hmc_mpm_steps_plain(h64.h, 5)) / 5
+        mcs_plain = t64 / k64 - spec["mpm_steps"] * t64_mpm + spec["mpm_steps"] * t_plain
+        fp64 = {"form": "the fused kernels instantiated in FP64", "value": v64, "unit": "site-updates/s",
+                "steps": k64, "speedup_fp32_over_fp64": value / ws / v64,
+                "mpm_cell_steps_per_s": N / t64_mpm, "mpm_ms_per_step": t64_mpm * 1e3,
+                "plain_unfused": {
+                    "form": "the explicit step in the plain form: unfused G2P/stress-increment, P2G and node kernels "
+                            "with every point's FP64 stress and every cell's corner forces in global memory "
+                            "(hmc_mpm_steps_plain)",
+                    "mpm_ms_per_step": t_plain * 1e3, "mpm_cell_steps_per_s": N / t_plain,
+                    "algorithmic_bytes_per_point_step": PLAIN_BYTES_PER_POINT,
+                    "mcs_ms": mcs_plain * 1e3,
+                    "mcs_composition": "the FP64 MCS with its 50 fused steps replaced by 50 plain steps",
+                    "site_updates_per_s": N / mcs_plain,
+                    "speedup_fp32_over_plain_fp64": value / ws / (N / mcs_plain),
+                    "mpm_speedup_fp32_over_plain_fp64": t_plain / t_mpm}}
         h64.close()
 
     # ---- error of the FP32 path against the FP64 path (outside the timed region) ----

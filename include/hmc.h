@@ -272,6 +272,20 @@ hmc_status hmc_sweep_half(hmc_handle *h, int32_t colour, int64_t *accepted);
  * NULL margin, or a handle whose sweeps do not read the stored stress. */
 hmc_status hmc_sweep_half_margins(hmc_handle *h, int32_t colour, double *margin, int64_t *accepted);
 
+/* The same explicit steps in the plain form of Sec. "Elastic Deformation", kept as
+ * the baseline the fused step is measured against: nodal velocities give each
+ * point's strain increment, Hooke's law (Eq. 1) updates the point's stress by it,
+ * and the stresses give the internal nodal forces -- three unfused kernels per step
+ * (forces per cell, node update, stress increments per cell) with every point's
+ * stress (6 doubles) and every cell's corner forces (24 doubles) stored in global
+ * memory between them.  Each call starts the point stresses from the total form
+ * C'(q)(Ebar + B u) of the current state, so while the spins are fixed it advances
+ * u and v as hmc_mpm_steps does, to FP64 rounding.  Single-replica FP64 handles
+ * only (HMC_ERR_ARG otherwise); the stress and force buffers (64 doubles per cell)
+ * are allocated by the first call and kept with the handle.  Stream-ordered; the
+ * stored stress that the sweeps read is not changed. */
+hmc_status hmc_mpm_steps_plain(hmc_handle *h, int32_t nsteps);
+
 /* Close a Monte Carlo step: with UNIAXIAL control update the mean strain from
  * the mean stress of the last hmc_compute_stress, then advance the counter. */
 hmc_status hmc_end_mcs(hmc_handle *h);

@@ -85,6 +85,7 @@ def _load():
         "hmc_set_spins": (st, [H, u16p]),
         "hmc_get_spins": (st, [H, u16p]),
         "hmc_mpm_steps": (st, [H, C.c_int32, dp]),
+        "hmc_mpm_steps_plain": (st, [H, C.c_int32]),
         "hmc_compute_stress": (st, [H, dp, dp]),
         "hmc_sweep_half": (st, [H, C.c_int32, i64p]),
         "hmc_sweep_half_margins": (st, [H, C.c_int32, dp, i64p]),
@@ -217,6 +218,10 @@ def hmc_mpm_steps(h, nsteps, want_energy=False):
     e = np.zeros(1) if want_energy else None
     _check(h, lib.hmc_mpm_steps(h, int(nsteps), _ptr(e, C.c_double)))
     return None if e is None else float(e[0])
+
+
+def hmc_mpm_steps_plain(h, nsteps):
+    _check(h, lib.hmc_mpm_steps_plain(h, int(nsteps)))
 
 
 def hmc_compute_stress(h):
@@ -411,6 +416,9 @@ class HMC:
 
     def mpm_steps(self, n, want_energy=False):
         return hmc_mpm_steps(self.h, n, want_energy)
+
+    def mpm_steps_plain(self, n):
+        hmc_mpm_steps_plain(self.h, n)
 
     def compute_stress(self):
         return hmc_compute_stress(self.h)

@@ -100,6 +100,7 @@ struct hmc_handle {
     long long mpm_total = 0;
     bool tuned = false;
     int sweep_cta = 256;                  // sweep threads per CTA (tuned)
+    double *plain_sig = nullptr, *plain_f = nullptr;   // the plain FP64 step's point stresses, cell forces
     bool store_eff = true;                // the step's stress pass stores the stress for the sweeps (tuned
                                           // when store_stress = 2)
     // derived scalars
@@ -525,7 +526,7 @@ void destroy_buffers(hmc_handle *h) {
     void *bufs[] = {h->spins, h->stage16, h->u[0], h->u[1], h->v, h->sig, h->ctab, h->cubw, h->wtab, h->atab, h->thr, h->counts,
                     h->bins, h->partials, h->fractions, h->binmap, h->st, h->d_reps, h->d_cta_rep, h->d_sched,
                     h->zone_work, h->snap, h->zone_count, h->ktab, h->zone_sched, h->cc_parent, h->cc_count,
-                    h->stab};
+                    h->stab, h->plain_sig, h->plain_f};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (h->cap) cudaStreamDestroy(h->cap);
@@ -1395,6 +1396,48 @@ hmc_status hmc_sweep_half_margins(hmc_handle *h, int32_t colour, double *margin,
     int64_t acc = 0;
     if ((s = read_accepted(h, &acc)) != HMC_OK) return s;
     if (accepted) *accepted = acc;
+    return HMC_OK;
+}
+
+hmc_status hmc_mpm_steps_plain(hmc_handle *h, int32_t nsteps) {
+    if (h) ++h->state_version;
+    hmc_status s = need_oriented(h);
+    if (s != HMC_OK) return s;
+    if (nsteps < 0) return fail(h, HMC_ERR_ARG, "nsteps < 0");
+    if (h->R != 1 || h->p.precision != HMC_FP64)
+        return fail(h, HMC_ERR_ARG, "hmc_mpm_steps_plain takes a single-replica FP64 handle");
+    const RepHost &R = h->reps[0];
+    if (!h->plain_sig) {
+        HMC_CK(h, cudaMalloc(&h->plain_sig, sizeof(double) * 48 * (size_t)R.nblk), "plain step stresses");
+        if (cudaMalloc(&h->plain_f, sizeof(double) * 24 * (size_t)R.nblk) != cudaSuccess) {
+            cudaFree(h->plain_sig);
+            h->plain_sig = nullptr;
+            return fail(h, HMC_ERR_OOM, "plain step cell forces");
+        }
+    }
+    hmc::PlainArgs a;
+    a.spins = h->spins;
+    a.ctab = static_cast<const double *>(h->ctab);
+    a.st = h->st;
+    a.v = static_cast<double *>(h->v);
+    a.sig = h->plain_sig;
+    a.fcell = h->plain_f;
+    a.dt = h->dt;
+    a.dt_over_m = h->dt / 8.0;   // lumped mass rho * V * sum_p N_I(x_p) = 8 voxels
+    a.keep = 1.0 - h->damping;
+    a.nbx = R.nbx;
+    a.nby = R.nby;
+    a.nbz = R.nbz;
+    a.nblk = (int)R.nblk;
+    a.u = static_cast<const double *>(h->u[h->cur]);
+    a.u_out = nullptr;
+    HMC_CK(h, hmc::launch_plain_init(a, h->stream), "plain step stress");
+    for (int k = 0; k < nsteps; ++k) {
+        a.u = static_cast<const double *>(h->u[h->cur]);
+        a.u_out = static_cast<double *>(h->u[h->cur ^ 1]);
+        HMC_CK(h, hmc::launch_plain_step(a, h->stream), "plain step");
+        h->cur ^= 1;
+    }
     return HMC_OK;
 }
 

@@ -115,6 +115,24 @@ struct MpmArgs {
 
 constexpr int MPM_STAB_MAX = 1024;   // orientations whose FP32 table the MPM step holds in shared memory
 
+// The plain (unfused, incremental) FP64 step of a single replica: point stresses
+// sig[6][nblk][8] (component, cell, local point a + 2b + 4c) and cell corner forces
+// fcell[24][nblk] kept in global memory between its kernels.
+struct PlainArgs {
+    const uint4 *spins;
+    const double *ctab;
+    const DevState *st;      // mean strain
+    const double *u;
+    double *u_out;
+    double *v;
+    double *sig;
+    double *fcell;
+    double dt, dt_over_m, keep;
+    int nbx, nby, nbz, nblk;
+};
+cudaError_t launch_plain_init(const PlainArgs &a, cudaStream_t s);
+cudaError_t launch_plain_step(const PlainArgs &a, cudaStream_t s);
+
 template <typename T>
 struct StressArgs {
     const Replica *reps;

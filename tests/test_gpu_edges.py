@@ -42,7 +42,9 @@ def run_both(g, o, n_mcs):
         assert ag == ao, f"MCS {m}: accepted {ag} vs {ao}"
         assert (g.spins() == o.spins).all(), f"MCS {m}: spins differ"
         u = g.nodal()[0]
-        assert np.linalg.norm(u - o.u) <= 1e-11 * max(np.linalg.norm(o.u), 1e-300)
+        # relative, with an absolute floor far below the load's displacement scale (strain x
+        # edge ~ 1e-2) for the homogeneous cases, where u is rounding noise around zero
+        assert np.linalg.norm(u - o.u) <= 1e-11 * np.linalg.norm(o.u) + 1e-14
 
 
 def test_smallest_grid(G):

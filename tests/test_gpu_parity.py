@@ -329,3 +329,28 @@ def test_sweep_margins_match_the_oracle(G, elastic):
         moved = o.spins != pre
         assert (moved <= ev).all()                 # every change came from an evaluated trial
         assert ((m[ev] <= 0) == moved[ev]).all()   # accepted exactly when the margin is <= 0
+
+
+def test_plain_fp64_step_matches_fused_and_oracle(G):
+    """The plain unfused incremental FP64 step (the baseline form) advances u and v as the
+    fused total-form step does, to FP64 rounding, on a ragged polycrystal; both match the
+    oracle.  FP32 and batch handles are refused."""
+    shape = (10, 18, 34)
+    g, o = make_pair(G, shape, 9, G.HMC_FP64, axis=(0.4, 1.0, 0.7), n_mpm=0, n_seeds=14)
+    rng = np.random.default_rng(4)
+    u0 = rng.normal(size=(np.prod(shape) // 8, 3)) * 1e-3
+    v0 = rng.normal(size=u0.shape) * 1e-4
+    g.set_nodal(u0, v0)
+    g.mpm_steps_plain(25)
+    up, vp = g.nodal()
+    g.set_nodal(u0, v0)
+    g.mpm_steps(25)
+    uf, vf = g.nodal()
+    o.u, o.v = u0.copy(), v0.copy()
+    o.mpm_steps(25)
+    assert rel(up, uf) < 1e-12 and rel(vp, vf) < 1e-12
+    assert rel(up, o.u) < 1e-12 and rel(vp, o.v) < 1e-12
+    g32, _ = make_pair(G, shape, 9, G.HMC_FP32, n_mpm=0, n_seeds=14)
+    with pytest.raises(G.HMCError) as e:
+        g32.mpm_steps_plain(1)
+    assert e.value.status == G.HMC_ERR_ARG
