@@ -62,30 +62,19 @@ struct Acc7<double> {
     __device__ __forceinline__ double get(int i) const { return v[i]; }
 };
 
-// Stores of one colour's component of a block's stress.  The red stress is read by the red
-// half sweep right after this pass (which takes its tiles in reverse order, so that it reads
-// first what this pass wrote last): it is stored with the normal L2 priority, so that the
-// last-written part can still be in L2 when the sweep reads it.  The black stress is read
-// only after the red sweep has streamed 200 MB through L2, so it is stored evict-first.
-template <typename T, bool KEEP>
+// Stores of one colour's component of a block's stress: streaming (evict-first), so that the
+// 403 MB written per pass do not push the spin field out of L2.  (Storing the red stress with
+// the normal priority, for the red half sweep that reads it next, measured no faster.)
+template <typename T>
 __device__ __forceinline__ void store4(T *p, const T (&v)[4]);
 template <>
-__device__ __forceinline__ void store4<float, false>(float *p, const float (&v)[4]) {
+__device__ __forceinline__ void store4<float>(float *p, const float (&v)[4]) {
     __stcs(reinterpret_cast<float4 *>(p), make_float4(v[0], v[1], v[2], v[3]));
 }
 template <>
-__device__ __forceinline__ void store4<float, true>(float *p, const float (&v)[4]) {
-    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
-}
-template <>
-__device__ __forceinline__ void store4<double, false>(double *p, const double (&v)[4]) {
+__device__ __forceinline__ void store4<double>(double *p, const double (&v)[4]) {
     __stcs(reinterpret_cast<double2 *>(p), make_double2(v[0], v[1]));
     __stcs(reinterpret_cast<double2 *>(p) + 1, make_double2(v[2], v[3]));
-}
-template <>
-__device__ __forceinline__ void store4<double, true>(double *p, const double (&v)[4]) {
-    reinterpret_cast<double2 *>(p)[0] = make_double2(v[0], v[1]);
-    reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
 }
 
 // Stress of the eight points of each cell from the current displacement; the
@@ -182,13 +171,7 @@ __global__ void __launch_bounds__(STRESS_THREADS, sizeof(T) == 4 ? 8 : 1) k_stre
             }
             if (STORE) {
 #pragma unroll
-                for (int k = 0; k < 6; ++k) {
-                    T *dst = sig + 4ll * ((long long)(c * 6 + k) * R.nblk + blk);
-                    if (c == 0)
-                        store4<T, true>(dst, out[k]);
-                    else
-                        store4<T, false>(dst, out[k]);
-                }
+                for (int k = 0; k < 6; ++k) store4<T>(sig + 4ll * ((long long)(c * 6 + k) * R.nblk + blk), out[k]);
             }
         }
 #pragma unroll

@@ -304,11 +304,16 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *b, unsigned parity
     }
     return false;
 }
+// The stress is read once per half sweep: its lines are marked evict-first in L2, so that
+// the 201 MB stream does not push the spin field (33.5 MB, read by every half sweep) out.
 __device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes, unsigned long long *b) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_u32(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_u32(b))
-                 : "memory");
+    asm volatile(
+        "{\n\t.reg .b64 pol;\n\t"
+        "createpolicy.fractional.L2::evict_first.b64 pol, 1.0;\n\t"
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], pol;\n\t}" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(b))
+        : "memory");
 }
 // ---------------------------------------------------------------------------
 // Flat kernel: one CTA per tile.  With the stored stress, thread 0 starts a bulk
