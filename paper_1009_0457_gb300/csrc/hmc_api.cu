@@ -1359,6 +1359,14 @@ hmc_status hmc_sweep_half(hmc_handle *h, int32_t colour, int64_t *accepted) {
     if (colour != 0 && colour != 1) return fail(h, HMC_ERR_ARG, "colour must be 0 or 1");
     HMC_CK(h, reset_accepted(h), "memset");
     HMC_CK(h, enq_sweep(h, colour, h->stream), "sweep launch");
+    if (fault("copy_lost")) {
+        // fault injection on the host: record what a CTA records when its stress copy never
+        // lands (wait_timeout = 2), so that the reporting path runs without any GPU fault
+        static const int32_t lost = 2;
+        HMC_CK(h, cudaMemcpyAsync(&sel_st(h)->wait_timeout, &lost, sizeof(lost), cudaMemcpyHostToDevice, h->stream),
+               "fault injection");
+        HMC_CK(h, cudaStreamSynchronize(h->stream), "sync");
+    }
     if (accepted) return read_accepted(h, accepted);
     return HMC_OK;
 }

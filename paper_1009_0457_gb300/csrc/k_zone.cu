@@ -254,23 +254,82 @@ __global__ void __launch_bounds__(32 * ZoneCfg<T>::WARPS, 2) k_zone(ZoneArgs<T> 
 
         // block Cholesky in the static order; a non-positive pivot marks the trial as failed
         bool ok = true;
-        for (int k = 0; k < 27; ++k) {
-            T *Dk = Kb + sch[ZS_DIAG + k] * ZBLK;
+        // the 3x3 diagonal factor of step k from reciprocal square roots (one special-function
+        // operation per pivot instead of a square root and a division); every lane holds it
+        T l00, l10, l11, l20, l21, l22, i00, i11, i22;
+        auto factor = [&](const T *Dk) {
             T r0[4], r1v[4], r2[4];
             ld4(Dk, r0);
             ld4(Dk + 4, r1v);
             ld4(Dk + 8, r2);
-            // the 3x3 diagonal factor from reciprocal square roots (one special-function
-            // operation per pivot instead of a square root and a division); the reciprocal
-            // pivots go to the rows' pad entries for the triangular solves below
-            const T a00 = r0[0], i00 = zrsqrt(a00), l00 = a00 * i00;
-            const T l10 = r1v[0] * i00, l20 = r2[0] * i00;
-            const T a11 = r1v[1] - l10 * l10, i11 = zrsqrt(a11), l11 = a11 * i11;
-            const T l21 = (r2[1] - l20 * l10) * i11;
-            const T a22 = r2[2] - l20 * l20 - l21 * l21, i22 = zrsqrt(a22), l22 = a22 * i22;
+            const T a00 = r0[0];
+            i00 = zrsqrt(a00);
+            l00 = a00 * i00;
+            l10 = r1v[0] * i00;
+            l20 = r2[0] * i00;
+            const T a11 = r1v[1] - l10 * l10;
+            i11 = zrsqrt(a11);
+            l11 = a11 * i11;
+            l21 = (r2[1] - l20 * l10) * i11;
+            const T a22 = r2[2] - l20 * l20 - l21 * l21;
+            i22 = zrsqrt(a22);
+            l22 = a22 * i22;
             ok = ok && (a00 > T(0)) && (a11 > T(0)) && (a22 > T(0)) && (i00 < T(3.0e38)) && (i11 < T(3.0e38)) &&
                  (i22 < T(3.0e38));
-            // column blocks (I, k): L_Ik = C_Ik L_kk^-T, from the factor each lane holds in registers
+        };
+        // row r of a column block (I, k): L_Ik = C_Ik L_kk^-T
+        auto solve_row = [&](T (&v)[4]) {
+            const T x0 = v[0] * i00;
+            const T x1 = (v[1] - x0 * l10) * i11;
+            const T x2 = (v[2] - x0 * l20 - x1 * l21) * i22;
+            v[0] = x0;
+            v[1] = x1;
+            v[2] = x2;
+        };
+        // C_IJ -= L_Ik L_Jk^T on the rows of C held in cv, stored back
+        auto update = [&](T *C, const T (&li)[3][4], const T (&lj)[3][4], T (&cv)[3][4]) {
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    cv[r][c] = fma(-li[r][0], lj[c][0], cv[r][c]);
+                    cv[r][c] = fma(-li[r][1], lj[c][1], cv[r][c]);
+                    cv[r][c] = fma(-li[r][2], lj[c][2], cv[r][c]);
+                }
+                st4(C + 4 * r, cv[r]);
+            }
+        };
+        // Steps of the 19 nodes outside the site's cell: their column blocks and factors are
+        // used only by the step's own updates, so each update lane forms the two column blocks
+        // it needs from the unsolved ones (the same arithmetic as a column solve) and nothing
+        // of the column is stored -- one warp barrier per step.
+        for (int k = 0; k < 19; ++k) {
+            factor(Kb + sch[ZS_DIAG + k] * ZBLK);
+            const int up0 = sch[ZS_UPOFF + k], up1 = sch[ZS_UPOFF + k + 1];
+            for (int t = up0 + 3 * lane; t < up1; t += 96) {
+                T *C = Kb + sch[t] * ZBLK;
+                const int sI = sch[t + 1], sJ = sch[t + 2];
+                const T *LI = Kb + sI * ZBLK, *LJ = Kb + sJ * ZBLK;
+                T li[3][4], lj[3][4], cv[3][4];
+#pragma unroll
+                for (int r = 0; r < 3; ++r) {
+                    ld4(LI + 4 * r, li[r]);
+                    ld4(LJ + 4 * r, lj[r]);
+                    ld4(C + 4 * r, cv[r]);
+                }
+#pragma unroll
+                for (int r = 0; r < 3; ++r) {
+                    solve_row(li[r]);
+                    solve_row(lj[r]);
+                }
+                update(C, li, lj, cv);
+            }
+            __syncwarp();
+        }
+        // steps of the site cell's 8 nodes: their column blocks and factors are kept for Y
+        for (int k = 19; k < 27; ++k) {
+            T *Dk = Kb + sch[ZS_DIAG + k] * ZBLK;
+            factor(Dk);
             const int nb0 = sch[ZS_NBOFF + k], nb1 = sch[ZS_NBOFF + k + 1];
             for (int t = nb0 + lane; t < nb1; t += 32) {
                 T *B = Kb + sch[t] * ZBLK;
@@ -278,12 +337,7 @@ __global__ void __launch_bounds__(32 * ZoneCfg<T>::WARPS, 2) k_zone(ZoneArgs<T> 
                 for (int r = 0; r < 3; ++r) {
                     T v[4];
                     ld4(B + 4 * r, v);
-                    const T x0 = v[0] * i00;
-                    const T x1 = (v[1] - x0 * l10) * i11;
-                    const T x2 = (v[2] - x0 * l20 - x1 * l21) * i22;
-                    v[0] = x0;
-                    v[1] = x1;
-                    v[2] = x2;
+                    solve_row(v);
                     st4(B + 4 * r, v);
                 }
             }
@@ -322,16 +376,7 @@ __global__ void __launch_bounds__(32 * ZoneCfg<T>::WARPS, 2) k_zone(ZoneArgs<T> 
 #pragma unroll
                     for (int r = 0; r < 3; ++r) ld4(C + 4 * r, cv[r]);
                 }
-#pragma unroll
-                for (int r = 0; r < 3; ++r) {
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        cv[r][c] = fma(-li[r][0], lj[c][0], cv[r][c]);
-                        cv[r][c] = fma(-li[r][1], lj[c][1], cv[r][c]);
-                        cv[r][c] = fma(-li[r][2], lj[c][2], cv[r][c]);
-                    }
-                    st4(C + 4 * r, cv[r]);
-                }
+                update(C, li, lj, cv);
             }
             __syncwarp();
         }

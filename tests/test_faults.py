@@ -82,3 +82,29 @@ def test_injected_copy_wait_runs_out_and_is_reported(G):
     assert e.value.status == G.HMC_ERR_TIMEOUT
     assert (g.spins() == sp).all()
     assert g.sweep_half(0) > 0
+
+
+@pytest.mark.gpu
+def test_injected_lost_copy_makes_the_handle_refuse_further_calls(G):
+    """HMC_FAULT=copy_lost records, on the host, what a sweep CTA records when its stress
+    copy never lands: the call reports HMC_ERR_TIMEOUT and every later call on the handle
+    is refused with HMC_ERR_STATE (its shared memory can no longer be trusted); other
+    handles are not affected and the handle can still be destroyed."""
+    from hmc_synth import voronoi_spins, euler_uniform_so3
+    g = G.HMC((8, 8, 8), 4, mpm_steps_per_mcs=2, elastic_scale=3e3)
+    sp = voronoi_spins((8, 8, 8), 6, 4, 1)
+    g.set_orientations(euler_uniform_so3(4, 1), sp)
+    g.compute_stress()
+    with _with_fault("copy_lost"):
+        with pytest.raises(G.HMCError) as e:
+            g.sweep_half(0)
+    assert e.value.status == G.HMC_ERR_TIMEOUT
+    for call in (lambda: g.sweep_half(1), lambda: g.mc_sweeps(1), lambda: g.mpm_steps(1)):
+        with pytest.raises(G.HMCError) as e:
+            call()
+        assert e.value.status == G.HMC_ERR_STATE
+    other = G.HMC((8, 8, 8), 4, mpm_steps_per_mcs=2)
+    other.set_orientations(euler_uniform_so3(4, 1), sp)
+    assert other.mc_sweeps(1) >= 0
+    other.close()
+    g.close()
