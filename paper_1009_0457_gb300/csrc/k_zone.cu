@@ -326,32 +326,46 @@ __global__ void __launch_bounds__(32 * ZoneCfg<T>::WARPS, 2) k_zone(ZoneArgs<T> 
             }
             __syncwarp();
         }
-        // steps of the site cell's 8 nodes: their column blocks and factors are kept for Y
+        // Steps of the site cell's 8 nodes: their column blocks and factors are kept for Y.  The
+        // update lanes form the column blocks they need from the unsolved ones as above; the
+        // column lanes (at most 8 per step) solve theirs now and store them after the step's
+        // barrier, when no lane reads the unsolved blocks any more, with lane 0's factor.
         for (int k = 19; k < 27; ++k) {
             T *Dk = Kb + sch[ZS_DIAG + k] * ZBLK;
             factor(Dk);
             const int nb0 = sch[ZS_NBOFF + k], nb1 = sch[ZS_NBOFF + k + 1];
-            for (int t = nb0 + lane; t < nb1; t += 32) {
-                T *B = Kb + sch[t] * ZBLK;
+            T *B = nb0 + lane < nb1 ? Kb + sch[nb0 + lane] * ZBLK : nullptr;
+            T bv[3][4];
+            if (B) {
 #pragma unroll
                 for (int r = 0; r < 3; ++r) {
-                    T v[4];
-                    ld4(B + 4 * r, v);
-                    solve_row(v);
-                    st4(B + 4 * r, v);
+                    ld4(B + 4 * r, bv[r]);
+                    solve_row(bv[r]);
                 }
             }
-            // the first update's target block is not touched by the column solves: read it now
             const int up0 = sch[ZS_UPOFF + k], up1 = sch[ZS_UPOFF + k + 1];
-            T cv[3][4];
-            if (up0 + 3 * lane < up1) {
-                const T *C = Kb + sch[up0 + 3 * lane] * ZBLK;
+            for (int t = up0 + 3 * lane; t < up1; t += 96) {
+                T *C = Kb + sch[t] * ZBLK;
+                const T *LI = Kb + sch[t + 1] * ZBLK, *LJ = Kb + sch[t + 2] * ZBLK;
+                T li[3][4], lj[3][4], cv[3][4];
 #pragma unroll
-                for (int r = 0; r < 3; ++r) ld4(C + 4 * r, cv[r]);
+                for (int r = 0; r < 3; ++r) {
+                    ld4(LI + 4 * r, li[r]);
+                    ld4(LJ + 4 * r, lj[r]);
+                    ld4(C + 4 * r, cv[r]);
+                }
+#pragma unroll
+                for (int r = 0; r < 3; ++r) {
+                    solve_row(li[r]);
+                    solve_row(lj[r]);
+                }
+                update(C, li, lj, cv);
             }
             __syncwarp();
-            // every lane has read the diagonal block: lane 0 stores its factor and reciprocal
-            // pivots (read again only by the triangular solve of Y, after the factorisation)
+            if (B) {
+#pragma unroll
+                for (int r = 0; r < 3; ++r) st4(B + 4 * r, bv[r]);
+            }
             if (lane == 0) {
                 Dk[0] = l00;
                 Dk[3] = i00;
@@ -363,23 +377,8 @@ __global__ void __launch_bounds__(32 * ZoneCfg<T>::WARPS, 2) k_zone(ZoneArgs<T> 
                 Dk[10] = l22;
                 Dk[11] = i22;
             }
-            for (int t = up0 + 3 * lane, first = 1; t < up1; t += 96, first = 0) {
-                T *C = Kb + sch[t] * ZBLK;
-                const T *LI = Kb + sch[t + 1] * ZBLK, *LJ = Kb + sch[t + 2] * ZBLK;
-                T li[3][4], lj[3][4];
-#pragma unroll
-                for (int r = 0; r < 3; ++r) {
-                    ld4(LI + 4 * r, li[r]);
-                    ld4(LJ + 4 * r, lj[r]);
-                }
-                if (!first) {
-#pragma unroll
-                    for (int r = 0; r < 3; ++r) ld4(C + 4 * r, cv[r]);
-                }
-                update(C, li, lj, cv);
-            }
-            __syncwarp();
         }
+        __syncwarp();
 
         // Y = L22^-1 B_p^T on the site's cell (orders 19..26): lane v < 6 takes column v
         const int pa = x & 1, pb = y & 1, pcq = z & 1;
