@@ -355,9 +355,10 @@ def run_ours(args):
     n_mpm = 50
     t_mpm = timed(lambda: G.lib.hmc_mpm_steps(h.h, n_mpm, None)) / n_mpm
     t_stress = timed(lambda: G.lib.hmc_compute_stress(h.h, None, None))
-    # the half sweeps as a step runs them: red after a stress pass, black after red (three rounds)
+    # the half sweeps as a step runs them: red after a stress pass, black after red (eight rounds;
+    # each half sweep's time depends on the state, so the median of sixteen)
     t_sweep = []
-    for _ in range(3):
+    for _ in range(8):
         assert G.lib.hmc_compute_stress(h.h, None, None) == 0
         t_sweep += [timed(lambda c=c: G.lib.hmc_sweep_half(h.h, c, None)) for c in (0, 1)]
     t_red, t_black = statistics.median(t_sweep[0::2]), statistics.median(t_sweep[1::2])

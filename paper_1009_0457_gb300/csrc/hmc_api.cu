@@ -322,6 +322,7 @@ hmc::SweepArgs<T> sweep_args(hmc_handle *h) {
     a.cta = h->sweep_cta;
     a.margin = nullptr;
     a.rep0 = h->rep0;
+    hmc::philox_round_keys(h->rep0.key0, h->rep0.key1, a.rkey);
     return a;
 }
 

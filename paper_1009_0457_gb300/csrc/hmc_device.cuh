@@ -33,6 +33,25 @@ __device__ __forceinline__ uint4 philox4(uint32_t c0, uint32_t c1, uint32_t c2, 
     return make_uint4(c0, c1, c2, c3);
 }
 
+// the same with the round keys given (philox_round_keys): kernels whose key is the same for
+// every thread read them from the kernel argument instead of forming them
+__device__ __forceinline__ uint4 philox4_rk(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                            const uint32_t (&rk)[20]) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const unsigned long long p0 = (unsigned long long)0xD2511F53u * c0;
+        const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c2;
+        const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        const uint32_t n0 = hi1 ^ c1 ^ rk[2 * r], n2 = hi0 ^ c3 ^ rk[2 * r + 1];
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+    }
+    return make_uint4(c0, c1, c2, c3);
+}
+
 // ---------------------------------------------------------------------------
 // Block layout.  Local corner index L = lx + 2 ly + 4 lz of a voxel inside its
 // 2x2x2 block; slot = position of the voxel's uint16 in the block's uint4.

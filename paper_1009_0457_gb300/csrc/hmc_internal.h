@@ -169,7 +169,17 @@ struct SweepArgs {
     double *margin;                  // margin form: (H - t) / max(1, |t|) of every trial evaluated with
                                      // the elastic term, natural site order (others untouched)
     Replica rep0;                    // replica 0's descriptor, passed by value
+    uint32_t rkey[20];               // with one replica: its Philox round keys (philox_round_keys)
 };
+
+// The ten round keys of Philox4x32-10 for key (k0, k1): round r uses (k0 + r W0, k1 + r W1)
+// mod 2^32 with the Weyl increments W0 = 0x9E3779B9, W1 = 0xBB67AE85.
+inline void philox_round_keys(uint32_t k0, uint32_t k1, uint32_t (&rk)[20]) {
+    for (int r = 0; r < 10; ++r) {
+        rk[2 * r] = k0 + (uint32_t)r * 0x9E3779B9u;
+        rk[2 * r + 1] = k1 + (uint32_t)r * 0xBB67AE85u;
+    }
+}
 
 // Elastic term of a sweep: none, one-point zone from the stored stress (constant
 // traction or constant strain), or the 27-point zone (trials listed by the

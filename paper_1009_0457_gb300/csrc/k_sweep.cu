@@ -137,18 +137,19 @@ __device__ __forceinline__ unsigned warp_reserve(unsigned *counter, int n, int l
 // belongs to slot i.  Neighbour trials take the acceptance word from the same
 // word w, as the low half of 6 w (the high half picks the neighbour); trials over
 // all orientations take it from a second block, counter word 3 = 4 + colour.
-template <int COL>
-__device__ __forceinline__ void block_draws(const Replica &R, int trial, int bx, int by, int bz, uint32_t mcs,
-                                            uint2 (&rnd)[4]) {
+// One-replica sweeps (ONE) take the round keys from the kernel argument (rk).
+template <int COL, bool ONE>
+__device__ __forceinline__ void block_draws(const Replica &R, const uint32_t (&rk)[20], int trial, int bx, int by,
+                                            int bz, uint32_t mcs, uint2 (&rnd)[4]) {
     const uint32_t s0 = 2u * ((uint32_t)bx + (uint32_t)R.nx * ((uint32_t)by + (uint32_t)R.ny * (uint32_t)bz));
-    const uint4 w = philox4(s0, mcs, R.replica, 2u + COL, R.key0, R.key1);
+    const uint4 w = ONE ? philox4_rk(s0, mcs, R.replica, 2u + COL, rk) : philox4(s0, mcs, R.replica, 2u + COL, R.key0, R.key1);
     if (trial == 0) {
         rnd[0] = make_uint2(w.x, 6u * w.x);
         rnd[1] = make_uint2(w.y, 6u * w.y);
         rnd[2] = make_uint2(w.z, 6u * w.z);
         rnd[3] = make_uint2(w.w, 6u * w.w);
     } else {
-        const uint4 v = philox4(s0, mcs, R.replica, 4u + COL, R.key0, R.key1);
+        const uint4 v = ONE ? philox4_rk(s0, mcs, R.replica, 4u + COL, rk) : philox4(s0, mcs, R.replica, 4u + COL, R.key0, R.key1);
         rnd[0] = make_uint2(w.x, v.x);
         rnd[1] = make_uint2(w.y, v.y);
         rnd[2] = make_uint2(w.z, v.z);
@@ -413,7 +414,7 @@ __global__ void __launch_bounds__(CTA, flat_min_ctas<T, MODE, RECOMP, CTA>())
         N[3] = __ldg(q2 + 2 * (blk + (by == nby - 1 ? -(nby - 1) * sxy : sxy)) + oc);
         N[4] = __ldg(q2 + 2 * (blk + (bz == 0 ? (nbz - 1) * sxz : -sxz)) + oc);
         N[5] = __ldg(q2 + 2 * (blk + (bz == nbz - 1 ? -(nbz - 1) * sxz : sxz)) + oc);
-        block_draws<COL>(R, a.trial, bx, by, bz, R.st->mcs, rnd);
+        block_draws<COL, ONE>(R, a.rkey, a.trial, bx, by, bz, R.st->mcs, rnd);
         uint16_t q[4];
         block_trials<COL>(a.trial, a.nq, mine, O, N, rnd, q, qn, dE);
         // recompute mode: the cell's displacement gradients, formed at the first listed trial
