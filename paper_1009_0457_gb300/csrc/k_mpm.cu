@@ -123,8 +123,10 @@ __device__ __forceinline__ void cubic_hooke(const float (&w)[12], const float (&
     }
     const float tr = __fadd_rn(__fadd_rn(e[0], e[1]), e[2]);
     const float p2 = __fsub_rn(__fsub_rn(tr, p0), p1);
-    const float c = __fmaf_rn(cub[3], p2, __fmul_rn(cub[0], tr));
-    const float d0 = __fmul_rn(cub[3], __fsub_rn(p0, p2)), d1 = __fmul_rn(cub[3], __fsub_rn(p1, p2));
+    // A = Ad p2; c = C12 tr + A; d_m = Ad p_m - A (one fused operation each)
+    const float A = __fmul_rn(cub[3], p2);
+    const float c = __fmaf_rn(cub[0], tr, A);
+    const float d0 = __fmaf_rn(cub[3], p0, -A), d1 = __fmaf_rn(cub[3], p1, -A);
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
         const float base = k < 3 ? __fmaf_rn(cub[1], e[k], c) : __fmul_rn(cub[2], e[k]);
@@ -141,8 +143,10 @@ __device__ __forceinline__ void cubic_hooke_paired(const float (&w)[12], const f
     const float p0 = pp.x, p1 = pp.y;
     const float tr = __fadd_rn(__fadd_rn(e[0], e[1]), e[2]);
     const float p2 = __fsub_rn(__fsub_rn(tr, p0), p1);
-    const float c = __fmaf_rn(cub[3], p2, __fmul_rn(cub[0], tr));
-    const float d0 = __fmul_rn(cub[3], __fsub_rn(p0, p2)), d1 = __fmul_rn(cub[3], __fsub_rn(p1, p2));
+    const float A = __fmul_rn(cub[3], p2);
+    const float c = __fmaf_rn(cub[0], tr, A);
+    const float2 dd = __ffma2_rn(make_float2(cub[3], cub[3]), pp, make_float2(-A, -A));
+    const float d0 = dd.x, d1 = dd.y;
     const float2 D0 = make_float2(d0, d0), D1 = make_float2(d1, d1);
     float2 base[3];
     base[0] = __ffma2_rn(make_float2(cub[1], cub[1]), make_float2(e[0], e[1]), make_float2(c, c));
@@ -504,8 +508,9 @@ __device__ __forceinline__ void cubic_hooke2(const float2 (&w)[12], const float 
     const float2 C44 = make_float2(cub[2], cub[2]), Ad = make_float2(cub[3], cub[3]);
     const float2 tr = p_add(p_add(e[0], e[1]), e[2]);
     const float2 p2 = p_sub(p_sub(tr, p0), p1);
-    const float2 c = p_fma(Ad, p2, p_mul(C12, tr));
-    const float2 d0 = p_mul(Ad, p_sub(p0, p2)), d1 = p_mul(Ad, p_sub(p1, p2));
+    const float2 A = p_mul(Ad, p2);
+    const float2 c = p_fma(C12, tr, A);
+    const float2 d0 = p_fma(Ad, p0, p_neg(A)), d1 = p_fma(Ad, p1, p_neg(A));
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
         const float2 base = k < 3 ? p_fma(C44x2, e[k], c) : p_mul(C44, e[k]);
