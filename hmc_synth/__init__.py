@@ -103,6 +103,25 @@ def random_spins(shape, Q: int, seed: int) -> np.ndarray:
     return rng.integers(0, Q, size=shape).astype(np.uint16)
 
 
+def box_grain_spins(shape, edge: int, Q: int, seed: int) -> np.ndarray:
+    """(nz,ny,nx) uint16 field of box-shaped grains: the orientation of voxel (x, y, z) is
+    (a[x // edge] ^ b[y // edge] ^ c[z // edge]) mod Q with a, b, c seeded uniform 16-bit
+    words.  Built one layer of boxes at a time, so it serves grids of billions of sites (a
+    grain boundary every edge voxels along each axis)."""
+    nz, ny, nx = shape
+    rng = np.random.default_rng([0x5EED, 5, int(seed)])
+    a = rng.integers(0, 1 << 16, size=nx // edge + 1, dtype=np.uint32)
+    b = rng.integers(0, 1 << 16, size=ny // edge + 1, dtype=np.uint32)
+    c = rng.integers(0, 1 << 16, size=nz // edge + 1, dtype=np.uint32)
+    ax = a[np.arange(nx) // edge]
+    by = b[np.arange(ny) // edge]
+    out = np.empty(shape, dtype=np.uint16)
+    plane = (by[:, None] ^ ax[None, :])
+    for z0 in range(0, nz, edge):
+        out[z0:z0 + edge] = ((plane ^ c[z0 // edge]) % Q).astype(np.uint16)[None]
+    return out
+
+
 # ---------------------------------------------------------------------------
 # Named workloads
 # ---------------------------------------------------------------------------

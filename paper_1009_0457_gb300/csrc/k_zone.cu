@@ -147,11 +147,12 @@ __global__ void __launch_bounds__(32 * ZoneCfg<T>::WARPS, 2) k_zone(ZoneArgs<T> 
 
     for (unsigned e = blockIdx.x * W + warp; e < n; e += gridDim.x * W) {
         const uint4 en = a.work[e];
-        const int p = (int)en.x;
+        const uint32_t p = en.x;   // site index: below 2^32, possibly above 2^31
         const Replica &R = a.reps[en.y];
         const uint32_t qn = en.z & 0xffffu, q = en.z >> 16, r1 = en.w;
         const int nx = R.nx, ny = R.ny, nz = R.nz;
-        const int x = p % nx, yz = p / nx, y = yz % ny, z = yz / ny;
+        const uint32_t yz = p / (uint32_t)nx;
+        const int x = (int)(p - yz * (uint32_t)nx), y = (int)(yz % (uint32_t)ny), z = (int)(yz / (uint32_t)ny);
         const int lox = (x - 1) >> 1, loy = (y - 1) >> 1, loz = (z - 1) >> 1;   // lowest zone node (may be -1)
         const int pcx = (x >> 1) - lox, pcy = (y >> 1) - loy, pcz = (z >> 1) - loz;   // site's zone cell
         const int refl = pcx + 2 * pcy + 4 * pcz;                                      // its reflection

@@ -103,3 +103,20 @@ def test_angle_histogram_of_the_z_rotation_set():
     f = O.texture_histogram(1, 9, counts, A, St, (1, 0, 0), 246.5, 147.3, 124.7)
     want = np.array([20, 20, 20, 20, 10, 0, 0, 0, 0]) / 90.0
     assert np.array_equal(f, want)
+
+
+def test_box_grain_spins_match_their_definition():
+    """Box grains: voxel (x, y, z) takes (a[x // e] ^ b[y // e] ^ c[z // e]) mod Q, here
+    evaluated voxel by voxel, with a grid whose edges are not multiples of e."""
+    shape, e, Q, seed = (13, 10, 22), 4, 37, 5
+    got = S.box_grain_spins(shape, e, Q, seed)
+    nz, ny, nx = shape
+    rng = np.random.default_rng([0x5EED, 5, seed])
+    a = rng.integers(0, 1 << 16, size=nx // e + 1, dtype=np.uint32)
+    b = rng.integers(0, 1 << 16, size=ny // e + 1, dtype=np.uint32)
+    c = rng.integers(0, 1 << 16, size=nz // e + 1, dtype=np.uint32)
+    for z in range(nz):
+        for y in range(ny):
+            for x in range(nx):
+                assert got[z, y, x] == (int(a[x // e]) ^ int(b[y // e]) ^ int(c[z // e])) % Q
+    assert got.dtype == np.uint16 and got.max() < Q
