@@ -39,7 +39,10 @@ def test_invalid_parameters_rejected_on_host(libhmc):
     bad = [dict(nx=5), dict(ny=2), dict(n_orient=0), dict(n_orient=70000), dict(kT=-1.0),
            dict(c11=100.0, c12=150.0), dict(precision=7), dict(bc=3), dict(trial=9), dict(elastic=4),
            dict(mpm_steps_per_mcs=-1), dict(damping=1.5), dict(load_axis=(0.0, 0.0, 0.0)),
-           dict(J=float("nan"))]
+           dict(J=float("nan")),
+           # one site over the 2^32 - 1 limit needs an odd edge; the smallest even grid over it
+           dict(nx=2048, ny=2048, nz=1024),
+           dict(elastic=2, nx=4, ny=6, nz=6)]
     for kw in bad:
         p = G.hmc_default_params(**kw)
         with pytest.raises(G.HMCError) as e:

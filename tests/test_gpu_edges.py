@@ -82,3 +82,25 @@ def test_zero_elastic_scale_is_pure_potts(G):
         ag, ao, ap = g.mc_sweeps(1), o.mc_sweeps(1), gp.mc_sweeps(1)
         assert ag == ao == ap, f"MCS {m}"
         assert (g.spins() == o.spins).all() and (gp.spins() == g.spins()).all(), f"MCS {m}"
+
+
+def test_empty_calls_and_refused_inputs_leave_the_state_alone(G):
+    """Zero counts do nothing; negative counts, a bad colour and an orientation index >= Q are
+    refused with HMC_ERR_ARG before anything is launched, and the handle then continues in
+    lock-step with the oracle."""
+    g, o = pair(G, (6, 8, 10), 5)
+    run_both(g, o, 1)
+    s0, (u0, v0), e0 = g.spins().copy(), g.nodal(), g.strain()
+    mcs0 = g.info().mcs
+    assert g.mc_sweeps(0) == 0
+    g.mpm_steps(0)
+    assert (g.spins() == s0).all() and g.info().mcs == mcs0
+    u1, v1 = g.nodal()
+    assert np.array_equal(u1, u0) and np.array_equal(v1, v0) and np.array_equal(g.strain(), e0)
+    for call in (lambda: g.mc_sweeps(-1), lambda: g.mpm_steps(-2), lambda: g.sweep_half(2),
+                 lambda: g.set_spins(np.where(np.arange(s0.size) == 17, 5, s0.ravel()).astype(np.uint16))):
+        with pytest.raises(G.HMCError) as e:
+            call()
+        assert e.value.status == G.HMC_ERR_ARG
+    assert (g.spins() == s0).all()
+    run_both(g, o, 2)
