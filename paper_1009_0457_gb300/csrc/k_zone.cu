@@ -15,13 +15,15 @@
 // singular only in the six rigid-body modes, which B_p does not see; holding six
 // DOFs of three non-collinear nodes outside the site's cell fixed removes them
 // without changing G.  G then follows from a block (3x3 per node) Cholesky
-// factorisation: the 19 nodes outside the site's cell are eliminated first
-// (corners, which create no fill, then edges, then face centres), the site's own
-// 8 nodes last, and with B_p^T nonzero only on those, G = Y^T Y for
-// Y = L22^-1 B_p^T from the trailing 24x24 factor.  Node coordinates are
-// reflected so that the site's cell is always the zone's cell (1,1,1); the
-// elimination schedule (which block pairs are structurally nonzero) is then the
-// same for every site and is built once on the host.
+// elimination of the matrix K bordered by B_p: two pseudo-nodes (orders 27 and 28)
+// carry the six rows of B_p, which are nonzero only on the site's own 8 nodes.
+// The 19 nodes outside the site's cell are eliminated first (corners, which create
+// no fill, then edges, then face centres), the site's 8 nodes next, and the
+// pseudo-nodes never: eliminating all 27 real nodes leaves -B_p K^+ B_p^T = -G in
+// the pseudo-nodes' three blocks (the Schur complement of K in the bordered
+// matrix).  Node coordinates are reflected so that the site's cell is always the
+// zone's cell (1,1,1); the elimination schedule (which block pairs are structurally
+// nonzero) is then the same for every site and is built once on the host.
 //
 // One warp per trial, taken from the work list that the compaction pass of the
 // sweep writes; the zone matrix lives in shared memory; the zone's orientations
@@ -38,16 +40,18 @@ namespace hmc {
 
 namespace {
 
-// Schedule table (uint16, built by zone_schedule):
+// Schedule table (uint16, built by zone_schedule), orders 0..26 the real nodes and 27, 28
+// the two pseudo-nodes of B_p (ZN = 29 orders):
 //   [0, 27)        elimination order of reflected node rx + 3 ry + 9 rz
 //   [27, 55)       per step k: first column-block entry (slot of block (I, k))
 //   [55, 83)       per step k: first update entry (slots of (I,J), (I,k), (J,k))
 //   [83, 110)      slot of the diagonal block of order k
-//   [110, 839)     slot of block (I, J), I >= J, in the filled pattern (0xffff: always zero)
+//   [110, 951)     slot of block (I, J), I >= J, of ZN x ZN in the filled pattern (0xffff: zero)
 //   then the column-block entries, then the update triples.
-constexpr int ZS_NBOFF = 27, ZS_UPOFF = 55, ZS_DIAG = 83, ZS_BIDX = 110, ZS_HDR = 839;
-constexpr int ZSCHED_CAP = 4096;
-constexpr int ZSLOT_CAP = 232;   // 3x3 blocks of the filled lower triangle (226 for this pattern)
+constexpr int ZN = 29;
+constexpr int ZS_NBOFF = 27, ZS_UPOFF = 55, ZS_DIAG = 83, ZS_BIDX = 110, ZS_HDR = ZS_BIDX + ZN * ZN;
+constexpr int ZSCHED_CAP = 4608;
+constexpr int ZSLOT_CAP = 248;   // 3x3 blocks of the filled lower triangle (245 for this pattern)
 constexpr int ZBLK = 12;         // a block: 3 rows of 4 values (the 4th pads a row to 16 B)
 constexpr int ZROW = 320;        // an element matrix's 300 upper-triangle entries, padded to 10 x 32
 constexpr int ZTRASH = (ZSLOT_CAP - 1) * ZBLK;   // an unused slot: target of the scatter's padding
@@ -67,7 +71,7 @@ __host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) & ~size
 __host__ __device__ constexpr size_t zone_cta_bytes() { return align16(ZSCHED_CAP * sizeof(uint16_t)); }
 template <typename T>
 __host__ __device__ constexpr size_t zone_warp_bytes() {
-    return align16((ZSLOT_CAP * ZBLK + 144 + 72) * sizeof(T) + 64 + 8 + 32 + 8);
+    return align16((ZSLOT_CAP * ZBLK + 72) * sizeof(T) + 64 + 8 + 32 + 8);
 }
 template <typename T>
 __host__ __device__ constexpr size_t zone_smem() {
@@ -130,9 +134,8 @@ __global__ void __launch_bounds__(32 * ZoneCfg<T>::WARPS, 2) k_zone(ZoneArgs<T> 
     uint16_t *sch = reinterpret_cast<uint16_t *>(smem);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned char *wb = smem + zone_cta_bytes() + warp * zone_warp_bytes<T>();
-    T *Kb = reinterpret_cast<T *>(wb);                     // block slots of the zone matrix
-    T *Ys = Kb + ZSLOT_CAP * ZBLK;                         // Y = L22^-1 B_p^T, 24 x 6
-    T *Gs = Ys + 144;                                      // G, 6 x 6
+    T *Kb = reinterpret_cast<T *>(wb);                     // block slots of the bordered zone matrix
+    T *Gs = Kb + ZSLOT_CAP * ZBLK;                         // G, 6 x 6
     T *dCs = Gs + 36;                                      // C'(q_new) - C'(q_old), 6 x 6
     uint8_t *dmap = reinterpret_cast<uint8_t *>(dCs + 36); // (zone cell, corner) -> node order
     uint8_t *inv = dmap + 64;                              // order - 19 -> corner of the site's cell
@@ -206,6 +209,20 @@ __global__ void __launch_bounds__(32 * ZoneCfg<T>::WARPS, 2) k_zone(ZoneArgs<T> 
             const int o = lane < 3 ? 0 : lane < 5 ? ordB : ordC, r = lane < 3 ? lane : lane == 3 ? 1 : 2;
             Kb[sch[ZS_DIAG + o] * ZBLK + 5 * r] = T(1);   // (r, r) of the diagonal block
         }
+        // the border: block (27 + P, 19 + nn) holds rows 3P..3P+2 of B_p on the DOFs of the site
+        // cell's node of order 19 + nn (lane 2 nn + P); B_p maps that corner's displacement to the
+        // site's strain (Voigt, engineering shear)
+        const int pa = x & 1, pb = y & 1, pcq = z & 1;
+        if (lane < 16) {
+            const int nn = lane >> 1, P = lane & 1, cr = inv[nn];
+            T g[3];
+            corner_grad<T>(pa, pb, pcq, cr & 1, (cr >> 1) & 1, cr >> 2, g);
+            T *Bk = Kb + sch[ZS_BIDX + ZN * (27 + P) + 19 + nn] * ZBLK;
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+#pragma unroll
+                for (int al = 0; al < 3; ++al) Bk[4 * r + al] = bt_entry<T>(g, al, 3 * P + r);
+        }
 
         // assembly: K = sum of B^T C' B over the zone's points (element tables per orientation and
         // position); the points of one zone cell share its DOF map, so they are summed in registers
@@ -256,8 +273,9 @@ __global__ void __launch_bounds__(32 * ZoneCfg<T>::WARPS, 2) k_zone(ZoneArgs<T> 
         // block Cholesky in the static order; a non-positive pivot marks the trial as failed
         bool ok = true;
         // the 3x3 diagonal factor of step k from reciprocal square roots (one special-function
-        // operation per pivot instead of a square root and a division); every lane holds it
-        T l00, l10, l11, l20, l21, l22, i00, i11, i22;
+        // operation per pivot instead of a square root and a division); every lane holds the
+        // off-diagonal entries and the reciprocal pivots, which is all the column solves use
+        T l10, l20, l21, i00, i11, i22;
         auto factor = [&](const T *Dk) {
             T r0[4], r1v[4], r2[4];
             ld4(Dk, r0);
@@ -265,16 +283,13 @@ __global__ void __launch_bounds__(32 * ZoneCfg<T>::WARPS, 2) k_zone(ZoneArgs<T> 
             ld4(Dk + 8, r2);
             const T a00 = r0[0];
             i00 = zrsqrt(a00);
-            l00 = a00 * i00;
             l10 = r1v[0] * i00;
             l20 = r2[0] * i00;
             const T a11 = r1v[1] - l10 * l10;
             i11 = zrsqrt(a11);
-            l11 = a11 * i11;
             l21 = (r2[1] - l20 * l10) * i11;
             const T a22 = r2[2] - l20 * l20 - l21 * l21;
             i22 = zrsqrt(a22);
-            l22 = a22 * i22;
             ok = ok && (a00 > T(0)) && (a11 > T(0)) && (a22 > T(0)) && (i00 < T(3.0e38)) && (i11 < T(3.0e38)) &&
                  (i22 < T(3.0e38));
         };
@@ -300,11 +315,11 @@ __global__ void __launch_bounds__(32 * ZoneCfg<T>::WARPS, 2) k_zone(ZoneArgs<T> 
                 st4(C + 4 * r, cv[r]);
             }
         };
-        // Steps of the 19 nodes outside the site's cell: their column blocks and factors are
-        // used only by the step's own updates, so each update lane forms the two column blocks
-        // it needs from the unsolved ones (the same arithmetic as a column solve) and nothing
-        // of the column is stored -- one warp barrier per step.
-        for (int k = 0; k < 19; ++k) {
+        // The 27 elimination steps.  No column block or factor is read after its own step (the
+        // border's Schur complement, not a stored factor, gives G), so each update lane forms the
+        // two column blocks it needs from the unsolved ones (the same arithmetic as a column
+        // solve) and nothing of the column is stored -- one warp barrier per step.
+        for (int k = 0; k < 27; ++k) {
             factor(Kb + sch[ZS_DIAG + k] * ZBLK);
             const int up0 = sch[ZS_UPOFF + k], up1 = sch[ZS_UPOFF + k + 1];
             for (int t = up0 + 3 * lane; t < up1; t += 96) {
@@ -327,107 +342,19 @@ __global__ void __launch_bounds__(32 * ZoneCfg<T>::WARPS, 2) k_zone(ZoneArgs<T> 
             }
             __syncwarp();
         }
-        // Steps of the site cell's 8 nodes: their column blocks and factors are kept for Y.  The
-        // update lanes form the column blocks they need from the unsolved ones as above; the
-        // column lanes (at most 8 per step) solve theirs now and store them after the step's
-        // barrier, when no lane reads the unsolved blocks any more, with lane 0's factor.
-        for (int k = 19; k < 27; ++k) {
-            T *Dk = Kb + sch[ZS_DIAG + k] * ZBLK;
-            factor(Dk);
-            const int nb0 = sch[ZS_NBOFF + k], nb1 = sch[ZS_NBOFF + k + 1];
-            T *B = nb0 + lane < nb1 ? Kb + sch[nb0 + lane] * ZBLK : nullptr;
-            T bv[3][4];
-            if (B) {
-#pragma unroll
-                for (int r = 0; r < 3; ++r) {
-                    ld4(B + 4 * r, bv[r]);
-                    solve_row(bv[r]);
-                }
-            }
-            const int up0 = sch[ZS_UPOFF + k], up1 = sch[ZS_UPOFF + k + 1];
-            for (int t = up0 + 3 * lane; t < up1; t += 96) {
-                T *C = Kb + sch[t] * ZBLK;
-                const T *LI = Kb + sch[t + 1] * ZBLK, *LJ = Kb + sch[t + 2] * ZBLK;
-                T li[3][4], lj[3][4], cv[3][4];
-#pragma unroll
-                for (int r = 0; r < 3; ++r) {
-                    ld4(LI + 4 * r, li[r]);
-                    ld4(LJ + 4 * r, lj[r]);
-                    ld4(C + 4 * r, cv[r]);
-                }
-#pragma unroll
-                for (int r = 0; r < 3; ++r) {
-                    solve_row(li[r]);
-                    solve_row(lj[r]);
-                }
-                update(C, li, lj, cv);
-            }
-            __syncwarp();
-            if (B) {
-#pragma unroll
-                for (int r = 0; r < 3; ++r) st4(B + 4 * r, bv[r]);
-            }
-            if (lane == 0) {
-                Dk[0] = l00;
-                Dk[3] = i00;
-                Dk[4] = l10;
-                Dk[5] = l11;
-                Dk[7] = i11;
-                Dk[8] = l20;
-                Dk[9] = l21;
-                Dk[10] = l22;
-                Dk[11] = i22;
-            }
-        }
-        __syncwarp();
 
-        // Y = L22^-1 B_p^T on the site's cell (orders 19..26): lane v < 6 takes column v
-        const int pa = x & 1, pb = y & 1, pcq = z & 1;
-        if (lane < 6) {
-            T yv[24];
-#pragma unroll
-            for (int nn = 0; nn < 8; ++nn) {
-                const int cr = inv[nn];
-                T g[3];
-                corner_grad<T>(pa, pb, pcq, cr & 1, (cr >> 1) & 1, cr >> 2, g);
-                T rhs[3];
-#pragma unroll
-                for (int al = 0; al < 3; ++al) rhs[al] = bt_entry<T>(g, al, lane);
-#pragma unroll
-                for (int m = 0; m < nn; ++m) {
-                    const T *L = Kb + sch[ZS_BIDX + 27 * (19 + nn) + 19 + m] * ZBLK;
-#pragma unroll
-                    for (int r = 0; r < 3; ++r) {
-                        T v[4];
-                        ld4(L + 4 * r, v);
-                        rhs[r] -= v[0] * yv[3 * m] + v[1] * yv[3 * m + 1] + v[2] * yv[3 * m + 2];
-                    }
-                }
-                const T *Ln = Kb + sch[ZS_DIAG + 19 + nn] * ZBLK;
-                T d0[4], d1[4], d2[4];
-                ld4(Ln, d0);
-                ld4(Ln + 4, d1);
-                ld4(Ln + 8, d2);
-                yv[3 * nn] = rhs[0] * d0[3];   // row pads hold the reciprocal pivots
-                yv[3 * nn + 1] = (rhs[1] - d1[0] * yv[3 * nn]) * d1[3];
-                yv[3 * nn + 2] = (rhs[2] - d2[0] * yv[3 * nn] - d2[1] * yv[3 * nn + 1]) * d2[3];
-            }
-#pragma unroll
-            for (int rrow = 0; rrow < 24; ++rrow) Ys[rrow * 6 + lane] = yv[rrow];
-        }
-        __syncwarp();
+        // G = -(the border's blocks after the elimination): lane 6 v + w (v, w < 6) reads
+        // entry (v, w) of the lower triangle of blocks (27 + v / 3, 27 + w / 3), v >= w
         if (lane < 21) {
             int v = 0, rem = lane;
             while (rem >= 6 - v) {
                 rem -= 6 - v;
                 ++v;
             }
-            const int w = v + rem;
-            T s = T(0);
-#pragma unroll
-            for (int rrow = 0; rrow < 24; ++rrow) s += Ys[rrow * 6 + v] * Ys[rrow * 6 + w];
-            Gs[6 * v + w] = s;
-            Gs[6 * w + v] = s;
+            const int w = v + rem;   // w >= v: entry (w, v) of the lower triangle
+            const T gv = -Kb[sch[ZS_BIDX + ZN * (27 + w / 3) + 27 + v / 3] * ZBLK + 4 * (w % 3) + v % 3];
+            Gs[6 * v + w] = gv;
+            Gs[6 * w + v] = gv;
         }
         // the site's strain from its cell's nodal displacements: lane = 3 corner + alpha
         T eps[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
@@ -619,7 +546,7 @@ namespace {
 struct ZoneLayout {
     std::vector<std::vector<int>> nb;                    // per step: column-block rows I
     std::vector<std::vector<std::pair<int, int>>> up;    // per step: update blocks (I, J)
-    std::vector<int> slot_of;                            // 27 * I + J -> slot (-1 if structurally zero)
+    std::vector<int> slot_of;                            // ZN * I + J -> slot (-1 if structurally zero)
 };
 
 int quarter_wavefronts(const int *s, int n) {
@@ -642,16 +569,10 @@ long step_cost(const ZoneLayout &L, int k) {
         for (int which = 0; which < 3; ++which) {
             for (int i = 0; i < n; ++i) {
                 const int I = u[q + i].first, J = u[q + i].second;
-                s[i] = L.slot_of[which == 0 ? 27 * I + J : which == 1 ? 27 * I + k : 27 * J + k];
+                s[i] = L.slot_of[which == 0 ? ZN * I + J : which == 1 ? ZN * I + k : ZN * J + k];
             }
             c += quarter_wavefronts(s, n) * (which == 0 ? 4 : 3);   // C: 3 loads + 3 stores
         }
-    }
-    const auto &b = L.nb[k];
-    for (size_t q = 0; q < b.size(); q += 8) {
-        const int n = (int)std::min<size_t>(8, b.size() - q);
-        for (int i = 0; i < n; ++i) s[i] = L.slot_of[27 * b[q + i] + k];
-        c += quarter_wavefronts(s, n) * 6;
     }
     return c;
 }
@@ -672,11 +593,10 @@ void optimise_layout(ZoneLayout &L, int nslots) {
         for (int k = 0; k < 27; ++k) {
             std::vector<int> ss;
             for (auto &ij : L.up[k]) {
-                ss.push_back(L.slot_of[27 * ij.first + ij.second]);
-                ss.push_back(L.slot_of[27 * ij.first + k]);
-                ss.push_back(L.slot_of[27 * ij.second + k]);
+                ss.push_back(L.slot_of[ZN * ij.first + ij.second]);
+                ss.push_back(L.slot_of[ZN * ij.first + k]);
+                ss.push_back(L.slot_of[ZN * ij.second + k]);
             }
-            for (int I : L.nb[k]) ss.push_back(L.slot_of[27 * I + k]);
             std::sort(ss.begin(), ss.end());
             ss.erase(std::unique(ss.begin(), ss.end()), ss.end());
             for (int x : ss) steps_of[x].push_back(k);
@@ -684,7 +604,7 @@ void optimise_layout(ZoneLayout &L, int nslots) {
     };
     rebuild();
     std::vector<int> owner(nslots, -1);   // slot -> 27 I + J
-    for (int b = 0; b < 27 * 27; ++b)
+    for (int b = 0; b < ZN * ZN; ++b)
         if (L.slot_of[b] >= 0) owner[L.slot_of[b]] = b;
     std::vector<long> cost(27);
     for (int k = 0; k < 27; ++k) cost[k] = step_cost(L, k);
@@ -762,17 +682,25 @@ std::vector<uint16_t> zone_schedule_build() {
     for (int c = 2; c <= 3; ++c)
         for (int n = 0; n < 27; ++n)
             if (cls(n) == c) order.push_back(n);
-    bool pat[27][27];
-    for (int i = 0; i < 27; ++i)
-        for (int j = 0; j < 27; ++j) {
+    // the real nodes share a block when they lie in a common zone cell (Chebyshev distance
+    // <= 1); the two border pseudo-nodes (orders 27, 28) share one with the site cell's nodes
+    // (orders 19..26) and with each other
+    bool pat[ZN][ZN];
+    for (int i = 0; i < ZN; ++i)
+        for (int j = 0; j < ZN; ++j) {
+            if (i >= 27 || j >= 27) {
+                pat[i][j] = std::min(i, j) >= 19;
+                continue;
+            }
             int dmax = 0;
             for (int d = 0; d < 3; ++d) dmax = std::max(dmax, std::abs(co(order[i], d) - co(order[j], d)));
             pat[i][j] = dmax <= 1;
         }
+    // symbolic elimination of the 27 real nodes (the pseudo-nodes are never eliminated)
     std::vector<std::vector<int>> nb(27);
     std::vector<std::vector<std::pair<int, int>>> up(27);
     for (int k = 0; k < 27; ++k) {
-        for (int i = k + 1; i < 27; ++i)
+        for (int i = k + 1; i < ZN; ++i)
             if (pat[i][k]) nb[k].push_back(i);
         for (int I : nb[k])
             for (int J : nb[k])
@@ -786,18 +714,18 @@ std::vector<uint16_t> zone_schedule_build() {
     ZoneLayout L;
     L.nb = nb;
     L.up = up;
-    L.slot_of.assign(27 * 27, -1);
+    L.slot_of.assign(ZN * ZN, -1);
     int slots = 0;
-    for (int I = 0; I < 27; ++I)
+    for (int I = 0; I < ZN; ++I)
         for (int J = 0; J <= I; ++J)
-            if (pat[I][J]) L.slot_of[27 * I + J] = slots++;
+            if (pat[I][J]) L.slot_of[ZN * I + J] = slots++;
     if (slots > ZSLOT_CAP - 1) return {};   // the last slot stays free (ZTRASH)
     optimise_layout(L, slots);
     up = L.up;
-    for (int I = 0; I < 27; ++I)
-        for (int J = 0; J < 27; ++J)
-            t[ZS_BIDX + 27 * I + J] = L.slot_of[27 * I + J] >= 0 ? (uint16_t)L.slot_of[27 * I + J] : (uint16_t)0xffff;
-    for (int k = 0; k < 27; ++k) t[ZS_DIAG + k] = t[ZS_BIDX + 28 * k];
+    for (int I = 0; I < ZN; ++I)
+        for (int J = 0; J < ZN; ++J)
+            t[ZS_BIDX + ZN * I + J] = L.slot_of[ZN * I + J] >= 0 ? (uint16_t)L.slot_of[ZN * I + J] : (uint16_t)0xffff;
+    for (int k = 0; k < 27; ++k) t[ZS_DIAG + k] = t[ZS_BIDX + (ZN + 1) * k];
     size_t off = ZS_HDR;
     for (int k = 0; k <= 27; ++k) {
         t[ZS_NBOFF + k] = (uint16_t)off;
@@ -808,12 +736,12 @@ std::vector<uint16_t> zone_schedule_build() {
         if (k < 27) off += 3 * up[k].size();
     }
     for (int k = 0; k < 27; ++k)
-        for (int I : nb[k]) t.push_back(t[ZS_BIDX + 27 * I + k]);
+        for (int I : nb[k]) t.push_back(t[ZS_BIDX + ZN * I + k]);
     for (int k = 0; k < 27; ++k)
         for (auto &ij : up[k]) {
-            t.push_back(t[ZS_BIDX + 27 * ij.first + ij.second]);
-            t.push_back(t[ZS_BIDX + 27 * ij.first + k]);
-            t.push_back(t[ZS_BIDX + 27 * ij.second + k]);
+            t.push_back(t[ZS_BIDX + ZN * ij.first + ij.second]);
+            t.push_back(t[ZS_BIDX + ZN * ij.first + k]);
+            t.push_back(t[ZS_BIDX + ZN * ij.second + k]);
         }
     if (t.size() > (size_t)ZSCHED_CAP) return {};
     return t;
@@ -847,7 +775,7 @@ std::vector<uint16_t> zone_scatter_table(const std::vector<uint16_t> &t) {
                         std::swap(o1, o2);
                         std::swap(a1, a2);
                     }
-                    out[(size_t)(rf * 8 + c) * ZROW + e] = (uint16_t)(t[ZS_BIDX + 27 * o1 + o2] * ZBLK + 4 * a1 + a2);
+                    out[(size_t)(rf * 8 + c) * ZROW + e] = (uint16_t)(t[ZS_BIDX + ZN * o1 + o2] * ZBLK + 4 * a1 + a2);
                 }
         }
     }
