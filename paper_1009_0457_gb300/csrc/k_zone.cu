@@ -224,52 +224,6 @@ __global__ void __launch_bounds__(32 * ZoneCfg<T>::WARPS, 2) k_zone(ZoneArgs<T> 
                 for (int al = 0; al < 3; ++al) Bk[4 * r + al] = bt_entry<T>(g, al, 3 * P + r);
         }
 
-        // assembly: K = sum of B^T C' B over the zone's points (element tables per orientation and
-        // position); the points of one zone cell share its DOF map, so they are summed in registers
-        // and scattered once per cell.  The element rows are read from L2 three points ahead of
-        // their sum (three register buffers in rotation), so that the loads overlap.
-        {
-            T acc[NJ], b0[NJ], b1[NJ], b2[NJ];
-#pragma unroll
-            for (int j = 0; j < NJ; ++j) acc[j] = T(0);
-            // element rows are padded with zeros to 320 entries, so every lane loads NJ of them
-            auto fetch = [&](int s, T(&v)[NJ]) {
-                const uint32_t qs = __shfl_sync(FULL, my_q, s), pos = __shfl_sync(FULL, my_pos, s);
-                const T *ke = a.ktab + ((size_t)qs * 8 + pos) * ZROW + lane;
-#pragma unroll
-                for (int j = 0; j < NJ; ++j) v[j] = __ldg(ke + 32 * j);
-            };
-            fetch(plist[0], b0);
-            fetch(plist[1], b1);
-            fetch(plist[2], b2);
-            int c = 0, cn = cend[0];
-            // add point u (held in buf), scatter when it closes its zone cell, refill buf with point u + 3
-            auto step = [&](int u, T(&buf)[NJ]) {
-#pragma unroll
-                for (int j = 0; j < NJ; ++j) acc[j] += buf[j];
-                if (u + 3 < 27) fetch(plist[u + 3], buf);
-                if (u + 1 == cn) {
-                    // the entries' places in the block slots for this reflection and zone cell
-                    // (zone_scatter_table): padding entries and those of fixed DOFs go to the
-                    // unused last slot, so the scatter has no branches
-                    const uint16_t *sc = a.scatter + (size_t)(refl * 8 + c) * ZROW + lane;
-#pragma unroll
-                    for (int j = 0; j < NJ; ++j) Kb[__ldg(sc + 32 * j)] += acc[j];
-#pragma unroll
-                    for (int j = 0; j < NJ; ++j) acc[j] = T(0);
-                    __syncwarp();
-                    ++c;
-                    cn = c < 8 ? cend[c] : 27;
-                }
-            };
-            for (int u = 0; u < 27; u += 3) {
-                step(u, b0);
-                step(u + 1, b1);
-                step(u + 2, b2);
-            }
-        }
-        __syncwarp();
-
         // block Cholesky in the static order; a non-positive pivot marks the trial as failed
         bool ok = true;
         // the 3x3 diagonal factor of step k from reciprocal square roots (one special-function
@@ -315,11 +269,11 @@ __global__ void __launch_bounds__(32 * ZoneCfg<T>::WARPS, 2) k_zone(ZoneArgs<T> 
                 st4(C + 4 * r, cv[r]);
             }
         };
-        // The 27 elimination steps.  No column block or factor is read after its own step (the
+        // Elimination step k.  No column block or factor is read after its own step (the
         // border's Schur complement, not a stored factor, gives G), so each update lane forms the
         // two column blocks it needs from the unsolved ones (the same arithmetic as a column
         // solve) and nothing of the column is stored -- one warp barrier per step.
-        for (int k = 0; k < 27; ++k) {
+        auto elim = [&](int k) {
             factor(Kb + sch[ZS_DIAG + k] * ZBLK);
             const int up0 = sch[ZS_UPOFF + k], up1 = sch[ZS_UPOFF + k + 1];
             for (int t = up0 + 3 * lane; t < up1; t += 96) {
@@ -341,7 +295,65 @@ __global__ void __launch_bounds__(32 * ZoneCfg<T>::WARPS, 2) k_zone(ZoneArgs<T> 
                 update(C, li, lj, cv);
             }
             __syncwarp();
+        };
+
+        // assembly: K = sum of B^T C' B over the zone's points (element tables per orientation and
+        // position); the points of one zone cell share its DOF map, so they are summed in registers
+        // and scattered once per cell.  The element rows are read from L2 three points ahead of
+        // their sum (three register buffers in rotation), so that the loads overlap.
+        {
+            T acc[NJ], b0[NJ], b1[NJ], b2[NJ];
+#pragma unroll
+            for (int j = 0; j < NJ; ++j) acc[j] = T(0);
+            // element rows are padded with zeros to 320 entries, so every lane loads NJ of them
+            auto fetch = [&](int s, T(&v)[NJ]) {
+                const uint32_t qs = __shfl_sync(FULL, my_q, s), pos = __shfl_sync(FULL, my_pos, s);
+                const T *ke = a.ktab + ((size_t)qs * 8 + pos) * ZROW + lane;
+#pragma unroll
+                for (int j = 0; j < NJ; ++j) v[j] = __ldg(ke + 32 * j);
+            };
+            fetch(plist[0], b0);
+            fetch(plist[1], b1);
+            fetch(plist[2], b2);
+            int c = 0, cn = cend[0];
+            // add point u (held in buf), scatter when it closes its zone cell, refill buf with point u + 3
+            auto step = [&](int u, T(&buf)[NJ]) {
+#pragma unroll
+                for (int j = 0; j < NJ; ++j) acc[j] += buf[j];
+                if (u + 3 < 27) fetch(plist[u + 3], buf);
+                if (u + 1 == cn) {
+                    // the entries' places in the block slots for this reflection and zone cell
+                    // (zone_scatter_table): padding entries and those of fixed DOFs go to the
+                    // unused last slot, so the scatter has no branches
+                    const uint16_t *sc = a.scatter + (size_t)(refl * 8 + c) * ZROW + lane;
+#pragma unroll
+                    for (int j = 0; j < NJ; ++j) Kb[__ldg(sc + 32 * j)] += acc[j];
+#pragma unroll
+                    for (int j = 0; j < NJ; ++j) acc[j] = T(0);
+                    __syncwarp();
+                    // the cell's outer corner (reflected cell rc, node (2 rcx, 2 rcy, 2 rcz)) lies
+                    // in this cell alone, so its blocks are complete: eliminate it now (steps
+                    // 1..6; node A and the site cell's corner excepted) while the next cell's
+                    // rows are in flight.  Later cells add to the blocks it updates.
+                    const int rc = c ^ (~refl & 7);
+                    const int kc = sch[2 * (rc & 1) + 6 * ((rc >> 1) & 1) + 18 * (rc >> 2)];
+                    if (kc >= 1 && kc <= 6) elim(kc);
+                    ++c;
+                    cn = c < 8 ? cend[c] : 27;
+                }
+            };
+            for (int u = 0; u < 27; u += 3) {
+                step(u, b0);
+                step(u + 1, b1);
+                step(u + 2, b2);
+            }
         }
+        __syncwarp();
+
+        // the remaining steps: edges, face centres, the site cell (the corners were eliminated
+        // during the assembly)
+        for (int k = 7; k < 27; ++k) elim(k);
+        __syncwarp();
 
         // G = -(the border's blocks after the elimination): lane 6 v + w (v, w < 6) reads
         // entry (v, w) of the lower triangle of blocks (27 + v / 3, 27 + w / 3), v >= w
@@ -684,12 +696,18 @@ std::vector<uint16_t> zone_schedule_build() {
             if (cls(n) == c) order.push_back(n);
     // the real nodes share a block when they lie in a common zone cell (Chebyshev distance
     // <= 1); the two border pseudo-nodes (orders 27, 28) share one with the site cell's nodes
-    // (orders 19..26) and with each other
+    // (orders 19..26) and with each other.  Node A (order 0) has all its DOFs held fixed: its
+    // row and column of K are zero but for the unit diagonal, so it shares no block and its
+    // elimination step is empty (the kernel starts at step 1).
     bool pat[ZN][ZN];
     for (int i = 0; i < ZN; ++i)
         for (int j = 0; j < ZN; ++j) {
             if (i >= 27 || j >= 27) {
                 pat[i][j] = std::min(i, j) >= 19;
+                continue;
+            }
+            if ((i == 0) != (j == 0)) {
+                pat[i][j] = false;
                 continue;
             }
             int dmax = 0;
