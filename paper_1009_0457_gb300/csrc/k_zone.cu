@@ -224,8 +224,9 @@ __global__ void __launch_bounds__(32 * ZoneCfg<T>::WARPS, 2) k_zone(ZoneArgs<T> 
                 for (int al = 0; al < 3; ++al) Bk[4 * r + al] = bt_entry<T>(g, al, 3 * P + r);
         }
 
-        // block Cholesky in the static order; a non-positive pivot marks the trial as failed
-        bool ok = true;
+        // block Cholesky in the static order; a non-positive pivot (the smallest one is kept) or a
+        // non-finite G marks the trial as failed
+        T pmin = T(1);
         // the 3x3 diagonal factor of step k from reciprocal square roots (one special-function
         // operation per pivot instead of a square root and a division); every lane holds the
         // off-diagonal entries and the reciprocal pivots, which is all the column solves use
@@ -244,8 +245,7 @@ __global__ void __launch_bounds__(32 * ZoneCfg<T>::WARPS, 2) k_zone(ZoneArgs<T> 
             l21 = (r2[1] - l20 * l10) * i11;
             const T a22 = r2[2] - l20 * l20 - l21 * l21;
             i22 = zrsqrt(a22);
-            ok = ok && (a00 > T(0)) && (a11 > T(0)) && (a22 > T(0)) && (i00 < T(3.0e38)) && (i11 < T(3.0e38)) &&
-                 (i22 < T(3.0e38));
+            pmin = fmin(pmin, fmin(a00, fmin(a11, a22)));
         };
         // row r of a column block (I, k): L_Ik = C_Ik L_kk^-T
         auto solve_row = [&](T (&v)[4]) {
@@ -357,6 +357,7 @@ __global__ void __launch_bounds__(32 * ZoneCfg<T>::WARPS, 2) k_zone(ZoneArgs<T> 
 
         // G = -(the border's blocks after the elimination): lane 6 v + w (v, w < 6) reads
         // entry (v, w) of the lower triangle of blocks (27 + v / 3, 27 + w / 3), v >= w
+        bool ok = pmin > T(0);
         if (lane < 21) {
             int v = 0, rem = lane;
             while (rem >= 6 - v) {
@@ -365,6 +366,7 @@ __global__ void __launch_bounds__(32 * ZoneCfg<T>::WARPS, 2) k_zone(ZoneArgs<T> 
             }
             const int w = v + rem;   // w >= v: entry (w, v) of the lower triangle
             const T gv = -Kb[sch[ZS_BIDX + ZN * (27 + w / 3) + 27 + v / 3] * ZBLK + 4 * (w % 3) + v % 3];
+            ok = ok && fabs(gv) <= T(3.0e38);   // a pivot that overflowed or was not a number
             Gs[6 * v + w] = gv;
             Gs[6 * w + v] = gv;
         }
