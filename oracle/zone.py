@@ -20,6 +20,9 @@ algebra on tiny periodic grids.
   minus the work of those fixed forces.  For the single-point zone this is
   Eq. 8 in the constant-traction reading; for the whole domain it is the
   brute-force shift.
+* ``zone_shift_local`` is the same shift for the 27-point zone (half-width 1)
+  written on the zone's own 27 nodes, so that it serves grids of any size
+  (pinned to ``zone_shift`` on small grids).
 """
 from __future__ import annotations
 
@@ -140,6 +143,78 @@ def zone_shift(spins, Ct, Ebar, u0, p, q_new, r, Bs=None):
     u1[dofs] = du
     W_new = energy(Bs, Cp2, Ebar, u1, pts) - g @ u1
     return W_new - W_old
+
+
+def zone_shift_local(spins, Ct, Ebar, u0, x, y, z, q_new):
+    """zone_shift for the zone of half-width 1 around voxel (x, y, z), on the zone's
+    own nodes: the 27 points span 2 x 2 x 2 cells and their 3 x 3 x 3 nodes (grid
+    edges >= 6, so the nodes are distinct), and every point's strain-displacement
+    map touches only those, so restricting B_p to the 81 zone DOFs changes nothing.
+    u0: (nnodes, 3) current displacement."""
+    nz, ny, nx = spins.shape
+    nbx, nby, nbz = nx // 2, ny // 2, nz // 2
+    u0 = np.asarray(u0).reshape(-1, 3)
+    lo = ((x - 1) // 2, (y - 1) // 2, (z - 1) // 2)          # the zone's lowest node (unwrapped)
+    nodes = [((lo[0] + i) % nbx) + nbx * (((lo[1] + j) % nby) + nby * ((lo[2] + k) % nbz))
+             for k in range(3) for j in range(3) for i in range(3)]
+    u = u0[nodes].reshape(-1)                                   # local DOF 3 (i + 3 j + 9 k) + alpha
+    pts, Bs, Cp = [], [], []
+    for dz in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                px, py, pz = x + dx, y + dy, z + dz                 # unwrapped voxel coordinates
+                xi = np.array([((px & 1) + 0.5) / H, ((py & 1) + 0.5) / H, ((pz & 1) + 0.5) / H])
+                B = np.zeros((6, 81))
+                for dk in (0, 1):
+                    for dj in (0, 1):
+                        for di in (0, 1):
+                            n = [xi[0] if di else 1 - xi[0], xi[1] if dj else 1 - xi[1], xi[2] if dk else 1 - xi[2]]
+                            sg = [(1 if di else -1) / H, (1 if dj else -1) / H, (1 if dk else -1) / H]
+                            g = (sg[0] * n[1] * n[2], n[0] * sg[1] * n[2], n[0] * n[1] * sg[2])
+                            li = (px // 2 + di - lo[0]) + 3 * ((py // 2 + dj - lo[1]) + 3 * (pz // 2 + dk - lo[2]))
+                            B[:, 3 * li + 0] += (g[0], 0, 0, 0, g[2], g[1])
+                            B[:, 3 * li + 1] += (0, g[1], 0, g[2], 0, g[0])
+                            B[:, 3 * li + 2] += (0, 0, g[2], g[1], g[0], 0)
+                Bs.append(B)
+                Cp.append(Ct[int(spins[pz % nz, py % ny, px % nx])])
+                pts.append((dx, dy, dz))
+    Bs = np.stack(Bs)
+    Cp = np.stack(Cp)
+    # dead forces of the reservoir on the zone's nodes, frozen at the current state
+    g = np.zeros(81)
+    for s in range(27):
+        g += VP * Bs[s].T @ (Cp[s] @ (Ebar + Bs[s] @ u))
+    W_old = energy(Bs, Cp, Ebar, u) - g @ u
+    Cp2 = Cp.copy()
+    Cp2[13] = Ct[q_new]                                          # the site: offset (0, 0, 0)
+    K, F = assemble(Bs, Cp2, Ebar)
+    du, *_ = np.linalg.lstsq(K, g - F, rcond=None)
+    W_new = energy(Bs, Cp2, Ebar, du) - g @ du
+    return W_new - W_old
+
+
+def site_trial_zone_local(spins, x, y, z, seed, mcs, replica, J, kT, trial, Q, lam, Ct, Ebar, u0):
+    """site_trial_zone for the zone of half-width 1 with zone_shift_local (any grid size)."""
+    from . import TRIAL_NEIGHBOR, accept_threshold, site_draws
+    nz, ny, nx = spins.shape
+    w = site_draws(nx, ny, x, y, z, seed, mcs, replica, trial)
+    nb = [int(spins[z, y, (x - 1) % nx]), int(spins[z, y, (x + 1) % nx]),
+          int(spins[z, (y - 1) % ny, x]), int(spins[z, (y + 1) % ny, x]),
+          int(spins[(z - 1) % nz, y, x]), int(spins[(z + 1) % nz, y, x])]
+    q = int(spins[z, y, x])
+    if trial == TRIAL_NEIGHBOR:
+        qn = nb[(int(w[0]) * 6) >> 32]
+    else:
+        qn = (int(w[0]) * int(Q)) >> 32
+    if qn == q:
+        return False, qn, 0.0, -1.0
+    dE = sum(1 for v in nb if v == q) - sum(1 for v in nb if v == qn)
+    dHe = lam * zone_shift_local(spins, Ct, Ebar, u0, x, y, z, qn)
+    if dHe == 0.0:
+        return (dE <= 0 or float(w[1]) < accept_threshold(dE, J, kT)), qn, J * dE, -1.0
+    Ht = J * dE + dHe
+    t = -kT * np.log((float(w[1]) + 0.5) / 4294967296.0) if kT > 0 else 0.0
+    return bool(Ht <= t), qn, Ht, t
 
 
 # ---------------------------------------------------------------------------

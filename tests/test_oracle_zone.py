@@ -97,3 +97,30 @@ def test_uniform_field_has_no_moves(poly):
     n, ch, _, _ = Z.half_sweep_zone(sp, 0, 4, 2, 0, 1.0, 0.7, O.TRIAL_NEIGHBOR, 5, 3e3, poly["Ct"],
                                     poly["E"], poly["u0"], 1, poly["Bs"])
     assert n == 0 and not sp.any()
+
+
+@pytest.mark.parametrize("shape", [(6, 6, 8), (8, 10, 6)])
+def test_local_radius_one_shift_equals_the_global_one(shape):
+    """zone_shift_local (the 27 nodes of the zone only) equals zone_shift with r = 1 on
+    the whole grid's strain matrices, for sites at every parity and at the periodic wrap,
+    and the local trial equals the global one decision for decision."""
+    eul = S.euler_uniform_so3(5, 31)
+    sp = S.voronoi_spins(shape, 6, 5, 32)
+    A, Ct, St = O.tables(eul, *C3)
+    Bs = Z.all_strain_matrices(shape)
+    rng = np.random.default_rng(33)
+    u0 = rng.normal(size=Bs.shape[2]) * 2e-4
+    E = np.array([1e-3, -3e-4, -4e-4, 2e-4, -1e-4, 1e-4])
+    nz, ny, nx = shape
+    sites = [(0, 0, 0), (nx - 1, ny - 1, nz - 1), (1, 2, 3), (2, 1, 0), (3, 3, 3), (nx - 2, 0, nz - 1)]
+    sites += [tuple(int(v) for v in rng.integers(0, [nx, ny, nz])) for _ in range(6)]
+    for (x, y, z) in sites:
+        p = x + nx * (y + ny * z)
+        for qn in (0, 3):
+            g = Z.zone_shift(sp, Ct, E, u0, p, qn, 1, Bs)
+            l = Z.zone_shift_local(sp, Ct, E, u0.reshape(-1, 3), x, y, z, qn)
+            assert abs(g - l) <= 1e-10 * abs(g) + 1e-15, (x, y, z, qn, g, l)
+        a = Z.site_trial_zone(sp, x, y, z, 7, 2, 0, 1.0, 0.7, O.TRIAL_NEIGHBOR, 5, 3e3, Ct, E, u0, 1, Bs)
+        b = Z.site_trial_zone_local(sp, x, y, z, 7, 2, 0, 1.0, 0.7, O.TRIAL_NEIGHBOR, 5, 3e3, Ct, E, u0)
+        assert a[0] == b[0] and a[1] == b[1]
+        assert abs(a[2] - b[2]) <= 1e-9 * max(1.0, abs(a[2]))
