@@ -134,3 +134,49 @@ def test_zone_needs_edges_of_six(G):
     with pytest.raises(G.HMCError) as e:
         G.HMC((4, 6, 6), 3, elastic=G.HMC_ELASTIC_ZONE1)
     assert e.value.status == G.HMC_ERR_ARG
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_zone_at_128_cubed_sampled(G, precision):
+    """The 27-point zone sweep on the 128^3 workload (Q = 256, 5 000 grains, 2e-3 along
+    [001]) in the launch configuration the bench times, against the oracle's zone solve on
+    the zone's own nodes (zone_shift_local) for sampled sites of one half sweep from a
+    synthetic displacement.  FP64: every sampled decision equal unless within 1e-9 of its
+    threshold; FP32: within 1e-4."""
+    spec, euler, spins = S.workload_inputs("ni128")
+    shape, Q = spec["shape"], spec["Q"]
+    nz, ny, nx = shape
+    seed = 0x5EED1280
+    g = G.HMC(shape, Q, precision=precision, J=spec["J"], kT=spec["kT"], load_axis=tuple(spec["axis"]),
+              strain=spec["strain"], elastic=G.HMC_ELASTIC_ZONE1, mpm_steps_per_mcs=spec["mpm_steps"], seed=seed,
+              **C3)
+    g.set_orientations(euler, spins)
+    A, Ct, St = O.tables(euler, C3["c11"], C3["c12"], C3["c44"])
+    E = O.initial_uniaxial_strain(O.reuss_compliance(St, O.orientation_counts(spins, Q)), tuple(spec["axis"]),
+                                  spec["strain"])
+    assert np.abs(g.strain() - E).max() < 1e-12 * np.abs(E).max()
+    nn = (nx // 2) * (ny // 2) * (nz // 2)
+    rng = np.random.default_rng(41)
+    u0 = rng.normal(size=(nn, 3)) * 2e-4
+    g.set_nodal(u0, np.zeros((nn, 3)))
+    u_o = u0.astype(np.float32).astype(np.float64) if precision == 1 else u0   # the device holds FP32
+    g.sweep_half(0)
+    after = g.spins()
+    lam = O.elastic_scale(max(shape))
+    tol = 1e-9 if precision == 0 else 1e-4
+    n = zoned = mis = 0
+    while zoned < 60:
+        x, y, z = (int(v) for v in rng.integers(0, [nx, ny, nz]))
+        if (x + y + z) & 1:
+            x = (x + 1) % nx
+        acc, qn, dH, t = Z.site_trial_zone_local(spins, x, y, z, seed, 0, 0, spec["J"], spec["kT"],
+                                                 O.TRIAL_NEIGHBOR, Q, lam, Ct, E, u_o)
+        q = int(spins[z, y, x])
+        zoned += int(qn != q)
+        n += 1
+        want = qn if acc else q
+        if after[z, y, x] != want:
+            mis += 1
+            assert t >= 0 and abs(dH - t) <= tol * max(1.0, abs(t)), (x, y, z, dH, t)
+    assert mis <= (0 if precision == 0 else 2)
+    g.close()
