@@ -71,7 +71,7 @@ __host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) & ~size
 __host__ __device__ constexpr size_t zone_cta_bytes() { return align16(ZSCHED_CAP * sizeof(uint16_t)); }
 template <typename T>
 __host__ __device__ constexpr size_t zone_warp_bytes() {
-    return align16((ZSLOT_CAP * ZBLK + 72) * sizeof(T) + 64 + 8 + 32 + 8);
+    return align16((ZSLOT_CAP * ZBLK + 72) * sizeof(T) + 8 + 32 + 8);
 }
 template <typename T>
 __host__ __device__ constexpr size_t zone_smem() {
@@ -137,8 +137,7 @@ __global__ void __launch_bounds__(32 * ZoneCfg<T>::WARPS, 2) k_zone(ZoneArgs<T> 
     T *Kb = reinterpret_cast<T *>(wb);                     // block slots of the bordered zone matrix
     T *Gs = Kb + ZSLOT_CAP * ZBLK;                         // G, 6 x 6
     T *dCs = Gs + 36;                                      // C'(q_new) - C'(q_old), 6 x 6
-    uint8_t *dmap = reinterpret_cast<uint8_t *>(dCs + 36); // (zone cell, corner) -> node order
-    uint8_t *inv = dmap + 64;                              // order - 19 -> corner of the site's cell
+    uint8_t *inv = reinterpret_cast<uint8_t *>(dCs + 36);  // order - 19 -> corner of the site's cell
     uint8_t *plist = inv + 8;                              // zone points grouped by zone cell
     uint8_t *cend = plist + 32;                            // end of each cell's group in plist
 
@@ -169,14 +168,12 @@ __global__ void __launch_bounds__(32 * ZoneCfg<T>::WARPS, 2) k_zone(ZoneArgs<T> 
             my_pos = (Xw & 1) + 2 * (Yw & 1) + 4 * (Zw & 1);
             my_q = spin_of(b, local_slot(my_pos));
         }
-        // node orders of each zone cell's corners, and the zone points grouped by cell
-        for (int l = lane; l < 64; l += 32) {
-            const int c = l >> 3, k = l & 7;
+        // the site cell's corners by node order (orders 19..26), and the zone points grouped by cell
+        if (lane < 8) {
+            const int c = pcx + 2 * pcy + 4 * pcz, k = lane;
             const int lx = (c & 1) + (k & 1), ly = ((c >> 1) & 1) + ((k >> 1) & 1), lz = (c >> 2) + (k >> 2);
             const int rx = pcx ? lx : 2 - lx, ry = pcy ? ly : 2 - ly, rz = pcz ? lz : 2 - lz;
-            const uint8_t o = (uint8_t)sch[rx + 3 * ry + 9 * rz];
-            dmap[l] = o;
-            if (c == pcx + 2 * pcy + 4 * pcz) inv[o - 19] = (uint8_t)k;
+            inv[sch[rx + 3 * ry + 9 * rz] - 19] = (uint8_t)k;
         }
         if (lane < 8) {
             // offsets of cell c along one axis: the site's own cell (1 in the zone when the
