@@ -46,6 +46,8 @@ FP32_LANES = 128
 # (corner differences, gradient interpolation, strain, Hooke's law in the cubic form
 # (66 flop), traction sums, force interpolation, corner assembly, node update), FMA = 2 flop
 MPM_FLOP_PER_POINT = 132
+# the FP64 step's Hooke product is the 21-entry symmetric row (72 flop instead of 66)
+MPM_FLOP_PER_POINT_F64 = 138
 MPM_BYTES_PER_POINT = {"f32": 8, "f64": 14}      # spin 2 + (u,v) read + (u,v) write, per point
 SWEEP_BYTES_PER_SITE = {"f32": 28, "f64": 52}    # spin read + write + stored stress read
 STRESS_BYTES_PER_SITE = {"f32": 27.5, "f64": 53}  # spin 2 + u read (per point) + stress write
@@ -54,6 +56,15 @@ STRESS_BYTES_PER_SITE = {"f32": 27.5, "f64": 53}  # spin 2 + u read (per point) 
 PLAIN_BYTES_PER_POINT = 48 + 2 * 24 + 12 + 96 + 2
 CROP = 64
 ENSEMBLE_STEPS = 10
+
+
+def measured_fma_peaks(G):
+    """The device's FP32 and FP64 fused multiply-add rates, measured by the library's
+    micro-benchmark (eight independent FMA chains per thread, best of three launches):
+    what the FP32 and FP64 pipes deliver at the clock they run at under that load."""
+    return {"fp32_tflops": G.hmc_fma_peak(G.HMC_FP32, 4096), "fp64_tflops": G.hmc_fma_peak(G.HMC_FP64, 256),
+            "how": "hmc_fma_peak: every thread of (resident CTAs per SM x SMs) CTAs of 256 runs 8 independent "
+                   "FMA chains, 2 flop per FMA, best of three launches after one warm-up"}
 
 
 def parse():
@@ -372,6 +383,7 @@ def run_ours(args):
     n_sms = torch.cuda.get_device_properties(local).multi_processor_count
     fp32_peak = n_sms * FP32_LANES * 2 * sm_max * 1e6 / 1e12
     mpm_tflops = MPM_FLOP_PER_POINT * N / t_mpm / 1e12
+    fma = measured_fma_peaks(G)
     sweep_gbs = SWEEP_BYTES_PER_SITE["f32"] * (N / 2) / t_sweep / 1e9
     roofline = {"kernel": "k_mpm_step<float> (fused explicit MPM step)", "bound": "alu",
                 "achieved": mpm_tflops, "peak": fp32_peak, "unit": "TFLOP/s", "frac": mpm_tflops / fp32_peak,
@@ -380,7 +392,8 @@ def run_ours(args):
                 "peak_source": f"derived: {n_sms} SMs x {FP32_LANES} FP32 lanes x 2 flop x {sm_max:.0f} MHz "
                                f"(max SM clock, {peak_src})",
                 "hbm_view": {"achieved_gbs": MPM_BYTES_PER_POINT["f32"] * N / t_mpm / 1e9, "peak": hbm,
-                             "frac": MPM_BYTES_PER_POINT["f32"] * N / t_mpm / 1e9 / hbm}}
+                             "frac": MPM_BYTES_PER_POINT["f32"] * N / t_mpm / 1e9 / hbm},
+                "measured_fma_peaks": dict(fma, frac_of_measured_fp32=mpm_tflops / fma["fp32_tflops"])}
     roofline_sweep = {"kernel": "k_sweep<float, elastic> (red/black half sweep)", "bound": "hbm",
                       "achieved": sweep_gbs, "peak": hbm, "unit": "GB/s", "frac": sweep_gbs / hbm,
                       "traffic": kernel_traffic("sweep"),
@@ -430,6 +443,8 @@ def run_ours(args):
         fp64 = {"form": "the fused kernels instantiated in FP64", "value": v64, "unit": "site-updates/s",
                 "steps": k64, "speedup_fp32_over_fp64": value / ws / v64,
                 "mpm_cell_steps_per_s": N / t64_mpm, "mpm_ms_per_step": t64_mpm * 1e3,
+                "mpm_tflops": MPM_FLOP_PER_POINT_F64 * N / t64_mpm / 1e12,
+                "mpm_frac_of_measured_fp64": MPM_FLOP_PER_POINT_F64 * N / t64_mpm / 1e12 / fma["fp64_tflops"],
                 "plain_unfused": {
                     "form": "the explicit step in the plain form: unfused G2P/stress-increment, P2G and node kernels "
                             "with every point's FP64 stress and every cell's corner forces in global memory "
@@ -691,6 +706,7 @@ def run_zone(args):
     _, sm_max, _ = peaks()
     n_sms = torch.cuda.get_device_properties(0).multi_processor_count
     peak = n_sms * FP32_LANES * 2 * sm_max / 1e6
+    fma = measured_fma_peaks(G)
     line = {"metric": METRIC, "value": N * args.steps / t, "unit": "site-updates/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -702,7 +718,8 @@ def run_zone(args):
                          "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                          "traffic": kernel_traffic("zone"),
                          "algorithmic": f"{ZONE_FLOP_PER_TRIAL} flop/trial x {ntr:.0f} trials per half sweep",
-                         "peak_source": f"derived: {n_sms} SMs x {FP32_LANES} FP32 lanes x 2 flop x {sm_max:.0f} MHz"},
+                         "peak_source": f"derived: {n_sms} SMs x {FP32_LANES} FP32 lanes x 2 flop x {sm_max:.0f} MHz",
+                         "measured_fma_peaks": dict(fma, frac_of_measured_fp32=achieved / fma["fp32_tflops"])},
             "gpu_launches": args.steps * (spec["mpm_steps"] + 2 + 2 * 2), "clocks": clk}
     print(json.dumps(line), flush=True)
     g.close()

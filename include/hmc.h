@@ -418,6 +418,15 @@ hmc_status hmc_adjoint_backward(hmc_handle *h, double gW, const double *g_field,
 /* Wait for all work on the handle's stream. */
 hmc_status hmc_synchronize(hmc_handle *h);
 
+/* Measured peak fused multiply-add rate of the current device (a measurement utility
+ * with no counterpart in the paper): precision HMC_FP32 or HMC_FP64; every thread of a
+ * grid of the resident CTAs per SM times the SM count runs eight independent FMA chains
+ * for iters x 16 steps; *tflops receives 2 flop per FMA over the best of three timed
+ * launches (CUDA events on a private stream).  Allocates and frees a small device buffer;
+ * HMC_ERR_ARG for a bad precision, iters outside 1..65536 or NULL tflops, HMC_ERR_CUDA
+ * on any CUDA error.  Needs no handle. */
+hmc_status hmc_fma_peak(int32_t precision, int32_t iters, double *tflops);
+
 /* Message of the last failed call on h (or of the last failed hmc_create when
  * h is NULL).  Valid until the next call on the same handle. */
 const char *hmc_last_error(const hmc_handle *h);

@@ -80,6 +80,7 @@ def _load():
         "hmc_select_replica": (st, [H, C.c_int32]),
         "hmc_get_tuning": (st, [H, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
         "hmc_get_sweep_tuning": (st, [H, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+        "hmc_fma_peak": (st, [C.c_int32, C.c_int32, C.POINTER(C.c_double)]),
         "hmc_destroy": (None, [H]),
         "hmc_set_orientations": (st, [H, dp, u16p]),
         "hmc_set_spins": (st, [H, u16p]),
@@ -164,6 +165,13 @@ def hmc_create_batch(params):
 
 def hmc_select_replica(h, r):
     _check(h, lib.hmc_select_replica(h, int(r)))
+
+
+def hmc_fma_peak(precision, iters=4096):
+    """Measured peak FMA rate of the current device in TFLOP/s (FP32 or FP64)."""
+    t = C.c_double(0.0)
+    _check(None, lib.hmc_fma_peak(int(precision), int(iters), C.byref(t)))
+    return t.value
 
 
 def hmc_get_sweep_tuning(h):

@@ -57,3 +57,12 @@ def test_default_params(libhmc):
     assert (p.nx, p.ny, p.nz, p.n_orient) == (32, 32, 32, 64)
     assert p.precision == G.HMC_FP32 and p.elastic == G.HMC_ELASTIC_TRACTION
     assert p.elastic_scale < 0 and p.dt < 0 and p.damping < 0
+
+
+def test_fma_peak_rejects_bad_arguments_on_host(libhmc):
+    import paper_1009_0457_gb300 as G
+    t = C.c_double(-1.0)
+    for prec, iters in [(7, 16), (G.HMC_FP32, 0), (G.HMC_FP64, -3), (G.HMC_FP32, (1 << 16) + 1)]:
+        assert G.lib.hmc_fma_peak(prec, iters, C.byref(t)) == G.HMC_ERR_ARG
+    assert G.lib.hmc_fma_peak(G.HMC_FP32, 16, None) == G.HMC_ERR_ARG
+    assert t.value == -1.0
