@@ -44,14 +44,15 @@ namespace {
 // Schedule table (uint16, built by zone_schedule), orders 0..26 the real nodes and 27, 28
 // the two pseudo-nodes of B_p (ZN = 29 orders):
 //   [0, 27)        elimination order of reflected node rx + 3 ry + 9 rz
-//   [27, 55)       per step k: first column-block entry (slot of block (I, k))
-//   [55, 83)       per step k: first update entry (slots of (I,J), (I,k), (J,k))
+//   [27]           number of update rounds (the first six are the outer corners' steps 1..6)
 //   [83, 110)      slot of the diagonal block of order k
 //   [110, 951)     slot of block (I, J), I >= J, of ZN x ZN in the filled pattern (0xffff: zero)
-//   then the column-block entries, then the update triples.
+//   [952, ...)     per round and lane: the slots of the lane's update -- target (I, J),
+//                  column blocks (I, k) and (J, k), diagonal block (k, k) -- or 0xffff (no update)
 constexpr int ZN = 29;
-constexpr int ZS_NBOFF = 27, ZS_UPOFF = 55, ZS_DIAG = 83, ZS_BIDX = 110, ZS_HDR = ZS_BIDX + ZN * ZN;
-constexpr int ZSCHED_CAP = 4608;
+constexpr int ZS_NROUND = 27, ZS_DIAG = 83, ZS_BIDX = 110, ZS_HDR = ZS_BIDX + ZN * ZN;
+constexpr int ZS_RND = (ZS_HDR + 3) & ~3;   // 8-byte aligned rounds of 32 x 4 entries
+constexpr int ZSCHED_CAP = 5184;
 constexpr int ZSLOT_CAP = 228;   // 3x3 blocks of the filled lower triangle (227 for this pattern) + the unused slot
 constexpr int ZBLK = 12;         // a block: 3 rows of 4 values (the 4th pads a row to 16 B)
 constexpr int ZROW = 320;        // an element matrix's 300 upper-triangle entries, padded to 10 x 32
@@ -267,28 +268,32 @@ __global__ void __launch_bounds__(32 * ZoneCfg<T>::WARPS, 2) k_zone(ZoneArgs<T> 
                 st4(C + 4 * r, cv[r]);
             }
         };
-        // Elimination step k.  No column block or factor is read after its own step (the
-        // border's Schur complement, not a stored factor, gives G), so each update lane forms the
-        // two column blocks it needs from the unsolved ones (the same arithmetic as a column
-        // solve) and nothing of the column is stored -- one warp barrier per step.
-        auto elim = [&](int k) {
-            factor(Kb + sch[ZS_DIAG + k] * ZBLK);
-            const int up0 = sch[ZS_UPOFF + k], up1 = sch[ZS_UPOFF + k + 1];
-            for (int t = up0 + 3 * lane; t < up1; t += 96) {
-                T *C = Kb + sch[t] * ZBLK;
-                const int sI = sch[t + 1], sJ = sch[t + 2];
-                const T *LI = Kb + sI * ZBLK, *LJ = Kb + sJ * ZBLK;
+        // One round of block updates, a warp barrier after it.  No column block or factor is
+        // read after its own step (the border's Schur complement, not a stored factor, gives
+        // G), so each update lane factors its step's pivot and forms the two column blocks it
+        // needs from the unsolved ones (the same arithmetic as a column solve); nothing of the
+        // column is stored.  The host schedules every update into the earliest round after
+        // the updates it reads (its pivot's and its column blocks' last updates, its target's
+        // previous one), so a round may hold the updates of several steps, and every block
+        // gets its updates in step order, as in a step-by-step elimination.
+        auto elim_round = [&](int r) {
+            const uint2 it = *reinterpret_cast<const uint2 *>(sch + ZS_RND + 128 * r + 4 * lane);
+            const uint32_t sC = it.x & 0xffffu;
+            if (sC != 0xffffu) {
+                factor(Kb + (it.y >> 16) * ZBLK);
+                T *C = Kb + sC * ZBLK;
+                const T *LI = Kb + (it.x >> 16) * ZBLK, *LJ = Kb + (it.y & 0xffffu) * ZBLK;
                 T li[3][4], lj[3][4], cv[3][4];
 #pragma unroll
-                for (int r = 0; r < 3; ++r) {
-                    ld4(LI + 4 * r, li[r]);
-                    ld4(LJ + 4 * r, lj[r]);
-                    ld4(C + 4 * r, cv[r]);
+                for (int rr = 0; rr < 3; ++rr) {
+                    ld4(LI + 4 * rr, li[rr]);
+                    ld4(LJ + 4 * rr, lj[rr]);
+                    ld4(C + 4 * rr, cv[rr]);
                 }
 #pragma unroll
-                for (int r = 0; r < 3; ++r) {
-                    solve_row(li[r]);
-                    solve_row(lj[r]);
+                for (int rr = 0; rr < 3; ++rr) {
+                    solve_row(li[rr]);
+                    solve_row(lj[rr]);
                 }
                 update(C, li, lj, cv);
             }
@@ -335,7 +340,7 @@ __global__ void __launch_bounds__(32 * ZoneCfg<T>::WARPS, 2) k_zone(ZoneArgs<T> 
                     // rows are in flight.  Later cells add to the blocks it updates.
                     const int rc = c ^ (~refl & 7);
                     const int kc = sch[2 * (rc & 1) + 6 * ((rc >> 1) & 1) + 18 * (rc >> 2)];
-                    if (kc >= 1 && kc <= 6) elim(kc);
+                    if (kc >= 1 && kc <= 6) elim_round(kc - 1);
                     ++c;
                     cn = c < 8 ? cend[c] : 27;
                 }
@@ -348,9 +353,10 @@ __global__ void __launch_bounds__(32 * ZoneCfg<T>::WARPS, 2) k_zone(ZoneArgs<T> 
         }
         __syncwarp();
 
-        // the remaining steps: edges and face centres, the site cell (the corners were eliminated
-        // during the assembly)
-        for (int k = 7; k < 27; ++k) elim(k);
+        // the remaining steps (edges and face centres, the site cell) in their scheduled rounds;
+        // the corners were eliminated during the assembly
+        const int nround = sch[ZS_NROUND];
+        for (int r = 6; r < nround; ++r) elim_round(r);
         __syncwarp();
 
         // G = -(the border's blocks after the elimination): lane 6 v + w (v, w < 6) reads
@@ -546,19 +552,23 @@ template cudaError_t launch_zone<double>(const ZoneArgs<double> &, int, cudaStre
 
 namespace {
 
+// One block update C_IJ -= L_Ik L_Jk^T of elimination step k, by block ids ZN * I + J.
+struct ZUpdate {
+    int C = -1, I = -1, J = -1, D = -1;   // target, column blocks (I, k) and (J, k), pivot (k, k)
+};
+
 // Shared-memory layout of the factorisation.  A block's row r of slot s is the 16-byte
 // unit 3 s + r of the warp's block area, so the eight lanes of a quarter warp that load
 // row r of distinct blocks s hit distinct bank groups exactly when their s are distinct
 // mod 8 (3 is odd); lanes loading the same block share the access.  The cost of a layout
-// is the number of shared-memory wavefronts of the block loads and stores of the column
-// solves and the updates (32 lanes, four quarters per 16-byte access), with the slots of
-// the blocks and the order of each step's updates as the free choices; neither changes
-// any arithmetic (each block gets one update per step, and where it is stored does not
-// matter), so every layout gives the same bits.
+// is the number of shared-memory wavefronts of the block loads and stores of the
+// updates (32 lanes, four quarters per 16-byte access), with the slots of the blocks and
+// the lane of each update within its round as the free choices; neither changes any
+// arithmetic (each block gets its updates in the same order, and where it is stored does
+// not matter), so every layout gives the same bits.
 struct ZoneLayout {
-    std::vector<std::vector<int>> nb;                    // per step: column-block rows I
-    std::vector<std::vector<std::pair<int, int>>> up;    // per step: update blocks (I, J)
-    std::vector<int> slot_of;                            // ZN * I + J -> slot (-1 if structurally zero)
+    std::vector<std::vector<ZUpdate>> rounds;   // per round 32 lanes (C < 0: no update)
+    std::vector<int> slot_of;                   // ZN * I + J -> slot (-1 if structurally zero)
 };
 
 int quarter_wavefronts(const int *s, int n) {
@@ -572,24 +582,24 @@ int quarter_wavefronts(const int *s, int n) {
     return w;
 }
 
-long step_cost(const ZoneLayout &L, int k) {
+long round_cost(const ZoneLayout &L, int r) {
     long c = 0;
     int s[8];
-    const auto &u = L.up[k];
-    for (size_t q = 0; q < u.size(); q += 8) {
-        const int n = (int)std::min<size_t>(8, u.size() - q);
-        for (int which = 0; which < 3; ++which) {
-            for (int i = 0; i < n; ++i) {
-                const int I = u[q + i].first, J = u[q + i].second;
-                s[i] = L.slot_of[which == 0 ? ZN * I + J : which == 1 ? ZN * I + k : ZN * J + k];
+    const auto &u = L.rounds[r];
+    for (int q = 0; q < 32; q += 8)
+        for (int which = 0; which < 4; ++which) {
+            int n = 0;
+            for (int i = q; i < q + 8; ++i) {
+                const ZUpdate &x = u[i];
+                if (x.C < 0) continue;
+                s[n++] = L.slot_of[which == 0 ? x.C : which == 1 ? x.I : which == 2 ? x.J : x.D];
             }
-            c += quarter_wavefronts(s, n) * (which == 0 ? 4 : 3);   // C: 3 loads + 3 stores
+            if (n) c += quarter_wavefronts(s, n) * (which == 0 ? 6 : 3);   // C: 3 loads + 3 stores
         }
-    }
     return c;
 }
 
-// Simulated annealing over slot swaps and swaps of two updates of one step (fixed seed,
+// Simulated annealing over slot swaps and swaps of two lanes of one round (fixed seed,
 // splitmix64; a few tenths of a second, once per process).
 void optimise_layout(ZoneLayout &L, int nslots) {
     uint64_t st = 0x5EEDC0DE12345ull;
@@ -599,60 +609,53 @@ void optimise_layout(ZoneLayout &L, int nslots) {
         z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
         return z ^ (z >> 31);
     };
-    std::vector<std::vector<int>> steps_of(nslots);   // steps whose cost involves a slot
-    auto rebuild = [&]() {
-        for (auto &v : steps_of) v.clear();
-        for (int k = 0; k < 27; ++k) {
-            std::vector<int> ss;
-            for (auto &ij : L.up[k]) {
-                ss.push_back(L.slot_of[ZN * ij.first + ij.second]);
-                ss.push_back(L.slot_of[ZN * ij.first + k]);
-                ss.push_back(L.slot_of[ZN * ij.second + k]);
-            }
-            std::sort(ss.begin(), ss.end());
-            ss.erase(std::unique(ss.begin(), ss.end()), ss.end());
-            for (int x : ss) steps_of[x].push_back(k);
-        }
-    };
-    rebuild();
-    std::vector<int> owner(nslots, -1);   // slot -> 27 I + J
+    const int nr = (int)L.rounds.size();
+    std::vector<std::vector<int>> rounds_of(nslots);   // rounds whose cost involves a slot
+    for (int r = 0; r < nr; ++r) {
+        std::vector<int> ss;
+        for (const ZUpdate &x : L.rounds[r])
+            if (x.C >= 0)
+                for (int b : {x.C, x.I, x.J, x.D}) ss.push_back(L.slot_of[b]);
+        std::sort(ss.begin(), ss.end());
+        ss.erase(std::unique(ss.begin(), ss.end()), ss.end());
+        for (int x : ss) rounds_of[x].push_back(r);
+    }
+    std::vector<int> owner(nslots, -1);   // slot -> ZN I + J
     for (int b = 0; b < ZN * ZN; ++b)
         if (L.slot_of[b] >= 0) owner[L.slot_of[b]] = b;
-    std::vector<long> cost(27);
-    for (int k = 0; k < 27; ++k) cost[k] = step_cost(L, k);
+    std::vector<long> cost(nr);
+    for (int r = 0; r < nr; ++r) cost[r] = round_cost(L, r);
     double T = 2.0;
     for (int it = 0; it < 120000; ++it) {
         if (rnd() & 1) {
             const int a = (int)(rnd() % nslots), b = (int)(rnd() % nslots);
             if (a == b || owner[a] < 0 || owner[b] < 0) continue;
-            std::vector<int> ks = steps_of[a];
-            ks.insert(ks.end(), steps_of[b].begin(), steps_of[b].end());
-            std::sort(ks.begin(), ks.end());
-            ks.erase(std::unique(ks.begin(), ks.end()), ks.end());
+            std::vector<int> rs = rounds_of[a];
+            rs.insert(rs.end(), rounds_of[b].begin(), rounds_of[b].end());
+            std::sort(rs.begin(), rs.end());
+            rs.erase(std::unique(rs.begin(), rs.end()), rs.end());
             long before = 0, after = 0;
-            for (int k : ks) before += cost[k];
+            for (int r : rs) before += cost[r];
             std::swap(L.slot_of[owner[a]], L.slot_of[owner[b]]);
-            std::vector<long> nc(ks.size());
-            for (size_t i = 0; i < ks.size(); ++i) after += (nc[i] = step_cost(L, ks[i]));
+            std::vector<long> nc(rs.size());
+            for (size_t i = 0; i < rs.size(); ++i) after += (nc[i] = round_cost(L, rs[i]));
             if (after <= before || (double)(rnd() >> 11) * 0x1.0p-53 < std::exp((before - after) / T)) {
                 std::swap(owner[a], owner[b]);
-                std::swap(steps_of[a], steps_of[b]);
-                for (size_t i = 0; i < ks.size(); ++i) cost[ks[i]] = nc[i];
+                std::swap(rounds_of[a], rounds_of[b]);
+                for (size_t i = 0; i < rs.size(); ++i) cost[rs[i]] = nc[i];
             } else {
                 std::swap(L.slot_of[owner[a]], L.slot_of[owner[b]]);
             }
         } else {
-            const int k = (int)(rnd() % 27);
-            const int n = (int)L.up[k].size();
-            if (n < 2) continue;
-            const int a = (int)(rnd() % n), b = (int)(rnd() % n);
-            if (a == b) continue;
-            std::swap(L.up[k][a], L.up[k][b]);
-            const long nc = step_cost(L, k);
-            if (nc <= cost[k] || (double)(rnd() >> 11) * 0x1.0p-53 < std::exp((cost[k] - nc) / T))
-                cost[k] = nc;
+            const int r = (int)(rnd() % nr);
+            const int a = (int)(rnd() % 32), b = (int)(rnd() % 32);
+            if (a == b || (L.rounds[r][a].C < 0 && L.rounds[r][b].C < 0)) continue;
+            std::swap(L.rounds[r][a], L.rounds[r][b]);
+            const long nc = round_cost(L, r);
+            if (nc <= cost[r] || (double)(rnd() >> 11) * 0x1.0p-53 < std::exp((cost[r] - nc) / T))
+                cost[r] = nc;
             else
-                std::swap(L.up[k][a], L.up[k][b]);
+                std::swap(L.rounds[r][a], L.rounds[r][b]);
         }
         T = std::max(0.05, T * 0.99995);
     }
@@ -664,9 +667,12 @@ void optimise_layout(ZoneLayout &L, int nslots) {
 // site's cell = nodes with all coordinates in {1,2}); layout at the top of this
 // file.  Nodes share a block of K when they lie in a common zone cell
 // (Chebyshev distance <= 1); the symbolic factorisation adds the fill of each
-// step, and every block of the filled lower triangle gets a storage slot, placed
-// (with the order of each step's updates) by optimise_layout to spread the lanes'
-// block accesses over the shared-memory banks.  Built once per process.
+// step.  The outer corners' steps (1..6) are one round each, run during the
+// assembly; the updates of the later steps are list-scheduled into rounds of 32
+// lanes, each as early as the updates it reads allow (longest remaining chain
+// first).  Every block of the filled lower triangle gets a storage slot, placed
+// (with the lane of each update) by optimise_layout to spread the lanes' block
+// accesses over the shared-memory banks.  Built once per process.
 std::vector<uint16_t> zone_schedule_build();
 
 std::vector<uint16_t> zone_schedule() {
@@ -688,10 +694,10 @@ std::vector<uint16_t> zone_schedule_build() {
     for (int n = 1; n < 27; ++n)
         if (cls(n) == 0) order.push_back(n);
     // the nine edge nodes and three face centres outside the site's cell, in the order with
-    // the fewest update rounds of 32 lanes (found by exhaustive local search over the orders
-    // of these 12 nodes): 576 block updates in 25 rounds, against 696 in 29 with all edges
-    // before the face centres.  Node B = (1,0,0) (y, z fixed) and node C = (0,1,0) (z fixed)
-    // are among them; any order of a positive definite matrix gives positive pivots.
+    // the fewest block updates (found by exhaustive local search over the orders of these 12
+    // nodes): 576 block updates, against 696 with all edges before the face centres.  Node
+    // B = (1,0,0) (y, z fixed) and node C = (0,1,0) (z fixed) are among them; any order of a
+    // positive definite matrix gives positive pivots.
     for (int n : {7, 1, 21, 4, 3, 5, 15, 9, 12, 19, 11, 10}) order.push_back(n);
     for (int n = 0; n < 27; ++n)
         if (cls(n) == 3) order.push_back(n);
@@ -716,23 +722,74 @@ std::vector<uint16_t> zone_schedule_build() {
             pat[i][j] = dmax <= 1;
         }
     // symbolic elimination of the 27 real nodes (the pseudo-nodes are never eliminated)
-    std::vector<std::vector<int>> nb(27);
-    std::vector<std::vector<std::pair<int, int>>> up(27);
+    std::vector<std::vector<ZUpdate>> up(27);
     for (int k = 0; k < 27; ++k) {
+        std::vector<int> nb;
         for (int i = k + 1; i < ZN; ++i)
-            if (pat[i][k]) nb[k].push_back(i);
-        for (int I : nb[k])
-            for (int J : nb[k])
+            if (pat[i][k]) nb.push_back(i);
+        for (int I : nb)
+            for (int J : nb)
                 if (J <= I) {
-                    up[k].push_back({I, J});
+                    up[k].push_back({ZN * I + J, ZN * I + k, ZN * J + k, (ZN + 1) * k});
                     pat[I][J] = pat[J][I] = true;
                 }
     }
-    std::vector<uint16_t> t(ZS_HDR, 0);
-    for (int i = 0; i < 27; ++i) t[order[i]] = (uint16_t)i;
     ZoneLayout L;
-    L.nb = nb;
-    L.up = up;
+    // steps 1..6 (the outer corners): one round each
+    for (int k = 1; k <= 6; ++k) {
+        if (up[k].size() > 32) return {};
+        std::vector<ZUpdate> r(32);
+        for (size_t i = 0; i < up[k].size(); ++i) r[i] = up[k][i];
+        L.rounds.push_back(r);
+    }
+    // steps 7..26: an update reads its pivot and its two column blocks after their last
+    // updates and its target after the target's previous update
+    std::vector<ZUpdate> items;
+    std::vector<int> step_of;
+    for (int k = 7; k < 27; ++k)
+        for (const ZUpdate &x : up[k]) {
+            items.push_back(x);
+            step_of.push_back(k);
+        }
+    const int ni = (int)items.size();
+    std::vector<std::vector<int>> deps(ni), succ(ni);
+    {
+        std::vector<int> last(ZN * ZN, -1);   // block -> latest update of it among the items so far
+        for (int i = 0; i < ni; ++i) {
+            for (int b : {items[i].D, items[i].I, items[i].J, items[i].C})
+                if (last[b] >= 0) deps[i].push_back(last[b]);
+            last[items[i].C] = i;
+        }
+        for (int i = 0; i < ni; ++i)
+            for (int d : deps[i]) succ[d].push_back(i);
+    }
+    // Items are in step order and an update's target is updated only by earlier steps, so
+    // "latest so far" is the last update before this step for the pivot, the column blocks
+    // and the target alike.  Chain lengths to the end, then greedy rounds.
+    std::vector<int> chain(ni, 1);
+    for (int i = ni - 1; i >= 0; --i)
+        for (int s2 : succ[i]) chain[i] = std::max(chain[i], chain[s2] + 1);
+    std::vector<int> round_of(ni, -1);
+    int left = ni;
+    for (int r = 0; left > 0; ++r) {
+        std::vector<int> ready;
+        for (int i = 0; i < ni; ++i) {
+            if (round_of[i] >= 0) continue;
+            bool ok = true;
+            for (int d : deps[i]) ok = ok && round_of[d] >= 0 && round_of[d] < r;
+            if (ok) ready.push_back(i);
+        }
+        std::stable_sort(ready.begin(), ready.end(), [&](int x, int y) { return chain[x] > chain[y]; });
+        if (ready.size() > 32) ready.resize(32);
+        std::vector<ZUpdate> rr(32);
+        for (size_t l = 0; l < ready.size(); ++l) {
+            rr[l] = items[ready[l]];
+            round_of[ready[l]] = r;
+        }
+        left -= (int)ready.size();
+        L.rounds.push_back(rr);
+        if (r > 4 * ni) return {};
+    }
     L.slot_of.assign(ZN * ZN, -1);
     int slots = 0;
     for (int I = 0; I < ZN; ++I)
@@ -740,29 +797,28 @@ std::vector<uint16_t> zone_schedule_build() {
             if (pat[I][J]) L.slot_of[ZN * I + J] = slots++;
     if (slots > ZSLOT_CAP - 1) return {};   // the last slot stays free (ZTRASH)
     optimise_layout(L, slots);
-    up = L.up;
+    const size_t nround = L.rounds.size();
+    if (ZS_RND + 128 * nround > (size_t)ZSCHED_CAP) return {};
+    std::vector<uint16_t> t(ZS_RND + 128 * nround, 0);
+    for (int i = 0; i < 27; ++i) t[order[i]] = (uint16_t)i;
+    t[ZS_NROUND] = (uint16_t)nround;
     for (int I = 0; I < ZN; ++I)
         for (int J = 0; J < ZN; ++J)
             t[ZS_BIDX + ZN * I + J] = L.slot_of[ZN * I + J] >= 0 ? (uint16_t)L.slot_of[ZN * I + J] : (uint16_t)0xffff;
     for (int k = 0; k < 27; ++k) t[ZS_DIAG + k] = t[ZS_BIDX + (ZN + 1) * k];
-    size_t off = ZS_HDR;
-    for (int k = 0; k <= 27; ++k) {
-        t[ZS_NBOFF + k] = (uint16_t)off;
-        if (k < 27) off += nb[k].size();
-    }
-    for (int k = 0; k <= 27; ++k) {
-        t[ZS_UPOFF + k] = (uint16_t)off;
-        if (k < 27) off += 3 * up[k].size();
-    }
-    for (int k = 0; k < 27; ++k)
-        for (int I : nb[k]) t.push_back(t[ZS_BIDX + ZN * I + k]);
-    for (int k = 0; k < 27; ++k)
-        for (auto &ij : up[k]) {
-            t.push_back(t[ZS_BIDX + ZN * ij.first + ij.second]);
-            t.push_back(t[ZS_BIDX + ZN * ij.first + k]);
-            t.push_back(t[ZS_BIDX + ZN * ij.second + k]);
+    for (size_t r = 0; r < nround; ++r)
+        for (int l = 0; l < 32; ++l) {
+            const ZUpdate &x = L.rounds[r][l];
+            uint16_t *e = &t[ZS_RND + 128 * r + 4 * l];
+            if (x.C < 0) {
+                e[0] = e[1] = e[2] = e[3] = 0xffff;
+                continue;
+            }
+            e[0] = (uint16_t)L.slot_of[x.C];
+            e[1] = (uint16_t)L.slot_of[x.I];
+            e[2] = (uint16_t)L.slot_of[x.J];
+            e[3] = (uint16_t)L.slot_of[x.D];
         }
-    if (t.size() > (size_t)ZSCHED_CAP) return {};
     return t;
 }
 
