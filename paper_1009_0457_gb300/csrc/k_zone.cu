@@ -170,6 +170,21 @@ __global__ void __launch_bounds__(32 * ZoneCfg<T>::WARPS, 2) k_zone(ZoneArgs<T> 
             my_pos = (Xw & 1) + 2 * (Yw & 1) + 4 * (Zw & 1);
             my_q = spin_of(b, local_slot(my_pos));
         }
+        // inputs of the decision that do not depend on the zone matrix, requested now so that
+        // their latency passes during the assembly: the site cell's nodal displacement component
+        // of lane 3 corner + alpha (lane < 24), and the two stiffness entries whose difference is
+        // entry lane of C'(q_new) - C'(q_old) (lane < 21)
+        T uv = T(0), c_new = T(0), c_old = T(0);
+        if (lane < 24) {
+            const int cr = lane / 3, al = lane % 3;
+            const int gi = wrapi((x >> 1) + (cr & 1), R.nbx), gj = wrapi((y >> 1) + ((cr >> 1) & 1), R.nby);
+            const int gk = wrapi((z >> 1) + (cr >> 2), R.nbz);
+            uv = a.u[3 * (R.blk_off + gi + (long long)R.nbx * (gj + (long long)R.nby * gk)) + al];
+        }
+        if (lane < 21) {
+            c_new = __ldg(a.ctab + 24 * (size_t)qn + lane);
+            c_old = __ldg(a.ctab + 24 * (size_t)q + lane);
+        }
         // the site cell's corners by node order (orders 19..26), and the zone points grouped by cell
         if (lane < 8) {
             const int c = pcx + 2 * pcy + 4 * pcz, k = lane;
@@ -378,9 +393,6 @@ __global__ void __launch_bounds__(32 * ZoneCfg<T>::WARPS, 2) k_zone(ZoneArgs<T> 
         T eps[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
         if (lane < 24) {
             const int cr = lane / 3, al = lane % 3;
-            const int gi = wrapi((x >> 1) + (cr & 1), R.nbx), gj = wrapi((y >> 1) + ((cr >> 1) & 1), R.nby);
-            const int gk = wrapi((z >> 1) + (cr >> 2), R.nbz);
-            const T uv = a.u[3 * (R.blk_off + gi + (long long)R.nbx * (gj + (long long)R.nby * gk)) + al];
             T g[3];
             corner_grad<T>(pa, pb, pcq, cr & 1, (cr >> 1) & 1, cr >> 2, g);
 #pragma unroll
@@ -407,7 +419,7 @@ __global__ void __launch_bounds__(32 * ZoneCfg<T>::WARPS, 2) k_zone(ZoneArgs<T> 
                 ++i;
             }
             const int j = i + rem;
-            const T d = __ldg(a.ctab + 24 * (size_t)qn + lane) - __ldg(a.ctab + 24 * (size_t)q + lane);
+            const T d = c_new - c_old;
             dCs[6 * i + j] = d;
             dCs[6 * j + i] = d;
         }
