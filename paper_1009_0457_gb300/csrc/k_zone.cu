@@ -9,22 +9,27 @@
 //     dH_e / lambda = 1/2 e0 . dC (I + G dC)^-1 e0,
 // e0 = the site's strain, dC = C'(q_new) - C'(q_old), and G = B_p K^+ B_p^T the
 // compliance of the zone seen at the site (K: the zone's stiffness with the old
-// orientations, B_p: the site's strain-displacement map).
+// orientations, B_p: the site's strain-displacement map).  With K' = K + B_p^T dC B_p,
+// the zone's stiffness with the site's new orientation, the Sherman-Morrison-Woodbury
+// identity turns this into
+//     dH_e / lambda = 1/2 e0 . dC e0 - 1/2 f . K'^+ f,    f = B_p^T dC e0,
+// the energy of the stiffness change at the current strain less what the zone
+// recovers by relaxing under the force f that the change exerts on the site's nodes.
 //
-// The zone spans 2x2x2 MPM cells and their 3x3x3 nodes (81 DOFs).  K is
-// singular only in the six rigid-body modes, which B_p does not see; holding six
-// DOFs of three non-collinear nodes outside the site's cell fixed removes them
-// without changing G.  G then follows from a block (3x3 per node) Cholesky
-// elimination of the matrix K bordered by B_p: two pseudo-nodes (orders 27 and 28)
-// carry the six rows of B_p, which are nonzero only on the site's own 8 nodes.
-// The 19 nodes outside the site's cell are eliminated first (corners, which create
-// no fill, then edges and face centres in the order that needs the fewest update
-// rounds), the site's 8 nodes next, and the
-// pseudo-nodes never: eliminating all 27 real nodes leaves -B_p K^+ B_p^T = -G in
-// the pseudo-nodes' three blocks (the Schur complement of K in the bordered
-// matrix).  Node coordinates are reflected so that the site's cell is always the
-// zone's cell (1,1,1); the elimination schedule (which block pairs are structurally
-// nonzero) is then the same for every site and is built once on the host.
+// The zone spans 2x2x2 MPM cells and their 3x3x3 nodes (81 DOFs).  K' is
+// singular only in the six rigid-body modes, which f does not load (B_p sees no
+// rigid motion); holding six DOFs of three non-collinear nodes outside the site's
+// cell fixed removes them without changing f . K'^+ f.  That form follows from a
+// block (3x3 per node) Cholesky elimination of K' bordered by f: one pseudo-node
+// (order 27) carries f in the first row of its blocks, nonzero only on the site's
+// own 8 nodes.  The 19 nodes outside the site's cell are eliminated first (corners,
+// which create no fill, then edges and face centres in the order that needs the
+// fewest block updates), the site's 8 nodes next, and the pseudo-node never:
+// eliminating all 27 real nodes leaves -f . K'^+ f in the first entry of the
+// pseudo-node's diagonal block (the Schur complement of K' in the bordered matrix).
+// Node coordinates are reflected so that the site's cell is always the zone's cell
+// (1,1,1); the elimination schedule (which block pairs are structurally nonzero) is
+// then the same for every site and is built once on the host.
 //
 // One warp per trial, taken from the work list that the compaction pass of the
 // sweep writes; the zone matrix lives in shared memory; the zone's orientations
@@ -41,19 +46,19 @@ namespace hmc {
 
 namespace {
 
-// Schedule table (uint16, built by zone_schedule), orders 0..26 the real nodes and 27, 28
-// the two pseudo-nodes of B_p (ZN = 29 orders):
+// Schedule table (uint16, built by zone_schedule), orders 0..26 the real nodes and 27 the
+// pseudo-node of f (ZN = 28 orders):
 //   [0, 27)        elimination order of reflected node rx + 3 ry + 9 rz
 //   [27]           number of update rounds (the first six are the outer corners' steps 1..6)
 //   [83, 110)      slot of the diagonal block of order k
-//   [110, 951)     slot of block (I, J), I >= J, of ZN x ZN in the filled pattern (0xffff: zero)
-//   [952, ...)     per round and lane: the slots of the lane's update -- target (I, J),
+//   [110, 894)     slot of block (I, J), I >= J, of ZN x ZN in the filled pattern (0xffff: zero)
+//   [896, ...)     per round and lane: the slots of the lane's update -- target (I, J),
 //                  column blocks (I, k) and (J, k), diagonal block (k, k) -- or 0xffff (no update)
-constexpr int ZN = 29;
+constexpr int ZN = 28;
 constexpr int ZS_NROUND = 27, ZS_DIAG = 83, ZS_BIDX = 110, ZS_HDR = ZS_BIDX + ZN * ZN;
 constexpr int ZS_RND = (ZS_HDR + 3) & ~3;   // 8-byte aligned rounds of 32 x 4 entries
 constexpr int ZSCHED_CAP = 5184;
-constexpr int ZSLOT_CAP = 228;   // 3x3 blocks of the filled lower triangle (227 for this pattern) + the unused slot
+constexpr int ZSLOT_CAP = 218;   // 3x3 blocks of the filled lower triangle (217 for this pattern) + the unused slot
 constexpr int ZBLK = 12;         // a block: 3 rows of 4 values (the 4th pads a row to 16 B)
 constexpr int ZROW = 320;        // an element matrix's 300 upper-triangle entries, padded to 10 x 32
 constexpr int ZTRASH = (ZSLOT_CAP - 1) * ZBLK;   // an unused slot: target of the scatter's padding
@@ -73,7 +78,7 @@ __host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) & ~size
 __host__ __device__ constexpr size_t zone_cta_bytes() { return align16(ZSCHED_CAP * sizeof(uint16_t)); }
 template <typename T>
 __host__ __device__ constexpr size_t zone_warp_bytes() {
-    return align16((ZSLOT_CAP * ZBLK + 72) * sizeof(T) + 8 + 32 + 8);
+    return align16((ZSLOT_CAP * ZBLK + 36) * sizeof(T) + 32 + 8);
 }
 template <typename T>
 __host__ __device__ constexpr size_t zone_smem() {
@@ -136,12 +141,10 @@ __global__ void __launch_bounds__(32 * ZoneCfg<T>::WARPS, 2) k_zone(ZoneArgs<T> 
     uint16_t *sch = reinterpret_cast<uint16_t *>(smem);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned char *wb = smem + zone_cta_bytes() + warp * zone_warp_bytes<T>();
-    T *Kb = reinterpret_cast<T *>(wb);                     // block slots of the bordered zone matrix
-    T *Gs = Kb + ZSLOT_CAP * ZBLK;                         // G, 6 x 6
-    T *dCs = Gs + 36;                                      // C'(q_new) - C'(q_old), 6 x 6
-    uint8_t *inv = reinterpret_cast<uint8_t *>(dCs + 36);  // order - 19 -> corner of the site's cell
-    uint8_t *plist = inv + 8;                              // zone points grouped by zone cell
-    uint8_t *cend = plist + 32;                            // end of each cell's group in plist
+    T *Kb = reinterpret_cast<T *>(wb);                       // block slots of the bordered zone matrix
+    T *dCs = Kb + ZSLOT_CAP * ZBLK;                          // C'(q_new) - C'(q_old), 6 x 6
+    uint8_t *plist = reinterpret_cast<uint8_t *>(dCs + 36);  // zone points grouped by zone cell
+    uint8_t *cend = plist + 32;                              // end of each cell's group in plist
 
     for (int i = threadIdx.x; i < a.nsched; i += blockDim.x) sch[i] = a.sched[i];
     __syncthreads();
@@ -161,7 +164,8 @@ __global__ void __launch_bounds__(32 * ZoneCfg<T>::WARPS, 2) k_zone(ZoneArgs<T> 
         const int pcx = (x >> 1) - lox, pcy = (y >> 1) - loy, pcz = (z >> 1) - loz;   // site's zone cell
         const int refl = pcx + 2 * pcy + 4 * pcz;                                      // its reflection
 
-        // the zone's 27 points: orientation (start-of-step copy) and position in its cell
+        // the zone's 27 points: orientation (start-of-step copy) and position in its cell; the
+        // assembly takes the site's (zone point 13) stiffness with its new orientation
         uint32_t my_q = 0, my_pos = 0;
         if (lane < 27) {
             const int Xw = wrapi(x + lane % 3 - 1, nx), Yw = wrapi(y + (lane / 3) % 3 - 1, ny);
@@ -170,6 +174,7 @@ __global__ void __launch_bounds__(32 * ZoneCfg<T>::WARPS, 2) k_zone(ZoneArgs<T> 
             my_pos = (Xw & 1) + 2 * (Yw & 1) + 4 * (Zw & 1);
             my_q = spin_of(b, local_slot(my_pos));
         }
+        const uint32_t asm_q = lane == 13 ? qn : my_q;
         // inputs of the decision that do not depend on the zone matrix, requested now so that
         // their latency passes during the assembly: the site cell's nodal displacement component
         // of lane 3 corner + alpha (lane < 24), and the two stiffness entries whose difference is
@@ -185,12 +190,14 @@ __global__ void __launch_bounds__(32 * ZoneCfg<T>::WARPS, 2) k_zone(ZoneArgs<T> 
             c_new = __ldg(a.ctab + 24 * (size_t)qn + lane);
             c_old = __ldg(a.ctab + 24 * (size_t)q + lane);
         }
-        // the site cell's corners by node order (orders 19..26), and the zone points grouped by cell
+        // the node order of corner lane of the site's cell (lane < 8), and the zone points grouped
+        // by cell
+        int my_ord = 0;
         if (lane < 8) {
             const int c = pcx + 2 * pcy + 4 * pcz, k = lane;
             const int lx = (c & 1) + (k & 1), ly = ((c >> 1) & 1) + ((k >> 1) & 1), lz = (c >> 2) + (k >> 2);
             const int rx = pcx ? lx : 2 - lx, ry = pcy ? ly : 2 - ly, rz = pcz ? lz : 2 - lz;
-            inv[sch[rx + 3 * ry + 9 * rz] - 19] = (uint8_t)k;
+            my_ord = sch[rx + 3 * ry + 9 * rz];
         }
         if (lane < 8) {
             // offsets of cell c along one axis: the site's own cell (1 in the zone when the
@@ -223,20 +230,7 @@ __global__ void __launch_bounds__(32 * ZoneCfg<T>::WARPS, 2) k_zone(ZoneArgs<T> 
             const int o = lane < 3 ? 0 : lane < 5 ? ordB : ordC, r = lane < 3 ? lane : lane == 3 ? 1 : 2;
             Kb[sch[ZS_DIAG + o] * ZBLK + 5 * r] = T(1);   // (r, r) of the diagonal block
         }
-        // the border: block (27 + P, 19 + nn) holds rows 3P..3P+2 of B_p on the DOFs of the site
-        // cell's node of order 19 + nn (lane 2 nn + P); B_p maps that corner's displacement to the
-        // site's strain (Voigt, engineering shear)
         const int pa = x & 1, pb = y & 1, pcq = z & 1;
-        if (lane < 16) {
-            const int nn = lane >> 1, P = lane & 1, cr = inv[nn];
-            T g[3];
-            corner_grad<T>(pa, pb, pcq, cr & 1, (cr >> 1) & 1, cr >> 2, g);
-            T *Bk = Kb + sch[ZS_BIDX + ZN * (27 + P) + 19 + nn] * ZBLK;
-#pragma unroll
-            for (int r = 0; r < 3; ++r)
-#pragma unroll
-                for (int al = 0; al < 3; ++al) Bk[4 * r + al] = bt_entry<T>(g, al, 3 * P + r);
-        }
 
         // block Cholesky in the static order; a non-positive pivot (the smallest one is kept) or a
         // non-finite G marks the trial as failed
@@ -325,7 +319,7 @@ __global__ void __launch_bounds__(32 * ZoneCfg<T>::WARPS, 2) k_zone(ZoneArgs<T> 
             for (int j = 0; j < NJ; ++j) acc[j] = T(0);
             // element rows are padded with zeros to 320 entries, so every lane loads NJ of them
             auto fetch = [&](int s, T(&v)[NJ]) {
-                const uint32_t qs = __shfl_sync(FULL, my_q, s), pos = __shfl_sync(FULL, my_pos, s);
+                const uint32_t qs = __shfl_sync(FULL, asm_q, s), pos = __shfl_sync(FULL, my_pos, s);
                 const T *ke = a.ktab + ((size_t)qs * 8 + pos) * ZROW + lane;
 #pragma unroll
                 for (int j = 0; j < NJ; ++j) v[j] = __ldg(ke + 32 * j);
@@ -368,49 +362,26 @@ __global__ void __launch_bounds__(32 * ZoneCfg<T>::WARPS, 2) k_zone(ZoneArgs<T> 
         }
         __syncwarp();
 
-        // the remaining steps (edges and face centres, the site cell) in their scheduled rounds;
-        // the corners were eliminated during the assembly
-        const int nround = sch[ZS_NROUND];
-        for (int r = 6; r < nround; ++r) elim_round(r);
-        __syncwarp();
-
-        // G = -(the border's blocks after the elimination): lane 6 v + w (v, w < 6) reads
-        // entry (v, w) of the lower triangle of blocks (27 + v / 3, 27 + w / 3), v >= w
-        bool ok = pmin > T(0);
-        if (lane < 21) {
-            int v = 0, rem = lane;
-            while (rem >= 6 - v) {
-                rem -= 6 - v;
-                ++v;
-            }
-            const int w = v + rem;   // w >= v: entry (w, v) of the lower triangle
-            const T gv = -Kb[sch[ZS_BIDX + ZN * (27 + w / 3) + 27 + v / 3] * ZBLK + 4 * (w % 3) + v % 3];
-            ok = ok && fabs(gv) <= T(3.0e38);   // a pivot that overflowed or was not a number
-            Gs[6 * v + w] = gv;
-            Gs[6 * w + v] = gv;
-        }
-        // the site's strain from its cell's nodal displacements: lane = 3 corner + alpha
-        T eps[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+        // the site's strain e0 = Ebar + B_p u from its cell's nodal displacements (lane =
+        // 3 corner + alpha), dC in shared memory, w = dC e0, and the border: row 0 of block
+        // (27, order of corner c) holds f = B_p^T w on that corner's DOFs (lane 3 c + alpha)
+        T e0[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
         if (lane < 24) {
             const int cr = lane / 3, al = lane % 3;
             T g[3];
             corner_grad<T>(pa, pb, pcq, cr & 1, (cr >> 1) & 1, cr >> 2, g);
 #pragma unroll
-            for (int k = 0; k < 6; ++k) eps[k] = bt_entry<T>(g, al, k) * uv;
+            for (int k = 0; k < 6; ++k) e0[k] = bt_entry<T>(g, al, k) * uv;
         }
 #pragma unroll
         for (int k = 0; k < 6; ++k)
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) eps[k] += __shfl_xor_sync(FULL, eps[k], o);
-        // bond-energy change from the six face neighbours (zone points 12, 14, 10, 16, 4, 22)
-        int dE = 0;
+            for (int o = 16; o > 0; o >>= 1) e0[k] += __shfl_xor_sync(FULL, e0[k], o);
         {
-            const int nbs[6] = {12, 14, 10, 16, 4, 22};
+            T eb[6];
+            load_ebar<T>(R.st, eb);
 #pragma unroll
-            for (int j = 0; j < 6; ++j) {
-                const uint32_t v = __shfl_sync(FULL, my_q, nbs[j]);
-                dE += (v == q) - (v == qn);
-            }
+            for (int k = 0; k < 6; ++k) e0[k] = eb[k] + e0[k];
         }
         if (lane < 21) {
             int i = 0, rem = lane;
@@ -424,79 +395,52 @@ __global__ void __launch_bounds__(32 * ZoneCfg<T>::WARPS, 2) k_zone(ZoneArgs<T> 
             dCs[6 * j + i] = d;
         }
         __syncwarp();
-        ok = __all_sync(FULL, ok);
-        T e0[6];
+        T wl = T(0);
+        if (lane < 6) {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) wl += dCs[6 * lane + k] * e0[k];
+        }
+        T w[6];
+#pragma unroll
+        for (int v = 0; v < 6; ++v) w[v] = __shfl_sync(FULL, wl, v);
+        const int ordc = __shfl_sync(FULL, my_ord, (lane / 3) & 7);
+        if (lane < 24) {
+            const int cr = lane / 3, al = lane % 3;
+            T g[3];
+            corner_grad<T>(pa, pb, pcq, cr & 1, (cr >> 1) & 1, cr >> 2, g);
+            T fv = T(0);
+#pragma unroll
+            for (int v = 0; v < 6; ++v) fv += bt_entry<T>(g, al, v) * w[v];
+            Kb[sch[ZS_BIDX + ZN * 27 + ordc] * ZBLK + al] = fv;
+        }
+        __syncwarp();
+
+        // the remaining steps (edges and face centres, the site cell) in their scheduled rounds;
+        // the corners were eliminated during the assembly
+        const int nround = sch[ZS_NROUND];
+        for (int r = 6; r < nround; ++r) elim_round(r);
+        __syncwarp();
+
+        // -f . K'^+ f, left in the first entry of the pseudo-node's diagonal block; a pivot that
+        // was not positive (the smallest is kept) or a result that overflowed or is not a
+        // number fails the trial
+        const T kf = Kb[sch[ZS_BIDX + ZN * 27 + 27] * ZBLK];
+        const bool ok = __all_sync(FULL, pmin > T(0)) && fabs(kf) <= T(3.0e38);
+        // bond-energy change from the six face neighbours (zone points 12, 14, 10, 16, 4, 22)
+        int dE = 0;
         {
-            T eb[6];
-            load_ebar<T>(R.st, eb);
+            const int nbs[6] = {12, 14, 10, 16, 4, 22};
 #pragma unroll
-            for (int k = 0; k < 6; ++k) e0[k] = eb[k] + eps[k];
-        }
-        // (I + G dC) eta = e0: lane i < 6 holds row i; partial pivoting across the lanes
-        T mrow[7];
-#pragma unroll
-        for (int j = 0; j < 6; ++j) {
-            T s = (lane == j) ? T(1) : T(0);
-            if (lane < 6) {
-#pragma unroll
-                for (int k = 0; k < 6; ++k) s += Gs[6 * lane + k] * dCs[6 * k + j];
+            for (int j = 0; j < 6; ++j) {
+                const uint32_t v = __shfl_sync(FULL, my_q, nbs[j]);
+                dE += (v == q) - (v == qn);
             }
-            mrow[j] = s;
-        }
-        mrow[6] = T(0);
-#pragma unroll
-        for (int k = 0; k < 6; ++k)
-            if (lane == k) mrow[6] = e0[k];
-#pragma unroll
-        for (int c = 0; c < 6; ++c) {
-            // pivot: the largest |entry| of column c in rows c..5, lowest row on ties; the rows live
-            // in lanes 0..5, so a butterfly over each group of eight lanes finds it in lanes 0..7
-            T v = (lane >= c && lane < 6) ? fabs(mrow[c]) : T(-1);
-            int piv = lane;
-#pragma unroll
-            for (int o = 4; o > 0; o >>= 1) {
-                const T ov = __shfl_xor_sync(FULL, v, o);
-                const int op = __shfl_xor_sync(FULL, piv, o);
-                if (ov > v || (ov == v && op < piv)) {
-                    v = ov;
-                    piv = op;
-                }
-            }
-            ok = ok && v > T(0);
-            // swap rows c and piv; the pivot row (now row c) is the one just read from lane piv
-            T prow[7];
-#pragma unroll
-            for (int j = 0; j < 7; ++j) {
-                const T rc = __shfl_sync(FULL, mrow[j], c), rp = __shfl_sync(FULL, mrow[j], piv);
-                prow[j] = rp;
-                if (lane == c)
-                    mrow[j] = rp;
-                else if (lane == piv)
-                    mrow[j] = rc;
-            }
-            if (lane > c && lane < 6) {
-                const T f = mrow[c] / prow[c];
-#pragma unroll
-                for (int j = c; j < 7; ++j) mrow[j] -= f * prow[j];
-            }
-        }
-        T eta[6];
-#pragma unroll
-        for (int i = 5; i >= 0; --i) {
-            T s = __shfl_sync(FULL, mrow[6], i);
-#pragma unroll
-            for (int j = i + 1; j < 6; ++j) s -= __shfl_sync(FULL, mrow[j], i) * eta[j];
-            eta[i] = s / __shfl_sync(FULL, mrow[i], i);
         }
         if (lane == 0) {
             T f = T(0);
 #pragma unroll
-            for (int i = 0; i < 6; ++i) {
-                T s = T(0);
-#pragma unroll
-                for (int j = 0; j < 6; ++j) s += dCs[6 * i + j] * eta[j];
-                f += e0[i] * s;
-            }
+            for (int i = 0; i < 6; ++i) f += e0[i] * w[i];
+            f += kf;
             const T dHe = (T)R.lam * T(0.5) * f;
             bool acc;
             if (!ok || !(dHe == dHe)) {

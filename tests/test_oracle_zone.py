@@ -72,6 +72,30 @@ def test_radius_one_shift_is_the_rank_six_update(poly):
         assert abs(got - ref) < 1e-8 * abs(ref)
 
 
+def test_radius_one_shift_is_the_relaxed_misfit_energy(poly):
+    """The same change in the form the GPU kernel evaluates: with K' the zone
+    stiffness with the point's new orientation and f = B_p^T dC e0,
+    1/2 e0.dC (I + G dC)^-1 e0 = 1/2 e0.dC e0 - 1/2 f.K'^+ f (Sherman-Morrison-Woodbury:
+    dC (I + G dC)^-1 = dC - dC B_p K'^+ B_p^T dC), checked against the oracle's zone
+    re-solve with K' from the oracle's own assembly."""
+    sp, Ct, Bs, E, u0 = poly["sp"], poly["Ct"], poly["Bs"], poly["E"], poly["u0"]
+    for p in (0, 29, 131, 287):
+        pts = Z.zone_points(sp.shape, p, 1)
+        q_old = int(sp.reshape(-1)[p])
+        q_new = (q_old + 2) % 5
+        Cp2 = Z.point_stiffness(sp, Ct).copy()
+        Cp2[p] = Ct[q_new]
+        K2, _ = Z.assemble(Bs, Cp2, E, pts)
+        dC = Ct[q_new] - Ct[q_old]
+        e0 = E + Bs[p] @ u0
+        f = Bs[p].T @ (dC @ e0)
+        ref = 0.5 * e0 @ dC @ e0 - 0.5 * f @ np.linalg.pinv(K2, rcond=1e-12) @ f
+        got = Z.zone_shift(sp, Ct, E, u0, p, q_new, 1, Bs)
+        assert abs(got - ref) < 1e-8 * abs(ref)
+        # the relaxation term is a real share of the change, not a rounding-level correction
+        assert 0.0 < f @ np.linalg.pinv(K2, rcond=1e-12) @ f
+
+
 def test_radius_one_sweep_reads_the_start_of_step(poly):
     sp0 = poly["sp"].copy()
     b = sp0.copy()
