@@ -90,6 +90,19 @@ __device__ __forceinline__ double zrsqrt(double x) { return rsqrt(x); }
 __device__ __forceinline__ float zlog(float x) { return logf(x); }
 __device__ __forceinline__ double zlog(double x) { return log(x); }
 
+// element-row loads: read once per point, mostly L2 hits, and not kept in L1, so that L1
+// holds the scatter-place table that every trial reads
+__device__ __forceinline__ float ldg_stream(const float *p) {
+    float v;
+    asm volatile("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ double ldg_stream(const double *p) {
+    double v;
+    asm volatile("ld.global.nc.L1::no_allocate.f64 %0, [%1];" : "=d"(v) : "l"(p));
+    return v;
+}
+
 __device__ __forceinline__ void ld4(const float *p, float (&v)[4]) {
     const float4 t = *reinterpret_cast<const float4 *>(p);
     v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
@@ -322,7 +335,7 @@ __global__ void __launch_bounds__(32 * ZoneCfg<T>::WARPS, 2) k_zone(ZoneArgs<T> 
                 const uint32_t qs = __shfl_sync(FULL, asm_q, s), pos = __shfl_sync(FULL, my_pos, s);
                 const T *ke = a.ktab + ((size_t)qs * 8 + pos) * ZROW + lane;
 #pragma unroll
-                for (int j = 0; j < NJ; ++j) v[j] = __ldg(ke + 32 * j);
+                for (int j = 0; j < NJ; ++j) v[j] = ldg_stream(ke + 32 * j);
             };
             fetch(plist[0], b0);
             fetch(plist[1], b1);
