@@ -165,8 +165,13 @@ __global__ void __launch_bounds__(32 * ZoneCfg<T>::WARPS, 2) k_zone(ZoneArgs<T> 
     const int ordB = sch[1], ordC = sch[3];
     const unsigned n = *a.count;
 
-    for (unsigned e = blockIdx.x * W + warp; e < n; e += gridDim.x * W) {
-        const uint4 en = a.work[e];
+    // each warp's next work item is read one trial ahead
+    const unsigned stride = gridDim.x * W;
+    uint4 en_next = make_uint4(0, 0, 0, 0);
+    if (blockIdx.x * W + warp < n) en_next = a.work[blockIdx.x * W + warp];
+    for (unsigned e = blockIdx.x * W + warp; e < n; e += stride) {
+        const uint4 en = en_next;
+        if (e + stride < n) en_next = a.work[e + stride];
         const uint32_t p = en.x;   // site index: below 2^32, possibly above 2^31
         const Replica &R = a.reps[en.y];
         const uint32_t qn = en.z & 0xffffu, q = en.z >> 16, r1 = en.w;
