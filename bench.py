@@ -195,8 +195,12 @@ def host_cores():
 
 
 def crops(spins, n):
-    """n disjoint CROP^3 crops of the field (as many as it holds, at most n)."""
+    """n disjoint CROP^3 crops of the field (as many as it holds, at most n); a field
+    smaller than CROP along any axis is taken whole, n times (independent runs of the
+    whole workload, one per process)."""
     nz, ny, nx = spins.shape
+    if min(nz, ny, nx) < CROP:
+        return [np.ascontiguousarray(spins) for _ in range(n)]
     out = []
     for z in range(0, nz - CROP + 1, CROP):
         for y in range(0, ny - CROP + 1, CROP):
@@ -204,6 +208,14 @@ def crops(spins, n):
                 if len(out) < n:
                     out.append(np.ascontiguousarray(spins[z:z + CROP, y:y + CROP, x:x + CROP]))
     return out
+
+
+def crop_desc(spins, nproc, sites):
+    """What the oracle processes ran on, for the sample strings."""
+    if min(spins.shape) < CROP:
+        edge = "x".join(str(d) for d in spins.shape[::-1])
+        return f"{nproc} independent runs of the whole {edge} field ({sites} sites in all)"
+    return f"{nproc} disjoint {CROP}^3 crops ({sites} sites)"
 
 
 def _oracle_crop_worker(spec, euler, crop, warmup, n_mcs, barrier, out):
@@ -257,7 +269,7 @@ def run_reference(args):
     spec, euler, spins = S.workload_inputs(args.workload)
     cores = host_cores()
     value, t, sites, nproc = oracle_rate(spec, euler, spins, args.steps, cores, warmup=args.warmup)
-    sample = (f"{nproc} disjoint {CROP}^3 crops ({sites} sites) of the {args.workload} microstructure, one "
+    sample = (f"{crop_desc(spins, nproc, sites)} of the {args.workload} microstructure, one "
               f"single-threaded oracle process per host core; each step one full oracle MCS in every crop "
               f"({spec['mpm_steps']} MPM steps, stress, red+black sweep), FP64")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "site-updates/s", "n_gpus": args.gpus,
@@ -281,7 +293,21 @@ def workload_config(spec, name):
                         f"{list(spec['axis'])} with traction-free sides, J=1, kT=0.7, {spec['mpm_steps']} explicit "
                         f"MPM steps per MCS, FP32 stress and zone energy, FP64 reductions",
             "sites": nx * ny * nz, "orientations": spec["Q"], "mpm_steps_per_mcs": spec["mpm_steps"],
-            "l2": "inputs larger than L2 (spins, nodal state and stored stress resident in HBM)"}
+            "l2": l2_statement(nx * ny * nz)}
+
+
+L2_BYTES = 129e6   # GB300's L2
+# FP32 bytes resident per site: spin 2, stored stress 24, two displacement buffers and the
+# velocity at one node per 8 sites (3 x 12 / 8)
+RESIDENT_BYTES_PER_SITE = 2 + 24 + 36 / 8
+
+
+def l2_statement(sites):
+    mb = RESIDENT_BYTES_PER_SITE * sites / 1e6
+    if mb * 1e6 > L2_BYTES:
+        return f"inputs larger than L2 ({mb:.0f} MB of spins, nodal state and stored stress resident in HBM)"
+    return (f"inputs smaller than L2 ({mb:.1f} MB resident): the steps run L2-resident, with no flush between "
+            f"them; a per-configuration figure, not an HBM measurement")
 
 
 def run_ours(args):
@@ -470,11 +496,11 @@ def run_ours(args):
         cores = host_cores()
         v, tt, n, nproc = oracle_rate(spec, euler, spins, 1, cores)
         cpu = {"kind": "oracle", "value": v, "unit": "site-updates/s", "cores": nproc,
-               "sample": f"{nproc} disjoint {CROP}^3 crops ({n} sites) of the workload's microstructure, one "
+               "sample": f"{crop_desc(spins, nproc, n)} of the workload's microstructure, one "
                          f"single-threaded oracle process per host core, one full MCS each ({spec['mpm_steps']} "
                          f"MPM steps, stress, red+black sweep), FP64, {tt:.1f} s wall",
                "one_core": {"value": v1, "unit": "site-updates/s", "cores": 1,
-                            "sample": f"one {CROP}^3 crop ({n1} sites), one full MCS, {t1:.1f} s"}}
+                            "sample": f"{crop_desc(spins, 1, n1)}, one full MCS, {t1:.1f} s"}}
 
     # ---- the batched ensemble (64 uneven replicas in one handle), one GPU only ----
     ens = None
