@@ -683,7 +683,10 @@ def ENSEMBLE_WORKLOAD(S, e):
             f"strain U[5e-4, 3e-3], 50 MPM steps per MCS, FP32, one launch per phase over all replicas")
 
 
-ZONE_FLOP_PER_TRIAL = 70_000   # assembly 8.1k adds, block Cholesky 56k, forward solve and G 4.6k, 6x6 solve 1k
+# a fixed unit for the zone's rate: the flops of the first sparse block elimination of a trial
+# (assembly 8.1k adds, block Cholesky 56k, forward solve and G 4.6k, 6x6 solve 1k); the current
+# kernel's bordered form does less work for the same trial
+ZONE_FLOP_PER_TRIAL = 70_000
 
 
 def run_zone(args):

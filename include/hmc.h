@@ -79,7 +79,9 @@ enum { HMC_BC_UNIAXIAL = 0, HMC_BC_STRAIN6 = 1, HMC_BC_TRACTION = 2 };
  * the shift is the change of its minimum potential energy,
  * 1/2 e0.dC (I + G dC)^-1 e0 with e0 the site's strain from the current nodal
  * displacement and mean strain, dC = C'(q_new) - C'(q_old), G the compliance of
- * the zone seen at the site.  ZONE1 evaluates every trial against the spins as
+ * the zone seen at the site (evaluated as the equal form 1/2 e0.dC e0 - 1/2 f.K'^+ f,
+ * K' the zone stiffness with the new orientation, f = B_p^T dC e0, B_p the site's
+ * strain-displacement map).  ZONE1 evaluates every trial against the spins as
  * they were at the start of the half step (the zone holds sites of the sweep's
  * own colour) and needs nx, ny, nz >= 6; it does not read the stored stress. */
 enum { HMC_ELASTIC_OFF = 0, HMC_ELASTIC_TRACTION = 1, HMC_ELASTIC_ZONE1 = 2, HMC_ELASTIC_STRAIN = 3 };

@@ -676,8 +676,8 @@ std::vector<uint16_t> zone_schedule_build() {
     for (int n = 0; n < 27; ++n)
         if (cls(n) == 3) order.push_back(n);
     // the real nodes share a block when they lie in a common zone cell (Chebyshev distance
-    // <= 1); the two border pseudo-nodes (orders 27, 28) share one with the site cell's nodes
-    // (orders 19..26) and with each other.  Node A (order 0) has all its DOFs held fixed: its
+    // <= 1); the border pseudo-node (order 27) shares one with the site cell's nodes (orders
+    // 19..26).  Node A (order 0) has all its DOFs held fixed: its
     // row and column of K are zero but for the unit diagonal, so it shares no block and its
     // elimination step is empty (the kernel starts at step 1).
     bool pat[ZN][ZN];
@@ -695,7 +695,7 @@ std::vector<uint16_t> zone_schedule_build() {
             for (int d = 0; d < 3; ++d) dmax = std::max(dmax, std::abs(co(order[i], d) - co(order[j], d)));
             pat[i][j] = dmax <= 1;
         }
-    // symbolic elimination of the 27 real nodes (the pseudo-nodes are never eliminated)
+    // symbolic elimination of the 27 real nodes (the pseudo-node is never eliminated)
     std::vector<std::vector<ZUpdate>> up(27);
     for (int k = 0; k < 27; ++k) {
         std::vector<int> nb;
