@@ -589,12 +589,15 @@ hmc_status upload_sched(hmc_handle *h, int variant) {
     return HMC_OK;
 }
 
-int grid_for_shape(hmc_handle *h, int shape, int per_sm_limit) {
+// Persistent MPM grid: resident CTAs per SM (at most per_sm_limit when positive) times the
+// SMs, and no more CTAs than leave min_planes work items (planes) to each.  Every CTA pays
+// one plane of restart for its range, so small grids trade that for parallelism.
+int grid_for_shape(hmc_handle *h, int shape, int per_sm_limit, int min_planes = 4) {
     int per_sm = h->p.precision == HMC_FP32 ? hmc::mpm_per_sm<float>(shape, h->p.n_orient)
                                             : hmc::mpm_per_sm<double>(shape, h->p.n_orient);
     if (per_sm_limit > 0 && per_sm > per_sm_limit) per_sm = per_sm_limit;
     long long g = (long long)per_sm * h->num_sms;
-    const long long cap = (h->mpm_total + 3) / 4;  // at least four planes per CTA
+    const long long cap = (h->mpm_total + min_planes - 1) / min_planes;
     if (g > cap) g = cap;
     return (int)(g < 1 ? 1 : g);
 }
@@ -634,9 +637,13 @@ hmc_status tune_mpm(hmc_handle *h, bool enabled, int &best_shape, int &best_grid
     const int nvariants = hmc::mpm_nvariants(h->p.precision == HMC_FP32);
     for (int shape = 0; shape < nvariants && err == cudaSuccess && s == HMC_OK; ++shape) {
         if ((s = upload_sched(h, shape)) != HMC_OK) break;
-        for (int lim : {0, 1}) {
-            const int grid = grid_for_shape(h, shape, lim);
-            if (lim == 1 && grid == grid_for_shape(h, shape, 0)) continue;
+        // full occupancy and one CTA per SM with at least four planes per CTA, then (small grids)
+        // full occupancy with at least two planes and with at least one
+        std::vector<int> tried;
+        for (int cand = 0; cand < 4; ++cand) {
+            const int grid = grid_for_shape(h, shape, cand == 1 ? 1 : 0, cand < 2 ? 4 : cand == 2 ? 2 : 1);
+            if (std::find(tried.begin(), tried.end(), grid) != tried.end()) continue;
+            tried.push_back(grid);
             const int saved_grid = h->mpm_grid;
             h->mpm_grid = grid;
             auto launch = [&]() {
