@@ -75,10 +75,21 @@ struct ZoneCfg<double> {
 };
 
 __host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
-__host__ __device__ constexpr size_t zone_cta_bytes() { return align16(ZSCHED_CAP * sizeof(uint16_t)); }
+__host__ __device__ constexpr size_t zone_sched_bytes() { return align16(ZSCHED_CAP * sizeof(uint16_t)); }
+// + per reflection of the site's cell: the zone points grouped by zone cell (32 bytes, 27
+// used) and the end of each cell's group (8 bytes)
+__host__ __device__ constexpr size_t zone_cta_bytes() { return zone_sched_bytes() + 8 * 32 + 8 * 8; }
 template <typename T>
 __host__ __device__ constexpr size_t zone_warp_bytes() {
-    return align16((ZSLOT_CAP * ZBLK + 36) * sizeof(T) + 32 + 8);
+    return align16((ZSLOT_CAP * ZBLK + 36) * sizeof(T));
+}
+
+// Zone offsets (-1, 0 or 1) along one axis of the points in zone cell bit cb when the site's
+// own cell is cell pc along that axis: the site's cell (pc; 1 in the zone when the
+// coordinate is even) holds offsets {0, +1} or {-1, 0}, the other cell the rest.
+__device__ __forceinline__ void zone_cell_span(int cb, int pc, int &lo, int &hi) {
+    lo = cb ? (pc ? 0 : 1) : -1;
+    hi = cb ? 1 : (pc ? -1 : 0);
 }
 template <typename T>
 __host__ __device__ constexpr size_t zone_smem() {
@@ -156,10 +167,27 @@ __global__ void __launch_bounds__(32 * ZoneCfg<T>::WARPS, 2) k_zone(ZoneArgs<T> 
     unsigned char *wb = smem + zone_cta_bytes() + warp * zone_warp_bytes<T>();
     T *Kb = reinterpret_cast<T *>(wb);                       // block slots of the bordered zone matrix
     T *dCs = Kb + ZSLOT_CAP * ZBLK;                          // C'(q_new) - C'(q_old), 6 x 6
-    uint8_t *plist = reinterpret_cast<uint8_t *>(dCs + 36);  // zone points grouped by zone cell
-    uint8_t *cend = plist + 32;                              // end of each cell's group in plist
+    uint8_t *plist_all = smem + zone_sched_bytes();        // [reflection][32]: points grouped by zone cell
+    uint8_t *cend_all = plist_all + 8 * 32;                // [reflection][8]: end of each cell's group
 
     for (int i = threadIdx.x; i < a.nsched; i += blockDim.x) sch[i] = a.sched[i];
+    // the zone's points grouped by zone cell, for each reflection rf (thread 8 rf + cell)
+    if (threadIdx.x < 64) {
+        const int rf = threadIdx.x >> 3, cell = threadIdx.x & 7;
+        const int px = rf & 1, py = (rf >> 1) & 1, pz = rf >> 2;
+        int w = 0, x0 = 0, x1 = 0, y0 = 0, y1 = 0, z0 = 0, z1 = 0;
+        for (int c = 0; c <= cell; ++c) {
+            zone_cell_span(c & 1, px, x0, x1);
+            zone_cell_span((c >> 1) & 1, py, y0, y1);
+            zone_cell_span(c >> 2, pz, z0, z1);
+            if (c < cell) w += (x1 - x0 + 1) * (y1 - y0 + 1) * (z1 - z0 + 1);
+        }
+        for (int dz = z0; dz <= z1; ++dz)
+            for (int dy = y0; dy <= y1; ++dy)
+                for (int dx = x0; dx <= x1; ++dx)
+                    plist_all[32 * rf + w++] = (uint8_t)((dx + 1) + 3 * (dy + 1) + 9 * (dz + 1));
+        cend_all[8 * rf + cell] = (uint8_t)w;
+    }
     __syncthreads();
     // fixed DOFs: all of node A (order 0), y and z of node B, z of node C
     const int ordB = sch[1], ordC = sch[3];
@@ -208,8 +236,8 @@ __global__ void __launch_bounds__(32 * ZoneCfg<T>::WARPS, 2) k_zone(ZoneArgs<T> 
             c_new = __ldg(a.ctab + 24 * (size_t)qn + lane);
             c_old = __ldg(a.ctab + 24 * (size_t)q + lane);
         }
-        // the node order of corner lane of the site's cell (lane < 8), and the zone points grouped
-        // by cell
+        // the node order of corner lane of the site's cell (lane < 8), and this reflection's zone
+        // points grouped by cell
         int my_ord = 0;
         if (lane < 8) {
             const int c = pcx + 2 * pcy + 4 * pcz, k = lane;
@@ -217,26 +245,7 @@ __global__ void __launch_bounds__(32 * ZoneCfg<T>::WARPS, 2) k_zone(ZoneArgs<T> 
             const int rx = pcx ? lx : 2 - lx, ry = pcy ? ly : 2 - ly, rz = pcz ? lz : 2 - lz;
             my_ord = sch[rx + 3 * ry + 9 * rz];
         }
-        if (lane < 8) {
-            // offsets of cell c along one axis: the site's own cell (1 in the zone when the
-            // coordinate is even) holds offsets {0,+1} or {-1,0}; the other holds the rest
-            const int cx = lane & 1, cy = (lane >> 1) & 1, cz = lane >> 2;
-            const int x0 = cx ? (pcx ? 0 : 1) : -1, x1 = cx ? 1 : (pcx ? -1 : 0);
-            const int y0 = cy ? (pcy ? 0 : 1) : -1, y1 = cy ? 1 : (pcy ? -1 : 0);
-            const int z0 = cz ? (pcz ? 0 : 1) : -1, z1 = cz ? 1 : (pcz ? -1 : 0);
-            const int cnt = (x1 - x0 + 1) * (y1 - y0 + 1) * (z1 - z0 + 1);
-            int incl = cnt;
-#pragma unroll
-            for (int o = 1; o < 8; o <<= 1) {
-                const int v = __shfl_up_sync(0xffu, incl, o);
-                if (lane >= o) incl += v;
-            }
-            int w = incl - cnt;
-            for (int dz = z0; dz <= z1; ++dz)
-                for (int dy = y0; dy <= y1; ++dy)
-                    for (int dx = x0; dx <= x1; ++dx) plist[w++] = (uint8_t)((dx + 1) + 3 * (dy + 1) + 9 * (dz + 1));
-            cend[lane] = (uint8_t)incl;
-        }
+        const uint8_t *plist = plist_all + 32 * refl, *cend = cend_all + 8 * refl;
         {
             using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
             V *kv = reinterpret_cast<V *>(Kb);
