@@ -79,3 +79,35 @@ def test_batch_with_half_ctas_equals_solo_runs(G, monkeypatch):
         g.mc_sweeps(2)
         assert np.array_equal(g.spins(), got[r]), f"replica {r}"
         g.close()
+
+
+def _run_tuned(G, shape, precision):
+    Q = 12
+    eul = S.euler_uniform_so3(Q, 6)
+    sp = S.voronoi_spins(shape, 18, Q, 6)
+    g = G.HMC(shape, Q, precision=precision, load_axis=(1, 1, 1.0), strain=2e-3, mpm_steps_per_mcs=6,
+              elastic=1, elastic_scale=2e3, seed=91, **C3)
+    g.set_orientations(eul, sp)
+    acc = g.mc_sweeps(3)
+    out = (acc, g.spins().copy(), g.nodal()[0], g.strain())
+    tuning = g.tuning()
+    g.close()
+    return out, tuning
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+def test_mpm_grid_size_gives_the_same_bits(G, monkeypatch, precision):
+    """A small grid (12 node planes of one tile): the tuner's persistent grid (it may take
+    one plane per CTA) and the default one for the same patch shape (at least four planes
+    per CTA) give the same spins, displacement and mean strain; the CTAs split the planes
+    differently, and every CTA recomputes the cells below its first plane."""
+    shape = (24, 16, 16)
+    monkeypatch.delenv("HMC_MPM_SHAPE", raising=False)
+    monkeypatch.setenv("HMC_AUTOTUNE", "1")
+    tuned, (shp, grid_tuned) = _run_tuned(G, shape, precision)
+    monkeypatch.setenv("HMC_MPM_SHAPE", str(shp))
+    forced, (shp2, grid_default) = _run_tuned(G, shape, precision)
+    assert shp2 == shp
+    _same(tuned, forced)
+    assert grid_default >= 1 and grid_tuned >= 1, (grid_tuned, grid_default)
+    print(f"MPM grid tuned {grid_tuned}, default {grid_default} (shape {shp})")
