@@ -180,3 +180,45 @@ def test_zone_at_128_cubed_sampled(G, precision):
             assert t >= 0 and abs(dH - t) <= tol * max(1.0, abs(t)), (x, y, z, dH, t)
     assert mis <= (0 if precision == 0 else 2)
     g.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_zone_trials_between_equal_stiffnesses(G, precision):
+    """Orientations 0, 1 and 2, 3 are the same rotation twice, so a trial between them changes
+    no stiffness: dC = 0, the border f = B_p^T dC e0 is zero, the elimination leaves exactly
+    zero and the trial is decided on the bond energy alone (the pure Potts rule), as in the
+    oracle's re-solve, which finds no energy change."""
+    shape, Q, seed, lam = (6, 8, 8), 4, 11, 3.0e3
+    eul = S.euler_uniform_so3(Q, seed)
+    eul[1] = eul[0]
+    eul[3] = eul[2]
+    sp = S.voronoi_spins(shape, 6, Q, seed + 1)
+    g = G.HMC(shape, Q, precision=precision, J=1.0, kT=0.7, bc=1, strain6=tuple(E6), load_axis=(0, 0, 1.0),
+              strain=2e-3, elastic=G.HMC_ELASTIC_ZONE1, trial=1, mpm_steps_per_mcs=0, dt=O.default_dt(**C3),
+              damping=0.05, elastic_scale=lam, seed=seed * 7919 + 3, **C3)
+    g.set_orientations(eul, sp)
+    _, Ct, _ = O.tables(eul, **C3)
+    assert np.array_equal(Ct[0], Ct[1]) and np.array_equal(Ct[2], Ct[3])
+    Bs = Z.all_strain_matrices(shape)
+    rng = np.random.default_rng(seed)
+    nn = int(np.prod(shape)) // 8
+    u0 = rng.normal(size=(nn, 3)) * 2e-4
+    g.set_nodal(u0, np.zeros((nn, 3)))
+    tol = 1e-9 if precision == 0 else 1e-4
+    spo = sp.copy()
+    equal_flips = 0
+    for colour in (0, 1):
+        g.set_spins(spo)
+        pre = spo.copy()
+        g.sweep_half(colour)
+        _, _, dH, t = Z.half_sweep_zone(spo, colour, seed * 7919 + 3, 0, 0, 1.0, 0.7, 1, Q, lam, Ct, E6,
+                                        u0.reshape(-1), 1, Bs)
+        gs = g.spins()
+        moved = pre != spo
+        equal_flips += int(np.sum(moved & ((pre // 2) == (spo // 2))))
+        for p in np.flatnonzero((gs != spo).ravel()):
+            assert abs(dH[p] - t[p]) <= tol * max(1.0, abs(t[p])), (p, dH[p], t[p])
+        if precision == 0:
+            assert (gs == spo).all()
+    assert equal_flips > 0   # trials between equal stiffnesses were taken
+    g.close()
