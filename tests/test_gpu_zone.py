@@ -222,3 +222,23 @@ def test_zone_trials_between_equal_stiffnesses(G, precision):
             assert (gs == spo).all()
     assert equal_flips > 0   # trials between equal stiffnesses were taken
     g.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_zone_with_zero_elastic_scale_is_pure_potts(G, precision):
+    """lambda = 0: every listed trial gets dH_e = 0 and the integer Metropolis threshold, so
+    three MCS of the 27-point zone mode equal three MCS with the elastic term off, bit for bit
+    (same draws, same decisions)."""
+    shape, Q, seed = (8, 6, 10), 6, 13
+    eul = S.euler_uniform_so3(Q, seed)
+    sp = S.voronoi_spins(shape, 7, Q, seed + 1)
+    out = []
+    for elastic in (G.HMC_ELASTIC_ZONE1, G.HMC_ELASTIC_OFF):
+        g = G.HMC(shape, Q, precision=precision, J=1.0, kT=0.7, elastic=elastic, elastic_scale=0.0,
+                  mpm_steps_per_mcs=3, seed=seed * 31 + 1, **C3)
+        g.set_orientations(eul, sp)
+        acc = g.mc_sweeps(3)
+        out.append((acc, g.spins().copy()))
+        g.close()
+    assert out[0][0] == out[1][0] and out[0][0] > 0
+    assert np.array_equal(out[0][1], out[1][1])
