@@ -689,6 +689,44 @@ def ENSEMBLE_WORKLOAD(S, e):
 ZONE_FLOP_PER_TRIAL = 70_000
 
 
+def zone_fp32_error(G, spec, euler, spins, kw):
+    """The 27-point zone's FP32 decisions against the library's FP64 zone path (pinned to the
+    oracle's zone re-solve by the parity tests), on the workload itself: both handles start
+    from the same state, the FP64 one takes the workload's MPM steps and its nodal state is
+    given to the FP32 one (rounded), and both then sweep one red and one black half on the same
+    spins; the fraction of the colour's sites whose decision differs."""
+    hs = {}
+    try:
+        for prec in (G.HMC_FP64, G.HMC_FP32):
+            hs[prec] = G.HMC(spec["shape"], spec["Q"], precision=prec, bc=G.HMC_BC_UNIAXIAL,
+                             load_axis=spec["axis"], strain=spec["strain"], elastic=G.HMC_ELASTIC_ZONE1,
+                             mpm_steps_per_mcs=spec["mpm_steps"], **kw)
+            hs[prec].set_orientations(euler, spins)
+        h64, h32 = hs[G.HMC_FP64], hs[G.HMC_FP32]
+        h64.mpm_steps(spec["mpm_steps"])
+        u, v = h64.nodal()
+        h32.set_nodal(u, v)
+        nz, ny, nx = spec["shape"]
+        par = (np.arange(nz)[:, None, None] + np.arange(ny)[None, :, None] + np.arange(nx)[None, None, :]) & 1
+        halves = []
+        for colour in (0, 1):
+            h32.set_spins(h64.spins())
+            before = h64.spins()
+            h64.sweep_half(colour)
+            trials = h64.info().zone_trials   # the listed trials of this half sweep
+            h32.sweep_half(colour)
+            mis = (h64.spins() != h32.spins()) & (par == colour)
+            halves.append({"colour": colour, "sites": int((par == colour).sum()), "mismatched": int(mis.sum()),
+                           "mismatch_fraction": int(mis.sum()) / int((par == colour).sum()),
+                           "zone_trials": int(trials), "accepted_fp64": int((h64.spins() != before).sum())})
+        return {"half_sweeps": halves, "mpm_steps": spec["mpm_steps"],
+                "reference": "the library's FP64 zone path from the same state (pinned to the FP64 oracle's "
+                             "zone re-solve by the parity tests)"}
+    finally:
+        for h in hs.values():
+            h.close()
+
+
 def run_zone(args):
     """The 27-point constant-traction zone (HMC_ELASTIC_ZONE1) on the 128^3
     microstructure: whole MCS timed with CUDA events, plus the zone half sweep
@@ -750,8 +788,10 @@ def run_zone(args):
                          "peak_source": f"derived: {n_sms} SMs x {FP32_LANES} FP32 lanes x 2 flop x {sm_max:.0f} MHz",
                          "measured_fma_peaks": dict(fma, frac_of_measured_fp32=achieved / fma["fp32_tflops"])},
             "gpu_launches": args.steps * (spec["mpm_steps"] + 2 + 2 * 2), "clocks": clk}
-    print(json.dumps(line), flush=True)
     g.close()
+    if not args.no_fp64:
+        line["fp32_error"] = zone_fp32_error(G, spec, euler, spins, kw)
+    print(json.dumps(line), flush=True)
     return 0
 
 
