@@ -853,8 +853,24 @@ def run_adjoint(args):
             "forward_ms": 1e3 * tf, "reverse_ms": 1e3 * tb, "plain_mpm_ms": 1e3 * t_mpm,
             "adjoint_cost_in_forward_steps": (tf + tb) / (t_mpm / ADJ_STEPS) / ADJ_STEPS,
             "gradient": [float(x) for x in grad]}
-    print(json.dumps(line), flush=True)
     g.close()
+    if not args.no_fp64:
+        # the FP32 gradient against the library's FP64 adjoint (pinned to the oracle's
+        # tangent-linear gradient by the parity tests), same map, same cotangent
+        h = G.HMC(spec["shape"], spec["Q"], precision=G.HMC_FP64, bc=G.HMC_BC_STRAIN6, strain6=tuple(E),
+                  mpm_steps_per_mcs=0, **kw)
+        h.set_orientations(euler, spins)
+        h.adjoint_forward(ADJ_STEPS, ADJ_EVERY)
+        g64 = np.asarray(h.adjoint_backward(0.5, g_field), dtype=np.float64)
+        h.close()
+        g32 = np.asarray(line["gradient"], dtype=np.float64)
+        rel = np.abs(g32 - g64) / np.maximum(np.abs(g64), 1e-300)
+        line["fp32_error"] = {"gradient_rel_err_per_component": [float(x) for x in rel],
+                              "gradient_rel_err_max": float(rel.max()),
+                              "gradient_rel_l2": float(np.linalg.norm(g32 - g64) / np.linalg.norm(g64)),
+                              "reference": "the library's FP64 adjoint of the same map (pinned to the FP64 "
+                                           "oracle's tangent-linear gradient by the parity tests)"}
+    print(json.dumps(line), flush=True)
     return 0
 
 
