@@ -471,12 +471,14 @@ def run_ours(args):
                 "mpm_cell_steps_per_s": N / t64_mpm, "mpm_ms_per_step": t64_mpm * 1e3,
                 "mpm_tflops": MPM_FLOP_PER_POINT_F64 * N / t64_mpm / 1e12,
                 "mpm_frac_of_measured_fp64": MPM_FLOP_PER_POINT_F64 * N / t64_mpm / 1e12 / fma["fp64_tflops"],
+                "mpm_hbm_frac": MPM_BYTES_PER_POINT["f64"] * N / t64_mpm / 1e9 / hbm,
                 "plain_unfused": {
                     "form": "the explicit step in the plain form: unfused G2P/stress-increment, P2G and node kernels "
                             "with every point's FP64 stress and every cell's corner forces in global memory "
                             "(hmc_mpm_steps_plain)",
                     "mpm_ms_per_step": t_plain * 1e3, "mpm_cell_steps_per_s": N / t_plain,
                     "algorithmic_bytes_per_point_step": PLAIN_BYTES_PER_POINT,
+                    "mpm_hbm_frac": PLAIN_BYTES_PER_POINT * N / t_plain / 1e9 / hbm,
                     "mcs_ms": mcs_plain * 1e3,
                     "mcs_composition": "the FP64 MCS with its 50 fused steps replaced by 50 plain steps",
                     "site_updates_per_s": N / mcs_plain,
