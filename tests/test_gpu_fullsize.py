@@ -139,3 +139,31 @@ def test_fullsize_graph_mcs_conserves_volume(big):
     assert counts.sum() == spins.size and abs(f.sum() - 1) < 1e-12
     assert (counts == np.bincount(after.ravel(), minlength=1024)).all()
     assert 0 < int((after != spins).sum()) <= acc
+
+
+def test_configured_500_mcs_run(big):
+    """The 256^3 workload run as configured: 500 Monte Carlo steps (50 MPM steps each, FP32
+    stress, FP64 reductions) with the ANGLE_100 histogram logged every 10 steps.  Every log
+    sums to one over all sites, the volumes recounted from the spins every 100 steps equal the
+    library's, every step accepts trials, and the mean strain and energy stay finite."""
+    G, spec, spins = big["G"], big["spec"], big["spins"]
+    kw = dict(J=spec["J"], kT=spec["kT"], c11=spec["c11"], c12=spec["c12"], c44=spec["c44"],
+              load_axis=spec["axis"], strain=spec["strain"], mpm_steps_per_mcs=spec["mpm_steps"], seed=3)
+    g = G.HMC(spec["shape"], spec["Q"], precision=G.HMC_FP32, **kw)
+    try:
+        g.set_orientations(spins=spins, euler=S.workload_inputs("ni256")[1])
+        first = None
+        for m in range(50):
+            acc = g.mc_sweeps(10)
+            assert acc > 0, m
+            f, counts = g.texture_histogram(G.HMC_HIST_ANGLE_100, 9)
+            assert counts.sum() == spins.size and abs(f.sum() - 1) < 1e-12, m
+            first = f.copy() if first is None else first
+            if m % 10 == 9:
+                assert (counts == np.bincount(g.spins().ravel(), minlength=spec["Q"])).all(), m
+        unlike, w, sig = g.energy()
+        assert np.all(np.isfinite(g.strain())) and np.isfinite(w) and np.all(np.isfinite(sig)) and unlike > 0
+        assert g.info().mcs == 500
+        assert np.abs(f - first).sum() > 0   # the texture evolves
+    finally:
+        g.close()
