@@ -150,3 +150,36 @@ def test_large_uneven_batch_equals_solo_runs(G, precision, elastic):
         g.close()
     b.close()
     assert acc_b == acc_s and acc_b > 0
+
+
+def test_configured_ensemble_200_mcs(G):
+    """The batched ensemble as configured: 64 replicas with edges from {48, 64, 96, 128, 160},
+    independent seeds, axes uniform on the sphere, strains uniform in [5e-4, 3e-3], Q = 256,
+    FP32, 200 Monte Carlo steps of 50 MPM steps in one handle.  Every replica accepts trials
+    and keeps its spins in range, its mean strain stays finite, and replica 0's spins equal
+    its own single-replica run over the first 5 steps."""
+    specs, euler, fields = S.ensemble_inputs()
+    per = [dict(load_axis=sp["axis"], strain=sp["strain"], seed=sp["mc_seed"], replica=r)
+           for r, sp in enumerate(specs)]
+    common = dict(S.COMMON)
+    b = G.HMCBatch([sp["shape"] for sp in specs], specs[0]["Q"], per, precision=G.HMC_FP32,
+                   mpm_steps_per_mcs=50, **common)
+    try:
+        b.set_orientations(euler, fields)
+        b.mc_sweeps(5)
+        kw = dict(common)
+        kw.update(per[0])
+        solo = G.HMC(specs[0]["shape"], specs[0]["Q"], precision=G.HMC_FP32, mpm_steps_per_mcs=50, **kw)
+        solo.set_orientations(euler, fields[0])
+        solo.mc_sweeps(5)
+        assert (solo.spins() == b.spins(0)).all()
+        solo.close()
+        acc = b.mc_sweeps(195)
+        assert acc > 0
+        for r, sp in enumerate(specs):
+            s = b.spins(r)
+            assert s.shape == tuple(sp["shape"]) and int(s.max()) < sp["Q"], r
+            assert (s != fields[r]).any(), r
+            assert np.all(np.isfinite(b.strain(r))), r
+    finally:
+        b.close()
